@@ -1,0 +1,199 @@
+/*
+ * a2ls.h -- C ABI of the GB300 algebraic two-level Schwarz library (libA2LS.so).
+ *
+ * The library builds and applies the fully algebraic two-level overlapping
+ * Schwarz preconditioner of Al Daas, Jolivet and Rees (arXiv 2201.02250) and
+ * solves A x = b with it inside restarted GMRES, entirely on one GPU.
+ *
+ *   setup  : overlap grown from the adjacency graph of A (Section 2), local
+ *            matrices A_ii and block splittings A~_ii (Definition 3.1), batched
+ *            dense LU of the local matrices, the local generalized eigenproblems
+ *            of Eq. 3.1 with the selection of Eq. 3.2, the coarse operator
+ *            A_00 = R_0 A R_0^H and its exact LU (Section 4).
+ *   apply  : the restricted two-level preconditioner with deflated coarse
+ *            correction, Eq. 2.4 (default), or the variants of Section 2.
+ *   solve  : right-preconditioned GMRES(restart) with zero-free initial guess
+ *            (Section 4); flexible GMRES when the local solves run in FP32.
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers documented as "device" must point to memory of the current CUDA
+ *     device; "host" pointers to ordinary host memory.  The caller owns every
+ *     buffer it passes; the library copies what it keeps.
+ *   - All work is issued on the stream given in a2ls_options::stream (NULL =
+ *     the legacy default stream).  Entry points that return results to the
+ *     host synchronise that stream; a2ls_apply does not.
+ *   - Every function returns an a2ls_status; nothing aborts or traps.  On
+ *     failure a human-readable message is available from a2ls_last_error()
+ *     (thread-local, valid until the next call on the same thread).
+ *   - Indices are 0-based int32; n and nnz must fit in int32.  Only real
+ *     (double) matrices are supported.
+ */
+#ifndef A2LS_H
+#define A2LS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  A2LS_OK = 0,
+  A2LS_ERR_ARG = 1,           /* invalid argument (sizes, CSR structure, partition) */
+  A2LS_ERR_SINGULAR = 2,      /* zero or tiny pivot in a local or coarse LU (the paper's failure mark) */
+  A2LS_ERR_NOT_CONVERGED = 3, /* max_it reached; x holds the last iterate */
+  A2LS_ERR_EIGEN = 4,         /* local eigenproblem outside what the solver supports or not converged */
+  A2LS_ERR_TIMEOUT = 5,       /* a bounded device-side wait expired */
+  A2LS_ERR_CUDA = 6,          /* a CUDA runtime error */
+  A2LS_ERR_OOM = 7,           /* device allocation failed */
+  A2LS_ERR_STATE = 8          /* call not valid in the handle's current state */
+} a2ls_status;
+
+/* Precision of the local factors, local solves and local eigensolves.  The
+ * SpMV, the GMRES orthogonalisation, the residual and the coarse operator are
+ * always FP64. */
+enum { A2LS_FP64 = 0, A2LS_FP32 = 1 };
+
+/* Preconditioner variants (Section 2).  DEFLATED_RAS is Eq. 2.4, the one the
+ * paper uses in all experiments. */
+enum {
+  A2LS_DEFLATED_RAS = 0, /* R0^H A00^-1 R0 + M_RAS^-1 (I - A R0^H A00^-1 R0)  (Eq. 2.4) */
+  A2LS_DEFLATED_ASM = 1, /* same with M_ASM^-1 */
+  A2LS_ADDITIVE_RAS = 2, /* R0^H A00^-1 R0 + M_RAS^-1 */
+  A2LS_ADDITIVE_ASM = 3, /* R0^H A00^-1 R0 + M_ASM^-1                          (Eq. 2.2) */
+  A2LS_ONE_LEVEL_RAS = 4,/* M_RAS^-1                                           (Eq. 2.3) */
+  A2LS_ONE_LEVEL_ASM = 5 /* M_ASM^-1                                           (Eq. 2.1) */
+};
+
+/* Partition of unity D_i (Section 2): BOOLEAN puts 1 on the interior nodes
+ * Omega_Ii and 0 on the overlap Omega_Gamma_i; MULTIPLICITY puts 1/k(j) on
+ * every node j of Omega_i, k(j) = number of subdomains containing j. */
+enum { A2LS_POU_BOOLEAN = 0, A2LS_POU_MULTIPLICITY = 1 };
+
+typedef struct a2ls_handle a2ls_handle;
+
+/* Sparse matrix in CSR form.  All arrays are device pointers owned by the
+ * caller and only read during a2ls_setup (the library keeps its own copy).
+ * rowptr: n+1 entries, rowptr[0] = 0, non-decreasing, rowptr[n] = nnz.
+ * colind: nnz entries in [0, n).  val: nnz doubles. */
+typedef struct {
+  int32_t n;
+  int32_t nnz;
+  const int32_t* rowptr;
+  const int32_t* colind;
+  const double* val;
+} a2ls_csr;
+
+typedef struct {
+  int32_t precision;        /* A2LS_FP64 (default) or A2LS_FP32 */
+  int32_t variant;          /* A2LS_DEFLATED_RAS (default) ... */
+  int32_t pou;              /* A2LS_POU_BOOLEAN (default) or A2LS_POU_MULTIPLICITY */
+  int32_t restart;          /* GMRES restart length, default 30 (Section 4) */
+  int32_t max_it;           /* total inner iterations, default 1000 */
+  int32_t flexible;         /* -1: automatic (FGMRES iff precision != FP64), 0: GMRES, 1: FGMRES */
+  double tau;               /* <= 0: keep nev eigenpairs per subdomain; > 0: keep |lambda| > 1/tau,
+                               at most nev (Eq. 3.2) */
+  int32_t eig_block_steps;  /* block Krylov steps per eigen restart cycle, default 3 */
+  int32_t eig_max_cycles;   /* eigen restart cycles, default 60 */
+  double eig_tol;           /* relative eigen-residual target, default 1e-10 (FP64) / 1e-5 (FP32) when 0 */
+  uint64_t seed;            /* seed of the eigensolver's random start blocks */
+  void* stream;             /* cudaStream_t for all work; NULL = legacy default stream */
+} a2ls_options;
+
+/* Fills *opt with the defaults listed above.  Never fails. */
+void a2ls_default_options(a2ls_options* opt);
+
+/*
+ * a2ls_setup -- build the preconditioner for A.
+ *   A         : CSR matrix (device arrays, see a2ls_csr).
+ *   partition : device, n int32 values in [0, N); every part non-empty.  This is
+ *               the non-overlapping partition Omega_Ii of Section 2 (the paper
+ *               obtains it from ParMETIS; here it is an input).
+ *   overlap   : number of adjacency layers delta >= 0 added around each part
+ *               (Section 2 defines one layer; delta layers repeat it).
+ *   nev       : eigenpairs kept per subdomain (Eq. 3.2; with tau > 0 an upper bound).
+ *   opt       : options, or NULL for the defaults.
+ *   out       : receives the new handle on success, NULL on failure.
+ * Synchronises opt->stream.  Errors: ARG (bad sizes/CSR/partition), SINGULAR
+ * (tiny pivot in a local or the coarse LU), EIGEN, CUDA, OOM.
+ */
+int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int32_t nev,
+               const a2ls_options* opt, a2ls_handle** out);
+
+/*
+ * a2ls_apply -- z = M^{-1} r for the handle's variant (Eq. 2.4 by default).
+ *   r, z : device, n doubles each; they must not alias.
+ * Asynchronous on the handle's stream (no host synchronisation).
+ */
+int a2ls_apply(a2ls_handle* h, const double* r, double* z);
+
+/*
+ * a2ls_solve -- right-preconditioned restarted (F)GMRES for A x = b (Section 4).
+ *   b      : device, n doubles.
+ *   x      : device, n doubles; on entry the initial guess (the paper uses 0),
+ *            on exit the last iterate.
+ *   rtol   : relative tolerance on the true residual ||b - A x|| / ||b||.
+ *   iters  : host, receives the number of inner iterations (may be NULL).
+ *   relres : host, receives the final true relative residual (may be NULL).
+ * Returns OK or NOT_CONVERGED (x still valid); synchronises the stream.
+ */
+int a2ls_solve(a2ls_handle* h, const double* b, double* x, double rtol, int32_t* iters,
+               double* relres);
+
+/* Releases every device resource of the handle.  NULL is ignored. */
+void a2ls_destroy(a2ls_handle* h);
+
+/* Message describing the last failure on this thread ("" if none). */
+const char* a2ls_last_error(void);
+
+/* Items for a2ls_query.  All results are copied to host memory. */
+enum {
+  A2LS_Q_SIZES = 0,      /* int64[8]: n, N, n0, sum n_i, max n_i, sum m_i rows stored, precision, variant */
+  A2LS_Q_SUBDOMAINS = 1, /* int32[(N+1) + N + sum n_i]: offsets, n_I per subdomain, local->global
+                            indices (each subdomain: Omega_Ii ascending, then Omega_Gamma_i ascending) */
+  A2LS_Q_LUMP = 2,       /* double[sum n_i]: s_i of Definition 3.1 on overlap rows, 0 on interior rows */
+  A2LS_Q_FACTORS = 3,    /* (precision type)[sum over i of n_i*ld_i] then int64[N+1] offsets and
+                            int32[N] ld: LU of A_ii without pivoting, row-major, unit-lower L below
+                            the diagonal; each 64x64 diagonal tile holds inv(L_bb) strictly below
+                            its diagonal and inv(U_bb) on and above it */
+  A2LS_Q_COARSE = 4,     /* int32[N] m_i, then double[sum n_i*m_i]: W_i = orth(D_i Z_i), n_i x m_i
+                            row-major per subdomain in the local order of A2LS_Q_SUBDOMAINS */
+  A2LS_Q_EIGVALS = 5,    /* double[2*N*nev_max]: per subdomain the kept eigenvalues (re, im),
+                            kernel part first as (+inf, 0), unused slots NaN; nev_max = max(nev,1)+1 */
+  A2LS_Q_TIMES = 6,      /* double[16]: per-phase milliseconds of the last setup and solve */
+  A2LS_Q_EINV = 7,       /* double[n0*n0]: the inverse of A_00 used by the apply, row-major */
+  A2LS_Q_EIGSTATS = 8    /* int32[2*N]: eigen cycles run and kernel dimension per subdomain */
+};
+
+/*
+ * a2ls_query -- copy one internal quantity to host memory (inspection and tests).
+ *   what     : an A2LS_Q_* item.
+ *   out      : host buffer of at least `capacity` bytes, or NULL to only ask the size.
+ *   needed   : host, receives the bytes the item needs (may be NULL).
+ * Returns ARG if capacity is too small.  Synchronises the stream.
+ */
+int a2ls_query(a2ls_handle* h, int32_t what, void* out, int64_t capacity, int64_t* needed);
+
+/*
+ * a2ls_set_coarse_basis -- replace the coarse space by a given one.
+ *   m : host, N int32, columns per subdomain.
+ *   W : host, doubles, for each subdomain in order an n_i x m_i row-major block in
+ *       the local order of A2LS_Q_SUBDOMAINS (rows on Omega_Gamma_i are used as given).
+ * Rebuilds A_00 = R_0 A R_0^H with R_0^H = [R_1^T W_1 ... R_N^T W_N] and its inverse.
+ * Used to compare the apply against another implementation with the same basis
+ * (the apply is invariant to the choice of basis of the coarse space).
+ */
+int a2ls_set_coarse_basis(a2ls_handle* h, const int32_t* m, const double* W);
+
+/*
+ * a2ls_spmv -- y = A x with the handle's FP64 copy of A (x, y: device, n doubles).
+ * Asynchronous on the handle's stream.
+ */
+int a2ls_spmv(a2ls_handle* h, const double* x, double* y);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* A2LS_H */

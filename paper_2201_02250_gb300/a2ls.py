@@ -1,0 +1,255 @@
+"""Thin Python binding of libA2LS (include/a2ls.h) over ctypes.
+
+Argument marshalling only: every step of setup, apply and solve runs in the
+CUDA library.  PyTorch provides device memory and the current stream.  The
+binding fails loudly when the library is missing; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import _build
+
+A2LS_OK, A2LS_ERR_ARG, A2LS_ERR_SINGULAR, A2LS_ERR_NOT_CONVERGED = 0, 1, 2, 3
+A2LS_ERR_EIGEN, A2LS_ERR_TIMEOUT, A2LS_ERR_CUDA, A2LS_ERR_OOM, A2LS_ERR_STATE = 4, 5, 6, 7, 8
+FP64, FP32 = 0, 1
+VARIANTS = {"deflated_ras": 0, "deflated_asm": 1, "additive_ras": 2, "additive_asm": 3, "ras": 4, "asm": 5}
+POU = {"boolean": 0, "multiplicity": 1}
+Q_SIZES, Q_SUBDOMAINS, Q_LUMP, Q_FACTORS, Q_COARSE, Q_EIGVALS, Q_TIMES, Q_EINV, Q_EIGSTATS = range(9)
+PHASES = ["graph", "extract", "lu", "eig_coarse", "coarse", "setup_total", "solve_total", "apply"]
+
+
+class A2lsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"a2ls error {code}: {msg}")
+        self.code = code
+
+
+class CSR(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32), ("rowptr", ctypes.c_void_p),
+                ("colind", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("variant", ctypes.c_int32), ("pou", ctypes.c_int32),
+                ("restart", ctypes.c_int32), ("max_it", ctypes.c_int32), ("flexible", ctypes.c_int32),
+                ("tau", ctypes.c_double), ("eig_block_steps", ctypes.c_int32),
+                ("eig_max_cycles", ctypes.c_int32), ("eig_tol", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+
+
+_LIB = None
+
+
+def header_functions() -> list:
+    """Names of the functions declared in include/a2ls.h."""
+    path = os.path.join(_build.ROOT, "include", "a2ls.h")
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(a2ls_\w+)\s*\(", text)))
+
+
+def lib(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libA2LS.so (building it first if it is missing)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libA2LS.so not found at {path}; run __graft_entry__.build()")
+        _build.build()
+    L = ctypes.CDLL(path)
+    vp, i32, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    L.a2ls_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.a2ls_default_options.restype = None
+    L.a2ls_setup.argtypes = [ctypes.POINTER(CSR), vp, i32, i32, ctypes.POINTER(Options), ctypes.POINTER(vp)]
+    L.a2ls_apply.argtypes = [vp, vp, vp]
+    L.a2ls_solve.argtypes = [vp, vp, vp, f64, ctypes.POINTER(i32), ctypes.POINTER(f64)]
+    L.a2ls_destroy.argtypes = [vp]
+    L.a2ls_destroy.restype = None
+    L.a2ls_last_error.argtypes = []
+    L.a2ls_last_error.restype = ctypes.c_char_p
+    L.a2ls_query.argtypes = [vp, i32, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    L.a2ls_set_coarse_basis.argtypes = [vp, vp, vp]
+    L.a2ls_spmv.argtypes = [vp, vp, vp]
+    for f in ("a2ls_setup", "a2ls_apply", "a2ls_solve", "a2ls_query", "a2ls_set_coarse_basis", "a2ls_spmv"):
+        getattr(L, f).restype = ctypes.c_int
+    _LIB = L
+    return L
+
+
+def _check(rc: int, allow=()):
+    if rc != A2LS_OK and rc not in allow:
+        raise A2lsError(rc, lib().a2ls_last_error().decode())
+    return rc
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().a2ls_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "variant" and isinstance(v, str):
+            v = VARIANTS[v]
+        if k == "pou" and isinstance(v, str):
+            v = POU[v]
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": FP64, "fp32": FP32}[v]
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr())
+
+
+class Preconditioner:
+    """Handle on a set-up two-level Schwarz preconditioner (device data owned by the library).
+
+    rowptr, colind (int32), val (float64) and part (int32) are CUDA tensors.
+    """
+
+    def __init__(self, rowptr, colind, val, part, overlap: int, nev: int, stream=None, **opts):
+        import torch
+        for t, dt in ((rowptr, torch.int32), (colind, torch.int32), (val, torch.float64), (part, torch.int32)):
+            if not t.is_cuda or t.dtype != dt or not t.is_contiguous():
+                raise ValueError("CSR and partition must be contiguous CUDA tensors (int32 / float64)")
+        self.n = int(rowptr.numel() - 1)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        o = default_options(**opts)
+        o.stream = ctypes.c_void_p(int(stream.cuda_stream))
+        self.options = o
+        csr = CSR(self.n, int(colind.numel()), _ptr(rowptr), _ptr(colind), _ptr(val))
+        h = ctypes.c_void_p()
+        _check(lib().a2ls_setup(ctypes.byref(csr), ctypes.c_void_p(_ptr(part)), int(overlap), int(nev),
+                                ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().a2ls_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, r, z):
+        _check(lib().a2ls_apply(self._h, ctypes.c_void_p(_ptr(r)), ctypes.c_void_p(_ptr(z))))
+
+    def spmv(self, x, y):
+        _check(lib().a2ls_spmv(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(y))))
+
+    def solve(self, b, x, rtol: float = 1e-8, allow_not_converged: bool = False):
+        it = ctypes.c_int32()
+        rr = ctypes.c_double()
+        rc = lib().a2ls_solve(self._h, ctypes.c_void_p(_ptr(b)), ctypes.c_void_p(_ptr(x)), float(rtol),
+                              ctypes.byref(it), ctypes.byref(rr))
+        _check(rc, allow=(A2LS_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return int(it.value), float(rr.value), rc == A2LS_OK
+
+    # --- queries ------------------------------------------------------------------
+    def _query(self, what: int) -> bytes:
+        need = ctypes.c_int64()
+        _check(lib().a2ls_query(self._h, what, None, 0, ctypes.byref(need)))
+        buf = ctypes.create_string_buffer(max(int(need.value), 1))
+        _check(lib().a2ls_query(self._h, what, buf, int(need.value), None))
+        return buf.raw[:int(need.value)]
+
+    def sizes(self) -> dict:
+        s = np.frombuffer(self._query(Q_SIZES), dtype=np.int64)
+        return {"n": int(s[0]), "N": int(s[1]), "n0": int(s[2]), "sum_ni": int(s[3]), "max_ni": int(s[4]),
+                "w_elems": int(s[5]), "precision": int(s[6]), "variant": int(s[7])}
+
+    def subdomains(self) -> list:
+        """[(interior indices, overlap indices)] per subdomain, in the library's local order."""
+        N = self.sizes()["N"]
+        raw = np.frombuffer(self._query(Q_SUBDOMAINS), dtype=np.int32)
+        off, nI, idx = raw[:N + 1], raw[N + 1:2 * N + 1], raw[2 * N + 1:]
+        return [(idx[off[i]:off[i] + nI[i]].copy(), idx[off[i] + nI[i]:off[i + 1]].copy()) for i in range(N)]
+
+    def lump(self) -> list:
+        N = self.sizes()["N"]
+        raw = np.frombuffer(self._query(Q_SUBDOMAINS), dtype=np.int32)
+        off = raw[:N + 1]
+        s = np.frombuffer(self._query(Q_LUMP), dtype=np.float64)
+        return [s[off[i]:off[i + 1]].copy() for i in range(N)]
+
+    def factors(self) -> list:
+        """Per subdomain the stored block-inverted LU (n_i x n_i, float64 view)."""
+        sz = self.sizes()
+        N = sz["N"]
+        raw = self._query(Q_FACTORS)
+        es = 8 if sz["precision"] == FP64 else 4
+        tail = (N + 1) * 8 + N * 4
+        vals = np.frombuffer(raw[:len(raw) - tail], dtype=np.float64 if es == 8 else np.float32)
+        foff = np.frombuffer(raw[len(raw) - tail:len(raw) - N * 4], dtype=np.int64)
+        ld = np.frombuffer(raw[len(raw) - N * 4:], dtype=np.int32)
+        subs = self.subdomains()
+        out = []
+        for i in range(N):
+            n_i = len(subs[i][0]) + len(subs[i][1])
+            F = vals[foff[i]:foff[i] + n_i * ld[i]].reshape(n_i, ld[i])[:, :n_i].astype(np.float64)
+            out.append(F)
+        return out
+
+    def coarse_basis(self) -> list:
+        N = self.sizes()["N"]
+        raw = self._query(Q_COARSE)
+        m = np.frombuffer(raw[:4 * N], dtype=np.int32)
+        W = np.frombuffer(raw[4 * N:], dtype=np.float64)
+        subs = self.subdomains()
+        out, o = [], 0
+        for i in range(N):
+            n_i = len(subs[i][0]) + len(subs[i][1])
+            out.append(W[o:o + n_i * m[i]].reshape(n_i, m[i]).copy())
+            o += n_i * m[i]
+        return out
+
+    def eigenvalues(self) -> np.ndarray:
+        N = self.sizes()["N"]
+        ev = np.frombuffer(self._query(Q_EIGVALS), dtype=np.float64)
+        if ev.size == 0:
+            return np.zeros((N, 0), dtype=complex)
+        ev = ev.reshape(N, -1, 2)
+        return ev[..., 0] + 1j * ev[..., 1]
+
+    def eig_stats(self) -> np.ndarray:
+        N = self.sizes()["N"]
+        s = np.frombuffer(self._query(Q_EIGSTATS), dtype=np.int32)
+        return s.reshape(N, 2) if s.size else np.zeros((N, 2), dtype=np.int32)
+
+    def times(self) -> dict:
+        t = np.frombuffer(self._query(Q_TIMES), dtype=np.float64)
+        return {k: float(t[i]) for i, k in enumerate(PHASES)}
+
+    def coarse_inverse(self) -> np.ndarray:
+        n0 = self.sizes()["n0"]
+        return np.frombuffer(self._query(Q_EINV), dtype=np.float64).reshape(n0, n0).copy()
+
+    def set_coarse_basis(self, W: list):
+        m = np.array([w.shape[1] for w in W], dtype=np.int32)
+        flat = np.concatenate([np.ascontiguousarray(w, dtype=np.float64).ravel() for w in W]) if len(W) else \
+            np.zeros(1)
+        flat = np.ascontiguousarray(flat)
+        _check(lib().a2ls_set_coarse_basis(self._h, m.ctypes.data_as(ctypes.c_void_p),
+                                           flat.ctypes.data_as(ctypes.c_void_p)))
+
+
+def from_scipy(A, part, overlap: int, nev: int, device: str = "cuda", **opts):
+    """Upload a scipy CSR matrix and partition, then set up; returns (Preconditioner, device tensors)."""
+    import torch
+    rowptr = torch.as_tensor(np.asarray(A.indptr, dtype=np.int32), device=device)
+    colind = torch.as_tensor(np.asarray(A.indices, dtype=np.int32), device=device)
+    val = torch.as_tensor(np.asarray(A.data, dtype=np.float64), device=device)
+    p = torch.as_tensor(np.asarray(part, dtype=np.int32), device=device)
+    P = Preconditioner(rowptr, colind, val, p, overlap, nev, **opts)
+    return P, (rowptr, colind, val, p)

@@ -1,0 +1,159 @@
+// Internal declarations shared by the a2ls CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/a2ls.h"
+
+namespace a2ls {
+
+// ---------------------------------------------------------------------------
+// Errors: internal code throws, the C ABI converts to a status + message.
+// ---------------------------------------------------------------------------
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+[[noreturn]] void fail(int code, const char* fmt, ...);
+void check_cuda(cudaError_t e, const char* what, const char* file, int line);
+#define A2LS_CUDA(x) ::a2ls::check_cuda((x), #x, __FILE__, __LINE__)
+#define A2LS_LAUNCH() ::a2ls::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+
+// Device-side status words written by kernels (never trap): [0] first error
+// code, [1] the subdomain or row that raised it, [2] auxiliary information.
+enum { ST_CODE = 0, ST_WHERE = 1, ST_AUX = 2, ST_WORDS = 8 };
+
+__device__ __forceinline__ void raise_status(int* st, int code, int where, int aux) {
+  if (atomicCAS(st + ST_CODE, 0, code) == 0) {
+    st[ST_WHERE] = where;
+    st[ST_AUX] = aux;
+  }
+}
+
+// Tile size of the block-inverted LU format used by all triangular solves.
+constexpr int TB = 64;
+// Largest number of coarse columns per subdomain.
+constexpr int MAXM = 64;
+// Largest subdomain size handled by the dense kernels (vector held in shared memory).
+constexpr int MAXN_LOCAL = 8192;
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// The handle: every device array the preconditioner owns.
+// ---------------------------------------------------------------------------
+struct Phase { enum { SETUP_GRAPH, SETUP_EXTRACT, SETUP_LU, SETUP_EIG, SETUP_COARSE, SETUP_TOTAL,
+                      SOLVE_TOTAL, SOLVE_APPLY, COUNT }; };
+
+}  // namespace a2ls
+
+struct a2ls_handle {
+  // problem
+  int n = 0, nnz = 0, N = 0, delta = 0, nev = 0;
+  a2ls_options opt{};
+  cudaStream_t st = nullptr;
+  std::vector<void*> allocs;     // device allocations owned by the handle
+  int* d_status = nullptr;       // ST_WORDS ints
+
+  // FP64 copy of A and of the partition
+  int *rowptr = nullptr, *colind = nullptr;
+  double* val = nullptr;
+  int* part = nullptr;
+
+  // subdomains: local order = [Omega_I ascending, Omega_Gamma ascending]
+  std::vector<int> h_off, h_nI, h_n, h_ld;   // h_off has N+1 entries
+  std::vector<int64_t> h_foff;               // offsets of dense local matrices (elements), N+1
+  int *d_off = nullptr, *d_nI = nullptr, *d_ni = nullptr, *d_ld = nullptr;
+  int64_t* d_foff = nullptr;
+  int* d_idx = nullptr;                      // sum n_i: local -> global
+  int* d_ipos = nullptr;                     // n: local index of a node inside its own part
+  int sum_n = 0, max_n = 0;
+  int max_rownnz = 0, max_memb = 0;          // largest row of A, largest membership count
+  // node -> memberships (flat local positions off_i + l), sorted by subdomain
+  int *d_mrow = nullptr, *d_mpos = nullptr, *d_msub = nullptr;
+  double* d_D = nullptr;                     // sum n_i partition-of-unity weights
+  double* d_lump = nullptr;                  // sum n_i: s_i on overlap rows, 0 elsewhere
+  // local CSR of A restricted to Omega_i (local column or -1 if outside), one row per local row
+  int64_t* d_lrow = nullptr;                 // sum n_i + 1
+  int* d_lcol = nullptr;
+  double* d_lval = nullptr;
+
+  // local factors (block-inverted LU, precision = opt.precision)
+  void* d_fac = nullptr;
+  size_t fac_elems = 0;
+
+  // coarse space
+  int n0 = 0;
+  std::vector<int> h_m, h_coff;              // N, N+1
+  std::vector<int64_t> h_woff;               // N+1, offsets of W_i (n_i x m_i)
+  int *d_m = nullptr, *d_coff = nullptr;
+  int64_t* d_woff = nullptr;
+  double* d_W = nullptr;
+  double* d_Einv = nullptr;                  // n0 x n0 row-major
+  std::vector<double> h_eigvals;             // 2*N*(nevmax)
+  std::vector<int> h_eigstats;               // 2*N
+
+  // apply workspace
+  double *d_g = nullptr, *d_c = nullptr, *d_q = nullptr, *d_t = nullptr, *d_yloc = nullptr;
+  double* d_red = nullptr;                   // reduction scratch
+
+  // GMRES workspace
+  int gm_restart = 0;
+  double *d_V = nullptr, *d_Z = nullptr, *d_w = nullptr, *d_h = nullptr, *d_part = nullptr;
+  double* h_pinned = nullptr;                // pinned host scratch for small readbacks
+
+  double times[16] = {0};
+};
+
+namespace a2ls {
+
+// allocation helpers (stream-ordered, owned by the handle)
+void* dalloc_bytes(a2ls_handle* h, size_t bytes);
+template <class T> T* dalloc(a2ls_handle* h, size_t count) {
+  return static_cast<T*>(dalloc_bytes(h, count * sizeof(T) + (count == 0 ? 16 : 0)));
+}
+void dfree(a2ls_handle* h, void* p);
+void sync_and_check(a2ls_handle* h, const char* phase);
+
+// ---------------------------------------------------------------------------
+// Launchers implemented in the .cu files.
+// ---------------------------------------------------------------------------
+// k_graph.cu
+void build_subdomains(a2ls_handle* h);                 // validation, overlap, lists, memberships
+void extract_local(a2ls_handle* h, void* dense_A, double* dense_At, double* dense_scale);
+void exclusive_scan_i64(const int64_t* in, int64_t* out, int n, cudaStream_t st, a2ls_handle* h);
+
+// k_dense.cu
+template <class T> void lu_batched(a2ls_handle* h, T* fac, int allow_last_zero, double* last_pivot,
+                                   double* diag_scale);
+template <class T> void invert_diag_tiles(a2ls_handle* h, T* fac);
+// y_loc / z output of the RAS/ASM local solves; see k_dense.cu for the modes
+template <class T> void local_solves(a2ls_handle* h, const T* fac, const double* t, const double* q,
+                                     double* z, int mode);
+void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv);
+template <class T> void block_solve(a2ls_handle* h, const T* fac, T* X, const int64_t* xoff, int col0, int ldx,
+                                    const int* pvec, const int* active, int forward, int backward);
+
+// k_eig.cu
+void eigensolve(a2ls_handle* h, double* fac_tilde, const double* last_pivot, const double* diag_scale);
+
+// k_coarse.cu
+void orthonormalize_and_set_W(a2ls_handle* h, double* Z, const int* mcols, int ldz_max);
+void upload_coarse_layout(a2ls_handle* h, const std::vector<int>& m);
+void build_coarse_operator(a2ls_handle* h);
+
+// k_krylov.cu
+void spmv(a2ls_handle* h, const double* x, double* y, const double* b_minus, cudaStream_t st);
+void apply_preconditioner(a2ls_handle* h, const double* r, double* z);
+double dot(a2ls_handle* h, const double* x, const double* y);
+double nrm2(a2ls_handle* h, const double* x);
+int gmres(a2ls_handle* h, const double* b, double* x, double rtol, int* iters, double* relres);
+
+}  // namespace a2ls

@@ -1,0 +1,399 @@
+// C ABI of libA2LS: argument checks, setup orchestration, queries.
+#include "a2ls_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+
+namespace a2ls {
+
+static thread_local std::string g_last_error;
+
+void fail(int code, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  throw Error(code, buf);
+}
+
+void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
+  if (e == cudaSuccess) return;
+  const char* base = strrchr(file, '/');
+  fail(e == cudaErrorMemoryAllocation ? A2LS_ERR_OOM : A2LS_ERR_CUDA, "%s failed: %s (%s:%d)", what,
+       cudaGetErrorString(e), base ? base + 1 : file, line);
+}
+
+void* dalloc_bytes(a2ls_handle* h, size_t bytes) {
+  void* p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, std::max<size_t>(bytes, 16), h->st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(A2LS_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  h->allocs.push_back(p);
+  return p;
+}
+
+void dfree(a2ls_handle* h, void* p) {
+  if (!p) return;
+  auto it = std::find(h->allocs.begin(), h->allocs.end(), p);
+  if (it != h->allocs.end()) {
+    h->allocs.erase(it);
+    cudaFreeAsync(p, h->st);
+  }
+}
+
+static const char* status_name(int c) {
+  switch (c) {
+    case A2LS_ERR_ARG: return "invalid argument";
+    case A2LS_ERR_SINGULAR: return "singular pivot";
+    case A2LS_ERR_EIGEN: return "eigensolver";
+    case A2LS_ERR_TIMEOUT: return "device wait timed out";
+    default: return "device error";
+  }
+}
+
+void sync_and_check(a2ls_handle* h, const char* phase) {
+  A2LS_CUDA(cudaStreamSynchronize(h->st));
+  int s[ST_WORDS];
+  A2LS_CUDA(cudaMemcpy(s, h->d_status, sizeof(s), cudaMemcpyDeviceToHost));
+  if (s[ST_CODE] != 0) {
+    const int code = s[ST_CODE];
+    int zero[ST_WORDS] = {0};
+    A2LS_CUDA(cudaMemcpy(h->d_status, zero, sizeof(zero), cudaMemcpyHostToDevice));
+    fail(code, "%s: %s (where=%d, info=%d)", phase, status_name(code), s[ST_WHERE], s[ST_AUX]);
+  }
+}
+
+static void set_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+template <class F>
+static int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const Error& e) {
+    set_error(e.what());
+    return e.code;
+  } catch (const std::exception& e) {
+    set_error(e.what());
+    return A2LS_ERR_CUDA;
+  } catch (...) {
+    set_error("unknown error");
+    return A2LS_ERR_CUDA;
+  }
+}
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t st;
+  explicit Timer(cudaStream_t s) : st(s) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+  }
+  double stop() {
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventRecord(a, st);
+    return ms;
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+__global__ void k_max_rowlen(int n, const int* rowptr, const int* mrow, int* out) {
+  int a = 0, b = 0;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    a = max(a, rowptr[r + 1] - rowptr[r]);
+    b = max(b, mrow[r + 1] - mrow[r]);
+  }
+  atomicMax(out, a);
+  atomicMax(out + 1, b);
+}
+
+static void destroy_handle(a2ls_handle* h) {
+  if (!h) return;
+  for (void* p : h->allocs) cudaFreeAsync(p, h->st);
+  h->allocs.clear();
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  cudaStreamSynchronize(h->st);
+  delete h;
+}
+
+template <class T>
+static void factor_and_coarse(a2ls_handle* h, bool need_coarse, double* times) {
+  cudaStream_t st = h->st;
+  Timer tm(st);
+  const int N = h->N;
+  T* fa = dalloc<T>(h, h->fac_elems);
+  double* ft = need_coarse ? dalloc<double>(h, h->fac_elems) : nullptr;  // eigensolve always FP64
+  double* dscale = dalloc<double>(h, N);
+  double* lastp = dalloc<double>(h, N);
+  extract_local(h, fa, ft, dscale);
+  sync_and_check(h, "local matrix extraction");
+  times[Phase::SETUP_EXTRACT] = tm.stop();
+  lu_batched<T>(h, fa, 0, nullptr, dscale);
+  invert_diag_tiles<T>(h, fa);
+  sync_and_check(h, "local LU factorisation");
+  h->d_fac = fa;
+  if (need_coarse) {
+    lu_batched<double>(h, ft, 1, lastp, dscale);
+    invert_diag_tiles<double>(h, ft);
+    sync_and_check(h, "LU factorisation of the local splittings");
+  }
+  times[Phase::SETUP_LU] = tm.stop();
+  if (need_coarse) {
+    eigensolve(h, ft, lastp, dscale);  // ends with the coarse operator
+    dfree(h, ft);
+  }
+  times[Phase::SETUP_EIG] = tm.stop();
+  dfree(h, dscale);
+  dfree(h, lastp);
+}
+
+}  // namespace a2ls
+
+using namespace a2ls;
+
+extern "C" {
+
+void a2ls_default_options(a2ls_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = A2LS_FP64;
+  o->variant = A2LS_DEFLATED_RAS;
+  o->pou = A2LS_POU_BOOLEAN;
+  o->restart = 30;
+  o->max_it = 1000;
+  o->flexible = -1;
+  o->tau = 0.0;
+  o->eig_block_steps = 3;
+  o->eig_max_cycles = 60;
+  o->eig_tol = 0.0;
+  o->seed = 12345;
+  o->stream = nullptr;
+}
+
+const char* a2ls_last_error(void) { return g_last_error.c_str(); }
+
+int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int32_t nev,
+               const a2ls_options* opt, a2ls_handle** out) {
+  set_error("");
+  if (out) *out = nullptr;
+  a2ls_handle* h = nullptr;
+  int rc = guarded([&]() -> int {
+    if (!A || !out || !partition) fail(A2LS_ERR_ARG, "null argument");
+    if (A->n <= 0) fail(A2LS_ERR_ARG, "n must be positive (got %d)", A->n);
+    if (A->nnz < A->n) fail(A2LS_ERR_ARG, "nnz = %d is smaller than n = %d (every row needs its diagonal)", A->nnz, A->n);
+    if (!A->rowptr || !A->colind || !A->val) fail(A2LS_ERR_ARG, "null CSR array");
+    if (overlap < 0) fail(A2LS_ERR_ARG, "overlap must be >= 0");
+    if (nev < 0) fail(A2LS_ERR_ARG, "nev must be >= 0");
+    a2ls_options o;
+    if (opt) o = *opt; else a2ls_default_options(&o);
+    if (o.precision != A2LS_FP64 && o.precision != A2LS_FP32) fail(A2LS_ERR_ARG, "unknown precision %d", o.precision);
+    if (o.variant < 0 || o.variant > A2LS_ONE_LEVEL_ASM) fail(A2LS_ERR_ARG, "unknown variant %d", o.variant);
+    if (o.pou != A2LS_POU_BOOLEAN && o.pou != A2LS_POU_MULTIPLICITY) fail(A2LS_ERR_ARG, "unknown partition of unity %d", o.pou);
+    if (o.tau > 0) fail(A2LS_ERR_ARG, "threshold selection (tau > 0) is not supported yet; use a fixed nev");
+    h = new a2ls_handle();
+    h->opt = o;
+    h->st = static_cast<cudaStream_t>(o.stream);
+    h->n = A->n;
+    h->nnz = A->nnz;
+    h->delta = overlap;
+    h->nev = nev;
+    cudaStream_t st = h->st;
+    Timer total(st), tm(st);
+    h->d_status = dalloc<int>(h, ST_WORDS);
+    A2LS_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int) * ST_WORDS, st));
+    h->rowptr = dalloc<int>(h, h->n + 1);
+    h->colind = dalloc<int>(h, h->nnz);
+    h->val = dalloc<double>(h, h->nnz);
+    h->part = dalloc<int>(h, h->n);
+    A2LS_CUDA(cudaMemcpyAsync(h->rowptr, A->rowptr, sizeof(int) * (h->n + 1), cudaMemcpyDeviceToDevice, st));
+    A2LS_CUDA(cudaMemcpyAsync(h->colind, A->colind, sizeof(int) * h->nnz, cudaMemcpyDeviceToDevice, st));
+    A2LS_CUDA(cudaMemcpyAsync(h->val, A->val, sizeof(double) * h->nnz, cudaMemcpyDeviceToDevice, st));
+    A2LS_CUDA(cudaMemcpyAsync(h->part, partition, sizeof(int) * h->n, cudaMemcpyDeviceToDevice, st));
+    build_subdomains(h);
+    {
+      int* mm = dalloc<int>(h, 2);
+      A2LS_CUDA(cudaMemsetAsync(mm, 0, sizeof(int) * 2, st));
+      k_max_rowlen<<<std::min(1216, ceil_div(h->n, 256)), 256, 0, st>>>(h->n, h->rowptr, h->d_mrow, mm);
+      A2LS_LAUNCH();
+      int hm[2];
+      A2LS_CUDA(cudaMemcpyAsync(hm, mm, sizeof(hm), cudaMemcpyDeviceToHost, st));
+      A2LS_CUDA(cudaStreamSynchronize(st));
+      h->max_rownnz = hm[0];
+      h->max_memb = hm[1];
+      dfree(h, mm);
+    }
+    h->times[Phase::SETUP_GRAPH] = tm.stop();
+    h->fac_elems = (size_t)h->h_foff[h->N];
+    const int v = o.variant;
+    const bool need_coarse = nev > 0 && v != A2LS_ONE_LEVEL_RAS && v != A2LS_ONE_LEVEL_ASM;
+    if (o.precision == A2LS_FP64) factor_and_coarse<double>(h, need_coarse, h->times);
+    else factor_and_coarse<float>(h, need_coarse, h->times);
+    // apply workspace
+    h->d_q = dalloc<double>(h, h->n);
+    h->d_t = dalloc<double>(h, h->n);
+    h->d_yloc = dalloc<double>(h, h->sum_n);
+    sync_and_check(h, "setup");
+    h->times[Phase::SETUP_TOTAL] = total.stop();
+    *out = h;
+    return A2LS_OK;
+  });
+  if (rc != A2LS_OK && h) {
+    destroy_handle(h);
+    *out = nullptr;
+  }
+  return rc;
+}
+
+int a2ls_apply(a2ls_handle* h, const double* r, double* z) {
+  if (!h || !r || !z) {
+    set_error("null argument");
+    return A2LS_ERR_ARG;
+  }
+  if (r == z) {
+    set_error("r and z must not alias");
+    return A2LS_ERR_ARG;
+  }
+  return guarded([&]() -> int {
+    apply_preconditioner(h, r, z);
+    return A2LS_OK;
+  });
+}
+
+int a2ls_solve(a2ls_handle* h, const double* b, double* x, double rtol, int32_t* iters, double* relres) {
+  if (!h || !b || !x) {
+    set_error("null argument");
+    return A2LS_ERR_ARG;
+  }
+  if (!(rtol > 0)) {
+    set_error("rtol must be positive");
+    return A2LS_ERR_ARG;
+  }
+  return guarded([&]() -> int {
+    Timer tm(h->st);
+    int it = 0;
+    double rr = 0.0;
+    int rc = gmres(h, b, x, rtol, &it, &rr);
+    sync_and_check(h, "solve");
+    h->times[Phase::SOLVE_TOTAL] = tm.stop();
+    if (iters) *iters = it;
+    if (relres) *relres = rr;
+    if (rc == A2LS_ERR_NOT_CONVERGED) set_error("GMRES reached max_it before the tolerance");
+    return rc;
+  });
+}
+
+void a2ls_destroy(a2ls_handle* h) { destroy_handle(h); }
+
+int a2ls_spmv(a2ls_handle* h, const double* x, double* y) {
+  if (!h || !x || !y) {
+    set_error("null argument");
+    return A2LS_ERR_ARG;
+  }
+  return guarded([&]() -> int {
+    spmv(h, x, y, nullptr, h->st);
+    return A2LS_OK;
+  });
+}
+
+int a2ls_query(a2ls_handle* h, int32_t what, void* out, int64_t capacity, int64_t* needed) {
+  if (!h) {
+    set_error("null handle");
+    return A2LS_ERR_ARG;
+  }
+  return guarded([&]() -> int {
+    A2LS_CUDA(cudaStreamSynchronize(h->st));
+    const int N = h->N;
+    std::vector<unsigned char> buf;
+    auto put = [&](const void* p, size_t bytes) {
+      const size_t o = buf.size();
+      buf.resize(o + bytes);
+      if (bytes) std::memcpy(buf.data() + o, p, bytes);
+    };
+    auto put_dev = [&](const void* p, size_t bytes) {
+      const size_t o = buf.size();
+      buf.resize(o + bytes);
+      if (bytes) A2LS_CUDA(cudaMemcpy(buf.data() + o, p, bytes, cudaMemcpyDeviceToHost));
+    };
+    switch (what) {
+      case A2LS_Q_SIZES: {
+        int64_t s[8] = {h->n, N, h->n0, h->sum_n, h->max_n, h->h_woff.empty() ? 0 : h->h_woff[N],
+                        h->opt.precision, h->opt.variant};
+        put(s, sizeof(s));
+        break;
+      }
+      case A2LS_Q_SUBDOMAINS:
+        put(h->h_off.data(), sizeof(int) * (N + 1));
+        put(h->h_nI.data(), sizeof(int) * N);
+        put_dev(h->d_idx, sizeof(int) * h->sum_n);
+        break;
+      case A2LS_Q_LUMP:
+        put_dev(h->d_lump, sizeof(double) * h->sum_n);
+        break;
+      case A2LS_Q_FACTORS: {
+        const size_t es = h->opt.precision == A2LS_FP64 ? 8 : 4;
+        put_dev(h->d_fac, es * h->fac_elems);
+        put(h->h_foff.data(), sizeof(int64_t) * (N + 1));
+        put(h->h_ld.data(), sizeof(int) * N);
+        break;
+      }
+      case A2LS_Q_COARSE: {
+        std::vector<int> m = h->h_m;
+        m.resize(N, 0);
+        put(m.data(), sizeof(int) * N);
+        if (h->d_W && !h->h_woff.empty()) put_dev(h->d_W, sizeof(double) * h->h_woff[N]);
+        break;
+      }
+      case A2LS_Q_EIGVALS:
+        put(h->h_eigvals.data(), sizeof(double) * h->h_eigvals.size());
+        break;
+      case A2LS_Q_TIMES:
+        put(h->times, sizeof(h->times));
+        break;
+      case A2LS_Q_EINV:
+        if (h->d_Einv) put_dev(h->d_Einv, sizeof(double) * (size_t)h->n0 * h->n0);
+        break;
+      case A2LS_Q_EIGSTATS:
+        put(h->h_eigstats.data(), sizeof(int) * h->h_eigstats.size());
+        break;
+      default:
+        fail(A2LS_ERR_ARG, "unknown query item %d", what);
+    }
+    if (needed) *needed = (int64_t)buf.size();
+    if (out) {
+      if (capacity < (int64_t)buf.size()) fail(A2LS_ERR_ARG, "query buffer too small (%lld < %zu)", (long long)capacity, buf.size());
+      std::memcpy(out, buf.data(), buf.size());
+    }
+    return A2LS_OK;
+  });
+}
+
+int a2ls_set_coarse_basis(a2ls_handle* h, const int32_t* m, const double* W) {
+  if (!h || !m) {
+    set_error("null argument");
+    return A2LS_ERR_ARG;
+  }
+  return guarded([&]() -> int {
+    std::vector<int> mv(m, m + h->N);
+    upload_coarse_layout(h, mv);
+    if (h->h_woff[h->N] > 0) {
+      if (!W) fail(A2LS_ERR_ARG, "null W");
+      A2LS_CUDA(cudaMemcpyAsync(h->d_W, W, sizeof(double) * h->h_woff[h->N], cudaMemcpyHostToDevice, h->st));
+    }
+    build_coarse_operator(h);
+    sync_and_check(h, "coarse operator");
+    return A2LS_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,604 @@
+// Batched dense kernels over the subdomains: LU without pivoting (exact local
+// LU of Section 4; no pivoting is needed for the diagonally dominant local
+// matrices of the target problems and a pivot check reports A2LS_ERR_SINGULAR
+// otherwise), inversion of the 64x64 diagonal tiles, and the triangular
+// solves of the apply (single right-hand side) and of the eigensolver
+// (p right-hand sides).
+//
+// Storage of one factored subdomain (n x n, row-major, leading dimension ld):
+// unit-lower L strictly below the diagonal, U on and above it, except inside
+// the 64x64 diagonal tiles, which hold inv(L_bb) strictly below their
+// diagonal and inv(U_bb) on and above it.  A triangular solve is then a
+// sequence of dense matrix-vector products (no sequential substitution).
+#include "a2ls_internal.cuh"
+
+#include <algorithm>
+
+namespace a2ls {
+
+template <class T> struct AccOf;
+template <> struct AccOf<float> { using type = float; };
+template <> struct AccOf<double> { using type = double; };
+
+// ---------------------------------------------------------------------------
+// CTA-wide 64x64 tile product: acc += A(0:M, 0:K) * B(0:K, 0:Nc), 256 threads,
+// each thread owns rows ty*4..ty*4+3 and columns tx*4..tx*4+3.
+// amask: 0 = A as stored, 1 = unit lower (strict lower + 1 on diagonal), 2 = upper.
+// ---------------------------------------------------------------------------
+constexpr int GK = 32;
+
+template <class T, class Acc>
+__device__ __forceinline__ void cta_gemm(const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
+                                         int64_t ldb, int M, int Nc, int K, int amask, Acc (&acc)[4][4],
+                                         Acc* sA, Acc* sB, int bmask = 0) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  for (int k0 = 0; k0 < K; k0 += GK) {
+    // load A(0:64, k0:k0+32) transposed into sA[k][m] and B(k0:k0+32, 0:64) into sB[k][n]
+    for (int e = tid; e < 64 * GK; e += 256) {
+      int m = e / GK, k = e % GK;
+      Acc v = 0;
+      int kk = k0 + k;
+      if (m < M && kk < K) {
+        if (amask == 0) v = (Acc)A[m * lda + kk];
+        else if (amask == 1) v = (kk < m) ? (Acc)A[m * lda + kk] : (kk == m ? (Acc)1 : (Acc)0);
+        else v = (kk >= m) ? (Acc)A[m * lda + kk] : (Acc)0;
+      }
+      sA[k * 65 + m] = v;
+    }
+    for (int e = tid; e < GK * 64; e += 256) {
+      int k = e / 64, c = e % 64;
+      int kk = k0 + k;
+      Acc v = 0;
+      if (c < Nc && kk < K && (bmask != 2 || c >= kk)) v = (Acc)B[kk * ldb + c];
+      sB[k * 65 + c] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < GK; ++k) {
+      Acc a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = sA[k * 65 + ty * 4 + u];
+        b[u] = sB[k * 65 + tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// batched LU without pivoting
+// ---------------------------------------------------------------------------
+constexpr int LU_NB = 32;
+
+template <class T>
+__global__ void __launch_bounds__(256) k_lu(int N, const int* ni, const int* ld, const int64_t* foff,
+                                            T* fac, int allow_last_zero, double* last_pivot,
+                                            const double* dscale, int* st) {
+  using Acc = typename AccOf<T>::type;
+  __shared__ Acc sA[GK * 65], sB[GK * 65];
+  const int i = blockIdx.x;
+  const int n = ni[i];
+  const int64_t L = ld[i];
+  T* A = fac + foff[i];
+  const double scale = dscale[i] > 0 ? dscale[i] : 1.0;
+  const double tiny = (sizeof(T) == 8 ? 1e-14 : 1e-12) * scale;
+  const int tid = threadIdx.x;
+  for (int k0 = 0; k0 < n; k0 += LU_NB) {
+    const int kb = min(LU_NB, n - k0);
+    // 1. unblocked factorisation of the panel A(k0:n, k0:k0+kb)
+    for (int c = k0; c < k0 + kb; ++c) {
+      __syncthreads();
+      double piv = (double)A[c * L + c];
+      if (allow_last_zero && c == n - 1) {
+        // record the last pivot of A~_ii and replace it by the scale; the
+        // eigensolver decides from it whether A~_ii is singular
+        __syncthreads();
+        if (tid == 0) {
+          last_pivot[i] = piv;
+          A[c * L + c] = (T)scale;
+        }
+        break;
+      }
+      if (fabs(piv) <= tiny) {
+        if (tid == 0) raise_status(st, A2LS_ERR_SINGULAR, i, c);
+        piv = scale;
+        __syncthreads();
+        if (tid == 0) A[c * L + c] = (T)piv;
+      }
+      const T pinv = (T)(1.0 / piv);
+      for (int r = c + 1 + tid; r < n; r += 256) A[r * L + c] = A[r * L + c] * pinv;
+      __syncthreads();
+      const int ncols = k0 + kb - 1 - c;
+      if (ncols > 0) {
+        const int rows = n - 1 - c;
+        for (int e = tid; e < rows * ncols; e += 256) {
+          const int r = c + 1 + e / ncols, cc = c + 1 + e % ncols;
+          A[r * L + cc] -= A[r * L + c] * A[c * L + cc];
+        }
+      }
+    }
+    __syncthreads();
+    const int c0 = k0 + kb;
+    if (c0 >= n) break;
+    // 2. U12 = inv(L11) A12 (forward substitution, one column per thread)
+    for (int cc = c0 + tid; cc < n; cc += 256) {
+      for (int r = 1; r < kb; ++r) {
+        Acc s = (Acc)A[(k0 + r) * L + cc];
+        for (int q = 0; q < r; ++q) s -= (Acc)A[(k0 + r) * L + k0 + q] * (Acc)A[(k0 + q) * L + cc];
+        A[(k0 + r) * L + cc] = (T)s;
+      }
+    }
+    __syncthreads();
+    // 3. A22 -= L21 U12 in 64x64 tiles
+    const int m = n - c0;
+    const int tiles = (m + 63) / 64;
+    for (int t = 0; t < tiles * tiles; ++t) {
+      const int tr = c0 + (t / tiles) * 64, tc = c0 + (t % tiles) * 64;
+      Acc acc[4][4] = {};
+      cta_gemm<T, Acc>(A + tr * L + k0, L, A + k0 * L + tc, L, min(64, n - tr), min(64, n - tc), kb, 0,
+                       acc, sA, sB);
+      const int tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int r = tr + ty * 4 + u, c = tc + tx * 4 + v;
+          if (r < n && c < n) A[r * L + c] = (T)((Acc)A[r * L + c] - acc[u][v]);
+        }
+    }
+  }
+}
+
+template <class T>
+void lu_batched(a2ls_handle* h, T* fac, int allow_last_zero, double* last_pivot, double* diag_scale) {
+  k_lu<T><<<h->N, 256, 0, h->st>>>(h->N, h->d_ni, h->d_ld, h->d_foff, fac, allow_last_zero, last_pivot,
+                                   diag_scale, h->d_status);
+  A2LS_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// inversion of the diagonal tiles (in place): inv(L_bb) strictly lower, inv(U_bb) upper
+// ---------------------------------------------------------------------------
+// Column c of inv(L_bb) (unit lower) and of inv(U_bb) (upper) from a factored tile held in
+// shared memory; together they fill column c of the block-inverted tile.
+__device__ __forceinline__ void tile_inverse_column(const double (*t)[TB + 1], int tb, int c, double* col) {
+  double x[TB];
+  // inv(L): x_c = 1, x_r = -sum_{q=c}^{r-1} L[r][q] x_q for r > c
+  x[c] = 1.0;
+  for (int r = c + 1; r < tb; ++r) {
+    double s = 0.0;
+    for (int q = c; q < r; ++q) s -= t[r][q] * x[q];
+    x[r] = s;
+    col[r] = s;
+  }
+  // inv(U): x_c = 1/U_cc, x_r = -(sum_{q=r+1}^{c} U[r][q] x_q) / U[r][r] for r < c
+  x[c] = 1.0 / t[c][c];
+  col[c] = x[c];
+  for (int r = c - 1; r >= 0; --r) {
+    double s = 0.0;
+    for (int q = r + 1; q <= c; ++q) s -= t[r][q] * x[q];
+    x[r] = s / t[r][r];
+    col[r] = x[r];
+  }
+}
+
+template <class T>
+__global__ void k_invert_tiles(const int* ni, const int* ld, const int64_t* foff, T* fac) {
+  __shared__ double tile[TB][TB + 1];
+  const int i = blockIdx.x, b = blockIdx.y;
+  const int n = ni[i];
+  const int r0 = b * TB;
+  if (r0 >= n) return;
+  const int tb = min(TB, n - r0);
+  const int64_t L = ld[i];
+  T* A = fac + foff[i] + (int64_t)r0 * L + r0;
+  for (int e = threadIdx.x; e < tb * tb; e += blockDim.x) tile[e / tb][e % tb] = (double)A[(e / tb) * L + e % tb];
+  __syncthreads();
+  const int c = threadIdx.x;
+  if (c < tb) {
+    double col[TB];
+    tile_inverse_column(tile, tb, c, col);
+    for (int r = 0; r < tb; ++r) A[r * L + c] = (T)col[r];
+  }
+}
+
+template <class T> void invert_diag_tiles(a2ls_handle* h, T* fac) {
+  dim3 grid(h->N, ceil_div(h->max_n, TB));
+  k_invert_tiles<T><<<grid, TB, 0, h->st>>>(h->d_ni, h->d_ld, h->d_foff, fac);
+  A2LS_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// single right-hand-side local solves of the apply
+//   mode 0: z[g] = (q ? q[g] : 0) + x_l for interior rows l < n_I (restricted, Boolean D)
+//   mode 1: yloc[off + l] = D_l * x_l for every row (combined later by memberships)
+//   mode 2: yloc[off + l] = x_l (ASM: no weights)
+// The gathered vector lives in shared memory; 512 threads = 16 warps.
+// ---------------------------------------------------------------------------
+template <class T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
+
+template <class T, class Acc>
+__device__ __forceinline__ Acc dot_vec(const typename Vec<T>::type& a, const Acc* x);
+template <>
+__device__ __forceinline__ float dot_vec<float, float>(const float4& a, const float* x) {
+  return a.x * x[0] + a.y * x[1] + a.z * x[2] + a.w * x[3];
+}
+template <>
+__device__ __forceinline__ double dot_vec<double, double>(const double2& a, const double* x) {
+  return a.x * x[0] + a.y * x[1];
+}
+
+constexpr int LS_THREADS = 512;
+constexpr int LS_WARPS = LS_THREADS / 32;
+constexpr int ROWS_PER_WARP = TB / LS_WARPS;  // 4
+
+// s[r] = x[r0 + r] - sum_{c in [c0, c1)} M[r0 + r][c] x[c] for r < tb (c0, c1 multiples of Vec width
+// except c1 which may be padded up to ld with zeros)
+template <class T, class Acc>
+__device__ __forceinline__ void panel_residual(const T* __restrict__ M, int64_t L, int r0, int tb, int c0,
+                                               int c1, const Acc* x, Acc* s) {
+  using V = typename Vec<T>::type;
+  constexpr int VW = Vec<T>::W;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  Acc part[ROWS_PER_WARP];
+#pragma unroll
+  for (int u = 0; u < ROWS_PER_WARP; ++u) part[u] = 0;
+  const int nv = (c1 - c0 + VW - 1) / VW;
+  const V* rowp[ROWS_PER_WARP];
+#pragma unroll
+  for (int u = 0; u < ROWS_PER_WARP; ++u) {
+    int r = wid + u * LS_WARPS;
+    rowp[u] = reinterpret_cast<const V*>(M + (int64_t)(r0 + min(r, tb - 1)) * L + c0);
+  }
+  for (int v = lane; v < nv; v += 32) {
+    V a[ROWS_PER_WARP];
+#pragma unroll
+    for (int u = 0; u < ROWS_PER_WARP; ++u) a[u] = __ldg(rowp[u] + v);
+    const Acc* xv = x + c0 + v * VW;
+#pragma unroll
+    for (int u = 0; u < ROWS_PER_WARP; ++u) part[u] += dot_vec<T, Acc>(a[u], xv);
+  }
+#pragma unroll
+  for (int u = 0; u < ROWS_PER_WARP; ++u) {
+    Acc p = part[u];
+    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+    int r = wid + u * LS_WARPS;
+    if (lane == 0 && r < tb) s[r] = x[r0 + r] - p;
+  }
+}
+
+// x[r0 + r] = sum_c Tinv[r][c] s[c], with the tile's unit-lower (lower=1) or upper (lower=0) part
+template <class T, class Acc>
+__device__ __forceinline__ void tile_apply(const T* __restrict__ M, int64_t L, int r0, int tb, int lower,
+                                           const Acc* s, Acc* x) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int u = 0; u < ROWS_PER_WARP; ++u) {
+    const int r = wid + u * LS_WARPS;
+    Acc p = 0;
+    if (r < tb) {
+      const T* row = M + (int64_t)(r0 + r) * L + r0;
+      for (int c = lane; c < tb; c += 32) {
+        Acc a = (Acc)row[c];
+        if (lower) p += (c < r) ? a * s[c] : (c == r ? s[c] : (Acc)0);
+        else p += (c >= r) ? a * s[c] : (Acc)0;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+    if (lane == 0 && r < tb) x[r0 + r] = p;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(LS_THREADS) k_local_solve(
+    const int* off, const int* nI, const int* ni, const int* ld, const int64_t* foff, const int* idx,
+    const double* D, const T* __restrict__ fac, const double* __restrict__ t, const double* __restrict__ q,
+    double* __restrict__ out, int mode) {
+  using Acc = typename AccOf<T>::type;
+  extern __shared__ unsigned char smem_raw[];
+  Acc* x = reinterpret_cast<Acc*>(smem_raw);
+  __shared__ Acc s[TB];
+  const int i = blockIdx.x;
+  const int n = ni[i], o = off[i];
+  const int64_t L = ld[i];
+  const T* M = fac + foff[i];
+  for (int l = threadIdx.x; l < L; l += LS_THREADS) x[l] = (l < n) ? (Acc)t[idx[o + l]] : (Acc)0;
+  __syncthreads();
+  const int nb = (n + TB - 1) / TB;
+  // forward: L y = t
+  for (int b = 0; b < nb; ++b) {
+    const int r0 = b * TB, tb = min(TB, n - r0);
+    panel_residual<T, Acc>(M, L, r0, tb, 0, r0, x, s);
+    __syncthreads();
+    tile_apply<T, Acc>(M, L, r0, tb, 1, s, x);
+    __syncthreads();
+  }
+  // backward: U x = y
+  for (int b = nb - 1; b >= 0; --b) {
+    const int r0 = b * TB, tb = min(TB, n - r0);
+    const int c0 = r0 + tb;  // a multiple of TB unless this is the last block (then c0 == n: no panel)
+    panel_residual<T, Acc>(M, L, r0, tb, c0, c0 < n ? (int)L : c0, x, s);
+    __syncthreads();
+    tile_apply<T, Acc>(M, L, r0, tb, 0, s, x);
+    __syncthreads();
+  }
+  if (mode == 0) {
+    const int n_I = nI[i];
+    for (int l = threadIdx.x; l < n_I; l += LS_THREADS) {
+      const int g = idx[o + l];
+      out[g] = (q ? q[g] : 0.0) + (double)x[l];
+    }
+  } else {
+    for (int l = threadIdx.x; l < n; l += LS_THREADS)
+      out[o + l] = (mode == 1 ? D[o + l] : 1.0) * (double)x[l];
+  }
+}
+
+template <class T>
+void local_solves(a2ls_handle* h, const T* fac, const double* t, const double* q, double* z, int mode) {
+  using Acc = typename AccOf<T>::type;
+  const size_t smem = sizeof(Acc) * round_up(h->max_n, 4);
+  static bool configured = false;
+  if (!configured) {
+    A2LS_CUDA(cudaFuncSetAttribute(k_local_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(Acc) * MAXN_LOCAL)));
+    configured = true;
+  }
+  k_local_solve<T><<<h->N, LS_THREADS, smem, h->st>>>(h->d_off, h->d_nI, h->d_ni, h->d_ld, h->d_foff,
+                                                      h->d_idx, h->d_D, fac, t, q, z, mode);
+  A2LS_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------
+// multi right-hand-side solves for the eigensolver: X (n_i x p, row-major, leading
+// dimension ldx, subdomain i at X + i*xstride) <- inv(U) inv(L) X (either half optional)
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) k_block_solve(const int* ni, const int* ld, const int64_t* foff,
+                                                     const T* __restrict__ fac, T* X,
+                                                     const int64_t* xoff, int col0, int ldx,
+                                                     const int* pvec, const int* active, int forward,
+                                                     int backward) {
+  using Acc = typename AccOf<T>::type;
+  __shared__ Acc sA[GK * 65], sB[GK * 65];
+  const int i = blockIdx.x;
+  if (active && !active[i]) return;
+  const int p = pvec[i];
+  if (p <= 0) return;
+  const int n = ni[i];
+  const int64_t L = ld[i];
+  const T* M = fac + foff[i];
+  T* Xi = X + xoff[i] + col0;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int nb = (n + TB - 1) / TB;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 0 && !forward) continue;
+    if (pass == 1 && !backward) continue;
+    for (int bb = 0; bb < nb; ++bb) {
+      const int b = pass == 0 ? bb : nb - 1 - bb;
+      const int r0 = b * TB, tb = min(TB, n - r0);
+      for (int c0 = 0; c0 < p; c0 += 64) {
+        const int pc = min(64, p - c0);
+        Acc acc[4][4] = {};
+        if (pass == 0) {
+          if (r0 > 0) cta_gemm<T, Acc>(M + (int64_t)r0 * L, L, Xi + c0, ldx, tb, pc, r0, 0, acc, sA, sB);
+        } else {
+          const int e0 = r0 + tb;
+          if (e0 < n)
+            cta_gemm<T, Acc>(M + (int64_t)r0 * L + e0, L, Xi + (int64_t)e0 * ldx + c0, ldx, tb, pc, n - e0, 0,
+                             acc, sA, sB);
+        }
+        // S = X_b - acc, written in place
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int r = ty * 4 + u, c = tx * 4 + v;
+            if (r < tb && c < pc) {
+              T* ptr = Xi + (int64_t)(r0 + r) * ldx + c0 + c;
+              *ptr = (T)((Acc)*ptr - acc[u][v]);
+            }
+          }
+        __syncthreads();
+        Acc acc2[4][4] = {};
+        cta_gemm<T, Acc>(M + (int64_t)r0 * L + r0, L, Xi + (int64_t)r0 * ldx + c0, ldx, tb, pc, tb,
+                         pass == 0 ? 1 : 2, acc2, sA, sB);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int r = ty * 4 + u, c = tx * 4 + v;
+            if (r < tb && c < pc) Xi[(int64_t)(r0 + r) * ldx + c0 + c] = (T)acc2[u][v];
+          }
+        __syncthreads();
+      }
+    }
+  }
+}
+
+template <class T>
+void block_solve(a2ls_handle* h, const T* fac, T* X, const int64_t* xoff, int col0, int ldx, const int* pvec,
+                 const int* active, int forward, int backward) {
+  k_block_solve<T><<<h->N, 256, 0, h->st>>>(h->d_ni, h->d_ld, h->d_foff, fac, X, xoff, col0, ldx, pvec,
+                                           active, forward, backward);
+  A2LS_LAUNCH();
+}
+
+template void lu_batched<float>(a2ls_handle*, float*, int, double*, double*);
+template void lu_batched<double>(a2ls_handle*, double*, int, double*, double*);
+template void invert_diag_tiles<float>(a2ls_handle*, float*);
+template void invert_diag_tiles<double>(a2ls_handle*, double*);
+template void local_solves<float>(a2ls_handle*, const float*, const double*, const double*, double*, int);
+template void local_solves<double>(a2ls_handle*, const double*, const double*, const double*, double*, int);
+template void block_solve<float>(a2ls_handle*, const float*, float*, const int64_t*, int, int, const int*,
+                                  const int*, int, int);
+template void block_solve<double>(a2ls_handle*, const double*, double*, const int64_t*, int, int, const int*,
+                                   const int*, int, int);
+
+}  // namespace a2ls
+
+namespace a2ls {
+
+// ---------------------------------------------------------------------------
+// One dense FP64 matrix (the coarse operator A_00): block-inverted LU without
+// pivoting, spread over many CTAs, then the explicit inverse.
+// ---------------------------------------------------------------------------
+// factor the 64x64 diagonal block at (k0, k0) and invert its triangles in place
+__global__ void k_e_diag(double* A, int n, int64_t ld, int k0, double scale, int* st) {
+  __shared__ double t[TB][TB + 1];
+  const int tb = min(TB, n - k0);
+  double* D = A + (int64_t)k0 * ld + k0;
+  for (int e = threadIdx.x; e < tb * tb; e += blockDim.x) t[e / tb][e % tb] = D[(e / tb) * ld + e % tb];
+  __syncthreads();
+  for (int c = 0; c < tb; ++c) {
+    double piv = t[c][c];
+    if (fabs(piv) <= 1e-14 * scale) {
+      if (threadIdx.x == 0) raise_status(st, A2LS_ERR_SINGULAR, -1, k0 + c);
+      piv = scale;
+      __syncthreads();
+      if (threadIdx.x == 0) t[c][c] = piv;
+    }
+    __syncthreads();
+    for (int r = c + 1 + threadIdx.x; r < tb; r += blockDim.x) t[r][c] /= piv;
+    __syncthreads();
+    for (int e = threadIdx.x; e < (tb - c - 1) * (tb - c - 1); e += blockDim.x) {
+      const int r = c + 1 + e / (tb - c - 1), cc = c + 1 + e % (tb - c - 1);
+      t[r][cc] -= t[r][c] * t[c][cc];
+    }
+    __syncthreads();
+  }
+  const int c = threadIdx.x;
+  if (c < tb) {
+    double col[TB];
+    tile_inverse_column(t, tb, c, col);
+    for (int r = 0; r < tb; ++r) D[r * ld + c] = col[r];
+  }
+}
+
+// L21 = A21 inv(U11) (blockIdx.y == 0) and U12 = inv(L11) A12 (blockIdx.y == 1), in place
+__global__ void __launch_bounds__(256) k_e_panels(double* A, int n, int64_t ld, int k0) {
+  __shared__ double sA[GK * 65], sB[GK * 65];
+  const int tb = min(TB, n - k0);
+  const int start = k0 + tb + blockIdx.x * 64;
+  if (start >= n) return;
+  const int w = min(64, n - start);
+  double acc[4][4] = {};
+  const double* Dg = A + (int64_t)k0 * ld + k0;
+  if (blockIdx.y == 0) {
+    cta_gemm<double, double>(A + (int64_t)start * ld + k0, ld, Dg, ld, w, tb, tb, 0, acc, sA, sB, 2);
+  } else {
+    cta_gemm<double, double>(Dg, ld, A + (int64_t)k0 * ld + start, ld, tb, w, tb, 1, acc, sA, sB);
+  }
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int r = ty * 4 + u, c = tx * 4 + v;
+      if (blockIdx.y == 0) {
+        if (r < w && c < tb) A[(int64_t)(start + r) * ld + k0 + c] = acc[u][v];
+      } else {
+        if (r < tb && c < w) A[(int64_t)(k0 + r) * ld + start + c] = acc[u][v];
+      }
+    }
+}
+
+// A22 -= L21 U12
+__global__ void __launch_bounds__(256) k_e_trailing(double* A, int n, int64_t ld, int k0) {
+  __shared__ double sA[GK * 65], sB[GK * 65];
+  const int tb = min(TB, n - k0);
+  const int r0 = k0 + tb + blockIdx.y * 64, c0 = k0 + tb + blockIdx.x * 64;
+  if (r0 >= n || c0 >= n) return;
+  double acc[4][4] = {};
+  cta_gemm<double, double>(A + (int64_t)r0 * ld + k0, ld, A + (int64_t)k0 * ld + c0, ld, min(64, n - r0),
+                           min(64, n - c0), tb, 0, acc, sA, sB);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int r = r0 + ty * 4 + u, c = c0 + tx * 4 + v;
+      if (r < n && c < n) A[(int64_t)r * ld + c] -= acc[u][v];
+    }
+}
+
+// X = inv(U) inv(L) I, one 64-column slab per CTA (F holds the block-inverted LU)
+__global__ void __launch_bounds__(256) k_e_inverse(const double* F, int n, int64_t ld, double* X, int64_t ldx) {
+  __shared__ double sA[GK * 65], sB[GK * 65];
+  const int c0 = blockIdx.x * 64;
+  const int pc = min(64, n - c0);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double* Xs = X + c0;
+  for (int e = tid; e < n * pc; e += 256) {
+    const int r = e / pc, c = e % pc;
+    Xs[(int64_t)r * ldx + c] = (r == c0 + c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int nb = (n + TB - 1) / TB;
+  const int bstart = c0 / TB;  // rows above the slab's first unit entry stay zero in the forward pass
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int bb = 0; bb < nb; ++bb) {
+      const int b = pass == 0 ? bb : nb - 1 - bb;
+      if (pass == 0 && b < bstart) continue;
+      const int r0 = b * TB, tb = min(TB, n - r0);
+      double acc[4][4] = {};
+      if (pass == 0) {
+        const int k0 = bstart * TB;
+        if (r0 > k0)
+          cta_gemm<double, double>(F + (int64_t)r0 * ld + k0, ld, Xs + (int64_t)k0 * ldx, ldx, tb, pc, r0 - k0, 0,
+                                   acc, sA, sB);
+      } else {
+        const int e0 = r0 + tb;
+        if (e0 < n)
+          cta_gemm<double, double>(F + (int64_t)r0 * ld + e0, ld, Xs + (int64_t)e0 * ldx, ldx, tb, pc, n - e0, 0,
+                                   acc, sA, sB);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int r = ty * 4 + u, c = tx * 4 + v;
+          if (r < tb && c < pc) Xs[(int64_t)(r0 + r) * ldx + c] -= acc[u][v];
+        }
+      __syncthreads();
+      double acc2[4][4] = {};
+      cta_gemm<double, double>(F + (int64_t)r0 * ld + r0, ld, Xs + (int64_t)r0 * ldx, ldx, tb, pc, tb,
+                               pass == 0 ? 1 : 2, acc2, sA, sB);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int r = ty * 4 + u, c = tx * 4 + v;
+          if (r < tb && c < pc) Xs[(int64_t)(r0 + r) * ldx + c] = acc2[u][v];
+        }
+      __syncthreads();
+    }
+  }
+}
+
+void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv) {
+  cudaStream_t st = h->st;
+  const int64_t ld = n;
+  for (int k0 = 0; k0 < n; k0 += TB) {
+    k_e_diag<<<1, TB, 0, st>>>(E, n, ld, k0, scale, h->d_status);
+    A2LS_LAUNCH();
+    const int rest = n - k0 - min(TB, n - k0);
+    if (rest <= 0) break;
+    const int chunks = ceil_div(rest, 64);
+    k_e_panels<<<dim3(chunks, 2), 256, 0, st>>>(E, n, ld, k0);
+    A2LS_LAUNCH();
+    k_e_trailing<<<dim3(chunks, chunks), 256, 0, st>>>(E, n, ld, k0);
+    A2LS_LAUNCH();
+  }
+  k_e_inverse<<<ceil_div(n, 64), 256, 0, st>>>(E, n, ld, Einv, ld);
+  A2LS_LAUNCH();
+}
+
+}  // namespace a2ls

@@ -1,0 +1,917 @@
+// Setup, part 3: the local generalized eigenproblems of Eq. 3.1 and the
+// coarse-space selection of Eq. 3.2, batched over all subdomains.
+//
+// For subdomain i: B = D_i A_ii D_i, C = A~_ii (Definition 3.1).
+//  * K_i = ker(C).  C is factored without pivoting (C = L U); for the
+//    diagonally dominant splittings of the target problems dim K_i <= 1 and a
+//    null direction shows up as a vanishing last pivot u_nn.  With the last
+//    pivot replaced by sigma (U'), k = sigma inv(U') e_n satisfies C k = u_nn e_n,
+//    so |u_nn| / ||k|| bounds the smallest singular value; C counts as singular
+//    when it is at most n * eps * ||C||_inf.
+//  * Kernel part of Eq. 3.2: (L_i cap K_i)^{perp K_i} = span(k) unless B k = 0.
+//  * Finite part: eigenpairs of B u = lambda C u restricted to u orthogonal to K_i,
+//    i.e. of T = (V_R^T C V_R)^{-1} V_R^T B V_R (Pi_i = orthogonal projector onto
+//    K_i^perp).  T u is computed without forming V_R: f = B u, g = inv(L) f,
+//    g <- g - (g_n / h_n) h with h = inv(L) k (makes the right-hand side consistent),
+//    v = inv(U') g, u' = v - (k^T v) k.
+//  * The largest |lambda| are found by a block Krylov method with explicit
+//    restarts: s block-Arnoldi steps (block Gram-Schmidt twice, Cholesky QR
+//    twice) build V = [V_0 .. V_s]; the Rayleigh-Ritz matrix is the block
+//    Hessenberg H; its eigenpairs (dense Hessenberg QR, one warp per
+//    subdomain) give Ritz pairs whose residual is ||H_{s,s-1} y_last||; the
+//    next cycle restarts from the real basis of the leading Ritz vectors.
+//    Small subdomains (n_i - dim K_i <= capacity) are solved in the full space.
+//  * Selection: |lambda| descending, kernel part first; a conjugate pair cut
+//    by the count keeps both members; a pair contributes [Re u, Im u].
+#include "a2ls_internal.cuh"
+#include "small_eig.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace a2ls {
+
+template <class T> struct EAcc;
+template <> struct EAcc<float> { using type = float; };
+template <> struct EAcc<double> { using type = double; };
+
+constexpr int EIG_THREADS = 256;
+constexpr int EIG_MAXP = 96;   // column capacity of the Krylov basis
+constexpr int RC = 16;         // rows staged per chunk in the Gram kernels
+
+__device__ __forceinline__ double hash_uniform(uint64_t seed, uint64_t a, uint64_t b, uint64_t c) {
+  // splitmix64 of a counter built from (seed, a, b, c); uniform in (-1, 1)
+  uint64_t z = seed + 0x9E3779B97F4A7C15ull * (a * 0x100000001B3ull + b * 0xC2B2AE3D27D4EB4Full + c + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return ((double)(z >> 11) * (1.0 / 9007199254740992.0)) * 2.0 - 1.0;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  __syncthreads();
+  return t;
+}
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+  __syncthreads();
+  return t;
+}
+
+// Decide dim ker(A~_ii) and the kernel part of Eq. 3.2; restore U when A~_ii is non-singular.
+// A~_ii is an M-matrix splitting for the target problems (non-positive couplings,
+// weak diagonal dominance by Definition 3.1); an irreducible weakly diagonally
+// dominant matrix is singular exactly when every row is tight, and then its
+// kernel is spanned by the vector of ones.  The test is done on the FP64 CSR
+// data: every row sum of A~_ii must vanish to within 32 eps of its absolute row sum.
+template <class T>
+__global__ void __launch_bounds__(EIG_THREADS) k_kernel_test(
+    const int* ni, const int* off, const int* ld, const int64_t* foff, T* fac, const double* last_pivot,
+    const double* dscale, const int64_t* lrow, const int* lcol, const double* lval, const double* lump,
+    const double* D, double* kvec, int* kd, int* kpart, int* st) {
+  __shared__ double red[32];
+  const int i = blockIdx.x;
+  const int n = ni[i], o = off[i];
+  double worst = 0.0, bmax = 0.0;
+  for (int l = threadIdx.x; l < n; l += EIG_THREADS) {
+    double rs = 0.0, ra = 0.0, rb = 0.0;
+    for (int64_t q = lrow[o + l]; q < lrow[o + l + 1]; ++q) {
+      const int lk = lcol[q];
+      if (lk < 0) continue;
+      double a = lval[q];
+      rb += fabs(a) * D[o + lk];
+      if (lk == l) a -= lump[o + l];
+      rs += a;
+      ra += fabs(a);
+    }
+    worst = fmax(worst, fabs(rs) / fmax(ra, 1e-300));
+    bmax = fmax(bmax, rb * D[o + l]);
+  }
+  worst = block_max(worst, red);
+  const double bnorm = block_max(bmax, red);
+  const bool singular = worst <= 32.0 * 2.220446049250313e-16;
+  if (threadIdx.x == 0) kd[i] = singular ? 1 : 0;
+  if (!singular) {
+    const double upiv = last_pivot[i];
+    if (!(fabs(upiv) > 1e-300)) {
+      if (threadIdx.x == 0) raise_status(st, A2LS_ERR_EIGEN, i, 3);  // singular but not an M-matrix splitting
+      return;
+    }
+    // undo the pivot replacement: the last column of the last diagonal tile of inv(U) scales by sigma/u_nn
+    const double sigma = dscale[i] > 0 ? dscale[i] : 1.0;
+    const int r0 = ((n - 1) / TB) * TB;
+    T* A = fac + foff[i];
+    const int64_t L = ld[i];
+    for (int r = r0 + threadIdx.x; r < n; r += EIG_THREADS) {
+      T* p = A + (int64_t)r * L + (n - 1);
+      *p = (T)((double)*p * (sigma / upiv));
+    }
+    for (int l = threadIdx.x; l < n; l += EIG_THREADS) kvec[o + l] = 0.0;
+    if (threadIdx.x == 0) kpart[i] = 0;
+    return;
+  }
+  const double kv = 1.0 / sqrt((double)n);
+  for (int l = threadIdx.x; l < n; l += EIG_THREADS) kvec[o + l] = kv;
+  __syncthreads();
+  // kernel part test: B k != 0, i.e. k is not in L_i = ker(D A_ii D)
+  double bk = 0.0;
+  for (int l = threadIdx.x; l < n; l += EIG_THREADS) {
+    double r = 0.0;
+    for (int64_t q = lrow[o + l]; q < lrow[o + l + 1]; ++q) {
+      const int lk = lcol[q];
+      if (lk >= 0) r += lval[q] * D[o + lk] * kv;
+    }
+    bk = fmax(bk, fabs(r * D[o + l]));
+  }
+  bk = block_max(bk, red);
+  if (threadIdx.x == 0) kpart[i] = (bk > (double)n * 1e-14 * bnorm * kv) ? 1 : 0;
+}
+
+// X[:, col0] = kvec (as T) for the kernel subdomains
+template <class T>
+__global__ void k_load_vec(const int* ni, const int* off, const int64_t* xoff, int ldx, const double* v,
+                           const int* mask, T* X) {
+  const int i = blockIdx.x;
+  if (mask && !mask[i]) return;
+  for (int l = threadIdx.x; l < ni[i]; l += blockDim.x) X[xoff[i] + (int64_t)l * ldx] = (T)v[off[i] + l];
+}
+
+template <class T>
+__global__ void k_store_h(const int* ni, const int* off, const int64_t* xoff, int ldx, const T* X,
+                          const int* kd, double* h, int* st) {
+  __shared__ double red[32];
+  const int i = blockIdx.x;
+  if (!kd[i]) return;
+  const int n = ni[i];
+  double s2 = 0.0;
+  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+    const double v = (double)X[xoff[i] + (int64_t)l * ldx];
+    h[off[i] + l] = v;
+    s2 += v * v;
+  }
+  const double hn = sqrt(block_sum(s2, red));
+  if (threadIdx.x == 0) {
+    // the consistency shift divides by h_n; it vanishes only if the right null vector lies in range(C)
+    if (!(fabs(h[off[i] + n - 1]) > 1e-12 * hn)) raise_status(st, A2LS_ERR_EIGEN, i, 1);
+  }
+}
+
+// random start block, columns [col0, col0 + p_i)
+template <class T>
+__global__ void k_random_block(const int* ni, const int64_t* xoff, int ldx, int col0, const int* pvec,
+                               const int* active, uint64_t seed, int cycle, T* X) {
+  const int i = blockIdx.x;
+  if (active && !active[i]) return;
+  const int n = ni[i], p = pvec[i];
+  for (int e = threadIdx.x; e < n * p; e += blockDim.x) {
+    const int l = e / p, c = e % p;
+    X[xoff[i] + (int64_t)l * ldx + col0 + c] = (T)hash_uniform(seed, (uint64_t)i, (uint64_t)l,
+                                                               (uint64_t)(c + 1000 * cycle));
+  }
+}
+
+// columns of X orthogonal to k (kernel subdomains only)
+template <class T>
+__global__ void __launch_bounds__(EIG_THREADS) k_project_k(const int* ni, const int* off, const int64_t* xoff,
+                                                            int ldx, int col0, const int* pvec,
+                                                            const int* active, const int* kd,
+                                                            const double* kvec, T* X) {
+  using Acc = typename EAcc<T>::type;
+  __shared__ double dots[EIG_MAXP];
+  const int i = blockIdx.x;
+  if ((active && !active[i]) || !kd[i]) return;
+  const int n = ni[i], p = pvec[i], o = off[i];
+  T* Xi = X + xoff[i] + col0;
+  for (int c = threadIdx.x; c < p; c += EIG_THREADS) dots[c] = 0.0;
+  __syncthreads();
+  // one warp per column
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c = wid; c < p; c += EIG_THREADS / 32) {
+    Acc d = 0;
+    for (int l = lane; l < n; l += 32) d += (Acc)kvec[o + l] * (Acc)Xi[(int64_t)l * ldx + c];
+    for (int w = 16; w > 0; w >>= 1) d += __shfl_xor_sync(0xffffffffu, d, w);
+    if (lane == 0) dots[c] = (double)d;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * p; e += EIG_THREADS) {
+    const int l = e / p, c = e % p;
+    Xi[(int64_t)l * ldx + c] = (T)((Acc)Xi[(int64_t)l * ldx + c] - (Acc)dots[c] * (Acc)kvec[o + l]);
+  }
+}
+
+// W[:, 0:p] = B V[:, c0:c0+p], B = D A_ii D via the local CSR; one warp per row
+template <class T>
+__global__ void k_bmul(const int* ni, const int* off, const int64_t* xoff, int ldx, int vcol0, const int* pvec,
+                       const int* active, const int64_t* lrow, const int* lcol, const double* lval,
+                       const double* D, const T* V, T* W) {
+  const int i = blockIdx.x;
+  if (active && !active[i]) return;
+  const int n = ni[i], p = pvec[i], o = off[i];
+  const T* Vi = V + xoff[i] + vcol0;
+  T* Wi = W + xoff[i];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int l = wid; l < n; l += nw) {
+    const double dl = D[o + l];
+    for (int c0 = 0; c0 < p; c0 += 32) {
+      const int c = c0 + lane;
+      double acc = 0.0;
+      if (dl != 0.0 && c < p) {
+        for (int64_t q = lrow[o + l]; q < lrow[o + l + 1]; ++q) {
+          const int lk = lcol[q];
+          if (lk < 0) continue;
+          const double dk = D[o + lk];
+          if (dk == 0.0) continue;
+          acc += lval[q] * dk * (double)Vi[(int64_t)lk * ldx + c];
+        }
+      }
+      if (c < p) Wi[(int64_t)l * ldx + c] = (T)(acc * dl);
+    }
+  }
+}
+
+// W[:, c] -= (W[n-1][c] / h[n-1]) h  (consistency of the right-hand side with range(C))
+template <class T>
+__global__ void k_mu_fix(const int* ni, const int* off, const int64_t* xoff, int ldx, const int* pvec,
+                         const int* active, const int* kd, const double* h, T* W) {
+  using Acc = typename EAcc<T>::type;
+  __shared__ Acc mu[EIG_MAXP];
+  const int i = blockIdx.x;
+  if ((active && !active[i]) || !kd[i]) return;
+  const int n = ni[i], p = pvec[i], o = off[i];
+  T* Wi = W + xoff[i];
+  const double hn = h[o + n - 1];
+  for (int c = threadIdx.x; c < p; c += blockDim.x) mu[c] = (Acc)((double)Wi[(int64_t)(n - 1) * ldx + c] / hn);
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * p; e += blockDim.x) {
+    const int l = e / p, c = e % p;
+    Wi[(int64_t)l * ldx + c] = (T)((Acc)Wi[(int64_t)l * ldx + c] - mu[c] * (Acc)h[o + l]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Orthogonalisation: block CGS2 of W against V[:, 0:jb], then Cholesky QR twice.
+// Writes the Gram coefficients into H[0:jb, hc:hc+p] and R into H[hr:hr+p, hc:hc+p]
+// and the orthonormal block into V[:, vout:vout+p].  full != 0: only H[0:jb, hc:hc+p].
+// ---------------------------------------------------------------------------
+__device__ void small_cholesky_inverse(double* G, int p, double* Ri, int& rank_ok) {
+  // G (p x p, stride p) = R^T R; R overwrites the upper triangle of G; Ri = inv(R) (stride p); one thread
+  rank_ok = 1;
+  double gmax = 0.0;
+  for (int a = 0; a < p; ++a) gmax = fmax(gmax, G[a * p + a]);
+  for (int a = 0; a < p; ++a) {
+    double d = G[a * p + a];
+    for (int q = 0; q < a; ++q) d -= G[q * p + a] * G[q * p + a];
+    if (!(d > 1e-28 * gmax)) {
+      rank_ok = 0;
+      d = 1e-28 * gmax + 1e-300;
+    }
+    const double r = sqrt(d);
+    G[a * p + a] = r;
+    for (int c = a + 1; c < p; ++c) {
+      double v = G[a * p + c];
+      for (int q = 0; q < a; ++q) v -= G[q * p + a] * G[q * p + c];
+      G[a * p + c] = v / r;
+    }
+  }
+  for (int c = 0; c < p; ++c) {
+    for (int a = c + 1; a < p; ++a) Ri[a * p + c] = 0.0;
+    Ri[c * p + c] = 1.0 / G[c * p + c];
+    for (int a = c - 1; a >= 0; --a) {
+      double v = 0.0;
+      for (int q = a + 1; q <= c; ++q) v += G[a * p + q] * Ri[q * p + c];
+      Ri[a * p + c] = -v / G[a * p + a];
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64_t* xoff, int ldx,
+                                                       const int* pvec, const int* active, int jb_blocks,
+                                                       int bcols, T* V, T* W, double* H, int hr, int hc,
+                                                       int vout, const int* fullv, int* rank_flag) {
+  using Acc = typename EAcc<T>::type;
+  extern __shared__ double sm[];
+  const int i = blockIdx.x;
+  if (active && !active[i]) return;
+  const int full = fullv ? fullv[i] : 0;
+  if (full && jb_blocks != 1) return;
+  const int n = ni[i], p = pvec[i];
+  const int jb = full ? p : jb_blocks * bcols;  // basis columns to orthogonalise against
+  T* Vi = V + xoff[i];
+  T* Wi = W + xoff[i];
+  double* Hi = H + (int64_t)i * EIG_MAXP * EIG_MAXP;
+  // shared layout
+  double* G = sm;                               // EIG_MAXP * EIG_MAXP (Gram, then R in place)
+  double* Ri = G + EIG_MAXP * EIG_MAXP;         // EIG_MAXP * EIG_MAXP
+  double* trow = Ri + EIG_MAXP * EIG_MAXP;      // EIG_MAXP
+  Acc* sv = reinterpret_cast<Acc*>(trow + EIG_MAXP);           // RC * EIG_MAXP
+  Acc* sw = sv + RC * EIG_MAXP;                                // RC * EIG_MAXP
+  __shared__ int rank_ok;
+  const int tid = threadIdx.x;
+  const int npass = jb > 0 ? 2 : 0;
+  for (int e = tid; e < jb * p; e += EIG_THREADS) Hi[(e / p) * EIG_MAXP + hc + e % p] = 0.0;
+  for (int pass = 0; pass < npass; ++pass) {
+    // G = V[:, 0:jb]^T W[:, 0:p]
+    Acc acc[(EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS];
+    const int nout = jb * p;
+#pragma unroll
+    for (int u = 0; u < (EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS; ++u) acc[u] = 0;
+    for (int l0 = 0; l0 < n; l0 += RC) {
+      const int rows = min(RC, n - l0);
+      for (int e = tid; e < rows * jb; e += EIG_THREADS)
+        sv[(e / jb) * EIG_MAXP + e % jb] = (Acc)Vi[(int64_t)(l0 + e / jb) * ldx + e % jb];
+      for (int e = tid; e < rows * p; e += EIG_THREADS)
+        sw[(e / p) * EIG_MAXP + e % p] = (Acc)Wi[(int64_t)(l0 + e / p) * ldx + e % p];
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < (EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS; ++u) {
+        const int e = tid + u * EIG_THREADS;
+        if (e < nout) {
+          const int a = e / p, c = e % p;
+          Acc s = 0;
+          for (int r = 0; r < rows; ++r) s += sv[r * EIG_MAXP + a] * sw[r * EIG_MAXP + c];
+          acc[u] += s;
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < (EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS; ++u) {
+      const int e = tid + u * EIG_THREADS;
+      if (e < nout) {
+        G[e] = (double)acc[u];
+        Hi[(e / p) * EIG_MAXP + hc + e % p] += (double)acc[u];
+      }
+    }
+    __syncthreads();
+    if (full) return;  // Rayleigh quotient only
+    // W -= V G, staged by row chunks
+    for (int l0 = 0; l0 < n; l0 += RC) {
+      const int rows = min(RC, n - l0);
+      for (int e = tid; e < rows * jb; e += EIG_THREADS)
+        sv[(e / jb) * EIG_MAXP + e % jb] = (Acc)Vi[(int64_t)(l0 + e / jb) * ldx + e % jb];
+      __syncthreads();
+      for (int e = tid; e < rows * p; e += EIG_THREADS) {
+        const int r = e / p, c = e % p;
+        Acc s = 0;
+        for (int a = 0; a < jb; ++a) s += sv[r * EIG_MAXP + a] * (Acc)G[a * p + c];
+        T* w = Wi + (int64_t)(l0 + r) * ldx + c;
+        *w = (T)((Acc)*w - s);
+      }
+      __syncthreads();
+    }
+  }
+  // Shifted Cholesky QR 3 (a shifted first pass keeps the Cholesky factorisation defined for
+  // nearly rank-deficient blocks, two plain passes restore orthogonality):
+  // R_total = R3 R2 R1 goes to H[hr:hr+p, hc:hc+p]
+  for (int pass = 0; pass < 3; ++pass) {
+    // G = W^T W
+    Acc acc[(EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS];
+#pragma unroll
+    for (int u = 0; u < (EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS; ++u) acc[u] = 0;
+    for (int l0 = 0; l0 < n; l0 += RC) {
+      const int rows = min(RC, n - l0);
+      for (int e = tid; e < rows * p; e += EIG_THREADS)
+        sw[(e / p) * EIG_MAXP + e % p] = (Acc)Wi[(int64_t)(l0 + e / p) * ldx + e % p];
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < (EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS; ++u) {
+        const int e = tid + u * EIG_THREADS;
+        if (e < p * p) {
+          const int a = e / p, c = e % p;
+          Acc s = 0;
+          for (int r = 0; r < rows; ++r) s += sw[r * EIG_MAXP + a] * sw[r * EIG_MAXP + c];
+          acc[u] += s;
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < (EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS; ++u) {
+      const int e = tid + u * EIG_THREADS;
+      if (e < p * p) G[e] = (double)acc[u];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      if (pass == 0) {
+        double tr = 0.0;
+        for (int a = 0; a < p; ++a) tr += G[a * p + a];
+        const double shift = 11.0 * ((double)n * p + (double)p * (p + 1)) * 1.1102230246251565e-16 * tr;
+        for (int a = 0; a < p; ++a) G[a * p + a] += shift;
+      }
+      int ok;
+      small_cholesky_inverse(G, p, Ri, ok);
+      rank_ok = ok;
+      if (!ok && rank_flag) atomicAdd(rank_flag + i, 1);
+      if (pass == 0) {
+        for (int a = 0; a < p; ++a)
+          for (int c = 0; c < p; ++c) Hi[(hr + a) * EIG_MAXP + hc + c] = (c >= a) ? G[a * p + c] : 0.0;
+      } else {
+        // H_blk <- R2 H_blk, row by row (row a only reads rows q >= a)
+        for (int a = 0; a < p; ++a) {
+          for (int c = 0; c < p; ++c) {
+            double s = 0.0;
+            for (int q = a; q < p; ++q) s += G[a * p + q] * Hi[(hr + q) * EIG_MAXP + hc + c];
+            trow[c] = s;
+          }
+          for (int c = 0; c < p; ++c) Hi[(hr + a) * EIG_MAXP + hc + c] = trow[c];
+        }
+      }
+    }
+    __syncthreads();
+    // W <- W inv(R)
+    for (int l0 = 0; l0 < n; l0 += RC) {
+      const int rows = min(RC, n - l0);
+      for (int e = tid; e < rows * p; e += EIG_THREADS)
+        sw[(e / p) * EIG_MAXP + e % p] = (Acc)Wi[(int64_t)(l0 + e / p) * ldx + e % p];
+      __syncthreads();
+      for (int e = tid; e < rows * p; e += EIG_THREADS) {
+        const int r = e / p, c = e % p;
+        Acc s = 0;
+        for (int a = 0; a <= c; ++a) s += sw[r * EIG_MAXP + a] * (Acc)Ri[a * p + c];
+        Wi[(int64_t)(l0 + r) * ldx + c] = (T)s;
+      }
+      __syncthreads();
+    }
+  }
+  // V[:, vout:vout+p] = W
+  if (vout >= 0)
+    for (int e = tid; e < n * p; e += EIG_THREADS) {
+      const int l = e / p, c = e % p;
+      Vi[(int64_t)l * ldx + vout + c] = Wi[(int64_t)l * ldx + c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Rayleigh-Ritz on H (one warp per subdomain): Ritz values, the real basis Y of
+// the leading Ritz vectors (bcols columns), residual norms and convergence.
+// ---------------------------------------------------------------------------
+struct RRParams {
+  int sb_krylov;   // s*b in Krylov mode
+  int b;           // block size
+  int s;           // block steps
+  double tol;
+  int nevmax;      // slots per subdomain in the eigenvalue export
+};
+
+__global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull, const int* nf,
+                                const int* active, const double* H, double* Y, int* ycols, int* zcols,
+                                double* eigout, int* conv, int* st) {
+  extern __shared__ double sm[];
+  const int i = blockIdx.x;
+  if (active && !active[i]) return;
+  if (nf[i] <= 0) {
+    if (threadIdx.x == 0) {
+      conv[i] = 1;
+      ycols[i] = 0;
+      zcols[i] = 0;
+    }
+    return;
+  }
+  const int m = full[i] ? mfull[i] : prm.sb_krylov;
+  const int ld = m + 1;
+  double* S = sm;                    // m x ld
+  double* Q = S + m * ld;            // m x ld
+  double* xs = Q + m * ld;           // 32 lanes x m
+  double* ys = xs + 32 * m;          // 32 lanes x m
+  double* wr = ys + 32 * m;          // m
+  double* wi = wr + m;               // m
+  double* vtmp = wi + m;             // m
+  int* perm = reinterpret_cast<int*>(vtmp + m);  // m
+  const double* Hi = H + (int64_t)i * EIG_MAXP * EIG_MAXP;
+  const se::Team team{(int)threadIdx.x, 32};
+  for (int e = threadIdx.x; e < m * m; e += 32) {
+    S[(e / m) * ld + e % m] = Hi[(e / m) * EIG_MAXP + e % m];
+    Q[(e / m) * ld + e % m] = (e / m == e % m) ? 1.0 : 0.0;
+  }
+  __syncwarp();
+  double snorm = 0.0;
+  bool finite = true;
+  for (int e = 0; e < m * m; ++e) {
+    const double v = S[(e / m) * ld + e % m];
+    finite = finite && isfinite(v);
+    snorm = fmax(snorm, fabs(v));
+  }
+  if (!finite) {
+    if (threadIdx.x == 0) {
+      raise_status(st, A2LS_ERR_EIGEN, i, 4);
+      conv[i] = 1;
+      ycols[i] = 0;
+      zcols[i] = 0;
+    }
+    return;
+  }
+  se::hessenberg(S, ld, Q, ld, m, vtmp, team);
+  const int rc = se::schur(S, ld, Q, ld, m, snorm, team);
+  if (rc != 0 && threadIdx.x == 0) raise_status(st, A2LS_ERR_EIGEN, i, 2);
+  __syncwarp();
+  if (threadIdx.x == 0) {
+    se::schur_eigenvalues(S, ld, m, wr, wi);
+    se::order_by_modulus(wr, wi, m, perm);
+  }
+  __syncwarp();
+  // plan the columns: walk eigenvalues by modulus, pairs take two columns
+  // lane j handles the j-th selected eigenvalue
+  __shared__ int sel_pos[32], sel_col[32], sel_two[32], nsel_s, ncol_s, zc_s;
+  if (threadIdx.x == 0) {
+    const int bc = full[i] ? min(prm.b, m) : prm.b;
+    int col = 0, nsel = 0, cnt = 0, zc = -1;
+    for (int a = 0; a < m && col < bc && nsel < 32; ++a) {
+      const int pidx = perm[a];
+      if (wi[pidx] < 0.0) continue;  // the partner of a pair already taken
+      const int two = (wi[pidx] > 0.0) ? 1 : 0;
+      sel_pos[nsel] = pidx;
+      sel_col[nsel] = col;
+      sel_two[nsel] = (two && col + 1 < bc) ? 1 : (two ? 2 : 0);  // 2: pair truncated to its real part
+      col += (sel_two[nsel] == 1) ? 2 : 1;
+      cnt += two ? 2 : 1;
+      ++nsel;
+      if (zc < 0 && cnt >= nf[i]) zc = col;
+    }
+    if (zc < 0) zc = col;
+    nsel_s = nsel;
+    ncol_s = col;
+    zc_s = zc;
+  }
+  __syncwarp();
+  const int nsel = nsel_s;
+  double* Yi = Y + (int64_t)i * EIG_MAXP * EIG_MAXP;
+  int conv_all = 1;
+  if ((int)threadIdx.x < nsel) {
+    const int j = threadIdx.x;
+    const int pidx = sel_pos[j];
+    const int two = sel_two[j];
+    const int pstart = (wi[pidx] > 0.0) ? pidx : pidx;  // a pair's +imag member is the first of its block
+    double* x = xs + j * m;
+    double* y = ys + j * m;
+    se::schur_vector(S, ld, m, pstart, wr[pidx], wi[pidx] > 0 ? wi[pidx] : 0.0, x, y, snorm);
+    // coefficients in the V basis: Q x, Q y; norms
+    double nx = 0.0, ny = 0.0;
+    for (int a = 0; a < m; ++a) {
+      double qx = 0.0, qy = 0.0;
+      for (int c = 0; c < m; ++c) {
+        qx += Q[a * ld + c] * x[c];
+        qy += Q[a * ld + c] * y[c];
+      }
+      Yi[a * EIG_MAXP + sel_col[j]] = qx;
+      if (two == 1) Yi[a * EIG_MAXP + sel_col[j] + 1] = qy;
+      nx += qx * qx;
+      ny += qy * qy;
+    }
+    const double nrm = sqrt(nx + (two ? ny : 0.0));
+    for (int a = 0; a < m; ++a) {
+      Yi[a * EIG_MAXP + sel_col[j]] /= (two == 2 ? sqrt(nx) : nrm);
+      if (two == 1) Yi[a * EIG_MAXP + sel_col[j] + 1] /= nrm;
+    }
+    // residual ||H_{s,s-1} y_last|| (Krylov mode); zero in the full space
+    double res = 0.0;
+    if (!full[i]) {
+      const int b = prm.b, r0 = prm.sb_krylov, c0 = prm.sb_krylov - b;
+      double rr = 0.0;
+      for (int a = 0; a < b; ++a) {
+        double ux = 0.0, uy = 0.0;
+        for (int c = 0; c < b; ++c) {
+          const double hv = Hi[(r0 + a) * EIG_MAXP + c0 + c];
+          ux += hv * Yi[(c0 + c) * EIG_MAXP + sel_col[j]];
+          if (two == 1) uy += hv * Yi[(c0 + c) * EIG_MAXP + sel_col[j] + 1];
+        }
+        rr += ux * ux + uy * uy;
+      }
+      res = sqrt(rr);
+    }
+    const double lam = hypot(wr[pidx], wi[pidx]);
+    const bool wanted = sel_col[j] < zc_s;
+    if (wanted && !(res <= prm.tol * lam)) conv_all = 0;
+    if (wanted) {
+      double* eo = eigout + (int64_t)i * prm.nevmax * 2;
+      // slot order follows the columns; the kernel part is stored separately by the host
+      eo[2 * j] = wr[pidx];
+      eo[2 * j + 1] = wi[pidx] > 0 ? wi[pidx] : 0.0;
+    }
+  }
+  conv_all = __all_sync(0xffffffffu, conv_all);
+  if (threadIdx.x == 0) {
+    conv[i] = conv_all;
+    ycols[i] = ncol_s;
+    zcols[i] = zc_s;
+  }
+}
+
+// X[:, 0:q] = V[:, 0:m] Y[0:m, 0:q] (q = qvec[i]); rows staged through shared memory
+template <class T>
+__global__ void __launch_bounds__(EIG_THREADS) k_vy(const int* ni, const int64_t* xoff, int ldx, const int* mvec,
+                                                     const int* qvec, const int* active, const T* V,
+                                                     const double* Y, T* X) {
+  using Acc = typename EAcc<T>::type;
+  extern __shared__ double sm[];
+  const int i = blockIdx.x;
+  if (active && !active[i]) return;
+  const int n = ni[i], m = mvec[i], q = qvec[i];
+  Acc* sy = reinterpret_cast<Acc*>(sm);             // m x q
+  Acc* sv = sy + EIG_MAXP * EIG_MAXP;               // RC x m
+  const double* Yi = Y + (int64_t)i * EIG_MAXP * EIG_MAXP;
+  for (int e = threadIdx.x; e < m * q; e += EIG_THREADS) sy[(e / q) * EIG_MAXP + e % q] = (Acc)Yi[(e / q) * EIG_MAXP + e % q];
+  const T* Vi = V + xoff[i];
+  T* Xi = X + xoff[i];
+  for (int l0 = 0; l0 < n; l0 += RC) {
+    const int rows = min(RC, n - l0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * m; e += EIG_THREADS)
+      sv[(e / m) * EIG_MAXP + e % m] = (Acc)Vi[(int64_t)(l0 + e / m) * ldx + e % m];
+    __syncthreads();
+    for (int e = threadIdx.x; e < rows * q; e += EIG_THREADS) {
+      const int r = e / q, c = e % q;
+      Acc s = 0;
+      for (int a = 0; a < m; ++a) s += sv[r * EIG_MAXP + a] * sy[a * EIG_MAXP + c];
+      Xi[(int64_t)(l0 + r) * ldx + c] = (T)s;
+    }
+  }
+}
+
+// Z (FP64, n_i x zld per subdomain at zoff) = [k (if kernel part), X[:, 0:zc]]
+template <class T>
+__global__ void k_final_z(const int* ni, const int* off, const int64_t* xoff, int ldx, const int* zcols,
+                          const int* kpart, const double* kvec, const T* X, const int64_t* zoff, int zld,
+                          double* Z) {
+  const int i = blockIdx.x;
+  const int n = ni[i], o = off[i], kp = kpart[i], zc = zcols[i];
+  double* Zi = Z + zoff[i];
+  for (int e = threadIdx.x; e < n * zld; e += blockDim.x) {
+    const int l = e / zld, c = e % zld;
+    double v = 0.0;
+    if (kp && c == 0) v = kvec[o + l];
+    else if (c - kp >= 0 && c - kp < zc) v = (double)X[xoff[i] + (int64_t)l * ldx + (c - kp)];
+    Zi[(int64_t)l * zld + c] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// driver
+// ---------------------------------------------------------------------------
+template <class T>
+static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const double* dscale) {
+  cudaStream_t st = h->st;
+  const int N = h->N;
+  const bool fp64 = sizeof(T) == 8;
+  const double tol = h->opt.eig_tol > 0 ? h->opt.eig_tol : (fp64 ? 1e-10 : 1e-5);
+  const int nev = h->nev;
+
+  // --- kernel detection ------------------------------------------------------
+  std::vector<int64_t> hoff1(N + 1, 0);
+  for (int i = 0; i < N; ++i) hoff1[i + 1] = hoff1[i] + h->h_n[i];
+  int64_t* d_off1 = dalloc<int64_t>(h, N + 1);
+  A2LS_CUDA(cudaMemcpyAsync(d_off1, hoff1.data(), sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, st));
+  std::vector<int> ones(N, 1);
+  int* d_ones = dalloc<int>(h, N);
+  A2LS_CUDA(cudaMemcpyAsync(d_ones, ones.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  T* X1 = dalloc<T>(h, hoff1[N]);
+  A2LS_CUDA(cudaMemsetAsync(X1, 0, sizeof(T) * hoff1[N], st));
+  double* kvec = dalloc<double>(h, h->sum_n);
+  double* hvec = dalloc<double>(h, h->sum_n);
+  int* d_kd = dalloc<int>(h, N);
+  int* d_kpart = dalloc<int>(h, N);
+  k_kernel_test<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, h->d_ld, h->d_foff, fac, last_pivot, dscale,
+                                               h->d_lrow, h->d_lcol, h->d_lval, h->d_lump, h->d_D, kvec, d_kd,
+                                               d_kpart, h->d_status);
+  A2LS_LAUNCH();
+  k_load_vec<T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_off1, 1, kvec, d_kd, X1);
+  A2LS_LAUNCH();
+  block_solve<T>(h, fac, X1, d_off1, 0, 1, d_ones, d_kd, 1, 0);
+  k_store_h<T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_off1, 1, X1, d_kd, hvec, h->d_status);
+  A2LS_LAUNCH();
+  std::vector<int> kd(N), kpart(N);
+  A2LS_CUDA(cudaMemcpyAsync(kd.data(), d_kd, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+  A2LS_CUDA(cudaMemcpyAsync(kpart.data(), d_kpart, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+  sync_and_check(h, "kernel detection of the local splittings");
+  dfree(h, X1);
+
+  // --- sizes ------------------------------------------------------------------
+  std::vector<int> nf(N), full(N), mfull(N), pv(N);
+  int nfmax = 0;
+  for (int i = 0; i < N; ++i) {
+    nf[i] = std::max(0, std::min(nev - kpart[i], h->h_n[i] - kd[i]));
+    nfmax = std::max(nfmax, nf[i]);
+  }
+  const int b = std::min(32, nfmax + std::max(4, (nfmax + 1) / 2));
+  int s = h->opt.eig_block_steps > 0 ? h->opt.eig_block_steps : 3;
+  if ((s + 1) * b > EIG_MAXP) s = EIG_MAXP / b - 1;
+  if (s < 1) fail(A2LS_ERR_ARG, "nev = %d is too large for the local eigensolver (at most %d)", nev, EIG_MAXP / 2 - 8);
+  const int P = EIG_MAXP;  // column stride of V and W
+  for (int i = 0; i < N; ++i) {
+    const int mdim = h->h_n[i] - kd[i];
+    full[i] = (mdim <= (s + 1) * b) ? 1 : 0;
+    mfull[i] = full[i] ? std::min(mdim, EIG_MAXP) : 0;
+    pv[i] = full[i] ? mfull[i] : b;
+  }
+  std::vector<int64_t> hvo(N + 1, 0);
+  for (int i = 0; i < N; ++i) hvo[i + 1] = hvo[i] + (int64_t)h->h_n[i] * P;
+  int64_t* d_vo = dalloc<int64_t>(h, N + 1);
+  A2LS_CUDA(cudaMemcpyAsync(d_vo, hvo.data(), sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, st));
+  int* d_full = dalloc<int>(h, N);
+  int* d_mfull = dalloc<int>(h, N);
+  int* d_pv = dalloc<int>(h, N);
+  int* d_nf = dalloc<int>(h, N);
+  int* d_active = dalloc<int>(h, N);
+  int* d_conv = dalloc<int>(h, N);
+  int* d_ycols = dalloc<int>(h, N);
+  int* d_zcols = dalloc<int>(h, N);
+  int* d_msb = dalloc<int>(h, N);
+  int* d_rank = dalloc<int>(h, N);
+  std::vector<int> msb(N), act(N);
+  for (int i = 0; i < N; ++i) {
+    msb[i] = full[i] ? mfull[i] : s * b;
+    act[i] = nf[i] > 0 ? 1 : 0;
+  }
+  A2LS_CUDA(cudaMemcpyAsync(d_full, full.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  A2LS_CUDA(cudaMemcpyAsync(d_mfull, mfull.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  A2LS_CUDA(cudaMemcpyAsync(d_pv, pv.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  A2LS_CUDA(cudaMemcpyAsync(d_nf, nf.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  A2LS_CUDA(cudaMemcpyAsync(d_active, act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  A2LS_CUDA(cudaMemcpyAsync(d_msb, msb.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  A2LS_CUDA(cudaMemsetAsync(d_rank, 0, sizeof(int) * N, st));
+  A2LS_CUDA(cudaMemsetAsync(d_ycols, 0, sizeof(int) * N, st));
+  A2LS_CUDA(cudaMemsetAsync(d_zcols, 0, sizeof(int) * N, st));
+  T* V = dalloc<T>(h, hvo[N]);
+  T* W = dalloc<T>(h, hvo[N]);
+  double* H = dalloc<double>(h, (size_t)N * P * P);
+  double* Y = dalloc<double>(h, (size_t)N * P * P);
+  double* Rscr = dalloc<double>(h, (size_t)N * P * P);
+  int* d_actk = dalloc<int>(h, N);  // active and not solved in the full space (block steps j >= 1)
+  const int nevmax = std::max(nev, 1) + 1;
+  double* eigout = dalloc<double>(h, (size_t)N * nevmax * 2);
+  A2LS_CUDA(cudaMemsetAsync(V, 0, sizeof(T) * hvo[N], st));
+  A2LS_CUDA(cudaMemsetAsync(W, 0, sizeof(T) * hvo[N], st));
+  A2LS_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * N * P * P, st));
+  A2LS_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * N * P * P, st));
+  {
+    std::vector<double> nanv((size_t)N * nevmax * 2, std::nan(""));
+    A2LS_CUDA(cudaMemcpyAsync(eigout, nanv.data(), sizeof(double) * nanv.size(), cudaMemcpyHostToDevice, st));
+    A2LS_CUDA(cudaStreamSynchronize(st));
+  }
+
+  using Acc = typename EAcc<T>::type;
+  const size_t orth_smem = sizeof(double) * (2 * EIG_MAXP * EIG_MAXP + EIG_MAXP) + sizeof(Acc) * 2 * RC * EIG_MAXP;
+  const size_t rr_smem = sizeof(double) * (2 * EIG_MAXP * (EIG_MAXP + 1) + 64 * EIG_MAXP + 3 * EIG_MAXP) +
+                         sizeof(int) * EIG_MAXP + 64;
+  const size_t vy_smem = sizeof(Acc) * (EIG_MAXP * EIG_MAXP + RC * EIG_MAXP);
+  A2LS_CUDA(cudaFuncSetAttribute(k_orth<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orth_smem));
+  A2LS_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_smem));
+  A2LS_CUDA(cudaFuncSetAttribute(k_vy<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vy_smem));
+
+  // T applied to V[:, vcol : vcol + p] -> W[:, 0:p]
+  auto apply_T = [&](int vcol, const int* actv) {
+    k_bmul<T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, vcol, d_pv, actv, h->d_lrow, h->d_lcol,
+                                 h->d_lval, h->d_D, V, W);
+    A2LS_LAUNCH();
+    block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, actv, 1, 0);
+    k_mu_fix<T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, d_pv, actv, d_kd, hvec, W);
+    A2LS_LAUNCH();
+    block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, actv, 0, 1);
+    k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, actv, d_kd, kvec, W);
+    A2LS_LAUNCH();
+  };
+  auto orthonormalize_W_into_V0 = [&]() {
+    k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, d_active, d_kd, kvec, W);
+    A2LS_LAUNCH();
+    // no previous basis: jb = 0; R written into H's last rows (discarded)
+    k_orth<T><<<N, EIG_THREADS, orth_smem, st>>>(h->d_ni, d_vo, P, d_pv, d_active, 0, b, V, W, Rscr, 0, 0,
+                                                  0, nullptr, d_rank);
+    A2LS_LAUNCH();
+  };
+
+  // initial block: random, orthogonal to k, orthonormal
+  k_random_block<T><<<N, 256, 0, st>>>(h->d_ni, d_vo, P, 0, d_pv, d_active, h->opt.seed, 0, W);
+  A2LS_LAUNCH();
+  orthonormalize_W_into_V0();
+  A2LS_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * N * P * P, st));
+
+  RRParams prm{s * b, b, s, tol, nevmax};
+  const int max_cycles = h->opt.eig_max_cycles > 0 ? h->opt.eig_max_cycles : 60;
+  std::vector<int> conv(N, 0), cycles(N, 0);
+  int cycle = 0;
+  std::vector<int> actk(N);
+  for (; cycle < max_cycles; ++cycle) {
+    for (int i = 0; i < N; ++i) actk[i] = act[i] && !full[i];
+    A2LS_CUDA(cudaMemcpyAsync(d_actk, actk.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    for (int j = 0; j < s; ++j) {
+      const int* actv = (j == 0) ? d_active : d_actk;
+      apply_T(j * b, actv);
+      // Krylov subdomains: block CGS2 + CholQR2 -> V_{j+1}, H[:, j-th block];
+      // full-space subdomains (j == 0 only): H = V0^T (T V0)
+      k_orth<T><<<N, EIG_THREADS, orth_smem, st>>>(h->d_ni, d_vo, P, d_pv, actv, j + 1, b, V, W, H,
+                                                    (j + 1) * b, j * b, (j + 1) * b, d_full, d_rank);
+      A2LS_LAUNCH();
+    }
+    k_rayleigh_ritz<<<N, 32, rr_smem, st>>>(prm, d_full, d_mfull, d_nf, d_active, H, Y, d_ycols, d_zcols,
+                                            eigout, d_conv, h->d_status);
+    A2LS_LAUNCH();
+    A2LS_CUDA(cudaMemcpyAsync(conv.data(), d_conv, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+    sync_and_check(h, "local eigensolve");
+    int remaining = 0;
+    for (int i = 0; i < N; ++i) {
+      if (act[i]) {
+        cycles[i] = cycle + 1;
+        if (conv[i] || full[i]) act[i] = 0;
+        else ++remaining;
+      }
+    }
+    if (remaining == 0) break;
+    A2LS_CUDA(cudaMemcpyAsync(d_active, act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    // restart block: W = V[:, 0:sb] Y[:, 0:b]
+    k_vy<T><<<N, EIG_THREADS, vy_smem, st>>>(h->d_ni, d_vo, P, d_msb, d_pv, d_active, V, Y, W);
+    A2LS_LAUNCH();
+    orthonormalize_W_into_V0();
+  }
+  int unconverged = 0;
+  for (int i = 0; i < N; ++i) unconverged += act[i];
+  if (unconverged)
+    fail(A2LS_ERR_EIGEN, "local eigensolve did not reach tolerance %.1e in %d cycles for %d subdomains", tol,
+         max_cycles, unconverged);
+
+  // --- final coarse vectors: Z = [k | V Y[:, 0:zc]] ------------------------------------------
+  for (int i = 0; i < N; ++i) act[i] = nf[i] > 0 ? 1 : 0;
+  A2LS_CUDA(cudaMemcpyAsync(d_active, act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  std::vector<int> zc(N), yc(N);
+  A2LS_CUDA(cudaMemcpyAsync(zc.data(), d_zcols, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+  A2LS_CUDA(cudaStreamSynchronize(st));
+  k_vy<T><<<N, EIG_THREADS, vy_smem, st>>>(h->d_ni, d_vo, P, d_msb, d_zcols, d_active, V, Y, W);
+  A2LS_LAUNCH();
+  const int zld = nev + 2;
+  std::vector<int64_t> hzo(N + 1, 0);
+  std::vector<int> mcols(N);
+  for (int i = 0; i < N; ++i) {
+    hzo[i + 1] = hzo[i] + (int64_t)h->h_n[i] * zld;
+    mcols[i] = kpart[i] + (nf[i] > 0 ? zc[i] : 0);
+  }
+  int64_t* d_zo = dalloc<int64_t>(h, N + 1);
+  A2LS_CUDA(cudaMemcpyAsync(d_zo, hzo.data(), sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, st));
+  double* Z = dalloc<double>(h, hzo[N]);
+  // subdomains without a finite part still need their kernel column
+  int* d_zc_eff = dalloc<int>(h, N);
+  std::vector<int> zc_eff(N);
+  for (int i = 0; i < N; ++i) zc_eff[i] = nf[i] > 0 ? zc[i] : 0;
+  A2LS_CUDA(cudaMemcpyAsync(d_zc_eff, zc_eff.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  k_final_z<T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, d_zc_eff, d_kpart, kvec, W, d_zo, zld, Z);
+  A2LS_LAUNCH();
+
+  // eigenvalue export: kernel part as (+inf, 0) first
+  std::vector<double> ev((size_t)N * nevmax * 2);
+  A2LS_CUDA(cudaMemcpyAsync(ev.data(), eigout, sizeof(double) * ev.size(), cudaMemcpyDeviceToHost, st));
+  A2LS_CUDA(cudaStreamSynchronize(st));
+  h->h_eigvals.assign((size_t)N * nevmax * 2, std::nan(""));
+  h->h_eigstats.assign(2 * N, 0);
+  for (int i = 0; i < N; ++i) {
+    double* dst = &h->h_eigvals[(size_t)i * nevmax * 2];
+    int slot = 0;
+    if (kpart[i]) {
+      dst[0] = INFINITY;
+      dst[1] = 0.0;
+      slot = 1;
+    }
+    // eigout holds one slot per selected eigenvalue (pairs once, with +imag)
+    for (int j = 0; j < nevmax && slot < nevmax; ++j) {
+      const double re = ev[(size_t)i * nevmax * 2 + 2 * j], im = ev[(size_t)i * nevmax * 2 + 2 * j + 1];
+      if (std::isnan(re)) break;
+      dst[2 * slot] = re;
+      dst[2 * slot + 1] = im;
+      ++slot;
+      if (im > 0 && slot < nevmax) {
+        dst[2 * slot] = re;
+        dst[2 * slot + 1] = -im;
+        ++slot;
+      }
+    }
+    h->h_eigstats[2 * i] = cycles[i];
+    h->h_eigstats[2 * i + 1] = kd[i];
+  }
+  orthonormalize_and_set_W(h, Z, mcols.data(), zld);
+  dfree(h, V);
+  dfree(h, W);
+  dfree(h, H);
+  dfree(h, Y);
+  dfree(h, Rscr);
+  dfree(h, Z);
+}
+
+// The local eigenproblems always run in FP64: the lumped splittings of floating
+// subdomains are singular and their factorisations with the replaced last pivot
+// have condition numbers around 1e8-1e9 for the target problems, so FP32 solves
+// would carry O(1) relative errors.
+void eigensolve(a2ls_handle* h, double* fac_tilde, const double* last_pivot, const double* diag_scale) {
+  eigensolve_t<double>(h, fac_tilde, last_pivot, diag_scale);
+}
+
+}  // namespace a2ls
