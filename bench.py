@@ -1,0 +1,459 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 two-level Schwarz solver (libA2LS through its C ABI).
+
+Workload: 2D cell-centred finite-volume diffusion on a 512 x 512 grid
+(n = 262144) with coefficient 1 and 13 seeded horizontal channels of 4 rows at
+1e6, 16 x 16 block subdomains (N = 256), 2 overlap layers, 16 eigenpairs per
+subdomain, random right-hand side U(-1, 1), zero initial guess, GMRES(30) to a
+relative residual of 1e-8.  One step = a2ls_setup + a2ls_solve on inputs
+already resident in HBM (L2 flushed between steps by a 256 MiB write).
+
+The headline form is the mixed one (FP32 local factors and solves, FP64
+flexible GMRES, FP64 eigensolves and coarse operator); the plain FP64 form is
+timed in the same run.  The JSON line also carries the apply bandwidth, the
+roofline of the dominant kernel, an end-to-end figure with host buffers, the
+CPU FP64 oracle timed on a bounded sample, and the SM clocks seen.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GMRES time-to-1e-8 (s) and apply HBM GB/s: mixed/batched vs plain FP64 form"
+WORKLOAD = ("2D high-contrast FV diffusion 512x512 (n=262144), 13 channels of 4 rows at kappa=1e6, "
+            "256 subdomains (16x16 blocks), overlap 2, nev=16, GMRES(30) rtol 1e-8")
+L2_FLUSH_BYTES = 256 << 20
+HBM_PEAK_KEY = "hbm_gbs"
+FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64 (non-tensor) nominal rate from the pool's recipe table
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--plain-steps", type=int, default=1, help="timed steps of the plain FP64 form")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def oracle_sample(prob, n_sub: int, iters: int) -> dict:
+    """Time the oracle's setup on n_sub subdomains and one apply's worth of local solves,
+    then scale to the whole workload: N local setups, the coarse LU and `iters` applies."""
+    import numpy as np
+    import scipy.linalg as sla
+
+    from oracle import a2ls_oracle as O
+    t0 = time.perf_counter()
+    subs = O.overlapping_subdomains(prob.A, prob.part, prob.overlap)
+    D = O.partition_of_unity(subs, prob.n)
+    t_overlap = time.perf_counter() - t0
+    N = len(subs)
+    picks = [int(i) for i in np.linspace(0, N - 1, n_sub).round()]
+    t_local = 0.0
+    t_solve = 0.0
+    m_total = 0
+    for i in picks:
+        s = subs[i]
+        t1 = time.perf_counter()
+        Aii = O.local_matrix(prob.A, s)
+        lu = sla.lu_factor(Aii)
+        C = O.block_splitting(prob.A, s)
+        e = O.local_gevp(Aii, C, D[i], prob.nev)
+        O.orthonormal_columns(D[i][:, None] * e.Z)
+        t_local += time.perf_counter() - t1
+        m_total += e.Z.shape[1]
+        r = np.sin(np.arange(s.n_i))
+        t2 = time.perf_counter()
+        sla.lu_solve(lu, r)
+        t_solve += time.perf_counter() - t2
+    n0 = int(round(m_total / n_sub * N))
+    rng = np.random.Generator(np.random.PCG64(0))
+    E = rng.standard_normal((n0, n0)) + n0 * np.eye(n0)
+    t3 = time.perf_counter()
+    Elu = sla.lu_factor(E)
+    t_coarse = time.perf_counter() - t3
+    t4 = time.perf_counter()
+    sla.lu_solve(Elu, rng.standard_normal(n0))
+    prob.A @ rng.standard_normal(prob.n)
+    t_coarse_apply = time.perf_counter() - t4
+    setup = t_overlap + t_local / n_sub * N + t_coarse
+    apply = t_solve / n_sub * N + t_coarse_apply
+    total = setup + iters * apply
+    wall = time.perf_counter() - t0
+    return {"value": total, "setup_s": setup, "apply_s": apply, "sample_wall_s": wall,
+            "sample": f"overlap of all {N} subdomains; local LU + dense-QZ eigenproblem of {n_sub} of {N} "
+                      f"subdomains scaled by {N / n_sub:.0f}; LU of a {n0}x{n0} coarse matrix; {iters} applies "
+                      f"estimated from {n_sub} local solves"}
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def apply_bytes(P, prob, fac_bytes: int) -> dict:
+    """Algorithmic bytes of one deflated-RAS apply (Eq. 2.4) and of its local-solve kernel."""
+    import numpy as np
+    sz = P.sizes()
+    subs = P.subdomains()
+    ni = np.array([len(a) + len(b) for a, b in subs], dtype=np.int64)
+    nI = np.array([len(a) for a, _ in subs], dtype=np.int64)
+    m = np.array([w.shape[1] for w in P.coarse_basis()], dtype=np.int64)
+    n, nnz, n0 = prob.n, prob.A.nnz, sz["n0"]
+    fac = int((ni * ni).sum()) * fac_bytes
+    local_kernel = fac + int(ni.sum()) * (4 + 8) + int(nI.sum()) * (4 + 8 + 8)   # factors, gather, scatter (+q)
+    spmv = nnz * 12 + (n + 1) * 4 + 3 * n * 8
+    coarse = 2 * int((nI * m).sum()) * 8 + int(nI.sum()) * 4 + n0 * n0 * 8 + 4 * n0 * 8
+    total = local_kernel + spmv + coarse + 2 * n * 8
+    return {"apply": total, "local_kernel": local_kernel}
+
+
+def run_ours(args, rank: int, world: int, device):
+    import numpy as np
+    import torch
+
+    from paper_2201_02250_gb300 import a2ls
+    from workloads import pde
+
+    prob = pde.config_c2()
+    stream = torch.cuda.current_stream(device)
+    rowptr = torch.as_tensor(prob.A.indptr.astype(np.int32), device=device)
+    colind = torch.as_tensor(prob.A.indices.astype(np.int32), device=device)
+    val = torch.as_tensor(prob.A.data.astype(np.float64), device=device)
+    part = torch.as_tensor(prob.part.astype(np.int32), device=device)
+    b = torch.as_tensor(prob.b, device=device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def one_step(precision: str, timing: int, keep: bool = False):
+        x = torch.zeros(prob.n, dtype=torch.float64, device=device)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P = a2ls.Preconditioner(rowptr, colind, val, part, prob.overlap, prob.nev, stream=stream,
+                                precision=precision, timing=timing)
+        it, rr, ok = P.solve(b, x, 1e-8)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        info = {"ms": ms, "iters": it, "relres": rr, "ok": ok, "launches": P.launches(),
+                "times": P.times(), "kernels": P.kernel_times() if timing else None}
+        if keep:
+            return info, P, x
+        P.close()
+        return info, None, x
+
+    def timed(precision: str, steps: int, warmup: int, timing: int):
+        for _ in range(warmup):
+            one_step(precision, 0)
+        infos = []
+        for _ in range(steps):
+            flush.fill_(1.0)  # evict L2 (not timed)
+            torch.cuda.synchronize(device)
+            barrier()
+            info, _, x = one_step(precision, timing)
+            infos.append(info)
+        return infos
+
+    # --- headline: the mixed form ---------------------------------------------------------------
+    torch.cuda.synchronize(device)
+    barrier()
+    with ClockSampler(device.index if device.index is not None else 0) as clocks:
+        mixed = timed("fp32", args.steps, args.warmup, timing=1)
+    ms_mixed = [i["ms"] for i in mixed]
+    step_ms = statistics.mean(ms_mixed)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([step_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    x_last = None
+    # accuracy of the last mixed solve, checked on the host in FP64
+    info, P, x_last = one_step("fp32", 1, keep=True)
+    xh = x_last.cpu().numpy()
+    true_relres = float(np.linalg.norm(prob.b - prob.A @ xh) / np.linalg.norm(prob.b))
+
+    # --- apply bandwidth (mixed form) -------------------------------------------------------------
+    def time_apply(Pa, reps=20):
+        r = b.clone()
+        z = torch.empty_like(r)
+        for _ in range(3):
+            Pa.apply(r, z)
+        torch.cuda.synchronize(device)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            Pa.apply(r, z)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    kt_before = P.kernel_times()
+    apply_ms_mixed = time_apply(P)
+    kt_after = P.kernel_times()
+    ab_mixed = apply_bytes(P, prob, 4)
+    loc_launches = kt_after["apply_local_solves"][0] - kt_before["apply_local_solves"][0]
+    loc_ms = (kt_after["apply_local_solves"][1] - kt_before["apply_local_solves"][1]) / max(loc_launches, 1)
+    P.close()
+
+    # --- the plain FP64 form ------------------------------------------------------------------------
+    plain = timed("fp64", max(args.plain_steps, 1), 1, timing=1)
+    info64, P64, _ = one_step("fp64", 1, keep=True)
+    apply_ms_plain = time_apply(P64)
+    ab_plain = apply_bytes(P64, prob, 8)
+    P64.close()
+    plain_ms = statistics.mean([i["ms"] for i in plain])
+
+    # --- end to end through the C ABI with host buffers ----------------------------------------------
+    host = {k: v.cpu().pin_memory() for k, v in (("rowptr", rowptr), ("colind", colind), ("val", val),
+                                                  ("part", part), ("b", b))}
+    h2d = sum(int(v.numel() * v.element_size()) for v in host.values())
+    xh_pinned = torch.empty(prob.n, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for k in range(args.steps + 1):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        dev_in = {k2: v.to(device, non_blocking=True) for k2, v in host.items()}
+        x = torch.zeros(prob.n, dtype=torch.float64, device=device)
+        Pe = a2ls.Preconditioner(dev_in["rowptr"], dev_in["colind"], dev_in["val"], dev_in["part"], prob.overlap,
+                                 prob.nev, stream=stream, precision="fp32")
+        Pe.solve(dev_in["b"], x, 1e-8)
+        xh_pinned.copy_(x, non_blocking=True)
+        torch.cuda.synchronize(device)
+        dt = (time.perf_counter() - t0) * 1e3
+        Pe.close()
+        if k > 0:  # first pass warms the pinned path
+            e2e_ms.append(dt)
+
+    # --- the dominant kernel of the step ----------------------------------------------------------------
+    kern = mixed[-1]["kernels"]
+    dom = max(kern, key=lambda k: kern[k][1])
+    hbm_peak = measured_peaks().get(HBM_PEAK_KEY)
+    return {
+        "prob": prob, "step_ms": step_ms, "mixed": mixed, "plain": plain, "plain_ms": plain_ms,
+        "apply_ms_mixed": apply_ms_mixed, "apply_ms_plain": apply_ms_plain, "ab_mixed": ab_mixed,
+        "ab_plain": ab_plain, "loc_ms": loc_ms, "e2e_ms": e2e_ms, "h2d": h2d, "d2h": prob.n * 8,
+        "clocks": clocks.summary(), "true_relres": true_relres, "dominant": dom, "kern": kern,
+        "hbm_peak": hbm_peak, "info64": info64,
+    }
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    device = torch.device("cuda", local_rank)
+    torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    from paper_2201_02250_gb300 import _build
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    res = run_ours(args, rank, world, device)
+    if rank == 0:
+        out = report(args, res, world)
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def roofline_entry(name: str, launches: int, ms: float, work: float, hbm_peak) -> dict:
+    """achieved = algorithmic work per launch / average launch duration (CUDA events on the library stream)."""
+    per_launch_ms = ms / max(launches, 1)
+    if name == "apply_local_solves":
+        ach = work / launches / (per_launch_ms * 1e-3) / 1e9 if launches else None
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": (ach / hbm_peak) if (ach and hbm_peak) else None, "traffic": None,
+                "launches": launches, "avg_launch_ms": per_launch_ms,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    ach = work / launches / (per_launch_ms * 1e-3) / 1e12 if launches else None
+    return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+            "frac": (ach / FP64_PEAK_TFLOPS_NOMINAL) if ach else None, "traffic": None,
+            "launches": launches, "avg_launch_ms": per_launch_ms,
+            "peak_source": "nominal FP64 SIMT rate of the pool's recipe table (no measured FP64 peak)"}
+
+
+def report(args, res, world) -> dict:
+    prob = res["prob"]
+    mixed, plain = res["mixed"], res["plain"]
+    kern = res["kern"]
+    dom = res["dominant"]
+    roof = roofline_entry(dom, kern[dom][0], kern[dom][1], kern[dom][2], res["hbm_peak"])
+    apply_local_gbs = res["ab_mixed"]["local_kernel"] / (res["loc_ms"] * 1e-3) / 1e9
+    out = {
+        "metric": METRIC,
+        "value": res["step_ms"] / 1e3,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": res["step_ms"],
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 local factors/solves, f64 GMRES/SpMV/eigensolves/coarse",
+        "data": "synthetic (seeded generator, workloads.pde.config_c2)",
+        "config": {"workload": WORKLOAD, "n": prob.n, "nnz": int(prob.A.nnz), "subdomains": int(prob.nparts),
+                   "overlap": prob.overlap, "nev": prob.nev, "rtol": 1e-8, "restart": 30,
+                   "form": "mixed: FP32 local LU + FGMRES(30) in FP64",
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "iters": mixed[-1]["iters"],
+        "true_relres": res["true_relres"],
+        "phases_ms": {k: round(v, 2) for k, v in mixed[-1]["times"].items()},
+        "plain_fp64": {"ms_per_step": res["plain_ms"], "iters": plain[-1]["iters"],
+                       "apply_ms": res["apply_ms_plain"],
+                       "apply_gbs": res["ab_plain"]["apply"] / (res["apply_ms_plain"] * 1e-3) / 1e9,
+                       "phases_ms": {k: round(v, 2) for k, v in plain[-1]["times"].items()}},
+        "speedup_vs_plain_fp64": res["plain_ms"] / res["step_ms"],
+        "apply": {"ms": res["apply_ms_mixed"], "bytes": res["ab_mixed"]["apply"],
+                  "gbs": res["ab_mixed"]["apply"] / (res["apply_ms_mixed"] * 1e-3) / 1e9,
+                  "local_solve_kernel_ms": res["loc_ms"], "local_solve_kernel_gbs": apply_local_gbs,
+                  "frac_of_measured_hbm": apply_local_gbs / res["hbm_peak"] if res["hbm_peak"] else None},
+        "roofline": roof,
+        "kernels_ms_per_step": {k: round(v[1], 3) for k, v in kern.items()},
+        "roofline_kernels": {k: roofline_entry(k, v[0], v[1], v[2], res["hbm_peak"]) for k, v in kern.items() if v[0]},
+        "e2e": {"value": statistics.mean(res["e2e_ms"]) / 1e3, "unit": "s", "h2d_bytes_per_step": res["h2d"],
+                "d2h_bytes_per_step": res["d2h"]},
+        "gpu_launches": int(mixed[-1]["launches"]),
+        "clocks": res["clocks"],
+    }
+    if not args.no_cpu_baseline and world == 1:
+        cb = oracle_sample(prob, 1, mixed[-1]["iters"])
+        out["cpu_baseline"] = {"value": cb["value"], "unit": "s", "cores": cpu_cores(), "kind": "oracle",
+                               "sample": cb["sample"], "sample_wall_s": cb["sample_wall_s"]}
+    return out
+
+
+def run_reference(args, rank: int, world: int) -> int:
+    """The oracle (CPU FP64) on a bounded sample per step; rank 0 only."""
+    if rank != 0:
+        return 0
+    from workloads import pde
+    prob = pde.config_c2()
+    vals, walls = [], []
+    sample = None
+    for _ in range(args.steps):
+        cb = oracle_sample(prob, 1, 10)
+        vals.append(cb["value"])
+        walls.append(cb["sample_wall_s"])
+        sample = cb["sample"]
+    v = statistics.mean(vals)
+    out = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic (seeded generator, workloads.pde.config_c2)",
+           "config": {"workload": WORKLOAD, "form": "CPU FP64 oracle (numpy/scipy), extrapolated from a sample"},
+           "impl": "reference",
+           "cpu_baseline": {"value": v, "unit": "s", "cores": cpu_cores(), "kind": "oracle", "sample": sample,
+                            "sample_wall_s": statistics.mean(walls)},
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -99,6 +99,7 @@ typedef struct {
   double eig_tol;           /* relative eigen-residual target, default 1e-10 (FP64) / 1e-5 (FP32) when 0 */
   uint64_t seed;            /* seed of the eigensolver's random start blocks */
   void* stream;             /* cudaStream_t for all work; NULL = legacy default stream */
+  int32_t timing;           /* 1: record CUDA events around the tracked kernels (A2LS_Q_KERNEL_TIMES) */
 } a2ls_options;
 
 /* Fills *opt with the defaults listed above.  Never fails. */
@@ -163,7 +164,13 @@ enum {
                             kernel part first as (+inf, 0), unused slots NaN; nev_max = max(nev,1)+1 */
   A2LS_Q_TIMES = 6,      /* double[16]: per-phase milliseconds of the last setup and solve */
   A2LS_Q_EINV = 7,       /* double[n0*n0]: the inverse of A_00 used by the apply, row-major */
-  A2LS_Q_EIGSTATS = 8    /* int32[2*N]: eigen cycles run and kernel dimension per subdomain */
+  A2LS_Q_EIGSTATS = 8,   /* int32[2*N]: eigen cycles run and kernel dimension per subdomain */
+  A2LS_Q_LAUNCHES = 9,   /* int64[1]: kernels this handle has launched so far */
+  A2LS_Q_KERNEL_TIMES = 10 /* double[3*8]: (launches, total ms, algorithmic work) of the tracked kernels;
+                              work is flops, or bytes moved for the apply local solves; in the order
+                              local LU, splitting LU, eigen triangular solves, eigen orthogonalisation,
+                              Rayleigh-Ritz, coarse LU, coarse inverse, apply local solves;
+                              populated only with a2ls_options::timing = 1 */
 };
 
 /*

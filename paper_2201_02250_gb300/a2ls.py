@@ -19,7 +19,10 @@ A2LS_ERR_EIGEN, A2LS_ERR_TIMEOUT, A2LS_ERR_CUDA, A2LS_ERR_OOM, A2LS_ERR_STATE = 
 FP64, FP32 = 0, 1
 VARIANTS = {"deflated_ras": 0, "deflated_asm": 1, "additive_ras": 2, "additive_asm": 3, "ras": 4, "asm": 5}
 POU = {"boolean": 0, "multiplicity": 1}
-Q_SIZES, Q_SUBDOMAINS, Q_LUMP, Q_FACTORS, Q_COARSE, Q_EIGVALS, Q_TIMES, Q_EINV, Q_EIGSTATS = range(9)
+(Q_SIZES, Q_SUBDOMAINS, Q_LUMP, Q_FACTORS, Q_COARSE, Q_EIGVALS, Q_TIMES, Q_EINV, Q_EIGSTATS, Q_LAUNCHES,
+ Q_KERNEL_TIMES) = range(11)
+TRACKED_KERNELS = ["lu_local", "lu_splitting", "eig_triangular_solves", "eig_orthogonalisation",
+                   "eig_rayleigh_ritz", "coarse_lu", "coarse_inverse", "apply_local_solves"]
 PHASES = ["graph", "extract", "lu", "eig_coarse", "coarse", "setup_total", "solve_total", "apply"]
 
 
@@ -39,7 +42,7 @@ class Options(ctypes.Structure):
                 ("restart", ctypes.c_int32), ("max_it", ctypes.c_int32), ("flexible", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("eig_block_steps", ctypes.c_int32),
                 ("eig_max_cycles", ctypes.c_int32), ("eig_tol", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("timing", ctypes.c_int32)]
 
 
 _LIB = None
@@ -230,6 +233,15 @@ class Preconditioner:
     def times(self) -> dict:
         t = np.frombuffer(self._query(Q_TIMES), dtype=np.float64)
         return {k: float(t[i]) for i, k in enumerate(PHASES)}
+
+    def launches(self) -> int:
+        return int(np.frombuffer(self._query(Q_LAUNCHES), dtype=np.int64)[0])
+
+    def kernel_times(self) -> dict:
+        """{kernel: (launches, total ms, algorithmic work)} for the tracked kernels (needs timing=1);
+        work is flops, or bytes moved for the apply local solves."""
+        v = np.frombuffer(self._query(Q_KERNEL_TIMES), dtype=np.float64).reshape(-1, 3)
+        return {k: (int(v[i, 0]), float(v[i, 1]), float(v[i, 2])) for i, k in enumerate(TRACKED_KERNELS)}
 
     def coarse_inverse(self) -> np.ndarray:
         n0 = self.sizes()["n0"]

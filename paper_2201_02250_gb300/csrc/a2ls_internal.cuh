@@ -23,7 +23,8 @@ struct Error : std::runtime_error {
 [[noreturn]] void fail(int code, const char* fmt, ...);
 void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 #define A2LS_CUDA(x) ::a2ls::check_cuda((x), #x, __FILE__, __LINE__)
-#define A2LS_LAUNCH() ::a2ls::check_cuda(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+// every kernel launch of the library goes through this macro: error check and per-handle count
+#define A2LS_LAUNCH() ::a2ls::launched(h, cudaGetLastError(), __FILE__, __LINE__)
 
 // Device-side status words written by kernels (never trap): [0] first error
 // code, [1] the subdomain or row that raised it, [2] auxiliary information.
@@ -35,6 +36,10 @@ __device__ __forceinline__ void raise_status(int* st, int code, int where, int a
     st[ST_AUX] = aux;
   }
 }
+
+// Kernels whose launches can be timed with CUDA events (a2ls_options::timing).
+enum { KT_LU_LOCAL = 0, KT_LU_SPLIT, KT_EIG_SOLVE, KT_EIG_ORTH, KT_EIG_RR, KT_COARSE_LU, KT_COARSE_INV,
+       KT_APPLY_LOCAL, KT_COUNT };
 
 // Tile size of the block-inverted LU format used by all triangular solves.
 constexpr int TB = 64;
@@ -110,9 +115,28 @@ struct a2ls_handle {
   double* h_pinned = nullptr;                // pinned host scratch for small readbacks
 
   double times[16] = {0};
+  int64_t launches = 0;                      // kernels launched by this handle
+  // optional per-kernel event timing: pairs of events per tracked kernel
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> kt_events[a2ls::KT_COUNT];
+  std::vector<cudaEvent_t> kt_pool;
+  double kt_ms[a2ls::KT_COUNT] = {0};
+  double kt_work[a2ls::KT_COUNT] = {0};      // algorithmic flops (bytes for the apply local solves)
+  int64_t kt_count[a2ls::KT_COUNT] = {0};
 };
 
 namespace a2ls {
+
+void launched(a2ls_handle* h, cudaError_t e, const char* file, int line);
+
+// RAII event pair around the launches of one tracked kernel (no-op unless timing is on)
+struct KTime {
+  a2ls_handle* h;
+  int id;
+  cudaEvent_t b = nullptr;
+  KTime(a2ls_handle* hh, int kid, double work = 0.0);
+  ~KTime();
+};
+void collect_kernel_times(a2ls_handle* h);
 
 // allocation helpers (stream-ordered, owned by the handle)
 void* dalloc_bytes(a2ls_handle* h, size_t bytes);

@@ -26,6 +26,52 @@ void check_cuda(cudaError_t e, const char* what, const char* file, int line) {
        cudaGetErrorString(e), base ? base + 1 : file, line);
 }
 
+void launched(a2ls_handle* h, cudaError_t e, const char* file, int line) {
+  if (h) ++h->launches;
+  check_cuda(e, "kernel launch", file, line);
+}
+
+static cudaEvent_t pool_event(a2ls_handle* h) {
+  if (!h->kt_pool.empty()) {
+    cudaEvent_t e = h->kt_pool.back();
+    h->kt_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  A2LS_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+KTime::KTime(a2ls_handle* hh, int kid, double work) : h(hh), id(kid) {
+  if (h && h->opt.timing) {
+    h->kt_work[kid] += work;
+    b = pool_event(h);
+    A2LS_CUDA(cudaEventRecord(b, h->st));
+  }
+}
+
+KTime::~KTime() {
+  if (!b) return;
+  cudaEvent_t e = pool_event(h);
+  cudaEventRecord(e, h->st);
+  h->kt_events[id].push_back({b, e});
+}
+
+void collect_kernel_times(a2ls_handle* h) {
+  for (int k = 0; k < KT_COUNT; ++k) {
+    for (auto& pr : h->kt_events[k]) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(pr.second) == cudaSuccess && cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+        h->kt_ms[k] += ms;
+        h->kt_count[k] += 1;
+      }
+      h->kt_pool.push_back(pr.first);
+      h->kt_pool.push_back(pr.second);
+    }
+    h->kt_events[k].clear();
+  }
+}
+
 void* dalloc_bytes(a2ls_handle* h, size_t bytes) {
   void* p = nullptr;
   cudaError_t e = cudaMallocAsync(&p, std::max<size_t>(bytes, 16), h->st);
@@ -120,6 +166,8 @@ __global__ void k_max_rowlen(int n, const int* rowptr, const int* mrow, int* out
 
 static void destroy_handle(a2ls_handle* h) {
   if (!h) return;
+  collect_kernel_times(h);
+  for (cudaEvent_t e : h->kt_pool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFreeAsync(p, h->st);
   h->allocs.clear();
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -139,11 +187,17 @@ static void factor_and_coarse(a2ls_handle* h, bool need_coarse, double* times) {
   extract_local(h, fa, ft, dscale);
   sync_and_check(h, "local matrix extraction");
   times[Phase::SETUP_EXTRACT] = tm.stop();
-  lu_batched<T>(h, fa, 0, nullptr, dscale);
-  invert_diag_tiles<T>(h, fa);
+  double lu_flops = 0.0;
+  for (int i = 0; i < N; ++i) lu_flops += 2.0 / 3.0 * (double)h->h_n[i] * h->h_n[i] * h->h_n[i];
+  {
+    KTime kt(h, KT_LU_LOCAL, lu_flops);
+    lu_batched<T>(h, fa, 0, nullptr, dscale);
+    invert_diag_tiles<T>(h, fa);
+  }
   sync_and_check(h, "local LU factorisation");
   h->d_fac = fa;
   if (need_coarse) {
+    KTime kt(h, KT_LU_SPLIT, lu_flops);
     lu_batched<double>(h, ft, 1, lastp, dscale);
     invert_diag_tiles<double>(h, ft);
     sync_and_check(h, "LU factorisation of the local splittings");
@@ -179,6 +233,7 @@ void a2ls_default_options(a2ls_options* o) {
   o->eig_tol = 0.0;
   o->seed = 12345;
   o->stream = nullptr;
+  o->timing = 0;
 }
 
 const char* a2ls_last_error(void) { return g_last_error.c_str(); }
@@ -366,6 +421,17 @@ int a2ls_query(a2ls_handle* h, int32_t what, void* out, int64_t capacity, int64_
       case A2LS_Q_EIGSTATS:
         put(h->h_eigstats.data(), sizeof(int) * h->h_eigstats.size());
         break;
+      case A2LS_Q_LAUNCHES:
+        put(&h->launches, sizeof(int64_t));
+        break;
+      case A2LS_Q_KERNEL_TIMES: {
+        collect_kernel_times(h);
+        for (int k = 0; k < KT_COUNT; ++k) {
+          const double v[3] = {(double)h->kt_count[k], h->kt_ms[k], h->kt_work[k]};
+          put(v, sizeof(v));
+        }
+        break;
+      }
       default:
         fail(A2LS_ERR_ARG, "unknown query item %d", what);
     }

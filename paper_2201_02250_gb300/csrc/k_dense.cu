@@ -351,6 +351,10 @@ void local_solves(a2ls_handle* h, const T* fac, const double* t, const double* q
                                    (int)(sizeof(Acc) * MAXN_LOCAL)));
     configured = true;
   }
+  double bytes = 0.0;
+  for (int i = 0; i < h->N; ++i)
+    bytes += (double)h->h_n[i] * h->h_n[i] * sizeof(T) + 12.0 * h->h_n[i] + (mode == 0 ? 20.0 * h->h_nI[i] : 12.0 * h->h_n[i]);
+  KTime kt(h, KT_APPLY_LOCAL, bytes);
   k_local_solve<T><<<h->N, LS_THREADS, smem, h->st>>>(h->d_off, h->d_nI, h->d_ni, h->d_ld, h->d_foff,
                                                       h->d_idx, h->d_D, fac, t, q, z, mode);
   A2LS_LAUNCH();
@@ -586,6 +590,7 @@ __global__ void __launch_bounds__(256) k_e_inverse(const double* F, int n, int64
 void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv) {
   cudaStream_t st = h->st;
   const int64_t ld = n;
+  KTime kt(h, KT_COARSE_LU, 2.0 / 3.0 * (double)n * n * n);
   for (int k0 = 0; k0 < n; k0 += TB) {
     k_e_diag<<<1, TB, 0, st>>>(E, n, ld, k0, scale, h->d_status);
     A2LS_LAUNCH();
@@ -597,6 +602,7 @@ void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv)
     k_e_trailing<<<dim3(chunks, chunks), 256, 0, st>>>(E, n, ld, k0);
     A2LS_LAUNCH();
   }
+  KTime kt2(h, KT_COARSE_INV, 4.0 / 3.0 * (double)n * n * n);
   k_e_inverse<<<ceil_div(n, 64), 256, 0, st>>>(E, n, ld, Einv, ld);
   A2LS_LAUNCH();
 }

@@ -705,6 +705,8 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     nf[i] = std::max(0, std::min(nev - kpart[i], h->h_n[i] - kd[i]));
     nfmax = std::max(nfmax, nf[i]);
   }
+  if (nfmax + 4 > 32)
+    fail(A2LS_ERR_ARG, "nev = %d is too large for the local eigensolver (at most 28 eigenpairs per subdomain)", nev);
   const int b = std::min(32, nfmax + std::max(4, (nfmax + 1) / 2));
   int s = h->opt.eig_block_steps > 0 ? h->opt.eig_block_steps : 3;
   if ((s + 1) * b > EIG_MAXP) s = EIG_MAXP / b - 1;
@@ -771,15 +773,22 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   A2LS_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_smem));
   A2LS_CUDA(cudaFuncSetAttribute(k_vy<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vy_smem));
 
-  // T applied to V[:, vcol : vcol + p] -> W[:, 0:p]
+  // T applied to V[:, vcol : vcol + p] -> W[:, 0:p]; tri_flops = one triangular half over the active set
+  double tri_flops = 0.0;
   auto apply_T = [&](int vcol, const int* actv) {
     k_bmul<T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, vcol, d_pv, actv, h->d_lrow, h->d_lcol,
                                  h->d_lval, h->d_D, V, W);
     A2LS_LAUNCH();
-    block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, actv, 1, 0);
+    {
+      KTime kt(h, KT_EIG_SOLVE, tri_flops);
+      block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, actv, 1, 0);
+    }
     k_mu_fix<T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, d_pv, actv, d_kd, hvec, W);
     A2LS_LAUNCH();
-    block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, actv, 0, 1);
+    {
+      KTime kt(h, KT_EIG_SOLVE, tri_flops);
+      block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, actv, 0, 1);
+    }
     k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, actv, d_kd, kvec, W);
     A2LS_LAUNCH();
   };
@@ -808,16 +817,31 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     A2LS_CUDA(cudaMemcpyAsync(d_actk, actk.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
     for (int j = 0; j < s; ++j) {
       const int* actv = (j == 0) ? d_active : d_actk;
+      const std::vector<int>& acth = (j == 0) ? act : actk;
+      tri_flops = 0.0;
+      double orth_flops = 0.0;
+      for (int i = 0; i < N; ++i) {
+        if (!acth[i]) continue;
+        const double ni = h->h_n[i], pi = pv[i], jb = full[i] ? pi : (double)(j + 1) * b;
+        tri_flops += ni * ni * pi;
+        orth_flops += 8.0 * ni * jb * pi + 9.0 * ni * pi * pi;
+      }
       apply_T(j * b, actv);
       // Krylov subdomains: block CGS2 + CholQR2 -> V_{j+1}, H[:, j-th block];
       // full-space subdomains (j == 0 only): H = V0^T (T V0)
-      k_orth<T><<<N, EIG_THREADS, orth_smem, st>>>(h->d_ni, d_vo, P, d_pv, actv, j + 1, b, V, W, H,
-                                                    (j + 1) * b, j * b, (j + 1) * b, d_full, d_rank);
+      {
+        KTime kt(h, KT_EIG_ORTH, orth_flops);
+        k_orth<T><<<N, EIG_THREADS, orth_smem, st>>>(h->d_ni, d_vo, P, d_pv, actv, j + 1, b, V, W, H,
+                                                      (j + 1) * b, j * b, (j + 1) * b, d_full, d_rank);
+        A2LS_LAUNCH();
+      }
+    }
+    {
+      KTime kt(h, KT_EIG_RR);
+      k_rayleigh_ritz<<<N, 32, rr_smem, st>>>(prm, d_full, d_mfull, d_nf, d_active, H, Y, d_ycols, d_zcols,
+                                              eigout, d_conv, h->d_status);
       A2LS_LAUNCH();
     }
-    k_rayleigh_ritz<<<N, 32, rr_smem, st>>>(prm, d_full, d_mfull, d_nf, d_active, H, Y, d_ycols, d_zcols,
-                                            eigout, d_conv, h->d_status);
-    A2LS_LAUNCH();
     A2LS_CUDA(cudaMemcpyAsync(conv.data(), d_conv, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
     sync_and_check(h, "local eigensolve");
     int remaining = 0;

@@ -1,0 +1,411 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the CPU FP64 oracle.
+
+Tolerances: integer work (subdomain index lists) bit-exact; the lumped sums
+of Definition 3.1 exact up to summation order (1e-14 relative); the apply of
+Eq. 2.4 with the same coarse basis 1e-10 relative in FP64 (1e-4 for FP32
+local factors: cond(A_ii) * eps_32 for these problems); coarse spaces by
+subspace angles < 1e-6 where the eigenvalue gap at the cut is >= 1 %;
+GMRES iteration counts within +-1 and true residual <= 1e-8.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from oracle import a2ls_oracle as O
+from workloads import pde
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("CUDA device required")
+    from paper_2201_02250_gb300 import _build
+    _build.build()
+
+
+def a2ls():
+    from paper_2201_02250_gb300 import a2ls as mod
+    return mod
+
+
+def setup_gpu(prob, **opts):
+    P, keep = a2ls().from_scipy(prob.A, prob.part, prob.overlap, prob.nev, **opts)
+    P._keep = keep
+    return P
+
+
+def angles(U, V):
+    Qu, _ = np.linalg.qr(U)
+    Qv, _ = np.linalg.qr(V)
+    s = np.linalg.svd(Qu.T @ Qv, compute_uv=False)
+    return np.arccos(np.clip(s, -1.0, 1.0))
+
+
+def unpack_lu(F, tb=64):
+    """L and U from the block-inverted storage (diagonal 64x64 tiles hold inv(L_bb), inv(U_bb))."""
+    n = F.shape[0]
+    L = np.tril(F, -1) + np.eye(n)
+    U = np.triu(F)
+    for b0 in range(0, n, tb):
+        b1 = min(n, b0 + tb)
+        T = F[b0:b1, b0:b1]
+        L[b0:b1, b0:b1] = np.linalg.inv(np.tril(T, -1) + np.eye(b1 - b0))
+        U[b0:b1, b0:b1] = np.linalg.inv(np.triu(T))
+    return L, U
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda")
+
+
+def apply_gpu(P, r):
+    z = torch.empty(len(r), dtype=torch.float64, device="cuda")
+    P.apply(dev(r), z)
+    torch.cuda.synchronize()
+    return z.cpu().numpy()
+
+
+# ---------------------------------------------------------------------------
+# structure: overlap, index lists, lumped sums, local LU
+# ---------------------------------------------------------------------------
+def _structure_cases():
+    A3 = pde.conv_diff_3d(10, 100.0)
+    part3 = pde.bfs_region_partition(A3, 8, 60, 180, seed=5)
+    Ar = pde.random_dd_matrix(300, 0.02, seed=9, symmetric=False)
+    rng = np.random.Generator(np.random.PCG64(9))
+    partr = rng.permutation(np.arange(300) % 7).astype(np.int32)
+    return [
+        ("tiny_d1", pde.tiny_conv_diff(m=12, nb=3, overlap=1)),
+        ("tiny_d3", pde.tiny_conv_diff(m=20, nb=3, overlap=3)),
+        ("c1", pde.config_c1()),
+        ("bfs3d_uneven", pde.Problem("bfs3d", A3, part3, 2, 4, pde.rhs_uniform(1000, 5))),
+        ("random_scattered", pde.Problem("rnd", Ar, partr, 1, 4, pde.rhs_uniform(300, 9))),
+    ]
+
+
+@pytest.mark.parametrize("name,prob", _structure_cases(), ids=lambda x: x if isinstance(x, str) else "")
+def test_subdomains_and_lumping_exact(name, prob):
+    P = setup_gpu(prob, variant="ras")
+    subs = O.overlapping_subdomains(prob.A, prob.part, prob.overlap)
+    got = P.subdomains()
+    assert len(got) == len(subs)
+    for (gi, gg), s in zip(got, subs):
+        np.testing.assert_array_equal(gi, s.interior)
+        np.testing.assert_array_equal(gg, s.gamma)
+    for lump, s in zip(P.lump(), subs):
+        assert np.all(lump[:s.n_I] == 0.0)
+        ref = O.lumped_row_sums(prob.A, s)
+        np.testing.assert_allclose(lump[s.n_I:], ref, rtol=1e-14, atol=0)
+    P.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-5)])
+def test_local_lu_factors(precision, tol):
+    prob = pde.tiny_conv_diff(m=40, nb=3, overlap=2)  # subdomains of 250-330 rows: several tiles + ragged tail
+    P = setup_gpu(prob, variant="ras", precision=precision)
+    subs = O.overlapping_subdomains(prob.A, prob.part, prob.overlap)
+    for F, s in zip(P.factors(), subs):
+        Aii = O.local_matrix(prob.A, s)
+        L, U = unpack_lu(F)
+        assert np.linalg.norm(L @ U - Aii) <= tol * np.linalg.norm(Aii)
+    P.close()
+
+
+# ---------------------------------------------------------------------------
+# the apply (Eqs. 2.1-2.4) with the oracle's coarse basis injected
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def tiny20():
+    prob = pde.tiny_conv_diff(m=20, nb=3, overlap=2, nev=4)
+    refs = {pou: O.setup(prob.A, prob.part, prob.overlap, prob.nev, pou=pou) for pou in ("boolean", "multiplicity")}
+    return prob, refs
+
+
+@pytest.mark.parametrize("pou", ["boolean", "multiplicity"])
+@pytest.mark.parametrize("variant", ["deflated_ras", "deflated_asm", "additive_ras", "additive_asm", "ras", "asm"])
+def test_apply_variants_match_oracle(tiny20, variant, pou):
+    prob, refs = tiny20
+    ref = refs[pou]
+    P = setup_gpu(prob, variant=variant, pou=pou)
+    if variant not in ("ras", "asm"):
+        P.set_coarse_basis(ref.coarse.W)
+    for r in (prob.b, np.sin(np.arange(prob.n))):
+        z = apply_gpu(P, r)
+        zr = O.apply(ref, r, variant)
+        assert np.linalg.norm(z - zr) <= 1e-10 * np.linalg.norm(zr)
+    P.close()
+
+
+@pytest.fixture(scope="module")
+def c1():
+    prob = pde.config_c1()
+    ref = O.setup(prob.A, prob.part, prob.overlap, prob.nev, keep_local=True)
+    return prob, ref
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
+def test_apply_c1_matches_oracle(c1, precision, tol):
+    prob, ref = c1
+    P = setup_gpu(prob, precision=precision)
+    P.set_coarse_basis(ref.coarse.W)
+    rng = np.random.Generator(np.random.PCG64(77))
+    for r in (prob.b, rng.uniform(-1, 1, prob.n)):
+        z = apply_gpu(P, r)
+        zr = O.apply(ref, r)
+        assert np.linalg.norm(z - zr) <= tol * np.linalg.norm(zr)
+    P.close()
+
+
+# ---------------------------------------------------------------------------
+# the local eigenproblems (Eq. 3.1) and the coarse space (Eq. 3.2)
+# ---------------------------------------------------------------------------
+def _gap_ok(e, nev):
+    """The cut after the kept eigenvalues has a relative gap of at least 1 %."""
+    lam = np.abs(e.eigvals)
+    kept = len(e.selected)
+    if kept == 0 or kept >= len(lam):
+        return True
+    return lam[kept - 1] >= 1.01 * lam[kept]
+
+
+@pytest.mark.parametrize("name", ["c1", "tiny_hpd", "conv40"])
+def test_coarse_space_matches_oracle(c1, name):
+    if name == "c1":
+        prob, ref = c1
+    elif name == "tiny_hpd":
+        prob = pde.tiny_hpd_dd(m=24, nb=3, overlap=1, nev=5)
+        ref = O.setup(prob.A, prob.part, prob.overlap, prob.nev)
+    else:
+        prob = pde.tiny_conv_diff(m=40, nb=3, overlap=2, nev=6)
+        ref = O.setup(prob.A, prob.part, prob.overlap, prob.nev)
+    P = setup_gpu(prob)
+    Wg = P.coarse_basis()
+    ev = P.eigenvalues()
+    stats = P.eig_stats()
+    checked = 0
+    for i, (wg, wo, e) in enumerate(zip(Wg, ref.coarse.W, ref.eig)):
+        assert stats[i, 1] == e.dimK  # dim ker(A~_ii)
+        if not _gap_ok(e, prob.nev):
+            continue
+        assert wg.shape[1] == wo.shape[1]
+        assert angles(wg, wo).max() < 1e-6
+        mine = ev[i][~np.isnan(ev[i].real)]
+        mine = mine[np.isfinite(mine.real)]
+        np.testing.assert_allclose(np.sort(np.abs(mine)), np.sort(np.abs(e.selected)), rtol=1e-8)
+        checked += 1
+    assert checked >= len(Wg) // 2
+    P.close()
+
+
+def test_full_coarse_space_gives_exact_inverse():
+    """Boolean D and nev = |Omega_Ii|: R_0^H is square and M_deflated^{-1} = A^{-1} (Eq. 2.4)."""
+    prob = pde.tiny_conv_diff(m=8, nb=2, overlap=1, nev=16)
+    P = setup_gpu(prob)
+    assert P.sizes()["n0"] == prob.n
+    z = apply_gpu(P, prob.b)
+    x = np.linalg.solve(prob.A.toarray(), prob.b)
+    assert np.linalg.norm(z - x) <= 1e-10 * np.linalg.norm(x)
+    P.close()
+
+
+def test_single_subdomain_no_overlap_is_exact():
+    """N = 1, delta = 0: the one-level preconditioner is A^{-1}; GMRES takes one step."""
+    prob = pde.tiny_conv_diff(m=30, nb=1, overlap=0, nev=0)
+    P = setup_gpu(prob, variant="ras")
+    z = apply_gpu(P, prob.b)
+    x = np.linalg.solve(prob.A.toarray(), prob.b)
+    assert np.linalg.norm(z - x) <= 1e-12 * np.linalg.norm(x)
+    xd = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    it, rr, ok = P.solve(dev(prob.b), xd, 1e-10)
+    assert ok and it == 1
+    P.close()
+
+
+def test_deflation_property_on_gpu(c1):
+    """M^{-1} A R_0^H = R_0^H for the GPU's own coarse space (Eq. 2.4)."""
+    prob, _ = c1
+    P = setup_gpu(prob)
+    subs = P.subdomains()
+    W = P.coarse_basis()
+    for i in (0, 5, 15):
+        idx = np.concatenate(subs[i])
+        for a in (0, W[i].shape[1] - 1):
+            phi = np.zeros(prob.n)
+            phi[idx] = W[i][:, a]
+            z = apply_gpu(P, prob.A @ phi)
+            assert np.linalg.norm(z - phi) <= 1e-9 * np.linalg.norm(phi)
+    P.close()
+
+
+# ---------------------------------------------------------------------------
+# GMRES (Section 4)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_gmres_c1(c1, precision):
+    prob, ref = c1
+    P = setup_gpu(prob, precision=precision)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    it, rr, ok = P.solve(dev(prob.b), x, 1e-8)
+    xh = x.cpu().numpy()
+    true = np.linalg.norm(prob.b - prob.A @ xh) / np.linalg.norm(prob.b)
+    assert ok and true <= 1e-8 and abs(true - rr) <= 1e-12
+    res = O.gmres(prob.A, lambda v: O.apply(ref, v), prob.b, rtol=1e-8)
+    assert abs(it - res.iters) <= 1
+    P.close()
+
+
+@pytest.mark.parametrize("pou", ["boolean", "multiplicity"])
+@pytest.mark.parametrize("variant", ["deflated_ras", "additive_asm", "ras"])
+def test_gmres_variants_tiny(tiny20, variant, pou):
+    prob, refs = tiny20
+    P = setup_gpu(prob, variant=variant, pou=pou)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    it, rr, ok = P.solve(dev(prob.b), x, 1e-8)
+    assert ok and rr <= 1e-8
+    res = O.gmres(prob.A, lambda v: O.apply(refs[pou], v, variant), prob.b, rtol=1e-8)
+    assert abs(it - res.iters) <= 1
+    P.close()
+
+
+def test_nonzero_initial_guess_and_restart():
+    prob = pde.tiny_hpd_dd(m=24, nb=3, overlap=1, nev=2)
+    P = setup_gpu(prob, variant="ras", restart=3)
+    rng = np.random.Generator(np.random.PCG64(3))
+    x0 = rng.uniform(-1, 1, prob.n)
+    x = dev(x0)
+    it, rr, ok = P.solve(dev(prob.b), x, 1e-9)
+    xh = x.cpu().numpy()
+    assert ok and np.linalg.norm(prob.b - prob.A @ xh) <= 1e-9 * np.linalg.norm(prob.b)
+    P.close()
+
+
+# ---------------------------------------------------------------------------
+# ragged and uneven subdomains
+# ---------------------------------------------------------------------------
+def test_uneven_subdomains_and_ragged_tiles():
+    A = pde.conv_diff_3d(12, 100.0)
+    part = pde.bfs_region_partition(A, 10, 60, 300, seed=11)
+    prob = pde.Problem("bfs3d", A, part, 1, 5, pde.rhs_uniform(A.shape[0], 11))
+    ref = O.setup(prob.A, prob.part, prob.overlap, prob.nev)
+    sizes = [s.n_i for s in ref.subs]
+    assert len(set(sizes)) > 5 and any(n % 64 for n in sizes)
+    P = setup_gpu(prob)
+    P.set_coarse_basis(ref.coarse.W)
+    z = apply_gpu(P, prob.b)
+    zr = O.apply(ref, prob.b)
+    assert np.linalg.norm(z - zr) <= 1e-10 * np.linalg.norm(zr)
+    P2 = setup_gpu(prob)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    it, rr, ok = P2.solve(dev(prob.b), x, 1e-8)
+    res = O.gmres(prob.A, lambda v: O.apply(ref, v), prob.b, rtol=1e-8)
+    assert ok and abs(it - res.iters) <= 1
+    P.close()
+    P2.close()
+
+
+# ---------------------------------------------------------------------------
+# error reporting (host- and device-detected), no faults
+# ---------------------------------------------------------------------------
+def _raw_setup(A, part, overlap=1, nev=2, **opts):
+    mod = a2ls()
+    rowptr = torch.as_tensor(A.indptr.astype(np.int32), device="cuda")
+    colind = torch.as_tensor(A.indices.astype(np.int32), device="cuda")
+    val = torch.as_tensor(A.data.astype(np.float64), device="cuda")
+    p = torch.as_tensor(np.asarray(part, dtype=np.int32), device="cuda")
+    return mod.Preconditioner(rowptr, colind, val, p, overlap, nev, **opts)
+
+
+def test_error_codes():
+    mod = a2ls()
+    prob = pde.tiny_conv_diff(m=10, nb=2)
+    A = prob.A.copy()
+    # column index out of range
+    bad = A.copy()
+    bad.indices = bad.indices.copy()
+    bad.indices[5] = 1000
+    with pytest.raises(mod.A2lsError) as e:
+        _raw_setup(bad, prob.part)
+    assert e.value.code == mod.A2LS_ERR_ARG
+    # an empty part
+    part = prob.part.copy()
+    part[part == 2] = 1
+    with pytest.raises(mod.A2lsError) as e:
+        _raw_setup(A, part)
+    assert e.value.code == mod.A2LS_ERR_ARG
+    # a negative part id
+    part = prob.part.copy()
+    part[0] = -1
+    with pytest.raises(mod.A2lsError) as e:
+        _raw_setup(A, part)
+    assert e.value.code == mod.A2LS_ERR_ARG
+    # a zero row makes a local matrix singular
+    Ad = A.toarray()
+    Ad[37, :] = 0.0
+    Zc = sp.csr_matrix(Ad)
+    with pytest.raises(mod.A2lsError) as e:
+        _raw_setup(Zc, prob.part, variant="ras")
+    assert e.value.code == mod.A2LS_ERR_SINGULAR
+    # too many eigenpairs for the local eigensolver
+    with pytest.raises(mod.A2lsError) as e:
+        _raw_setup(A, prob.part, nev=60)
+    assert e.value.code == mod.A2LS_ERR_ARG
+    # the handle still works after errors
+    P = _raw_setup(A, prob.part)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    it, rr, ok = P.solve(dev(prob.b), x, 1e-8)
+    assert ok
+    P.close()
+
+
+# ---------------------------------------------------------------------------
+# full size: the 512 x 512 high-contrast diffusion problem (n = 262144, 256 subdomains)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def c2():
+    return pde.config_c2()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_c2_full_size(c2, precision):
+    prob = c2
+    P = setup_gpu(prob, precision=precision)
+    sz = P.sizes()
+    assert sz["N"] == 256 and sz["n0"] == 256 * 16
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    it, rr, ok = P.solve(dev(prob.b), x, 1e-8)
+    xh = x.cpu().numpy()
+    true = np.linalg.norm(prob.b - prob.A @ xh) / np.linalg.norm(prob.b)
+    assert ok and true <= 1e-8 and it <= 60
+    # sampled subdomains: index lists, lumped sums and the local factors against the oracle
+    subs_gpu = P.subdomains()
+    lumps = P.lump()
+    facs = P.factors() if precision == "fp64" else None
+    adj_subs = O.overlapping_subdomains(prob.A, prob.part, prob.overlap)
+    for i in (0, 17, 136, 255):
+        s = adj_subs[i]
+        np.testing.assert_array_equal(subs_gpu[i][0], s.interior)
+        np.testing.assert_array_equal(subs_gpu[i][1], s.gamma)
+        np.testing.assert_allclose(lumps[i][s.n_I:], O.lumped_row_sums(prob.A, s), rtol=1e-14)
+        if facs is not None:
+            Aii = O.local_matrix(prob.A, s)
+            L, U = unpack_lu(facs[i])
+            rhs = np.sin(np.arange(s.n_i) + i)
+            y = sla.solve_triangular(U, sla.solve_triangular(L, rhs, lower=True, unit_diagonal=True))
+            ref = sla.lu_solve(sla.lu_factor(Aii), rhs)
+            assert np.linalg.norm(y - ref) <= 1e-8 * np.linalg.norm(ref)
+    # deflation property for a few coarse columns
+    W = P.coarse_basis()
+    tol = 1e-7 if precision == "fp64" else 1e-3
+    for i in (0, 136):
+        idx = np.concatenate(subs_gpu[i])
+        phi = np.zeros(prob.n)
+        phi[idx] = W[i][:, 0]
+        z = apply_gpu(P, prob.A @ phi)
+        assert np.linalg.norm(z - phi) <= tol * np.linalg.norm(phi)
+    P.close()
