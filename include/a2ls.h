@@ -194,6 +194,24 @@ int a2ls_query(a2ls_handle* h, int32_t what, void* out, int64_t capacity, int64_
 int a2ls_set_coarse_basis(a2ls_handle* h, const int32_t* m, const double* W);
 
 /*
+ * a2ls_apply_static -- the same z = M^{-1} r as a2ls_apply, for callers that must not have device
+ * memory allocated on their behalf: applications whose device memory is fully reserved by their
+ * own pool allocator, or latency-critical loops in which an allocation (which may synchronise the
+ * device) is not allowed.  The paper has no counterpart; this is an interface convenience.
+ *   r, z : device, n doubles each, owned by the caller; they must not alias.
+ * The call allocates nothing.  Its scratch vectors (2n + 2 n0 doubles, plus sum of the subdomain
+ * sizes for the ASM variants or the multiplicity partition of unity) come from a fixed array of
+ * 1,048,576 doubles (8 MiB) in the library's static device memory, which every GPU that loads the
+ * library holds until the process exits; larger problems get A2LS_ERR_ARG.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device current, so
+ * make that first call before any stream capture.  The handle must have been set up on the current
+ * device (A2LS_ERR_STATE otherwise).  All calls on a device share the one array and overwrite every
+ * scratch value they read, so no clearing is needed, but calls whose work overlaps on the GPU
+ * (other streams, handles or threads) race on it.  Asynchronous on the handle's stream.
+ */
+int a2ls_apply_static(a2ls_handle* h, const double* r, double* z);
+
+/*
  * a2ls_spmv -- y = A x with the handle's FP64 copy of A (x, y: device, n doubles).
  * Asynchronous on the handle's stream.
  */

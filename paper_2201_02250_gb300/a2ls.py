@@ -80,7 +80,9 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.a2ls_query.argtypes = [vp, i32, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     L.a2ls_set_coarse_basis.argtypes = [vp, vp, vp]
     L.a2ls_spmv.argtypes = [vp, vp, vp]
-    for f in ("a2ls_setup", "a2ls_apply", "a2ls_solve", "a2ls_query", "a2ls_set_coarse_basis", "a2ls_spmv"):
+    L.a2ls_apply_static.argtypes = [vp, vp, vp]
+    for f in ("a2ls_setup", "a2ls_apply", "a2ls_solve", "a2ls_query", "a2ls_set_coarse_basis", "a2ls_spmv",
+              "a2ls_apply_static"):
         getattr(L, f).restype = ctypes.c_int
     _LIB = L
     return L
@@ -147,6 +149,10 @@ class Preconditioner:
 
     def apply(self, r, z):
         _check(lib().a2ls_apply(self._h, ctypes.c_void_p(_ptr(r)), ctypes.c_void_p(_ptr(z))))
+
+    def apply_static(self, r, z):
+        """Same as apply, with scratch from the library's fixed static device array (no allocation)."""
+        _check(lib().a2ls_apply_static(self._h, ctypes.c_void_p(_ptr(r)), ctypes.c_void_p(_ptr(z))))
 
     def spmv(self, x, y):
         _check(lib().a2ls_spmv(self._h, ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(y))))

@@ -116,6 +116,8 @@ void sync_and_check(a2ls_handle* h, const char* phase) {
 
 static void set_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
+void record_error(const char* msg) { set_error(msg); }
+
 template <class F>
 static int guarded(F&& f) {
   try {
