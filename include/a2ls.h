@@ -50,9 +50,11 @@ typedef enum {
   A2LS_ERR_STATE = 8          /* call not valid in the handle's current state */
 } a2ls_status;
 
-/* Precision of the local factors, local solves and local eigensolves.  The
- * SpMV, the GMRES orthogonalisation, the residual and the coarse operator are
- * always FP64. */
+/* Precision of the local factors of A_ii and of the local solves of the apply
+ * (a2ls_options::precision), and of the factorisation of A~_ii and the local
+ * eigensolves (a2ls_options::eig_precision).  The SpMV, the GMRES
+ * orthogonalisation, the residual, the small Rayleigh-Ritz problems and the
+ * coarse operator are always FP64. */
 enum { A2LS_FP64 = 0, A2LS_FP32 = 1 };
 
 /* Preconditioner variants (Section 2).  DEFLATED_RAS is Eq. 2.4, the one the
@@ -96,10 +98,14 @@ typedef struct {
                                at most nev (Eq. 3.2) */
   int32_t eig_block_steps;  /* block Krylov steps per eigen restart cycle, default 3 */
   int32_t eig_max_cycles;   /* eigen restart cycles, default 60 */
-  double eig_tol;           /* relative eigen-residual target, default 1e-10 (FP64) / 1e-5 (FP32) when 0 */
+  double eig_tol;           /* relative eigen-residual target; 0 = default: 1e-10 when precision is FP64,
+                               1e-4 otherwise (a preconditioner's coarse space needs no more) */
   uint64_t seed;            /* seed of the eigensolver's random start blocks */
   void* stream;             /* cudaStream_t for all work; NULL = legacy default stream */
   int32_t timing;           /* 1: record CUDA events around the tracked kernels (A2LS_Q_KERNEL_TIMES) */
+  int32_t eig_precision;    /* precision of the factorisation of A~_ii and of the local eigensolves:
+                               -1 (default) = FP64 always; A2LS_FP64; A2LS_FP32 (only for local splittings
+                               whose conditioning FP32 can resolve; high-contrast problems need FP64) */
 } a2ls_options;
 
 /* Fills *opt with the defaults listed above.  Never fails. */

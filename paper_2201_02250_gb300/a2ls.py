@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
                 ("restart", ctypes.c_int32), ("max_it", ctypes.c_int32), ("flexible", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("eig_block_steps", ctypes.c_int32),
                 ("eig_max_cycles", ctypes.c_int32), ("eig_tol", ctypes.c_double),
-                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("timing", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("timing", ctypes.c_int32),
+                ("eig_precision", ctypes.c_int32)]
 
 
 _LIB = None
@@ -102,7 +103,7 @@ def default_options(**kw) -> Options:
             v = VARIANTS[v]
         if k == "pou" and isinstance(v, str):
             v = POU[v]
-        if k == "precision" and isinstance(v, str):
+        if k in ("precision", "eig_precision") and isinstance(v, str):
             v = {"fp64": FP64, "fp32": FP32}[v]
         setattr(o, k, v)
     return o

@@ -96,7 +96,8 @@ struct a2ls_handle {
 
   // coarse space
   int n0 = 0;
-  std::vector<int> h_m, h_coff;              // N, N+1
+  int coarse_band = 0;                       // bandwidth of A_00 in its block order
+  std::vector<int> h_m, h_coff;              // N, N+1 (coff in the banded block order)
   std::vector<int64_t> h_woff;               // N+1, offsets of W_i (n_i x m_i)
   int *d_m = nullptr, *d_coff = nullptr;
   int64_t* d_woff = nullptr;
@@ -151,7 +152,7 @@ void sync_and_check(a2ls_handle* h, const char* phase);
 // ---------------------------------------------------------------------------
 // k_graph.cu
 void build_subdomains(a2ls_handle* h);                 // validation, overlap, lists, memberships
-void extract_local(a2ls_handle* h, void* dense_A, double* dense_At, double* dense_scale);
+void extract_local(a2ls_handle* h, void* dense_A, void* dense_At, double* dense_scale);
 void exclusive_scan_i64(const int64_t* in, int64_t* out, int n, cudaStream_t st, a2ls_handle* h);
 
 // k_dense.cu
@@ -161,12 +162,12 @@ template <class T> void invert_diag_tiles(a2ls_handle* h, T* fac);
 // y_loc / z output of the RAS/ASM local solves; see k_dense.cu for the modes
 template <class T> void local_solves(a2ls_handle* h, const T* fac, const double* t, const double* q,
                                      double* z, int mode);
-void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv);
+void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv, int band);
 template <class T> void block_solve(a2ls_handle* h, const T* fac, T* X, const int64_t* xoff, int col0, int ldx,
                                     const int* pvec, const int* active, int forward, int backward);
 
 // k_eig.cu
-void eigensolve(a2ls_handle* h, double* fac_tilde, const double* last_pivot, const double* diag_scale);
+void eigensolve(a2ls_handle* h, void* fac_tilde, const double* last_pivot, const double* diag_scale);
 
 // k_coarse.cu
 void orthonormalize_and_set_W(a2ls_handle* h, double* Z, const int* mcols, int ldz_max);

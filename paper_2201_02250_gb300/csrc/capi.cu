@@ -177,13 +177,13 @@ static void destroy_handle(a2ls_handle* h) {
   delete h;
 }
 
-template <class T>
+template <class T, class TT>
 static void factor_and_coarse(a2ls_handle* h, bool need_coarse, double* times) {
   cudaStream_t st = h->st;
   Timer tm(st);
   const int N = h->N;
   T* fa = dalloc<T>(h, h->fac_elems);
-  double* ft = need_coarse ? dalloc<double>(h, h->fac_elems) : nullptr;  // eigensolve always FP64
+  TT* ft = need_coarse ? dalloc<TT>(h, h->fac_elems) : nullptr;  // A~_ii factors (eigensolve precision)
   double* dscale = dalloc<double>(h, N);
   double* lastp = dalloc<double>(h, N);
   extract_local(h, fa, ft, dscale);
@@ -200,8 +200,8 @@ static void factor_and_coarse(a2ls_handle* h, bool need_coarse, double* times) {
   h->d_fac = fa;
   if (need_coarse) {
     KTime kt(h, KT_LU_SPLIT, lu_flops);
-    lu_batched<double>(h, ft, 1, lastp, dscale);
-    invert_diag_tiles<double>(h, ft);
+    lu_batched<TT>(h, ft, 1, lastp, dscale);
+    invert_diag_tiles<TT>(h, ft);
     sync_and_check(h, "LU factorisation of the local splittings");
   }
   times[Phase::SETUP_LU] = tm.stop();
@@ -236,6 +236,7 @@ void a2ls_default_options(a2ls_options* o) {
   o->seed = 12345;
   o->stream = nullptr;
   o->timing = 0;
+  o->eig_precision = -1;
 }
 
 const char* a2ls_last_error(void) { return g_last_error.c_str(); }
@@ -294,8 +295,13 @@ int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int
     h->fac_elems = (size_t)h->h_foff[h->N];
     const int v = o.variant;
     const bool need_coarse = nev > 0 && v != A2LS_ONE_LEVEL_RAS && v != A2LS_ONE_LEVEL_ASM;
-    if (o.precision == A2LS_FP64) factor_and_coarse<double>(h, need_coarse, h->times);
-    else factor_and_coarse<float>(h, need_coarse, h->times);
+    const int ep = (o.eig_precision < 0) ? A2LS_FP64 : o.eig_precision;
+    if (ep != A2LS_FP64 && ep != A2LS_FP32) fail(A2LS_ERR_ARG, "unknown eig_precision %d", o.eig_precision);
+    h->opt.eig_precision = ep;
+    if (o.precision == A2LS_FP64 && ep == A2LS_FP64) factor_and_coarse<double, double>(h, need_coarse, h->times);
+    else if (o.precision == A2LS_FP64) factor_and_coarse<double, float>(h, need_coarse, h->times);
+    else if (ep == A2LS_FP64) factor_and_coarse<float, double>(h, need_coarse, h->times);
+    else factor_and_coarse<float, float>(h, need_coarse, h->times);
     // apply workspace
     h->d_q = dalloc<double>(h, h->n);
     h->d_t = dalloc<double>(h, h->n);

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 namespace a2ls {
 
@@ -221,6 +222,67 @@ __global__ void k_diag_absmax(const double* E, int n, double* out) {
     atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(v));
 }
 
+// Order the coarse blocks (subdomains) so that A_00 has a small bandwidth: the
+// natural order or reverse Cuthill-McKee on the subdomain coupling graph,
+// whichever gives the narrower band.  The LU without pivoting keeps its fill
+// inside the band, and the inverse is formed from the banded factors.
+static int band_of(const std::vector<int2>& pairs, const std::vector<int>& coff, const std::vector<int>& m) {
+  int w = 0;
+  for (const int2& p : pairs) {
+    if (m[p.x] == 0 || m[p.y] == 0) continue;
+    w = std::max(w, coff[p.x] + m[p.x] - 1 - coff[p.y]);
+    w = std::max(w, coff[p.y] + m[p.y] - 1 - coff[p.x]);
+  }
+  return w;
+}
+
+static std::vector<int> offsets_for(const std::vector<int>& order, const std::vector<int>& m) {
+  std::vector<int> coff(m.size() + 1, 0);
+  int acc = 0;
+  for (int i : order) {
+    coff[i] = acc;
+    acc += m[i];
+  }
+  coff[m.size()] = acc;
+  return coff;
+}
+
+void choose_coarse_order(a2ls_handle* h, const std::vector<int2>& pairs) {
+  const int N = h->N;
+  std::vector<std::vector<int>> adj(N);
+  for (const int2& p : pairs)
+    if (p.x != p.y) adj[p.x].push_back(p.y);
+  std::vector<int> natural(N);
+  for (int i = 0; i < N; ++i) natural[i] = i;
+  // reverse Cuthill-McKee from a minimum-degree node of every component
+  std::vector<int> order, seen(N, 0);
+  for (int start = 0; (int)order.size() < N;) {
+    int best = -1;
+    for (int i = 0; i < N; ++i)
+      if (!seen[i] && (best < 0 || adj[i].size() < adj[best].size())) best = i;
+    start = best;
+    std::vector<int> queue{start};
+    seen[start] = 1;
+    for (size_t q = 0; q < queue.size(); ++q) {
+      std::vector<int> nb;
+      for (int j : adj[queue[q]])
+        if (!seen[j]) {
+          seen[j] = 1;
+          nb.push_back(j);
+        }
+      std::sort(nb.begin(), nb.end(), [&](int a, int b) { return adj[a].size() < adj[b].size() || (adj[a].size() == adj[b].size() && a < b); });
+      queue.insert(queue.end(), nb.begin(), nb.end());
+    }
+    order.insert(order.end(), queue.begin(), queue.end());
+  }
+  std::reverse(order.begin(), order.end());
+  std::vector<int> c_nat = offsets_for(natural, h->h_m), c_rcm = offsets_for(order, h->h_m);
+  const int w_nat = band_of(pairs, c_nat, h->h_m), w_rcm = band_of(pairs, c_rcm, h->h_m);
+  h->h_coff = (w_rcm < w_nat) ? c_rcm : c_nat;
+  h->coarse_band = std::min(w_nat, w_rcm);
+  A2LS_CUDA(cudaMemcpyAsync(h->d_coff, h->h_coff.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, h->st));
+}
+
 void build_coarse_operator(a2ls_handle* h) {
   const int N = h->N, n0 = h->n0;
   cudaStream_t st = h->st;
@@ -243,6 +305,7 @@ void build_coarse_operator(a2ls_handle* h) {
     for (int j = 0; j < N; ++j)
       if (hb[(size_t)i * words + (j >> 5)] & (1u << (j & 31))) pairs.push_back(make_int2(i, j));
   dfree(h, bits);
+  choose_coarse_order(h, pairs);
   double* E = dalloc<double>(h, (size_t)n0 * n0);
   A2LS_CUDA(cudaMemsetAsync(E, 0, sizeof(double) * n0 * n0, st));
   if (!pairs.empty()) {
@@ -267,7 +330,7 @@ void build_coarse_operator(a2ls_handle* h) {
   dfree(h, dmax);
   if (!(scale > 0.0)) fail(A2LS_ERR_SINGULAR, "coarse operator has a zero diagonal");
   h->d_Einv = dalloc<double>(h, (size_t)n0 * n0);
-  dense_inverse(h, E, n0, scale, h->d_Einv);
+  dense_inverse(h, E, n0, scale, h->d_Einv, h->coarse_band);
   sync_and_check(h, "coarse operator");
   dfree(h, E);
   // apply workspace sized by n0

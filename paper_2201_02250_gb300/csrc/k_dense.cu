@@ -71,6 +71,52 @@ __device__ __forceinline__ void cta_gemm(const T* __restrict__ A, int64_t lda, c
 }
 
 // ---------------------------------------------------------------------------
+// Narrow tile product for p <= 32 right-hand sides: acc += A(0:M, 0:K) * B(0:K, 0:Nc),
+// M <= 64, Nc <= 32; 256 threads, thread (ty, tx) owns rows 2ty, 2ty+1 and columns 4tx..4tx+3.
+// amask as in cta_gemm.
+// ---------------------------------------------------------------------------
+template <class T, class Acc>
+__device__ __forceinline__ void cta_gemm_n32(const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
+                                             int64_t ldb, int M, int Nc, int K, int amask, Acc (&acc)[2][4],
+                                             Acc* sA, Acc* sB) {
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+  for (int k0 = 0; k0 < K; k0 += GK) {
+    for (int e = tid; e < 64 * GK; e += 256) {
+      const int m = e / GK, k = e % GK;
+      Acc v = 0;
+      const int kk = k0 + k;
+      if (m < M && kk < K) {
+        if (amask == 0) v = (Acc)A[m * lda + kk];
+        else if (amask == 1) v = (kk < m) ? (Acc)A[m * lda + kk] : (kk == m ? (Acc)1 : (Acc)0);
+        else v = (kk >= m) ? (Acc)A[m * lda + kk] : (Acc)0;
+      }
+      sA[k * 65 + m] = v;
+    }
+    for (int e = tid; e < GK * 32; e += 256) {
+      const int k = e / 32, c = e % 32;
+      const int kk = k0 + k;
+      sB[k * 33 + c] = (c < Nc && kk < K) ? (Acc)B[kk * ldb + c] : (Acc)0;
+    }
+    __syncthreads();
+    if (tx * 4 < Nc) {
+#pragma unroll 8
+      for (int k = 0; k < GK; ++k) {
+        const Acc a0 = sA[k * 65 + ty * 2], a1 = sA[k * 65 + ty * 2 + 1];
+        Acc b[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) b[v] = sB[k * 33 + tx * 4 + v];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          acc[0][v] += a0 * b[v];
+          acc[1][v] += a1 * b[v];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // batched LU without pivoting
 // ---------------------------------------------------------------------------
 constexpr int LU_NB = 32;
@@ -371,7 +417,7 @@ __global__ void __launch_bounds__(256) k_block_solve(const int* ni, const int* l
                                                      const int* pvec, const int* active, int forward,
                                                      int backward) {
   using Acc = typename AccOf<T>::type;
-  __shared__ Acc sA[GK * 65], sB[GK * 65];
+  __shared__ Acc sA[GK * 65], sB[GK * 33];
   const int i = blockIdx.x;
   if (active && !active[i]) return;
   const int p = pvec[i];
@@ -380,7 +426,7 @@ __global__ void __launch_bounds__(256) k_block_solve(const int* ni, const int* l
   const int64_t L = ld[i];
   const T* M = fac + foff[i];
   T* Xi = X + xoff[i] + col0;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
   const int nb = (n + TB - 1) / TB;
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 0 && !forward) continue;
@@ -388,37 +434,37 @@ __global__ void __launch_bounds__(256) k_block_solve(const int* ni, const int* l
     for (int bb = 0; bb < nb; ++bb) {
       const int b = pass == 0 ? bb : nb - 1 - bb;
       const int r0 = b * TB, tb = min(TB, n - r0);
-      for (int c0 = 0; c0 < p; c0 += 64) {
-        const int pc = min(64, p - c0);
-        Acc acc[4][4] = {};
+      for (int c0 = 0; c0 < p; c0 += 32) {
+        const int pc = min(32, p - c0);
+        Acc acc[2][4] = {};
         if (pass == 0) {
-          if (r0 > 0) cta_gemm<T, Acc>(M + (int64_t)r0 * L, L, Xi + c0, ldx, tb, pc, r0, 0, acc, sA, sB);
+          if (r0 > 0) cta_gemm_n32<T, Acc>(M + (int64_t)r0 * L, L, Xi + c0, ldx, tb, pc, r0, 0, acc, sA, sB);
         } else {
           const int e0 = r0 + tb;
           if (e0 < n)
-            cta_gemm<T, Acc>(M + (int64_t)r0 * L + e0, L, Xi + (int64_t)e0 * ldx + c0, ldx, tb, pc, n - e0, 0,
-                             acc, sA, sB);
+            cta_gemm_n32<T, Acc>(M + (int64_t)r0 * L + e0, L, Xi + (int64_t)e0 * ldx + c0, ldx, tb, pc, n - e0,
+                                 0, acc, sA, sB);
         }
         // S = X_b - acc, written in place
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 2; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
-            const int r = ty * 4 + u, c = tx * 4 + v;
+            const int r = ty * 2 + u, c = tx * 4 + v;
             if (r < tb && c < pc) {
               T* ptr = Xi + (int64_t)(r0 + r) * ldx + c0 + c;
               *ptr = (T)((Acc)*ptr - acc[u][v]);
             }
           }
         __syncthreads();
-        Acc acc2[4][4] = {};
-        cta_gemm<T, Acc>(M + (int64_t)r0 * L + r0, L, Xi + (int64_t)r0 * ldx + c0, ldx, tb, pc, tb,
-                         pass == 0 ? 1 : 2, acc2, sA, sB);
+        Acc acc2[2][4] = {};
+        cta_gemm_n32<T, Acc>(M + (int64_t)r0 * L + r0, L, Xi + (int64_t)r0 * ldx + c0, ldx, tb, pc, tb,
+                             pass == 0 ? 1 : 2, acc2, sA, sB);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 2; ++u)
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
-            const int r = ty * 4 + u, c = tx * 4 + v;
+            const int r = ty * 2 + u, c = tx * 4 + v;
             if (r < tb && c < pc) Xi[(int64_t)(r0 + r) * ldx + c0 + c] = (T)acc2[u][v];
           }
         __syncthreads();
@@ -486,7 +532,8 @@ __global__ void k_e_diag(double* A, int n, int64_t ld, int k0, double scale, int
   }
 }
 
-// L21 = A21 inv(U11) (blockIdx.y == 0) and U12 = inv(L11) A12 (blockIdx.y == 1), in place
+// L21 = A21 inv(U11) (blockIdx.y == 0) and U12 = inv(L11) A12 (blockIdx.y == 1), in place;
+// the grid covers the band only (entries farther than the bandwidth from the diagonal are zero)
 __global__ void __launch_bounds__(256) k_e_panels(double* A, int n, int64_t ld, int k0) {
   __shared__ double sA[GK * 65], sB[GK * 65];
   const int tb = min(TB, n - k0);
@@ -534,7 +581,8 @@ __global__ void __launch_bounds__(256) k_e_trailing(double* A, int n, int64_t ld
 }
 
 // X = inv(U) inv(L) I, one 64-column slab per CTA (F holds the block-inverted LU)
-__global__ void __launch_bounds__(256) k_e_inverse(const double* F, int n, int64_t ld, double* X, int64_t ldx) {
+__global__ void __launch_bounds__(256) k_e_inverse(const double* F, int n, int64_t ld, double* X, int64_t ldx,
+                                                   int band) {
   __shared__ double sA[GK * 65], sB[GK * 65];
   const int c0 = blockIdx.x * 64;
   const int pc = min(64, n - c0);
@@ -554,14 +602,15 @@ __global__ void __launch_bounds__(256) k_e_inverse(const double* F, int n, int64
       const int r0 = b * TB, tb = min(TB, n - r0);
       double acc[4][4] = {};
       if (pass == 0) {
-        const int k0 = bstart * TB;
+        const int k0 = max(bstart * TB, r0 - band);  // L(r, c) = 0 for c < r - band
         if (r0 > k0)
           cta_gemm<double, double>(F + (int64_t)r0 * ld + k0, ld, Xs + (int64_t)k0 * ldx, ldx, tb, pc, r0 - k0, 0,
                                    acc, sA, sB);
       } else {
         const int e0 = r0 + tb;
-        if (e0 < n)
-          cta_gemm<double, double>(F + (int64_t)r0 * ld + e0, ld, Xs + (int64_t)e0 * ldx, ldx, tb, pc, n - e0, 0,
+        const int e1 = min(n, r0 + tb + band);       // U(r, c) = 0 for c > r + band
+        if (e0 < e1)
+          cta_gemm<double, double>(F + (int64_t)r0 * ld + e0, ld, Xs + (int64_t)e0 * ldx, ldx, tb, pc, e1 - e0, 0,
                                    acc, sA, sB);
       }
 #pragma unroll
@@ -587,14 +636,15 @@ __global__ void __launch_bounds__(256) k_e_inverse(const double* F, int n, int64
   }
 }
 
-void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv) {
+void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv, int band) {
   cudaStream_t st = h->st;
   const int64_t ld = n;
+  if (band <= 0 || band >= n) band = n;
   KTime kt(h, KT_COARSE_LU, 2.0 / 3.0 * (double)n * n * n);
   for (int k0 = 0; k0 < n; k0 += TB) {
     k_e_diag<<<1, TB, 0, st>>>(E, n, ld, k0, scale, h->d_status);
     A2LS_LAUNCH();
-    const int rest = n - k0 - min(TB, n - k0);
+    const int rest = min(n - k0 - min(TB, n - k0), band + TB);
     if (rest <= 0) break;
     const int chunks = ceil_div(rest, 64);
     k_e_panels<<<dim3(chunks, 2), 256, 0, st>>>(E, n, ld, k0);
@@ -603,7 +653,7 @@ void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv)
     A2LS_LAUNCH();
   }
   KTime kt2(h, KT_COARSE_INV, 4.0 / 3.0 * (double)n * n * n);
-  k_e_inverse<<<ceil_div(n, 64), 256, 0, st>>>(E, n, ld, Einv, ld);
+  k_e_inverse<<<ceil_div(n, 64), 256, 0, st>>>(E, n, ld, Einv, ld, band);
   A2LS_LAUNCH();
 }
 

@@ -552,26 +552,28 @@ __global__ void k_extract(int S, int N, const int* off, const int* nI, const int
   }
 }
 
-void extract_local(a2ls_handle* h, void* dense_A, double* dense_At, double* dense_scale) {
+template <class TA, class TT>
+static void launch_extract(a2ls_handle* h, void* dense_A, void* dense_At, double* dense_scale, int blocks) {
+  k_extract<TA, TT><<<blocks, 256, 0, h->st>>>(
+      h->sum_n, h->N, h->d_off, h->d_nI, h->d_ni, h->d_ld, h->d_foff, h->d_idx, h->d_ipos, h->part, h->rowptr,
+      h->colind, h->val, h->d_lrow, h->d_lcol, h->d_lval, h->d_lump, static_cast<TA*>(dense_A),
+      static_cast<TT*>(dense_At), dense_scale);
+  A2LS_LAUNCH();
+}
+
+void extract_local(a2ls_handle* h, void* dense_A, void* dense_At, double* dense_scale) {
   cudaStream_t st = h->st;
   h->d_lump = dalloc<double>(h, h->sum_n);
   A2LS_CUDA(cudaMemsetAsync(dense_scale, 0, sizeof(double) * h->N, st));
-  const size_t es = (h->opt.precision == A2LS_FP64) ? 8 : 4;
-  A2LS_CUDA(cudaMemsetAsync(dense_A, 0, h->fac_elems * es, st));
-  if (dense_At) A2LS_CUDA(cudaMemsetAsync(dense_At, 0, h->fac_elems * sizeof(double), st));
+  const size_t ea = (h->opt.precision == A2LS_FP64) ? 8 : 4;
+  const size_t et = (h->opt.eig_precision == A2LS_FP32) ? 4 : 8;
+  A2LS_CUDA(cudaMemsetAsync(dense_A, 0, h->fac_elems * ea, st));
+  if (dense_At) A2LS_CUDA(cudaMemsetAsync(dense_At, 0, h->fac_elems * et, st));
   const int blocks = std::min(152 * 16, ceil_div((int64_t)h->sum_n * 32, 256));
-  if (h->opt.precision == A2LS_FP64) {
-    k_extract<double, double><<<blocks, 256, 0, st>>>(
-        h->sum_n, h->N, h->d_off, h->d_nI, h->d_ni, h->d_ld, h->d_foff, h->d_idx, h->d_ipos, h->part,
-        h->rowptr, h->colind, h->val, h->d_lrow, h->d_lcol, h->d_lval, h->d_lump,
-        static_cast<double*>(dense_A), dense_At, dense_scale);
-  } else {
-    k_extract<float, double><<<blocks, 256, 0, st>>>(
-        h->sum_n, h->N, h->d_off, h->d_nI, h->d_ni, h->d_ld, h->d_foff, h->d_idx, h->d_ipos, h->part,
-        h->rowptr, h->colind, h->val, h->d_lrow, h->d_lcol, h->d_lval, h->d_lump,
-        static_cast<float*>(dense_A), dense_At, dense_scale);
-  }
-  A2LS_LAUNCH();
+  if (ea == 8 && et == 8) launch_extract<double, double>(h, dense_A, dense_At, dense_scale, blocks);
+  else if (ea == 8) launch_extract<double, float>(h, dense_A, dense_At, dense_scale, blocks);
+  else if (et == 8) launch_extract<float, double>(h, dense_A, dense_At, dense_scale, blocks);
+  else launch_extract<float, float>(h, dense_A, dense_At, dense_scale, blocks);
 }
 
 }  // namespace a2ls

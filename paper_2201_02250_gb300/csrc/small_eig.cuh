@@ -380,21 +380,23 @@ SE_HD inline void schur_vector(const double* S, int ld, int m, int p, double lr,
 }
 
 // Order of eigenvalues by decreasing modulus; within a pair the +imag member first.
-// perm: m ints.  Selection sort (m is small).
-SE_HD inline void order_by_modulus(const double* wr, const double* wi, int m, int* perm) {
-  for (int j = 0; j < m; ++j) perm[j] = j;
+// perm: m ints; mod: m doubles of scratch.  Selection sort (m is small).
+SE_HD inline void order_by_modulus(const double* wr, const double* wi, int m, int* perm, double* mod) {
+  for (int j = 0; j < m; ++j) {
+    perm[j] = j;
+    mod[j] = hypot(wr[j], wi[j]);
+  }
   for (int a = 0; a < m; ++a) {
     int best = a;
-    double bm = hypot(wr[perm[a]], wi[perm[a]]);
+    double bm = mod[perm[a]];
     for (int b = a + 1; b < m; ++b) {
-      double mb = hypot(wr[perm[b]], wi[perm[b]]);
-      if (mb > bm * (1 + 1e-14) ||
-          (fabs(mb - bm) <= 1e-14 * bm && wi[perm[b]] > wi[perm[best]])) {
+      const double mb = mod[perm[b]];
+      if (mb > bm * (1 + 1e-14) || (fabs(mb - bm) <= 1e-14 * bm && wi[perm[b]] > wi[perm[best]])) {
         best = b;
         bm = mb;
       }
     }
-    int tmp = perm[a];
+    const int tmp = perm[a];
     perm[a] = perm[best];
     perm[best] = tmp;
   }

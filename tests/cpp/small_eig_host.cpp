@@ -13,7 +13,7 @@ int main() {
   int m;
   if (std::scanf("%d", &m) != 1) return 1;
   const int ld = m + 1;
-  std::vector<double> H(m * ld), Q(m * ld, 0.0), v(m), wr(m), wi(m), x(m), y(m);
+  std::vector<double> H(m * ld), Q(m * ld, 0.0), v(m), wr(m), wi(m), x(m), y(m), mod(m);
   std::vector<int> perm(m);
   for (int r = 0; r < m; ++r)
     for (int c = 0; c < m; ++c)
@@ -26,7 +26,7 @@ int main() {
   hessenberg(H.data(), ld, Q.data(), ld, m, v.data(), t);
   const int rc = schur(H.data(), ld, Q.data(), ld, m, hn, t);
   schur_eigenvalues(H.data(), ld, m, wr.data(), wi.data());
-  order_by_modulus(wr.data(), wi.data(), m, perm.data());
+  order_by_modulus(wr.data(), wi.data(), m, perm.data(), mod.data());
   std::printf("%d\n", rc);
   for (int j = 0; j < m; ++j) std::printf("%.17g %.17g\n", wr[perm[j]], wi[perm[j]]);
   double snorm = 0.0;

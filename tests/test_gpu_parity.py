@@ -376,7 +376,8 @@ def test_c2_full_size(c2, precision):
     prob = c2
     P = setup_gpu(prob, precision=precision)
     sz = P.sizes()
-    assert sz["N"] == 256 and sz["n0"] == 256 * 16
+    # 16 per subdomain, one more where the cut keeps both members of a conjugate pair
+    assert sz["N"] == 256 and 256 * 16 <= sz["n0"] <= 256 * 17
     x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
     it, rr, ok = P.solve(dev(prob.b), x, 1e-8)
     xh = x.cpu().numpy()
