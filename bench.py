@@ -50,7 +50,22 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--plain-steps", type=int, default=1, help="timed steps of the plain FP64 form")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", choices=["c2", "c2_quarter"], default="c2",
+                   help="c2 = the headline 512x512 problem; c2_quarter = the same problem on a 256x256 grid "
+                        "with 64 subdomains (a small case for ncu captures)")
+    p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 form")
+    p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg with host buffers")
     return p.parse_args()
+
+
+def make_problem(name: str):
+    from workloads import pde
+    if name == "c2":
+        return pde.config_c2()
+    m = 256
+    A, _ = pde.high_contrast_fv_2d(m, seed=2)
+    return pde.Problem("c2_quarter_256", A, pde.block_partition_2d(m, 8), 2, 16, pde.rhs_uniform(m * m, 2),
+                       {"grid": m, "blocks": 8, "seed": 2})
 
 
 def measured_peaks() -> dict:
@@ -205,7 +220,7 @@ def run_ours(args, rank: int, world: int, device):
     from paper_2201_02250_gb300 import a2ls
     from workloads import pde
 
-    prob = pde.config_c2()
+    prob = make_problem(args.workload)
     stream = torch.cuda.current_stream(device)
     rowptr = torch.as_tensor(prob.A.indptr.astype(np.int32), device=device)
     colind = torch.as_tensor(prob.A.indices.astype(np.int32), device=device)
@@ -292,12 +307,15 @@ def run_ours(args, rank: int, world: int, device):
     P.close()
 
     # --- the plain FP64 form ------------------------------------------------------------------------
-    plain = timed("fp64", max(args.plain_steps, 1), 1, timing=1)
-    info64, P64, _ = one_step("fp64", 1, keep=True)
-    apply_ms_plain = time_apply(P64)
-    ab_plain = apply_bytes(P64, prob, 8)
-    P64.close()
-    plain_ms = statistics.mean([i["ms"] for i in plain])
+    if args.no_plain:
+        plain, info64, apply_ms_plain, ab_plain, plain_ms = None, None, None, None, None
+    else:
+        plain = timed("fp64", max(args.plain_steps, 1), 1, timing=1)
+        info64, P64, _ = one_step("fp64", 1, keep=True)
+        apply_ms_plain = time_apply(P64)
+        ab_plain = apply_bytes(P64, prob, 8)
+        P64.close()
+        plain_ms = statistics.mean([i["ms"] for i in plain])
 
     # --- end to end through the C ABI with host buffers ----------------------------------------------
     host = {k: v.cpu().pin_memory() for k, v in (("rowptr", rowptr), ("colind", colind), ("val", val),
@@ -305,7 +323,7 @@ def run_ours(args, rank: int, world: int, device):
     h2d = sum(int(v.numel() * v.element_size()) for v in host.values())
     xh_pinned = torch.empty(prob.n, dtype=torch.float64).pin_memory()
     e2e_ms = []
-    for k in range(args.steps + 1):
+    for k in range(0 if args.no_e2e else args.steps + 1):
         flush.fill_(1.0)
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
@@ -406,19 +424,19 @@ def report(args, res, world) -> dict:
         "vs_baseline": None,
         "dtype": "f32 local factors/solves, f64 GMRES/SpMV/eigensolves/coarse",
         "data": "synthetic (seeded generator, workloads.pde.config_c2)",
-        "config": {"workload": WORKLOAD, "n": prob.n, "nnz": int(prob.A.nnz), "subdomains": int(prob.nparts),
+        "config": {"workload": WORKLOAD if args.workload == "c2" else prob.name, "n": prob.n, "nnz": int(prob.A.nnz), "subdomains": int(prob.nparts),
                    "overlap": prob.overlap, "nev": prob.nev, "rtol": 1e-8, "restart": 30,
                    "form": "mixed: FP32 local LU of A_ii and FP32 local solves, FGMRES(30) in FP64, FP64 local eigensolves to 1e-4",
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
         "iters": mixed[-1]["iters"],
         "true_relres": res["true_relres"],
         "phases_ms": {k: round(v, 2) for k, v in mixed[-1]["times"].items()},
-        "plain_fp64": {"ms_per_step": res["plain_ms"], "iters": plain[-1]["iters"],
-                       "apply_ms": res["apply_ms_plain"],
-                       "apply_gbs": res["ab_plain"]["apply"] / (res["apply_ms_plain"] * 1e-3) / 1e9,
-                       "phases_ms": {k: round(v, 2) for k, v in plain[-1]["times"].items()},
-                       "kernels_ms_per_step": {k: round(v[1], 3) for k, v in plain[-1]["kernels"].items()}},
-        "speedup_vs_plain_fp64": res["plain_ms"] / res["step_ms"],
+        "plain_fp64": None if plain is None else {
+            "ms_per_step": res["plain_ms"], "iters": plain[-1]["iters"], "apply_ms": res["apply_ms_plain"],
+            "apply_gbs": res["ab_plain"]["apply"] / (res["apply_ms_plain"] * 1e-3) / 1e9,
+            "phases_ms": {k: round(v, 2) for k, v in plain[-1]["times"].items()},
+            "kernels_ms_per_step": {k: round(v[1], 3) for k, v in plain[-1]["kernels"].items()}},
+        "speedup_vs_plain_fp64": None if plain is None else res["plain_ms"] / res["step_ms"],
         "apply": {"ms": res["apply_ms_mixed"], "bytes": res["ab_mixed"]["apply"],
                   "gbs": res["ab_mixed"]["apply"] / (res["apply_ms_mixed"] * 1e-3) / 1e9,
                   "local_solve_kernel_ms": res["loc_ms"], "local_solve_kernel_gbs": apply_local_gbs,
@@ -426,8 +444,9 @@ def report(args, res, world) -> dict:
         "roofline": roof,
         "kernels_ms_per_step": {k: round(v[1], 3) for k, v in kern.items()},
         "roofline_kernels": {k: roofline_entry(k, v[0], v[1], v[2], res["hbm_peak"]) for k, v in kern.items() if v[0]},
-        "e2e": {"value": statistics.mean(res["e2e_ms"]) / 1e3, "unit": "s", "h2d_bytes_per_step": res["h2d"],
-                "d2h_bytes_per_step": res["d2h"]},
+        "e2e": None if not res["e2e_ms"] else {
+            "value": statistics.mean(res["e2e_ms"]) / 1e3, "unit": "s", "h2d_bytes_per_step": res["h2d"],
+            "d2h_bytes_per_step": res["d2h"]},
         "gpu_launches": int(mixed[-1]["launches"]),
         "clocks": res["clocks"],
     }
