@@ -164,7 +164,7 @@ template <class T> void local_solves(a2ls_handle* h, const T* fac, const double*
                                      double* z, int mode);
 void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv, int band);
 template <class T> void block_solve(a2ls_handle* h, const T* fac, T* X, const int64_t* xoff, int col0, int ldx,
-                                    const int* pvec, const int* active, int forward, int backward);
+                                    const int* pvec, int pmax, const int* active, int forward, int backward);
 
 // k_eig.cu
 void eigensolve(a2ls_handle* h, void* fac_tilde, const double* last_pivot, const double* diag_scale);

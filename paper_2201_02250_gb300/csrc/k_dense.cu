@@ -117,6 +117,46 @@ __device__ __forceinline__ void cta_gemm_n32(const T* __restrict__ A, int64_t ld
 }
 
 // ---------------------------------------------------------------------------
+// Narrowest tile product for the column chunks of the eigen solves: M <= 64 rows, Nc <= 8
+// columns; 256 threads, thread (ty, tx) owns row ty and columns 2tx, 2tx+1.
+// ---------------------------------------------------------------------------
+template <class T, class Acc>
+__device__ __forceinline__ void cta_gemm_n8(const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
+                                            int64_t ldb, int M, int Nc, int K, int amask, Acc (&acc)[2], Acc* sA,
+                                            Acc* sB) {
+  const int tid = threadIdx.x, tx = tid & 3, ty = tid >> 2;
+  for (int k0 = 0; k0 < K; k0 += GK) {
+    for (int e = tid; e < 64 * GK; e += 256) {
+      const int m = e / GK, k = e % GK;
+      Acc v = 0;
+      const int kk = k0 + k;
+      if (m < M && kk < K) {
+        if (amask == 0) v = (Acc)A[m * lda + kk];
+        else if (amask == 1) v = (kk < m) ? (Acc)A[m * lda + kk] : (kk == m ? (Acc)1 : (Acc)0);
+        else v = (kk >= m) ? (Acc)A[m * lda + kk] : (Acc)0;
+      }
+      sA[k * 65 + m] = v;
+    }
+    {
+      const int e = tid;  // GK * 8 == 256
+      const int k = e / 8, c = e % 8;
+      const int kk = k0 + k;
+      sB[k * 9 + c] = (c < Nc && kk < K) ? (Acc)B[kk * ldb + c] : (Acc)0;
+    }
+    __syncthreads();
+    if (tx * 2 < Nc) {
+#pragma unroll 8
+      for (int k = 0; k < GK; ++k) {
+        const Acc a = sA[k * 65 + ty];
+        acc[0] += a * sB[k * 9 + tx * 2];
+        acc[1] += a * sB[k * 9 + tx * 2 + 1];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // batched LU without pivoting
 // ---------------------------------------------------------------------------
 constexpr int LU_NB = 32;
@@ -410,6 +450,8 @@ void local_solves(a2ls_handle* h, const T* fac, const double* t, const double* q
 // multi right-hand-side solves for the eigensolver: X (n_i x p, row-major, leading
 // dimension ldx, subdomain i at X + i*xstride) <- inv(U) inv(L) X (either half optional)
 // ---------------------------------------------------------------------------
+// One CTA per (subdomain, chunk of 8 right-hand sides): blockIdx.y selects the chunk, so that the
+// FP64-bound solves of the eigen iteration spread over all SMs.
 template <class T>
 __global__ void __launch_bounds__(256) k_block_solve(const int* ni, const int* ld, const int64_t* foff,
                                                      const T* __restrict__ fac, T* X,
@@ -417,16 +459,18 @@ __global__ void __launch_bounds__(256) k_block_solve(const int* ni, const int* l
                                                      const int* pvec, const int* active, int forward,
                                                      int backward) {
   using Acc = typename AccOf<T>::type;
-  __shared__ Acc sA[GK * 65], sB[GK * 33];
+  __shared__ Acc sA[GK * 65], sB[GK * 9];
   const int i = blockIdx.x;
   if (active && !active[i]) return;
   const int p = pvec[i];
-  if (p <= 0) return;
+  const int c0 = blockIdx.y * 8;
+  if (c0 >= p) return;
+  const int pc = min(8, p - c0);
   const int n = ni[i];
   const int64_t L = ld[i];
   const T* M = fac + foff[i];
-  T* Xi = X + xoff[i] + col0;
-  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+  T* Xi = X + xoff[i] + col0 + c0;
+  const int tid = threadIdx.x, tx = tid & 3, ty = tid >> 2;
   const int nb = (n + TB - 1) / TB;
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 0 && !forward) continue;
@@ -434,50 +478,44 @@ __global__ void __launch_bounds__(256) k_block_solve(const int* ni, const int* l
     for (int bb = 0; bb < nb; ++bb) {
       const int b = pass == 0 ? bb : nb - 1 - bb;
       const int r0 = b * TB, tb = min(TB, n - r0);
-      for (int c0 = 0; c0 < p; c0 += 32) {
-        const int pc = min(32, p - c0);
-        Acc acc[2][4] = {};
-        if (pass == 0) {
-          if (r0 > 0) cta_gemm_n32<T, Acc>(M + (int64_t)r0 * L, L, Xi + c0, ldx, tb, pc, r0, 0, acc, sA, sB);
-        } else {
-          const int e0 = r0 + tb;
-          if (e0 < n)
-            cta_gemm_n32<T, Acc>(M + (int64_t)r0 * L + e0, L, Xi + (int64_t)e0 * ldx + c0, ldx, tb, pc, n - e0,
-                                 0, acc, sA, sB);
-        }
-        // S = X_b - acc, written in place
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int r = ty * 2 + u, c = tx * 4 + v;
-            if (r < tb && c < pc) {
-              T* ptr = Xi + (int64_t)(r0 + r) * ldx + c0 + c;
-              *ptr = (T)((Acc)*ptr - acc[u][v]);
-            }
-          }
-        __syncthreads();
-        Acc acc2[2][4] = {};
-        cta_gemm_n32<T, Acc>(M + (int64_t)r0 * L + r0, L, Xi + (int64_t)r0 * ldx + c0, ldx, tb, pc, tb,
-                             pass == 0 ? 1 : 2, acc2, sA, sB);
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int r = ty * 2 + u, c = tx * 4 + v;
-            if (r < tb && c < pc) Xi[(int64_t)(r0 + r) * ldx + c0 + c] = (T)acc2[u][v];
-          }
-        __syncthreads();
+      Acc acc[2] = {};
+      if (pass == 0) {
+        if (r0 > 0) cta_gemm_n8<T, Acc>(M + (int64_t)r0 * L, L, Xi, ldx, tb, pc, r0, 0, acc, sA, sB);
+      } else {
+        const int e0 = r0 + tb;
+        if (e0 < n)
+          cta_gemm_n8<T, Acc>(M + (int64_t)r0 * L + e0, L, Xi + (int64_t)e0 * ldx, ldx, tb, pc, n - e0, 0, acc, sA,
+                              sB);
       }
+      // S = X_b - acc, written in place
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        const int c = tx * 2 + v;
+        if (ty < tb && c < pc) {
+          T* ptr = Xi + (int64_t)(r0 + ty) * ldx + c;
+          *ptr = (T)((Acc)*ptr - acc[v]);
+        }
+      }
+      __syncthreads();
+      Acc acc2[2] = {};
+      cta_gemm_n8<T, Acc>(M + (int64_t)r0 * L + r0, L, Xi + (int64_t)r0 * ldx, ldx, tb, pc, tb, pass == 0 ? 1 : 2,
+                          acc2, sA, sB);
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        const int c = tx * 2 + v;
+        if (ty < tb && c < pc) Xi[(int64_t)(r0 + ty) * ldx + c] = (T)acc2[v];
+      }
+      __syncthreads();
     }
   }
 }
 
 template <class T>
 void block_solve(a2ls_handle* h, const T* fac, T* X, const int64_t* xoff, int col0, int ldx, const int* pvec,
-                 const int* active, int forward, int backward) {
-  k_block_solve<T><<<h->N, 256, 0, h->st>>>(h->d_ni, h->d_ld, h->d_foff, fac, X, xoff, col0, ldx, pvec,
-                                           active, forward, backward);
+                 int pmax, const int* active, int forward, int backward) {
+  dim3 grid(h->N, (std::max(pmax, 1) + 7) / 8);
+  k_block_solve<T><<<grid, 256, 0, h->st>>>(h->d_ni, h->d_ld, h->d_foff, fac, X, xoff, col0, ldx, pvec, active,
+                                           forward, backward);
   A2LS_LAUNCH();
 }
 
@@ -487,9 +525,9 @@ template void invert_diag_tiles<float>(a2ls_handle*, float*);
 template void invert_diag_tiles<double>(a2ls_handle*, double*);
 template void local_solves<float>(a2ls_handle*, const float*, const double*, const double*, double*, int);
 template void local_solves<double>(a2ls_handle*, const double*, const double*, const double*, double*, int);
-template void block_solve<float>(a2ls_handle*, const float*, float*, const int64_t*, int, int, const int*,
+template void block_solve<float>(a2ls_handle*, const float*, float*, const int64_t*, int, int, const int*, int,
                                   const int*, int, int);
-template void block_solve<double>(a2ls_handle*, const double*, double*, const int64_t*, int, int, const int*,
+template void block_solve<double>(a2ls_handle*, const double*, double*, const int64_t*, int, int, const int*, int,
                                    const int*, int, int);
 
 }  // namespace a2ls

@@ -512,12 +512,12 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
   double* vtmp = wi + m;             // m
   int* perm = reinterpret_cast<int*>(vtmp + m);  // m
   const double* Hi = H + (int64_t)i * EIG_MAXP * EIG_MAXP;
-  const se::Team team{(int)threadIdx.x, 32};
-  for (int e = threadIdx.x; e < m * m; e += 32) {
+  const se::Team team{(int)threadIdx.x, (int)blockDim.x};
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     S[(e / m) * ld + e % m] = Hi[(e / m) * EIG_MAXP + e % m];
     Q[(e / m) * ld + e % m] = (e / m == e % m) ? 1.0 : 0.0;
   }
-  __syncwarp();
+  __syncthreads();
   double snorm = 0.0;
   bool finite = true;
   for (int e = 0; e < m * m; ++e) {
@@ -537,12 +537,12 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
   se::hessenberg(S, ld, Q, ld, m, vtmp, team);
   const int rc = se::schur(S, ld, Q, ld, m, snorm, team);
   if (rc != 0 && threadIdx.x == 0) raise_status(st, A2LS_ERR_EIGEN, i, 2);
-  __syncwarp();
+  __syncthreads();
   if (threadIdx.x == 0) {
     se::schur_eigenvalues(S, ld, m, wr, wi);
     se::order_by_modulus(wr, wi, m, perm, vtmp);
   }
-  __syncwarp();
+  __syncthreads();
   // plan the columns: walk eigenvalues by modulus, pairs take two columns
   // lane j handles the j-th selected eigenvalue
   __shared__ int sel_pos[32], sel_col[32], sel_two[32], nsel_s, ncol_s, zc_s;
@@ -566,7 +566,7 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
     ncol_s = col;
     zc_s = zc;
   }
-  __syncwarp();
+  __syncthreads();
   const int nsel = nsel_s;
   double* Yi = Y + (int64_t)i * EIG_MAXP * EIG_MAXP;
   int conv_all = 1;
@@ -622,7 +622,7 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
       eo[2 * j + 1] = wi[pidx] > 0 ? wi[pidx] : 0.0;
     }
   }
-  conv_all = __all_sync(0xffffffffu, conv_all);
+  conv_all = __syncthreads_and(conv_all);
   if (threadIdx.x == 0) {
     conv[i] = conv_all;
     ycols[i] = ncol_s;
@@ -705,7 +705,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   int* d_kpart = dalloc<int>(h, N);
   k_unit_last<T><<<N, 32, 0, st>>>(h->d_ni, d_off1, dscale, X1);
   A2LS_LAUNCH();
-  block_solve<T>(h, fac, X1, d_off1, 0, 1, d_ones, nullptr, 0, 1);  // k' = sigma inv(U') e_n
+  block_solve<T>(h, fac, X1, d_off1, 0, 1, d_ones, 1, nullptr, 0, 1);  // k' = sigma inv(U') e_n
   const double eps_work = fp64 ? 2.220446049250313e-16 : 1.1920928955078125e-07;
   k_kernel_test<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, h->d_ld, h->d_foff, fac, last_pivot, dscale,
                                                h->d_lrow, h->d_lcol, h->d_lval, h->d_lump, h->d_D, d_off1, X1,
@@ -714,7 +714,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   A2LS_CUDA(cudaMemsetAsync(X1, 0, sizeof(T) * hoff1[N], st));
   k_load_vec<T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_off1, 1, kvec, d_kd, X1);
   A2LS_LAUNCH();
-  block_solve<T>(h, fac, X1, d_off1, 0, 1, d_ones, d_kd, 1, 0);
+  block_solve<T>(h, fac, X1, d_off1, 0, 1, d_ones, 1, d_kd, 1, 0);
   k_store_h<T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_off1, 1, X1, d_kd, hvec, h->d_status);
   A2LS_LAUNCH();
   std::vector<int> kd(N), kpart(N);
@@ -743,6 +743,8 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     mfull[i] = full[i] ? std::min(mdim, EIG_MAXP) : 0;
     pv[i] = full[i] ? mfull[i] : b;
   }
+  int pmax = 1;
+  for (int i = 0; i < N; ++i) pmax = std::max(pmax, pv[i]);
   std::vector<int64_t> hvo(N + 1, 0);
   for (int i = 0; i < N; ++i) hvo[i + 1] = hvo[i] + (int64_t)h->h_n[i] * P;
   int64_t* d_vo = dalloc<int64_t>(h, N + 1);
@@ -806,13 +808,13 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     A2LS_LAUNCH();
     {
       KTime kt(h, KT_EIG_SOLVE, tri_flops);
-      block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, actv, 1, 0);
+      block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, pmax, actv, 1, 0);
     }
     k_mu_fix<T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, d_pv, actv, d_kd, hvec, W);
     A2LS_LAUNCH();
     {
       KTime kt(h, KT_EIG_SOLVE, tri_flops);
-      block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, actv, 0, 1);
+      block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, pmax, actv, 0, 1);
     }
     k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, actv, d_kd, kvec, W);
     A2LS_LAUNCH();
@@ -863,7 +865,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     }
     {
       KTime kt(h, KT_EIG_RR);
-      k_rayleigh_ritz<<<N, 32, rr_smem, st>>>(prm, d_full, d_mfull, d_nf, d_active, H, Y, d_ycols, d_zcols,
+      k_rayleigh_ritz<<<N, 128, rr_smem, st>>>(prm, d_full, d_mfull, d_nf, d_active, H, Y, d_ycols, d_zcols,
                                               eigout, d_conv, h->d_status);
       A2LS_LAUNCH();
     }

@@ -4,8 +4,9 @@
 // Schur form (Golub & Van Loan, Matrix Computations, Sections 7.4-7.5),
 // eigenvectors by back-substitution on the quasi-triangular factor.
 //
-// The routines run on a "team": on the GPU one warp (lane = lane id, size 32,
-// sync = __syncwarp), on the host a single thread (lane 0, size 1, no sync).
+// The routines run on a "team": on the GPU the threads of one CTA (lane = thread
+// id, size = block size, sync = __syncthreads), on the host a single thread
+// (lane 0, size 1, no sync).
 // The matrix is row-major with leading dimension ld and lives in memory the
 // whole team can address (shared memory on the GPU).
 #pragma once
@@ -25,7 +26,7 @@ struct Team {
   int lane, size;
   SE_HD void sync() const {
 #ifdef __CUDA_ARCH__
-    __syncwarp();
+    __syncthreads();
 #endif
   }
 };
