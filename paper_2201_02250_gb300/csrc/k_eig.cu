@@ -232,14 +232,14 @@ __global__ void __launch_bounds__(EIG_THREADS) k_project_k(const int* ni, const 
 }
 
 // W[:, 0:p] = B V[:, c0:c0+p], B = D A_ii D via the local CSR; one warp per row
-template <class T>
+template <class TV, class T>
 __global__ void k_bmul(const int* ni, const int* off, const int64_t* xoff, int ldx, int vcol0, const int* pvec,
                        const int* active, const int64_t* lrow, const int* lcol, const double* lval,
-                       const double* D, const T* V, T* W) {
+                       const double* D, const TV* V, T* W) {
   const int i = blockIdx.x;
   if (active && !active[i]) return;
   const int n = ni[i], p = pvec[i], o = off[i];
-  const T* Vi = V + xoff[i] + vcol0;
+  const TV* Vi = V + xoff[i] + vcol0;
   T* Wi = W + xoff[i];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int l = wid; l < n; l += nw) {
@@ -285,17 +285,20 @@ __global__ void k_mu_fix(const int* ni, const int* off, const int64_t* xoff, int
 // Writes the Gram coefficients into H[0:jb, hc:hc+p] and R into H[hr:hr+p, hc:hc+p]
 // and the orthonormal block into V[:, vout:vout+p].  full != 0: only H[0:jb, hc:hc+p].
 // ---------------------------------------------------------------------------
-__device__ void small_cholesky_inverse(double* G, int p, double* Ri, int& rank_ok) {
-  // G (p x p, stride p) = R^T R; R overwrites the upper triangle of G; Ri = inv(R) (stride p); one thread
+__device__ void small_cholesky_inverse(double* G, int p, double* Ri, int& rank_ok, double abs_floor) {
+  // G (p x p, stride p) = R^T R; R overwrites the upper triangle of G; Ri = inv(R) (stride p); one thread.
+  // A pivot at or below 1e-28 of the largest diagonal (or abs_floor) marks a rank-deficient block; it is
+  // floored so that inv(R) stays finite in the working precision and a zero column stays zero.
   rank_ok = 1;
   double gmax = 0.0;
   for (int a = 0; a < p; ++a) gmax = fmax(gmax, G[a * p + a]);
+  const double floor_d = fmax(1e-28 * gmax, abs_floor);
   for (int a = 0; a < p; ++a) {
     double d = G[a * p + a];
     for (int q = 0; q < a; ++q) d -= G[q * p + a] * G[q * p + a];
-    if (!(d > 1e-28 * gmax)) {
+    if (!(d > floor_d)) {
       rank_ok = 0;
-      d = 1e-28 * gmax + 1e-300;
+      d = floor_d;
     }
     const double r = sqrt(d);
     G[a * p + a] = r;
@@ -316,10 +319,10 @@ __device__ void small_cholesky_inverse(double* G, int p, double* Ri, int& rank_o
   }
 }
 
-template <class T>
+template <class T, class TW>
 __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64_t* xoff, int ldx,
                                                        const int* pvec, const int* active, int jb_blocks,
-                                                       int bcols, T* V, T* W, double* H, int hr, int hc,
+                                                       int bcols, T* V, TW* W, double* H, int hr, int hc,
                                                        int vout, const int* fullv, int* rank_flag) {
   using Acc = typename EAcc<T>::type;
   extern __shared__ double sm[];
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
   const int n = ni[i], p = pvec[i];
   const int jb = full ? p : jb_blocks * bcols;  // basis columns to orthogonalise against
   T* Vi = V + xoff[i];
-  T* Wi = W + xoff[i];
+  TW* Wi = W + xoff[i];
   double* Hi = H + (int64_t)i * EIG_MAXP * EIG_MAXP;
   // shared layout
   double* G = sm;                               // EIG_MAXP * EIG_MAXP (Gram, then R in place)
@@ -387,8 +390,8 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
         const int r = e / p, c = e % p;
         Acc s = 0;
         for (int a = 0; a < jb; ++a) s += sv[r * EIG_MAXP + a] * (Acc)G[a * p + c];
-        T* w = Wi + (int64_t)(l0 + r) * ldx + c;
-        *w = (T)((Acc)*w - s);
+        TW* w = Wi + (int64_t)(l0 + r) * ldx + c;
+        *w = (TW)((Acc)*w - s);
       }
       __syncthreads();
     }
@@ -428,12 +431,12 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
       if (pass == 0) {
         double tr = 0.0;
         for (int a = 0; a < p; ++a) tr += G[a * p + a];
-        const double u = sizeof(T) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+        const double u = sizeof(Acc) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
         const double shift = 11.0 * ((double)n * p + (double)p * (p + 1)) * u * tr;
         for (int a = 0; a < p; ++a) G[a * p + a] += shift;
       }
       int ok;
-      small_cholesky_inverse(G, p, Ri, ok);
+      small_cholesky_inverse(G, p, Ri, ok, sizeof(Acc) == 4 ? 1e-30 : 1e-300);
       rank_ok = ok;
       if (!ok && rank_flag) atomicAdd(rank_flag + i, 1);
       if (pass == 0) {
@@ -462,7 +465,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
         const int r = e / p, c = e % p;
         Acc s = 0;
         for (int a = 0; a <= c; ++a) s += sw[r * EIG_MAXP + a] * (Acc)Ri[a * p + c];
-        Wi[(int64_t)(l0 + r) * ldx + c] = (T)s;
+        Wi[(int64_t)(l0 + r) * ldx + c] = (TW)s;
       }
       __syncthreads();
     }
@@ -471,7 +474,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
   if (vout >= 0)
     for (int e = tid; e < n * p; e += EIG_THREADS) {
       const int l = e / p, c = e % p;
-      Vi[(int64_t)l * ldx + vout + c] = Wi[(int64_t)l * ldx + c];
+      Vi[(int64_t)l * ldx + vout + c] = (T)Wi[(int64_t)l * ldx + c];
     }
 }
 
@@ -631,10 +634,10 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
 }
 
 // X[:, 0:q] = V[:, 0:m] Y[0:m, 0:q] (q = qvec[i]); rows staged through shared memory
-template <class T>
+template <class T, class TX>
 __global__ void __launch_bounds__(EIG_THREADS) k_vy(const int* ni, const int64_t* xoff, int ldx, const int* mvec,
                                                      const int* qvec, const int* active, const T* V,
-                                                     const double* Y, T* X) {
+                                                     const double* Y, TX* X) {
   using Acc = typename EAcc<T>::type;
   extern __shared__ double sm[];
   const int i = blockIdx.x;
@@ -645,7 +648,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_vy(const int* ni, const int64_t
   const double* Yi = Y + (int64_t)i * EIG_MAXP * EIG_MAXP;
   for (int e = threadIdx.x; e < m * q; e += EIG_THREADS) sy[(e / q) * EIG_MAXP + e % q] = (Acc)Yi[(e / q) * EIG_MAXP + e % q];
   const T* Vi = V + xoff[i];
-  T* Xi = X + xoff[i];
+  TX* Xi = X + xoff[i];
   for (int l0 = 0; l0 < n; l0 += RC) {
     const int rows = min(RC, n - l0);
     __syncthreads();
@@ -656,7 +659,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_vy(const int* ni, const int64_t
       const int r = e / q, c = e % q;
       Acc s = 0;
       for (int a = 0; a < m; ++a) s += sv[r * EIG_MAXP + a] * sy[a * EIG_MAXP + c];
-      Xi[(int64_t)(l0 + r) * ldx + c] = (T)s;
+      Xi[(int64_t)(l0 + r) * ldx + c] = (TX)s;
     }
   }
 }
@@ -681,7 +684,8 @@ __global__ void k_final_z(const int* ni, const int* off, const int64_t* xoff, in
 // ---------------------------------------------------------------------------
 // driver
 // ---------------------------------------------------------------------------
-template <class T>
+// T: the factors of A~_ii and the applications of T; TV: the Krylov basis and its orthogonalisation
+template <class T, class TV>
 static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const double* dscale) {
   cudaStream_t st = h->st;
   const int N = h->N;
@@ -773,7 +777,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   A2LS_CUDA(cudaMemsetAsync(d_rank, 0, sizeof(int) * N, st));
   A2LS_CUDA(cudaMemsetAsync(d_ycols, 0, sizeof(int) * N, st));
   A2LS_CUDA(cudaMemsetAsync(d_zcols, 0, sizeof(int) * N, st));
-  T* V = dalloc<T>(h, hvo[N]);
+  TV* V = dalloc<TV>(h, hvo[N]);
   T* W = dalloc<T>(h, hvo[N]);
   double* H = dalloc<double>(h, (size_t)N * P * P);
   double* Y = dalloc<double>(h, (size_t)N * P * P);
@@ -781,7 +785,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   int* d_actk = dalloc<int>(h, N);  // active and not solved in the full space (block steps j >= 1)
   const int nevmax = std::max(nev, 1) + 1;
   double* eigout = dalloc<double>(h, (size_t)N * nevmax * 2);
-  A2LS_CUDA(cudaMemsetAsync(V, 0, sizeof(T) * hvo[N], st));
+  A2LS_CUDA(cudaMemsetAsync(V, 0, sizeof(TV) * hvo[N], st));
   A2LS_CUDA(cudaMemsetAsync(W, 0, sizeof(T) * hvo[N], st));
   A2LS_CUDA(cudaMemsetAsync(H, 0, sizeof(double) * N * P * P, st));
   A2LS_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * N * P * P, st));
@@ -791,19 +795,19 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     A2LS_CUDA(cudaStreamSynchronize(st));
   }
 
-  using Acc = typename EAcc<T>::type;
+  using Acc = typename EAcc<TV>::type;
   const size_t orth_smem = sizeof(double) * (2 * EIG_MAXP * EIG_MAXP + EIG_MAXP) + sizeof(Acc) * 2 * RC * EIG_MAXP;
   const size_t rr_smem = sizeof(double) * (2 * EIG_MAXP * (EIG_MAXP + 1) + 64 * EIG_MAXP + 3 * EIG_MAXP) +
                          sizeof(int) * EIG_MAXP + 64;
   const size_t vy_smem = sizeof(Acc) * (EIG_MAXP * EIG_MAXP + RC * EIG_MAXP);
-  A2LS_CUDA(cudaFuncSetAttribute(k_orth<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orth_smem));
+  A2LS_CUDA(cudaFuncSetAttribute(k_orth<TV, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orth_smem));
   A2LS_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_smem));
-  A2LS_CUDA(cudaFuncSetAttribute(k_vy<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vy_smem));
+  A2LS_CUDA(cudaFuncSetAttribute(k_vy<TV, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vy_smem));
 
   // T applied to V[:, vcol : vcol + p] -> W[:, 0:p]; tri_flops = one triangular half over the active set
   double tri_flops = 0.0;
   auto apply_T = [&](int vcol, const int* actv) {
-    k_bmul<T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, vcol, d_pv, actv, h->d_lrow, h->d_lcol,
+    k_bmul<TV, T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, vcol, d_pv, actv, h->d_lrow, h->d_lcol,
                                  h->d_lval, h->d_D, V, W);
     A2LS_LAUNCH();
     {
@@ -823,7 +827,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, d_active, d_kd, kvec, W);
     A2LS_LAUNCH();
     // no previous basis: jb = 0; R written into H's last rows (discarded)
-    k_orth<T><<<N, EIG_THREADS, orth_smem, st>>>(h->d_ni, d_vo, P, d_pv, d_active, 0, b, V, W, Rscr, 0, 0,
+    k_orth<TV, T><<<N, EIG_THREADS, orth_smem, st>>>(h->d_ni, d_vo, P, d_pv, d_active, 0, b, V, W, Rscr, 0, 0,
                                                   0, nullptr, d_rank);
     A2LS_LAUNCH();
   };
@@ -858,7 +862,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
       // full-space subdomains (j == 0 only): H = V0^T (T V0)
       {
         KTime kt(h, KT_EIG_ORTH, orth_flops);
-        k_orth<T><<<N, EIG_THREADS, orth_smem, st>>>(h->d_ni, d_vo, P, d_pv, actv, j + 1, b, V, W, H,
+        k_orth<TV, T><<<N, EIG_THREADS, orth_smem, st>>>(h->d_ni, d_vo, P, d_pv, actv, j + 1, b, V, W, H,
                                                       (j + 1) * b, j * b, (j + 1) * b, d_full, d_rank);
         A2LS_LAUNCH();
       }
@@ -882,7 +886,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     if (remaining == 0) break;
     A2LS_CUDA(cudaMemcpyAsync(d_active, act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
     // restart block: W = V[:, 0:sb] Y[:, 0:b]
-    k_vy<T><<<N, EIG_THREADS, vy_smem, st>>>(h->d_ni, d_vo, P, d_msb, d_pv, d_active, V, Y, W);
+    k_vy<TV, T><<<N, EIG_THREADS, vy_smem, st>>>(h->d_ni, d_vo, P, d_msb, d_pv, d_active, V, Y, W);
     A2LS_LAUNCH();
     orthonormalize_W_into_V0();
   }
@@ -898,7 +902,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   std::vector<int> zc(N), yc(N);
   A2LS_CUDA(cudaMemcpyAsync(zc.data(), d_zcols, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
   A2LS_CUDA(cudaStreamSynchronize(st));
-  k_vy<T><<<N, EIG_THREADS, vy_smem, st>>>(h->d_ni, d_vo, P, d_msb, d_zcols, d_active, V, Y, W);
+  k_vy<TV, T><<<N, EIG_THREADS, vy_smem, st>>>(h->d_ni, d_vo, P, d_msb, d_zcols, d_active, V, Y, W);
   A2LS_LAUNCH();
   const int zld = nev + 2;
   std::vector<int64_t> hzo(N + 1, 0);
@@ -963,11 +967,13 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
 // kernel vector that the operator projects out: applications of T carry relative
 // errors of 1e-6 to 4e-3, which bounds how well the FP32 coarse space matches the
 // FP64 one (the flexible outer iteration absorbs the difference).
+// The Krylov basis has the precision of the solves with A~_ii.  (An FP32 basis with FP64 solves
+// produced non-finite Rayleigh-Ritz matrices on the high-contrast problem and is not used.)
 void eigensolve(a2ls_handle* h, void* fac_tilde, const double* last_pivot, const double* diag_scale) {
   if (h->opt.eig_precision != A2LS_FP32)
-    eigensolve_t<double>(h, static_cast<double*>(fac_tilde), last_pivot, diag_scale);
+    eigensolve_t<double, double>(h, static_cast<double*>(fac_tilde), last_pivot, diag_scale);
   else
-    eigensolve_t<float>(h, static_cast<float*>(fac_tilde), last_pivot, diag_scale);
+    eigensolve_t<float, float>(h, static_cast<float*>(fac_tilde), last_pivot, diag_scale);
 }
 
 }  // namespace a2ls
