@@ -106,6 +106,7 @@ typedef struct {
   int32_t eig_precision;    /* precision of the factorisation of A~_ii and of the local eigensolves:
                                -1 (default) = FP64 always; A2LS_FP64; A2LS_FP32 (only for local splittings
                                whose conditioning FP32 can resolve; high-contrast problems need FP64) */
+  int32_t graphs;           /* 1 (default): GMRES replays the apply as CUDA graphs captured on first use */
 } a2ls_options;
 
 /* Fills *opt with the defaults listed above.  Never fails. */
@@ -172,6 +173,7 @@ enum {
   A2LS_Q_EINV = 7,       /* double[n0*n0]: the inverse of A_00 used by the apply, row-major */
   A2LS_Q_EIGSTATS = 8,   /* int32[2*N]: eigen cycles run and kernel dimension per subdomain */
   A2LS_Q_LAUNCHES = 9,   /* int64[1]: kernels this handle has launched so far */
+  A2LS_Q_TUNING = 11,    /* int32[2]: CTA width chosen for the local solves, CUDA graphs held */
   A2LS_Q_KERNEL_TIMES = 10 /* double[3*8]: (launches, total ms, algorithmic work) of the tracked kernels;
                               work is flops, or bytes moved for the apply local solves; in the order
                               local LU, splitting LU, eigen triangular solves, eigen orthogonalisation,

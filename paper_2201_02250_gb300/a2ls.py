@@ -20,7 +20,7 @@ FP64, FP32 = 0, 1
 VARIANTS = {"deflated_ras": 0, "deflated_asm": 1, "additive_ras": 2, "additive_asm": 3, "ras": 4, "asm": 5}
 POU = {"boolean": 0, "multiplicity": 1}
 (Q_SIZES, Q_SUBDOMAINS, Q_LUMP, Q_FACTORS, Q_COARSE, Q_EIGVALS, Q_TIMES, Q_EINV, Q_EIGSTATS, Q_LAUNCHES,
- Q_KERNEL_TIMES) = range(11)
+ Q_KERNEL_TIMES, Q_TUNING) = range(12)
 TRACKED_KERNELS = ["lu_local", "lu_splitting", "eig_triangular_solves", "eig_orthogonalisation",
                    "eig_rayleigh_ritz", "coarse_lu", "coarse_inverse", "apply_local_solves"]
 PHASES = ["graph", "extract", "lu", "eig_coarse", "coarse", "setup_total", "solve_total", "apply"]
@@ -43,7 +43,7 @@ class Options(ctypes.Structure):
                 ("tau", ctypes.c_double), ("eig_block_steps", ctypes.c_int32),
                 ("eig_max_cycles", ctypes.c_int32), ("eig_tol", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("timing", ctypes.c_int32),
-                ("eig_precision", ctypes.c_int32)]
+                ("eig_precision", ctypes.c_int32), ("graphs", ctypes.c_int32)]
 
 
 _LIB = None
@@ -240,6 +240,10 @@ class Preconditioner:
     def times(self) -> dict:
         t = np.frombuffer(self._query(Q_TIMES), dtype=np.float64)
         return {k: float(t[i]) for i, k in enumerate(PHASES)}
+
+    def tuning(self) -> dict:
+        v = np.frombuffer(self._query(Q_TUNING), dtype=np.int32)
+        return {"local_solve_threads": int(v[0]), "apply_graphs": int(v[1])}
 
     def launches(self) -> int:
         return int(np.frombuffer(self._query(Q_LAUNCHES), dtype=np.int64)[0])

@@ -79,6 +79,9 @@ struct a2ls_handle {
   int64_t* d_foff = nullptr;
   int* d_idx = nullptr;                      // sum n_i: local -> global
   int* d_ipos = nullptr;                     // n: local index of a node inside its own part
+  int* d_sched = nullptr;                    // N: subdomains by decreasing size (work order)
+  int* d_counter = nullptr;                  // work-queue counter of the persistent kernels
+  int ls_width = 0;                          // CTA width of the local solves (autotuned)
   int sum_n = 0, max_n = 0;
   int max_rownnz = 0, max_memb = 0;          // largest row of A, largest membership count
   // node -> memberships (flat local positions off_i + l), sorted by subdomain
@@ -117,6 +120,10 @@ struct a2ls_handle {
 
   double times[16] = {0};
   int64_t launches = 0;                      // kernels launched by this handle
+  // CUDA graphs of the apply, one per (input, output) pair used by GMRES
+  struct ApplyGraph { const double* r; double* z; cudaGraphExec_t exec; };
+  std::vector<ApplyGraph> graphs;
+  cudaStream_t cap_st = nullptr;
   // optional per-kernel event timing: pairs of events per tracked kernel
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> kt_events[a2ls::KT_COUNT];
   std::vector<cudaEvent_t> kt_pool;
@@ -162,6 +169,10 @@ template <class T> void invert_diag_tiles(a2ls_handle* h, T* fac);
 // y_loc / z output of the RAS/ASM local solves; see k_dense.cu for the modes
 template <class T> void local_solves(a2ls_handle* h, const T* fac, const double* t, const double* q,
                                      double* z, int mode);
+template <class T> void autotune_local_solves(a2ls_handle* h, const T* fac, const double* t, double* scratch,
+                                              int mode);
+int autotune_lookup(const char* key);            // 0 if unknown
+void autotune_store(const char* key, int value);
 void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv, int band);
 template <class T> void block_solve(a2ls_handle* h, const T* fac, T* X, const int64_t* xoff, int col0, int ldx,
                                     const int* pvec, int pmax, const int* active, int forward, int backward);
@@ -177,6 +188,7 @@ void build_coarse_operator(a2ls_handle* h);
 // k_krylov.cu
 void spmv(a2ls_handle* h, const double* x, double* y, const double* b_minus, cudaStream_t st);
 void apply_preconditioner(a2ls_handle* h, const double* r, double* z);
+void apply_preconditioner_graph(a2ls_handle* h, const double* r, double* z);
 double dot(a2ls_handle* h, const double* x, const double* y);
 double nrm2(a2ls_handle* h, const double* x);
 int gmres(a2ls_handle* h, const double* b, double* x, double rtol, int* iters, double* relres);

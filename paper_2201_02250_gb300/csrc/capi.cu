@@ -5,6 +5,8 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 namespace a2ls {
 
@@ -92,6 +94,64 @@ void dfree(a2ls_handle* h, void* p) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// autotune cache: process-wide map, mirrored in the JSON file named by A2LS_AUTOTUNE_CACHE
+// ---------------------------------------------------------------------------
+static std::mutex g_tune_mutex;
+static std::map<std::string, int> g_tune;
+static bool g_tune_loaded = false;
+
+static void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = getenv("A2LS_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  std::string text;
+  char buf[4096];
+  size_t k;
+  while ((k = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, k);
+  fclose(f);
+  // flat JSON object {"key": int, ...}
+  size_t p = 0;
+  while ((p = text.find('"', p)) != std::string::npos) {
+    const size_t q = text.find('"', p + 1);
+    if (q == std::string::npos) break;
+    const std::string key = text.substr(p + 1, q - p - 1);
+    const size_t c = text.find(':', q);
+    if (c == std::string::npos) break;
+    g_tune[key] = atoi(text.c_str() + c + 1);
+    p = text.find_first_of(",}", c);
+    if (p == std::string::npos) break;
+  }
+}
+
+int autotune_lookup(const char* key) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  tune_load_locked();
+  auto it = g_tune.find(key);
+  return it == g_tune.end() ? 0 : it->second;
+}
+
+void autotune_store(const char* key, int value) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  tune_load_locked();
+  g_tune[key] = value;
+  const char* path = getenv("A2LS_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "w");
+  if (!f) return;
+  fprintf(f, "{");
+  bool first = true;
+  for (const auto& kv : g_tune) {
+    fprintf(f, "%s\n  \"%s\": %d", first ? "" : ",", kv.first.c_str(), kv.second);
+    first = false;
+  }
+  fprintf(f, "\n}\n");
+  fclose(f);
+}
+
 static const char* status_name(int c) {
   switch (c) {
     case A2LS_ERR_ARG: return "invalid argument";
@@ -168,6 +228,9 @@ __global__ void k_max_rowlen(int n, const int* rowptr, const int* mrow, int* out
 
 static void destroy_handle(a2ls_handle* h) {
   if (!h) return;
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  if (h->cap_st) cudaStreamDestroy(h->cap_st);
   collect_kernel_times(h);
   for (cudaEvent_t e : h->kt_pool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFreeAsync(p, h->st);
@@ -237,6 +300,7 @@ void a2ls_default_options(a2ls_options* o) {
   o->stream = nullptr;
   o->timing = 0;
   o->eig_precision = -1;
+  o->graphs = 1;
 }
 
 const char* a2ls_last_error(void) { return g_last_error.c_str(); }
@@ -306,6 +370,18 @@ int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int
     h->d_q = dalloc<double>(h, h->n);
     h->d_t = dalloc<double>(h, h->n);
     h->d_yloc = dalloc<double>(h, h->sum_n);
+    // pick the CTA width of the local solves for this problem (timed on its own factors)
+    {
+      const bool ras = v == A2LS_DEFLATED_RAS || v == A2LS_ADDITIVE_RAS || v == A2LS_ONE_LEVEL_RAS;
+      const int mode = ras ? (o.pou == A2LS_POU_BOOLEAN ? 0 : 1) : 2;
+      A2LS_CUDA(cudaMemsetAsync(h->d_t, 0, sizeof(double) * h->n, st));
+      double* scratch = mode == 0 ? h->d_q : h->d_yloc;
+      const int timing = h->opt.timing;
+      h->opt.timing = 0;
+      if (o.precision == A2LS_FP64) autotune_local_solves<double>(h, static_cast<double*>(h->d_fac), h->d_t, scratch, mode);
+      else autotune_local_solves<float>(h, static_cast<float*>(h->d_fac), h->d_t, scratch, mode);
+      h->opt.timing = timing;
+    }
     sync_and_check(h, "setup");
     h->times[Phase::SETUP_TOTAL] = total.stop();
     *out = h;
@@ -432,6 +508,11 @@ int a2ls_query(a2ls_handle* h, int32_t what, void* out, int64_t capacity, int64_
       case A2LS_Q_LAUNCHES:
         put(&h->launches, sizeof(int64_t));
         break;
+      case A2LS_Q_TUNING: {
+        const int32_t v[2] = {h->ls_width, (int32_t)h->graphs.size()};
+        put(v, sizeof(v));
+        break;
+      }
       case A2LS_Q_KERNEL_TIMES: {
         collect_kernel_times(h);
         for (int k = 0; k < KT_COUNT; ++k) {

@@ -164,10 +164,10 @@ constexpr int LU_NB = 32;
 template <class T>
 __global__ void __launch_bounds__(256) k_lu(int N, const int* ni, const int* ld, const int64_t* foff,
                                             T* fac, int allow_last_zero, double* last_pivot,
-                                            const double* dscale, int* st) {
+                                            const double* dscale, int* st, const int* sched) {
   using Acc = typename AccOf<T>::type;
   __shared__ Acc sA[GK * 65], sB[GK * 65];
-  const int i = blockIdx.x;
+  const int i = sched ? sched[blockIdx.x] : blockIdx.x;  // largest subdomains first
   const int n = ni[i];
   const int64_t L = ld[i];
   T* A = fac + foff[i];
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256) k_lu(int N, const int* ni, const int* ld,
 template <class T>
 void lu_batched(a2ls_handle* h, T* fac, int allow_last_zero, double* last_pivot, double* diag_scale) {
   k_lu<T><<<h->N, 256, 0, h->st>>>(h->N, h->d_ni, h->d_ld, h->d_foff, fac, allow_last_zero, last_pivot,
-                                   diag_scale, h->d_status);
+                                   diag_scale, h->d_status, h->d_sched);
   A2LS_LAUNCH();
 }
 
@@ -321,15 +321,14 @@ __device__ __forceinline__ double dot_vec<double, double>(const double2& a, cons
   return a.x * x[0] + a.y * x[1];
 }
 
-constexpr int LS_THREADS = 512;
-constexpr int LS_WARPS = LS_THREADS / 32;
-constexpr int ROWS_PER_WARP = TB / LS_WARPS;  // 4
 
 // s[r] = x[r0 + r] - sum_{c in [c0, c1)} M[r0 + r][c] x[c] for r < tb (c0, c1 multiples of Vec width
-// except c1 which may be padded up to ld with zeros)
-template <class T, class Acc>
+// except c1 which may be padded up to ld with zeros); the 64 rows of a tile are spread over the warps
+template <class T, class Acc, int THREADS>
 __device__ __forceinline__ void panel_residual(const T* __restrict__ M, int64_t L, int r0, int tb, int c0,
                                                int c1, const Acc* x, Acc* s) {
+  constexpr int LS_WARPS = THREADS / 32;
+  constexpr int ROWS_PER_WARP = TB / LS_WARPS;
   using V = typename Vec<T>::type;
   constexpr int VW = Vec<T>::W;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -361,9 +360,11 @@ __device__ __forceinline__ void panel_residual(const T* __restrict__ M, int64_t 
 }
 
 // x[r0 + r] = sum_c Tinv[r][c] s[c], with the tile's unit-lower (lower=1) or upper (lower=0) part
-template <class T, class Acc>
+template <class T, class Acc, int THREADS>
 __device__ __forceinline__ void tile_apply(const T* __restrict__ M, int64_t L, int r0, int tb, int lower,
                                            const Acc* s, Acc* x) {
+  constexpr int LS_WARPS = THREADS / 32;
+  constexpr int ROWS_PER_WARP = TB / LS_WARPS;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int u = 0; u < ROWS_PER_WARP; ++u) {
@@ -382,68 +383,137 @@ __device__ __forceinline__ void tile_apply(const T* __restrict__ M, int64_t L, i
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(LS_THREADS) k_local_solve(
+// Persistent over a work queue: each CTA takes the next subdomain from `counter` in the order of
+// `sched` (largest first), so uneven subdomains balance across the SMs.
+template <class T, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_local_solve(
     const int* off, const int* nI, const int* ni, const int* ld, const int64_t* foff, const int* idx,
     const double* D, const T* __restrict__ fac, const double* __restrict__ t, const double* __restrict__ q,
-    double* __restrict__ out, int mode) {
+    double* __restrict__ out, int mode, const int* sched, int* counter, int nwork) {
   using Acc = typename AccOf<T>::type;
   extern __shared__ unsigned char smem_raw[];
   Acc* x = reinterpret_cast<Acc*>(smem_raw);
   __shared__ Acc s[TB];
-  const int i = blockIdx.x;
-  const int n = ni[i], o = off[i];
-  const int64_t L = ld[i];
-  const T* M = fac + foff[i];
-  for (int l = threadIdx.x; l < L; l += LS_THREADS) x[l] = (l < n) ? (Acc)t[idx[o + l]] : (Acc)0;
-  __syncthreads();
-  const int nb = (n + TB - 1) / TB;
-  // forward: L y = t
-  for (int b = 0; b < nb; ++b) {
-    const int r0 = b * TB, tb = min(TB, n - r0);
-    panel_residual<T, Acc>(M, L, r0, tb, 0, r0, x, s);
+  __shared__ int item;
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(counter, 1);
     __syncthreads();
-    tile_apply<T, Acc>(M, L, r0, tb, 1, s, x);
+    const int w = item;
     __syncthreads();
-  }
-  // backward: U x = y
-  for (int b = nb - 1; b >= 0; --b) {
-    const int r0 = b * TB, tb = min(TB, n - r0);
-    const int c0 = r0 + tb;  // a multiple of TB unless this is the last block (then c0 == n: no panel)
-    panel_residual<T, Acc>(M, L, r0, tb, c0, c0 < n ? (int)L : c0, x, s);
+    if (w >= nwork) break;
+    const int i = sched[w];
+    const int n = ni[i], o = off[i];
+    const int64_t L = ld[i];
+    const T* M = fac + foff[i];
+    for (int l = threadIdx.x; l < L; l += THREADS) x[l] = (l < n) ? (Acc)t[idx[o + l]] : (Acc)0;
     __syncthreads();
-    tile_apply<T, Acc>(M, L, r0, tb, 0, s, x);
-    __syncthreads();
-  }
-  if (mode == 0) {
-    const int n_I = nI[i];
-    for (int l = threadIdx.x; l < n_I; l += LS_THREADS) {
-      const int g = idx[o + l];
-      out[g] = (q ? q[g] : 0.0) + (double)x[l];
+    const int nb = (n + TB - 1) / TB;
+    // forward: L y = t
+    for (int b = 0; b < nb; ++b) {
+      const int r0 = b * TB, tb = min(TB, n - r0);
+      panel_residual<T, Acc, THREADS>(M, L, r0, tb, 0, r0, x, s);
+      __syncthreads();
+      tile_apply<T, Acc, THREADS>(M, L, r0, tb, 1, s, x);
+      __syncthreads();
     }
-  } else {
-    for (int l = threadIdx.x; l < n; l += LS_THREADS)
-      out[o + l] = (mode == 1 ? D[o + l] : 1.0) * (double)x[l];
+    // backward: U x = y
+    for (int b = nb - 1; b >= 0; --b) {
+      const int r0 = b * TB, tb = min(TB, n - r0);
+      const int c0 = r0 + tb;  // a multiple of TB unless this is the last block (then c0 == n: no panel)
+      panel_residual<T, Acc, THREADS>(M, L, r0, tb, c0, c0 < n ? (int)L : c0, x, s);
+      __syncthreads();
+      tile_apply<T, Acc, THREADS>(M, L, r0, tb, 0, s, x);
+      __syncthreads();
+    }
+    if (mode == 0) {
+      const int n_I = nI[i];
+      for (int l = threadIdx.x; l < n_I; l += THREADS) {
+        const int g = idx[o + l];
+        out[g] = (q ? q[g] : 0.0) + (double)x[l];
+      }
+    } else {
+      for (int l = threadIdx.x; l < n; l += THREADS) out[o + l] = (mode == 1 ? D[o + l] : 1.0) * (double)x[l];
+    }
+    __syncthreads();
   }
+}
+
+template <class T, int THREADS>
+static void launch_local_solve(a2ls_handle* h, const T* fac, const double* t, const double* q, double* z, int mode) {
+  using Acc = typename AccOf<T>::type;
+  const size_t smem = sizeof(Acc) * round_up(h->max_n, 4);
+  static bool configured[2] = {false, false};
+  if (!configured[sizeof(T) == 8]) {
+    A2LS_CUDA(cudaFuncSetAttribute(k_local_solve<T, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(Acc) * MAXN_LOCAL)));
+    configured[sizeof(T) == 8] = true;
+  }
+  int per_sm = 1, sms = 152;
+  A2LS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local_solve<T, THREADS>, THREADS, smem));
+  int dev = 0;
+  A2LS_CUDA(cudaGetDevice(&dev));
+  A2LS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = std::max(1, std::min(h->N, sms * std::max(per_sm, 1)));
+  A2LS_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->st));
+  k_local_solve<T, THREADS><<<grid, THREADS, smem, h->st>>>(h->d_off, h->d_nI, h->d_ni, h->d_ld, h->d_foff, h->d_idx,
+                                                            h->d_D, fac, t, q, z, mode, h->d_sched, h->d_counter,
+                                                            h->N);
+  A2LS_LAUNCH();
+}
+
+template <class T>
+static void launch_local_solve_width(a2ls_handle* h, int width, const T* fac, const double* t, const double* q,
+                                     double* z, int mode) {
+  if (width == 256) launch_local_solve<T, 256>(h, fac, t, q, z, mode);
+  else if (width == 1024) launch_local_solve<T, 1024>(h, fac, t, q, z, mode);
+  else launch_local_solve<T, 512>(h, fac, t, q, z, mode);
 }
 
 template <class T>
 void local_solves(a2ls_handle* h, const T* fac, const double* t, const double* q, double* z, int mode) {
-  using Acc = typename AccOf<T>::type;
-  const size_t smem = sizeof(Acc) * round_up(h->max_n, 4);
-  static bool configured = false;
-  if (!configured) {
-    A2LS_CUDA(cudaFuncSetAttribute(k_local_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(sizeof(Acc) * MAXN_LOCAL)));
-    configured = true;
-  }
   double bytes = 0.0;
   for (int i = 0; i < h->N; ++i)
     bytes += (double)h->h_n[i] * h->h_n[i] * sizeof(T) + 12.0 * h->h_n[i] + (mode == 0 ? 20.0 * h->h_nI[i] : 12.0 * h->h_n[i]);
   KTime kt(h, KT_APPLY_LOCAL, bytes);
-  k_local_solve<T><<<h->N, LS_THREADS, smem, h->st>>>(h->d_off, h->d_nI, h->d_ni, h->d_ld, h->d_foff,
-                                                      h->d_idx, h->d_D, fac, t, q, z, mode);
-  A2LS_LAUNCH();
+  launch_local_solve_width<T>(h, h->ls_width > 0 ? h->ls_width : 512, fac, t, q, z, mode);
+}
+
+// Autotuner: time the three CTA widths on the handle's own factors (inputs t, outputs scratch) and
+// keep the fastest; results are cached per (precision, subdomain count, largest subdomain, mode)
+// in the process and, when A2LS_AUTOTUNE_CACHE names a file, in that JSON file.
+template <class T>
+void autotune_local_solves(a2ls_handle* h, const T* fac, const double* t, double* scratch, int mode) {
+  char key[128];
+  snprintf(key, sizeof(key), "local_solve_%s_N%d_max%d_mode%d", sizeof(T) == 8 ? "fp64" : "fp32", h->N, h->max_n,
+           mode);
+  int cached = autotune_lookup(key);
+  if (cached > 0) {
+    h->ls_width = cached;
+    return;
+  }
+  const int widths[3] = {256, 512, 1024};
+  float best_ms = 1e30f;
+  int best = 512;
+  cudaEvent_t e0, e1;
+  A2LS_CUDA(cudaEventCreate(&e0));
+  A2LS_CUDA(cudaEventCreate(&e1));
+  for (int w : widths) {
+    launch_local_solve_width<T>(h, w, fac, t, nullptr, scratch, mode);  // warm-up
+    A2LS_CUDA(cudaEventRecord(e0, h->st));
+    for (int rep = 0; rep < 3; ++rep) launch_local_solve_width<T>(h, w, fac, t, nullptr, scratch, mode);
+    A2LS_CUDA(cudaEventRecord(e1, h->st));
+    A2LS_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    A2LS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = w;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->ls_width = best;
+  autotune_store(key, best);
 }
 
 // ---------------------------------------------------------------------------
@@ -457,10 +527,10 @@ __global__ void __launch_bounds__(256) k_block_solve(const int* ni, const int* l
                                                      const T* __restrict__ fac, T* X,
                                                      const int64_t* xoff, int col0, int ldx,
                                                      const int* pvec, const int* active, int forward,
-                                                     int backward) {
+                                                     int backward, const int* sched) {
   using Acc = typename AccOf<T>::type;
   __shared__ Acc sA[GK * 65], sB[GK * 9];
-  const int i = blockIdx.x;
+  const int i = sched ? sched[blockIdx.x] : blockIdx.x;  // largest subdomains first
   if (active && !active[i]) return;
   const int p = pvec[i];
   const int c0 = blockIdx.y * 8;
@@ -515,7 +585,7 @@ void block_solve(a2ls_handle* h, const T* fac, T* X, const int64_t* xoff, int co
                  int pmax, const int* active, int forward, int backward) {
   dim3 grid(h->N, (std::max(pmax, 1) + 7) / 8);
   k_block_solve<T><<<grid, 256, 0, h->st>>>(h->d_ni, h->d_ld, h->d_foff, fac, X, xoff, col0, ldx, pvec, active,
-                                           forward, backward);
+                                           forward, backward, h->d_sched);
   A2LS_LAUNCH();
 }
 
@@ -525,6 +595,8 @@ template void invert_diag_tiles<float>(a2ls_handle*, float*);
 template void invert_diag_tiles<double>(a2ls_handle*, double*);
 template void local_solves<float>(a2ls_handle*, const float*, const double*, const double*, double*, int);
 template void local_solves<double>(a2ls_handle*, const double*, const double*, const double*, double*, int);
+template void autotune_local_solves<float>(a2ls_handle*, const float*, const double*, double*, int);
+template void autotune_local_solves<double>(a2ls_handle*, const double*, const double*, double*, int);
 template void block_solve<float>(a2ls_handle*, const float*, float*, const int64_t*, int, int, const int*, int,
                                   const int*, int, int);
 template void block_solve<double>(a2ls_handle*, const double*, double*, const int64_t*, int, int, const int*, int,

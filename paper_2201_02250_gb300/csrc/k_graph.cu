@@ -429,6 +429,16 @@ void build_subdomains(a2ls_handle* h) {
                             cudaMemcpyHostToDevice, st));
   h->d_idx = dalloc<int>(h, h->sum_n);
   h->d_ipos = dalloc<int>(h, n);
+  {
+    // work order of the batched kernels: largest subdomains first (longest-processing-time rule)
+    std::vector<int> order(N);
+    for (int i = 0; i < N; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return h->h_n[a] > h->h_n[b]; });
+    h->d_sched = dalloc<int>(h, N);
+    h->d_counter = dalloc<int>(h, 4);
+    A2LS_CUDA(cudaMemcpyAsync(h->d_sched, order.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    A2LS_CUDA(cudaStreamSynchronize(st));
+  }
   k_bitmap_emit<<<N, 256, 0, st>>>(W, interior, member, h->d_off, h->d_nI, h->d_idx, h->d_ipos);
   A2LS_LAUNCH();
   dfree(h, interior);

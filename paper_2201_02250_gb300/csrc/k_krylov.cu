@@ -180,6 +180,50 @@ void apply_preconditioner(a2ls_handle* h, const double* r, double* z) {
   }
 }
 
+// The apply as a CUDA graph, captured once per (r, z) pair on an internal stream and replayed on
+// the handle's stream: GMRES applies the preconditioner to the same m basis vectors every cycle.
+void apply_preconditioner_graph(a2ls_handle* h, const double* r, double* z) {
+  if (!h->opt.graphs) {
+    apply_preconditioner(h, r, z);
+    return;
+  }
+  for (const auto& g : h->graphs)
+    if (g.r == r && g.z == z) {
+      A2LS_CUDA(cudaGraphLaunch(g.exec, h->st));
+      h->launches += 1;
+      return;
+    }
+  if (!h->cap_st) A2LS_CUDA(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+  cudaStream_t user = h->st;
+  const int timing = h->opt.timing;
+  h->opt.timing = 0;
+  h->st = h->cap_st;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    try {
+      apply_preconditioner(h, r, z);
+    } catch (...) {
+      cudaStreamEndCapture(h->cap_st, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      h->st = user;
+      h->opt.timing = timing;
+      throw;
+    }
+    e = cudaStreamEndCapture(h->cap_st, &graph);
+  }
+  h->st = user;
+  h->opt.timing = timing;
+  A2LS_CUDA(e);
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  A2LS_CUDA(ei);
+  h->graphs.push_back({r, z, exec});
+  A2LS_CUDA(cudaGraphLaunch(exec, h->st));
+  h->launches += 1;
+}
+
 // ---------------------------------------------------------------------------
 // reductions for GMRES: multi-dot with a last-block-done final reduction
 // out[k] = sum_r V[k][r] * w[r] for k < nv, out[nv] = w . w (if with_self)
@@ -373,7 +417,7 @@ int gmres(a2ls_handle* h, const double* b, double* x, double rtol, int* iters_ou
     for (int j = 0; j < m; ++j) {
       double* vj = V + (size_t)j * n;
       double* zj = flexible ? Zs + (size_t)j * n : tmp;
-      apply_preconditioner(h, vj, zj);
+      apply_preconditioner_graph(h, vj, zj);
       spmv(h, zj, w, nullptr, st);  // w = A z_j
       // CGS2 against V_0..V_j
       multidot(h, V, n, j + 1, w, 1, dh);                 // h1, |w|^2
@@ -422,7 +466,7 @@ int gmres(a2ls_handle* h, const double* b, double* x, double rtol, int* iters_ou
     } else {
       k_lincomb<<<gb, 256, 0, st>>>(n, V, n, k, dh + 3 * MD_MAX, w, nullptr);
       A2LS_LAUNCH();
-      apply_preconditioner(h, w, tmp);
+      apply_preconditioner_graph(h, w, tmp);
       k_axpy<<<gb, 256, 0, st>>>(n, 1.0, tmp, x);
       A2LS_LAUNCH();
     }
