@@ -131,6 +131,56 @@ def high_contrast_fv_2d(m: int, seed: int, width: int = 4, fraction: float = 0.1
     return _finish(rows, cols, vals, m * m), kappa
 
 
+def gaussian_random_field(m: int, std: float, corr_len: float, seed: int) -> np.ndarray:
+    """Stationary Gaussian random field on the m x m cell centres of the unit square.
+
+    Gaussian covariance std^2 exp(-|d|^2 / (2 corr_len^2)), synthesised spectrally: white noise
+    filtered in Fourier space by the square root of the covariance's spectral density on a
+    doubled periodic grid, then cropped and rescaled to the requested standard deviation.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed + 100000))
+    M = 2 * m
+    k = np.fft.fftfreq(M, d=1.0 / M)  # integer wavenumbers on the doubled (period 2) domain
+    kx, ky = np.meshgrid(k, k, indexing="ij")
+    # spectral density of the Gaussian covariance (period 2): exp(-(pi l)^2 |k|^2 / 2) up to a constant
+    spec = np.exp(-0.5 * (np.pi * corr_len) ** 2 * (kx ** 2 + ky ** 2))
+    noise = rng.standard_normal((M, M)) + 1j * rng.standard_normal((M, M))
+    field = np.real(np.fft.ifft2(np.sqrt(spec) * noise))[:m, :m]
+    field = (field - field.mean()) / max(field.std(), 1e-300)
+    return std * field
+
+
+def fv_diffusion_2d(kappa: np.ndarray) -> sp.csr_matrix:
+    """Cell-centred finite-volume -div(kappa grad u) on a square grid, kappa[j, i] per cell,
+    harmonic-mean face transmissibilities, Dirichlet faces 2 kappa (cell k = j*m + i)."""
+    m = kappa.shape[0]
+    rows, cols, vals = [], [], []
+    for j in range(m):
+        for i in range(m):
+            k = j * m + i
+            kc = kappa[j, i]
+            d = 0.0
+            for (ii, jj) in ((i - 1, j), (i + 1, j), (i, j - 1), (i, j + 1)):
+                if 0 <= ii < m and 0 <= jj < m:
+                    kn = kappa[jj, ii]
+                    t = 2.0 * kc * kn / (kc + kn)
+                    rows.append(k); cols.append(jj * m + ii); vals.append(-t)
+                    d += t
+                else:
+                    d += 2.0 * kc
+            rows.append(k); cols.append(k); vals.append(d)
+    return _finish(rows, cols, vals, m * m)
+
+
+def config_c4(seed: int, m: int = 256, blocks: int = 8) -> Problem:
+    """Log-normal diffusion kappa = exp(g), g a Gaussian random field (std 2, correlation length
+    0.05), on an m x m grid; blocks x blocks subdomains, overlap 2, nev = 10."""
+    kappa = np.exp(gaussian_random_field(m, 2.0, 0.05, seed))
+    A = fv_diffusion_2d(kappa)
+    return Problem(f"c4_lognormal_{m}_s{seed}", A, block_partition_2d(m, blocks), 2, 10,
+                   rhs_uniform(m * m, seed), {"grid": m, "blocks": blocks, "seed": seed})
+
+
 def conv_diff_3d(m: int, beta: float) -> sp.csr_matrix:
     """-Laplace(u) + b.grad(u) on the m^3 interior grid of the unit cube.
 
