@@ -75,6 +75,11 @@ enum { A2LS_POU_BOOLEAN = 0, A2LS_POU_MULTIPLICITY = 1 };
 
 typedef struct a2ls_handle a2ls_handle;
 
+/* Learned warm start of the local eigensolves (not part of the paper): a message-passing network
+ * over each subdomain's local graph, see the a2ls_gnn_* entry points at the end of this header. */
+typedef struct a2ls_gnn a2ls_gnn;
+typedef struct a2ls_gnn_sample a2ls_gnn_sample;
+
 /* Sparse matrix in CSR form.  All arrays are device pointers owned by the
  * caller and only read during a2ls_setup (the library keeps its own copy).
  * rowptr: n+1 entries, rowptr[0] = 0, non-decreasing, rowptr[n] = nnz.
@@ -107,6 +112,9 @@ typedef struct {
                                -1 (default) = FP64 always; A2LS_FP64; A2LS_FP32 (only for local splittings
                                whose conditioning FP32 can resolve; high-contrast problems need FP64) */
   int32_t graphs;           /* 1 (default): GMRES replays the apply as CUDA graphs captured on first use */
+  const a2ls_gnn* warm_start; /* NULL (default): random start blocks for the local eigensolves; otherwise
+                                 the network's proposal (a2ls_gnn_forward) starts each subdomain's block
+                                 Krylov iteration.  The network is only read; it must outlive a2ls_setup. */
 } a2ls_options;
 
 /* Fills *opt with the defaults listed above.  Never fails. */
@@ -224,6 +232,80 @@ int a2ls_apply_static(a2ls_handle* h, const double* r, double* z);
  * Asynchronous on the handle's stream.
  */
 int a2ls_spmv(a2ls_handle* h, const double* x, double* y);
+
+/* ---------------------------------------------------------------------------------------------
+ * Learned warm start (not part of the paper; an addition of this library).
+ *
+ * The local eigenproblems of Eq. 3.1 are solved by a restarted block Krylov iteration whose
+ * starting block is random unless a2ls_options::warm_start names a network.  The network reads
+ * each subdomain's local matrix A_ii and lumped sums s_i (Definition 3.1) and proposes 16 columns:
+ *   edge weights  w_lk = (|a_lk| + |a_kl|) / (2 sqrt(|a_ll a_kk|)) on entries with a_lk, a_kl != 0;
+ *   features      x_l = [1, d_l / max d, clip(log(d_l / mean d) / 10, -1, 1), [l in Omega_Gamma_i],
+ *                        s_l / d_l, sum_k w_lk / 4], d_l = |a_ll|;
+ *   three message-passing layers of width 64, h_t = relu(h_{t-1} W_s + (W h_{t-1}) W_n + b),
+ *   an output layer to 16 columns and 32 steps of p <- 0.9 D^-1/2 W D^-1/2 p + 0.1 p_0.
+ * Weights are held in bfloat16 for the forward pass (FP32 master copy for training); all sums
+ * accumulate in FP32.  Training minimises, per subdomain, L_i = min_C ||Z_i - Y C||^2 / m_i (plus
+ * 1e-6 ||C||^2 / m_i) against the eigenvectors Z_i (n_i x m_i) that the setup selected, averaged over
+ * the subdomains with a target, with Adam (beta 0.9 / 0.999, eps 1e-8).
+ * Parameters are one float vector of a2ls_gnn_num_params() entries in this order, each matrix
+ * row-major (rows = inputs): W_in 6x64, b_in 64, then for t = 1..3: W_s,t 64x64, W_n,t 64x64,
+ * b_t 64, then W_out 64x16.
+ * All a2ls_gnn_* calls return an a2ls_status and synchronise their stream; a network must not be
+ * used by two calls at once.
+ * --------------------------------------------------------------------------------------------- */
+
+/* Number of float parameters of the network (26240). */
+int64_t a2ls_gnn_num_params(void);
+
+/* New network with He-normal weights (std sqrt(2 / inputs)) drawn from `seed`, zero biases.
+ * stream: cudaStream_t for the network's own work (NULL = legacy default stream). */
+int a2ls_gnn_create(uint64_t seed, void* stream, a2ls_gnn** out);
+int a2ls_gnn_destroy(a2ls_gnn* g);
+
+/* host: count = a2ls_gnn_num_params() floats.  set_params also clears the Adam state and the
+ * gradient accumulator. */
+int a2ls_gnn_get_params(a2ls_gnn* g, float* host, int64_t count);
+int a2ls_gnn_set_params(a2ls_gnn* g, const float* host, int64_t count);
+
+/* Mean of the gradients accumulated by a2ls_gnn_loss_grad since the last Adam step (zeros if none). */
+int a2ls_gnn_get_grads(a2ls_gnn* g, float* host, int64_t count);
+
+/* A training or inference sample: the local graphs and features of a set-up handle's subdomains
+ * and, as target, the eigenvectors its setup selected (none for one-level variants or nev = 0).
+ * The sample copies what it needs; the handle may be destroyed afterwards.  Its work runs on the
+ * handle's stream. */
+int a2ls_gnn_sample_create(a2ls_handle* h, a2ls_gnn_sample** out);
+/* Replace the target.  m: host, N int32 in [0, 32]; Z: host doubles, for each subdomain an
+ * n_i x m_i row-major block in the local order of A2LS_Q_SUBDOMAINS. */
+int a2ls_gnn_sample_set_target(a2ls_gnn_sample* s, const int32_t* m, const double* Z);
+int a2ls_gnn_sample_destroy(a2ls_gnn_sample* s);
+
+/* Items for a2ls_gnn_sample_query (copied to host; rows in the local order of A2LS_Q_SUBDOMAINS). */
+enum {
+  A2LS_GQ_FEATURES = 0,    /* float[sum n_i * 8]: the 6 features per row, then two zeros */
+  A2LS_GQ_ROWPTR = 1,      /* int64[sum n_i + 1]: entries of each row (one per entry of the row of A) */
+  A2LS_GQ_COLS = 2,        /* int32[entries]: flat row index off_i + k of the neighbour, or -1 */
+  A2LS_GQ_WEIGHTS = 3,     /* float[entries]: w_lk (0 where the column is -1) */
+  A2LS_GQ_SWEIGHTS = 4,    /* float[entries]: w_lk / sqrt(deg_l deg_k) */
+  A2LS_GQ_TARGET_COLS = 5  /* int32[N]: m_i of the target */
+};
+int a2ls_gnn_sample_query(a2ls_gnn_sample* s, int32_t what, void* out, int64_t capacity, int64_t* needed);
+
+/* Y: host, sum n_i x 16 floats, the network's proposal for every subdomain. */
+int a2ls_gnn_forward(a2ls_gnn* g, a2ls_gnn_sample* s, float* Y);
+
+/* Forward pass, loss and backward pass on one sample; adds the sample's gradient to the
+ * accumulator.  loss: host, receives the sample's mean loss (may be NULL).  STATE if the sample
+ * has no target. */
+int a2ls_gnn_loss_grad(a2ls_gnn* g, a2ls_gnn_sample* s, double* loss);
+
+/* One Adam step (Kingma and Ba, 2015) with the mean accumulated gradient; clears the accumulator.
+ * STATE if nothing was accumulated. */
+int a2ls_gnn_adam_step(a2ls_gnn* g, double lr);
+
+/* Kernels the network's own calls have launched so far. */
+int64_t a2ls_gnn_launches(const a2ls_gnn* g);
 
 #ifdef __cplusplus
 }

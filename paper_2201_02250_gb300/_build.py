@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libA2LS.so")
-SOURCES = ["capi.cu", "k_graph.cu", "k_dense.cu", "k_eig.cu", "k_coarse.cu", "k_krylov.cu", "k_static.cu"]
+SOURCES = ["capi.cu", "k_graph.cu", "k_dense.cu", "k_eig.cu", "k_coarse.cu", "k_krylov.cu", "k_static.cu", "k_gnn.cu"]
 HEADERS = [os.path.join(CSRC, "a2ls_internal.cuh"), os.path.join(CSRC, "small_eig.cuh"),
            os.path.join(ROOT, "include", "a2ls.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

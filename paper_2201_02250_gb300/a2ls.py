@@ -43,7 +43,7 @@ class Options(ctypes.Structure):
                 ("tau", ctypes.c_double), ("eig_block_steps", ctypes.c_int32),
                 ("eig_max_cycles", ctypes.c_int32), ("eig_tol", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("timing", ctypes.c_int32),
-                ("eig_precision", ctypes.c_int32), ("graphs", ctypes.c_int32)]
+                ("eig_precision", ctypes.c_int32), ("graphs", ctypes.c_int32), ("warm_start", ctypes.c_void_p)]
 
 
 _LIB = None
@@ -85,6 +85,29 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     for f in ("a2ls_setup", "a2ls_apply", "a2ls_solve", "a2ls_query", "a2ls_set_coarse_basis", "a2ls_spmv",
               "a2ls_apply_static"):
         getattr(L, f).restype = ctypes.c_int
+    # learned warm start
+    i64 = ctypes.c_int64
+    L.a2ls_gnn_num_params.argtypes = []
+    L.a2ls_gnn_num_params.restype = i64
+    L.a2ls_gnn_launches.argtypes = [vp]
+    L.a2ls_gnn_launches.restype = i64
+    L.a2ls_gnn_create.argtypes = [ctypes.c_uint64, vp, ctypes.POINTER(vp)]
+    L.a2ls_gnn_destroy.argtypes = [vp]
+    L.a2ls_gnn_get_params.argtypes = [vp, vp, i64]
+    L.a2ls_gnn_set_params.argtypes = [vp, vp, i64]
+    L.a2ls_gnn_get_grads.argtypes = [vp, vp, i64]
+    L.a2ls_gnn_sample_create.argtypes = [vp, ctypes.POINTER(vp)]
+    L.a2ls_gnn_sample_set_target.argtypes = [vp, vp, vp]
+    L.a2ls_gnn_sample_destroy.argtypes = [vp]
+    L.a2ls_gnn_sample_query.argtypes = [vp, i32, vp, i64, ctypes.POINTER(i64)]
+    L.a2ls_gnn_forward.argtypes = [vp, vp, vp]
+    L.a2ls_gnn_loss_grad.argtypes = [vp, vp, ctypes.POINTER(f64)]
+    L.a2ls_gnn_adam_step.argtypes = [vp, f64]
+    for f in ("a2ls_gnn_create", "a2ls_gnn_destroy", "a2ls_gnn_get_params", "a2ls_gnn_set_params",
+              "a2ls_gnn_get_grads", "a2ls_gnn_sample_create", "a2ls_gnn_sample_set_target",
+              "a2ls_gnn_sample_destroy", "a2ls_gnn_sample_query", "a2ls_gnn_forward", "a2ls_gnn_loss_grad",
+              "a2ls_gnn_adam_step"):
+        getattr(L, f).restype = ctypes.c_int
     _LIB = L
     return L
 
@@ -105,6 +128,8 @@ def default_options(**kw) -> Options:
             v = POU[v]
         if k in ("precision", "eig_precision") and isinstance(v, str):
             v = {"fp64": FP64, "fp32": FP32}[v]
+        if k == "warm_start":
+            v = None if v is None else v._g.value
         setattr(o, k, v)
     return o
 
@@ -131,6 +156,7 @@ class Preconditioner:
         o = default_options(**opts)
         o.stream = ctypes.c_void_p(int(stream.cuda_stream))
         self.options = o
+        self._warm = opts.get("warm_start")  # the network must outlive the setup call
         csr = CSR(self.n, int(colind.numel()), _ptr(rowptr), _ptr(colind), _ptr(val))
         h = ctypes.c_void_p()
         _check(lib().a2ls_setup(ctypes.byref(csr), ctypes.c_void_p(_ptr(part)), int(overlap), int(nev),
@@ -276,3 +302,114 @@ def from_scipy(A, part, overlap: int, nev: int, device: str = "cuda", **opts):
     p = torch.as_tensor(np.asarray(part, dtype=np.int32), device=device)
     P = Preconditioner(rowptr, colind, val, p, overlap, nev, **opts)
     return P, (rowptr, colind, val, p)
+
+
+# ---------------------------------------------------------------------------------------------
+# learned warm start of the local eigensolves
+# ---------------------------------------------------------------------------------------------
+GQ_FEATURES, GQ_ROWPTR, GQ_COLS, GQ_WEIGHTS, GQ_SWEIGHTS, GQ_TARGET_COLS = range(6)
+GNN_OUT = 16
+
+
+class WarmStartNet:
+    """The warm-start network (weights, Adam state) of the library; see a2ls_gnn_* in include/a2ls.h."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        g = ctypes.c_void_p()
+        _check(lib().a2ls_gnn_create(ctypes.c_uint64(seed), ctypes.c_void_p(int(stream.cuda_stream)),
+                                     ctypes.byref(g)))
+        self._g = g
+
+    @staticmethod
+    def num_params() -> int:
+        return int(lib().a2ls_gnn_num_params())
+
+    def close(self):
+        if getattr(self, "_g", None):
+            lib().a2ls_gnn_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.num_params(), dtype=np.float32)
+        _check(lib().a2ls_gnn_get_params(self._g, out.ctypes.data, out.size))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().a2ls_gnn_set_params(self._g, p.ctypes.data, p.size))
+
+    def grads(self) -> np.ndarray:
+        out = np.empty(self.num_params(), dtype=np.float32)
+        _check(lib().a2ls_gnn_get_grads(self._g, out.ctypes.data, out.size))
+        return out
+
+    def forward(self, sample: "GnnSample") -> np.ndarray:
+        out = np.empty((sample.rows, GNN_OUT), dtype=np.float32)
+        _check(lib().a2ls_gnn_forward(self._g, sample._s, out.ctypes.data))
+        return out
+
+    def loss_grad(self, sample: "GnnSample") -> float:
+        L = ctypes.c_double()
+        _check(lib().a2ls_gnn_loss_grad(self._g, sample._s, ctypes.byref(L)))
+        return float(L.value)
+
+    def adam_step(self, lr: float):
+        _check(lib().a2ls_gnn_adam_step(self._g, float(lr)))
+
+    def launches(self) -> int:
+        return int(lib().a2ls_gnn_launches(self._g))
+
+
+class GnnSample:
+    """Local graphs, features and target eigenvectors of a set-up Preconditioner's subdomains."""
+
+    def __init__(self, pre: Preconditioner):
+        s = ctypes.c_void_p()
+        _check(lib().a2ls_gnn_sample_create(pre._h, ctypes.byref(s)))
+        self._s = s
+        sz = pre.sizes()
+        self.N, self.rows = sz["N"], sz["sum_ni"]
+
+    def close(self):
+        if getattr(self, "_s", None):
+            lib().a2ls_gnn_sample_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _query(self, what: int, dtype) -> np.ndarray:
+        need = ctypes.c_int64()
+        _check(lib().a2ls_gnn_sample_query(self._s, what, None, 0, ctypes.byref(need)))
+        out = np.empty(int(need.value) // np.dtype(dtype).itemsize, dtype=dtype)
+        _check(lib().a2ls_gnn_sample_query(self._s, what, out.ctypes.data, int(need.value), None))
+        return out
+
+    def features(self) -> np.ndarray:
+        return self._query(GQ_FEATURES, np.float32).reshape(self.rows, 8)[:, :6]
+
+    def graph(self) -> dict:
+        return {"rowptr": self._query(GQ_ROWPTR, np.int64), "cols": self._query(GQ_COLS, np.int32),
+                "w": self._query(GQ_WEIGHTS, np.float32), "s": self._query(GQ_SWEIGHTS, np.float32)}
+
+    def target_cols(self) -> np.ndarray:
+        return self._query(GQ_TARGET_COLS, np.int32)
+
+    def set_target(self, Z: list):
+        """Z: one (n_i x m_i) array per subdomain, in the local order of Preconditioner.subdomains()."""
+        m = np.array([z.shape[1] for z in Z], dtype=np.int32)
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(z, dtype=np.float64).ravel() for z in Z]))
+        _check(lib().a2ls_gnn_sample_set_target(self._s, m.ctypes.data, flat.ctypes.data))

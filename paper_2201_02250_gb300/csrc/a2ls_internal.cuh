@@ -107,6 +107,12 @@ struct a2ls_handle {
   double* d_W = nullptr;
   double* d_Einv = nullptr;                  // n0 x n0 row-major
   std::vector<double> h_eigvals;             // 2*N*(nevmax)
+  // eigenvectors selected by the setup, Z_i = [k | V Y] (n_i x zld row-major per subdomain, FP64),
+  // kept as training targets of the warm-start network
+  double* d_zev = nullptr;
+  int64_t* d_zoff = nullptr;                 // N+1
+  int zld = 0;
+  std::vector<int> h_zcols;                  // N: columns of Z_i in use
   std::vector<int> h_eigstats;               // 2*N
 
   // apply workspace
@@ -176,6 +182,9 @@ void autotune_store(const char* key, int value);
 void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv, int band);
 template <class T> void block_solve(a2ls_handle* h, const T* fac, T* X, const int64_t* xoff, int col0, int ldx,
                                     const int* pvec, int pmax, const int* active, int forward, int backward);
+
+// k_gnn.cu: the warm-start network's proposal, Y = sum n_i x 16 FP32 on the handle's stream
+void gnn_infer(a2ls_handle* h, const a2ls_gnn* model, float* Y);
 
 // k_eig.cu
 void eigensolve(a2ls_handle* h, void* fac_tilde, const double* last_pivot, const double* diag_scale);

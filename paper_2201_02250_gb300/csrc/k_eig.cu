@@ -202,6 +202,44 @@ __global__ void k_random_block(const int* ni, const int64_t* xoff, int ldx, int 
   }
 }
 
+// warm start: columns c < 16 are the network's proposal Y scaled to unit norm plus a 1e-3 random
+// perturbation (keeps the block full rank where the proposal is not); further columns and subdomains
+// solved in the full space are random
+constexpr int WARM_COLS = 16;
+template <class T>
+__global__ void k_warm_block(const int* ni, const int* off, const int64_t* xoff, int ldx, const int* pvec,
+                             const int* active, const int* full, const float* Y, uint64_t seed, T* X) {
+  __shared__ double nrm[WARM_COLS];
+  const int i = blockIdx.x;
+  if (active && !active[i]) return;
+  const int n = ni[i], p = pvec[i], o = off[i];
+  const bool use = !full[i];
+  if (threadIdx.x < WARM_COLS) nrm[threadIdx.x] = 0.0;
+  __syncthreads();
+  if (use) {
+    // column norms: 16 threads per row
+    const int c = threadIdx.x & (WARM_COLS - 1);
+    double a = 0.0;
+    for (int l = threadIdx.x / WARM_COLS; l < n; l += blockDim.x / WARM_COLS) {
+      const double v = Y[(int64_t)(o + l) * WARM_COLS + c];
+      a += v * v;
+    }
+    atomicAdd(&nrm[c], a);
+  }
+  __syncthreads();
+  const double pert = 1e-3 / sqrt((double)n);
+  for (int e = threadIdx.x; e < n * p; e += blockDim.x) {
+    const int l = e / p, c = e % p;
+    const double u = hash_uniform(seed, (uint64_t)i, (uint64_t)l, (uint64_t)c);
+    double v = u;
+    if (use && c < WARM_COLS) {
+      const double s = nrm[c] > 0.0 ? 1.0 / sqrt(nrm[c]) : 0.0;
+      v = Y[(int64_t)(o + l) * WARM_COLS + c] * s + pert * u;
+    }
+    X[xoff[i] + (int64_t)l * ldx + c] = (T)v;
+  }
+}
+
 // columns of X orthogonal to k (kernel subdomains only)
 template <class T>
 __global__ void __launch_bounds__(EIG_THREADS) k_project_k(const int* ni, const int* off, const int64_t* xoff,
@@ -832,9 +870,17 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     A2LS_LAUNCH();
   };
 
-  // initial block: random, orthogonal to k, orthonormal
-  k_random_block<T><<<N, 256, 0, st>>>(h->d_ni, d_vo, P, 0, d_pv, d_active, h->opt.seed, 0, W);
-  A2LS_LAUNCH();
+  // initial block: random or the warm-start network's proposal, then orthogonal to k, orthonormal
+  if (h->opt.warm_start) {
+    float* Yw = dalloc<float>(h, (size_t)h->sum_n * WARM_COLS);
+    gnn_infer(h, h->opt.warm_start, Yw);
+    k_warm_block<T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, d_pv, d_active, d_full, Yw, h->opt.seed, W);
+    A2LS_LAUNCH();
+    dfree(h, Yw);
+  } else {
+    k_random_block<T><<<N, 256, 0, st>>>(h->d_ni, d_vo, P, 0, d_pv, d_active, h->opt.seed, 0, W);
+    A2LS_LAUNCH();
+  }
   orthonormalize_W_into_V0();
   A2LS_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * N * P * P, st));
 
@@ -958,7 +1004,13 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   dfree(h, H);
   dfree(h, Y);
   dfree(h, Rscr);
-  dfree(h, Z);
+  // keep Z (the eigenvectors behind the coarse space) as the warm-start network's training target
+  if (h->d_zev) dfree(h, h->d_zev);
+  if (h->d_zoff) dfree(h, h->d_zoff);
+  h->d_zev = Z;
+  h->d_zoff = d_zo;
+  h->zld = zld;
+  h->h_zcols = mcols;
 }
 
 // The local eigenproblems run in the precision of the local factors.  In FP32 the
