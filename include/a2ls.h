@@ -54,8 +54,10 @@ typedef enum {
  * (a2ls_options::precision), and of the factorisation of A~_ii and the local
  * eigensolves (a2ls_options::eig_precision).  The SpMV, the GMRES
  * orthogonalisation, the residual, the small Rayleigh-Ritz problems and the
- * coarse operator are always FP64. */
-enum { A2LS_FP64 = 0, A2LS_FP32 = 1 };
+ * coarse operator are always FP64.
+ * A2LS_FP32X2 (eigensolve only) is double-float arithmetic: each value is an unevaluated sum
+ * of two FP32 numbers (48-bit significand, FP32 exponent range), computed on the FP32 pipe. */
+enum { A2LS_FP64 = 0, A2LS_FP32 = 1, A2LS_FP32X2 = 2 };
 
 /* Preconditioner variants (Section 2).  DEFLATED_RAS is Eq. 2.4, the one the
  * paper uses in all experiments. */
@@ -109,8 +111,9 @@ typedef struct {
   void* stream;             /* cudaStream_t for all work; NULL = legacy default stream */
   int32_t timing;           /* 1: record CUDA events around the tracked kernels (A2LS_Q_KERNEL_TIMES) */
   int32_t eig_precision;    /* precision of the factorisation of A~_ii and of the local eigensolves:
-                               -1 (default) = FP64 always; A2LS_FP64; A2LS_FP32 (only for local splittings
-                               whose conditioning FP32 can resolve; high-contrast problems need FP64) */
+                               -1 (default) = FP64 when precision is FP64, else A2LS_FP32X2;
+                               A2LS_FP64; A2LS_FP32X2; A2LS_FP32 (only for local splittings whose
+                               conditioning FP32 can resolve; high-contrast problems need 48 bits) */
   int32_t graphs;           /* 1 (default): GMRES replays the apply as CUDA graphs captured on first use */
   const a2ls_gnn* warm_start; /* NULL (default): random start blocks for the local eigensolves; otherwise
                                  the network's proposal (a2ls_gnn_forward) starts each subdomain's block

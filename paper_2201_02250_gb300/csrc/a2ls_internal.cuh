@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/a2ls.h"
+#include "dfloat.cuh"
 
 namespace a2ls {
 

@@ -359,13 +359,19 @@ int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int
     h->fac_elems = (size_t)h->h_foff[h->N];
     const int v = o.variant;
     const bool need_coarse = nev > 0 && v != A2LS_ONE_LEVEL_RAS && v != A2LS_ONE_LEVEL_ASM;
-    const int ep = (o.eig_precision < 0) ? A2LS_FP64 : o.eig_precision;
-    if (ep != A2LS_FP64 && ep != A2LS_FP32) fail(A2LS_ERR_ARG, "unknown eig_precision %d", o.eig_precision);
+    const int ep = (o.eig_precision < 0) ? (o.precision == A2LS_FP64 ? A2LS_FP64 : A2LS_FP32X2) : o.eig_precision;
+    if (ep != A2LS_FP64 && ep != A2LS_FP32 && ep != A2LS_FP32X2)
+      fail(A2LS_ERR_ARG, "unknown eig_precision %d", o.eig_precision);
     h->opt.eig_precision = ep;
-    if (o.precision == A2LS_FP64 && ep == A2LS_FP64) factor_and_coarse<double, double>(h, need_coarse, h->times);
-    else if (o.precision == A2LS_FP64) factor_and_coarse<double, float>(h, need_coarse, h->times);
-    else if (ep == A2LS_FP64) factor_and_coarse<float, double>(h, need_coarse, h->times);
-    else factor_and_coarse<float, float>(h, need_coarse, h->times);
+    if (o.precision == A2LS_FP64) {
+      if (ep == A2LS_FP64) factor_and_coarse<double, double>(h, need_coarse, h->times);
+      else if (ep == A2LS_FP32) factor_and_coarse<double, float>(h, need_coarse, h->times);
+      else factor_and_coarse<double, dfloat>(h, need_coarse, h->times);
+    } else {
+      if (ep == A2LS_FP64) factor_and_coarse<float, double>(h, need_coarse, h->times);
+      else if (ep == A2LS_FP32) factor_and_coarse<float, float>(h, need_coarse, h->times);
+      else factor_and_coarse<float, dfloat>(h, need_coarse, h->times);
+    }
     // apply workspace
     h->d_q = dalloc<double>(h, h->n);
     h->d_t = dalloc<double>(h, h->n);

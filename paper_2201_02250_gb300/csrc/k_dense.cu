@@ -19,6 +19,7 @@ namespace a2ls {
 template <class T> struct AccOf;
 template <> struct AccOf<float> { using type = float; };
 template <> struct AccOf<double> { using type = double; };
+template <> struct AccOf<dfloat> { using type = dfloat; };
 
 // ---------------------------------------------------------------------------
 // CTA-wide 64x64 tile product: acc += A(0:M, 0:K) * B(0:K, 0:Nc), 256 threads,
@@ -64,7 +65,7 @@ __device__ __forceinline__ void cta_gemm(const T* __restrict__ A, int64_t lda, c
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        for (int v = 0; v < 4; ++v) mac(acc[u][v], a[u], b[v]);
     }
     __syncthreads();
   }
@@ -107,8 +108,8 @@ __device__ __forceinline__ void cta_gemm_n32(const T* __restrict__ A, int64_t ld
         for (int v = 0; v < 4; ++v) b[v] = sB[k * 33 + tx * 4 + v];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          acc[0][v] += a0 * b[v];
-          acc[1][v] += a1 * b[v];
+          mac(acc[0][v], a0, b[v]);
+          mac(acc[1][v], a1, b[v]);
         }
       }
     }
@@ -148,8 +149,8 @@ __device__ __forceinline__ void cta_gemm_n8(const T* __restrict__ A, int64_t lda
 #pragma unroll 8
       for (int k = 0; k < GK; ++k) {
         const Acc a = sA[k * 65 + ty];
-        acc[0] += a * sB[k * 9 + tx * 2];
-        acc[1] += a * sB[k * 9 + tx * 2 + 1];
+        mac(acc[0], a, sB[k * 9 + tx * 2]);
+        mac(acc[1], a, sB[k * 9 + tx * 2 + 1]);
       }
     }
     __syncthreads();
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(256) k_lu(int N, const int* ni, const int* ld,
   const int64_t L = ld[i];
   T* A = fac + foff[i];
   const double scale = dscale[i] > 0 ? dscale[i] : 1.0;
-  const double tiny = (sizeof(T) == 8 ? 1e-14 : 1e-12) * scale;
+  const double tiny = (Unit<T>::u < 1e-15 ? 1e-14 : 1e-12) * scale;
   const int tid = threadIdx.x;
   for (int k0 = 0; k0 < n; k0 += LU_NB) {
     const int kb = min(LU_NB, n - k0);
@@ -573,7 +574,7 @@ __global__ void __launch_bounds__(256) k_block_solve(const int* ni, const int* l
 #pragma unroll
       for (int v = 0; v < 2; ++v) {
         const int c = tx * 2 + v;
-        if (ty < tb && c < pc) Xi[(int64_t)(r0 + ty) * ldx + c] = (T)acc2[v];
+        if (ty < tb && c < pc) Xi[(int64_t)(r0 + ty) * ldx + c] = (T)finish(acc2[v]);
       }
       __syncthreads();
     }
@@ -600,6 +601,10 @@ template void autotune_local_solves<double>(a2ls_handle*, const double*, const d
 template void block_solve<float>(a2ls_handle*, const float*, float*, const int64_t*, int, int, const int*, int,
                                   const int*, int, int);
 template void block_solve<double>(a2ls_handle*, const double*, double*, const int64_t*, int, int, const int*, int,
+                                   const int*, int, int);
+template void lu_batched<dfloat>(a2ls_handle*, dfloat*, int, double*, double*);
+template void invert_diag_tiles<dfloat>(a2ls_handle*, dfloat*);
+template void block_solve<dfloat>(a2ls_handle*, const dfloat*, dfloat*, const int64_t*, int, int, const int*, int,
                                    const int*, int, int);
 
 }  // namespace a2ls

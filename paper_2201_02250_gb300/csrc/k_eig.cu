@@ -35,6 +35,11 @@ namespace a2ls {
 template <class T> struct EAcc;
 template <> struct EAcc<float> { using type = float; };
 template <> struct EAcc<double> { using type = double; };
+template <> struct EAcc<dfloat> { using type = dfloat; };
+// smallest Gram pivot kept finite: FP32 and double-float share FP32's exponent range
+template <class T> struct Tiny { static constexpr double v = 1e-300; };
+template <> struct Tiny<float> { static constexpr double v = 1e-30; };
+template <> struct Tiny<dfloat> { static constexpr double v = 1e-30; };
 
 constexpr int EIG_THREADS = 256;
 constexpr int EIG_MAXP = 96;   // column capacity of the Krylov basis
@@ -259,7 +264,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_project_k(const int* ni, const 
   for (int c = wid; c < p; c += EIG_THREADS / 32) {
     Acc d = 0;
     for (int l = lane; l < n; l += 32) d += (Acc)kvec[o + l] * (Acc)Xi[(int64_t)l * ldx + c];
-    for (int w = 16; w > 0; w >>= 1) d += __shfl_xor_sync(0xffffffffu, d, w);
+    for (int w = 16; w > 0; w >>= 1) d += warp_xor(d, w);
     if (lane == 0) dots[c] = (double)d;
   }
   __syncthreads();
@@ -402,7 +407,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
         if (e < nout) {
           const int a = e / p, c = e % p;
           Acc s = 0;
-          for (int r = 0; r < rows; ++r) s += sv[r * EIG_MAXP + a] * sw[r * EIG_MAXP + c];
+          for (int r = 0; r < rows; ++r) mac(s, sv[r * EIG_MAXP + a], sw[r * EIG_MAXP + c]);
           acc[u] += s;
         }
       }
@@ -418,7 +423,10 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
     }
     __syncthreads();
     if (full) return;  // Rayleigh quotient only
-    // W -= V G, staged by row chunks
+    // W -= V G, staged by row chunks; G converted once to the working arithmetic (in Ri's space)
+    Acc* Ga = reinterpret_cast<Acc*>(Ri);
+    for (int e = tid; e < nout; e += EIG_THREADS) Ga[e] = (Acc)G[e];
+    __syncthreads();
     for (int l0 = 0; l0 < n; l0 += RC) {
       const int rows = min(RC, n - l0);
       for (int e = tid; e < rows * jb; e += EIG_THREADS)
@@ -427,7 +435,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
       for (int e = tid; e < rows * p; e += EIG_THREADS) {
         const int r = e / p, c = e % p;
         Acc s = 0;
-        for (int a = 0; a < jb; ++a) s += sv[r * EIG_MAXP + a] * (Acc)G[a * p + c];
+        for (int a = 0; a < jb; ++a) mac(s, sv[r * EIG_MAXP + a], Ga[a * p + c]);
         TW* w = Wi + (int64_t)(l0 + r) * ldx + c;
         *w = (TW)((Acc)*w - s);
       }
@@ -453,7 +461,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
         if (e < p * p) {
           const int a = e / p, c = e % p;
           Acc s = 0;
-          for (int r = 0; r < rows; ++r) s += sw[r * EIG_MAXP + a] * sw[r * EIG_MAXP + c];
+          for (int r = 0; r < rows; ++r) mac(s, sw[r * EIG_MAXP + a], sw[r * EIG_MAXP + c]);
           acc[u] += s;
         }
       }
@@ -469,12 +477,12 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
       if (pass == 0) {
         double tr = 0.0;
         for (int a = 0; a < p; ++a) tr += G[a * p + a];
-        const double u = sizeof(Acc) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+        const double u = Unit<Acc>::u;
         const double shift = 11.0 * ((double)n * p + (double)p * (p + 1)) * u * tr;
         for (int a = 0; a < p; ++a) G[a * p + a] += shift;
       }
       int ok;
-      small_cholesky_inverse(G, p, Ri, ok, sizeof(Acc) == 4 ? 1e-30 : 1e-300);
+      small_cholesky_inverse(G, p, Ri, ok, Tiny<Acc>::v);
       rank_ok = ok;
       if (!ok && rank_flag) atomicAdd(rank_flag + i, 1);
       if (pass == 0) {
@@ -493,7 +501,10 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
       }
     }
     __syncthreads();
-    // W <- W inv(R)
+    // W <- W inv(R); inv(R) converted once to the working arithmetic (in G's space, free now)
+    Acc* Ra = reinterpret_cast<Acc*>(G);
+    for (int e = tid; e < p * p; e += EIG_THREADS) Ra[e] = (Acc)Ri[e];
+    __syncthreads();
     for (int l0 = 0; l0 < n; l0 += RC) {
       const int rows = min(RC, n - l0);
       for (int e = tid; e < rows * p; e += EIG_THREADS)
@@ -502,8 +513,8 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
       for (int e = tid; e < rows * p; e += EIG_THREADS) {
         const int r = e / p, c = e % p;
         Acc s = 0;
-        for (int a = 0; a <= c; ++a) s += sw[r * EIG_MAXP + a] * (Acc)Ri[a * p + c];
-        Wi[(int64_t)(l0 + r) * ldx + c] = (TW)s;
+        for (int a = 0; a <= c; ++a) mac(s, sw[r * EIG_MAXP + a], Ra[a * p + c]);
+        Wi[(int64_t)(l0 + r) * ldx + c] = (TW)finish(s);
       }
       __syncthreads();
     }
@@ -696,8 +707,8 @@ __global__ void __launch_bounds__(EIG_THREADS) k_vy(const int* ni, const int64_t
     for (int e = threadIdx.x; e < rows * q; e += EIG_THREADS) {
       const int r = e / q, c = e % q;
       Acc s = 0;
-      for (int a = 0; a < m; ++a) s += sv[r * EIG_MAXP + a] * sy[a * EIG_MAXP + c];
-      Xi[(int64_t)(l0 + r) * ldx + c] = (TX)s;
+      for (int a = 0; a < m; ++a) mac(s, sv[r * EIG_MAXP + a], sy[a * EIG_MAXP + c]);
+      Xi[(int64_t)(l0 + r) * ldx + c] = (TX)finish(s);
     }
   }
 }
@@ -727,7 +738,6 @@ template <class T, class TV>
 static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const double* dscale) {
   cudaStream_t st = h->st;
   const int N = h->N;
-  const bool fp64 = sizeof(T) == 8;
   const double tol = h->opt.eig_tol > 0 ? h->opt.eig_tol : (h->opt.precision == A2LS_FP64 ? 1e-10 : 1e-4);
   const int nev = h->nev;
 
@@ -748,7 +758,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   k_unit_last<T><<<N, 32, 0, st>>>(h->d_ni, d_off1, dscale, X1);
   A2LS_LAUNCH();
   block_solve<T>(h, fac, X1, d_off1, 0, 1, d_ones, 1, nullptr, 0, 1);  // k' = sigma inv(U') e_n
-  const double eps_work = fp64 ? 2.220446049250313e-16 : 1.1920928955078125e-07;
+  const double eps_work = 2.0 * Unit<T>::u;
   k_kernel_test<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, h->d_ld, h->d_foff, fac, last_pivot, dscale,
                                                h->d_lrow, h->d_lcol, h->d_lval, h->d_lump, h->d_D, d_off1, X1,
                                                eps_work, kvec, d_kd, d_kpart, h->d_status);
@@ -1022,10 +1032,12 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
 // The Krylov basis has the precision of the solves with A~_ii.  (An FP32 basis with FP64 solves
 // produced non-finite Rayleigh-Ritz matrices on the high-contrast problem and is not used.)
 void eigensolve(a2ls_handle* h, void* fac_tilde, const double* last_pivot, const double* diag_scale) {
-  if (h->opt.eig_precision != A2LS_FP32)
-    eigensolve_t<double, double>(h, static_cast<double*>(fac_tilde), last_pivot, diag_scale);
-  else
+  if (h->opt.eig_precision == A2LS_FP32)
     eigensolve_t<float, float>(h, static_cast<float*>(fac_tilde), last_pivot, diag_scale);
+  else if (h->opt.eig_precision == A2LS_FP32X2)
+    eigensolve_t<dfloat, dfloat>(h, static_cast<dfloat*>(fac_tilde), last_pivot, diag_scale);
+  else
+    eigensolve_t<double, double>(h, static_cast<double*>(fac_tilde), last_pivot, diag_scale);
 }
 
 }  // namespace a2ls

@@ -580,10 +580,16 @@ void extract_local(a2ls_handle* h, void* dense_A, void* dense_At, double* dense_
   A2LS_CUDA(cudaMemsetAsync(dense_A, 0, h->fac_elems * ea, st));
   if (dense_At) A2LS_CUDA(cudaMemsetAsync(dense_At, 0, h->fac_elems * et, st));
   const int blocks = std::min(152 * 16, ceil_div((int64_t)h->sum_n * 32, 256));
-  if (ea == 8 && et == 8) launch_extract<double, double>(h, dense_A, dense_At, dense_scale, blocks);
-  else if (ea == 8) launch_extract<double, float>(h, dense_A, dense_At, dense_scale, blocks);
-  else if (et == 8) launch_extract<float, double>(h, dense_A, dense_At, dense_scale, blocks);
-  else launch_extract<float, float>(h, dense_A, dense_At, dense_scale, blocks);
+  const int ep = h->opt.eig_precision;
+  if (ea == 8) {
+    if (ep == A2LS_FP32) launch_extract<double, float>(h, dense_A, dense_At, dense_scale, blocks);
+    else if (ep == A2LS_FP32X2) launch_extract<double, dfloat>(h, dense_A, dense_At, dense_scale, blocks);
+    else launch_extract<double, double>(h, dense_A, dense_At, dense_scale, blocks);
+  } else {
+    if (ep == A2LS_FP32) launch_extract<float, float>(h, dense_A, dense_At, dense_scale, blocks);
+    else if (ep == A2LS_FP32X2) launch_extract<float, dfloat>(h, dense_A, dense_At, dense_scale, blocks);
+    else launch_extract<float, double>(h, dense_A, dense_At, dense_scale, blocks);
+  }
 }
 
 }  // namespace a2ls
