@@ -171,7 +171,8 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, int n, cudaStream_t st,
 
 // k_dense.cu
 template <class T> void lu_batched(a2ls_handle* h, T* fac, int allow_last_zero, double* last_pivot,
-                                   double* diag_scale);
+                                   double* diag_scale, int phase = -1);
+template <class TS, class TD> void schur_copy(a2ls_handle* h, const TS* src, TD* dst, const double* last_pivot);
 template <class T> void invert_diag_tiles(a2ls_handle* h, T* fac);
 // y_loc / z output of the RAS/ASM local solves; see k_dense.cu for the modes
 template <class T> void local_solves(a2ls_handle* h, const T* fac, const double* t, const double* q,

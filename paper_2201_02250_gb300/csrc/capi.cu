@@ -252,21 +252,41 @@ static void factor_and_coarse(a2ls_handle* h, bool need_coarse, double* times) {
   extract_local(h, fa, ft, dscale);
   sync_and_check(h, "local matrix extraction");
   times[Phase::SETUP_EXTRACT] = tm.stop();
-  double lu_flops = 0.0;
-  for (int i = 0; i < N; ++i) lu_flops += 2.0 / 3.0 * (double)h->h_n[i] * h->h_n[i] * h->h_n[i];
-  {
+  double lu_flops = 0.0, gamma_flops = 0.0;
+  for (int i = 0; i < N; ++i) {
+    const double ni = h->h_n[i], ng = h->h_n[i] - h->h_nI[i];
+    lu_flops += 2.0 / 3.0 * ni * ni * ni;
+    gamma_flops += 2.0 / 3.0 * ng * ng * ng;
+  }
+  // A_ii and A~_ii share their interior block, so one factorisation of the splitting serves both
+  // when it runs in at least the precision of the A_ii factors; only the Schur complement on the
+  // overlap rows is factored twice.
+  const bool share = need_coarse && Unit<TT>::u <= Unit<T>::u;
+  if (!share) {
     KTime kt(h, KT_LU_LOCAL, lu_flops);
     lu_batched<T>(h, fa, 0, nullptr, dscale);
     invert_diag_tiles<T>(h, fa);
   }
-  sync_and_check(h, "local LU factorisation");
-  h->d_fac = fa;
   if (need_coarse) {
-    KTime kt(h, KT_LU_SPLIT, lu_flops);
-    lu_batched<TT>(h, ft, 1, lastp, dscale);
-    invert_diag_tiles<TT>(h, ft);
-    sync_and_check(h, "LU factorisation of the local splittings");
+    {
+      KTime kt(h, KT_LU_SPLIT, lu_flops);
+      if (share) {
+        lu_batched<TT>(h, ft, 1, lastp, dscale, 0);
+        schur_copy<TT, T>(h, ft, fa, lastp);
+        lu_batched<TT>(h, ft, 1, lastp, dscale, 1);
+      } else {
+        lu_batched<TT>(h, ft, 1, lastp, dscale);
+      }
+      invert_diag_tiles<TT>(h, ft);
+    }
+    if (share) {
+      KTime kt(h, KT_LU_LOCAL, gamma_flops);
+      lu_batched<T>(h, fa, 0, nullptr, dscale, 1);
+      invert_diag_tiles<T>(h, fa);
+    }
   }
+  sync_and_check(h, "LU factorisation of the local matrices and splittings");
+  h->d_fac = fa;
   times[Phase::SETUP_LU] = tm.stop();
   if (need_coarse) {
     eigensolve(h, ft, lastp, dscale);  // ends with the coarse operator

@@ -162,10 +162,13 @@ __device__ __forceinline__ void cta_gemm_n8(const T* __restrict__ A, int64_t lda
 // ---------------------------------------------------------------------------
 constexpr int LU_NB = 32;
 
+// phase: -1 all columns; 0 the interior columns [0, n_I) (the trailing Schur complement on the
+// overlap rows is left in place); 1 the remaining columns [n_I, n).
 template <class T>
 __global__ void __launch_bounds__(256) k_lu(int N, const int* ni, const int* ld, const int64_t* foff,
                                             T* fac, int allow_last_zero, double* last_pivot,
-                                            const double* dscale, int* st, const int* sched) {
+                                            const double* dscale, int* st, const int* sched, const int* nI,
+                                            int phase) {
   using Acc = typename AccOf<T>::type;
   __shared__ Acc sA[GK * 65], sB[GK * 65];
   const int i = sched ? sched[blockIdx.x] : blockIdx.x;  // largest subdomains first
@@ -175,8 +178,10 @@ __global__ void __launch_bounds__(256) k_lu(int N, const int* ni, const int* ld,
   const double scale = dscale[i] > 0 ? dscale[i] : 1.0;
   const double tiny = (Unit<T>::u < 1e-15 ? 1e-14 : 1e-12) * scale;
   const int tid = threadIdx.x;
-  for (int k0 = 0; k0 < n; k0 += LU_NB) {
-    const int kb = min(LU_NB, n - k0);
+  const int kbeg = (phase == 1) ? nI[i] : 0;
+  const int kend = (phase == 0) ? nI[i] : n;
+  for (int k0 = kbeg; k0 < kend; k0 += LU_NB) {
+    const int kb = min(LU_NB, kend - k0);
     // 1. unblocked factorisation of the panel A(k0:n, k0:k0+kb)
     for (int c = k0; c < k0 + kb; ++c) {
       __syncthreads();
@@ -242,11 +247,48 @@ __global__ void __launch_bounds__(256) k_lu(int N, const int* ni, const int* ld,
 }
 
 template <class T>
-void lu_batched(a2ls_handle* h, T* fac, int allow_last_zero, double* last_pivot, double* diag_scale) {
+void lu_batched(a2ls_handle* h, T* fac, int allow_last_zero, double* last_pivot, double* diag_scale, int phase) {
   k_lu<T><<<h->N, 256, 0, h->st>>>(h->N, h->d_ni, h->d_ld, h->d_foff, fac, allow_last_zero, last_pivot,
-                                   diag_scale, h->d_status, h->d_sched);
+                                   diag_scale, h->d_status, h->d_sched, h->d_nI, phase);
   A2LS_LAUNCH();
 }
+
+// A_ii from the splitting's partial factorisation.  A~_ii differs from A_ii only on the diagonal of the
+// overlap rows (Definition 3.1: A~ = A_ii - diag(s_i) there), so after the interior columns are
+// eliminated both share every factor entry and their Schur complements on the overlap differ by
+// diag(s_i): dst = src + diag(s_i) on the overlap block, converted to the precision of the A_ii
+// factors.  When the subdomain has no overlap rows the splitting's replaced last pivot is restored.
+template <class TS, class TD>
+__global__ void k_schur_copy(const int* ni, const int* nI, const int* ld, const int64_t* foff, const int* off,
+                             const TS* __restrict__ src, TD* __restrict__ dst, const double* lump,
+                             const double* last_pivot) {
+  const int i = blockIdx.x;
+  const int n = ni[i], n_I = nI[i];
+  const int64_t L = ld[i];
+  const TS* S = src + foff[i];
+  TD* D = dst + foff[i];
+  for (int r = blockIdx.y; r < n; r += gridDim.y)
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      double v = (double)S[(int64_t)r * L + c];
+      if (r == c && r >= n_I) v += lump[off[i] + r];
+      if (r == c && r == n - 1 && n_I == n && last_pivot) v = last_pivot[i];
+      D[(int64_t)r * L + c] = (TD)v;
+    }
+}
+
+template <class TS, class TD>
+void schur_copy(a2ls_handle* h, const TS* src, TD* dst, const double* last_pivot) {
+  dim3 grid(h->N, 32);
+  k_schur_copy<TS, TD><<<grid, 256, 0, h->st>>>(h->d_ni, h->d_nI, h->d_ld, h->d_foff, h->d_off, src, dst,
+                                                h->d_lump, last_pivot);
+  A2LS_LAUNCH();
+}
+template void schur_copy<double, double>(a2ls_handle*, const double*, double*, const double*);
+template void schur_copy<double, float>(a2ls_handle*, const double*, float*, const double*);
+template void schur_copy<float, double>(a2ls_handle*, const float*, double*, const double*);
+template void schur_copy<float, float>(a2ls_handle*, const float*, float*, const double*);
+template void schur_copy<dfloat, double>(a2ls_handle*, const dfloat*, double*, const double*);
+template void schur_copy<dfloat, float>(a2ls_handle*, const dfloat*, float*, const double*);
 
 // ---------------------------------------------------------------------------
 // inversion of the diagonal tiles (in place): inv(L_bb) strictly lower, inv(U_bb) upper
@@ -590,8 +632,8 @@ void block_solve(a2ls_handle* h, const T* fac, T* X, const int64_t* xoff, int co
   A2LS_LAUNCH();
 }
 
-template void lu_batched<float>(a2ls_handle*, float*, int, double*, double*);
-template void lu_batched<double>(a2ls_handle*, double*, int, double*, double*);
+template void lu_batched<float>(a2ls_handle*, float*, int, double*, double*, int);
+template void lu_batched<double>(a2ls_handle*, double*, int, double*, double*, int);
 template void invert_diag_tiles<float>(a2ls_handle*, float*);
 template void invert_diag_tiles<double>(a2ls_handle*, double*);
 template void local_solves<float>(a2ls_handle*, const float*, const double*, const double*, double*, int);
@@ -602,7 +644,7 @@ template void block_solve<float>(a2ls_handle*, const float*, float*, const int64
                                   const int*, int, int);
 template void block_solve<double>(a2ls_handle*, const double*, double*, const int64_t*, int, int, const int*, int,
                                    const int*, int, int);
-template void lu_batched<dfloat>(a2ls_handle*, dfloat*, int, double*, double*);
+template void lu_batched<dfloat>(a2ls_handle*, dfloat*, int, double*, double*, int);
 template void invert_diag_tiles<dfloat>(a2ls_handle*, dfloat*);
 template void block_solve<dfloat>(a2ls_handle*, const dfloat*, dfloat*, const int64_t*, int, int, const int*, int,
                                    const int*, int, int);
@@ -615,9 +657,11 @@ namespace a2ls {
 // One dense FP64 matrix (the coarse operator A_00): block-inverted LU without
 // pivoting, spread over many CTAs, then the explicit inverse.
 // ---------------------------------------------------------------------------
-// factor the 64x64 diagonal block at (k0, k0) and invert its triangles in place
-__global__ void k_e_diag(double* A, int n, int64_t ld, int k0, double scale, int* st) {
-  __shared__ double t[TB][TB + 1];
+// factor the 64x64 diagonal block at (k0, k0) and invert its triangles in place (256 threads:
+// the LU column by column, then threads 0-63 form the columns of inv(L) and threads 64-127 those of
+// inv(U), each in shared memory)
+__global__ void __launch_bounds__(256) k_e_diag(double* A, int n, int64_t ld, int k0, double scale, int* st) {
+  __shared__ double t[TB][TB + 1], s[TB][TB + 1];
   const int tb = min(TB, n - k0);
   double* D = A + (int64_t)k0 * ld + k0;
   for (int e = threadIdx.x; e < tb * tb; e += blockDim.x) t[e / tb][e % tb] = D[(e / tb) * ld + e % tb];
@@ -627,81 +671,104 @@ __global__ void k_e_diag(double* A, int n, int64_t ld, int k0, double scale, int
     if (fabs(piv) <= 1e-14 * scale) {
       if (threadIdx.x == 0) raise_status(st, A2LS_ERR_SINGULAR, -1, k0 + c);
       piv = scale;
-      __syncthreads();
-      if (threadIdx.x == 0) t[c][c] = piv;
     }
     __syncthreads();
+    if (threadIdx.x == 0) t[c][c] = piv;
     for (int r = c + 1 + threadIdx.x; r < tb; r += blockDim.x) t[r][c] /= piv;
     __syncthreads();
-    for (int e = threadIdx.x; e < (tb - c - 1) * (tb - c - 1); e += blockDim.x) {
-      const int r = c + 1 + e / (tb - c - 1), cc = c + 1 + e % (tb - c - 1);
+    const int w = tb - c - 1;
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+      const int r = c + 1 + e / w, cc = c + 1 + e % w;
       t[r][cc] -= t[r][c] * t[c][cc];
     }
     __syncthreads();
   }
-  const int c = threadIdx.x;
-  if (c < tb) {
-    double col[TB];
-    tile_inverse_column(t, tb, c, col);
-    for (int r = 0; r < tb; ++r) D[r * ld + c] = col[r];
+  const int c = threadIdx.x & (TB - 1);
+  if (threadIdx.x < TB && c < tb) {
+    // inv(L) (unit lower), column c below the diagonal: x_r = -(L[r][c] + sum_{q=c+1}^{r-1} L[r][q] x_q)
+    for (int r = c + 1; r < tb; ++r) {
+      double v = t[r][c];
+      for (int q = c + 1; q < r; ++q) v += t[r][q] * s[q][c];
+      s[r][c] = -v;
+    }
+  } else if (threadIdx.x >= TB && threadIdx.x < 2 * TB && c < tb) {
+    // inv(U), column c on and above the diagonal: x_c = 1/U_cc, x_r = -(sum_{q=r+1}^{c} U[r][q] x_q) / U_rr
+    s[c][c] = 1.0 / t[c][c];
+    for (int r = c - 1; r >= 0; --r) {
+      double v = 0.0;
+      for (int q = r + 1; q <= c; ++q) v += t[r][q] * s[q][c];
+      s[r][c] = -v / t[r][r];
+    }
   }
+  __syncthreads();
+  for (int e = threadIdx.x; e < tb * tb; e += blockDim.x) D[(e / tb) * ld + e % tb] = s[e / tb][e % tb];
 }
 
-// L21 = A21 inv(U11) (blockIdx.y == 0) and U12 = inv(L11) A12 (blockIdx.y == 1), in place;
-// the grid covers the band only (entries farther than the bandwidth from the diagonal are zero)
-__global__ void __launch_bounds__(256) k_e_panels(double* A, int n, int64_t ld, int k0) {
-  __shared__ double sA[GK * 65], sB[GK * 65];
+// One step of the coarse LU outside the diagonal block, in pieces small enough to spread over the
+// SMs (the FP64 work of a 64 x 64 x 64 tile product takes one SM about 70 us):
+//   MODE 0: L21 = A21 inv(U11), a 16-row piece per CTA (rows of A21 are independent);
+//   MODE 1: U12 = inv(L11) A12, a 16-column piece per CTA (columns of A12 are independent);
+//   MODE 2: A22 -= L21 U12, a 16 x 64 piece per CTA.
+// The operands of a piece are staged in shared memory before it is overwritten.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_e_update(double* A, int n, int64_t ld, int k0, int span) {
+  constexpr int R = (MODE == 1) ? TB : 16;
+  constexpr int C = (MODE == 1) ? 16 : TB;
+  __shared__ double sa[R][TB + 1], sb[TB][C + 1];
   const int tb = min(TB, n - k0);
-  const int start = k0 + tb + blockIdx.x * 64;
-  if (start >= n) return;
-  const int w = min(64, n - start);
-  double acc[4][4] = {};
+  const int first = k0 + tb;
+  int r0, c0;
+  if (MODE == 0) { r0 = first + blockIdx.x * 16; c0 = k0; }
+  else if (MODE == 1) { r0 = k0; c0 = first + blockIdx.x * 16; }
+  else { r0 = first + blockIdx.y * 16; c0 = first + blockIdx.x * TB; }
+  const int end = min(n, first + span);
+  if (r0 >= (MODE == 1 ? n : end) || c0 >= (MODE == 0 ? n : end)) return;
+  const int rows = (MODE == 1) ? tb : min(R, end - r0);
+  const int cols = (MODE == 0) ? tb : min(C, end - c0);
   const double* Dg = A + (int64_t)k0 * ld + k0;
-  if (blockIdx.y == 0) {
-    cta_gemm<double, double>(A + (int64_t)start * ld + k0, ld, Dg, ld, w, tb, tb, 0, acc, sA, sB, 2);
-  } else {
-    cta_gemm<double, double>(Dg, ld, A + (int64_t)k0 * ld + start, ld, tb, w, tb, 1, acc, sA, sB);
+  // A operand: MODE 0 the rows of A21, MODE 1 unit-lower inv(L11), MODE 2 the rows of L21
+  for (int e = threadIdx.x; e < R * TB; e += blockDim.x) {
+    const int r = e / TB, q = e % TB;
+    double v = 0.0;
+    if (r < rows && q < tb) {
+      if (MODE == 1) v = (q < r) ? Dg[(int64_t)r * ld + q] : (q == r ? 1.0 : 0.0);
+      else v = A[(int64_t)(r0 + r) * ld + k0 + q];
+    }
+    sa[r][q] = v;
   }
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int r = ty * 4 + u, c = tx * 4 + v;
-      if (blockIdx.y == 0) {
-        if (r < w && c < tb) A[(int64_t)(start + r) * ld + k0 + c] = acc[u][v];
-      } else {
-        if (r < tb && c < w) A[(int64_t)(k0 + r) * ld + start + c] = acc[u][v];
-      }
+  // B operand: MODE 0 upper inv(U11), MODE 1 the columns of A12, MODE 2 the columns of U12
+  for (int e = threadIdx.x; e < TB * C; e += blockDim.x) {
+    const int q = e / C, c = e % C;
+    double v = 0.0;
+    if (q < tb && c < cols) {
+      if (MODE == 0) v = (c >= q) ? Dg[(int64_t)q * ld + c] : 0.0;
+      else v = A[(int64_t)(k0 + q) * ld + c0 + c];
     }
+    sb[q][c] = v;
+  }
+  __syncthreads();
+  // 256 threads x 4 outputs
+  for (int o = threadIdx.x; o < R * C; o += blockDim.x) {
+    const int r = o / C, c = o % C;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int q = 0; q < TB; ++q) acc += sa[r][q] * sb[q][c];
+    if (r < rows && c < cols) {
+      double* dst = (MODE == 1) ? A + (int64_t)(k0 + r) * ld + c0 + c : A + (int64_t)(r0 + r) * ld + c0 + c;
+      if (MODE == 2) *dst -= acc;
+      else *dst = acc;
+    }
+  }
 }
 
-// A22 -= L21 U12
-__global__ void __launch_bounds__(256) k_e_trailing(double* A, int n, int64_t ld, int k0) {
-  __shared__ double sA[GK * 65], sB[GK * 65];
-  const int tb = min(TB, n - k0);
-  const int r0 = k0 + tb + blockIdx.y * 64, c0 = k0 + tb + blockIdx.x * 64;
-  if (r0 >= n || c0 >= n) return;
-  double acc[4][4] = {};
-  cta_gemm<double, double>(A + (int64_t)r0 * ld + k0, ld, A + (int64_t)k0 * ld + c0, ld, min(64, n - r0),
-                           min(64, n - c0), tb, 0, acc, sA, sB);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-#pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int r = r0 + ty * 4 + u, c = c0 + tx * 4 + v;
-      if (r < n && c < n) A[(int64_t)r * ld + c] -= acc[u][v];
-    }
-}
-
-// X = inv(U) inv(L) I, one 64-column slab per CTA (F holds the block-inverted LU)
+// X = inv(U) inv(L) I, one 32-column slab per CTA (F holds the block-inverted LU)
+constexpr int EINV_W = 32;
 __global__ void __launch_bounds__(256) k_e_inverse(const double* F, int n, int64_t ld, double* X, int64_t ldx,
                                                    int band) {
-  __shared__ double sA[GK * 65], sB[GK * 65];
-  const int c0 = blockIdx.x * 64;
-  const int pc = min(64, n - c0);
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  __shared__ double sA[GK * 65], sB[GK * 33];
+  const int c0 = blockIdx.x * EINV_W;
+  const int pc = min(EINV_W, n - c0);
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
   double* Xs = X + c0;
   for (int e = tid; e < n * pc; e += 256) {
     const int r = e / pc, c = e % pc;
@@ -715,35 +782,35 @@ __global__ void __launch_bounds__(256) k_e_inverse(const double* F, int n, int64
       const int b = pass == 0 ? bb : nb - 1 - bb;
       if (pass == 0 && b < bstart) continue;
       const int r0 = b * TB, tb = min(TB, n - r0);
-      double acc[4][4] = {};
+      double acc[2][4] = {};
       if (pass == 0) {
         const int k0 = max(bstart * TB, r0 - band);  // L(r, c) = 0 for c < r - band
         if (r0 > k0)
-          cta_gemm<double, double>(F + (int64_t)r0 * ld + k0, ld, Xs + (int64_t)k0 * ldx, ldx, tb, pc, r0 - k0, 0,
-                                   acc, sA, sB);
+          cta_gemm_n32<double, double>(F + (int64_t)r0 * ld + k0, ld, Xs + (int64_t)k0 * ldx, ldx, tb, pc, r0 - k0,
+                                       0, acc, sA, sB);
       } else {
         const int e0 = r0 + tb;
         const int e1 = min(n, r0 + tb + band);       // U(r, c) = 0 for c > r + band
         if (e0 < e1)
-          cta_gemm<double, double>(F + (int64_t)r0 * ld + e0, ld, Xs + (int64_t)e0 * ldx, ldx, tb, pc, e1 - e0, 0,
-                                   acc, sA, sB);
+          cta_gemm_n32<double, double>(F + (int64_t)r0 * ld + e0, ld, Xs + (int64_t)e0 * ldx, ldx, tb, pc, e1 - e0,
+                                       0, acc, sA, sB);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 2; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const int r = ty * 4 + u, c = tx * 4 + v;
+          const int r = ty * 2 + u, c = tx * 4 + v;
           if (r < tb && c < pc) Xs[(int64_t)(r0 + r) * ldx + c] -= acc[u][v];
         }
       __syncthreads();
-      double acc2[4][4] = {};
-      cta_gemm<double, double>(F + (int64_t)r0 * ld + r0, ld, Xs + (int64_t)r0 * ldx, ldx, tb, pc, tb,
-                               pass == 0 ? 1 : 2, acc2, sA, sB);
+      double acc2[2][4] = {};
+      cta_gemm_n32<double, double>(F + (int64_t)r0 * ld + r0, ld, Xs + (int64_t)r0 * ldx, ldx, tb, pc, tb,
+                                   pass == 0 ? 1 : 2, acc2, sA, sB);
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 2; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const int r = ty * 4 + u, c = tx * 4 + v;
+          const int r = ty * 2 + u, c = tx * 4 + v;
           if (r < tb && c < pc) Xs[(int64_t)(r0 + r) * ldx + c] = acc2[u][v];
         }
       __syncthreads();
@@ -755,20 +822,25 @@ void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv,
   cudaStream_t st = h->st;
   const int64_t ld = n;
   if (band <= 0 || band >= n) band = n;
+  {
   KTime kt(h, KT_COARSE_LU, 2.0 / 3.0 * (double)n * n * n);
   for (int k0 = 0; k0 < n; k0 += TB) {
-    k_e_diag<<<1, TB, 0, st>>>(E, n, ld, k0, scale, h->d_status);
+    k_e_diag<<<1, 256, 0, st>>>(E, n, ld, k0, scale, h->d_status);
     A2LS_LAUNCH();
+    // entries farther than the bandwidth from the diagonal are zero and stay zero
     const int rest = min(n - k0 - min(TB, n - k0), band + TB);
     if (rest <= 0) break;
-    const int chunks = ceil_div(rest, 64);
-    k_e_panels<<<dim3(chunks, 2), 256, 0, st>>>(E, n, ld, k0);
+    const int p16 = ceil_div(rest, 16);
+    k_e_update<0><<<p16, 256, 0, st>>>(E, n, ld, k0, rest);
     A2LS_LAUNCH();
-    k_e_trailing<<<dim3(chunks, chunks), 256, 0, st>>>(E, n, ld, k0);
+    k_e_update<1><<<p16, 256, 0, st>>>(E, n, ld, k0, rest);
+    A2LS_LAUNCH();
+    k_e_update<2><<<dim3(ceil_div(rest, TB), p16), 256, 0, st>>>(E, n, ld, k0, rest);
     A2LS_LAUNCH();
   }
+  }
   KTime kt2(h, KT_COARSE_INV, 4.0 / 3.0 * (double)n * n * n);
-  k_e_inverse<<<ceil_div(n, 64), 256, 0, st>>>(E, n, ld, Einv, ld, band);
+  k_e_inverse<<<ceil_div(n, EINV_W), 256, 0, st>>>(E, n, ld, Einv, ld, band);
   A2LS_LAUNCH();
 }
 

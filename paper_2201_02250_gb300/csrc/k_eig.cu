@@ -362,11 +362,53 @@ __device__ void small_cholesky_inverse(double* G, int p, double* Ri, int& rank_o
   }
 }
 
+constexpr int ORTH_THREADS = 512;
+constexpr int ORC = 32;                  // rows staged per chunk in k_orth
+constexpr int ORTH_NB = (EIG_MAXP / 2) * (EIG_MAXP / 2) / ORTH_THREADS + 1;  // 2x2 blocks per thread
+
+// acc[k] += X[0:rows, a0:a0+2]^T Y[0:rows, c0:c0+2] for the 2x2 output blocks b = tid + k * ORTH_THREADS,
+// (a0, c0) = 2 * (b / nbc, b % nbc); X and Y are staged row chunks (stride EIG_MAXP) whose padding
+// column (index jb or p when odd) holds zeros.
+template <class Acc>
+__device__ __forceinline__ void gram_chunk(const Acc* X, const Acc* Y, int rows, int nbr, int nbc,
+                                           Acc (&acc)[ORTH_NB][4]) {
+#pragma unroll
+  for (int k = 0; k < ORTH_NB; ++k) {
+    const int b = threadIdx.x + k * ORTH_THREADS;
+    if (b < nbr * nbc) {
+      const int a0 = 2 * (b / nbc), c0 = 2 * (b % nbc);
+      Acc s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      for (int r = 0; r < rows; ++r) {
+        const Acc x0 = X[r * EIG_MAXP + a0], x1 = X[r * EIG_MAXP + a0 + 1];
+        const Acc y0 = Y[r * EIG_MAXP + c0], y1 = Y[r * EIG_MAXP + c0 + 1];
+        mac(s0, x0, y0);
+        mac(s1, x0, y1);
+        mac(s2, x1, y0);
+        mac(s3, x1, y1);
+      }
+      acc[k][0] += finish(s0);
+      acc[k][1] += finish(s1);
+      acc[k][2] += finish(s2);
+      acc[k][3] += finish(s3);
+    }
+  }
+}
+
+// stage rows [l0, l0 + rows) of M (cols 0:w) into S (stride EIG_MAXP), zero padding column w
+template <class Acc, class TM>
+__device__ __forceinline__ void stage_rows(Acc* S, const TM* M, int64_t ldx, int l0, int rows, int w) {
+  const int wp = w + (w & 1);
+  for (int e = threadIdx.x; e < rows * wp; e += ORTH_THREADS) {
+    const int r = e / wp, c = e % wp;
+    S[r * EIG_MAXP + c] = c < w ? (Acc)M[(int64_t)(l0 + r) * ldx + c] : (Acc)0;
+  }
+}
+
 template <class T, class TW>
-__global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64_t* xoff, int ldx,
-                                                       const int* pvec, const int* active, int jb_blocks,
-                                                       int bcols, T* V, TW* W, double* H, int hr, int hc,
-                                                       int vout, const int* fullv, int* rank_flag) {
+__global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int64_t* xoff, int ldx,
+                                                        const int* pvec, const int* active, int jb_blocks,
+                                                        int bcols, T* V, TW* W, double* H, int hr, int hc,
+                                                        int vout, const int* fullv, int* rank_flag) {
   using Acc = typename EAcc<T>::type;
   extern __shared__ double sm[];
   const int i = blockIdx.x;
@@ -382,57 +424,52 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
   double* G = sm;                               // EIG_MAXP * EIG_MAXP (Gram, then R in place)
   double* Ri = G + EIG_MAXP * EIG_MAXP;         // EIG_MAXP * EIG_MAXP
   double* trow = Ri + EIG_MAXP * EIG_MAXP;      // EIG_MAXP
-  Acc* sv = reinterpret_cast<Acc*>(trow + EIG_MAXP);           // RC * EIG_MAXP
-  Acc* sw = sv + RC * EIG_MAXP;                                // RC * EIG_MAXP
-  __shared__ int rank_ok;
+  Acc* sv = reinterpret_cast<Acc*>(trow + EIG_MAXP);           // ORC * EIG_MAXP
+  Acc* sw = sv + ORC * EIG_MAXP;                               // ORC * EIG_MAXP
   const int tid = threadIdx.x;
   const int npass = jb > 0 ? 2 : 0;
-  for (int e = tid; e < jb * p; e += EIG_THREADS) Hi[(e / p) * EIG_MAXP + hc + e % p] = 0.0;
+  const int nbj = (jb + 1) / 2, nbp = (p + 1) / 2;
+  for (int e = tid; e < jb * p; e += ORTH_THREADS) Hi[(e / p) * EIG_MAXP + hc + e % p] = 0.0;
   for (int pass = 0; pass < npass; ++pass) {
     // G = V[:, 0:jb]^T W[:, 0:p]
-    Acc acc[(EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS];
-    const int nout = jb * p;
+    Acc acc[ORTH_NB][4];
 #pragma unroll
-    for (int u = 0; u < (EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS; ++u) acc[u] = 0;
-    for (int l0 = 0; l0 < n; l0 += RC) {
-      const int rows = min(RC, n - l0);
-      for (int e = tid; e < rows * jb; e += EIG_THREADS)
-        sv[(e / jb) * EIG_MAXP + e % jb] = (Acc)Vi[(int64_t)(l0 + e / jb) * ldx + e % jb];
-      for (int e = tid; e < rows * p; e += EIG_THREADS)
-        sw[(e / p) * EIG_MAXP + e % p] = (Acc)Wi[(int64_t)(l0 + e / p) * ldx + e % p];
+    for (int k = 0; k < ORTH_NB; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0;
+    for (int l0 = 0; l0 < n; l0 += ORC) {
+      const int rows = min(ORC, n - l0);
+      stage_rows(sv, Vi, ldx, l0, rows, jb);
+      stage_rows(sw, Wi, ldx, l0, rows, p);
       __syncthreads();
-#pragma unroll
-      for (int u = 0; u < (EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS; ++u) {
-        const int e = tid + u * EIG_THREADS;
-        if (e < nout) {
-          const int a = e / p, c = e % p;
-          Acc s = 0;
-          for (int r = 0; r < rows; ++r) mac(s, sv[r * EIG_MAXP + a], sw[r * EIG_MAXP + c]);
-          acc[u] += s;
-        }
-      }
+      gram_chunk(sv, sw, rows, nbj, nbp, acc);
       __syncthreads();
     }
 #pragma unroll
-    for (int u = 0; u < (EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS; ++u) {
-      const int e = tid + u * EIG_THREADS;
-      if (e < nout) {
-        G[e] = (double)acc[u];
-        Hi[(e / p) * EIG_MAXP + hc + e % p] += (double)acc[u];
+    for (int k = 0; k < ORTH_NB; ++k) {
+      const int b = tid + k * ORTH_THREADS;
+      if (b < nbj * nbp) {
+        const int a0 = 2 * (b / nbp), c0 = 2 * (b % nbp);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int a = a0 + (q >> 1), c = c0 + (q & 1);
+          if (a < jb && c < p) {
+            const double v = (double)acc[k][q];
+            G[a * p + c] = v;
+            Hi[a * EIG_MAXP + hc + c] += v;
+          }
+        }
       }
     }
     __syncthreads();
     if (full) return;  // Rayleigh quotient only
     // W -= V G, staged by row chunks; G converted once to the working arithmetic (in Ri's space)
     Acc* Ga = reinterpret_cast<Acc*>(Ri);
-    for (int e = tid; e < nout; e += EIG_THREADS) Ga[e] = (Acc)G[e];
+    for (int e = tid; e < jb * p; e += ORTH_THREADS) Ga[e] = (Acc)G[e];
     __syncthreads();
-    for (int l0 = 0; l0 < n; l0 += RC) {
-      const int rows = min(RC, n - l0);
-      for (int e = tid; e < rows * jb; e += EIG_THREADS)
-        sv[(e / jb) * EIG_MAXP + e % jb] = (Acc)Vi[(int64_t)(l0 + e / jb) * ldx + e % jb];
+    for (int l0 = 0; l0 < n; l0 += ORC) {
+      const int rows = min(ORC, n - l0);
+      stage_rows(sv, Vi, ldx, l0, rows, jb);
       __syncthreads();
-      for (int e = tid; e < rows * p; e += EIG_THREADS) {
+      for (int e = tid; e < rows * p; e += ORTH_THREADS) {
         const int r = e / p, c = e % p;
         Acc s = 0;
         for (int a = 0; a < jb; ++a) mac(s, sv[r * EIG_MAXP + a], Ga[a * p + c]);
@@ -447,30 +484,27 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
   // R_total = R3 R2 R1 goes to H[hr:hr+p, hc:hc+p]
   for (int pass = 0; pass < 3; ++pass) {
     // G = W^T W
-    Acc acc[(EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS];
+    Acc acc[ORTH_NB][4];
 #pragma unroll
-    for (int u = 0; u < (EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS; ++u) acc[u] = 0;
-    for (int l0 = 0; l0 < n; l0 += RC) {
-      const int rows = min(RC, n - l0);
-      for (int e = tid; e < rows * p; e += EIG_THREADS)
-        sw[(e / p) * EIG_MAXP + e % p] = (Acc)Wi[(int64_t)(l0 + e / p) * ldx + e % p];
+    for (int k = 0; k < ORTH_NB; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0;
+    for (int l0 = 0; l0 < n; l0 += ORC) {
+      const int rows = min(ORC, n - l0);
+      stage_rows(sw, Wi, ldx, l0, rows, p);
       __syncthreads();
-#pragma unroll
-      for (int u = 0; u < (EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS; ++u) {
-        const int e = tid + u * EIG_THREADS;
-        if (e < p * p) {
-          const int a = e / p, c = e % p;
-          Acc s = 0;
-          for (int r = 0; r < rows; ++r) mac(s, sw[r * EIG_MAXP + a], sw[r * EIG_MAXP + c]);
-          acc[u] += s;
-        }
-      }
+      gram_chunk(sw, sw, rows, nbp, nbp, acc);
       __syncthreads();
     }
 #pragma unroll
-    for (int u = 0; u < (EIG_MAXP * EIG_MAXP + EIG_THREADS - 1) / EIG_THREADS; ++u) {
-      const int e = tid + u * EIG_THREADS;
-      if (e < p * p) G[e] = (double)acc[u];
+    for (int k = 0; k < ORTH_NB; ++k) {
+      const int b = tid + k * ORTH_THREADS;
+      if (b < nbp * nbp) {
+        const int a0 = 2 * (b / nbp), c0 = 2 * (b % nbp);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int a = a0 + (q >> 1), c = c0 + (q & 1);
+          if (a < p && c < p) G[a * p + c] = (double)acc[k][q];
+        }
+      }
     }
     __syncthreads();
     if (tid == 0) {
@@ -483,7 +517,6 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
       }
       int ok;
       small_cholesky_inverse(G, p, Ri, ok, Tiny<Acc>::v);
-      rank_ok = ok;
       if (!ok && rank_flag) atomicAdd(rank_flag + i, 1);
       if (pass == 0) {
         for (int a = 0; a < p; ++a)
@@ -503,14 +536,13 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
     __syncthreads();
     // W <- W inv(R); inv(R) converted once to the working arithmetic (in G's space, free now)
     Acc* Ra = reinterpret_cast<Acc*>(G);
-    for (int e = tid; e < p * p; e += EIG_THREADS) Ra[e] = (Acc)Ri[e];
+    for (int e = tid; e < p * p; e += ORTH_THREADS) Ra[e] = (Acc)Ri[e];
     __syncthreads();
-    for (int l0 = 0; l0 < n; l0 += RC) {
-      const int rows = min(RC, n - l0);
-      for (int e = tid; e < rows * p; e += EIG_THREADS)
-        sw[(e / p) * EIG_MAXP + e % p] = (Acc)Wi[(int64_t)(l0 + e / p) * ldx + e % p];
+    for (int l0 = 0; l0 < n; l0 += ORC) {
+      const int rows = min(ORC, n - l0);
+      stage_rows(sw, Wi, ldx, l0, rows, p);
       __syncthreads();
-      for (int e = tid; e < rows * p; e += EIG_THREADS) {
+      for (int e = tid; e < rows * p; e += ORTH_THREADS) {
         const int r = e / p, c = e % p;
         Acc s = 0;
         for (int a = 0; a <= c; ++a) mac(s, sw[r * EIG_MAXP + a], Ra[a * p + c]);
@@ -521,7 +553,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_orth(const int* ni, const int64
   }
   // V[:, vout:vout+p] = W
   if (vout >= 0)
-    for (int e = tid; e < n * p; e += EIG_THREADS) {
+    for (int e = tid; e < n * p; e += ORTH_THREADS) {
       const int l = e / p, c = e % p;
       Vi[(int64_t)l * ldx + vout + c] = (T)Wi[(int64_t)l * ldx + c];
     }
@@ -844,7 +876,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   }
 
   using Acc = typename EAcc<TV>::type;
-  const size_t orth_smem = sizeof(double) * (2 * EIG_MAXP * EIG_MAXP + EIG_MAXP) + sizeof(Acc) * 2 * RC * EIG_MAXP;
+  const size_t orth_smem = sizeof(double) * (2 * EIG_MAXP * EIG_MAXP + EIG_MAXP) + sizeof(Acc) * 2 * ORC * EIG_MAXP;
   const size_t rr_smem = sizeof(double) * (2 * EIG_MAXP * (EIG_MAXP + 1) + 64 * EIG_MAXP + 3 * EIG_MAXP) +
                          sizeof(int) * EIG_MAXP + 64;
   const size_t vy_smem = sizeof(Acc) * (EIG_MAXP * EIG_MAXP + RC * EIG_MAXP);
@@ -875,7 +907,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, d_active, d_kd, kvec, W);
     A2LS_LAUNCH();
     // no previous basis: jb = 0; R written into H's last rows (discarded)
-    k_orth<TV, T><<<N, EIG_THREADS, orth_smem, st>>>(h->d_ni, d_vo, P, d_pv, d_active, 0, b, V, W, Rscr, 0, 0,
+    k_orth<TV, T><<<N, ORTH_THREADS, orth_smem, st>>>(h->d_ni, d_vo, P, d_pv, d_active, 0, b, V, W, Rscr, 0, 0,
                                                   0, nullptr, d_rank);
     A2LS_LAUNCH();
   };
@@ -918,7 +950,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
       // full-space subdomains (j == 0 only): H = V0^T (T V0)
       {
         KTime kt(h, KT_EIG_ORTH, orth_flops);
-        k_orth<TV, T><<<N, EIG_THREADS, orth_smem, st>>>(h->d_ni, d_vo, P, d_pv, actv, j + 1, b, V, W, H,
+        k_orth<TV, T><<<N, ORTH_THREADS, orth_smem, st>>>(h->d_ni, d_vo, P, d_pv, actv, j + 1, b, V, W, H,
                                                       (j + 1) * b, j * b, (j + 1) * b, d_full, d_rank);
         A2LS_LAUNCH();
       }
