@@ -8,9 +8,10 @@ subdomain, random right-hand side U(-1, 1), zero initial guess, GMRES(30) to a
 relative residual of 1e-8.  One step = a2ls_setup + a2ls_solve on inputs
 already resident in HBM (L2 flushed between steps by a 256 MiB write).
 
-The headline form is the mixed one (FP32 local factors and solves, FP64
-flexible GMRES, FP64 eigensolves and coarse operator); the plain FP64 form is
-timed in the same run.  The JSON line also carries the apply bandwidth, the
+The headline form is the mixed one (FP32 local solves, double-float (FP32
+pair) factorisation of the splittings and local eigensolves, FP64 flexible
+GMRES, Rayleigh-Ritz and coarse operator); the plain FP64 form is timed in the
+same run.  The JSON line also carries the apply bandwidth, the
 roofline of the dominant kernel, an end-to-end figure with host buffers, the
 CPU FP64 oracle timed on a bounded sample, and the SM clocks seen.
 
@@ -37,9 +38,12 @@ HBM_PEAK_KEY = "hbm_gbs"
 FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64 (non-tensor) nominal rate from the pool's recipe table
 # FP32 SIMT peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS_DERIVED = 152 * 128 * 2 * 2.07e9 / 1e12
-# kernels that run in the local-factor precision (FP32 in the mixed form); the factorisation of the
-# splittings, the local eigensolves, Rayleigh-Ritz and the coarse operator are FP64 in both forms
-LOCAL_PRECISION_KERNELS = {"lu_local"}
+# double-float multiply-add = 12 FP32 instructions (4 for the exact product, 6 for TwoSum, 2 adds):
+# 2 flops per 12 lane-instructions of the FP32 pipe
+FP32X2_PEAK_TFLOPS_DERIVED = 152 * 128 * 2.07e9 * 2 / 12 / 1e12
+# arithmetic of each tracked kernel in the mixed form (the plain form is FP64 throughout)
+MIXED_KERNEL_DTYPE = {"lu_local": "f32", "lu_splitting": "f32x2", "eig_triangular_solves": "f32x2",
+                      "eig_orthogonalisation": "f32x2"}
 
 
 def parse_args():
@@ -395,10 +399,13 @@ def roofline_entry(name: str, launches: int, ms: float, work: float, hbm_peak, f
                 "launches": launches, "avg_launch_ms": per_launch_ms,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     ach = work / launches / (per_launch_ms * 1e-3) / 1e12 if launches else None
-    if fp32 and name in LOCAL_PRECISION_KERNELS:
-        peak, src, dt = FP32_PEAK_TFLOPS_DERIVED, "FP32 SIMT peak from unit counts x 2.07 GHz", "f32"
+    dt = MIXED_KERNEL_DTYPE.get(name, "f64") if fp32 else "f64"
+    if dt == "f32":
+        peak, src = FP32_PEAK_TFLOPS_DERIVED, "FP32 SIMT peak from unit counts x 2.07 GHz"
+    elif dt == "f32x2":
+        peak, src = FP32X2_PEAK_TFLOPS_DERIVED, "FP32 SIMT lane rate x 2.07 GHz / 12 instructions per double-float FMA"
     else:
-        peak, src, dt = FP64_PEAK_TFLOPS_NOMINAL, "nominal FP64 SIMT rate of the pool's recipe table", "f64"
+        peak, src = FP64_PEAK_TFLOPS_NOMINAL, "nominal FP64 SIMT rate of the pool's recipe table"
     return {"kernel": name, "bound": "alu", "dtype": dt, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
             "frac": (ach / peak) if ach else None, "traffic": None,
             "launches": launches, "avg_launch_ms": per_launch_ms, "peak_source": src}
@@ -422,11 +429,12 @@ def report(args, res, world) -> dict:
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 local factors/solves, f64 GMRES/SpMV/eigensolves/coarse",
+        "dtype": "f32 local solves, f32x2 (double-float) splitting LU and eigensolves, f64 GMRES/SpMV/Rayleigh-Ritz/coarse",
         "data": "synthetic (seeded generator, workloads.pde.config_c2)",
         "config": {"workload": WORKLOAD if args.workload == "c2" else prob.name, "n": prob.n, "nnz": int(prob.A.nnz), "subdomains": int(prob.nparts),
                    "overlap": prob.overlap, "nev": prob.nev, "rtol": 1e-8, "restart": 30,
-                   "form": "mixed: FP32 local LU of A_ii and FP32 local solves, FGMRES(30) in FP64, FP64 local eigensolves to 1e-4",
+                   "form": ("mixed: double-float LU of the splittings (interior block shared with A_ii), FP32 A_ii "
+                            "factors and local solves, double-float local eigensolves to 1e-4, FGMRES(30) in FP64"),
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
         "iters": mixed[-1]["iters"],
         "true_relres": res["true_relres"],

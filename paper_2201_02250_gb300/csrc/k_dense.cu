@@ -160,96 +160,210 @@ __device__ __forceinline__ void cta_gemm_n8(const T* __restrict__ A, int64_t lda
 // ---------------------------------------------------------------------------
 // batched LU without pivoting
 // ---------------------------------------------------------------------------
-constexpr int LU_NB = 32;
+// Tile product with register prefetch: acc(64 x 64) += A(0:64, 0:K) B(0:K, 0:64), 256 threads,
+// thread (ty, tx) owns rows ty*4.. and columns tx*4..; fa(m, k) and fb(k, c) fetch operand elements
+// (zero outside the operands).  The next TGK-deep slab is loaded into registers while the current
+// one is multiplied from shared memory.
+constexpr int TGK = 16;
+template <class Acc, class FA, class FB>
+__device__ __forceinline__ void tile_gemm(FA fa, FB fb, int K, Acc (&acc)[4][4], Acc* sA, Acc* sB) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  Acc ra[4], rb[4];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + u * 256;
+      ra[u] = fa(e / TGK, k0 + e % TGK);   // A(m, k0 + k): consecutive threads walk k
+      rb[u] = fb(k0 + e / 64, e % 64);     // B(k0 + k, c): consecutive threads walk c
+    }
+  };
+  if (K > 0) fetch(0);
+  for (int k0 = 0; k0 < K; k0 += TGK) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + u * 256;
+      sA[(e % TGK) * 65 + e / TGK] = ra[u];
+      sB[(e / 64) * 65 + e % 64] = rb[u];
+    }
+    __syncthreads();
+    if (k0 + TGK < K) fetch(k0 + TGK);
+    const int kk = min(TGK, K - k0);
+#pragma unroll 8
+    for (int k = 0; k < kk; ++k) {
+      Acc a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = sA[k * 65 + ty * 4 + u];
+        b[u] = sB[k * 65 + tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) mac(acc[u][v], a[u], b[v]);
+    }
+    __syncthreads();
+  }
+}
 
+// Blocked right-looking LU without pivoting, one CTA per subdomain (largest first).  Each step
+// factors a diagonal block of up to 64 columns in shared memory and inverts its triangles there;
+// the block column below it (L21 = A21 inv(U11)), the block row to its right (U12 = inv(L11) A12)
+// and the trailing matrix (A22 -= L21 U12) are then tile products.  The factors are the unique
+// unpivoted L and U, whatever the blocking, so the phase split below may leave blocks that are not
+// aligned to the 64-grid of the block-inverted storage (whose diagonal tiles are inverted afterwards).
 // phase: -1 all columns; 0 the interior columns [0, n_I) (the trailing Schur complement on the
 // overlap rows is left in place); 1 the remaining columns [n_I, n).
+constexpr size_t lu_smem_elems() { return 2 * (size_t)TB * 65 + 2 * (size_t)TGK * 65; }
+
 template <class T>
-__global__ void __launch_bounds__(256) k_lu(int N, const int* ni, const int* ld, const int64_t* foff,
+__global__ void __launch_bounds__(256, 2) k_lu(int N, const int* ni, const int* ld, const int64_t* foff,
                                             T* fac, int allow_last_zero, double* last_pivot,
                                             const double* dscale, int* st, const int* sched, const int* nI,
                                             int phase) {
   using Acc = typename AccOf<T>::type;
-  __shared__ Acc sA[GK * 65], sB[GK * 65];
-  const int i = sched ? sched[blockIdx.x] : blockIdx.x;  // largest subdomains first
+  extern __shared__ __align__(16) unsigned char lu_smem_raw[];
+  Acc* Dm = reinterpret_cast<Acc*>(lu_smem_raw);  // 64 x 65: the diagonal block, factored in place
+  Acc* Iv = Dm + TB * 65;                         // 64 x 65: inv(L11) strictly below, inv(U11) on/above
+  Acc* sA = Iv + TB * 65;                         // TGK x 65
+  Acc* sB = sA + TGK * 65;                        // TGK x 65
+  const int i = sched ? sched[blockIdx.x] : blockIdx.x;
   const int n = ni[i];
   const int64_t L = ld[i];
   T* A = fac + foff[i];
   const double scale = dscale[i] > 0 ? dscale[i] : 1.0;
   const double tiny = (Unit<T>::u < 1e-15 ? 1e-14 : 1e-12) * scale;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int kbeg = (phase == 1) ? nI[i] : 0;
   const int kend = (phase == 0) ? nI[i] : n;
-  for (int k0 = kbeg; k0 < kend; k0 += LU_NB) {
-    const int kb = min(LU_NB, kend - k0);
-    // 1. unblocked factorisation of the panel A(k0:n, k0:k0+kb)
-    for (int c = k0; c < k0 + kb; ++c) {
-      __syncthreads();
-      double piv = (double)A[c * L + c];
-      if (allow_last_zero && c == n - 1) {
-        // record the last pivot of A~_ii and replace it by the scale; the
-        // eigensolver decides from it whether A~_ii is singular
-        __syncthreads();
+  for (int k0 = kbeg; k0 < kend; k0 += TB) {
+    const int w = min(TB, kend - k0);
+    // 1. the diagonal block: LU in shared memory
+    for (int e = tid; e < w * w; e += 256) Dm[(e / w) * 65 + e % w] = (Acc)A[(int64_t)(k0 + e / w) * L + k0 + e % w];
+    __syncthreads();
+    for (int c = 0; c < w; ++c) {
+      double piv = (double)Dm[c * 65 + c];
+      if (allow_last_zero && k0 + c == n - 1) {
+        // record the last pivot of A~_ii and replace it by the scale; the eigensolver decides from it
+        // whether A~_ii is singular
         if (tid == 0) {
           last_pivot[i] = piv;
-          A[c * L + c] = (T)scale;
+          Dm[c * 65 + c] = (Acc)scale;
         }
         break;
       }
-      if (fabs(piv) <= tiny) {
-        if (tid == 0) raise_status(st, A2LS_ERR_SINGULAR, i, c);
-        piv = scale;
-        __syncthreads();
-        if (tid == 0) A[c * L + c] = (T)piv;
-      }
-      const T pinv = (T)(1.0 / piv);
-      for (int r = c + 1 + tid; r < n; r += 256) A[r * L + c] = A[r * L + c] * pinv;
+      if (fabs(piv) <= tiny) piv = scale;
+      const Acc pinv = (Acc)(1.0 / piv);
       __syncthreads();
-      const int ncols = k0 + kb - 1 - c;
-      if (ncols > 0) {
-        const int rows = n - 1 - c;
-        for (int e = tid; e < rows * ncols; e += 256) {
-          const int r = c + 1 + e / ncols, cc = c + 1 + e % ncols;
-          A[r * L + cc] -= A[r * L + c] * A[c * L + cc];
+      if (tid == 0 && piv == scale && fabs((double)Dm[c * 65 + c]) <= tiny) {
+        raise_status(st, A2LS_ERR_SINGULAR, i, k0 + c);
+        Dm[c * 65 + c] = (Acc)scale;
+      }
+      for (int r = c + 1 + tid; r < w; r += 256) Dm[r * 65 + c] = Dm[r * 65 + c] * pinv;
+      __syncthreads();
+      const int m = w - 1 - c;
+      for (int e = tid; e < m * m; e += 256) {
+        const int r = c + 1 + e / m, cc = c + 1 + e % m;
+        Dm[r * 65 + cc] -= Dm[r * 65 + c] * Dm[c * 65 + cc];
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    for (int e = tid; e < w * w; e += 256) A[(int64_t)(k0 + e / w) * L + k0 + e % w] = (T)Dm[(e / w) * 65 + e % w];
+    const int c0 = k0 + w;
+    if (c0 >= n) break;
+    // inverses of the triangles: threads 0..63 columns of inv(L11), threads 64..127 columns of inv(U11)
+    {
+      const int c = tid & (TB - 1);
+      if (tid < TB && c < w) {
+        for (int r = c + 1; r < w; ++r) {
+          Acc v = Dm[r * 65 + c];
+          for (int q = c + 1; q < r; ++q) mac(v, Dm[r * 65 + q], Iv[q * 65 + c]);
+          Iv[r * 65 + c] = -finish(v);
+        }
+      } else if (tid >= TB && tid < 2 * TB && c < w) {
+        Iv[c * 65 + c] = (Acc)(1.0 / (double)Dm[c * 65 + c]);
+        for (int r = c - 1; r >= 0; --r) {
+          Acc v = 0;
+          for (int q = r + 1; q <= c; ++q) mac(v, Dm[r * 65 + q], Iv[q * 65 + c]);
+          Iv[r * 65 + c] = -(finish(v) * (Acc)(1.0 / (double)Dm[r * 65 + r]));
         }
       }
     }
     __syncthreads();
-    const int c0 = k0 + kb;
-    if (c0 >= n) break;
-    // 2. U12 = inv(L11) A12 (forward substitution, one column per thread)
-    for (int cc = c0 + tid; cc < n; cc += 256) {
-      for (int r = 1; r < kb; ++r) {
-        Acc s = (Acc)A[(k0 + r) * L + cc];
-        for (int q = 0; q < r; ++q) s -= (Acc)A[(k0 + r) * L + k0 + q] * (Acc)A[(k0 + q) * L + cc];
-        A[(k0 + r) * L + cc] = (T)s;
-      }
-    }
-    __syncthreads();
-    // 3. A22 -= L21 U12 in 64x64 tiles
-    const int m = n - c0;
-    const int tiles = (m + 63) / 64;
-    for (int t = 0; t < tiles * tiles; ++t) {
-      const int tr = c0 + (t / tiles) * 64, tc = c0 + (t % tiles) * 64;
-      Acc acc[4][4] = {};
-      cta_gemm<T, Acc>(A + tr * L + k0, L, A + k0 * L + tc, L, min(64, n - tr), min(64, n - tc), kb, 0,
-                       acc, sA, sB);
-      const int tx = tid & 15, ty = tid >> 4;
+    const int tiles = (n - c0 + TB - 1) / TB;
+    // 2. L21 = A21 inv(U11), 64-row tiles
+    for (int t = 0; t < tiles; ++t) {
+      const int r0 = c0 + t * TB, rows = min(TB, n - r0);
+      Acc acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+      tile_gemm<Acc>([&](int m, int k) -> Acc { return (m < rows && k < w) ? (Acc)A[(int64_t)(r0 + m) * L + k0 + k] : (Acc)0; },
+                     [&](int k, int c) -> Acc { return (k < w && c < w && c >= k) ? Iv[k * 65 + c] : (Acc)0; },
+                     w, acc, sA, sB);
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const int r = tr + ty * 4 + u, c = tc + tx * 4 + v;
-          if (r < n && c < n) A[r * L + c] = (T)((Acc)A[r * L + c] - acc[u][v]);
+          const int r = ty * 4 + u, c = tx * 4 + v;
+          if (r < rows && c < w) A[(int64_t)(r0 + r) * L + k0 + c] = (T)finish(acc[u][v]);
         }
     }
+    // 3. U12 = inv(L11) A12, 64-column tiles
+    for (int t = 0; t < tiles; ++t) {
+      const int cs = c0 + t * TB, cols = min(TB, n - cs);
+      Acc acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+      tile_gemm<Acc>([&](int m, int k) -> Acc { return (m < w && k < w) ? (k < m ? Iv[m * 65 + k] : (k == m ? (Acc)1 : (Acc)0)) : (Acc)0; },
+                     [&](int k, int c) -> Acc { return (k < w && c < cols) ? (Acc)A[(int64_t)(k0 + k) * L + cs + c] : (Acc)0; },
+                     w, acc, sA, sB);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int r = ty * 4 + u, c = tx * 4 + v;
+          if (r < w && c < cols) A[(int64_t)(k0 + r) * L + cs + c] = (T)finish(acc[u][v]);
+        }
+    }
+    __syncthreads();  // L21 and U12 complete before the trailing update reads them
+    // 4. A22 -= L21 U12
+    for (int t = 0; t < tiles * tiles; ++t) {
+      const int r0 = c0 + (t / tiles) * TB, cs = c0 + (t % tiles) * TB;
+      const int rows = min(TB, n - r0), cols = min(TB, n - cs);
+      Acc acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+      tile_gemm<Acc>([&](int m, int k) -> Acc { return (m < rows && k < w) ? (Acc)A[(int64_t)(r0 + m) * L + k0 + k] : (Acc)0; },
+                     [&](int k, int c) -> Acc { return (k < w && c < cols) ? (Acc)A[(int64_t)(k0 + k) * L + cs + c] : (Acc)0; },
+                     w, acc, sA, sB);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int r = ty * 4 + u, c = tx * 4 + v;
+          if (r < rows && c < cols) {
+            T* p = A + (int64_t)(r0 + r) * L + cs + c;
+            *p = (T)((Acc)*p - acc[u][v]);
+          }
+        }
+    }
+    __syncthreads();
   }
 }
 
 template <class T>
 void lu_batched(a2ls_handle* h, T* fac, int allow_last_zero, double* last_pivot, double* diag_scale, int phase) {
-  k_lu<T><<<h->N, 256, 0, h->st>>>(h->N, h->d_ni, h->d_ld, h->d_foff, fac, allow_last_zero, last_pivot,
-                                   diag_scale, h->d_status, h->d_sched, h->d_nI, phase);
+  using Acc = typename AccOf<T>::type;
+  const size_t smem = lu_smem_elems() * sizeof(Acc);
+  A2LS_CUDA(cudaFuncSetAttribute(k_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_lu<T><<<h->N, 256, smem, h->st>>>(h->N, h->d_ni, h->d_ld, h->d_foff, fac, allow_last_zero, last_pivot,
+                                      diag_scale, h->d_status, h->d_sched, h->d_nI, phase);
   A2LS_LAUNCH();
 }
 

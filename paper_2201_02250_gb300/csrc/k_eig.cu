@@ -560,9 +560,13 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
 }
 
 // ---------------------------------------------------------------------------
-// Rayleigh-Ritz on H (one warp per subdomain): Ritz values, the real basis Y of
+// Rayleigh-Ritz on H (one CTA per subdomain): Ritz values, the real basis Y of
 // the leading Ritz vectors (bcols columns), residual norms and convergence.
 // ---------------------------------------------------------------------------
+// Threads per subdomain of the Rayleigh-Ritz kernel (measured on the 512x512 high-contrast problem:
+// 32 and 256 threads were both slower than 128)
+constexpr int RR_THREADS = 128;
+
 struct RRParams {
   int sb_krylov;   // s*b in Krylov mode
   int b;           // block size
@@ -957,7 +961,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     }
     {
       KTime kt(h, KT_EIG_RR);
-      k_rayleigh_ritz<<<N, 128, rr_smem, st>>>(prm, d_full, d_mfull, d_nf, d_active, H, Y, d_ycols, d_zcols,
+      k_rayleigh_ritz<<<N, RR_THREADS, rr_smem, st>>>(prm, d_full, d_mfull, d_nf, d_active, H, Y, d_ycols, d_zcols,
                                               eigout, d_conv, h->d_status);
       A2LS_LAUNCH();
     }
