@@ -364,35 +364,7 @@ __device__ void small_cholesky_inverse(double* G, int p, double* Ri, int& rank_o
 
 constexpr int ORTH_THREADS = 512;
 constexpr int ORC = 32;                  // rows staged per chunk in k_orth
-constexpr int ORTH_NB = (EIG_MAXP / 2) * (EIG_MAXP / 2) / ORTH_THREADS + 1;  // 2x2 blocks per thread
-
-// acc[k] += X[0:rows, a0:a0+2]^T Y[0:rows, c0:c0+2] for the 2x2 output blocks b = tid + k * ORTH_THREADS,
-// (a0, c0) = 2 * (b / nbc, b % nbc); X and Y are staged row chunks (stride EIG_MAXP) whose padding
-// column (index jb or p when odd) holds zeros.
-template <class Acc>
-__device__ __forceinline__ void gram_chunk(const Acc* X, const Acc* Y, int rows, int nbr, int nbc,
-                                           Acc (&acc)[ORTH_NB][4]) {
-#pragma unroll
-  for (int k = 0; k < ORTH_NB; ++k) {
-    const int b = threadIdx.x + k * ORTH_THREADS;
-    if (b < nbr * nbc) {
-      const int a0 = 2 * (b / nbc), c0 = 2 * (b % nbc);
-      Acc s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-      for (int r = 0; r < rows; ++r) {
-        const Acc x0 = X[r * EIG_MAXP + a0], x1 = X[r * EIG_MAXP + a0 + 1];
-        const Acc y0 = Y[r * EIG_MAXP + c0], y1 = Y[r * EIG_MAXP + c0 + 1];
-        mac(s0, x0, y0);
-        mac(s1, x0, y1);
-        mac(s2, x1, y0);
-        mac(s3, x1, y1);
-      }
-      acc[k][0] += finish(s0);
-      acc[k][1] += finish(s1);
-      acc[k][2] += finish(s2);
-      acc[k][3] += finish(s3);
-    }
-  }
-}
+constexpr int ORTH_NB = (EIG_MAXP / 2) * (EIG_MAXP / 2) / ORTH_THREADS + 1;  // Gram items per thread
 
 // stage rows [l0, l0 + rows) of M (cols 0:w) into S (stride EIG_MAXP), zero padding column w
 template <class Acc, class TM>
@@ -404,11 +376,133 @@ __device__ __forceinline__ void stage_rows(Acc* S, const TM* M, int64_t ldx, int
   }
 }
 
+// Gram product G (nx x ny, row-major, stride ny) = X^T Y over the n rows of X and Y (global, leading
+// dimension ldx), split into 2x2 output blocks and, when there are fewer blocks than threads, into
+// ng row groups (split-K) whose partial sums are added at the end.  Xs, Ys: staging chunks; Ps:
+// scratch of ORTH_THREADS x 4 values for the partial sums (may alias Xs).  Ends with a barrier.
+template <class Acc, class TX, class TY>
+__device__ void gram_product(const TX* X, const TY* Y, int64_t ldx, int n, int nx, int ny, bool same, Acc* Xs,
+                             Acc* Ys, double* G, Acc* Ps) {
+  const int tid = threadIdx.x;
+  const int nbr = (nx + 1) / 2, nbc = (ny + 1) / 2, nb = nbr * nbc;
+  const int ng = nb >= ORTH_THREADS ? 1 : min(8, ORTH_THREADS / nb);
+  const int items = nb * ng;
+  Acc acc[ORTH_NB][4];
+#pragma unroll
+  for (int k = 0; k < ORTH_NB; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0;
+  for (int l0 = 0; l0 < n; l0 += ORC) {
+    const int rows = min(ORC, n - l0);
+    stage_rows(Xs, X, ldx, l0, rows, nx);
+    if (!same) stage_rows(Ys, Y, ldx, l0, rows, ny);
+    __syncthreads();
+    const Acc* Yr = same ? Xs : Ys;
+#pragma unroll
+    for (int k = 0; k < ORTH_NB; ++k) {
+      const int w = tid + k * ORTH_THREADS;
+      if (w < items) {
+        const int b = w % nb, g = w / nb;
+        const int a0 = 2 * (b / nbc), c0 = 2 * (b % nbc);
+        Acc s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        for (int r = g; r < rows; r += ng) {
+          const Acc x0 = Xs[r * EIG_MAXP + a0], x1 = Xs[r * EIG_MAXP + a0 + 1];
+          const Acc y0 = Yr[r * EIG_MAXP + c0], y1 = Yr[r * EIG_MAXP + c0 + 1];
+          mac(s0, x0, y0);
+          mac(s1, x0, y1);
+          mac(s2, x1, y0);
+          mac(s3, x1, y1);
+        }
+        acc[k][0] += finish(s0);
+        acc[k][1] += finish(s1);
+        acc[k][2] += finish(s2);
+        acc[k][3] += finish(s3);
+      }
+    }
+    __syncthreads();
+  }
+  if (ng == 1) {
+#pragma unroll
+    for (int k = 0; k < ORTH_NB; ++k) {
+      const int b = tid + k * ORTH_THREADS;
+      if (b < nb) {
+        const int a0 = 2 * (b / nbc), c0 = 2 * (b % nbc);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int a = a0 + (q >> 1), c = c0 + (q & 1);
+          if (a < nx && c < ny) G[a * ny + c] = (double)acc[k][q];
+        }
+      }
+    }
+  } else {
+    if (tid < items)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) Ps[tid * 4 + q] = acc[0][q];
+    __syncthreads();
+    if (tid < nb) {
+      const int a0 = 2 * (tid / nbc), c0 = 2 * (tid % nbc);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        Acc s = Ps[tid * 4 + q];
+        for (int g = 1; g < ng; ++g) s += Ps[(g * nb + tid) * 4 + q];
+        const int a = a0 + (q >> 1), c = c0 + (q & 1);
+        if (a < nx && c < ny) G[a * ny + c] = (double)s;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// One warp: G (p x p, stride p) = R^T R by Cholesky, R into G's upper triangle, Ri = inv(R) (stride p).
+// A pivot at or below 1e-28 of the largest diagonal (or abs_floor) marks a rank-deficient block; it is
+// floored so that inv(R) stays finite in the working precision and a zero column stays zero.
+// Returns 1 when no pivot was floored (valid on every lane).
+__device__ int warp_cholesky_inverse(double* G, int p, double* Ri, double abs_floor) {
+  const int lane = threadIdx.x & 31;
+  double gm = 0.0;
+  for (int a = lane; a < p; a += 32) gm = fmax(gm, G[a * p + a]);
+  for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+  const double floor_d = fmax(1e-28 * gm, abs_floor);
+  int ok = 1;
+  for (int a = 0; a < p; ++a) {
+    double part = 0.0;
+    for (int q = lane; q < a; q += 32) part += G[q * p + a] * G[q * p + a];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    double d = G[a * p + a] - part;
+    if (!(d > floor_d)) {
+      ok = 0;
+      d = floor_d;
+    }
+    const double r = sqrt(d);
+    for (int c = a + 1 + lane; c < p; c += 32) {
+      double v = G[a * p + c];
+      for (int q = 0; q < a; ++q) v -= G[q * p + a] * G[q * p + c];
+      G[a * p + c] = v / r;
+    }
+    __syncwarp();
+    if (lane == 0) G[a * p + a] = r;
+    __syncwarp();
+  }
+  for (int c = lane; c < p; c += 32) {
+    for (int a = c + 1; a < p; ++a) Ri[a * p + c] = 0.0;
+    Ri[c * p + c] = 1.0 / G[c * p + c];
+    for (int a = c - 1; a >= 0; --a) {
+      double v = 0.0;
+      for (int q = a + 1; q <= c; ++q) v += G[a * p + q] * Ri[q * p + c];
+      Ri[a * p + c] = -v / G[a * p + a];
+    }
+  }
+  __syncwarp();
+  return ok;
+}
+
+// Orthogonalisation: block CGS2 of W against V[:, 0:jb], then Cholesky QR three times (the first
+// shifted).  Writes the Gram coefficients into H[0:jb, hc:hc+p] and R into H[hr:hr+p, hc:hc+p] and
+// the orthonormal block into V[:, vout:vout+p].  full != 0: only H[0:jb, hc:hc+p].
+// Shared memory: G and Ri (gcap doubles each), trow, two staging chunks of ORC x EIG_MAXP.
 template <class T, class TW>
 __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int64_t* xoff, int ldx,
                                                         const int* pvec, const int* active, int jb_blocks,
                                                         int bcols, T* V, TW* W, double* H, int hr, int hc,
-                                                        int vout, const int* fullv, int* rank_flag) {
+                                                        int vout, const int* fullv, int* rank_flag, int gcap) {
   using Acc = typename EAcc<T>::type;
   extern __shared__ double sm[];
   const int i = blockIdx.x;
@@ -420,61 +514,43 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
   T* Vi = V + xoff[i];
   TW* Wi = W + xoff[i];
   double* Hi = H + (int64_t)i * EIG_MAXP * EIG_MAXP;
-  // shared layout
-  double* G = sm;                               // EIG_MAXP * EIG_MAXP (Gram, then R in place)
-  double* Ri = G + EIG_MAXP * EIG_MAXP;         // EIG_MAXP * EIG_MAXP
-  double* trow = Ri + EIG_MAXP * EIG_MAXP;      // EIG_MAXP
+  double* G = sm;                               // gcap: Gram, then R in place
+  double* Ri = G + gcap;                        // gcap
+  double* trow = Ri + gcap;                     // EIG_MAXP
   Acc* sv = reinterpret_cast<Acc*>(trow + EIG_MAXP);           // ORC * EIG_MAXP
   Acc* sw = sv + ORC * EIG_MAXP;                               // ORC * EIG_MAXP
+  __shared__ int rank_ok;
   const int tid = threadIdx.x;
+  const int pp = p + (p & 1);                   // padded column count of the converted coefficients
   const int npass = jb > 0 ? 2 : 0;
-  const int nbj = (jb + 1) / 2, nbp = (p + 1) / 2;
   for (int e = tid; e < jb * p; e += ORTH_THREADS) Hi[(e / p) * EIG_MAXP + hc + e % p] = 0.0;
   for (int pass = 0; pass < npass; ++pass) {
     // G = V[:, 0:jb]^T W[:, 0:p]
-    Acc acc[ORTH_NB][4];
-#pragma unroll
-    for (int k = 0; k < ORTH_NB; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0;
-    for (int l0 = 0; l0 < n; l0 += ORC) {
-      const int rows = min(ORC, n - l0);
-      stage_rows(sv, Vi, ldx, l0, rows, jb);
-      stage_rows(sw, Wi, ldx, l0, rows, p);
-      __syncthreads();
-      gram_chunk(sv, sw, rows, nbj, nbp, acc);
-      __syncthreads();
-    }
-#pragma unroll
-    for (int k = 0; k < ORTH_NB; ++k) {
-      const int b = tid + k * ORTH_THREADS;
-      if (b < nbj * nbp) {
-        const int a0 = 2 * (b / nbp), c0 = 2 * (b % nbp);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int a = a0 + (q >> 1), c = c0 + (q & 1);
-          if (a < jb && c < p) {
-            const double v = (double)acc[k][q];
-            G[a * p + c] = v;
-            Hi[a * EIG_MAXP + hc + c] += v;
-          }
-        }
-      }
-    }
-    __syncthreads();
+    gram_product<Acc>(Vi, Wi, (int64_t)ldx, n, jb, p, false, sv, sw, G, sv);
+    for (int e = tid; e < jb * p; e += ORTH_THREADS) Hi[(e / p) * EIG_MAXP + hc + e % p] += G[e];
     if (full) return;  // Rayleigh quotient only
-    // W -= V G, staged by row chunks; G converted once to the working arithmetic (in Ri's space)
+    // W -= V G; G converted once to the working arithmetic (in Ri's space, padded to pp columns)
     Acc* Ga = reinterpret_cast<Acc*>(Ri);
-    for (int e = tid; e < jb * p; e += ORTH_THREADS) Ga[e] = (Acc)G[e];
+    for (int e = tid; e < jb * pp; e += ORTH_THREADS) {
+      const int a = e / pp, c = e % pp;
+      Ga[e] = c < p ? (Acc)G[a * p + c] : (Acc)0;
+    }
     __syncthreads();
     for (int l0 = 0; l0 < n; l0 += ORC) {
       const int rows = min(ORC, n - l0);
       stage_rows(sv, Vi, ldx, l0, rows, jb);
       __syncthreads();
-      for (int e = tid; e < rows * p; e += ORTH_THREADS) {
-        const int r = e / p, c = e % p;
-        Acc s = 0;
-        for (int a = 0; a < jb; ++a) mac(s, sv[r * EIG_MAXP + a], Ga[a * p + c]);
+      for (int e = tid; e < rows * (pp / 2); e += ORTH_THREADS) {
+        const int r = e / (pp / 2), c = 2 * (e % (pp / 2));
+        Acc s0 = 0, s1 = 0;
+        for (int a = 0; a < jb; ++a) {
+          const Acc v = sv[r * EIG_MAXP + a];
+          mac(s0, v, Ga[a * pp + c]);
+          mac(s1, v, Ga[a * pp + c + 1]);
+        }
         TW* w = Wi + (int64_t)(l0 + r) * ldx + c;
-        *w = (TW)((Acc)*w - s);
+        w[0] = (TW)((Acc)w[0] - s0);
+        if (c + 1 < p) w[1] = (TW)((Acc)w[1] - s1);
       }
       __syncthreads();
     }
@@ -483,70 +559,64 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
   // nearly rank-deficient blocks, two plain passes restore orthogonality):
   // R_total = R3 R2 R1 goes to H[hr:hr+p, hc:hc+p]
   for (int pass = 0; pass < 3; ++pass) {
-    // G = W^T W
-    Acc acc[ORTH_NB][4];
-#pragma unroll
-    for (int k = 0; k < ORTH_NB; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0;
-    for (int l0 = 0; l0 < n; l0 += ORC) {
-      const int rows = min(ORC, n - l0);
-      stage_rows(sw, Wi, ldx, l0, rows, p);
-      __syncthreads();
-      gram_chunk(sw, sw, rows, nbp, nbp, acc);
-      __syncthreads();
-    }
-#pragma unroll
-    for (int k = 0; k < ORTH_NB; ++k) {
-      const int b = tid + k * ORTH_THREADS;
-      if (b < nbp * nbp) {
-        const int a0 = 2 * (b / nbp), c0 = 2 * (b % nbp);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int a = a0 + (q >> 1), c = c0 + (q & 1);
-          if (a < p && c < p) G[a * p + c] = (double)acc[k][q];
-        }
-      }
-    }
-    __syncthreads();
-    if (tid == 0) {
+    gram_product<Acc>(Wi, Wi, (int64_t)ldx, n, p, p, true, sw, sw, G, sv);
+    if (tid < 32) {
       if (pass == 0) {
         double tr = 0.0;
-        for (int a = 0; a < p; ++a) tr += G[a * p + a];
+        for (int a = tid; a < p; a += 32) tr += G[a * p + a];
+        for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
         const double u = Unit<Acc>::u;
         const double shift = 11.0 * ((double)n * p + (double)p * (p + 1)) * u * tr;
-        for (int a = 0; a < p; ++a) G[a * p + a] += shift;
+        for (int a = tid; a < p; a += 32) G[a * p + a] += shift;
+        __syncwarp();
       }
-      int ok;
-      small_cholesky_inverse(G, p, Ri, ok, Tiny<Acc>::v);
-      if (!ok && rank_flag) atomicAdd(rank_flag + i, 1);
-      if (pass == 0) {
-        for (int a = 0; a < p; ++a)
-          for (int c = 0; c < p; ++c) Hi[(hr + a) * EIG_MAXP + hc + c] = (c >= a) ? G[a * p + c] : 0.0;
-      } else {
-        // H_blk <- R2 H_blk, row by row (row a only reads rows q >= a)
-        for (int a = 0; a < p; ++a) {
-          for (int c = 0; c < p; ++c) {
-            double s = 0.0;
-            for (int q = a; q < p; ++q) s += G[a * p + q] * Hi[(hr + q) * EIG_MAXP + hc + c];
-            trow[c] = s;
-          }
-          for (int c = 0; c < p; ++c) Hi[(hr + a) * EIG_MAXP + hc + c] = trow[c];
-        }
+      const int ok = warp_cholesky_inverse(G, p, Ri, Tiny<Acc>::v);
+      if (tid == 0) {
+        rank_ok = ok;
+        if (!ok && rank_flag) atomicAdd(rank_flag + i, 1);
       }
     }
     __syncthreads();
-    // W <- W inv(R); inv(R) converted once to the working arithmetic (in G's space, free now)
+    if (pass == 0) {
+      for (int e = tid; e < p * p; e += ORTH_THREADS) {
+        const int a = e / p, c = e % p;
+        Hi[(hr + a) * EIG_MAXP + hc + c] = (c >= a) ? G[a * p + c] : 0.0;
+      }
+    } else {
+      // H_blk <- R H_blk (R upper triangular), through a temporary in the staging space
+      double* tmp = reinterpret_cast<double*>(sw);
+      for (int e = tid; e < p * p; e += ORTH_THREADS) {
+        const int a = e / p, c = e % p;
+        double s = 0.0;
+        for (int q = a; q < p; ++q) s += G[a * p + q] * Hi[(hr + q) * EIG_MAXP + hc + c];
+        tmp[e] = s;
+      }
+      __syncthreads();
+      for (int e = tid; e < p * p; e += ORTH_THREADS) Hi[(hr + e / p) * EIG_MAXP + hc + e % p] = tmp[e];
+    }
+    __syncthreads();
+    // W <- W inv(R); inv(R) converted once to the working arithmetic (in G's space, padded to pp columns)
     Acc* Ra = reinterpret_cast<Acc*>(G);
-    for (int e = tid; e < p * p; e += ORTH_THREADS) Ra[e] = (Acc)Ri[e];
+    for (int e = tid; e < p * pp; e += ORTH_THREADS) {
+      const int a = e / pp, c = e % pp;
+      Ra[e] = c < p ? (Acc)Ri[a * p + c] : (Acc)0;
+    }
     __syncthreads();
     for (int l0 = 0; l0 < n; l0 += ORC) {
       const int rows = min(ORC, n - l0);
       stage_rows(sw, Wi, ldx, l0, rows, p);
       __syncthreads();
-      for (int e = tid; e < rows * p; e += ORTH_THREADS) {
-        const int r = e / p, c = e % p;
-        Acc s = 0;
-        for (int a = 0; a <= c; ++a) mac(s, sw[r * EIG_MAXP + a], Ra[a * p + c]);
-        Wi[(int64_t)(l0 + r) * ldx + c] = (TW)finish(s);
+      for (int e = tid; e < rows * (pp / 2); e += ORTH_THREADS) {
+        const int r = e / (pp / 2), c = 2 * (e % (pp / 2));
+        Acc s0 = 0, s1 = 0;
+        for (int a = 0; a <= c + 1 && a < p; ++a) {
+          const Acc v = sw[r * EIG_MAXP + a];
+          mac(s0, v, Ra[a * pp + c]);
+          mac(s1, v, Ra[a * pp + c + 1]);
+        }
+        TW* w = Wi + (int64_t)(l0 + r) * ldx + c;
+        w[0] = (TW)finish(s0);
+        if (c + 1 < p) w[1] = (TW)finish(s1);
       }
       __syncthreads();
     }
@@ -880,7 +950,15 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   }
 
   using Acc = typename EAcc<TV>::type;
-  const size_t orth_smem = sizeof(double) * (2 * EIG_MAXP * EIG_MAXP + EIG_MAXP) + sizeof(Acc) * 2 * ORC * EIG_MAXP;
+  // Gram space: jb x p <= EIG_MAXP x 32 in Krylov mode; EIG_MAXP^2 where a full-space subdomain is
+  // orthogonalised (first block step only)
+  bool any_full = false;
+  for (int i = 0; i < N; ++i) any_full = any_full || (full[i] && act[i]);
+  const int gcap_k = EIG_MAXP * 32, gcap_f = any_full ? EIG_MAXP * EIG_MAXP : gcap_k;
+  auto orth_smem_for = [&](int gcap) {
+    return sizeof(double) * (2 * (size_t)gcap + EIG_MAXP) + sizeof(Acc) * 2 * ORC * EIG_MAXP;
+  };
+  const size_t orth_smem = orth_smem_for(gcap_f);
   const size_t rr_smem = sizeof(double) * (2 * EIG_MAXP * (EIG_MAXP + 1) + 64 * EIG_MAXP + 3 * EIG_MAXP) +
                          sizeof(int) * EIG_MAXP + 64;
   const size_t vy_smem = sizeof(Acc) * (EIG_MAXP * EIG_MAXP + RC * EIG_MAXP);
@@ -911,8 +989,8 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, d_active, d_kd, kvec, W);
     A2LS_LAUNCH();
     // no previous basis: jb = 0; R written into H's last rows (discarded)
-    k_orth<TV, T><<<N, ORTH_THREADS, orth_smem, st>>>(h->d_ni, d_vo, P, d_pv, d_active, 0, b, V, W, Rscr, 0, 0,
-                                                  0, nullptr, d_rank);
+    k_orth<TV, T><<<N, ORTH_THREADS, orth_smem_for(gcap_k), st>>>(h->d_ni, d_vo, P, d_pv, d_active, 0, b, V, W,
+                                                                  Rscr, 0, 0, 0, nullptr, d_rank, gcap_k);
     A2LS_LAUNCH();
   };
 
@@ -954,8 +1032,9 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
       // full-space subdomains (j == 0 only): H = V0^T (T V0)
       {
         KTime kt(h, KT_EIG_ORTH, orth_flops);
-        k_orth<TV, T><<<N, ORTH_THREADS, orth_smem, st>>>(h->d_ni, d_vo, P, d_pv, actv, j + 1, b, V, W, H,
-                                                      (j + 1) * b, j * b, (j + 1) * b, d_full, d_rank);
+        const int gcap = (j == 0) ? gcap_f : gcap_k;
+        k_orth<TV, T><<<N, ORTH_THREADS, orth_smem_for(gcap), st>>>(h->d_ni, d_vo, P, d_pv, actv, j + 1, b, V, W, H,
+                                                      (j + 1) * b, j * b, (j + 1) * b, d_full, d_rank, gcap);
         A2LS_LAUNCH();
       }
     }

@@ -236,16 +236,43 @@ SE_HD inline int schur(double* H, int ld, double* Q, int ldq, int m, double hnor
       y = g * (h00 + h11 - s1r - s2r);
       z = g * h21;
     }
+    // Bulge chase.  For k > lo the reflector is built from column k-1 (rows k..k+2), which it maps to
+    // (alpha, 0, 0) exactly; that column is therefore not part of the left update but written
+    // directly, after the barrier that separates every thread's read of (x, y, z) from the writes,
+    // which keeps each step at two barriers.
+    t.sync();  // the shift and deflation reads above precede the first update
     for (int k = lo; k <= hi - 2; ++k) {
       double u1, u2, beta;
       if (make_reflector(x, y, z, u1, u2, beta)) {
-        int c0 = k > lo ? k - 1 : lo;
-        int r1 = (k + 3 <= hi) ? k + 3 : hi;
+        const double alpha = -sgn(sqrt(x * x + y * y + z * z), x);
+        const int c0 = k > lo ? k : lo;
+        const int r1 = (k + 3 <= hi) ? k + 3 : hi;
+        for (int c = c0 + t.lane; c < m; c += t.size) {
+          double d = H[k * ld + c] + u1 * H[(k + 1) * ld + c] + u2 * H[(k + 2) * ld + c];
+          d *= beta;
+          H[k * ld + c] -= d;
+          H[(k + 1) * ld + c] -= d * u1;
+          H[(k + 2) * ld + c] -= d * u2;
+        }
         t.sync();
-        apply_reflector(H, ld, Q, ldq, m, k, 3, u1, u2, beta, c0, r1, t);
         if (k > lo && t.lane == 0) {
+          H[k * ld + k - 1] = alpha;
           H[(k + 1) * ld + k - 1] = 0.0;
           H[(k + 2) * ld + k - 1] = 0.0;
+        }
+        for (int r = t.lane; r <= r1; r += t.size) {
+          double d = H[r * ld + k] + u1 * H[r * ld + k + 1] + u2 * H[r * ld + k + 2];
+          d *= beta;
+          H[r * ld + k] -= d;
+          H[r * ld + k + 1] -= d * u1;
+          H[r * ld + k + 2] -= d * u2;
+        }
+        for (int r = t.lane; r < m; r += t.size) {
+          double d = Q[r * ldq + k] + u1 * Q[r * ldq + k + 1] + u2 * Q[r * ldq + k + 2];
+          d *= beta;
+          Q[r * ldq + k] -= d;
+          Q[r * ldq + k + 1] -= d * u1;
+          Q[r * ldq + k + 2] -= d * u2;
         }
         t.sync();
       }
