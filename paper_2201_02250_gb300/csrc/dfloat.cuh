@@ -76,6 +76,25 @@ __device__ __forceinline__ void df_mac(dfloat& acc, dfloat a, dfloat b) {
 }
 __device__ __forceinline__ dfloat df_normalize(dfloat a) { return df_quick_two_sum(a.hi, a.lo); }
 
+__device__ __forceinline__ dfloat& operator/=(dfloat& a, dfloat b) { return a = a / b; }
+// ordering of normalised values (|lo| <= ulp(hi) / 2)
+__device__ __forceinline__ bool operator<(dfloat a, dfloat b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool operator>(dfloat a, dfloat b) { return b < a; }
+__device__ __forceinline__ bool operator<=(dfloat a, dfloat b) { return !(b < a); }
+__device__ __forceinline__ bool operator>=(dfloat a, dfloat b) { return !(a < b); }
+__device__ __forceinline__ bool operator==(dfloat a, dfloat b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ bool operator!=(dfloat a, dfloat b) { return !(a == b); }
+// scalar helpers used by the small dense eigensolver when it runs in double-float
+__device__ __forceinline__ dfloat se_abs(dfloat a) { return (a.hi < 0.f || (a.hi == 0.f && a.lo < 0.f)) ? -a : a; }
+// square root: the FP32 root refined by one Newton step in double-float
+__device__ __forceinline__ dfloat se_sqrt(dfloat a) {
+  if (!(a.hi > 0.f)) return dfloat(0.f, 0.f);
+  const float s = __fsqrt_rn(a.hi);
+  const dfloat r = a - dfloat(s, 0.f) * dfloat(s, 0.f);
+  return df_quick_two_sum(s, __fdiv_rn(r.hi, 2.f * s));
+}
+__device__ __forceinline__ double se_dbl(dfloat a) { return (double)a; }
+
 __device__ __forceinline__ dfloat shfl_xor(dfloat v, int lane_mask) {
   return dfloat(__shfl_xor_sync(0xffffffffu, v.hi, lane_mask), __shfl_xor_sync(0xffffffffu, v.lo, lane_mask));
 }

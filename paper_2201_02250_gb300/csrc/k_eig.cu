@@ -32,6 +32,13 @@
 
 namespace a2ls {
 
+namespace se {
+template <> struct SeEps<dfloat> {
+  static constexpr double v = 1.4210854715202004e-14;  // 2^-46
+  static constexpr double big = 1e30;                  // within FP32's exponent range
+};
+}  // namespace se
+
 template <class T> struct EAcc;
 template <> struct EAcc<float> { using type = float; };
 template <> struct EAcc<double> { using type = double; };
@@ -637,6 +644,10 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
 // 32 and 256 threads were both slower than 128)
 constexpr int RR_THREADS = 128;
 
+// arithmetic of the Rayleigh-Ritz step: FP64, or double-float when the eigensolve runs in double-float
+template <class T> struct RRType { using type = double; };
+template <> struct RRType<dfloat> { using type = dfloat; };
+
 struct RRParams {
   int sb_krylov;   // s*b in Krylov mode
   int b;           // block size
@@ -645,6 +656,7 @@ struct RRParams {
   int nevmax;      // slots per subdomain in the eigenvalue export
 };
 
+template <class R>
 __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull, const int* nf,
                                 const int* active, const double* H, double* Y, int* ycols, int* zcols,
                                 double* eigout, int* conv, int* st) {
@@ -661,25 +673,26 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
   }
   const int m = full[i] ? mfull[i] : prm.sb_krylov;
   const int ld = m + 1;
-  double* S = sm;                    // m x ld
-  double* Q = S + m * ld;            // m x ld
-  double* xs = Q + m * ld;           // 32 lanes x m
-  double* ys = xs + 32 * m;          // 32 lanes x m
-  double* wr = ys + 32 * m;          // m
+  R* S = reinterpret_cast<R*>(sm);   // m x ld
+  R* Q = S + m * ld;                 // m x ld
+  R* xs = Q + m * ld;                // 32 lanes x m
+  R* ys = xs + 32 * m;               // 32 lanes x m
+  R* vtmp = ys + 32 * m;             // m
+  double* wr = reinterpret_cast<double*>(vtmp + m);  // m
   double* wi = wr + m;               // m
-  double* vtmp = wi + m;             // m
-  int* perm = reinterpret_cast<int*>(vtmp + m);  // m
+  double* mod = wi + m;              // m
+  int* perm = reinterpret_cast<int*>(mod + m);  // m
   const double* Hi = H + (int64_t)i * EIG_MAXP * EIG_MAXP;
   const se::Team team{(int)threadIdx.x, (int)blockDim.x};
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-    S[(e / m) * ld + e % m] = Hi[(e / m) * EIG_MAXP + e % m];
-    Q[(e / m) * ld + e % m] = (e / m == e % m) ? 1.0 : 0.0;
+    S[(e / m) * ld + e % m] = (R)Hi[(e / m) * EIG_MAXP + e % m];
+    Q[(e / m) * ld + e % m] = (R)((e / m == e % m) ? 1.0 : 0.0);
   }
   __syncthreads();
   double snorm = 0.0;
   bool finite = true;
   for (int e = 0; e < m * m; ++e) {
-    const double v = S[(e / m) * ld + e % m];
+    const double v = Hi[(e / m) * EIG_MAXP + e % m];
     finite = finite && isfinite(v);
     snorm = fmax(snorm, fabs(v));
   }
@@ -698,7 +711,7 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
   __syncthreads();
   if (threadIdx.x == 0) {
     se::schur_eigenvalues(S, ld, m, wr, wi);
-    se::order_by_modulus(wr, wi, m, perm, vtmp);
+    se::order_by_modulus(wr, wi, m, perm, mod);
   }
   __syncthreads();
   // plan the columns: walk eigenvalues by modulus, pairs take two columns
@@ -733,17 +746,18 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
     const int pidx = sel_pos[j];
     const int two = sel_two[j];
     const int pstart = (wi[pidx] > 0.0) ? pidx : pidx;  // a pair's +imag member is the first of its block
-    double* x = xs + j * m;
-    double* y = ys + j * m;
+    R* x = xs + j * m;
+    R* y = ys + j * m;
     se::schur_vector(S, ld, m, pstart, wr[pidx], wi[pidx] > 0 ? wi[pidx] : 0.0, x, y, snorm);
     // coefficients in the V basis: Q x, Q y; norms
     double nx = 0.0, ny = 0.0;
     for (int a = 0; a < m; ++a) {
-      double qx = 0.0, qy = 0.0;
+      R qxr = 0.0, qyr = 0.0;
       for (int c = 0; c < m; ++c) {
-        qx += Q[a * ld + c] * x[c];
-        qy += Q[a * ld + c] * y[c];
+        qxr += Q[a * ld + c] * x[c];
+        qyr += Q[a * ld + c] * y[c];
       }
+      const double qx = (double)qxr, qy = (double)qyr;
       Yi[a * EIG_MAXP + sel_col[j]] = qx;
       if (two == 1) Yi[a * EIG_MAXP + sel_col[j] + 1] = qy;
       nx += qx * qx;
@@ -959,11 +973,12 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     return sizeof(double) * (2 * (size_t)gcap + EIG_MAXP) + sizeof(Acc) * 2 * ORC * EIG_MAXP;
   };
   const size_t orth_smem = orth_smem_for(gcap_f);
-  const size_t rr_smem = sizeof(double) * (2 * EIG_MAXP * (EIG_MAXP + 1) + 64 * EIG_MAXP + 3 * EIG_MAXP) +
+  using RT = typename RRType<T>::type;
+  const size_t rr_smem = sizeof(double) * (2 * EIG_MAXP * (EIG_MAXP + 1) + 64 * EIG_MAXP + 4 * EIG_MAXP) +
                          sizeof(int) * EIG_MAXP + 64;
   const size_t vy_smem = sizeof(Acc) * (EIG_MAXP * EIG_MAXP + RC * EIG_MAXP);
   A2LS_CUDA(cudaFuncSetAttribute(k_orth<TV, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orth_smem));
-  A2LS_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_smem));
+  A2LS_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_smem));
   A2LS_CUDA(cudaFuncSetAttribute(k_vy<TV, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vy_smem));
 
   // T applied to V[:, vcol : vcol + p] -> W[:, 0:p]; tri_flops = one triangular half over the active set
@@ -1040,7 +1055,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     }
     {
       KTime kt(h, KT_EIG_RR);
-      k_rayleigh_ritz<<<N, RR_THREADS, rr_smem, st>>>(prm, d_full, d_mfull, d_nf, d_active, H, Y, d_ycols, d_zcols,
+      k_rayleigh_ritz<RT><<<N, RR_THREADS, rr_smem, st>>>(prm, d_full, d_mfull, d_nf, d_active, H, Y, d_ycols, d_zcols,
                                               eigout, d_conv, h->d_status);
       A2LS_LAUNCH();
     }

@@ -31,29 +31,41 @@ struct Team {
   }
 };
 
-SE_HD inline double sgn(double a, double b) { return b >= 0 ? fabs(a) : -fabs(a); }
+// Scalar helpers of the arithmetic R the routines run in (double here; other arithmetics provide
+// their own overloads of se_abs, se_sqrt and se_dbl next to their type and specialise SeEps).
+SE_HD inline double se_abs(double x) { return fabs(x); }
+SE_HD inline double se_sqrt(double x) { return sqrt(x); }
+SE_HD inline double se_dbl(double x) { return x; }
+template <class R> struct SeEps {
+  static constexpr double v = 2.220446049250313e-16;  // machine epsilon of R
+  static constexpr double big = 1e100;                // rescaling threshold of the back substitution
+};
+
+template <class R>
+SE_HD inline R sgn(R a, R b) { return b >= R(0.0) ? se_abs(a) : -se_abs(a); }
 
 // Reduce H (m x m) to upper Hessenberg form, accumulating the orthogonal factor in Q (Q <- Q P).
 // v: scratch of m doubles.
-SE_HD inline void hessenberg(double* H, int ld, double* Q, int ldq, int m, double* v, const Team& t) {
+template <class R>
+SE_HD inline void hessenberg(R* H, int ld, R* Q, int ldq, int m, R* v, const Team& t) {
   for (int k = 0; k + 2 < m; ++k) {
     // Householder vector for x = H[k+1.., k]
-    double nrm2 = 0.0;
+    R nrm2 = 0.0;
     for (int r = k + 1; r < m; ++r) nrm2 += H[r * ld + k] * H[r * ld + k];
-    double nrm = sqrt(nrm2);
+    R nrm = se_sqrt(nrm2);
     if (nrm == 0.0) continue;
-    double x0 = H[(k + 1) * ld + k];
-    double alpha = -sgn(nrm, x0);
+    R x0 = H[(k + 1) * ld + k];
+    R alpha = -sgn(nrm, x0);
     // v = x - alpha e1, scaled so that P = I - 2 v v^T / (v^T v)
-    double vtv = nrm2 - x0 * x0 + (x0 - alpha) * (x0 - alpha);
+    R vtv = nrm2 - x0 * x0 + (x0 - alpha) * (x0 - alpha);
     if (vtv == 0.0) continue;
     t.sync();
     for (int r = k + 1 + t.lane; r < m; r += t.size) v[r] = (r == k + 1) ? (x0 - alpha) : H[r * ld + k];
     t.sync();
-    const double beta = 2.0 / vtv;
+    const R beta = 2.0 / vtv;
     // left: rows k+1.., columns k..m-1
     for (int c = k + t.lane; c < m; c += t.size) {
-      double d = 0.0;
+      R d = 0.0;
       for (int r = k + 1; r < m; ++r) d += v[r] * H[r * ld + c];
       d *= beta;
       for (int r = k + 1; r < m; ++r) H[r * ld + c] -= d * v[r];
@@ -61,11 +73,11 @@ SE_HD inline void hessenberg(double* H, int ld, double* Q, int ldq, int m, doubl
     t.sync();
     // right: all rows, columns k+1..
     for (int r = t.lane; r < m; r += t.size) {
-      double d = 0.0;
+      R d = 0.0;
       for (int c = k + 1; c < m; ++c) d += H[r * ld + c] * v[c];
       d *= beta;
       for (int c = k + 1; c < m; ++c) H[r * ld + c] -= d * v[c];
-      double e = 0.0;
+      R e = 0.0;
       for (int c = k + 1; c < m; ++c) e += Q[r * ldq + c] * v[c];
       e *= beta;
       for (int c = k + 1; c < m; ++c) Q[r * ldq + c] -= e * v[c];
@@ -82,10 +94,11 @@ SE_HD inline void hessenberg(double* H, int ld, double* Q, int ldq, int m, doubl
 // Apply a 3-element (or 2-element when nv == 2) reflector I - beta u u^T with u = (1, u1, u2)
 // to rows k..k+nv-1 of H from the left (columns c0..m-1) and to columns k..k+nv-1 from the
 // right (rows 0..r1) and to Q's columns.
-SE_HD inline void apply_reflector(double* H, int ld, double* Q, int ldq, int m, int k, int nv, double u1,
-                                  double u2, double beta, int c0, int r1, const Team& t) {
+template <class R>
+SE_HD inline void apply_reflector(R* H, int ld, R* Q, int ldq, int m, int k, int nv, R u1, R u2, R beta,
+                                  int c0, int r1, const Team& t) {
   for (int c = c0 + t.lane; c < m; c += t.size) {
-    double d = H[k * ld + c] + u1 * H[(k + 1) * ld + c] + (nv == 3 ? u2 * H[(k + 2) * ld + c] : 0.0);
+    R d = H[k * ld + c] + u1 * H[(k + 1) * ld + c] + (nv == 3 ? u2 * H[(k + 2) * ld + c] : 0.0);
     d *= beta;
     H[k * ld + c] -= d;
     H[(k + 1) * ld + c] -= d * u1;
@@ -93,14 +106,14 @@ SE_HD inline void apply_reflector(double* H, int ld, double* Q, int ldq, int m, 
   }
   t.sync();
   for (int r = t.lane; r <= r1; r += t.size) {
-    double d = H[r * ld + k] + u1 * H[r * ld + k + 1] + (nv == 3 ? u2 * H[r * ld + k + 2] : 0.0);
+    R d = H[r * ld + k] + u1 * H[r * ld + k + 1] + (nv == 3 ? u2 * H[r * ld + k + 2] : 0.0);
     d *= beta;
     H[r * ld + k] -= d;
     H[r * ld + k + 1] -= d * u1;
     if (nv == 3) H[r * ld + k + 2] -= d * u2;
   }
   for (int r = t.lane; r < m; r += t.size) {
-    double d = Q[r * ldq + k] + u1 * Q[r * ldq + k + 1] + (nv == 3 ? u2 * Q[r * ldq + k + 2] : 0.0);
+    R d = Q[r * ldq + k] + u1 * Q[r * ldq + k + 1] + (nv == 3 ? u2 * Q[r * ldq + k + 2] : 0.0);
     d *= beta;
     Q[r * ldq + k] -= d;
     Q[r * ldq + k + 1] -= d * u1;
@@ -110,11 +123,12 @@ SE_HD inline void apply_reflector(double* H, int ld, double* Q, int ldq, int m, 
 }
 
 // Householder reflector mapping (x, y, z) to (alpha, 0, 0): returns beta and u = (1, u1, u2).
-SE_HD inline bool make_reflector(double x, double y, double z, double& u1, double& u2, double& beta) {
-  double nrm = sqrt(x * x + y * y + z * z);
+template <class R>
+SE_HD inline bool make_reflector(R x, R y, R z, R& u1, R& u2, R& beta) {
+  R nrm = se_sqrt(x * x + y * y + z * z);
   if (nrm == 0.0) return false;
-  double alpha = -sgn(nrm, x);
-  double v0 = x - alpha;
+  R alpha = -sgn(nrm, x);
+  R v0 = x - alpha;
   if (v0 == 0.0) return false;
   u1 = y / v0;
   u2 = z / v0;
@@ -123,34 +137,35 @@ SE_HD inline bool make_reflector(double x, double y, double z, double& u1, doubl
 }
 
 // Make a 2x2 diagonal block with real eigenvalues upper triangular by a rotation (rows/cols p, p+1).
-SE_HD inline void split_2x2(double* H, int ld, double* Q, int ldq, int m, int p, const Team& t) {
+template <class R>
+SE_HD inline void split_2x2(R* H, int ld, R* Q, int ldq, int m, int p, const Team& t) {
   t.sync();
-  double a = H[p * ld + p], b = H[p * ld + p + 1], c = H[(p + 1) * ld + p], d = H[(p + 1) * ld + p + 1];
-  double hm = 0.5 * (a - d);
-  double disc = hm * hm + b * c;
+  R a = H[p * ld + p], b = H[p * ld + p + 1], c = H[(p + 1) * ld + p], d = H[(p + 1) * ld + p + 1];
+  R hm = 0.5 * (a - d);
+  R disc = hm * hm + b * c;
   if (disc < 0.0 || c == 0.0) return;
-  // eigenvalue closest to d: lambda = d + (hm +- sqrt(disc)) ... pick the one of larger magnitude shift
-  double sq = sqrt(disc);
-  double lam = 0.5 * (a + d) + (hm >= 0 ? sq : -sq);
+  // eigenvalue closest to d: lambda = d + (hm +- se_sqrt(disc)) ... pick the one of larger magnitude shift
+  R sq = se_sqrt(disc);
+  R lam = 0.5 * (a + d) + (hm >= 0 ? sq : -sq);
   // eigenvector (lam - d, c) of the block; rotation taking it to e1
-  double x = lam - d, y = c;
-  double r = sqrt(x * x + y * y);
+  R x = lam - d, y = c;
+  R r = se_sqrt(x * x + y * y);
   if (r == 0.0) return;
-  double cs = x / r, sn = y / r;
+  R cs = x / r, sn = y / r;
   // rows p, p+1: G^T H
   for (int col = p + t.lane; col < m; col += t.size) {
-    double h1 = H[p * ld + col], h2 = H[(p + 1) * ld + col];
+    R h1 = H[p * ld + col], h2 = H[(p + 1) * ld + col];
     H[p * ld + col] = cs * h1 + sn * h2;
     H[(p + 1) * ld + col] = -sn * h1 + cs * h2;
   }
   t.sync();
   for (int row = t.lane; row <= p + 1; row += t.size) {
-    double h1 = H[row * ld + p], h2 = H[row * ld + p + 1];
+    R h1 = H[row * ld + p], h2 = H[row * ld + p + 1];
     H[row * ld + p] = cs * h1 + sn * h2;
     H[row * ld + p + 1] = -sn * h1 + cs * h2;
   }
   for (int row = t.lane; row < m; row += t.size) {
-    double q1 = Q[row * ldq + p], q2 = Q[row * ldq + p + 1];
+    R q1 = Q[row * ldq + p], q2 = Q[row * ldq + p + 1];
     Q[row * ldq + p] = cs * q1 + sn * q2;
     Q[row * ldq + p + 1] = -sn * q1 + cs * q2;
   }
@@ -159,19 +174,20 @@ SE_HD inline void split_2x2(double* H, int ld, double* Q, int ldq, int m, int p,
   t.sync();
 }
 
-// Francis double-shift QR on an upper Hessenberg H, full Schur form, Q accumulated.
+// Francis R-shift QR on an upper Hessenberg H, full Schur form, Q accumulated.
 // A subdiagonal entry is neglected when it is below eps times its two diagonal
 // neighbours or below eps times hnorm (the largest entry of the input), which keeps
 // clusters of eigenvalues near zero from stalling the iteration; the result is
 // backward stable relative to hnorm.  Returns 0 on success, -1 on no convergence.
-SE_HD inline int schur(double* H, int ld, double* Q, int ldq, int m, double hnorm, const Team& t) {
-  const double eps = 2.220446049250313e-16;
+template <class R>
+SE_HD inline int schur(R* H, int ld, R* Q, int ldq, int m, double hnorm_, const Team& t) {
+  const R eps = R(SeEps<R>::v), hnorm = R(hnorm_);
   int hi = m - 1, iter = 0, total = 0;
   while (hi >= 0) {
     int lo = hi;
     while (lo > 0) {
-      double s = fabs(H[(lo - 1) * ld + lo - 1]) + fabs(H[lo * ld + lo]);
-      const double sub = fabs(H[lo * ld + lo - 1]);
+      R s = se_abs(H[(lo - 1) * ld + lo - 1]) + se_abs(H[lo * ld + lo]);
+      const R sub = se_abs(H[lo * ld + lo - 1]);
       if (sub <= eps * s || sub <= eps * hnorm) break;
       --lo;
     }
@@ -195,11 +211,11 @@ SE_HD inline int schur(double* H, int ld, double* Q, int ldq, int m, double hnor
     if (++total > 60 * m) return -1;
     // Shifts: the eigenvalues of the trailing 2x2 block (a real pair is replaced by its member
     // closer to the last diagonal entry, used twice), or an exceptional pair every 11th step.
-    double s1r, s1i, s2r, s2i;
+    R s1r, s1i, s2r, s2i;
     {
-      double a, b, c, d;
+      R a, b, c, d;
       if (iter % 11 == 10) {
-        const double w = fabs(H[hi * ld + hi - 1]) + fabs(H[(hi - 1) * ld + hi - 2]);
+        const R w = se_abs(H[hi * ld + hi - 1]) + se_abs(H[(hi - 1) * ld + hi - 2]);
         a = 0.75 * w + H[hi * ld + hi];
         b = -0.4375 * w;
         c = w;
@@ -210,28 +226,28 @@ SE_HD inline int schur(double* H, int ld, double* Q, int ldq, int m, double hnor
         c = H[hi * ld + hi - 1];
         d = H[hi * ld + hi];
       }
-      const double hm = 0.5 * (a - d);
-      const double disc = hm * hm + b * c;
-      const double mean = 0.5 * (a + d);
+      const R hm = 0.5 * (a - d);
+      const R disc = hm * hm + b * c;
+      const R mean = 0.5 * (a + d);
       if (disc >= 0.0) {
-        const double sq = sqrt(disc);
-        const double r1 = mean + sq, r2 = mean - sq;
-        const double sh = (fabs(r1 - d) <= fabs(r2 - d)) ? r1 : r2;
+        const R sq = se_sqrt(disc);
+        const R r1 = mean + sq, r2 = mean - sq;
+        const R sh = (se_abs(r1 - d) <= se_abs(r2 - d)) ? r1 : r2;
         s1r = s2r = sh;
         s1i = s2i = 0.0;
       } else {
         s1r = s2r = mean;
-        s1i = sqrt(-disc);
+        s1i = se_sqrt(-disc);
         s2i = -s1i;
       }
     }
     // first column of (H - s1)(H - s2), formed from differences to avoid cancellation
-    double x, y, z;
+    R x, y, z;
     {
-      const double h00 = H[lo * ld + lo], h01 = H[lo * ld + lo + 1], h10 = H[(lo + 1) * ld + lo];
-      const double h11 = H[(lo + 1) * ld + lo + 1], h21 = H[(lo + 2) * ld + lo + 1];
-      const double sc = fabs(h00 - s2r) + fabs(s2i) + fabs(h10);
-      const double g = (sc > 0.0) ? h10 / sc : 0.0;
+      const R h00 = H[lo * ld + lo], h01 = H[lo * ld + lo + 1], h10 = H[(lo + 1) * ld + lo];
+      const R h11 = H[(lo + 1) * ld + lo + 1], h21 = H[(lo + 2) * ld + lo + 1];
+      const R sc = se_abs(h00 - s2r) + se_abs(s2i) + se_abs(h10);
+      const R g = (sc > 0.0) ? h10 / sc : 0.0;
       x = g * h01 + (h00 - s1r) * ((h00 - s2r) / (sc > 0.0 ? sc : 1.0)) - s1i * (s2i / (sc > 0.0 ? sc : 1.0));
       y = g * (h00 + h11 - s1r - s2r);
       z = g * h21;
@@ -242,13 +258,13 @@ SE_HD inline int schur(double* H, int ld, double* Q, int ldq, int m, double hnor
     // which keeps each step at two barriers.
     t.sync();  // the shift and deflation reads above precede the first update
     for (int k = lo; k <= hi - 2; ++k) {
-      double u1, u2, beta;
+      R u1, u2, beta;
       if (make_reflector(x, y, z, u1, u2, beta)) {
-        const double alpha = -sgn(sqrt(x * x + y * y + z * z), x);
+        const R alpha = -sgn(se_sqrt(x * x + y * y + z * z), x);
         const int c0 = k > lo ? k : lo;
         const int r1 = (k + 3 <= hi) ? k + 3 : hi;
         for (int c = c0 + t.lane; c < m; c += t.size) {
-          double d = H[k * ld + c] + u1 * H[(k + 1) * ld + c] + u2 * H[(k + 2) * ld + c];
+          R d = H[k * ld + c] + u1 * H[(k + 1) * ld + c] + u2 * H[(k + 2) * ld + c];
           d *= beta;
           H[k * ld + c] -= d;
           H[(k + 1) * ld + c] -= d * u1;
@@ -261,14 +277,14 @@ SE_HD inline int schur(double* H, int ld, double* Q, int ldq, int m, double hnor
           H[(k + 2) * ld + k - 1] = 0.0;
         }
         for (int r = t.lane; r <= r1; r += t.size) {
-          double d = H[r * ld + k] + u1 * H[r * ld + k + 1] + u2 * H[r * ld + k + 2];
+          R d = H[r * ld + k] + u1 * H[r * ld + k + 1] + u2 * H[r * ld + k + 2];
           d *= beta;
           H[r * ld + k] -= d;
           H[r * ld + k + 1] -= d * u1;
           H[r * ld + k + 2] -= d * u2;
         }
         for (int r = t.lane; r < m; r += t.size) {
-          double d = Q[r * ldq + k] + u1 * Q[r * ldq + k + 1] + u2 * Q[r * ldq + k + 2];
+          R d = Q[r * ldq + k] + u1 * Q[r * ldq + k + 1] + u2 * Q[r * ldq + k + 2];
           d *= beta;
           Q[r * ldq + k] -= d;
           Q[r * ldq + k + 1] -= d * u1;
@@ -282,10 +298,10 @@ SE_HD inline int schur(double* H, int ld, double* Q, int ldq, int m, double hnor
     }
     // final 2-element reflector on rows hi-1, hi
     {
-      double u1, u2, beta;
-      if (make_reflector(x, y, 0.0, u1, u2, beta)) {
+      R u1, u2, beta;
+      if (make_reflector<R>(x, y, R(0.0), u1, u2, beta)) {
         t.sync();
-        apply_reflector(H, ld, Q, ldq, m, hi - 1, 2, u1, 0.0, beta, hi - 2, hi, t);
+        apply_reflector<R>(H, ld, Q, ldq, m, hi - 1, 2, u1, R(0.0), beta, hi - 2, hi, t);
         if (t.lane == 0) H[hi * ld + hi - 2] = 0.0;
         t.sync();
       }
@@ -295,27 +311,28 @@ SE_HD inline int schur(double* H, int ld, double* Q, int ldq, int m, double hnor
 }
 
 // Eigenvalues of the quasi-triangular S: wr[j], wi[j] (a complex pair occupies j, j+1 with wi[j] > 0).
-SE_HD inline void schur_eigenvalues(const double* S, int ld, int m, double* wr, double* wi) {
+template <class R>
+SE_HD inline void schur_eigenvalues(const R* S, int ld, int m, double* wr, double* wi) {
   int j = 0;
   while (j < m) {
     if (j + 1 < m && S[(j + 1) * ld + j] != 0.0) {
-      double a = S[j * ld + j], b = S[j * ld + j + 1], c = S[(j + 1) * ld + j], d = S[(j + 1) * ld + j + 1];
-      double hm = 0.5 * (a - d);
-      double disc = hm * hm + b * c;
-      double re = 0.5 * (a + d);
-      double im = sqrt(fabs(disc));
+      R a = S[j * ld + j], b = S[j * ld + j + 1], c = S[(j + 1) * ld + j], d = S[(j + 1) * ld + j + 1];
+      R hm = 0.5 * (a - d);
+      R disc = hm * hm + b * c;
+      R re = 0.5 * (a + d);
+      R im = se_sqrt(se_abs(disc));
       if (disc >= 0.0) {  // not split (should not happen after split_2x2); report real values
-        wr[j] = re + im;
-        wr[j + 1] = re - im;
+        wr[j] = se_dbl(re + im);
+        wr[j + 1] = se_dbl(re - im);
         wi[j] = wi[j + 1] = 0.0;
       } else {
-        wr[j] = wr[j + 1] = re;
-        wi[j] = im;
-        wi[j + 1] = -im;
+        wr[j] = wr[j + 1] = se_dbl(re);
+        wi[j] = se_dbl(im);
+        wi[j + 1] = -se_dbl(im);
       }
       j += 2;
     } else {
-      wr[j] = S[j * ld + j];
+      wr[j] = se_dbl(S[j * ld + j]);
       wi[j] = 0.0;
       j += 1;
     }
@@ -324,9 +341,11 @@ SE_HD inline void schur_eigenvalues(const double* S, int ld, int m, double* wr, 
 
 // Eigenvector of the quasi-triangular S for the eigenvalue at position p (real: x; complex
 // pair starting at p: x + i y).  x, y have m entries; entries above p are filled, below zero.
-SE_HD inline void schur_vector(const double* S, int ld, int m, int p, double lr, double li, double* x,
-                               double* y, double snorm) {
-  const double small = 1e-300 + 2.220446049250313e-16 * snorm;
+template <class R>
+SE_HD inline void schur_vector(const R* S, int ld, int m, int p, double lr_, double li_, R* x, R* y,
+                               double snorm) {
+  const R small = R(1e-300 + SeEps<R>::v * snorm);
+  const R lr = R(lr_), li = R(li_);
   for (int q = 0; q < m; ++q) {
     x[q] = 0.0;
     y[q] = 0.0;
@@ -337,7 +356,7 @@ SE_HD inline void schur_vector(const double* S, int ld, int m, int p, double lr,
     top = p - 1;
   } else {
     // block rows p, p+1: (a - lambda) x_p + b x_{p+1} = 0 -> x_p = b, x_{p+1} = lambda - a
-    double a = S[p * ld + p], b = S[p * ld + p + 1];
+    R a = S[p * ld + p], b = S[p * ld + p + 1];
     x[p] = b;
     y[p] = 0.0;
     x[p + 1] = lr - a;
@@ -349,43 +368,43 @@ SE_HD inline void schur_vector(const double* S, int ld, int m, int p, double lr,
   while (q >= 0) {
     if (q > 0 && S[q * ld + q - 1] != 0.0) {
       // 2x2 block rows q-1, q: solve (S_blk - lambda I) [u; w] = -rhs
-      double r1r = 0, r1i = 0, r2r = 0, r2i = 0;
+      R r1r = 0, r1i = 0, r2r = 0, r2i = 0;
       for (int c = q + 1; c <= last; ++c) {
         r1r += S[(q - 1) * ld + c] * x[c];
         r1i += S[(q - 1) * ld + c] * y[c];
         r2r += S[q * ld + c] * x[c];
         r2i += S[q * ld + c] * y[c];
       }
-      double a11r = S[(q - 1) * ld + q - 1] - lr, a11i = -li;
-      double a12 = S[(q - 1) * ld + q], a21 = S[q * ld + q - 1];
-      double a22r = S[q * ld + q] - lr, a22i = -li;
+      R a11r = S[(q - 1) * ld + q - 1] - lr, a11i = -li;
+      R a12 = S[(q - 1) * ld + q], a21 = S[q * ld + q - 1];
+      R a22r = S[q * ld + q] - lr, a22i = -li;
       // det = a11*a22 - a12*a21 (complex)
-      double dr = a11r * a22r - a11i * a22i - a12 * a21;
-      double di = a11r * a22i + a11i * a22r;
-      double dn = dr * dr + di * di;
+      R dr = a11r * a22r - a11i * a22i - a12 * a21;
+      R di = a11r * a22i + a11i * a22r;
+      R dn = dr * dr + di * di;
       if (dn < small * small) {
         dr = small;
         di = 0.0;
         dn = small * small;
       }
       // [u; w] = -inv(A) r,  inv(A) = [a22 -a12; -a21 a11] / det
-      double ur = -(a22r * r1r - a22i * r1i - a12 * r2r);
-      double ui = -(a22r * r1i + a22i * r1r - a12 * r2i);
-      double wr_ = -(-a21 * r1r + a11r * r2r - a11i * r2i);
-      double wi_ = -(-a21 * r1i + a11r * r2i + a11i * r2r);
+      R ur = -(a22r * r1r - a22i * r1i - a12 * r2r);
+      R ui = -(a22r * r1i + a22i * r1r - a12 * r2i);
+      R wr_ = -(-a21 * r1r + a11r * r2r - a11i * r2i);
+      R wi_ = -(-a21 * r1i + a11r * r2i + a11i * r2r);
       x[q - 1] = (ur * dr + ui * di) / dn;
       y[q - 1] = (ui * dr - ur * di) / dn;
       x[q] = (wr_ * dr + wi_ * di) / dn;
       y[q] = (wi_ * dr - wr_ * di) / dn;
       q -= 2;
     } else {
-      double rr = 0, ri = 0;
+      R rr = 0, ri = 0;
       for (int c = q + 1; c <= last; ++c) {
         rr += S[q * ld + c] * x[c];
         ri += S[q * ld + c] * y[c];
       }
-      double dr = S[q * ld + q] - lr, di = -li;
-      double dn = dr * dr + di * di;
+      R dr = S[q * ld + q] - lr, di = -li;
+      R dn = dr * dr + di * di;
       if (dn < small * small) {
         dr = small;
         di = 0.0;
@@ -396,9 +415,12 @@ SE_HD inline void schur_vector(const double* S, int ld, int m, int p, double lr,
       q -= 1;
     }
     // rescale to avoid overflow
-    double mx = 0.0;
-    for (int c = (q + 1 > 0 ? q + 1 : 0); c <= last; ++c) mx = fmax(mx, fabs(x[c]) + fabs(y[c]));
-    if (mx > 1e100) {
+    R mx = 0.0;
+    for (int c = (q + 1 > 0 ? q + 1 : 0); c <= last; ++c) {
+      const R v = se_abs(x[c]) + se_abs(y[c]);
+      if (v > mx) mx = v;
+    }
+    if (mx > R(SeEps<R>::big)) {
       for (int c = 0; c <= last; ++c) {
         x[c] /= mx;
         y[c] /= mx;
