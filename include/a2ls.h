@@ -53,8 +53,11 @@ typedef enum {
 /* Precision of the local factors of A_ii and of the local solves of the apply
  * (a2ls_options::precision), and of the factorisation of A~_ii and the local
  * eigensolves (a2ls_options::eig_precision).  The SpMV, the GMRES
- * orthogonalisation, the residual, the small Rayleigh-Ritz problems and the
- * coarse operator are always FP64.
+ * orthogonalisation, the residual and the coarse operator and its factorisation
+ * are always FP64; the small Rayleigh-Ritz problems run in FP64, or in
+ * double-float with a double-float eigensolve; the mixed form (precision FP32)
+ * forms the explicit inverse of the coarse operator from its FP64 factors in
+ * double-float.
  * A2LS_FP32X2 (eigensolve only) is double-float arithmetic: each value is an unevaluated sum
  * of two FP32 numbers (48-bit significand, FP32 exponent range), computed on the FP32 pipe. */
 enum { A2LS_FP64 = 0, A2LS_FP32 = 1, A2LS_FP32X2 = 2 };

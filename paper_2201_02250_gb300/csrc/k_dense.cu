@@ -160,11 +160,28 @@ __device__ __forceinline__ void cta_gemm_n8(const T* __restrict__ A, int64_t lda
 // ---------------------------------------------------------------------------
 // batched LU without pivoting
 // ---------------------------------------------------------------------------
+// Four consecutive shared-memory values as vector loads (the address is 16-byte aligned: rows of the
+// staged tiles are TS = 68 elements long and the column offset is a multiple of 4).
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void load4(const dfloat* p, dfloat (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 2);
+  v[0] = dfloat(a.x, a.y); v[1] = dfloat(a.z, a.w); v[2] = dfloat(b.x, b.y); v[3] = dfloat(b.z, b.w);
+}
+
 // Tile product with register prefetch: acc(64 x 64) += A(0:64, 0:K) B(0:K, 0:64), 256 threads,
 // thread (ty, tx) owns rows ty*4.. and columns tx*4..; fa(m, k) and fb(k, c) fetch operand elements
 // (zero outside the operands).  The next TGK-deep slab is loaded into registers while the current
-// one is multiplied from shared memory.
+// one is multiplied from shared memory, where each k holds a row of TS elements so that a thread's
+// four operands are one or two vector loads and the 16 threads of a row group read disjoint banks.
 constexpr int TGK = 16;
+constexpr int TS = 68;
 template <class Acc, class FA, class FB>
 __device__ __forceinline__ void tile_gemm(FA fa, FB fb, int K, Acc (&acc)[4][4], Acc* sA, Acc* sB) {
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -182,8 +199,8 @@ __device__ __forceinline__ void tile_gemm(FA fa, FB fb, int K, Acc (&acc)[4][4],
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int e = tid + u * 256;
-      sA[(e % TGK) * 65 + e / TGK] = ra[u];
-      sB[(e / 64) * 65 + e % 64] = rb[u];
+      sA[(e % TGK) * TS + e / TGK] = ra[u];
+      sB[(e / 64) * TS + e % 64] = rb[u];
     }
     __syncthreads();
     if (k0 + TGK < K) fetch(k0 + TGK);
@@ -191,11 +208,8 @@ __device__ __forceinline__ void tile_gemm(FA fa, FB fb, int K, Acc (&acc)[4][4],
 #pragma unroll 8
     for (int k = 0; k < kk; ++k) {
       Acc a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        a[u] = sA[k * 65 + ty * 4 + u];
-        b[u] = sB[k * 65 + tx * 4 + u];
-      }
+      load4(sA + k * TS + ty * 4, a);
+      load4(sB + k * TS + tx * 4, b);
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -213,7 +227,7 @@ __device__ __forceinline__ void tile_gemm(FA fa, FB fb, int K, Acc (&acc)[4][4],
 // aligned to the 64-grid of the block-inverted storage (whose diagonal tiles are inverted afterwards).
 // phase: -1 all columns; 0 the interior columns [0, n_I) (the trailing Schur complement on the
 // overlap rows is left in place); 1 the remaining columns [n_I, n).
-constexpr size_t lu_smem_elems() { return 2 * (size_t)TB * 65 + 2 * (size_t)TGK * 65; }
+constexpr size_t lu_smem_elems() { return 2 * (size_t)TB * 65 + 2 * (size_t)TGK * TS; }
 
 template <class T>
 __global__ void __launch_bounds__(256, 2) k_lu(int N, const int* ni, const int* ld, const int64_t* foff,
@@ -224,8 +238,8 @@ __global__ void __launch_bounds__(256, 2) k_lu(int N, const int* ni, const int* 
   extern __shared__ __align__(16) unsigned char lu_smem_raw[];
   Acc* Dm = reinterpret_cast<Acc*>(lu_smem_raw);  // 64 x 65: the diagonal block, factored in place
   Acc* Iv = Dm + TB * 65;                         // 64 x 65: inv(L11) strictly below, inv(U11) on/above
-  Acc* sA = Iv + TB * 65;                         // TGK x 65
-  Acc* sB = sA + TGK * 65;                        // TGK x 65
+  Acc* sA = Iv + TB * 65;                         // TGK x TS (16-byte aligned: 2 * 64 * 65 is even)
+  Acc* sB = sA + TGK * TS;                        // TGK x TS
   const int i = sched ? sched[blockIdx.x] : blockIdx.x;
   const int n = ni[i];
   const int64_t L = ld[i];
@@ -876,10 +890,12 @@ __global__ void __launch_bounds__(256) k_e_update(double* A, int n, int64_t ld, 
 }
 
 // X = inv(U) inv(L) I, one 32-column slab per CTA (F holds the block-inverted LU)
+// Acc: the arithmetic of the substitutions (FP64, or double-float in the mixed form); F and X are FP64.
 constexpr int EINV_W = 32;
+template <class Acc>
 __global__ void __launch_bounds__(256) k_e_inverse(const double* F, int n, int64_t ld, double* X, int64_t ldx,
                                                    int band) {
-  __shared__ double sA[GK * 65], sB[GK * 33];
+  __shared__ Acc sA[GK * 65], sB[GK * 33];
   const int c0 = blockIdx.x * EINV_W;
   const int pc = min(EINV_W, n - c0);
   const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
@@ -896,36 +912,47 @@ __global__ void __launch_bounds__(256) k_e_inverse(const double* F, int n, int64
       const int b = pass == 0 ? bb : nb - 1 - bb;
       if (pass == 0 && b < bstart) continue;
       const int r0 = b * TB, tb = min(TB, n - r0);
-      double acc[2][4] = {};
+      Acc acc[2][4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0;
       if (pass == 0) {
         const int k0 = max(bstart * TB, r0 - band);  // L(r, c) = 0 for c < r - band
         if (r0 > k0)
-          cta_gemm_n32<double, double>(F + (int64_t)r0 * ld + k0, ld, Xs + (int64_t)k0 * ldx, ldx, tb, pc, r0 - k0,
-                                       0, acc, sA, sB);
+          cta_gemm_n32<double, Acc>(F + (int64_t)r0 * ld + k0, ld, Xs + (int64_t)k0 * ldx, ldx, tb, pc, r0 - k0,
+                                    0, acc, sA, sB);
       } else {
         const int e0 = r0 + tb;
         const int e1 = min(n, r0 + tb + band);       // U(r, c) = 0 for c > r + band
         if (e0 < e1)
-          cta_gemm_n32<double, double>(F + (int64_t)r0 * ld + e0, ld, Xs + (int64_t)e0 * ldx, ldx, tb, pc, e1 - e0,
-                                       0, acc, sA, sB);
+          cta_gemm_n32<double, Acc>(F + (int64_t)r0 * ld + e0, ld, Xs + (int64_t)e0 * ldx, ldx, tb, pc, e1 - e0,
+                                    0, acc, sA, sB);
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const int r = ty * 2 + u, c = tx * 4 + v;
-          if (r < tb && c < pc) Xs[(int64_t)(r0 + r) * ldx + c] -= acc[u][v];
+          if (r < tb && c < pc) {
+            double* x = Xs + (int64_t)(r0 + r) * ldx + c;
+            *x = (double)((Acc)*x - acc[u][v]);
+          }
         }
       __syncthreads();
-      double acc2[2][4] = {};
-      cta_gemm_n32<double, double>(F + (int64_t)r0 * ld + r0, ld, Xs + (int64_t)r0 * ldx, ldx, tb, pc, tb,
-                                   pass == 0 ? 1 : 2, acc2, sA, sB);
+      Acc acc2[2][4];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc2[u][v] = 0;
+      cta_gemm_n32<double, Acc>(F + (int64_t)r0 * ld + r0, ld, Xs + (int64_t)r0 * ldx, ldx, tb, pc, tb,
+                                pass == 0 ? 1 : 2, acc2, sA, sB);
 #pragma unroll
       for (int u = 0; u < 2; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const int r = ty * 2 + u, c = tx * 4 + v;
-          if (r < tb && c < pc) Xs[(int64_t)(r0 + r) * ldx + c] = acc2[u][v];
+          if (r < tb && c < pc) Xs[(int64_t)(r0 + r) * ldx + c] = (double)finish(acc2[u][v]);
         }
       __syncthreads();
     }
@@ -954,7 +981,11 @@ void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv,
   }
   }
   KTime kt2(h, KT_COARSE_INV, 4.0 / 3.0 * (double)n * n * n);
-  k_e_inverse<<<ceil_div(n, EINV_W), 256, 0, st>>>(E, n, ld, Einv, ld, band);
+  // the mixed form forms the inverse from the FP64 factors in double-float arithmetic
+  if (h->opt.precision == A2LS_FP32)
+    k_e_inverse<dfloat><<<ceil_div(n, EINV_W), 256, 0, st>>>(E, n, ld, Einv, ld, band);
+  else
+    k_e_inverse<double><<<ceil_div(n, EINV_W), 256, 0, st>>>(E, n, ld, Einv, ld, band);
   A2LS_LAUNCH();
 }
 
