@@ -342,7 +342,6 @@ int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int
     if (o.precision != A2LS_FP64 && o.precision != A2LS_FP32) fail(A2LS_ERR_ARG, "unknown precision %d", o.precision);
     if (o.variant < 0 || o.variant > A2LS_ONE_LEVEL_ASM) fail(A2LS_ERR_ARG, "unknown variant %d", o.variant);
     if (o.pou != A2LS_POU_BOOLEAN && o.pou != A2LS_POU_MULTIPLICITY) fail(A2LS_ERR_ARG, "unknown partition of unity %d", o.pou);
-    if (o.tau > 0) fail(A2LS_ERR_ARG, "threshold selection (tau > 0) is not supported yet; use a fixed nev");
     h = new a2ls_handle();
     h->opt = o;
     h->st = static_cast<cudaStream_t>(o.stream);

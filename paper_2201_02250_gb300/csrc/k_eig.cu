@@ -654,6 +654,7 @@ struct RRParams {
   int s;           // block steps
   double tol;
   int nevmax;      // slots per subdomain in the eigenvalue export
+  double tau;      // > 0: keep only |lambda| > 1 / tau (Eq. 3.2), at most nev
 };
 
 template <class R>
@@ -724,6 +725,9 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
       const int pidx = perm[a];
       if (wi[pidx] < 0.0) continue;  // the partner of a pair already taken
       const int two = (wi[pidx] > 0.0) ? 1 : 0;
+      // threshold selection (Eq. 3.2): the wanted set ends before the first |lambda| <= 1/tau; the
+      // rest of the block is still filled, it carries the restart
+      if (prm.tau > 0.0 && zc < 0 && !(mod[pidx] * prm.tau > 1.0)) zc = col;
       sel_pos[nsel] = pidx;
       sel_col[nsel] = col;
       sel_two[nsel] = (two && col + 1 < bc) ? 1 : (two ? 2 : 0);  // 2: pair truncated to its real part
@@ -1023,7 +1027,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   orthonormalize_W_into_V0();
   A2LS_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * N * P * P, st));
 
-  RRParams prm{s * b, b, s, tol, nevmax};
+  RRParams prm{s * b, b, s, tol, nevmax, h->opt.tau};
   const int max_cycles = h->opt.eig_max_cycles > 0 ? h->opt.eig_max_cycles : 60;
   std::vector<int> conv(N, 0), cycles(N, 0);
   int cycle = 0;

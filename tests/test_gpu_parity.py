@@ -412,3 +412,57 @@ def test_c2_full_size(c2, precision):
         z = apply_gpu(P, prob.A @ phi)
         assert np.linalg.norm(z - phi) <= tol * np.linalg.norm(phi)
     P.close()
+
+
+# ---------------------------------------------------------------------------
+# threshold selection (Eq. 3.2 with tau)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("eigp", ["fp64", "fp32x2"])
+@pytest.mark.parametrize("name,tau", [("hpd24", 0.3), ("c1", 0.3), ("c1", 0.1), ("conv40", 0.3)])
+def test_tau_selection_matches_oracle(name, tau, eigp):
+    """Keep |lambda| > 1/tau (at most nev): per-subdomain counts and spans as the oracle's, away
+    from ambiguous cuts; subdomains may keep no vector at all."""
+    prob = {"hpd24": lambda: pde.tiny_hpd_dd(m=24, nb=3, overlap=1, nev=10),
+            "c1": pde.config_c1,
+            "conv40": lambda: pde.tiny_conv_diff(m=40, nb=3, overlap=2, nev=12)}[name]()
+    ref = O.setup(prob.A, prob.part, prob.overlap, prob.nev, tau=tau)
+    P = setup_gpu(prob, tau=tau, eig_precision=eigp)
+    Wg = P.coarse_basis()
+    checked = 0
+    for wg, wo, e in zip(Wg, ref.coarse.W, ref.eig):
+        lam = np.abs(e.eigvals)
+        if np.any(np.abs(lam - 1.0 / tau) < 0.01 / tau):
+            continue  # an eigenvalue within 1 % of the threshold
+        k = len(e.selected)
+        if 0 < k < len(lam) and lam[k - 1] < 1.01 * lam[k]:
+            continue
+        assert wg.shape[1] == wo.shape[1]
+        if wo.shape[1]:
+            assert angles(wg, wo).max() < 1e-6
+        checked += 1
+    assert checked >= len(Wg) // 2
+    assert P.sizes()["n0"] == sum(w.shape[1] for w in Wg)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    it, rr, ok = P.solve(dev(prob.b), x, 1e-8)
+    true = np.linalg.norm(prob.b - prob.A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
+    assert ok and true <= 1e-8
+    res = O.gmres(prob.A, lambda v: O.apply(ref, v), prob.b, rtol=1e-8)
+    assert abs(it - res.iters) <= 1
+    P.close()
+
+
+def test_condition_bound_on_gpu_coarse_space():
+    """Section 3.2's bound kappa(M^{-1} A) <= (k_c+1)(2 + (2k_c+1) k_m / tau) for the additive ASM
+    two-level operator built from the GPU's own tau-selected coarse space (M^{-1} applied on the GPU)."""
+    for seed, tau in ((21, 0.3), (22, 0.1), (23, 0.5)):
+        P0 = pde.tiny_hpd_dd(m=10, nb=3, overlap=1, seed=seed, contrast=1e4)
+        P = setup_gpu(P0, tau=tau, variant="additive_asm")
+        Ad = P0.A.toarray()
+        MA = np.stack([apply_gpu(P, Ad[:, j]) for j in range(P0.n)], axis=1)
+        ev = np.linalg.eigvals(MA)
+        assert np.max(np.abs(ev.imag)) < 1e-8 * np.max(ev.real)
+        kappa = np.max(ev.real) / np.min(ev.real)
+        subs = O.overlapping_subdomains(P0.A, P0.part, 1)
+        bound = O.condition_bound(subs, P0.n, tau)
+        assert kappa <= bound, (seed, kappa, bound)
+        P.close()
