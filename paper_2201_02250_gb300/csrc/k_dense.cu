@@ -421,32 +421,12 @@ template void schur_copy<dfloat, float>(a2ls_handle*, const dfloat*, float*, con
 // ---------------------------------------------------------------------------
 // inversion of the diagonal tiles (in place): inv(L_bb) strictly lower, inv(U_bb) upper
 // ---------------------------------------------------------------------------
-// Column c of inv(L_bb) (unit lower) and of inv(U_bb) (upper) from a factored tile held in
-// shared memory; together they fill column c of the block-inverted tile.
-__device__ __forceinline__ void tile_inverse_column(const double (*t)[TB + 1], int tb, int c, double* col) {
-  double x[TB];
-  // inv(L): x_c = 1, x_r = -sum_{q=c}^{r-1} L[r][q] x_q for r > c
-  x[c] = 1.0;
-  for (int r = c + 1; r < tb; ++r) {
-    double s = 0.0;
-    for (int q = c; q < r; ++q) s -= t[r][q] * x[q];
-    x[r] = s;
-    col[r] = s;
-  }
-  // inv(U): x_c = 1/U_cc, x_r = -(sum_{q=r+1}^{c} U[r][q] x_q) / U[r][r] for r < c
-  x[c] = 1.0 / t[c][c];
-  col[c] = x[c];
-  for (int r = c - 1; r >= 0; --r) {
-    double s = 0.0;
-    for (int q = r + 1; q <= c; ++q) s -= t[r][q] * x[q];
-    x[r] = s / t[r][r];
-    col[r] = x[r];
-  }
-}
-
+// one CTA of 128 threads per (subdomain, diagonal tile): threads 0..63 form the columns of inv(L_bb)
+// below the diagonal, threads 64..127 those of inv(U_bb), in FP64 in shared memory
 template <class T>
-__global__ void k_invert_tiles(const int* ni, const int* ld, const int64_t* foff, T* fac) {
-  __shared__ double tile[TB][TB + 1];
+__global__ void __launch_bounds__(2 * TB) k_invert_tiles(const int* ni, const int* ld, const int64_t* foff,
+                                                         T* fac) {
+  __shared__ double t[TB][TB + 1], s[TB][TB + 1];
   const int i = blockIdx.x, b = blockIdx.y;
   const int n = ni[i];
   const int r0 = b * TB;
@@ -454,19 +434,32 @@ __global__ void k_invert_tiles(const int* ni, const int* ld, const int64_t* foff
   const int tb = min(TB, n - r0);
   const int64_t L = ld[i];
   T* A = fac + foff[i] + (int64_t)r0 * L + r0;
-  for (int e = threadIdx.x; e < tb * tb; e += blockDim.x) tile[e / tb][e % tb] = (double)A[(e / tb) * L + e % tb];
+  for (int e = threadIdx.x; e < tb * tb; e += blockDim.x) t[e / tb][e % tb] = (double)A[(e / tb) * L + e % tb];
   __syncthreads();
-  const int c = threadIdx.x;
-  if (c < tb) {
-    double col[TB];
-    tile_inverse_column(tile, tb, c, col);
-    for (int r = 0; r < tb; ++r) A[r * L + c] = (T)col[r];
+  const int c = threadIdx.x & (TB - 1);
+  if (threadIdx.x < TB && c < tb) {
+    // inv(L) (unit lower), column c below the diagonal: x_r = -(L[r][c] + sum_{q=c+1}^{r-1} L[r][q] x_q)
+    for (int r = c + 1; r < tb; ++r) {
+      double v = t[r][c];
+      for (int q = c + 1; q < r; ++q) v += t[r][q] * s[q][c];
+      s[r][c] = -v;
+    }
+  } else if (threadIdx.x >= TB && c < tb) {
+    // inv(U), column c on and above the diagonal
+    s[c][c] = 1.0 / t[c][c];
+    for (int r = c - 1; r >= 0; --r) {
+      double v = 0.0;
+      for (int q = r + 1; q <= c; ++q) v += t[r][q] * s[q][c];
+      s[r][c] = -v / t[r][r];
+    }
   }
+  __syncthreads();
+  for (int e = threadIdx.x; e < tb * tb; e += blockDim.x) A[(e / tb) * L + e % tb] = (T)s[e / tb][e % tb];
 }
 
 template <class T> void invert_diag_tiles(a2ls_handle* h, T* fac) {
   dim3 grid(h->N, ceil_div(h->max_n, TB));
-  k_invert_tiles<T><<<grid, TB, 0, h->st>>>(h->d_ni, h->d_ld, h->d_foff, fac);
+  k_invert_tiles<T><<<grid, 2 * TB, 0, h->st>>>(h->d_ni, h->d_ld, h->d_foff, fac);
   A2LS_LAUNCH();
 }
 

@@ -292,7 +292,8 @@ __global__ void k_bmul(const int* ni, const int* off, const int64_t* xoff, int l
   const TV* Vi = V + xoff[i] + vcol0;
   T* Wi = W + xoff[i];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int l = wid; l < n; l += nw) {
+  // rows spread over the gridDim.y CTAs of the subdomain and their warps
+  for (int l = blockIdx.y * nw + wid; l < n; l += nw * gridDim.y) {
     const double dl = D[o + l];
     for (int c0 = 0; c0 < p; c0 += 32) {
       const int c = c0 + lane;
@@ -988,7 +989,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   // T applied to V[:, vcol : vcol + p] -> W[:, 0:p]; tri_flops = one triangular half over the active set
   double tri_flops = 0.0;
   auto apply_T = [&](int vcol, const int* actv) {
-    k_bmul<TV, T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, vcol, d_pv, actv, h->d_lrow, h->d_lcol,
+    k_bmul<TV, T><<<dim3(N, 8), 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, vcol, d_pv, actv, h->d_lrow, h->d_lcol,
                                  h->d_lval, h->d_D, V, W);
     A2LS_LAUNCH();
     {
