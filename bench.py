@@ -250,6 +250,7 @@ def run_ours(args, rank: int, world: int, device):
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         info = {"ms": ms, "iters": it, "relres": rr, "ok": ok, "launches": P.launches(),
+                "eig_unconverged": P.eig_unconverged(),
                 "times": P.times(), "kernels": P.kernel_times() if timing else None}
         if keep:
             return info, P, x
@@ -440,6 +441,7 @@ def report(args, res, world) -> dict:
                             "factors and local solves, double-float local eigensolves to 1e-4, FGMRES(30) in FP64"),
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
         "iters": mixed[-1]["iters"],
+        "eig_unconverged_subdomains": mixed[-1]["eig_unconverged"],
         "true_relres": res["true_relres"],
         "phases_ms": {k: round(v, 2) for k, v in mixed[-1]["times"].items()},
         "plain_fp64": None if plain is None else {

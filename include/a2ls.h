@@ -121,6 +121,10 @@ typedef struct {
   const a2ls_gnn* warm_start; /* NULL (default): random start blocks for the local eigensolves; otherwise
                                  the network's proposal (a2ls_gnn_forward) starts each subdomain's block
                                  Krylov iteration.  The network is only read; it must outlive a2ls_setup. */
+  int32_t eig_strict;       /* 0 (default): a local eigensolve that misses eig_tol after eig_max_cycles keeps
+                               the Ritz vectors it reached (still a valid coarse space, possibly a weaker
+                               one; counted by A2LS_Q_EIG_UNCONVERGED); 1: a2ls_setup fails with
+                               A2LS_ERR_EIGEN instead */
 } a2ls_options;
 
 /* Fills *opt with the defaults listed above.  Never fails. */
@@ -188,12 +192,35 @@ enum {
   A2LS_Q_EIGSTATS = 8,   /* int32[2*N]: eigen cycles run and kernel dimension per subdomain */
   A2LS_Q_LAUNCHES = 9,   /* int64[1]: kernels this handle has launched so far */
   A2LS_Q_TUNING = 11,    /* int32[2]: CTA width chosen for the local solves, CUDA graphs held */
+  A2LS_Q_EIG_UNCONVERGED = 12, /* int32[1]: subdomains whose eigensolve stopped at eig_max_cycles */
   A2LS_Q_KERNEL_TIMES = 10 /* double[3*8]: (launches, total ms, algorithmic work) of the tracked kernels;
                               work is flops, or bytes moved for the apply local solves; in the order
                               local LU, splitting LU, eigen triangular solves, eigen orthogonalisation,
                               Rayleigh-Ritz, coarse LU, coarse inverse, apply local solves;
                               populated only with a2ls_options::timing = 1 */
 };
+
+/*
+ * a2ls_solve_multi -- solve A X = B for nrhs right-hand sides with the same preconditioner.
+ *   B, X     : device, n x nrhs doubles, column k at offset k*n (X holds the initial guesses on input).
+ *   iters    : host, nrhs int32 (may be NULL); relres: host, nrhs doubles (may be NULL).
+ * Each column runs its own (F)GMRES as a2ls_solve does, one after another on the handle's stream,
+ * sharing the setup.  Returns OK when every column converged, NOT_CONVERGED if any did not (its X
+ * column holds the last iterate), or the first other error.
+ */
+int a2ls_solve_multi(a2ls_handle* h, int32_t nrhs, const double* B, double* X, double rtol, int32_t* iters,
+                     double* relres);
+
+/*
+ * a2ls_setup_batch -- set up nsys independent systems with one call.
+ *   A[k], partition[k], overlap[k], nev[k] : as for a2ls_setup, per system; opt shared (may be NULL).
+ *   out      : host array of nsys handles, filled on success (all NULL on failure; every handle
+ *              created before the failing system is destroyed again).
+ * The systems are set up one after another on the options' stream; each setup batches all of its
+ * subdomains into single launches.  Each handle is used and destroyed on its own.
+ */
+int a2ls_setup_batch(int32_t nsys, const a2ls_csr* A, const int32_t* const* partition, const int32_t* overlap,
+                     const int32_t* nev, const a2ls_options* opt, a2ls_handle** out);
 
 /*
  * a2ls_query -- copy one internal quantity to host memory (inspection and tests).

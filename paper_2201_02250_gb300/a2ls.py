@@ -20,7 +20,7 @@ FP64, FP32, FP32X2 = 0, 1, 2
 VARIANTS = {"deflated_ras": 0, "deflated_asm": 1, "additive_ras": 2, "additive_asm": 3, "ras": 4, "asm": 5}
 POU = {"boolean": 0, "multiplicity": 1}
 (Q_SIZES, Q_SUBDOMAINS, Q_LUMP, Q_FACTORS, Q_COARSE, Q_EIGVALS, Q_TIMES, Q_EINV, Q_EIGSTATS, Q_LAUNCHES,
- Q_KERNEL_TIMES, Q_TUNING) = range(12)
+ Q_KERNEL_TIMES, Q_TUNING, Q_EIG_UNCONVERGED) = range(13)
 TRACKED_KERNELS = ["lu_local", "lu_splitting", "eig_triangular_solves", "eig_orthogonalisation",
                    "eig_rayleigh_ritz", "coarse_lu", "coarse_inverse", "apply_local_solves"]
 PHASES = ["graph", "extract", "lu", "eig_coarse", "coarse", "setup_total", "solve_total", "apply"]
@@ -43,7 +43,8 @@ class Options(ctypes.Structure):
                 ("tau", ctypes.c_double), ("eig_block_steps", ctypes.c_int32),
                 ("eig_max_cycles", ctypes.c_int32), ("eig_tol", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("timing", ctypes.c_int32),
-                ("eig_precision", ctypes.c_int32), ("graphs", ctypes.c_int32), ("warm_start", ctypes.c_void_p)]
+                ("eig_precision", ctypes.c_int32), ("graphs", ctypes.c_int32), ("warm_start", ctypes.c_void_p),
+                ("eig_strict", ctypes.c_int32)]
 
 
 _LIB = None
@@ -82,8 +83,10 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.a2ls_set_coarse_basis.argtypes = [vp, vp, vp]
     L.a2ls_spmv.argtypes = [vp, vp, vp]
     L.a2ls_apply_static.argtypes = [vp, vp, vp]
+    L.a2ls_solve_multi.argtypes = [vp, i32, vp, vp, f64, vp, vp]
+    L.a2ls_setup_batch.argtypes = [i32, vp, vp, vp, vp, ctypes.POINTER(Options), vp]
     for f in ("a2ls_setup", "a2ls_apply", "a2ls_solve", "a2ls_query", "a2ls_set_coarse_basis", "a2ls_spmv",
-              "a2ls_apply_static"):
+              "a2ls_apply_static", "a2ls_solve_multi", "a2ls_setup_batch"):
         getattr(L, f).restype = ctypes.c_int
     # learned warm start
     i64 = ctypes.c_int64
@@ -192,6 +195,16 @@ class Preconditioner:
         _check(rc, allow=(A2LS_ERR_NOT_CONVERGED,) if allow_not_converged else ())
         return int(it.value), float(rr.value), rc == A2LS_OK
 
+    def solve_multi(self, B, X, rtol: float = 1e-8, allow_not_converged: bool = False):
+        """B, X: CUDA float64 tensors of shape (nrhs, n), one right-hand side per row."""
+        nrhs = int(B.shape[0])
+        it = np.zeros(nrhs, dtype=np.int32)
+        rr = np.zeros(nrhs, dtype=np.float64)
+        rc = lib().a2ls_solve_multi(self._h, nrhs, ctypes.c_void_p(_ptr(B)), ctypes.c_void_p(_ptr(X)), float(rtol),
+                                    it.ctypes.data, rr.ctypes.data)
+        _check(rc, allow=(A2LS_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return it, rr, rc == A2LS_OK
+
     # --- queries ------------------------------------------------------------------
     def _query(self, what: int) -> bytes:
         need = ctypes.c_int64()
@@ -270,6 +283,10 @@ class Preconditioner:
     def tuning(self) -> dict:
         v = np.frombuffer(self._query(Q_TUNING), dtype=np.int32)
         return {"local_solve_threads": int(v[0]), "apply_graphs": int(v[1])}
+
+    def eig_unconverged(self) -> int:
+        """Subdomains whose local eigensolve stopped at eig_max_cycles without reaching eig_tol."""
+        return int(np.frombuffer(self._query(Q_EIG_UNCONVERGED), dtype=np.int32)[0])
 
     def launches(self) -> int:
         return int(np.frombuffer(self._query(Q_LAUNCHES), dtype=np.int64)[0])
@@ -366,6 +383,10 @@ class WarmStartNet:
     def adam_step(self, lr: float):
         _check(lib().a2ls_gnn_adam_step(self._g, float(lr)))
 
+    def eig_unconverged(self) -> int:
+        """Subdomains whose local eigensolve stopped at eig_max_cycles without reaching eig_tol."""
+        return int(np.frombuffer(self._query(Q_EIG_UNCONVERGED), dtype=np.int32)[0])
+
     def launches(self) -> int:
         return int(lib().a2ls_gnn_launches(self._g))
 
@@ -413,3 +434,32 @@ class GnnSample:
         m = np.array([z.shape[1] for z in Z], dtype=np.int32)
         flat = np.ascontiguousarray(np.concatenate([np.asarray(z, dtype=np.float64).ravel() for z in Z]))
         _check(lib().a2ls_gnn_sample_set_target(self._s, m.ctypes.data, flat.ctypes.data))
+
+
+def setup_batch(systems: list, stream=None, **opts) -> list:
+    """a2ls_setup_batch over [(rowptr, colind, val, part, overlap, nev)] CUDA tensors; returns Preconditioners."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    nsys = len(systems)
+    csrs = (CSR * max(nsys, 1))()
+    parts = (ctypes.c_void_p * max(nsys, 1))()
+    ov = np.zeros(max(nsys, 1), dtype=np.int32)
+    nv = np.zeros(max(nsys, 1), dtype=np.int32)
+    for k, (rowptr, colind, val, part, overlap, nev) in enumerate(systems):
+        csrs[k] = CSR(int(rowptr.numel() - 1), int(colind.numel()), _ptr(rowptr), _ptr(colind), _ptr(val))
+        parts[k] = _ptr(part)
+        ov[k], nv[k] = overlap, nev
+    o = default_options(**opts)
+    o.stream = ctypes.c_void_p(int(stream.cuda_stream))
+    out = (ctypes.c_void_p * max(nsys, 1))()
+    _check(lib().a2ls_setup_batch(nsys, csrs, parts, ov.ctypes.data, nv.ctypes.data, ctypes.byref(o), out))
+    handles = []
+    for k in range(nsys):
+        P = Preconditioner.__new__(Preconditioner)
+        P.n = int(systems[k][0].numel() - 1)
+        P.stream, P.options, P._warm = stream, o, opts.get("warm_start")
+        P._h = ctypes.c_void_p(out[k])
+        P._keep = systems[k]
+        handles.append(P)
+    return handles

@@ -321,6 +321,8 @@ void a2ls_default_options(a2ls_options* o) {
   o->timing = 0;
   o->eig_precision = -1;
   o->graphs = 1;
+  o->warm_start = nullptr;
+  o->eig_strict = 0;
 }
 
 const char* a2ls_last_error(void) { return g_last_error.c_str(); }
@@ -457,6 +459,61 @@ int a2ls_solve(a2ls_handle* h, const double* b, double* x, double rtol, int32_t*
   });
 }
 
+int a2ls_solve_multi(a2ls_handle* h, int32_t nrhs, const double* B, double* X, double rtol, int32_t* iters,
+                     double* relres) {
+  if (!h || (nrhs > 0 && (!B || !X))) {
+    set_error("null argument");
+    return A2LS_ERR_ARG;
+  }
+  if (nrhs < 0) {
+    set_error("nrhs must be >= 0");
+    return A2LS_ERR_ARG;
+  }
+  if (!(rtol > 0)) {
+    set_error("rtol must be positive");
+    return A2LS_ERR_ARG;
+  }
+  return guarded([&]() -> int {
+    Timer tm(h->st);
+    int worst = A2LS_OK;
+    for (int k = 0; k < nrhs; ++k) {
+      int it = 0;
+      double rr = 0.0;
+      const int rc = gmres(h, B + (size_t)k * h->n, X + (size_t)k * h->n, rtol, &it, &rr);
+      sync_and_check(h, "solve");
+      if (iters) iters[k] = it;
+      if (relres) relres[k] = rr;
+      if (rc != A2LS_OK) worst = rc;
+    }
+    h->times[Phase::SOLVE_TOTAL] = tm.stop();
+    if (worst == A2LS_ERR_NOT_CONVERGED) set_error("GMRES reached max_it before the tolerance for a right-hand side");
+    return worst;
+  });
+}
+
+int a2ls_setup_batch(int32_t nsys, const a2ls_csr* A, const int32_t* const* partition, const int32_t* overlap,
+                     const int32_t* nev, const a2ls_options* opt, a2ls_handle** out) {
+  set_error("");
+  if (nsys < 0 || (nsys > 0 && (!A || !partition || !overlap || !nev || !out))) {
+    set_error("null argument");
+    return A2LS_ERR_ARG;
+  }
+  for (int k = 0; k < nsys; ++k) out[k] = nullptr;
+  for (int k = 0; k < nsys; ++k) {
+    const int rc = a2ls_setup(&A[k], partition[k], overlap[k], nev[k], opt, &out[k]);
+    if (rc != A2LS_OK) {
+      const std::string msg = std::string("system ") + std::to_string(k) + ": " + a2ls_last_error();
+      for (int j = 0; j < k; ++j) {
+        destroy_handle(out[j]);
+        out[j] = nullptr;
+      }
+      set_error(msg.c_str());
+      return rc;
+    }
+  }
+  return A2LS_OK;
+}
+
 void a2ls_destroy(a2ls_handle* h) { destroy_handle(h); }
 
 int a2ls_spmv(a2ls_handle* h, const double* x, double* y) {
@@ -536,6 +593,11 @@ int a2ls_query(a2ls_handle* h, int32_t what, void* out, int64_t capacity, int64_
       case A2LS_Q_TUNING: {
         const int32_t v[2] = {h->ls_width, (int32_t)h->graphs.size()};
         put(v, sizeof(v));
+        break;
+      }
+      case A2LS_Q_EIG_UNCONVERGED: {
+        const int32_t v = h->eig_unconverged;
+        put(&v, sizeof(v));
         break;
       }
       case A2LS_Q_KERNEL_TIMES: {

@@ -1074,7 +1074,8 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
         else ++remaining;
       }
     }
-    if (remaining == 0) break;
+    // after the last cycle V and Y stay as they are: the unconverged subdomains keep their Ritz vectors
+    if (remaining == 0 || cycle + 1 == max_cycles) break;
     A2LS_CUDA(cudaMemcpyAsync(d_active, act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
     // restart block: W = V[:, 0:sb] Y[:, 0:b]
     k_vy<TV, T><<<N, EIG_THREADS, vy_smem, st>>>(h->d_ni, d_vo, P, d_msb, d_pv, d_active, V, Y, W);
@@ -1083,7 +1084,8 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   }
   int unconverged = 0;
   for (int i = 0; i < N; ++i) unconverged += act[i];
-  if (unconverged)
+  h->eig_unconverged = unconverged;
+  if (unconverged && h->opt.eig_strict)
     fail(A2LS_ERR_EIGEN, "local eigensolve did not reach tolerance %.1e in %d cycles for %d subdomains", tol,
          max_cycles, unconverged);
 

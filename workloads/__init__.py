@@ -10,9 +10,9 @@ from .pde import (Problem, conv_diff_2d, high_contrast_fv_2d, conv_diff_3d,
                   block_partition_2d, block_partition_3d, bfs_region_partition,
                   rhs_uniform, config_c1, config_c2, config_c3, tiny_conv_diff,
                   tiny_hpd_dd, random_dd_matrix, gaussian_random_field,
-                  fv_diffusion_2d, config_c4)
+                  fv_diffusion_2d, config_c4, config_c5)
 
 __all__ = ["Problem", "conv_diff_2d", "high_contrast_fv_2d", "conv_diff_3d",
            "block_partition_2d", "block_partition_3d", "bfs_region_partition",
            "rhs_uniform", "config_c1", "config_c2", "config_c3", "tiny_conv_diff",
-           "tiny_hpd_dd", "random_dd_matrix", "gaussian_random_field", "fv_diffusion_2d", "config_c4"]
+           "tiny_hpd_dd", "random_dd_matrix", "gaussian_random_field", "fv_diffusion_2d", "config_c4", "config_c5"]

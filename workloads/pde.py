@@ -181,6 +181,25 @@ def config_c4(seed: int, m: int = 256, blocks: int = 8) -> Problem:
                    rhs_uniform(m * m, seed), {"grid": m, "blocks": blocks, "seed": seed})
 
 
+def config_c5(seed: int = 5, nsys: int = 48, side_min: int = 64, side_max: int = 256, nrhs: int = 4) -> list:
+    """Mixed batch of independent 2D convection-diffusion systems: grid side uniform in
+    [side_min, side_max], Peclet number |b| uniform in [1, 500], angle uniform in [0, 2 pi),
+    nb = clamp(ceil(side / 48), 3, 16) blocks per direction, overlap 1, nev 8, nrhs right-hand sides
+    U(-1, 1) each (stored as rows of meta["B"])."""
+    rng = np.random.Generator(np.random.PCG64(seed + 100000))
+    out = []
+    for k in range(nsys):
+        side = int(rng.integers(side_min, side_max + 1))
+        pe = float(rng.uniform(1.0, 500.0))
+        theta = float(rng.uniform(0.0, 2.0 * math.pi))
+        nb = min(16, max(3, math.ceil(side / 48)))
+        A = conv_diff_2d(side, pe, theta)
+        B = np.stack([rhs_uniform(side * side, seed * 1000 + 10 * k + r) for r in range(nrhs)])
+        out.append(Problem(f"c5_sys{k}_{side}", A, block_partition_2d(side, nb), 1, 8, B[0],
+                           {"grid": side, "peclet": pe, "theta": theta, "blocks": nb, "B": B}))
+    return out
+
+
 def conv_diff_3d(m: int, beta: float) -> sp.csr_matrix:
     """-Laplace(u) + b.grad(u) on the m^3 interior grid of the unit cube.
 
