@@ -93,6 +93,11 @@ struct a2ls_handle {
   int64_t* d_lrow = nullptr;                 // sum n_i + 1
   int* d_lcol = nullptr;
   double* d_lval = nullptr;
+  // envelope of the local pattern: first column of each row, first row of each column (local
+  // indices, sum n_i each), and their minima per 64-row / 64-column tile (offsets h_toff)
+  int *d_pf = nullptr, *d_pg = nullptr;
+  std::vector<int> h_toff;
+  int *d_toff = nullptr, *d_tf = nullptr, *d_tg = nullptr;
 
   // local factors (block-inverted LU, precision = opt.precision)
   void* d_fac = nullptr;

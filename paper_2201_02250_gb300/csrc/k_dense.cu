@@ -233,9 +233,10 @@ template <class T>
 __global__ void __launch_bounds__(256, 2) k_lu(int N, const int* ni, const int* ld, const int64_t* foff,
                                             T* fac, int allow_last_zero, double* last_pivot,
                                             const double* dscale, int* st, const int* sched, const int* nI,
-                                            int phase) {
+                                            int phase, const int* off, const int* pf, const int* pg) {
   using Acc = typename AccOf<T>::type;
   extern __shared__ __align__(16) unsigned char lu_smem_raw[];
+  __shared__ unsigned char lnz[MAXN_LOCAL / TB + 1], unz[MAXN_LOCAL / TB + 1];
   Acc* Dm = reinterpret_cast<Acc*>(lu_smem_raw);  // 64 x 65: the diagonal block, factored in place
   Acc* Iv = Dm + TB * 65;                         // 64 x 65: inv(L11) strictly below, inv(U11) on/above
   Acc* sA = Iv + TB * 65;                         // TGK x TS (16-byte aligned: 2 * 64 * 65 is even)
@@ -303,10 +304,32 @@ __global__ void __launch_bounds__(256, 2) k_lu(int N, const int* ni, const int* 
         }
       }
     }
-    __syncthreads();
     const int tiles = (n - c0 + TB - 1) / TB;
+    // envelope: a row tile of L21 is nonzero only if one of its rows starts left of c0, a column tile
+    // of U12 only if one of its columns starts above c0
+    {
+      const int lane = tid & 31, warp = tid >> 5, o = off[i];
+      for (int t = warp; t < tiles; t += 8) {
+        const int a0 = c0 + t * TB, a1 = min(n, a0 + TB);
+        int fm = n, gm = n;
+        for (int r = a0 + lane; r < a1; r += 32) {
+          fm = min(fm, pf[o + r]);
+          gm = min(gm, pg[o + r]);
+        }
+        for (int q = 16; q > 0; q >>= 1) {
+          fm = min(fm, __shfl_xor_sync(0xffffffffu, fm, q));
+          gm = min(gm, __shfl_xor_sync(0xffffffffu, gm, q));
+        }
+        if (lane == 0) {
+          lnz[t] = fm < c0;
+          unz[t] = gm < c0;
+        }
+      }
+    }
+    __syncthreads();
     // 2. L21 = A21 inv(U11), 64-row tiles
     for (int t = 0; t < tiles; ++t) {
+      if (!lnz[t]) continue;
       const int r0 = c0 + t * TB, rows = min(TB, n - r0);
       Acc acc[4][4];
 #pragma unroll
@@ -326,6 +349,7 @@ __global__ void __launch_bounds__(256, 2) k_lu(int N, const int* ni, const int* 
     }
     // 3. U12 = inv(L11) A12, 64-column tiles
     for (int t = 0; t < tiles; ++t) {
+      if (!unz[t]) continue;
       const int cs = c0 + t * TB, cols = min(TB, n - cs);
       Acc acc[4][4];
 #pragma unroll
@@ -346,6 +370,7 @@ __global__ void __launch_bounds__(256, 2) k_lu(int N, const int* ni, const int* 
     __syncthreads();  // L21 and U12 complete before the trailing update reads them
     // 4. A22 -= L21 U12
     for (int t = 0; t < tiles * tiles; ++t) {
+      if (!lnz[t / tiles] || !unz[t % tiles]) continue;
       const int r0 = c0 + (t / tiles) * TB, cs = c0 + (t % tiles) * TB;
       const int rows = min(TB, n - r0), cols = min(TB, n - cs);
       Acc acc[4][4];
@@ -377,7 +402,8 @@ void lu_batched(a2ls_handle* h, T* fac, int allow_last_zero, double* last_pivot,
   const size_t smem = lu_smem_elems() * sizeof(Acc);
   A2LS_CUDA(cudaFuncSetAttribute(k_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_lu<T><<<h->N, 256, smem, h->st>>>(h->N, h->d_ni, h->d_ld, h->d_foff, fac, allow_last_zero, last_pivot,
-                                      diag_scale, h->d_status, h->d_sched, h->d_nI, phase);
+                                      diag_scale, h->d_status, h->d_sched, h->d_nI, phase, h->d_off, h->d_pf,
+                                      h->d_pg);
   A2LS_LAUNCH();
 }
 
@@ -486,19 +512,16 @@ __device__ __forceinline__ double dot_vec<double, double>(const double2& a, cons
 }
 
 
-// s[r] = x[r0 + r] - sum_{c in [c0, c1)} M[r0 + r][c] x[c] for r < tb (c0, c1 multiples of Vec width
-// except c1 which may be padded up to ld with zeros); the 64 rows of a tile are spread over the warps
+// part[u] += sum_{c in [c0, c1)} M[r0 + r][c] x[c] for the rows r = wid + u * warps of a 64-row tile
+// (c0 and c1 multiples of the vector width, c1 up to ld with zeros in x beyond n)
 template <class T, class Acc, int THREADS>
-__device__ __forceinline__ void panel_residual(const T* __restrict__ M, int64_t L, int r0, int tb, int c0,
-                                               int c1, const Acc* x, Acc* s) {
+__device__ __forceinline__ void panel_accumulate(const T* __restrict__ M, int64_t L, int r0, int tb, int c0,
+                                                 int c1, const Acc* x, Acc (&part)[TB / (THREADS / 32)]) {
   constexpr int LS_WARPS = THREADS / 32;
   constexpr int ROWS_PER_WARP = TB / LS_WARPS;
   using V = typename Vec<T>::type;
   constexpr int VW = Vec<T>::W;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  Acc part[ROWS_PER_WARP];
-#pragma unroll
-  for (int u = 0; u < ROWS_PER_WARP; ++u) part[u] = 0;
   const int nv = (c1 - c0 + VW - 1) / VW;
   const V* rowp[ROWS_PER_WARP];
 #pragma unroll
@@ -514,6 +537,15 @@ __device__ __forceinline__ void panel_residual(const T* __restrict__ M, int64_t 
 #pragma unroll
     for (int u = 0; u < ROWS_PER_WARP; ++u) part[u] += dot_vec<T, Acc>(a[u], xv);
   }
+}
+
+// s[r] = x[r0 + r] - (warp sum of part) for the tile's rows
+template <class Acc, int THREADS>
+__device__ __forceinline__ void panel_finish(Acc (&part)[TB / (THREADS / 32)], int r0, int tb, const Acc* x,
+                                             Acc* s) {
+  constexpr int LS_WARPS = THREADS / 32;
+  constexpr int ROWS_PER_WARP = TB / LS_WARPS;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int u = 0; u < ROWS_PER_WARP; ++u) {
     Acc p = part[u];
@@ -553,8 +585,11 @@ template <class T, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_local_solve(
     const int* off, const int* nI, const int* ni, const int* ld, const int64_t* foff, const int* idx,
     const double* D, const T* __restrict__ fac, const double* __restrict__ t, const double* __restrict__ q,
-    double* __restrict__ out, int mode, const int* sched, int* counter, int nwork) {
+    double* __restrict__ out, int mode, const int* sched, int* counter, int nwork, const int* toff, const int* tf,
+    const int* tg) {
   using Acc = typename AccOf<T>::type;
+  constexpr int RPW = TB / (THREADS / 32);
+  constexpr int VW = Vec<T>::W;
   extern __shared__ unsigned char smem_raw[];
   Acc* x = reinterpret_cast<Acc*>(smem_raw);
   __shared__ Acc s[TB];
@@ -572,19 +607,33 @@ __global__ void __launch_bounds__(THREADS) k_local_solve(
     for (int l = threadIdx.x; l < L; l += THREADS) x[l] = (l < n) ? (Acc)t[idx[o + l]] : (Acc)0;
     __syncthreads();
     const int nb = (n + TB - 1) / TB;
-    // forward: L y = t
+    const int* tfi = tf + toff[i];
+    const int* tgi = tg + toff[i];
+    // forward: L y = t; L[r][c] = 0 left of the block's first envelope column
     for (int b = 0; b < nb; ++b) {
       const int r0 = b * TB, tb = min(TB, n - r0);
-      panel_residual<T, Acc, THREADS>(M, L, r0, tb, 0, r0, x, s);
+      Acc part[RPW];
+#pragma unroll
+      for (int u = 0; u < RPW; ++u) part[u] = 0;
+      const int fs = (tfi[b] / VW) * VW;
+      if (r0 > fs) panel_accumulate<T, Acc, THREADS>(M, L, r0, tb, fs, r0, x, part);
+      panel_finish<Acc, THREADS>(part, r0, tb, x, s);
       __syncthreads();
       tile_apply<T, Acc, THREADS>(M, L, r0, tb, 1, s, x);
       __syncthreads();
     }
-    // backward: U x = y
+    // backward: U x = y; the 64-column tiles whose columns all start below the block are zero
     for (int b = nb - 1; b >= 0; --b) {
       const int r0 = b * TB, tb = min(TB, n - r0);
-      const int c0 = r0 + tb;  // a multiple of TB unless this is the last block (then c0 == n: no panel)
-      panel_residual<T, Acc, THREADS>(M, L, r0, tb, c0, c0 < n ? (int)L : c0, x, s);
+      Acc part[RPW];
+#pragma unroll
+      for (int u = 0; u < RPW; ++u) part[u] = 0;
+      for (int cb = b + 1; cb < nb; ++cb) {
+        if (tgi[cb] > r0 + tb - 1) continue;
+        const int e0 = cb * TB, e1 = (cb == nb - 1) ? (int)L : e0 + TB;
+        panel_accumulate<T, Acc, THREADS>(M, L, r0, tb, e0, e1, x, part);
+      }
+      panel_finish<Acc, THREADS>(part, r0, tb, x, s);
       __syncthreads();
       tile_apply<T, Acc, THREADS>(M, L, r0, tb, 0, s, x);
       __syncthreads();
@@ -621,7 +670,7 @@ static void launch_local_solve(a2ls_handle* h, const T* fac, const double* t, co
   A2LS_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->st));
   k_local_solve<T, THREADS><<<grid, THREADS, smem, h->st>>>(h->d_off, h->d_nI, h->d_ni, h->d_ld, h->d_foff, h->d_idx,
                                                             h->d_D, fac, t, q, z, mode, h->d_sched, h->d_counter,
-                                                            h->N);
+                                                            h->N, h->d_toff, h->d_tf, h->d_tg);
   A2LS_LAUNCH();
 }
 
@@ -691,7 +740,8 @@ __global__ void __launch_bounds__(256) k_block_solve(const int* ni, const int* l
                                                      const T* __restrict__ fac, T* X,
                                                      const int64_t* xoff, int col0, int ldx,
                                                      const int* pvec, const int* active, int forward,
-                                                     int backward, const int* sched) {
+                                                     int backward, const int* sched, const int* toff,
+                                                     const int* tf, const int* tg) {
   using Acc = typename AccOf<T>::type;
   __shared__ Acc sA[GK * 65], sB[GK * 9];
   const int i = sched ? sched[blockIdx.x] : blockIdx.x;  // largest subdomains first
@@ -714,12 +764,19 @@ __global__ void __launch_bounds__(256) k_block_solve(const int* ni, const int* l
       const int r0 = b * TB, tb = min(TB, n - r0);
       Acc acc[2] = {};
       if (pass == 0) {
-        if (r0 > 0) cta_gemm_n8<T, Acc>(M + (int64_t)r0 * L, L, Xi, ldx, tb, pc, r0, 0, acc, sA, sB);
-      } else {
-        const int e0 = r0 + tb;
-        if (e0 < n)
-          cta_gemm_n8<T, Acc>(M + (int64_t)r0 * L + e0, L, Xi + (int64_t)e0 * ldx, ldx, tb, pc, n - e0, 0, acc, sA,
+        // L[r][c] = 0 left of the block's first envelope column
+        const int fs = tf[toff[i] + b];
+        if (r0 > fs)
+          cta_gemm_n8<T, Acc>(M + (int64_t)r0 * L + fs, L, Xi + (int64_t)fs * ldx, ldx, tb, pc, r0 - fs, 0, acc, sA,
                               sB);
+      } else {
+        // U[r][c] = 0 above column c's first envelope row: skip the 64-column tiles that start below
+        for (int cb = b + 1; cb < nb; ++cb) {
+          if (tg[toff[i] + cb] > r0 + tb - 1) continue;
+          const int e0 = cb * TB;
+          cta_gemm_n8<T, Acc>(M + (int64_t)r0 * L + e0, L, Xi + (int64_t)e0 * ldx, ldx, tb, pc, min(TB, n - e0), 0,
+                              acc, sA, sB);
+        }
       }
       // S = X_b - acc, written in place
 #pragma unroll
@@ -749,7 +806,7 @@ void block_solve(a2ls_handle* h, const T* fac, T* X, const int64_t* xoff, int co
                  int pmax, const int* active, int forward, int backward) {
   dim3 grid(h->N, (std::max(pmax, 1) + 7) / 8);
   k_block_solve<T><<<grid, 256, 0, h->st>>>(h->d_ni, h->d_ld, h->d_foff, fac, X, xoff, col0, ldx, pvec, active,
-                                           forward, backward, h->d_sched);
+                                           forward, backward, h->d_sched, h->d_toff, h->d_tf, h->d_tg);
   A2LS_LAUNCH();
 }
 

@@ -571,6 +571,75 @@ static void launch_extract(a2ls_handle* h, void* dense_A, void* dense_At, double
   A2LS_LAUNCH();
 }
 
+// ---------------------------------------------------------------------------
+// envelope of the local matrices (A_ii and A~_ii share their pattern): for row l the first column
+// f_l with a nonzero, for column c the first row g_c with a nonzero.  Gaussian elimination without
+// pivoting keeps L inside the row envelope (L[l][c] = 0 for c < f_l) and U inside the column
+// envelope (U[r][c] = 0 for r < g_c), so tiles outside them stay exactly zero and are skipped.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int subdomain_of(int p, int N, const int* off) {
+  int lo = 0, hi = N;  // off[lo] <= p < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= p) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// g_c starts at c (the diagonal)
+__global__ void k_profile_init(int S, int N, const int* off, int* pg) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < S; p += gridDim.x * blockDim.x)
+    pg[p] = p - off[subdomain_of(p, N, off)];
+}
+
+__global__ void k_profile_rows(int S, int N, const int* off, const int64_t* lrow, const int* lcol, int* pf, int* pg) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < S; p += gridDim.x * blockDim.x) {
+    const int o = off[subdomain_of(p, N, off)], l = p - o;
+    int f = l;
+    for (int64_t q = lrow[p]; q < lrow[p + 1]; ++q) {
+      const int k = lcol[q];
+      if (k < 0) continue;
+      f = min(f, k);
+      atomicMin(pg + o + k, l);
+    }
+    pf[p] = f;
+  }
+}
+
+// minima of f over the 64-row tiles and of g over the 64-column tiles of each subdomain
+__global__ void k_profile_tiles(const int* off, const int* ni, const int* toff, const int* pf, const int* pg,
+                                int* tf, int* tg) {
+  const int i = blockIdx.x, o = off[i], n = ni[i], nt = toff[i + 1] - toff[i];
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    int a = n, b = n;
+    for (int l = t * TB; l < min(n, (t + 1) * TB); ++l) {
+      a = min(a, pf[o + l]);
+      b = min(b, pg[o + l]);
+    }
+    tf[toff[i] + t] = a;
+    tg[toff[i] + t] = b;
+  }
+}
+
+void compute_profiles(a2ls_handle* h) {
+  cudaStream_t st = h->st;
+  const int S = h->sum_n, N = h->N;
+  h->d_pf = dalloc<int>(h, S);
+  h->d_pg = dalloc<int>(h, S);
+  k_profile_init<<<grid_for(S, 256), 256, 0, st>>>(S, N, h->d_off, h->d_pg);
+  A2LS_LAUNCH();
+  k_profile_rows<<<grid_for(S, 256), 256, 0, st>>>(S, N, h->d_off, h->d_lrow, h->d_lcol, h->d_pf, h->d_pg);
+  A2LS_LAUNCH();
+  h->h_toff.assign(N + 1, 0);
+  for (int i = 0; i < N; ++i) h->h_toff[i + 1] = h->h_toff[i] + (h->h_n[i] + TB - 1) / TB;
+  h->d_toff = dalloc<int>(h, N + 1);
+  A2LS_CUDA(cudaMemcpyAsync(h->d_toff, h->h_toff.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, st));
+  h->d_tf = dalloc<int>(h, h->h_toff[N]);
+  h->d_tg = dalloc<int>(h, h->h_toff[N]);
+  k_profile_tiles<<<N, 64, 0, st>>>(h->d_off, h->d_ni, h->d_toff, h->d_pf, h->d_pg, h->d_tf, h->d_tg);
+  A2LS_LAUNCH();
+}
+
 void extract_local(a2ls_handle* h, void* dense_A, void* dense_At, double* dense_scale) {
   cudaStream_t st = h->st;
   h->d_lump = dalloc<double>(h, h->sum_n);
@@ -590,6 +659,7 @@ void extract_local(a2ls_handle* h, void* dense_A, void* dense_At, double* dense_
     else if (ep == A2LS_FP32X2) launch_extract<float, dfloat>(h, dense_A, dense_At, dense_scale, blocks);
     else launch_extract<float, double>(h, dense_A, dense_At, dense_scale, blocks);
   }
+  compute_profiles(h);
 }
 
 }  // namespace a2ls
