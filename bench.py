@@ -201,7 +201,8 @@ class ClockSampler:
 # our arm
 # ---------------------------------------------------------------------------
 def apply_bytes(P, prob, fac_bytes: int) -> dict:
-    """Algorithmic bytes of one deflated-RAS apply (Eq. 2.4) and of its local-solve kernel."""
+    """Algorithmic bytes of one deflated-RAS apply (Eq. 2.4) and of its local-solve kernel: the local
+    factors count with their envelope entries (the zero tiles outside it are not read)."""
     import numpy as np
     sz = P.sizes()
     subs = P.subdomains()
@@ -209,7 +210,8 @@ def apply_bytes(P, prob, fac_bytes: int) -> dict:
     nI = np.array([len(a) for a, _ in subs], dtype=np.int64)
     m = np.array([w.shape[1] for w in P.coarse_basis()], dtype=np.int64)
     n, nnz, n0 = prob.n, prob.A.nnz, sz["n0"]
-    fac = int((ni * ni).sum()) * fac_bytes
+    env = P.envelope()
+    fac = int((env[:, 2] + env[:, 3] - ni).sum()) * fac_bytes   # factor entries inside the envelope
     local_kernel = fac + int(ni.sum()) * (4 + 8) + int(nI.sum()) * (4 + 8 + 8)   # factors, gather, scatter (+q)
     spmv = nnz * 12 + (n + 1) * 4 + 3 * n * 8
     coarse = 2 * int((nI * m).sum()) * 8 + int(nI.sum()) * 4 + n0 * n0 * 8 + 4 * n0 * 8

@@ -193,6 +193,11 @@ enum {
   A2LS_Q_LAUNCHES = 9,   /* int64[1]: kernels this handle has launched so far */
   A2LS_Q_TUNING = 11,    /* int32[2]: CTA width chosen for the local solves, CUDA graphs held */
   A2LS_Q_EIG_UNCONVERGED = 12, /* int32[1]: subdomains whose eigensolve stopped at eig_max_cycles */
+  A2LS_Q_ENVELOPE = 13,  /* double[4*N]: per subdomain the flops of an LU confined to the envelope of the
+                            local pattern (all pivots; overlap pivots only), and the entries of L's row
+                            envelope and U's column envelope (sum_r r - f_r + 1, sum_c c - g_c + 1), f_r / g_c
+                            being the first nonzero column of row r / row of column c; the factors are
+                            zero outside these envelopes and the kernels skip the 64x64 tiles there */
   A2LS_Q_KERNEL_TIMES = 10 /* double[3*8]: (launches, total ms, algorithmic work) of the tracked kernels;
                               work is flops, or bytes moved for the apply local solves; in the order
                               local LU, splitting LU, eigen triangular solves, eigen orthogonalisation,

@@ -20,7 +20,7 @@ FP64, FP32, FP32X2 = 0, 1, 2
 VARIANTS = {"deflated_ras": 0, "deflated_asm": 1, "additive_ras": 2, "additive_asm": 3, "ras": 4, "asm": 5}
 POU = {"boolean": 0, "multiplicity": 1}
 (Q_SIZES, Q_SUBDOMAINS, Q_LUMP, Q_FACTORS, Q_COARSE, Q_EIGVALS, Q_TIMES, Q_EINV, Q_EIGSTATS, Q_LAUNCHES,
- Q_KERNEL_TIMES, Q_TUNING, Q_EIG_UNCONVERGED) = range(13)
+ Q_KERNEL_TIMES, Q_TUNING, Q_EIG_UNCONVERGED, Q_ENVELOPE) = range(14)
 TRACKED_KERNELS = ["lu_local", "lu_splitting", "eig_triangular_solves", "eig_orthogonalisation",
                    "eig_rayleigh_ritz", "coarse_lu", "coarse_inverse", "apply_local_solves"]
 PHASES = ["graph", "extract", "lu", "eig_coarse", "coarse", "setup_total", "solve_total", "apply"]
@@ -284,6 +284,10 @@ class Preconditioner:
         v = np.frombuffer(self._query(Q_TUNING), dtype=np.int32)
         return {"local_solve_threads": int(v[0]), "apply_graphs": int(v[1])}
 
+    def envelope(self) -> np.ndarray:
+        """(N, 4): envelope LU flops (all pivots, overlap pivots), L row-envelope and U column-envelope entries."""
+        return np.frombuffer(self._query(Q_ENVELOPE), dtype=np.float64).reshape(-1, 4).copy()
+
     def eig_unconverged(self) -> int:
         """Subdomains whose local eigensolve stopped at eig_max_cycles without reaching eig_tol."""
         return int(np.frombuffer(self._query(Q_EIG_UNCONVERGED), dtype=np.int32)[0])
@@ -382,6 +386,10 @@ class WarmStartNet:
 
     def adam_step(self, lr: float):
         _check(lib().a2ls_gnn_adam_step(self._g, float(lr)))
+
+    def envelope(self) -> np.ndarray:
+        """(N, 4): envelope LU flops (all pivots, overlap pivots), L row-envelope and U column-envelope entries."""
+        return np.frombuffer(self._query(Q_ENVELOPE), dtype=np.float64).reshape(-1, 4).copy()
 
     def eig_unconverged(self) -> int:
         """Subdomains whose local eigensolve stopped at eig_max_cycles without reaching eig_tol."""

@@ -98,6 +98,8 @@ struct a2ls_handle {
   int *d_pf = nullptr, *d_pg = nullptr;
   std::vector<int> h_toff;
   int *d_toff = nullptr, *d_tf = nullptr, *d_tg = nullptr;
+  // per subdomain: envelope LU flops (all pivots, overlap pivots), L and U envelope entries
+  std::vector<double> h_env;
 
   // local factors (block-inverted LU, precision = opt.precision)
   void* d_fac = nullptr;

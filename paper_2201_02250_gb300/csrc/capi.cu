@@ -252,11 +252,11 @@ static void factor_and_coarse(a2ls_handle* h, bool need_coarse, double* times) {
   extract_local(h, fa, ft, dscale);
   sync_and_check(h, "local matrix extraction");
   times[Phase::SETUP_EXTRACT] = tm.stop();
+  // algorithmic work: the flops of an LU confined to the envelope of the local pattern
   double lu_flops = 0.0, gamma_flops = 0.0;
   for (int i = 0; i < N; ++i) {
-    const double ni = h->h_n[i], ng = h->h_n[i] - h->h_nI[i];
-    lu_flops += 2.0 / 3.0 * ni * ni * ni;
-    gamma_flops += 2.0 / 3.0 * ng * ng * ng;
+    lu_flops += h->h_env[4 * i];
+    gamma_flops += h->h_env[4 * i + 1];
   }
   // A_ii and A~_ii share their interior block, so one factorisation of the splitting serves both
   // when it runs in at least the precision of the A_ii factors; only the Schur complement on the
@@ -595,6 +595,9 @@ int a2ls_query(a2ls_handle* h, int32_t what, void* out, int64_t capacity, int64_
         put(v, sizeof(v));
         break;
       }
+      case A2LS_Q_ENVELOPE:
+        put(h->h_env.data(), sizeof(double) * h->h_env.size());
+        break;
       case A2LS_Q_EIG_UNCONVERGED: {
         const int32_t v = h->eig_unconverged;
         put(&v, sizeof(v));

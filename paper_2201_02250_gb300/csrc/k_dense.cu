@@ -684,9 +684,13 @@ static void launch_local_solve_width(a2ls_handle* h, int width, const T* fac, co
 
 template <class T>
 void local_solves(a2ls_handle* h, const T* fac, const double* t, const double* q, double* z, int mode) {
+  // algorithmic bytes: the factor entries inside the envelope (L's rows, U's columns, diagonal once),
+  // the gather of t and the scatter of the solution
   double bytes = 0.0;
-  for (int i = 0; i < h->N; ++i)
-    bytes += (double)h->h_n[i] * h->h_n[i] * sizeof(T) + 12.0 * h->h_n[i] + (mode == 0 ? 20.0 * h->h_nI[i] : 12.0 * h->h_n[i]);
+  if (h->opt.timing)
+    for (int i = 0; i < h->N; ++i)
+      bytes += (h->h_env[4 * i + 2] + h->h_env[4 * i + 3] - h->h_n[i]) * sizeof(T) + 12.0 * h->h_n[i] +
+               (mode == 0 ? 20.0 * h->h_nI[i] : 12.0 * h->h_n[i]);
   KTime kt(h, KT_APPLY_LOCAL, bytes);
   launch_local_solve_width<T>(h, h->ls_width > 0 ? h->ls_width : 512, fac, t, q, z, mode);
 }

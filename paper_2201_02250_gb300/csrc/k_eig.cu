@@ -986,20 +986,21 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   A2LS_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_smem));
   A2LS_CUDA(cudaFuncSetAttribute(k_vy<TV, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vy_smem));
 
-  // T applied to V[:, vcol : vcol + p] -> W[:, 0:p]; tri_flops = one triangular half over the active set
-  double tri_flops = 0.0;
+  // T applied to V[:, vcol : vcol + p] -> W[:, 0:p]; fwd/bwd_flops: the two triangular halves over the
+  // active set, counted inside the envelope of the factors
+  double fwd_flops = 0.0, bwd_flops = 0.0;
   auto apply_T = [&](int vcol, const int* actv) {
     k_bmul<TV, T><<<dim3(N, 8), 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, vcol, d_pv, actv, h->d_lrow, h->d_lcol,
                                  h->d_lval, h->d_D, V, W);
     A2LS_LAUNCH();
     {
-      KTime kt(h, KT_EIG_SOLVE, tri_flops);
+      KTime kt(h, KT_EIG_SOLVE, fwd_flops);
       block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, pmax, actv, 1, 0);
     }
     k_mu_fix<T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, d_pv, actv, d_kd, hvec, W);
     A2LS_LAUNCH();
     {
-      KTime kt(h, KT_EIG_SOLVE, tri_flops);
+      KTime kt(h, KT_EIG_SOLVE, bwd_flops);
       block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, pmax, actv, 0, 1);
     }
     k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, actv, d_kd, kvec, W);
@@ -1039,12 +1040,13 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     for (int j = 0; j < s; ++j) {
       const int* actv = (j == 0) ? d_active : d_actk;
       const std::vector<int>& acth = (j == 0) ? act : actk;
-      tri_flops = 0.0;
+      fwd_flops = bwd_flops = 0.0;
       double orth_flops = 0.0;
       for (int i = 0; i < N; ++i) {
         if (!acth[i]) continue;
         const double ni = h->h_n[i], pi = pv[i], jb = full[i] ? pi : (double)(j + 1) * b;
-        tri_flops += ni * ni * pi;
+        fwd_flops += 2.0 * h->h_env[4 * i + 2] * pi;
+        bwd_flops += 2.0 * h->h_env[4 * i + 3] * pi;
         orth_flops += 8.0 * ni * jb * pi + 9.0 * ni * pi * pi;
       }
       apply_T(j * b, actv);

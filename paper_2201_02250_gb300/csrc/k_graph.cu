@@ -621,6 +621,54 @@ __global__ void k_profile_tiles(const int* off, const int* ni, const int* toff, 
   }
 }
 
+// Algorithmic work of the envelope-aware kernels per subdomain: out[4i] = LU flops over all pivots,
+// out[4i+1] = LU flops over the overlap pivots (k >= n_I), out[4i+2] = entries of L's row envelope
+// (sum_r r - f_r + 1), out[4i+3] = entries of U's column envelope (sum_c c - g_c + 1).  Pivot k updates
+// (#rows r > k with f_r <= k) x (#columns c > k with g_c <= k) entries, two flops each.
+__global__ void k_envelope_counts(const int* off, const int* ni, const int* nI, const int* pf, const int* pg,
+                                  double* out) {
+  extern __shared__ int cnt[];  // 2n: histograms of f and g
+  __shared__ double red[2][32];
+  const int i = blockIdx.x, o = off[i], n = ni[i], n_I = nI[i];
+  for (int e = threadIdx.x; e < 2 * n; e += blockDim.x) cnt[e] = 0;
+  __syncthreads();
+  double sf = 0.0, sg = 0.0;
+  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+    atomicAdd(&cnt[pf[o + l]], 1);
+    atomicAdd(&cnt[n + pg[o + l]], 1);
+    sf += (double)(l - pf[o + l] + 1);
+    sg += (double)(l - pg[o + l] + 1);
+  }
+  for (int q = 16; q > 0; q >>= 1) {
+    sf += __shfl_xor_sync(0xffffffffu, sf, q);
+    sg += __shfl_xor_sync(0xffffffffu, sg, q);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sf;
+    red[1][threadIdx.x >> 5] = sg;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tf = 0.0, tg = 0.0, full = 0.0, gam = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      tf += red[0][w];
+      tg += red[1][w];
+    }
+    long long cf = 0, cg = 0;
+    for (int k = 0; k < n; ++k) {
+      cf += cnt[k];
+      cg += cnt[n + k];
+      const double t = 2.0 * (double)(cf - k - 1) * (double)(cg - k - 1);
+      full += t;
+      if (k >= n_I) gam += t;
+    }
+    out[4 * i] = full;
+    out[4 * i + 1] = gam;
+    out[4 * i + 2] = tf;
+    out[4 * i + 3] = tg;
+  }
+}
+
 void compute_profiles(a2ls_handle* h) {
   cudaStream_t st = h->st;
   const int S = h->sum_n, N = h->N;
@@ -638,6 +686,15 @@ void compute_profiles(a2ls_handle* h) {
   h->d_tg = dalloc<int>(h, h->h_toff[N]);
   k_profile_tiles<<<N, 64, 0, st>>>(h->d_off, h->d_ni, h->d_toff, h->d_pf, h->d_pg, h->d_tf, h->d_tg);
   A2LS_LAUNCH();
+  double* d_env = dalloc<double>(h, 4 * (size_t)N);
+  const size_t smem = sizeof(int) * 2 * (size_t)h->max_n;
+  A2LS_CUDA(cudaFuncSetAttribute(k_envelope_counts, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_envelope_counts<<<N, 256, smem, st>>>(h->d_off, h->d_ni, h->d_nI, h->d_pf, h->d_pg, d_env);
+  A2LS_LAUNCH();
+  h->h_env.assign(4 * (size_t)N, 0.0);
+  A2LS_CUDA(cudaMemcpyAsync(h->h_env.data(), d_env, sizeof(double) * 4 * N, cudaMemcpyDeviceToHost, st));
+  A2LS_CUDA(cudaStreamSynchronize(st));
+  dfree(h, d_env);
 }
 
 void extract_local(a2ls_handle* h, void* dense_A, void* dense_At, double* dense_scale) {

@@ -466,3 +466,45 @@ def test_condition_bound_on_gpu_coarse_space():
         bound = O.condition_bound(subs, P0.n, tau)
         assert kappa <= bound, (seed, kappa, bound)
         P.close()
+
+
+# ---------------------------------------------------------------------------
+# envelope of the local factors
+# ---------------------------------------------------------------------------
+def _envelope(Aii):
+    n = Aii.shape[0]
+    nz = Aii != 0
+    f = np.array([np.flatnonzero(nz[r]).min() for r in range(n)])
+    g = np.array([np.flatnonzero(nz[:, c]).min() for c in range(n)])
+    return f, g
+
+
+def test_envelope_counts_and_zero_factor_tiles():
+    """Without pivoting L stays inside the row envelope and U inside the column envelope of A_ii:
+    the stored factors are exactly zero there (outside the inverted diagonal tiles), and the reported
+    work is the envelope LU's flop count (sum over pivots of 2 x rows x columns updated)."""
+    A3 = pde.conv_diff_3d(10, 100.0)
+    part3 = pde.bfs_region_partition(A3, 8, 60, 180, seed=5)
+    for A, part, delta in ((A3, part3, 1), (pde.config_c1().A, pde.config_c1().part, 1)):
+        P, keep = a2ls().from_scipy(A, part, delta, 4, precision="fp64")
+        env = P.envelope()
+        facs = P.factors()
+        subs = O.overlapping_subdomains(A, part, delta)
+        for i, s in enumerate(subs):
+            Aii = O.local_matrix(A, s)
+            f, g = _envelope(Aii)
+            n = len(f)
+            assert env[i, 2] == np.sum(np.arange(n) - f + 1)
+            assert env[i, 3] == np.sum(np.arange(n) - g + 1)
+            lu = 0.0
+            for k in range(n):
+                rows = np.sum((f <= k) & (np.arange(n) > k))
+                cols = np.sum((g <= k) & (np.arange(n) > k))
+                lu += 2.0 * rows * cols
+            assert env[i, 0] == lu
+            F = facs[i]
+            r, c = np.indices(F.shape)
+            outside = ((c < r) & (c < f[r])) | ((r < c) & (r < g[c]))
+            same_tile = (r // 64) == (c // 64)
+            assert np.all(F[outside & ~same_tile] == 0.0)
+        P.close()
