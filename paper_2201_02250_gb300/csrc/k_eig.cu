@@ -675,20 +675,21 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
   }
   const int m = full[i] ? mfull[i] : prm.sb_krylov;
   const int ld = m + 1;
+  // sized for the launch's largest m and block size b (two CTAs per SM fit for m = 72, b = 24)
   R* S = reinterpret_cast<R*>(sm);   // m x ld
-  R* Q = S + m * ld;                 // m x ld
-  R* xs = Q + m * ld;                // 32 lanes x m
-  R* ys = xs + 32 * m;               // 32 lanes x m
-  R* vtmp = ys + 32 * m;             // m
+  R* Q = S + m * ld;                 // m x m
+  R* xs = Q + m * m;                 // b lanes x m
+  R* ys = xs + prm.b * m;            // b lanes x m
+  R* vtmp = ys + prm.b * m;          // m (Hessenberg scratch, then the moduli)
+  double* mod = reinterpret_cast<double*>(vtmp);
   double* wr = reinterpret_cast<double*>(vtmp + m);  // m
   double* wi = wr + m;               // m
-  double* mod = wi + m;              // m
-  int* perm = reinterpret_cast<int*>(mod + m);  // m
+  int* perm = reinterpret_cast<int*>(wi + m);  // m
   const double* Hi = H + (int64_t)i * EIG_MAXP * EIG_MAXP;
   const se::Team team{(int)threadIdx.x, (int)blockDim.x};
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     S[(e / m) * ld + e % m] = (R)Hi[(e / m) * EIG_MAXP + e % m];
-    Q[(e / m) * ld + e % m] = (R)((e / m == e % m) ? 1.0 : 0.0);
+    Q[(e / m) * m + e % m] = (R)((e / m == e % m) ? 1.0 : 0.0);
   }
   __syncthreads();
   double snorm = 0.0;
@@ -707,8 +708,8 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
     }
     return;
   }
-  se::hessenberg(S, ld, Q, ld, m, vtmp, team);
-  const int rc = se::schur(S, ld, Q, ld, m, snorm, team);
+  se::hessenberg(S, ld, Q, m, m, vtmp, team);
+  const int rc = se::schur(S, ld, Q, m, m, snorm, team);
   if (rc != 0 && threadIdx.x == 0) raise_status(st, A2LS_ERR_EIGEN, i, 2);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -759,8 +760,8 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
     for (int a = 0; a < m; ++a) {
       R qxr = 0.0, qyr = 0.0;
       for (int c = 0; c < m; ++c) {
-        qxr += Q[a * ld + c] * x[c];
-        qyr += Q[a * ld + c] * y[c];
+        qxr += Q[a * m + c] * x[c];
+        qyr += Q[a * m + c] * y[c];
       }
       const double qx = (double)qxr, qy = (double)qyr;
       Yi[a * EIG_MAXP + sel_col[j]] = qx;
@@ -979,7 +980,11 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   };
   const size_t orth_smem = orth_smem_for(gcap_f);
   using RT = typename RRType<T>::type;
-  const size_t rr_smem = sizeof(double) * (2 * EIG_MAXP * (EIG_MAXP + 1) + 64 * EIG_MAXP + 4 * EIG_MAXP) +
+  int m_max = s * b;
+  for (int i = 0; i < N; ++i)
+    if (full[i]) m_max = std::max(m_max, mfull[i]);
+  const size_t rr_smem = sizeof(double) * ((size_t)m_max * (m_max + 1) + (size_t)m_max * m_max + 2 * (size_t)b * m_max +
+                                           3 * (size_t)m_max) +
                          sizeof(int) * EIG_MAXP + 64;
   const size_t vy_smem = sizeof(Acc) * (EIG_MAXP * EIG_MAXP + RC * EIG_MAXP);
   A2LS_CUDA(cudaFuncSetAttribute(k_orth<TV, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orth_smem));
