@@ -371,7 +371,7 @@ __device__ void small_cholesky_inverse(double* G, int p, double* Ri, int& rank_o
 }
 
 constexpr int ORTH_THREADS = 512;
-constexpr int ORC = 32;                  // rows staged per chunk in k_orth
+constexpr int ORC_MAX = 64;              // rows staged per chunk in k_orth (64, or 32 with full-space Gram)
 constexpr int ORTH_NB = (EIG_MAXP / 2) * (EIG_MAXP / 2) / ORTH_THREADS + 1;  // Gram items per thread
 
 // stage rows [l0, l0 + rows) of M (cols 0:w) into S (stride EIG_MAXP), zero padding column w
@@ -390,7 +390,7 @@ __device__ __forceinline__ void stage_rows(Acc* S, const TM* M, int64_t ldx, int
 // scratch of ORTH_THREADS x 4 values for the partial sums (may alias Xs).  Ends with a barrier.
 template <class Acc, class TX, class TY>
 __device__ void gram_product(const TX* X, const TY* Y, int64_t ldx, int n, int nx, int ny, bool same, Acc* Xs,
-                             Acc* Ys, double* G, Acc* Ps) {
+                             Acc* Ys, double* G, Acc* Ps, int orc) {
   const int tid = threadIdx.x;
   const int nbr = (nx + 1) / 2, nbc = (ny + 1) / 2, nb = nbr * nbc;
   const int ng = nb >= ORTH_THREADS ? 1 : min(8, ORTH_THREADS / nb);
@@ -398,8 +398,8 @@ __device__ void gram_product(const TX* X, const TY* Y, int64_t ldx, int n, int n
   Acc acc[ORTH_NB][4];
 #pragma unroll
   for (int k = 0; k < ORTH_NB; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0;
-  for (int l0 = 0; l0 < n; l0 += ORC) {
-    const int rows = min(ORC, n - l0);
+  for (int l0 = 0; l0 < n; l0 += orc) {
+    const int rows = min(orc, n - l0);
     stage_rows(Xs, X, ldx, l0, rows, nx);
     if (!same) stage_rows(Ys, Y, ldx, l0, rows, ny);
     __syncthreads();
@@ -505,12 +505,13 @@ __device__ int warp_cholesky_inverse(double* G, int p, double* Ri, double abs_fl
 // Orthogonalisation: block CGS2 of W against V[:, 0:jb], then Cholesky QR three times (the first
 // shifted).  Writes the Gram coefficients into H[0:jb, hc:hc+p] and R into H[hr:hr+p, hc:hc+p] and
 // the orthonormal block into V[:, vout:vout+p].  full != 0: only H[0:jb, hc:hc+p].
-// Shared memory: G and Ri (gcap doubles each), trow, two staging chunks of ORC x EIG_MAXP.
+// Shared memory: G and Ri (gcap doubles each), trow, two staging chunks of orc x EIG_MAXP.
 template <class T, class TW>
 __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int64_t* xoff, int ldx,
                                                         const int* pvec, const int* active, int jb_blocks,
                                                         int bcols, T* V, TW* W, double* H, int hr, int hc,
-                                                        int vout, const int* fullv, int* rank_flag, int gcap) {
+                                                        int vout, const int* fullv, int* rank_flag, int gcap,
+                                                        int orc) {
   using Acc = typename EAcc<T>::type;
   extern __shared__ double sm[];
   const int i = blockIdx.x;
@@ -525,8 +526,8 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
   double* G = sm;                               // gcap: Gram, then R in place
   double* Ri = G + gcap;                        // gcap
   double* trow = Ri + gcap;                     // EIG_MAXP
-  Acc* sv = reinterpret_cast<Acc*>(trow + EIG_MAXP);           // ORC * EIG_MAXP
-  Acc* sw = sv + ORC * EIG_MAXP;                               // ORC * EIG_MAXP
+  Acc* sv = reinterpret_cast<Acc*>(trow + EIG_MAXP);           // orc * EIG_MAXP
+  Acc* sw = sv + orc * EIG_MAXP;                               // orc * EIG_MAXP
   __shared__ int rank_ok;
   const int tid = threadIdx.x;
   const int pp = p + (p & 1);                   // padded column count of the converted coefficients
@@ -534,7 +535,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
   for (int e = tid; e < jb * p; e += ORTH_THREADS) Hi[(e / p) * EIG_MAXP + hc + e % p] = 0.0;
   for (int pass = 0; pass < npass; ++pass) {
     // G = V[:, 0:jb]^T W[:, 0:p]
-    gram_product<Acc>(Vi, Wi, (int64_t)ldx, n, jb, p, false, sv, sw, G, sv);
+    gram_product<Acc>(Vi, Wi, (int64_t)ldx, n, jb, p, false, sv, sw, G, sv, orc);
     for (int e = tid; e < jb * p; e += ORTH_THREADS) Hi[(e / p) * EIG_MAXP + hc + e % p] += G[e];
     if (full) return;  // Rayleigh quotient only
     // W -= V G; G converted once to the working arithmetic (in Ri's space, padded to pp columns)
@@ -544,8 +545,8 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
       Ga[e] = c < p ? (Acc)G[a * p + c] : (Acc)0;
     }
     __syncthreads();
-    for (int l0 = 0; l0 < n; l0 += ORC) {
-      const int rows = min(ORC, n - l0);
+    for (int l0 = 0; l0 < n; l0 += orc) {
+      const int rows = min(orc, n - l0);
       stage_rows(sv, Vi, ldx, l0, rows, jb);
       __syncthreads();
       for (int e = tid; e < rows * (pp / 2); e += ORTH_THREADS) {
@@ -567,7 +568,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
   // nearly rank-deficient blocks, two plain passes restore orthogonality):
   // R_total = R3 R2 R1 goes to H[hr:hr+p, hc:hc+p]
   for (int pass = 0; pass < 3; ++pass) {
-    gram_product<Acc>(Wi, Wi, (int64_t)ldx, n, p, p, true, sw, sw, G, sv);
+    gram_product<Acc>(Wi, Wi, (int64_t)ldx, n, p, p, true, sw, sw, G, sv, orc);
     if (tid < 32) {
       if (pass == 0) {
         double tr = 0.0;
@@ -610,8 +611,8 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
       Ra[e] = c < p ? (Acc)Ri[a * p + c] : (Acc)0;
     }
     __syncthreads();
-    for (int l0 = 0; l0 < n; l0 += ORC) {
-      const int rows = min(ORC, n - l0);
+    for (int l0 = 0; l0 < n; l0 += orc) {
+      const int rows = min(orc, n - l0);
       stage_rows(sw, Wi, ldx, l0, rows, p);
       __syncthreads();
       for (int e = tid; e < rows * (pp / 2); e += ORTH_THREADS) {
@@ -975,8 +976,9 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   bool any_full = false;
   for (int i = 0; i < N; ++i) any_full = any_full || (full[i] && act[i]);
   const int gcap_k = EIG_MAXP * 32, gcap_f = any_full ? EIG_MAXP * EIG_MAXP : gcap_k;
+  auto orc_for = [&](int gcap) { return gcap > gcap_k ? 32 : ORC_MAX; };
   auto orth_smem_for = [&](int gcap) {
-    return sizeof(double) * (2 * (size_t)gcap + EIG_MAXP) + sizeof(Acc) * 2 * ORC * EIG_MAXP;
+    return sizeof(double) * (2 * (size_t)gcap + EIG_MAXP) + sizeof(Acc) * 2 * (size_t)orc_for(gcap) * EIG_MAXP;
   };
   const size_t orth_smem = orth_smem_for(gcap_f);
   using RT = typename RRType<T>::type;
@@ -1016,7 +1018,8 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     A2LS_LAUNCH();
     // no previous basis: jb = 0; R written into H's last rows (discarded)
     k_orth<TV, T><<<N, ORTH_THREADS, orth_smem_for(gcap_k), st>>>(h->d_ni, d_vo, P, d_pv, d_active, 0, b, V, W,
-                                                                  Rscr, 0, 0, 0, nullptr, d_rank, gcap_k);
+                                                                  Rscr, 0, 0, 0, nullptr, d_rank, gcap_k,
+                                                                  orc_for(gcap_k));
     A2LS_LAUNCH();
   };
 
@@ -1061,7 +1064,8 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
         KTime kt(h, KT_EIG_ORTH, orth_flops);
         const int gcap = (j == 0) ? gcap_f : gcap_k;
         k_orth<TV, T><<<N, ORTH_THREADS, orth_smem_for(gcap), st>>>(h->d_ni, d_vo, P, d_pv, actv, j + 1, b, V, W, H,
-                                                      (j + 1) * b, j * b, (j + 1) * b, d_full, d_rank, gcap);
+                                                      (j + 1) * b, j * b, (j + 1) * b, d_full, d_rank, gcap,
+                                                      orc_for(gcap));
         A2LS_LAUNCH();
       }
     }
