@@ -27,6 +27,7 @@
 #include "small_eig.cuh"
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 
@@ -282,10 +283,18 @@ __global__ void __launch_bounds__(EIG_THREADS) k_project_k(const int* ni, const 
 }
 
 // W[:, 0:p] = B V[:, c0:c0+p], B = D A_ii D via the local CSR; one warp per row
+// lval and D in the working arithmetic of the eigensolve (converted once per setup)
+template <class T>
+__global__ void k_convert(int64_t count, const double* __restrict__ in, T* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (T)in[e];
+}
+
 template <class TV, class T>
 __global__ void k_bmul(const int* ni, const int* off, const int64_t* xoff, int ldx, int vcol0, const int* pvec,
-                       const int* active, const int64_t* lrow, const int* lcol, const double* lval,
-                       const double* D, const TV* V, T* W) {
+                       const int* active, const int64_t* lrow, const int* lcol,
+                       const typename EAcc<T>::type* lval, const typename EAcc<T>::type* D, const TV* V, T* W) {
+  using Acc = typename EAcc<T>::type;
   const int i = blockIdx.x;
   if (active && !active[i]) return;
   const int n = ni[i], p = pvec[i], o = off[i];
@@ -294,20 +303,20 @@ __global__ void k_bmul(const int* ni, const int* off, const int64_t* xoff, int l
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   // rows spread over the gridDim.y CTAs of the subdomain and their warps
   for (int l = blockIdx.y * nw + wid; l < n; l += nw * gridDim.y) {
-    const double dl = D[o + l];
+    const Acc dl = D[o + l];
     for (int c0 = 0; c0 < p; c0 += 32) {
       const int c = c0 + lane;
-      double acc = 0.0;
-      if (dl != 0.0 && c < p) {
+      Acc acc = 0;
+      if (dl != Acc(0) && c < p) {
         for (int64_t q = lrow[o + l]; q < lrow[o + l + 1]; ++q) {
           const int lk = lcol[q];
           if (lk < 0) continue;
-          const double dk = D[o + lk];
-          if (dk == 0.0) continue;
-          acc += lval[q] * dk * (double)Vi[(int64_t)lk * ldx + c];
+          const Acc dk = D[o + lk];
+          if (dk == Acc(0)) continue;
+          mac(acc, lval[q] * dk, (Acc)Vi[(int64_t)lk * ldx + c]);
         }
       }
-      if (c < p) Wi[(int64_t)l * ldx + c] = (T)(acc * dl);
+      if (c < p) Wi[(int64_t)l * ldx + c] = (T)(finish(acc) * dl);
     }
   }
 }
@@ -372,15 +381,16 @@ __device__ void small_cholesky_inverse(double* G, int p, double* Ri, int& rank_o
 
 constexpr int ORTH_THREADS = 512;
 constexpr int ORC_MAX = 64;              // rows staged per chunk in k_orth (64, or 32 with full-space Gram)
+constexpr int SROW = EIG_MAXP + 1;       // row stride of the staged chunks (odd: rows fall on different banks)
 constexpr int ORTH_NB = (EIG_MAXP / 2) * (EIG_MAXP / 2) / ORTH_THREADS + 1;  // Gram items per thread
 
-// stage rows [l0, l0 + rows) of M (cols 0:w) into S (stride EIG_MAXP), zero padding column w
+// stage rows [l0, l0 + rows) of M (cols 0:w) into S (stride SROW), zero padding column w
 template <class Acc, class TM>
 __device__ __forceinline__ void stage_rows(Acc* S, const TM* M, int64_t ldx, int l0, int rows, int w) {
   const int wp = w + (w & 1);
   for (int e = threadIdx.x; e < rows * wp; e += ORTH_THREADS) {
     const int r = e / wp, c = e % wp;
-    S[r * EIG_MAXP + c] = c < w ? (Acc)M[(int64_t)(l0 + r) * ldx + c] : (Acc)0;
+    S[r * SROW + c] = c < w ? (Acc)M[(int64_t)(l0 + r) * ldx + c] : (Acc)0;
   }
 }
 
@@ -412,8 +422,8 @@ __device__ void gram_product(const TX* X, const TY* Y, int64_t ldx, int n, int n
         const int a0 = 2 * (b / nbc), c0 = 2 * (b % nbc);
         Acc s0 = 0, s1 = 0, s2 = 0, s3 = 0;
         for (int r = g; r < rows; r += ng) {
-          const Acc x0 = Xs[r * EIG_MAXP + a0], x1 = Xs[r * EIG_MAXP + a0 + 1];
-          const Acc y0 = Yr[r * EIG_MAXP + c0], y1 = Yr[r * EIG_MAXP + c0 + 1];
+          const Acc x0 = Xs[r * SROW + a0], x1 = Xs[r * SROW + a0 + 1];
+          const Acc y0 = Yr[r * SROW + c0], y1 = Yr[r * SROW + c0 + 1];
           mac(s0, x0, y0);
           mac(s1, x0, y1);
           mac(s2, x1, y0);
@@ -526,8 +536,8 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
   double* G = sm;                               // gcap: Gram, then R in place
   double* Ri = G + gcap;                        // gcap
   double* trow = Ri + gcap;                     // EIG_MAXP
-  Acc* sv = reinterpret_cast<Acc*>(trow + EIG_MAXP);           // orc * EIG_MAXP
-  Acc* sw = sv + orc * EIG_MAXP;                               // orc * EIG_MAXP
+  Acc* sv = reinterpret_cast<Acc*>(trow + EIG_MAXP);           // orc * SROW
+  Acc* sw = sv + orc * SROW;                                   // orc * SROW
   __shared__ int rank_ok;
   const int tid = threadIdx.x;
   const int pp = p + (p & 1);                   // padded column count of the converted coefficients
@@ -553,7 +563,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
         const int r = e / (pp / 2), c = 2 * (e % (pp / 2));
         Acc s0 = 0, s1 = 0;
         for (int a = 0; a < jb; ++a) {
-          const Acc v = sv[r * EIG_MAXP + a];
+          const Acc v = sv[r * SROW + a];
           mac(s0, v, Ga[a * pp + c]);
           mac(s1, v, Ga[a * pp + c + 1]);
         }
@@ -619,7 +629,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
         const int r = e / (pp / 2), c = 2 * (e % (pp / 2));
         Acc s0 = 0, s1 = 0;
         for (int a = 0; a <= c + 1 && a < p; ++a) {
-          const Acc v = sw[r * EIG_MAXP + a];
+          const Acc v = sw[r * SROW + a];
           mac(s0, v, Ra[a * pp + c]);
           mac(s1, v, Ra[a * pp + c + 1]);
         }
@@ -978,7 +988,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   const int gcap_k = EIG_MAXP * 32, gcap_f = any_full ? EIG_MAXP * EIG_MAXP : gcap_k;
   auto orc_for = [&](int gcap) { return gcap > gcap_k ? 32 : ORC_MAX; };
   auto orth_smem_for = [&](int gcap) {
-    return sizeof(double) * (2 * (size_t)gcap + EIG_MAXP) + sizeof(Acc) * 2 * (size_t)orc_for(gcap) * EIG_MAXP;
+    return sizeof(double) * (2 * (size_t)gcap + EIG_MAXP) + sizeof(Acc) * 2 * (size_t)orc_for(gcap) * SROW;
   };
   const size_t orth_smem = orth_smem_for(gcap_f);
   using RT = typename RRType<T>::type;
@@ -996,9 +1006,29 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   // T applied to V[:, vcol : vcol + p] -> W[:, 0:p]; fwd/bwd_flops: the two triangular halves over the
   // active set, counted inside the envelope of the factors
   double fwd_flops = 0.0, bwd_flops = 0.0;
+  // local CSR values and partition of unity in the arithmetic of the B products
+  using BAcc = typename EAcc<T>::type;
+  const BAcc* lvalB = nullptr;
+  const BAcc* DB = nullptr;
+  if constexpr (std::is_same<BAcc, double>::value) {
+    lvalB = h->d_lval;
+    DB = h->d_D;
+  } else {
+    int64_t lnnz = 0;
+    A2LS_CUDA(cudaMemcpyAsync(&lnnz, h->d_lrow + h->sum_n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    A2LS_CUDA(cudaStreamSynchronize(st));
+    BAcc* lv = dalloc<BAcc>(h, lnnz);
+    BAcc* dv = dalloc<BAcc>(h, h->sum_n);
+    k_convert<BAcc><<<std::min<int64_t>(152 * 8, (lnnz + 255) / 256 + 1), 256, 0, st>>>(lnnz, h->d_lval, lv);
+    A2LS_LAUNCH();
+    k_convert<BAcc><<<std::min<int64_t>(152 * 8, (h->sum_n + 255) / 256 + 1), 256, 0, st>>>(h->sum_n, h->d_D, dv);
+    A2LS_LAUNCH();
+    lvalB = lv;
+    DB = dv;
+  }
   auto apply_T = [&](int vcol, const int* actv) {
     k_bmul<TV, T><<<dim3(N, 8), 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, vcol, d_pv, actv, h->d_lrow, h->d_lcol,
-                                 h->d_lval, h->d_D, V, W);
+                                             lvalB, DB, V, W);
     A2LS_LAUNCH();
     {
       KTime kt(h, KT_EIG_SOLVE, fwd_flops);
@@ -1162,6 +1192,10 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   dfree(h, H);
   dfree(h, Y);
   dfree(h, Rscr);
+  if constexpr (!std::is_same<BAcc, double>::value) {
+    dfree(h, const_cast<BAcc*>(lvalB));
+    dfree(h, const_cast<BAcc*>(DB));
+  }
   // keep Z (the eigenvectors behind the coarse space) as the warm-start network's training target
   if (h->d_zev) dfree(h, h->d_zev);
   if (h->d_zoff) dfree(h, h->d_zoff);
