@@ -421,13 +421,19 @@ __global__ void k_schur_copy(const int* ni, const int* nI, const int* ld, const 
   const int64_t L = ld[i];
   const TS* S = src + foff[i];
   TD* D = dst + foff[i];
-  for (int r = blockIdx.y; r < n; r += gridDim.y)
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-      double v = (double)S[(int64_t)r * L + c];
-      if (r == c && r >= n_I) v += lump[off[i] + r];
-      if (r == c && r == n - 1 && n_I == n && last_pivot) v = last_pivot[i];
-      D[(int64_t)r * L + c] = (TD)v;
+  for (int r = blockIdx.y; r < n; r += gridDim.y) {
+    const TS* Sr = S + (int64_t)r * L;
+    TD* Dr = D + (int64_t)r * L;
+    // off-diagonal entries convert directly (a double-float pair rounds to FP32 as hi + lo)
+    for (int c = threadIdx.x; c < n; c += blockDim.x)
+      if (c != r) Dr[c] = (TD)Sr[c];
+    if (threadIdx.x == 0) {
+      double v = (double)Sr[r];
+      if (r >= n_I) v += lump[off[i] + r];
+      if (r == n - 1 && n_I == n && last_pivot) v = last_pivot[i];
+      Dr[r] = (TD)v;
     }
+  }
 }
 
 template <class TS, class TD>
@@ -836,67 +842,115 @@ template void block_solve<dfloat>(a2ls_handle*, const dfloat*, dfloat*, const in
 namespace a2ls {
 
 // ---------------------------------------------------------------------------
-// One dense FP64 matrix (the coarse operator A_00): block-inverted LU without
+// One dense matrix (the coarse operator A_00): block-inverted LU without
 // pivoting, spread over many CTAs, then the explicit inverse.
 // ---------------------------------------------------------------------------
-// factor the 64x64 diagonal block at (k0, k0) and invert its triangles in place (256 threads:
-// the LU column by column, then threads 0-63 form the columns of inv(L) and threads 64-127 those of
-// inv(U), each in shared memory)
-__global__ void __launch_bounds__(256) k_e_diag(double* A, int n, int64_t ld, int k0, double scale, int* st) {
-  __shared__ double t[TB][TB + 1], s[TB][TB + 1];
+// Factor the 64x64 diagonal block at (k0, k0) and invert its triangles in place, in the arithmetic
+// and storage R (FP64, or double-float in the mixed form).  256 threads.
+// LU: thread (ty, tx) = (tid / 64, tid % 64) owns column tx and the rows ty, ty + 4, ...; step c
+// subtracts a21 (a12 / pivot)^T from the trailing block, so that the multipliers of column c are
+// formed only once, after the loop (l_rc = a_rc / pivot_c).  The owner of entry (c+1, c+1) checks the
+// next pivot right after its own update, so each step needs one barrier.
+// Inverses: two threads per column, each summing every other term of the column's dot products with
+// two accumulators (a quarter of the serial chain); threads 0-127 form inv(L), 128-255 inv(U).
+template <class R>
+__device__ __forceinline__ R e_recip(R x) { return R(1.0) / x; }
+
+template <class R>
+__global__ void __launch_bounds__(256) k_e_diag(R* A, int n, int64_t ld, int k0, double scale, int* st) {
+  __shared__ R t[TB][TB + 1], s[TB][TB + 1];
+  __shared__ R rp[TB];
   const int tb = min(TB, n - k0);
-  double* D = A + (int64_t)k0 * ld + k0;
-  for (int e = threadIdx.x; e < tb * tb; e += blockDim.x) t[e / tb][e % tb] = D[(e / tb) * ld + e % tb];
+  R* D = A + (int64_t)k0 * ld + k0;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < tb * tb; e += blockDim.x) t[e / tb][e % tb] = D[(e / tb) * ld + e % tb];
   __syncthreads();
-  for (int c = 0; c < tb; ++c) {
-    double piv = t[c][c];
-    if (fabs(piv) <= 1e-14 * scale) {
-      if (threadIdx.x == 0) raise_status(st, A2LS_ERR_SINGULAR, -1, k0 + c);
-      piv = scale;
+  auto pivot = [&](int c) {
+    R piv = t[c][c];
+    if (fabs((double)piv) <= 1e-14 * scale) {
+      raise_status(st, A2LS_ERR_SINGULAR, -1, k0 + c);
+      piv = R(scale);
+      t[c][c] = piv;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) t[c][c] = piv;
-    for (int r = c + 1 + threadIdx.x; r < tb; r += blockDim.x) t[r][c] /= piv;
-    __syncthreads();
-    const int w = tb - c - 1;
-    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
-      const int r = c + 1 + e / w, cc = c + 1 + e % w;
-      t[r][cc] -= t[r][c] * t[c][cc];
+    rp[c] = e_recip(piv);
+  };
+  if (tid == 0) pivot(0);
+  __syncthreads();
+  const int tx = tid & (TB - 1), ty = tid >> 6;
+  for (int c = 0; c + 1 < tb; ++c) {
+    if (tx > c && tx < tb) {
+      const R u = t[c][tx] * rp[c];
+      for (int r = c + 1 + ((ty - c - 1) & 3); r < tb; r += 4) t[r][tx] -= t[r][c] * u;
+      if (tx == c + 1 && ty == ((c + 1) & 3)) pivot(c + 1);
     }
     __syncthreads();
   }
-  const int c = threadIdx.x & (TB - 1);
-  if (threadIdx.x < TB && c < tb) {
-    // inv(L) (unit lower), column c below the diagonal: x_r = -(L[r][c] + sum_{q=c+1}^{r-1} L[r][q] x_q)
-    for (int r = c + 1; r < tb; ++r) {
-      double v = t[r][c];
-      for (int q = c + 1; q < r; ++q) v += t[r][q] * s[q][c];
-      s[r][c] = -v;
+  // multipliers of L
+  for (int e = tid; e < tb * tb; e += blockDim.x) {
+    const int r = e / tb, c = e % tb;
+    if (r > c) t[r][c] *= rp[c];
+  }
+  __syncthreads();
+  const int col = (tid & 127) >> 1, h = tid & 1;
+  const bool active_col = col < tb;
+  if (tid < 128) {
+    // inv(L) (unit lower), column col: x_r = -(L[r][col] + sum_{q=col+1}^{r-1} L[r][q] x_q); this thread
+    // sums the q with (q - col - 1) % 2 == h and writes the rows r with (r - col - 1) % 2 == h, so it
+    // reads only entries that it wrote itself
+    for (int r = 1; r < TB; ++r) {  // uniform across the warp: the pair sum below is a full-warp shuffle
+      R a0 = R(0.0), a1 = R(0.0);
+      const bool act = active_col && r > col && r < tb;
+      if (act) {
+        int q = col + 1 + h;
+        for (; q + 2 < r; q += 4) {
+          mac(a0, t[r][q], s[q][col]);
+          mac(a1, t[r][q + 2], s[q + 2][col]);
+        }
+        if (q < r) mac(a0, t[r][q], s[q][col]);
+      }
+      R v = finish(a0) + finish(a1);
+      v += warp_xor(v, 1);
+      if (act && ((r - col - 1) & 1) == h) s[r][col] = -(t[r][col] + v);
     }
-  } else if (threadIdx.x >= TB && threadIdx.x < 2 * TB && c < tb) {
-    // inv(U), column c on and above the diagonal: x_c = 1/U_cc, x_r = -(sum_{q=r+1}^{c} U[r][q] x_q) / U_rr
-    s[c][c] = 1.0 / t[c][c];
-    for (int r = c - 1; r >= 0; --r) {
-      double v = 0.0;
-      for (int q = r + 1; q <= c; ++q) v += t[r][q] * s[q][c];
-      s[r][c] = -v / t[r][r];
+  } else {
+    // inv(U), column col: x_col = 1 / U_col,col, x_r = -(sum_{q=r+1}^{col} U[r][q] x_q) / U_rr; this
+    // thread sums the q with (col - q) % 2 == h and writes the rows with (col - r) % 2 == h
+    if (active_col && h == 0) s[col][col] = rp[col];
+    for (int r = TB - 2; r >= 0; --r) {
+      R a0 = R(0.0), a1 = R(0.0);
+      const bool act = active_col && r < col;
+      if (act) {
+        int q = col - h;
+        for (; q - 2 > r; q -= 4) {
+          mac(a0, t[r][q], s[q][col]);
+          mac(a1, t[r][q - 2], s[q - 2][col]);
+        }
+        if (q > r) mac(a0, t[r][q], s[q][col]);
+      }
+      R v = finish(a0) + finish(a1);
+      v += warp_xor(v, 1);
+      if (act && ((col - r) & 1) == h) s[r][col] = -(v * rp[r]);
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < tb * tb; e += blockDim.x) D[(e / tb) * ld + e % tb] = s[e / tb][e % tb];
+  for (int e = tid; e < tb * tb; e += blockDim.x) {
+    const int r = e / tb, c = e % tb;
+    D[r * ld + c] = s[r][c];
+  }
 }
 
 // One step of the coarse LU outside the diagonal block, in pieces small enough to spread over the
-// SMs (the FP64 work of a 64 x 64 x 64 tile product takes one SM about 70 us):
+// SMs, in the arithmetic R of the factorisation:
 //   MODE 0: L21 = A21 inv(U11), a 16-row piece per CTA (rows of A21 are independent);
 //   MODE 1: U12 = inv(L11) A12, a 16-column piece per CTA (columns of A12 are independent);
 //   MODE 2: A22 -= L21 U12, a 16 x 64 piece per CTA.
-// The operands of a piece are staged in shared memory before it is overwritten.
-template <int MODE>
-__global__ void __launch_bounds__(256) k_e_update(double* A, int n, int64_t ld, int k0, int span) {
-  constexpr int R = (MODE == 1) ? TB : 16;
-  constexpr int C = (MODE == 1) ? 16 : TB;
-  __shared__ double sa[R][TB + 1], sb[TB][C + 1];
+// The operands of a piece are staged in shared memory before it is overwritten; each thread forms
+// four outputs with independent accumulators.
+template <int MODE, class R>
+__global__ void __launch_bounds__(256) k_e_update(R* A, int n, int64_t ld, int k0, int span) {
+  constexpr int PR = (MODE == 1) ? TB : 16;
+  constexpr int PC = (MODE == 1) ? 16 : TB;
+  __shared__ R sa[PR][TB + 1], sb[TB][PC + 1];
   const int tb = min(TB, n - k0);
   const int first = k0 + tb;
   int r0, c0;
@@ -905,58 +959,65 @@ __global__ void __launch_bounds__(256) k_e_update(double* A, int n, int64_t ld, 
   else { r0 = first + blockIdx.y * 16; c0 = first + blockIdx.x * TB; }
   const int end = min(n, first + span);
   if (r0 >= (MODE == 1 ? n : end) || c0 >= (MODE == 0 ? n : end)) return;
-  const int rows = (MODE == 1) ? tb : min(R, end - r0);
-  const int cols = (MODE == 0) ? tb : min(C, end - c0);
-  const double* Dg = A + (int64_t)k0 * ld + k0;
+  const int rows = (MODE == 1) ? tb : min(PR, end - r0);
+  const int cols = (MODE == 0) ? tb : min(PC, end - c0);
+  const R* Dg = A + (int64_t)k0 * ld + k0;
+  const R zero(0.0), one(1.0);
   // A operand: MODE 0 the rows of A21, MODE 1 unit-lower inv(L11), MODE 2 the rows of L21
-  for (int e = threadIdx.x; e < R * TB; e += blockDim.x) {
+  for (int e = threadIdx.x; e < PR * TB; e += blockDim.x) {
     const int r = e / TB, q = e % TB;
-    double v = 0.0;
+    R v = zero;
     if (r < rows && q < tb) {
-      if (MODE == 1) v = (q < r) ? Dg[(int64_t)r * ld + q] : (q == r ? 1.0 : 0.0);
+      if (MODE == 1) v = (q < r) ? Dg[(int64_t)r * ld + q] : (q == r ? one : zero);
       else v = A[(int64_t)(r0 + r) * ld + k0 + q];
     }
     sa[r][q] = v;
   }
   // B operand: MODE 0 upper inv(U11), MODE 1 the columns of A12, MODE 2 the columns of U12
-  for (int e = threadIdx.x; e < TB * C; e += blockDim.x) {
-    const int q = e / C, c = e % C;
-    double v = 0.0;
+  for (int e = threadIdx.x; e < TB * PC; e += blockDim.x) {
+    const int q = e / PC, c = e % PC;
+    R v = zero;
     if (q < tb && c < cols) {
-      if (MODE == 0) v = (c >= q) ? Dg[(int64_t)q * ld + c] : 0.0;
+      if (MODE == 0) v = (c >= q) ? Dg[(int64_t)q * ld + c] : zero;
       else v = A[(int64_t)(k0 + q) * ld + c0 + c];
     }
     sb[q][c] = v;
   }
   __syncthreads();
-  // 256 threads x 4 outputs
-  for (int o = threadIdx.x; o < R * C; o += blockDim.x) {
-    const int r = o / C, c = o % C;
-    double acc = 0.0;
-#pragma unroll 8
-    for (int q = 0; q < TB; ++q) acc += sa[r][q] * sb[q][c];
+  static_assert(PR * PC == 4 * 256, "four outputs per thread");
+  R acc[4] = {zero, zero, zero, zero};
+#pragma unroll 4
+  for (int q = 0; q < TB; ++q)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int o = threadIdx.x + 256 * j;
+      mac(acc[j], sa[o / PC][q], sb[q][o % PC]);
+    }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int o = threadIdx.x + 256 * j;
+    const int r = o / PC, c = o % PC;
     if (r < rows && c < cols) {
-      double* dst = (MODE == 1) ? A + (int64_t)(k0 + r) * ld + c0 + c : A + (int64_t)(r0 + r) * ld + c0 + c;
-      if (MODE == 2) *dst -= acc;
-      else *dst = acc;
+      R* dst = (MODE == 1) ? A + (int64_t)(k0 + r) * ld + c0 + c : A + (int64_t)(r0 + r) * ld + c0 + c;
+      if (MODE == 2) *dst = *dst - finish(acc[j]);
+      else *dst = finish(acc[j]);
     }
   }
 }
 
-// X = inv(U) inv(L) I, one 32-column slab per CTA (F holds the block-inverted LU)
-// Acc: the arithmetic of the substitutions (FP64, or double-float in the mixed form); F and X are FP64.
+// X = inv(U) inv(L) I, one 32-column slab per CTA (F holds the block-inverted LU), all in the
+// arithmetic and storage R of the factorisation
 constexpr int EINV_W = 32;
-template <class Acc>
-__global__ void __launch_bounds__(256) k_e_inverse(const double* F, int n, int64_t ld, double* X, int64_t ldx,
-                                                   int band) {
-  __shared__ Acc sA[GK * 65], sB[GK * 33];
+template <class R>
+__global__ void __launch_bounds__(256) k_e_inverse(const R* F, int n, int64_t ld, R* X, int64_t ldx, int band) {
+  __shared__ R sA[GK * 65], sB[GK * 33];
   const int c0 = blockIdx.x * EINV_W;
   const int pc = min(EINV_W, n - c0);
   const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
-  double* Xs = X + c0;
+  R* Xs = X + c0;
   for (int e = tid; e < n * pc; e += 256) {
     const int r = e / pc, c = e % pc;
-    Xs[(int64_t)r * ldx + c] = (r == c0 + c) ? 1.0 : 0.0;
+    Xs[(int64_t)r * ldx + c] = (r == c0 + c) ? R(1.0) : R(0.0);
   }
   __syncthreads();
   const int nb = (n + TB - 1) / TB;
@@ -966,22 +1027,22 @@ __global__ void __launch_bounds__(256) k_e_inverse(const double* F, int n, int64
       const int b = pass == 0 ? bb : nb - 1 - bb;
       if (pass == 0 && b < bstart) continue;
       const int r0 = b * TB, tb = min(TB, n - r0);
-      Acc acc[2][4];
+      R acc[2][4];
 #pragma unroll
       for (int u = 0; u < 2; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+        for (int v = 0; v < 4; ++v) acc[u][v] = R(0.0);
       if (pass == 0) {
         const int k0 = max(bstart * TB, r0 - band);  // L(r, c) = 0 for c < r - band
         if (r0 > k0)
-          cta_gemm_n32<double, Acc>(F + (int64_t)r0 * ld + k0, ld, Xs + (int64_t)k0 * ldx, ldx, tb, pc, r0 - k0,
-                                    0, acc, sA, sB);
+          cta_gemm_n32<R, R>(F + (int64_t)r0 * ld + k0, ld, Xs + (int64_t)k0 * ldx, ldx, tb, pc, r0 - k0, 0, acc,
+                             sA, sB);
       } else {
         const int e0 = r0 + tb;
         const int e1 = min(n, r0 + tb + band);       // U(r, c) = 0 for c > r + band
         if (e0 < e1)
-          cta_gemm_n32<double, Acc>(F + (int64_t)r0 * ld + e0, ld, Xs + (int64_t)e0 * ldx, ldx, tb, pc, e1 - e0,
-                                    0, acc, sA, sB);
+          cta_gemm_n32<R, R>(F + (int64_t)r0 * ld + e0, ld, Xs + (int64_t)e0 * ldx, ldx, tb, pc, e1 - e0, 0, acc,
+                             sA, sB);
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u)
@@ -989,58 +1050,86 @@ __global__ void __launch_bounds__(256) k_e_inverse(const double* F, int n, int64
         for (int v = 0; v < 4; ++v) {
           const int r = ty * 2 + u, c = tx * 4 + v;
           if (r < tb && c < pc) {
-            double* x = Xs + (int64_t)(r0 + r) * ldx + c;
-            *x = (double)((Acc)*x - acc[u][v]);
+            R* x = Xs + (int64_t)(r0 + r) * ldx + c;
+            *x = *x - finish(acc[u][v]);
           }
         }
       __syncthreads();
-      Acc acc2[2][4];
+      R acc2[2][4];
 #pragma unroll
       for (int u = 0; u < 2; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc2[u][v] = 0;
-      cta_gemm_n32<double, Acc>(F + (int64_t)r0 * ld + r0, ld, Xs + (int64_t)r0 * ldx, ldx, tb, pc, tb,
-                                pass == 0 ? 1 : 2, acc2, sA, sB);
+        for (int v = 0; v < 4; ++v) acc2[u][v] = R(0.0);
+      cta_gemm_n32<R, R>(F + (int64_t)r0 * ld + r0, ld, Xs + (int64_t)r0 * ldx, ldx, tb, pc, tb,
+                         pass == 0 ? 1 : 2, acc2, sA, sB);
 #pragma unroll
       for (int u = 0; u < 2; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           const int r = ty * 2 + u, c = tx * 4 + v;
-          if (r < tb && c < pc) Xs[(int64_t)(r0 + r) * ldx + c] = (double)finish(acc2[u][v]);
+          if (r < tb && c < pc) Xs[(int64_t)(r0 + r) * ldx + c] = finish(acc2[u][v]);
         }
       __syncthreads();
     }
   }
 }
 
-void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv, int band) {
+// in-place conversions between an FP64 array and its double-float image (same 8-byte slots)
+__global__ void k_to_dfloat_inplace(int64_t count, double* p) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const dfloat v(p[e]);
+    reinterpret_cast<dfloat*>(p)[e] = v;
+  }
+}
+__global__ void k_to_double_inplace(int64_t count, double* p) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)reinterpret_cast<const dfloat*>(p)[e];
+    p[e] = v;
+  }
+}
+
+template <class R>
+static void dense_inverse_t(a2ls_handle* h, R* E, int n, double scale, R* Einv, int band) {
   cudaStream_t st = h->st;
   const int64_t ld = n;
-  if (band <= 0 || band >= n) band = n;
   {
-  KTime kt(h, KT_COARSE_LU, 2.0 / 3.0 * (double)n * n * n);
-  for (int k0 = 0; k0 < n; k0 += TB) {
-    k_e_diag<<<1, 256, 0, st>>>(E, n, ld, k0, scale, h->d_status);
-    A2LS_LAUNCH();
-    // entries farther than the bandwidth from the diagonal are zero and stay zero
-    const int rest = min(n - k0 - min(TB, n - k0), band + TB);
-    if (rest <= 0) break;
-    const int p16 = ceil_div(rest, 16);
-    k_e_update<0><<<p16, 256, 0, st>>>(E, n, ld, k0, rest);
-    A2LS_LAUNCH();
-    k_e_update<1><<<p16, 256, 0, st>>>(E, n, ld, k0, rest);
-    A2LS_LAUNCH();
-    k_e_update<2><<<dim3(ceil_div(rest, TB), p16), 256, 0, st>>>(E, n, ld, k0, rest);
-    A2LS_LAUNCH();
-  }
+    KTime kt(h, KT_COARSE_LU, 2.0 / 3.0 * (double)n * n * n);
+    for (int k0 = 0; k0 < n; k0 += TB) {
+      k_e_diag<R><<<1, 256, 0, st>>>(E, n, ld, k0, scale, h->d_status);
+      A2LS_LAUNCH();
+      // entries farther than the bandwidth from the diagonal are zero and stay zero
+      const int rest = min(n - k0 - min(TB, n - k0), band + TB);
+      if (rest <= 0) break;
+      const int p16 = ceil_div(rest, 16);
+      k_e_update<0, R><<<p16, 256, 0, st>>>(E, n, ld, k0, rest);
+      A2LS_LAUNCH();
+      k_e_update<1, R><<<p16, 256, 0, st>>>(E, n, ld, k0, rest);
+      A2LS_LAUNCH();
+      k_e_update<2, R><<<dim3(ceil_div(rest, TB), p16), 256, 0, st>>>(E, n, ld, k0, rest);
+      A2LS_LAUNCH();
+    }
   }
   KTime kt2(h, KT_COARSE_INV, 4.0 / 3.0 * (double)n * n * n);
-  // the mixed form forms the inverse from the FP64 factors in double-float arithmetic
-  if (h->opt.precision == A2LS_FP32)
-    k_e_inverse<dfloat><<<ceil_div(n, EINV_W), 256, 0, st>>>(E, n, ld, Einv, ld, band);
-  else
-    k_e_inverse<double><<<ceil_div(n, EINV_W), 256, 0, st>>>(E, n, ld, Einv, ld, band);
+  k_e_inverse<R><<<ceil_div(n, EINV_W), 256, 0, st>>>(E, n, ld, Einv, ld, band);
   A2LS_LAUNCH();
+}
+
+// The coarse operator E (FP64, n x n, overwritten) factored and inverted into Einv (FP64).  The
+// mixed form runs the factorisation and the inverse in double-float arithmetic on double-float
+// images of E and Einv held in the same buffers.
+void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv, int band) {
+  if (band <= 0 || band >= n) band = n;
+  const int64_t nn = (int64_t)n * n;
+  const int grid = (int)std::min<int64_t>(152 * 8, (nn + 255) / 256 + 1);
+  if (h->opt.precision == A2LS_FP32) {
+    k_to_dfloat_inplace<<<grid, 256, 0, h->st>>>(nn, E);
+    A2LS_LAUNCH();
+    dense_inverse_t<dfloat>(h, reinterpret_cast<dfloat*>(E), n, scale, reinterpret_cast<dfloat*>(Einv), band);
+    k_to_double_inplace<<<grid, 256, 0, h->st>>>(nn, Einv);
+    A2LS_LAUNCH();
+  } else {
+    dense_inverse_t<double>(h, E, n, scale, Einv, band);
+  }
 }
 
 }  // namespace a2ls

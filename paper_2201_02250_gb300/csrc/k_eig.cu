@@ -258,27 +258,28 @@ template <class T>
 __global__ void __launch_bounds__(EIG_THREADS) k_project_k(const int* ni, const int* off, const int64_t* xoff,
                                                             int ldx, int col0, const int* pvec,
                                                             const int* active, const int* kd,
-                                                            const double* kvec, T* X) {
+                                                            const typename EAcc<T>::type* kvec, T* X) {
   using Acc = typename EAcc<T>::type;
-  __shared__ double dots[EIG_MAXP];
+  __shared__ Acc dots[EIG_MAXP];
   const int i = blockIdx.x;
   if ((active && !active[i]) || !kd[i]) return;
   const int n = ni[i], p = pvec[i], o = off[i];
   T* Xi = X + xoff[i] + col0;
-  for (int c = threadIdx.x; c < p; c += EIG_THREADS) dots[c] = 0.0;
+  for (int c = threadIdx.x; c < p; c += EIG_THREADS) dots[c] = 0;
   __syncthreads();
   // one warp per column
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int c = wid; c < p; c += EIG_THREADS / 32) {
     Acc d = 0;
-    for (int l = lane; l < n; l += 32) d += (Acc)kvec[o + l] * (Acc)Xi[(int64_t)l * ldx + c];
+    for (int l = lane; l < n; l += 32) mac(d, kvec[o + l], (Acc)Xi[(int64_t)l * ldx + c]);
+    d = finish(d);
     for (int w = 16; w > 0; w >>= 1) d += warp_xor(d, w);
-    if (lane == 0) dots[c] = (double)d;
+    if (lane == 0) dots[c] = d;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < n * p; e += EIG_THREADS) {
     const int l = e / p, c = e % p;
-    Xi[(int64_t)l * ldx + c] = (T)((Acc)Xi[(int64_t)l * ldx + c] - (Acc)dots[c] * (Acc)kvec[o + l]);
+    Xi[(int64_t)l * ldx + c] = (T)((Acc)Xi[(int64_t)l * ldx + c] - dots[c] * kvec[o + l]);
   }
 }
 
@@ -1006,14 +1007,20 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   // T applied to V[:, vcol : vcol + p] -> W[:, 0:p]; fwd/bwd_flops: the two triangular halves over the
   // active set, counted inside the envelope of the factors
   double fwd_flops = 0.0, bwd_flops = 0.0;
-  // local CSR values and partition of unity in the arithmetic of the B products
+  // local CSR values, partition of unity and kernel vectors in the arithmetic of the eigensolve
   using BAcc = typename EAcc<T>::type;
   const BAcc* lvalB = nullptr;
   const BAcc* DB = nullptr;
+  const BAcc* kvB = nullptr;
   if constexpr (std::is_same<BAcc, double>::value) {
     lvalB = h->d_lval;
     DB = h->d_D;
+    kvB = kvec;
   } else {
+    BAcc* kv = dalloc<BAcc>(h, h->sum_n);
+    k_convert<BAcc><<<std::min<int64_t>(152 * 8, (h->sum_n + 255) / 256 + 1), 256, 0, st>>>(h->sum_n, kvec, kv);
+    A2LS_LAUNCH();
+    kvB = kv;
     int64_t lnnz = 0;
     A2LS_CUDA(cudaMemcpyAsync(&lnnz, h->d_lrow + h->sum_n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     A2LS_CUDA(cudaStreamSynchronize(st));
@@ -1040,11 +1047,11 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
       KTime kt(h, KT_EIG_SOLVE, bwd_flops);
       block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, pmax, actv, 0, 1);
     }
-    k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, actv, d_kd, kvec, W);
+    k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, actv, d_kd, kvB, W);
     A2LS_LAUNCH();
   };
   auto orthonormalize_W_into_V0 = [&]() {
-    k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, d_active, d_kd, kvec, W);
+    k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, d_active, d_kd, kvB, W);
     A2LS_LAUNCH();
     // no previous basis: jb = 0; R written into H's last rows (discarded)
     k_orth<TV, T><<<N, ORTH_THREADS, orth_smem_for(gcap_k), st>>>(h->d_ni, d_vo, P, d_pv, d_active, 0, b, V, W,
@@ -1195,6 +1202,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   if constexpr (!std::is_same<BAcc, double>::value) {
     dfree(h, const_cast<BAcc*>(lvalB));
     dfree(h, const_cast<BAcc*>(DB));
+    dfree(h, const_cast<BAcc*>(kvB));
   }
   // keep Z (the eigenvectors behind the coarse space) as the warm-start network's training target
   if (h->d_zev) dfree(h, h->d_zev);
