@@ -43,7 +43,8 @@ FP32_PEAK_TFLOPS_DERIVED = 152 * 128 * 2 * 2.07e9 / 1e12
 FP32X2_PEAK_TFLOPS_DERIVED = 152 * 128 * 2.07e9 * 2 / 12 / 1e12
 # arithmetic of each tracked kernel in the mixed form (the plain form is FP64 throughout)
 MIXED_KERNEL_DTYPE = {"lu_local": "f32", "lu_splitting": "f32x2", "eig_triangular_solves": "f32x2",
-                      "eig_orthogonalisation": "f32x2"}
+                      "eig_orthogonalisation": "f32x2", "eig_rayleigh_ritz": "f32x2", "coarse_lu": "f32x2",
+                      "coarse_inverse": "f32x2"}
 
 
 def parse_args():
@@ -435,12 +436,14 @@ def report(args, res, world) -> dict:
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 local solves, f32x2 (double-float) splitting LU and eigensolves, f64 GMRES/SpMV/Rayleigh-Ritz/coarse",
+        "dtype": ("f32 local solves, f32x2 (double-float) splitting LU, eigensolves and coarse factorisation, "
+                  "f64 GMRES/SpMV/coarse apply"),
         "data": "synthetic (seeded generator, workloads.pde.config_c2)",
         "config": {"workload": WORKLOAD if args.workload == "c2" else prob.name, "n": prob.n, "nnz": int(prob.A.nnz), "subdomains": int(prob.nparts),
                    "overlap": prob.overlap, "nev": prob.nev, "rtol": 1e-8, "restart": 30,
                    "form": ("mixed: double-float LU of the splittings (interior block shared with A_ii), FP32 A_ii "
-                            "factors and local solves, double-float local eigensolves to 1e-4, FGMRES(30) in FP64"),
+                            "factors and local solves, double-float local eigensolves to 1e-4, double-float coarse LU "
+                            "and inverse, FGMRES(30) in FP64"),
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
         "iters": mixed[-1]["iters"],
         "eig_unconverged_subdomains": mixed[-1]["eig_unconverged"],

@@ -18,6 +18,7 @@ struct dfloat {
   dfloat() = default;
   __host__ __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
   __host__ __device__ dfloat(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  __host__ __device__ constexpr dfloat(float x) : hi(x), lo(0.f) {}
   __host__ __device__ dfloat(int x) : dfloat((double)x) {}
   __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
   __host__ __device__ explicit operator float() const { return hi + lo; }

@@ -471,15 +471,16 @@ __device__ void gram_product(const TX* X, const TY* Y, int64_t ldx, int n, int n
 }
 
 // One warp: G (p x p, stride p) = R^T R by Cholesky, R into G's upper triangle, Ri = inv(R) (stride p).
-// A pivot at or below 1e-28 of the largest diagonal (or abs_floor) marks a rank-deficient block; it is
-// floored so that inv(R) stays finite in the working precision and a zero column stays zero.
-// Returns 1 when no pivot was floored (valid on every lane).
-__device__ int warp_cholesky_inverse(double* G, int p, double* Ri, double abs_floor) {
+// A pivot at or below rel_floor of the largest diagonal (or abs_floor) marks a rank-deficient block:
+// rel_floor is the squared unit roundoff of the arithmetic that formed G (at least 1e-28), below which
+// a pivot is rounding noise.  It is floored so that inv(R) amplifies that noise to O(1) at most and a
+// zero column stays zero.  Returns 1 when no pivot was floored (valid on every lane).
+__device__ int warp_cholesky_inverse(double* G, int p, double* Ri, double abs_floor, double rel_floor) {
   const int lane = threadIdx.x & 31;
   double gm = 0.0;
   for (int a = lane; a < p; a += 32) gm = fmax(gm, G[a * p + a]);
   for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
-  const double floor_d = fmax(1e-28 * gm, abs_floor);
+  const double floor_d = fmax(rel_floor * gm, abs_floor);
   int ok = 1;
   for (int a = 0; a < p; ++a) {
     double part = 0.0;
@@ -590,7 +591,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
         for (int a = tid; a < p; a += 32) G[a * p + a] += shift;
         __syncwarp();
       }
-      const int ok = warp_cholesky_inverse(G, p, Ri, Tiny<Acc>::v);
+      const int ok = warp_cholesky_inverse(G, p, Ri, Tiny<Acc>::v, fmax(1e-28, Unit<Acc>::u * Unit<Acc>::u));
       if (tid == 0) {
         rank_ok = ok;
         if (!ok && rank_flag) atomicAdd(rank_flag + i, 1);
