@@ -157,6 +157,57 @@ __device__ __forceinline__ void cta_gemm_n8(const T* __restrict__ A, int64_t lda
   }
 }
 
+// Inverses of the triangles of a factored tb x tb block t (unit lower L strictly below the diagonal,
+// U on and above it) into s, given rp[c] = 1 / U_cc.  256 threads, two per column: each sums every
+// other term of the column's dot products with two accumulators (a quarter of the serial chain);
+// threads 0-127 form inv(L), 128-255 inv(U).  The pair sums are full-warp shuffles, so every thread
+// of the block must call this.
+template <class R>
+__device__ void tile_inverses(const R (*t)[TB + 1], R (*s)[TB + 1], const R* rp, int tb) {
+  const int tid = threadIdx.x;
+  const int col = (tid & 127) >> 1, h = tid & 1;
+  const bool active_col = col < tb;
+  if (tid < 128) {
+    // inv(L), column col: x_r = -(L[r][col] + sum_{q=col+1}^{r-1} L[r][q] x_q); this thread sums the q
+    // with (q - col - 1) % 2 == h and writes the rows r with (r - col - 1) % 2 == h, so it reads only
+    // entries that it wrote itself
+    for (int r = 1; r < TB; ++r) {  // uniform across the warp
+      R a0 = R(0.0), a1 = R(0.0);
+      const bool act = active_col && r > col && r < tb;
+      if (act) {
+        int q = col + 1 + h;
+        for (; q + 2 < r; q += 4) {
+          mac(a0, t[r][q], s[q][col]);
+          mac(a1, t[r][q + 2], s[q + 2][col]);
+        }
+        if (q < r) mac(a0, t[r][q], s[q][col]);
+      }
+      R v = finish(a0) + finish(a1);
+      v += warp_xor(v, 1);
+      if (act && ((r - col - 1) & 1) == h) s[r][col] = -(t[r][col] + v);
+    }
+  } else {
+    // inv(U), column col: x_col = 1 / U_col,col, x_r = -(sum_{q=r+1}^{col} U[r][q] x_q) / U_rr; this
+    // thread sums the q with (col - q) % 2 == h and writes the rows with (col - r) % 2 == h
+    if (active_col && h == 0) s[col][col] = rp[col];
+    for (int r = TB - 2; r >= 0; --r) {
+      R a0 = R(0.0), a1 = R(0.0);
+      const bool act = active_col && r < col;
+      if (act) {
+        int q = col - h;
+        for (; q - 2 > r; q -= 4) {
+          mac(a0, t[r][q], s[q][col]);
+          mac(a1, t[r][q - 2], s[q - 2][col]);
+        }
+        if (q > r) mac(a0, t[r][q], s[q][col]);
+      }
+      R v = finish(a0) + finish(a1);
+      v += warp_xor(v, 1);
+      if (act && ((col - r) & 1) == h) s[r][col] = -(v * rp[r]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // batched LU without pivoting
 // ---------------------------------------------------------------------------
@@ -237,6 +288,7 @@ __global__ void __launch_bounds__(256, 2) k_lu(int N, const int* ni, const int* 
   using Acc = typename AccOf<T>::type;
   extern __shared__ __align__(16) unsigned char lu_smem_raw[];
   __shared__ unsigned char lnz[MAXN_LOCAL / TB + 1], unz[MAXN_LOCAL / TB + 1];
+  __shared__ Acc rdiag[TB];                       // reciprocals of the diagonal block's pivots
   Acc* Dm = reinterpret_cast<Acc*>(lu_smem_raw);  // 64 x 65: the diagonal block, factored in place
   Acc* Iv = Dm + TB * 65;                         // 64 x 65: inv(L11) strictly below, inv(U11) on/above
   Acc* sA = Iv + TB * 65;                         // TGK x TS (16-byte aligned: 2 * 64 * 65 is even)
@@ -256,23 +308,26 @@ __global__ void __launch_bounds__(256, 2) k_lu(int N, const int* ni, const int* 
     for (int e = tid; e < w * w; e += 256) Dm[(e / w) * 65 + e % w] = (Acc)A[(int64_t)(k0 + e / w) * L + k0 + e % w];
     __syncthreads();
     for (int c = 0; c < w; ++c) {
-      double piv = (double)Dm[c * 65 + c];
       if (allow_last_zero && k0 + c == n - 1) {
         // record the last pivot of A~_ii and replace it by the scale; the eigensolver decides from it
         // whether A~_ii is singular
         if (tid == 0) {
-          last_pivot[i] = piv;
+          last_pivot[i] = (double)Dm[c * 65 + c];
           Dm[c * 65 + c] = (Acc)scale;
+          rdiag[c] = Acc(1.0) / Dm[c * 65 + c];
         }
         break;
       }
-      if (fabs(piv) <= tiny) piv = scale;
-      const Acc pinv = (Acc)(1.0 / piv);
-      __syncthreads();
-      if (tid == 0 && piv == scale && fabs((double)Dm[c * 65 + c]) <= tiny) {
-        raise_status(st, A2LS_ERR_SINGULAR, i, k0 + c);
-        Dm[c * 65 + c] = (Acc)scale;
+      // one thread checks the pivot and forms its reciprocal in the working arithmetic
+      if (tid == 0) {
+        if (fabs((double)Dm[c * 65 + c]) <= tiny) {
+          raise_status(st, A2LS_ERR_SINGULAR, i, k0 + c);
+          Dm[c * 65 + c] = (Acc)scale;
+        }
+        rdiag[c] = Acc(1.0) / Dm[c * 65 + c];
       }
+      __syncthreads();
+      const Acc pinv = rdiag[c];
       for (int r = c + 1 + tid; r < w; r += 256) Dm[r * 65 + c] = Dm[r * 65 + c] * pinv;
       __syncthreads();
       const int m = w - 1 - c;
@@ -286,24 +341,8 @@ __global__ void __launch_bounds__(256, 2) k_lu(int N, const int* ni, const int* 
     for (int e = tid; e < w * w; e += 256) A[(int64_t)(k0 + e / w) * L + k0 + e % w] = (T)Dm[(e / w) * 65 + e % w];
     const int c0 = k0 + w;
     if (c0 >= n) break;
-    // inverses of the triangles: threads 0..63 columns of inv(L11), threads 64..127 columns of inv(U11)
-    {
-      const int c = tid & (TB - 1);
-      if (tid < TB && c < w) {
-        for (int r = c + 1; r < w; ++r) {
-          Acc v = Dm[r * 65 + c];
-          for (int q = c + 1; q < r; ++q) mac(v, Dm[r * 65 + q], Iv[q * 65 + c]);
-          Iv[r * 65 + c] = -finish(v);
-        }
-      } else if (tid >= TB && tid < 2 * TB && c < w) {
-        Iv[c * 65 + c] = (Acc)(1.0 / (double)Dm[c * 65 + c]);
-        for (int r = c - 1; r >= 0; --r) {
-          Acc v = 0;
-          for (int q = r + 1; q <= c; ++q) mac(v, Dm[r * 65 + q], Iv[q * 65 + c]);
-          Iv[r * 65 + c] = -(finish(v) * (Acc)(1.0 / (double)Dm[r * 65 + r]));
-        }
-      }
-    }
+    // inverses of the triangles: inv(L11) strictly below the diagonal, inv(U11) on and above
+    tile_inverses<Acc>(reinterpret_cast<const Acc(*)[TB + 1]>(Dm), reinterpret_cast<Acc(*)[TB + 1]>(Iv), rdiag, w);
     const int tiles = (n - c0 + TB - 1) / TB;
     // envelope: a row tile of L21 is nonzero only if one of its rows starts left of c0, a column tile
     // of U12 only if one of its columns starts above c0
@@ -453,12 +492,17 @@ template void schur_copy<dfloat, float>(a2ls_handle*, const dfloat*, float*, con
 // ---------------------------------------------------------------------------
 // inversion of the diagonal tiles (in place): inv(L_bb) strictly lower, inv(U_bb) upper
 // ---------------------------------------------------------------------------
-// one CTA of 128 threads per (subdomain, diagonal tile): threads 0..63 form the columns of inv(L_bb)
-// below the diagonal, threads 64..127 those of inv(U_bb), in FP64 in shared memory
+// arithmetic of the tile inverses: FP64 for FP64 factors, double-float for FP32 and double-float ones
+template <class T> struct InvAcc { using type = dfloat; };
+template <> struct InvAcc<double> { using type = double; };
+
+// one CTA of 256 threads per (subdomain, diagonal tile), in shared memory
 template <class T>
-__global__ void __launch_bounds__(2 * TB) k_invert_tiles(const int* ni, const int* ld, const int64_t* foff,
+__global__ void __launch_bounds__(4 * TB) k_invert_tiles(const int* ni, const int* ld, const int64_t* foff,
                                                          T* fac) {
-  __shared__ double t[TB][TB + 1], s[TB][TB + 1];
+  using R = typename InvAcc<T>::type;
+  __shared__ R t[TB][TB + 1], s[TB][TB + 1];
+  __shared__ R rp[TB];
   const int i = blockIdx.x, b = blockIdx.y;
   const int n = ni[i];
   const int r0 = b * TB;
@@ -466,32 +510,18 @@ __global__ void __launch_bounds__(2 * TB) k_invert_tiles(const int* ni, const in
   const int tb = min(TB, n - r0);
   const int64_t L = ld[i];
   T* A = fac + foff[i] + (int64_t)r0 * L + r0;
-  for (int e = threadIdx.x; e < tb * tb; e += blockDim.x) t[e / tb][e % tb] = (double)A[(e / tb) * L + e % tb];
+  for (int e = threadIdx.x; e < tb * tb; e += blockDim.x) t[e / tb][e % tb] = R(A[(e / tb) * L + e % tb]);
   __syncthreads();
-  const int c = threadIdx.x & (TB - 1);
-  if (threadIdx.x < TB && c < tb) {
-    // inv(L) (unit lower), column c below the diagonal: x_r = -(L[r][c] + sum_{q=c+1}^{r-1} L[r][q] x_q)
-    for (int r = c + 1; r < tb; ++r) {
-      double v = t[r][c];
-      for (int q = c + 1; q < r; ++q) v += t[r][q] * s[q][c];
-      s[r][c] = -v;
-    }
-  } else if (threadIdx.x >= TB && c < tb) {
-    // inv(U), column c on and above the diagonal
-    s[c][c] = 1.0 / t[c][c];
-    for (int r = c - 1; r >= 0; --r) {
-      double v = 0.0;
-      for (int q = r + 1; q <= c; ++q) v += t[r][q] * s[q][c];
-      s[r][c] = -v / t[r][r];
-    }
-  }
+  if (threadIdx.x < tb) rp[threadIdx.x] = R(1.0) / t[threadIdx.x][threadIdx.x];
+  __syncthreads();
+  tile_inverses<R>(t, s, rp, tb);
   __syncthreads();
   for (int e = threadIdx.x; e < tb * tb; e += blockDim.x) A[(e / tb) * L + e % tb] = (T)s[e / tb][e % tb];
 }
 
 template <class T> void invert_diag_tiles(a2ls_handle* h, T* fac) {
   dim3 grid(h->N, ceil_div(h->max_n, TB));
-  k_invert_tiles<T><<<grid, 2 * TB, 0, h->st>>>(h->d_ni, h->d_ld, h->d_foff, fac);
+  k_invert_tiles<T><<<grid, 4 * TB, 0, h->st>>>(h->d_ni, h->d_ld, h->d_foff, fac);
   A2LS_LAUNCH();
 }
 
@@ -851,8 +881,7 @@ namespace a2ls {
 // subtracts a21 (a12 / pivot)^T from the trailing block, so that the multipliers of column c are
 // formed only once, after the loop (l_rc = a_rc / pivot_c).  The owner of entry (c+1, c+1) checks the
 // next pivot right after its own update, so each step needs one barrier.
-// Inverses: two threads per column, each summing every other term of the column's dot products with
-// two accumulators (a quarter of the serial chain); threads 0-127 form inv(L), 128-255 inv(U).
+// Inverses: tile_inverses (two threads per column).
 template <class R>
 __device__ __forceinline__ R e_recip(R x) { return R(1.0) / x; }
 
@@ -891,47 +920,7 @@ __global__ void __launch_bounds__(256) k_e_diag(R* A, int n, int64_t ld, int k0,
     if (r > c) t[r][c] *= rp[c];
   }
   __syncthreads();
-  const int col = (tid & 127) >> 1, h = tid & 1;
-  const bool active_col = col < tb;
-  if (tid < 128) {
-    // inv(L) (unit lower), column col: x_r = -(L[r][col] + sum_{q=col+1}^{r-1} L[r][q] x_q); this thread
-    // sums the q with (q - col - 1) % 2 == h and writes the rows r with (r - col - 1) % 2 == h, so it
-    // reads only entries that it wrote itself
-    for (int r = 1; r < TB; ++r) {  // uniform across the warp: the pair sum below is a full-warp shuffle
-      R a0 = R(0.0), a1 = R(0.0);
-      const bool act = active_col && r > col && r < tb;
-      if (act) {
-        int q = col + 1 + h;
-        for (; q + 2 < r; q += 4) {
-          mac(a0, t[r][q], s[q][col]);
-          mac(a1, t[r][q + 2], s[q + 2][col]);
-        }
-        if (q < r) mac(a0, t[r][q], s[q][col]);
-      }
-      R v = finish(a0) + finish(a1);
-      v += warp_xor(v, 1);
-      if (act && ((r - col - 1) & 1) == h) s[r][col] = -(t[r][col] + v);
-    }
-  } else {
-    // inv(U), column col: x_col = 1 / U_col,col, x_r = -(sum_{q=r+1}^{col} U[r][q] x_q) / U_rr; this
-    // thread sums the q with (col - q) % 2 == h and writes the rows with (col - r) % 2 == h
-    if (active_col && h == 0) s[col][col] = rp[col];
-    for (int r = TB - 2; r >= 0; --r) {
-      R a0 = R(0.0), a1 = R(0.0);
-      const bool act = active_col && r < col;
-      if (act) {
-        int q = col - h;
-        for (; q - 2 > r; q -= 4) {
-          mac(a0, t[r][q], s[q][col]);
-          mac(a1, t[r][q - 2], s[q - 2][col]);
-        }
-        if (q > r) mac(a0, t[r][q], s[q][col]);
-      }
-      R v = finish(a0) + finish(a1);
-      v += warp_xor(v, 1);
-      if (act && ((col - r) & 1) == h) s[r][col] = -(v * rp[r]);
-    }
-  }
+  tile_inverses<R>(t, s, rp, tb);
   __syncthreads();
   for (int e = tid; e < tb * tb; e += blockDim.x) {
     const int r = e / tb, c = e % tb;

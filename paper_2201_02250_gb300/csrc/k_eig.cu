@@ -1108,7 +1108,15 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
       }
     }
     {
-      KTime kt(h, KT_EIG_RR);
+      // algorithmic work: a real Schur form with its orthogonal factor (25 m^3, the usual count for
+      // Hessenberg reduction plus Francis iteration) and the coefficients of b Ritz vectors (2 b m^2)
+      double rr_flops = 0.0;
+      for (int i = 0; i < N; ++i) {
+        if (!act[i]) continue;
+        const double m = full[i] ? (double)mfull[i] : (double)s * b;
+        rr_flops += 25.0 * m * m * m + 2.0 * b * m * m;
+      }
+      KTime kt(h, KT_EIG_RR, rr_flops);
       k_rayleigh_ritz<RT><<<N, RR_THREADS, rr_smem, st>>>(prm, d_full, d_mfull, d_nf, d_active, H, Y, d_ycols, d_zcols,
                                               eigout, d_conv, h->d_status);
       A2LS_LAUNCH();
