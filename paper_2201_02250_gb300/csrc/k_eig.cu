@@ -382,92 +382,131 @@ __device__ void small_cholesky_inverse(double* G, int p, double* Ri, int& rank_o
 
 constexpr int ORTH_THREADS = 512;
 constexpr int ORC_MAX = 64;              // rows staged per chunk in k_orth (64, or 32 with full-space Gram)
-constexpr int SROW = EIG_MAXP + 1;       // row stride of the staged chunks (odd: rows fall on different banks)
-constexpr int ORTH_NB = (EIG_MAXP / 2) * (EIG_MAXP / 2) / ORTH_THREADS + 1;  // Gram items per thread
+// row stride of the staged chunks: even, so that column pairs are 16-byte aligned for vector loads;
+// 98 x 8 bytes puts consecutive rows 4 banks apart
+constexpr int SROW = EIG_MAXP + 2;
+constexpr int GRAM_NG_MAX = 16;          // row groups (split-K) of a Gram product
 
-// stage rows [l0, l0 + rows) of M (cols 0:w) into S (stride SROW), zero padding column w
+// stage rows [l0, l0 + rows) of M (cols 0:w) into S (stride SROW), zero padding to a multiple of 4
 template <class Acc, class TM>
 __device__ __forceinline__ void stage_rows(Acc* S, const TM* M, int64_t ldx, int l0, int rows, int w) {
-  const int wp = w + (w & 1);
+  const int wp = (w + 3) & ~3;
   for (int e = threadIdx.x; e < rows * wp; e += ORTH_THREADS) {
     const int r = e / wp, c = e % wp;
     S[r * SROW + c] = c < w ? (Acc)M[(int64_t)(l0 + r) * ldx + c] : (Acc)0;
   }
 }
 
+// two consecutive staged values with one vector load (p is aligned to twice the element size)
+__device__ __forceinline__ void ld2(const double* p, double& a, double& b) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void ld2(const dfloat* p, dfloat& a, dfloat& b) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = dfloat(v.x, v.y);
+  b = dfloat(v.z, v.w);
+}
+__device__ __forceinline__ void ld2(const float* p, float& a, float& b) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  a = v.x;
+  b = v.y;
+}
+
 // Gram product G (nx x ny, row-major, stride ny) = X^T Y over the n rows of X and Y (global, leading
-// dimension ldx), split into 2x2 output blocks and, when there are fewer blocks than threads, into
-// ng row groups (split-K) whose partial sums are added at the end.  Xs, Ys: staging chunks; Ps:
-// scratch of ORTH_THREADS x 4 values for the partial sums (may alias Xs).  Ends with a barrier.
+// dimension ldx).  Each item is a 4 x 2 output block; with fewer blocks than threads the rows are
+// split into ng groups (split-K) whose partial sums are added at the end.  same (X == Y, nx == ny):
+// only the blocks that reach the upper triangle are formed, the lower triangle is mirrored.
+// Xs, Ys: staging chunks; Ps: scratch of ORTH_THREADS x 8 values for the partial sums (may alias
+// the staging chunks).  Ends with a barrier.
 template <class Acc, class TX, class TY>
 __device__ void gram_product(const TX* X, const TY* Y, int64_t ldx, int n, int nx, int ny, bool same, Acc* Xs,
                              Acc* Ys, double* G, Acc* Ps, int orc) {
   const int tid = threadIdx.x;
-  const int nbr = (nx + 1) / 2, nbc = (ny + 1) / 2, nb = nbr * nbc;
-  const int ng = nb >= ORTH_THREADS ? 1 : min(8, ORTH_THREADS / nb);
+  const int nbr = (nx + 3) / 4, nbc = (ny + 1) / 2;
+  // block (br, bc) covers rows 4br..4br+3 and columns 2bc..2bc+1; with X == Y only bc >= 2br
+  auto row_blocks = [&](int br) { return same ? max(0, nbc - 2 * br) : nbc; };
+  int nb = 0;
+  for (int br = 0; br < nbr; ++br) nb += row_blocks(br);
+  auto block_of = [&](int b, int& a0, int& c0) {
+    int br = 0;
+    while (b >= row_blocks(br)) b -= row_blocks(br++);
+    a0 = 4 * br;
+    c0 = 2 * (nbc - row_blocks(br) + b);
+  };
+  const int ng = nb >= ORTH_THREADS ? 1 : min(GRAM_NG_MAX, ORTH_THREADS / nb);
   const int items = nb * ng;
-  Acc acc[ORTH_NB][4];
+  // more blocks than threads (full-space Gram of a small subdomain): several passes over the rows
+  for (int w0 = 0; w0 < items; w0 += ORTH_THREADS) {
+    const int w = w0 + tid;
+    const bool valid = w < items;
+    int a0 = 0, c0 = 0, g = 0;
+    if (valid) {
+      block_of(w % nb, a0, c0);
+      g = w / nb;
+    }
+    Acc acc[8];
 #pragma unroll
-  for (int k = 0; k < ORTH_NB; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0;
-  for (int l0 = 0; l0 < n; l0 += orc) {
-    const int rows = min(orc, n - l0);
-    stage_rows(Xs, X, ldx, l0, rows, nx);
-    if (!same) stage_rows(Ys, Y, ldx, l0, rows, ny);
-    __syncthreads();
-    const Acc* Yr = same ? Xs : Ys;
+    for (int q = 0; q < 8; ++q) acc[q] = 0;
+    for (int l0 = 0; l0 < n; l0 += orc) {
+      const int rows = min(orc, n - l0);
+      stage_rows(Xs, X, ldx, l0, rows, nx);
+      if (!same) stage_rows(Ys, Y, ldx, l0, rows, ny);
+      __syncthreads();
+      const Acc* Yr = same ? Xs : Ys;
+      if (valid) {
+        Acc s[8];
 #pragma unroll
-    for (int k = 0; k < ORTH_NB; ++k) {
-      const int w = tid + k * ORTH_THREADS;
-      if (w < items) {
-        const int b = w % nb, g = w / nb;
-        const int a0 = 2 * (b / nbc), c0 = 2 * (b % nbc);
-        Acc s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        for (int q = 0; q < 8; ++q) s[q] = 0;
         for (int r = g; r < rows; r += ng) {
-          const Acc x0 = Xs[r * SROW + a0], x1 = Xs[r * SROW + a0 + 1];
-          const Acc y0 = Yr[r * SROW + c0], y1 = Yr[r * SROW + c0 + 1];
-          mac(s0, x0, y0);
-          mac(s1, x0, y1);
-          mac(s2, x1, y0);
-          mac(s3, x1, y1);
+          Acc x[4], y[2];
+          ld2(Xs + r * SROW + a0, x[0], x[1]);
+          ld2(Xs + r * SROW + a0 + 2, x[2], x[3]);
+          ld2(Yr + r * SROW + c0, y[0], y[1]);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            mac(s[2 * u], x[u], y[0]);
+            mac(s[2 * u + 1], x[u], y[1]);
+          }
         }
-        acc[k][0] += finish(s0);
-        acc[k][1] += finish(s1);
-        acc[k][2] += finish(s2);
-        acc[k][3] += finish(s3);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] += finish(s[q]);
       }
+      __syncthreads();
     }
-    __syncthreads();
-  }
-  if (ng == 1) {
+    if (ng == 1) {
+      if (valid)
 #pragma unroll
-    for (int k = 0; k < ORTH_NB; ++k) {
-      const int b = tid + k * ORTH_THREADS;
-      if (b < nb) {
-        const int a0 = 2 * (b / nbc), c0 = 2 * (b % nbc);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 8; ++q) {
           const int a = a0 + (q >> 1), c = c0 + (q & 1);
-          if (a < nx && c < ny) G[a * ny + c] = (double)acc[k][q];
+          if (a < nx && c < ny && (!same || c >= a)) G[a * ny + c] = (double)acc[q];
+        }
+    } else {  // items <= ORTH_THREADS: a single pass
+      if (valid)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) Ps[tid * 8 + q] = acc[q];
+      __syncthreads();
+      if (tid < nb) {
+        block_of(tid, a0, c0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          Acc sum = Ps[tid * 8 + q];
+          for (int gg = 1; gg < ng; ++gg) sum += Ps[(gg * nb + tid) * 8 + q];
+          const int a = a0 + (q >> 1), c = c0 + (q & 1);
+          if (a < nx && c < ny && (!same || c >= a)) G[a * ny + c] = (double)sum;
         }
       }
     }
-  } else {
-    if (tid < items)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) Ps[tid * 4 + q] = acc[0][q];
     __syncthreads();
-    if (tid < nb) {
-      const int a0 = 2 * (tid / nbc), c0 = 2 * (tid % nbc);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        Acc s = Ps[tid * 4 + q];
-        for (int g = 1; g < ng; ++g) s += Ps[(g * nb + tid) * 4 + q];
-        const int a = a0 + (q >> 1), c = c0 + (q & 1);
-        if (a < nx && c < ny) G[a * ny + c] = (double)s;
-      }
-    }
   }
-  __syncthreads();
+  if (same) {
+    for (int e = tid; e < nx * nx; e += ORTH_THREADS) {
+      const int a = e / nx, c = e % nx;
+      if (c < a) G[a * nx + c] = G[c * nx + a];
+    }
+    __syncthreads();
+  }
 }
 
 // One warp: G (p x p, stride p) = R^T R by Cholesky, R into G's upper triangle, Ri = inv(R) (stride p).
@@ -525,7 +564,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
                                                         int vout, const int* fullv, int* rank_flag, int gcap,
                                                         int orc) {
   using Acc = typename EAcc<T>::type;
-  extern __shared__ double sm[];
+  extern __shared__ __align__(16) double sm[];
   const int i = blockIdx.x;
   if (active && !active[i]) return;
   const int full = fullv ? fullv[i] : 0;
@@ -542,7 +581,9 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
   Acc* sw = sv + orc * SROW;                                   // orc * SROW
   __shared__ int rank_ok;
   const int tid = threadIdx.x;
-  const int pp = p + (p & 1);                   // padded column count of the converted coefficients
+  // the updates W -= V G and W <- W inv(R): each thread forms one row of a group of 3 columns (with
+  // 64-row chunks and p = 24 that is exactly one item per thread); coefficients padded to pp columns
+  const int ncg = (p + 2) / 3, pp = 3 * ncg;
   const int npass = jb > 0 ? 2 : 0;
   for (int e = tid; e < jb * p; e += ORTH_THREADS) Hi[(e / p) * EIG_MAXP + hc + e % p] = 0.0;
   for (int pass = 0; pass < npass; ++pass) {
@@ -561,17 +602,19 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
       const int rows = min(orc, n - l0);
       stage_rows(sv, Vi, ldx, l0, rows, jb);
       __syncthreads();
-      for (int e = tid; e < rows * (pp / 2); e += ORTH_THREADS) {
-        const int r = e / (pp / 2), c = 2 * (e % (pp / 2));
-        Acc s0 = 0, s1 = 0;
+      for (int e = tid; e < rows * ncg; e += ORTH_THREADS) {
+        const int r = e / ncg, c = 3 * (e % ncg);
+        Acc s0 = 0, s1 = 0, s2 = 0;
         for (int a = 0; a < jb; ++a) {
           const Acc v = sv[r * SROW + a];
           mac(s0, v, Ga[a * pp + c]);
           mac(s1, v, Ga[a * pp + c + 1]);
+          mac(s2, v, Ga[a * pp + c + 2]);
         }
         TW* w = Wi + (int64_t)(l0 + r) * ldx + c;
         w[0] = (TW)((Acc)w[0] - s0);
         if (c + 1 < p) w[1] = (TW)((Acc)w[1] - s1);
+        if (c + 2 < p) w[2] = (TW)((Acc)w[2] - s2);
       }
       __syncthreads();
     }
@@ -627,17 +670,19 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
       const int rows = min(orc, n - l0);
       stage_rows(sw, Wi, ldx, l0, rows, p);
       __syncthreads();
-      for (int e = tid; e < rows * (pp / 2); e += ORTH_THREADS) {
-        const int r = e / (pp / 2), c = 2 * (e % (pp / 2));
-        Acc s0 = 0, s1 = 0;
-        for (int a = 0; a <= c + 1 && a < p; ++a) {
+      for (int e = tid; e < rows * ncg; e += ORTH_THREADS) {
+        const int r = e / ncg, c = 3 * (e % ncg);
+        Acc s0 = 0, s1 = 0, s2 = 0;
+        for (int a = 0; a <= c + 2 && a < p; ++a) {
           const Acc v = sw[r * SROW + a];
           mac(s0, v, Ra[a * pp + c]);
           mac(s1, v, Ra[a * pp + c + 1]);
+          mac(s2, v, Ra[a * pp + c + 2]);
         }
         TW* w = Wi + (int64_t)(l0 + r) * ldx + c;
         w[0] = (TW)finish(s0);
         if (c + 1 < p) w[1] = (TW)finish(s1);
+        if (c + 2 < p) w[2] = (TW)finish(s2);
       }
       __syncthreads();
     }
