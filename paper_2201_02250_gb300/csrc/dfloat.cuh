@@ -95,6 +95,8 @@ __device__ __forceinline__ dfloat se_sqrt(dfloat a) {
   return df_quick_two_sum(s, __fdiv_rn(r.hi, 2.f * s));
 }
 __device__ __forceinline__ double se_dbl(dfloat a) { return (double)a; }
+__device__ __forceinline__ void se_mac(dfloat& acc, dfloat a, dfloat b) { df_mac(acc, a, b); }
+__device__ __forceinline__ dfloat se_fin(dfloat a) { return df_normalize(a); }
 
 __device__ __forceinline__ dfloat shfl_xor(dfloat v, int lane_mask) {
   return dfloat(__shfl_xor_sync(0xffffffffu, v.hi, lane_mask), __shfl_xor_sync(0xffffffffu, v.lo, lane_mask));

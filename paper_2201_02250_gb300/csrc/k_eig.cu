@@ -805,27 +805,42 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
   const int nsel = nsel_s;
   double* Yi = Y + (int64_t)i * EIG_MAXP * EIG_MAXP;
   int conv_all = 1;
+  // Schur vectors: one selected eigenvalue per thread (a pair's +imag member is the first of its block)
+  if ((int)threadIdx.x < nsel) {
+    const int j = threadIdx.x;
+    const int pidx = sel_pos[j];
+    se::schur_vector(S, ld, m, pidx, wr[pidx], wi[pidx] > 0 ? wi[pidx] : 0.0, xs + j * m, ys + j * m, snorm);
+  }
+  __syncthreads();
+  // coefficients in the V basis, Q x and Q y: one (row, vector) pair per thread; each row's sum starts
+  // at its own column so that the threads of a warp read different shared-memory banks
+  for (int e = threadIdx.x; e < nsel * m; e += blockDim.x) {
+    const int j = e / m, a = e % m;
+    const R* x = xs + j * m;
+    const R* y = ys + j * m;
+    const R* Qa = Q + a * m;
+    R qx = 0.0, qy = 0.0;
+    for (int c = 0, cc = a; c < m; ++c, cc = (cc + 1 == m) ? 0 : cc + 1) {
+      mac(qx, Qa[cc], x[cc]);
+      mac(qy, Qa[cc], y[cc]);
+    }
+    Yi[a * EIG_MAXP + sel_col[j]] = (double)finish(qx);
+    if (sel_two[j] == 1) Yi[a * EIG_MAXP + sel_col[j] + 1] = (double)finish(qy);
+  }
+  __syncthreads();
   if ((int)threadIdx.x < nsel) {
     const int j = threadIdx.x;
     const int pidx = sel_pos[j];
     const int two = sel_two[j];
-    const int pstart = (wi[pidx] > 0.0) ? pidx : pidx;  // a pair's +imag member is the first of its block
-    R* x = xs + j * m;
-    R* y = ys + j * m;
-    se::schur_vector(S, ld, m, pstart, wr[pidx], wi[pidx] > 0 ? wi[pidx] : 0.0, x, y, snorm);
-    // coefficients in the V basis: Q x, Q y; norms
+    // norms
     double nx = 0.0, ny = 0.0;
     for (int a = 0; a < m; ++a) {
-      R qxr = 0.0, qyr = 0.0;
-      for (int c = 0; c < m; ++c) {
-        qxr += Q[a * m + c] * x[c];
-        qyr += Q[a * m + c] * y[c];
-      }
-      const double qx = (double)qxr, qy = (double)qyr;
-      Yi[a * EIG_MAXP + sel_col[j]] = qx;
-      if (two == 1) Yi[a * EIG_MAXP + sel_col[j] + 1] = qy;
+      const double qx = Yi[a * EIG_MAXP + sel_col[j]];
       nx += qx * qx;
-      ny += qy * qy;
+      if (two == 1) {
+        const double qy = Yi[a * EIG_MAXP + sel_col[j] + 1];
+        ny += qy * qy;
+      }
     }
     const double nrm = sqrt(nx + (two ? ny : 0.0));
     for (int a = 0; a < m; ++a) {
@@ -858,6 +873,13 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
       eo[2 * j + 1] = wi[pidx] > 0 ? wi[pidx] : 0.0;
     }
   }
+  // slots past this cycle's wanted set must not keep values written by an earlier cycle
+  for (int j = threadIdx.x; j < prm.nevmax; j += blockDim.x)
+    if (!(j < nsel && sel_col[j] < zc_s)) {
+      double* eo = eigout + (int64_t)i * prm.nevmax * 2;
+      eo[2 * j] = nan("");
+      eo[2 * j + 1] = nan("");
+    }
   conv_all = __syncthreads_and(conv_all);
   if (threadIdx.x == 0) {
     conv[i] = conv_all;

@@ -36,6 +36,10 @@ struct Team {
 SE_HD inline double se_abs(double x) { return fabs(x); }
 SE_HD inline double se_sqrt(double x) { return sqrt(x); }
 SE_HD inline double se_dbl(double x) { return x; }
+// acc += a * b in the dot products, and the value of an accumulator (an arithmetic with a cheaper
+// unnormalised multiply-add overloads both)
+SE_HD inline void se_mac(double& acc, double a, double b) { acc += a * b; }
+SE_HD inline double se_fin(double a) { return a; }
 template <class R> struct SeEps {
   static constexpr double v = 2.220446049250313e-16;  // machine epsilon of R
   static constexpr double big = 1e100;                // rescaling threshold of the back substitution
@@ -45,42 +49,61 @@ template <class R>
 SE_HD inline R sgn(R a, R b) { return b >= R(0.0) ? se_abs(a) : -se_abs(a); }
 
 // Reduce H (m x m) to upper Hessenberg form, accumulating the orthogonal factor in Q (Q <- Q P).
-// v: scratch of m doubles.
+// v: scratch of m values.  Each reflector takes two phases of the team: the left update (one column
+// per thread) together with the first rows of Q, then the right update of H (one row per thread)
+// together with the remaining rows of Q (with 128 threads and m <= 85 no thread holds more than one
+// item per phase).
 template <class R>
 SE_HD inline void hessenberg(R* H, int ld, R* Q, int ldq, int m, R* v, const Team& t) {
   for (int k = 0; k + 2 < m; ++k) {
     // Householder vector for x = H[k+1.., k]
     R nrm2 = 0.0;
-    for (int r = k + 1; r < m; ++r) nrm2 += H[r * ld + k] * H[r * ld + k];
+    for (int r = k + 1; r < m; ++r) se_mac(nrm2, H[r * ld + k], H[r * ld + k]);
+    nrm2 = se_fin(nrm2);
     R nrm = se_sqrt(nrm2);
     if (nrm == 0.0) continue;
     R x0 = H[(k + 1) * ld + k];
     R alpha = -sgn(nrm, x0);
-    // v = x - alpha e1, scaled so that P = I - 2 v v^T / (v^T v)
+    // v = x - alpha e1, scaled so that P = I - 2 v v^T / (v^T v); v^T v = 2 nrm |x0 - alpha|
     R vtv = nrm2 - x0 * x0 + (x0 - alpha) * (x0 - alpha);
     if (vtv == 0.0) continue;
     t.sync();
     for (int r = k + 1 + t.lane; r < m; r += t.size) v[r] = (r == k + 1) ? (x0 - alpha) : H[r * ld + k];
     t.sync();
     const R beta = 2.0 / vtv;
-    // left: rows k+1.., columns k..m-1
-    for (int c = k + t.lane; c < m; c += t.size) {
-      R d = 0.0;
-      for (int r = k + 1; r < m; ++r) d += v[r] * H[r * ld + c];
-      d *= beta;
-      for (int r = k + 1; r < m; ++r) H[r * ld + c] -= d * v[r];
+    const int ncol = m - k;                                  // left update: columns k..m-1
+    const int qa = (t.size > ncol) ? ((t.size - ncol < m) ? t.size - ncol : m) : 0;  // Q rows in phase 1
+    for (int idx = t.lane; idx < ncol + qa; idx += t.size) {
+      if (idx < ncol) {
+        const int c = k + idx;
+        R d = 0.0;
+        for (int r = k + 1; r < m; ++r) se_mac(d, v[r], H[r * ld + c]);
+        d = se_fin(d) * beta;
+        for (int r = k + 1; r < m; ++r) H[r * ld + c] -= d * v[r];
+      } else {
+        const int r = idx - ncol;
+        R e = 0.0;
+        for (int c = k + 1; c < m; ++c) se_mac(e, Q[r * ldq + c], v[c]);
+        e = se_fin(e) * beta;
+        for (int c = k + 1; c < m; ++c) Q[r * ldq + c] -= e * v[c];
+      }
     }
     t.sync();
-    // right: all rows, columns k+1..
-    for (int r = t.lane; r < m; r += t.size) {
-      R d = 0.0;
-      for (int c = k + 1; c < m; ++c) d += H[r * ld + c] * v[c];
-      d *= beta;
-      for (int c = k + 1; c < m; ++c) H[r * ld + c] -= d * v[c];
-      R e = 0.0;
-      for (int c = k + 1; c < m; ++c) e += Q[r * ldq + c] * v[c];
-      e *= beta;
-      for (int c = k + 1; c < m; ++c) Q[r * ldq + c] -= e * v[c];
+    // right: all rows of H, columns k+1..; the remaining rows of Q
+    for (int idx = t.lane; idx < m + (m - qa); idx += t.size) {
+      if (idx < m) {
+        const int r = idx;
+        R d = 0.0;
+        for (int c = k + 1; c < m; ++c) se_mac(d, H[r * ld + c], v[c]);
+        d = se_fin(d) * beta;
+        for (int c = k + 1; c < m; ++c) H[r * ld + c] -= d * v[c];
+      } else {
+        const int r = qa + idx - m;
+        R e = 0.0;
+        for (int c = k + 1; c < m; ++c) se_mac(e, Q[r * ldq + c], v[c]);
+        e = se_fin(e) * beta;
+        for (int c = k + 1; c < m; ++c) Q[r * ldq + c] -= e * v[c];
+      }
     }
     t.sync();
     if (t.lane == 0) {
@@ -122,17 +145,19 @@ SE_HD inline void apply_reflector(R* H, int ld, R* Q, int ldq, int m, int k, int
   t.sync();
 }
 
-// Householder reflector mapping (x, y, z) to (alpha, 0, 0): returns beta and u = (1, u1, u2).
+// Householder reflector mapping (x, y, z) to (alpha, 0, 0): returns alpha, beta and u = (1, u1, u2).
+// With v = (v0, y, z), v0 = x - alpha, v^T v = 2 |alpha| |v0|, so beta = 2 v0^2 / v^T v = v0 / (-alpha).
 template <class R>
-SE_HD inline bool make_reflector(R x, R y, R z, R& u1, R& u2, R& beta) {
+SE_HD inline bool make_reflector(R x, R y, R z, R& u1, R& u2, R& beta, R& alpha) {
   R nrm = se_sqrt(x * x + y * y + z * z);
   if (nrm == 0.0) return false;
-  R alpha = -sgn(nrm, x);
+  alpha = -sgn(nrm, x);
   R v0 = x - alpha;
   if (v0 == 0.0) return false;
-  u1 = y / v0;
-  u2 = z / v0;
-  beta = 2.0 / (1.0 + u1 * u1 + u2 * u2);
+  const R iv = R(1.0) / v0;
+  u1 = y * iv;
+  u2 = z * iv;
+  beta = v0 / (-alpha);
   return true;
 }
 
@@ -258,17 +283,32 @@ SE_HD inline int schur(R* H, int ld, R* Q, int ldq, int m, double hnorm_, const 
     // which keeps each step at two barriers.
     t.sync();  // the shift and deflation reads above precede the first update
     for (int k = lo; k <= hi - 2; ++k) {
-      R u1, u2, beta;
-      if (make_reflector(x, y, z, u1, u2, beta)) {
-        const R alpha = -sgn(se_sqrt(x * x + y * y + z * z), x);
+      R u1, u2, beta, alpha;
+      if (make_reflector(x, y, z, u1, u2, beta, alpha)) {
         const int c0 = k > lo ? k : lo;
         const int r1 = (k + 3 <= hi) ? k + 3 : hi;
-        for (int c = c0 + t.lane; c < m; c += t.size) {
-          R d = H[k * ld + c] + u1 * H[(k + 1) * ld + c] + u2 * H[(k + 2) * ld + c];
-          d *= beta;
-          H[k * ld + c] -= d;
-          H[(k + 1) * ld + c] -= d * u1;
-          H[(k + 2) * ld + c] -= d * u2;
+        // phase 1: rows k..k+2 from the left (columns c0..m-1) and the first qa rows of Q; phase 2:
+        // columns k..k+2 from the right (rows 0..r1) and the remaining rows of Q (Q's update depends
+        // on the reflector only, so it fills the threads that the H updates leave idle)
+        const int ncol = m - c0;
+        const int qa = (t.size > ncol) ? ((t.size - ncol < m) ? t.size - ncol : m) : 0;
+        for (int idx = t.lane; idx < ncol + qa; idx += t.size) {
+          R* a;
+          int st;
+          if (idx < ncol) {
+            a = H + k * ld + c0 + idx;
+            st = ld;
+          } else {
+            a = Q + (idx - ncol) * ldq + k;
+            st = 1;
+          }
+          R d = a[0];
+          se_mac(d, u1, a[st]);
+          se_mac(d, u2, a[2 * st]);
+          d = se_fin(d) * beta;
+          a[0] -= d;
+          a[st] -= d * u1;
+          a[2 * st] -= d * u2;
         }
         t.sync();
         if (k > lo && t.lane == 0) {
@@ -276,19 +316,15 @@ SE_HD inline int schur(R* H, int ld, R* Q, int ldq, int m, double hnorm_, const 
           H[(k + 1) * ld + k - 1] = 0.0;
           H[(k + 2) * ld + k - 1] = 0.0;
         }
-        for (int r = t.lane; r <= r1; r += t.size) {
-          R d = H[r * ld + k] + u1 * H[r * ld + k + 1] + u2 * H[r * ld + k + 2];
-          d *= beta;
-          H[r * ld + k] -= d;
-          H[r * ld + k + 1] -= d * u1;
-          H[r * ld + k + 2] -= d * u2;
-        }
-        for (int r = t.lane; r < m; r += t.size) {
-          R d = Q[r * ldq + k] + u1 * Q[r * ldq + k + 1] + u2 * Q[r * ldq + k + 2];
-          d *= beta;
-          Q[r * ldq + k] -= d;
-          Q[r * ldq + k + 1] -= d * u1;
-          Q[r * ldq + k + 2] -= d * u2;
+        for (int idx = t.lane; idx < (r1 + 1) + (m - qa); idx += t.size) {
+          R* a = (idx <= r1) ? H + idx * ld + k : Q + (qa + idx - (r1 + 1)) * ldq + k;
+          R d = a[0];
+          se_mac(d, u1, a[1]);
+          se_mac(d, u2, a[2]);
+          d = se_fin(d) * beta;
+          a[0] -= d;
+          a[1] -= d * u1;
+          a[2] -= d * u2;
         }
         t.sync();
       }
@@ -298,8 +334,8 @@ SE_HD inline int schur(R* H, int ld, R* Q, int ldq, int m, double hnorm_, const 
     }
     // final 2-element reflector on rows hi-1, hi
     {
-      R u1, u2, beta;
-      if (make_reflector<R>(x, y, R(0.0), u1, u2, beta)) {
+      R u1, u2, beta, alpha;
+      if (make_reflector<R>(x, y, R(0.0), u1, u2, beta, alpha)) {
         t.sync();
         apply_reflector<R>(H, ld, Q, ldq, m, hi - 1, 2, u1, R(0.0), beta, hi - 2, hi, t);
         if (t.lane == 0) H[hi * ld + hi - 2] = 0.0;
@@ -364,17 +400,26 @@ SE_HD inline void schur_vector(const R* S, int ld, int m, int p, double lr_, dou
     top = p - 1;
   }
   const int last = (li == 0.0) ? p : p + 1;
+  R mx = 0.0;
+  for (int c = top + 1; c <= last; ++c) {
+    const R v = se_abs(x[c]) + se_abs(y[c]);
+    if (v > mx) mx = v;
+  }
   int q = top;
   while (q >= 0) {
     if (q > 0 && S[q * ld + q - 1] != 0.0) {
       // 2x2 block rows q-1, q: solve (S_blk - lambda I) [u; w] = -rhs
       R r1r = 0, r1i = 0, r2r = 0, r2i = 0;
       for (int c = q + 1; c <= last; ++c) {
-        r1r += S[(q - 1) * ld + c] * x[c];
-        r1i += S[(q - 1) * ld + c] * y[c];
-        r2r += S[q * ld + c] * x[c];
-        r2i += S[q * ld + c] * y[c];
+        se_mac(r1r, S[(q - 1) * ld + c], x[c]);
+        se_mac(r1i, S[(q - 1) * ld + c], y[c]);
+        se_mac(r2r, S[q * ld + c], x[c]);
+        se_mac(r2i, S[q * ld + c], y[c]);
       }
+      r1r = se_fin(r1r);
+      r1i = se_fin(r1i);
+      r2r = se_fin(r2r);
+      r2i = se_fin(r2i);
       R a11r = S[(q - 1) * ld + q - 1] - lr, a11i = -li;
       R a12 = S[(q - 1) * ld + q], a21 = S[q * ld + q - 1];
       R a22r = S[q * ld + q] - lr, a22i = -li;
@@ -400,9 +445,11 @@ SE_HD inline void schur_vector(const R* S, int ld, int m, int p, double lr_, dou
     } else {
       R rr = 0, ri = 0;
       for (int c = q + 1; c <= last; ++c) {
-        rr += S[q * ld + c] * x[c];
-        ri += S[q * ld + c] * y[c];
+        se_mac(rr, S[q * ld + c], x[c]);
+        se_mac(ri, S[q * ld + c], y[c]);
       }
+      rr = se_fin(rr);
+      ri = se_fin(ri);
       R dr = S[q * ld + q] - lr, di = -li;
       R dn = dr * dr + di * di;
       if (dn < small * small) {
@@ -414,17 +461,18 @@ SE_HD inline void schur_vector(const R* S, int ld, int m, int p, double lr_, dou
       y[q] = -(ri * dr - rr * di) / dn;
       q -= 1;
     }
-    // rescale to avoid overflow
-    R mx = 0.0;
-    for (int c = (q + 1 > 0 ? q + 1 : 0); c <= last; ++c) {
+    // rescale to avoid overflow: mx is the largest |x_c| + |y_c| over the entries computed so far
+    for (int c = q + 1; c <= q + 2 && c <= last; ++c) {
       const R v = se_abs(x[c]) + se_abs(y[c]);
       if (v > mx) mx = v;
     }
     if (mx > R(SeEps<R>::big)) {
+      const R inv = R(1.0) / mx;
       for (int c = 0; c <= last; ++c) {
-        x[c] /= mx;
-        y[c] /= mx;
+        x[c] *= inv;
+        y[c] *= inv;
       }
+      mx = R(1.0);
     }
   }
 }
