@@ -1081,8 +1081,19 @@ template <class R>
 static void dense_inverse_t(a2ls_handle* h, R* E, int n, double scale, R* Einv, int band) {
   cudaStream_t st = h->st;
   const int64_t ld = n;
+  // algorithmic work of a banded LU without pivoting (bandwidth band) and of the inverse formed from
+  // its factors: forward substitution of the identity with L, backward substitution of the dense
+  // result with U
+  double lu_flops = 0.0, inv_flops = 0.0;
+  for (int k = 0; k < n; ++k) {
+    const double l = std::min(band, n - 1 - k);
+    lu_flops += l + 2.0 * l * l;
+    const double d = n - 1 - k, dw = std::min<double>(d, band);
+    inv_flops += dw * (dw + 1.0) + 2.0 * std::max(0.0, d - band) * band;  // column k of inv(L)
+    inv_flops += (double)n * (2.0 * l + 1.0);                              // row k of the U solve
+  }
   {
-    KTime kt(h, KT_COARSE_LU, 2.0 / 3.0 * (double)n * n * n);
+    KTime kt(h, KT_COARSE_LU, lu_flops);
     for (int k0 = 0; k0 < n; k0 += TB) {
       k_e_diag<R><<<1, 256, 0, st>>>(E, n, ld, k0, scale, h->d_status);
       A2LS_LAUNCH();
@@ -1098,7 +1109,7 @@ static void dense_inverse_t(a2ls_handle* h, R* E, int n, double scale, R* Einv, 
       A2LS_LAUNCH();
     }
   }
-  KTime kt2(h, KT_COARSE_INV, 4.0 / 3.0 * (double)n * n * n);
+  KTime kt2(h, KT_COARSE_INV, inv_flops);
   k_e_inverse<R><<<ceil_div(n, EINV_W), 256, 0, st>>>(E, n, ld, Einv, ld, band);
   A2LS_LAUNCH();
 }
