@@ -42,6 +42,11 @@ FP32_PEAK_TFLOPS_DERIVED = 152 * 128 * 2 * 2.07e9 / 1e12
 # 2 flops per 12 lane-instructions of the FP32 pipe
 FP32X2_PEAK_TFLOPS_DERIVED = 152 * 128 * 2.07e9 * 2 / 12 / 1e12
 # arithmetic of each tracked kernel in the mixed form (the plain form is FP64 throughout)
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per subdomain and launch of the
+# mixed-form kernels, from one ncu capture of each on the 256x256 case (64 subdomains of the C2 size;
+# the kernels work subdomain by subdomain, so the traffic of a launch grows with the subdomains it
+# covers).  A kernel changed after its capture has no entry (traffic null).
+NCU_TRAFFIC_PER_SUBDOMAIN = {"eig_orthogonalisation": 0.7525e6, "eig_triangular_solves": 2.7497e6}
 MIXED_KERNEL_DTYPE = {"lu_local": "f32", "lu_splitting": "f32x2", "eig_triangular_solves": "f32x2",
                       "eig_orthogonalisation": "f32x2", "eig_rayleigh_ritz": "f32x2", "coarse_lu": "f32x2",
                       "coarse_inverse": "f32x2"}
@@ -396,7 +401,8 @@ def main():
     return 0
 
 
-def roofline_entry(name: str, launches: int, ms: float, work: float, hbm_peak, fp32: bool = True) -> dict:
+def roofline_entry(name: str, launches: int, ms: float, work: float, hbm_peak, fp32: bool = True,
+                   subdomains: int = 0) -> dict:
     """achieved = algorithmic work per launch / average launch duration (CUDA events on the library stream)."""
     per_launch_ms = ms / max(launches, 1)
     if name == "apply_local_solves":
@@ -413,8 +419,10 @@ def roofline_entry(name: str, launches: int, ms: float, work: float, hbm_peak, f
         peak, src = FP32X2_PEAK_TFLOPS_DERIVED, "FP32 SIMT lane rate x 2.07 GHz / 12 instructions per double-float FMA"
     else:
         peak, src = FP64_PEAK_TFLOPS_NOMINAL, "nominal FP64 SIMT rate of the pool's recipe table"
+    per_sub = NCU_TRAFFIC_PER_SUBDOMAIN.get(name) if fp32 else None
+    traffic = per_sub * subdomains if (per_sub and subdomains) else None
     return {"kernel": name, "bound": "alu", "dtype": dt, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": (ach / peak) if ach else None, "traffic": None,
+            "frac": (ach / peak) if ach else None, "traffic": traffic,
             "launches": launches, "avg_launch_ms": per_launch_ms, "peak_source": src}
 
 
@@ -423,7 +431,8 @@ def report(args, res, world) -> dict:
     mixed, plain = res["mixed"], res["plain"]
     kern = res["kern"]
     dom = res["dominant"]
-    roof = roofline_entry(dom, kern[dom][0], kern[dom][1], kern[dom][2], res["hbm_peak"])
+    roof = roofline_entry(dom, kern[dom][0], kern[dom][1], kern[dom][2], res["hbm_peak"],
+                          subdomains=int(prob.nparts))
     apply_local_gbs = res["ab_mixed"]["local_kernel"] / (res["loc_ms"] * 1e-3) / 1e9
     out = {
         "metric": METRIC,
@@ -466,7 +475,8 @@ def report(args, res, world) -> dict:
                   "frac_of_measured_hbm": apply_local_gbs / res["hbm_peak"] if res["hbm_peak"] else None},
         "roofline": roof,
         "kernels_ms_per_step": {k: round(v[1], 3) for k, v in kern.items()},
-        "roofline_kernels": {k: roofline_entry(k, v[0], v[1], v[2], res["hbm_peak"]) for k, v in kern.items() if v[0]},
+        "roofline_kernels": {k: roofline_entry(k, v[0], v[1], v[2], res["hbm_peak"], subdomains=int(prob.nparts))
+                             for k, v in kern.items() if v[0]},
         "e2e": None if not res["e2e_ms"] else {
             "value": statistics.mean(res["e2e_ms"]) / 1e3, "unit": "s", "h2d_bytes_per_step": res["h2d"],
             "d2h_bytes_per_step": res["d2h"]},
