@@ -173,6 +173,16 @@ void a2ls_destroy(a2ls_handle* h);
 /* Message describing the last failure on this thread ("" if none). */
 const char* a2ls_last_error(void);
 
+/*
+ * a2ls_trim_memory -- memory management of the implementation (the paper has no counterpart).
+ * Handles take their device memory from one stream-ordered memory pool per device, owned by the
+ * library, that keeps the blocks a destroyed handle frees for the next setup: repeated setups of
+ * similar size then neither map nor unmap device memory.  This call returns the pools' unused
+ * blocks to the system (memory of live handles stays).  Call it after destroying handles when other
+ * code needs the memory.  Thread-safe; returns OK, or ERR_CUDA if the runtime reports an error.
+ */
+int a2ls_trim_memory(void);
+
 /* Items for a2ls_query.  All results are copied to host memory. */
 enum {
   A2LS_Q_SIZES = 0,      /* int64[8]: n, N, n0, sum n_i, max n_i, sum m_i rows stored, precision, variant */

@@ -85,8 +85,9 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.a2ls_apply_static.argtypes = [vp, vp, vp]
     L.a2ls_solve_multi.argtypes = [vp, i32, vp, vp, f64, vp, vp]
     L.a2ls_setup_batch.argtypes = [i32, vp, vp, vp, vp, ctypes.POINTER(Options), vp]
+    L.a2ls_trim_memory.argtypes = []
     for f in ("a2ls_setup", "a2ls_apply", "a2ls_solve", "a2ls_query", "a2ls_set_coarse_basis", "a2ls_spmv",
-              "a2ls_apply_static", "a2ls_solve_multi", "a2ls_setup_batch"):
+              "a2ls_apply_static", "a2ls_solve_multi", "a2ls_setup_batch", "a2ls_trim_memory"):
         getattr(L, f).restype = ctypes.c_int
     # learned warm start
     i64 = ctypes.c_int64
@@ -312,6 +313,11 @@ class Preconditioner:
         flat = np.ascontiguousarray(flat)
         _check(lib().a2ls_set_coarse_basis(self._h, m.ctypes.data_as(ctypes.c_void_p),
                                            flat.ctypes.data_as(ctypes.c_void_p)))
+
+
+def trim_memory() -> None:
+    """Return the unused blocks of the library's device memory pools to the system (a2ls_trim_memory)."""
+    _check(lib().a2ls_trim_memory())
 
 
 def from_scipy(A, part, overlap: int, nev: int, device: str = "cuda", **opts):

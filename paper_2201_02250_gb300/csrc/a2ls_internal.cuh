@@ -66,6 +66,7 @@ struct a2ls_handle {
   a2ls_options opt{};
   cudaStream_t st = nullptr;
   std::vector<void*> allocs;     // device allocations owned by the handle
+  cudaMemPool_t pool = nullptr;  // the library's memory pool of the handle's device (null: default pool)
   int* d_status = nullptr;       // ST_WORDS ints
 
   // FP64 copy of A and of the partition

@@ -106,3 +106,25 @@ def test_setup_batch_failure_releases_earlier_systems():
         a2ls().setup_batch([_tensors(good), _tensors(bad)])
     assert e.value.code == a2ls().A2LS_ERR_ARG
     assert "system 1" in str(e.value)
+
+
+def test_memory_pool_keeps_and_trims_blocks():
+    """Handles allocate from the library's pool, which keeps freed blocks until a2ls_trim_memory."""
+    mod = a2ls()
+    prob = pde.tiny_conv_diff(m=48, nb=3, overlap=2, nev=6)
+    P = mod.setup_batch([_tensors(prob)])[0]
+    P.close()
+    torch.cuda.synchronize()
+    free_kept, _ = torch.cuda.mem_get_info()
+    mod.trim_memory()
+    torch.cuda.synchronize()
+    free_trimmed, _ = torch.cuda.mem_get_info()
+    assert free_trimmed >= free_kept
+    # a setup after the trim maps fresh blocks and solves as before
+    P = mod.setup_batch([_tensors(prob)])[0]
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    it, rr, ok = P.solve(torch.as_tensor(prob.b, device="cuda"), x, 1e-8)
+    true = np.linalg.norm(prob.b - prob.A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
+    assert ok and true <= 1e-8
+    P.close()
+    mod.trim_memory()

@@ -43,6 +43,7 @@ def test_argument_errors_without_device(lib):
     assert lib.a2ls_apply(None, None, None) == a2ls.A2LS_ERR_ARG
     assert lib.a2ls_query(None, 0, None, 0, None) == a2ls.A2LS_ERR_ARG
     lib.a2ls_destroy(None)
+    assert lib.a2ls_trim_memory() == 0  # no pool exists before the first setup on a device
 
 
 @pytest.fixture(scope="module")
