@@ -994,15 +994,16 @@ __global__ void __launch_bounds__(256) k_e_update(R* A, int n, int64_t ld, int k
   }
 }
 
-// X = inv(U) inv(L) I, one 32-column slab per CTA (F holds the block-inverted LU), all in the
-// arithmetic and storage R of the factorisation
-constexpr int EINV_W = 32;
+// X = inv(U) inv(L) I, one 8-column slab per CTA (F holds the block-inverted LU), all in the
+// arithmetic and storage R of the factorisation.  Narrow slabs give n/8 CTAs: each CTA's sweep over
+// the row blocks is a chain of dependent tile products, so more and shorter chains fill the SMs.
+constexpr int EINV_W = 8;
 template <class R>
 __global__ void __launch_bounds__(256) k_e_inverse(const R* F, int n, int64_t ld, R* X, int64_t ldx, int band) {
-  __shared__ R sA[GK * 65], sB[GK * 33];
+  __shared__ R sA[GK * 65], sB[GK * 9];
   const int c0 = blockIdx.x * EINV_W;
   const int pc = min(EINV_W, n - c0);
-  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+  const int tid = threadIdx.x, tx = tid & 3, ty = tid >> 2;
   R* Xs = X + c0;
   for (int e = tid; e < n * pc; e += 256) {
     const int r = e / pc, c = e % pc;
@@ -1016,48 +1017,36 @@ __global__ void __launch_bounds__(256) k_e_inverse(const R* F, int n, int64_t ld
       const int b = pass == 0 ? bb : nb - 1 - bb;
       if (pass == 0 && b < bstart) continue;
       const int r0 = b * TB, tb = min(TB, n - r0);
-      R acc[2][4];
-#pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = R(0.0);
+      R acc[2] = {R(0.0), R(0.0)};
       if (pass == 0) {
         const int k0 = max(bstart * TB, r0 - band);  // L(r, c) = 0 for c < r - band
         if (r0 > k0)
-          cta_gemm_n32<R, R>(F + (int64_t)r0 * ld + k0, ld, Xs + (int64_t)k0 * ldx, ldx, tb, pc, r0 - k0, 0, acc,
-                             sA, sB);
+          cta_gemm_n8<R, R>(F + (int64_t)r0 * ld + k0, ld, Xs + (int64_t)k0 * ldx, ldx, tb, pc, r0 - k0, 0, acc, sA,
+                            sB);
       } else {
         const int e0 = r0 + tb;
         const int e1 = min(n, r0 + tb + band);       // U(r, c) = 0 for c > r + band
         if (e0 < e1)
-          cta_gemm_n32<R, R>(F + (int64_t)r0 * ld + e0, ld, Xs + (int64_t)e0 * ldx, ldx, tb, pc, e1 - e0, 0, acc,
-                             sA, sB);
+          cta_gemm_n8<R, R>(F + (int64_t)r0 * ld + e0, ld, Xs + (int64_t)e0 * ldx, ldx, tb, pc, e1 - e0, 0, acc, sA,
+                            sB);
       }
 #pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const int r = ty * 2 + u, c = tx * 4 + v;
-          if (r < tb && c < pc) {
-            R* x = Xs + (int64_t)(r0 + r) * ldx + c;
-            *x = *x - finish(acc[u][v]);
-          }
+      for (int v = 0; v < 2; ++v) {
+        const int c = tx * 2 + v;
+        if (ty < tb && c < pc) {
+          R* x = Xs + (int64_t)(r0 + ty) * ldx + c;
+          *x = *x - finish(acc[v]);
         }
+      }
       __syncthreads();
-      R acc2[2][4];
+      R acc2[2] = {R(0.0), R(0.0)};
+      cta_gemm_n8<R, R>(F + (int64_t)r0 * ld + r0, ld, Xs + (int64_t)r0 * ldx, ldx, tb, pc, tb, pass == 0 ? 1 : 2,
+                        acc2, sA, sB);
 #pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc2[u][v] = R(0.0);
-      cta_gemm_n32<R, R>(F + (int64_t)r0 * ld + r0, ld, Xs + (int64_t)r0 * ldx, ldx, tb, pc, tb,
-                         pass == 0 ? 1 : 2, acc2, sA, sB);
-#pragma unroll
-      for (int u = 0; u < 2; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const int r = ty * 2 + u, c = tx * 4 + v;
-          if (r < tb && c < pc) Xs[(int64_t)(r0 + r) * ldx + c] = finish(acc2[u][v]);
-        }
+      for (int v = 0; v < 2; ++v) {
+        const int c = tx * 2 + v;
+        if (ty < tb && c < pc) Xs[(int64_t)(r0 + ty) * ldx + c] = finish(acc2[v]);
+      }
       __syncthreads();
     }
   }
