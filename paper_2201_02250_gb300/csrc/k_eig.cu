@@ -38,6 +38,7 @@ template <> struct SeEps<dfloat> {
   static constexpr double v = 1.4210854715202004e-14;  // 2^-46
   static constexpr double big = 1e30;                  // within FP32's exponent range
 };
+template <> struct SeEarlyReflector<dfloat> { static constexpr bool value = false; };
 }  // namespace se
 
 template <class T> struct EAcc;
@@ -767,7 +768,8 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
     return;
   }
   se::hessenberg(S, ld, Q, m, m, vtmp, team);
-  const int rc = se::schur(S, ld, Q, m, m, snorm, team);
+  __shared__ R snap[14];
+  const int rc = se::schur(S, ld, Q, m, m, snorm, team, snap);
   if (rc != 0 && threadIdx.x == 0) raise_status(st, A2LS_ERR_EIGEN, i, 2);
   __syncthreads();
   if (threadIdx.x == 0) {

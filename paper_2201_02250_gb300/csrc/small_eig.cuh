@@ -45,6 +45,12 @@ template <class R> struct SeEps {
   static constexpr double big = 1e100;                // rescaling threshold of the back substitution
 };
 
+// Whether the Francis iteration forms the next bulge reflector during the right update (one thread,
+// from a snapshot) rather than with every thread after it.  Measured on GB300: faster in FP64
+// (Rayleigh-Ritz 178 -> 147 ms per 512x512 setup), slower in double-float (28.7 -> 30.3 ms), whose
+// longer reflector arithmetic on one thread outlasts the right update.
+template <class R> struct SeEarlyReflector { static constexpr bool value = true; };
+
 template <class R>
 SE_HD inline R sgn(R a, R b) { return b >= R(0.0) ? se_abs(a) : -se_abs(a); }
 
@@ -204,8 +210,11 @@ SE_HD inline void split_2x2(R* H, int ld, R* Q, int ldq, int m, int p, const Tea
 // neighbours or below eps times hnorm (the largest entry of the input), which keeps
 // clusters of eigenvalues near zero from stalling the iteration; the result is
 // backward stable relative to hnorm.  Returns 0 on success, -1 on no convergence.
+// snap: 14 values of scratch shared by the team (may be null for a one-thread team).
 template <class R>
-SE_HD inline int schur(R* H, int ld, R* Q, int ldq, int m, double hnorm_, const Team& t) {
+SE_HD inline int schur(R* H, int ld, R* Q, int ldq, int m, double hnorm_, const Team& t, R* snap = nullptr) {
+  R snap_local[14];
+  if (!snap) snap = snap_local;
   const R eps = R(SeEps<R>::v), hnorm = R(hnorm_);
   int hi = m - 1, iter = 0, total = 0;
   while (hi >= 0) {
@@ -280,11 +289,20 @@ SE_HD inline int schur(R* H, int ld, R* Q, int ldq, int m, double hnorm_, const 
     // Bulge chase.  For k > lo the reflector is built from column k-1 (rows k..k+2), which it maps to
     // (alpha, 0, 0) exactly; that column is therefore not part of the left update but written
     // directly, after the barrier that separates every thread's read of (x, y, z) from the writes,
-    // which keeps each step at two barriers.
+    // which keeps each step at two barriers.  The next step's reflector comes from column k after
+    // this step's right update; one thread recomputes its three entries from a snapshot of rows
+    // k+1..k+3 (columns k..k+2) taken in the left phase and forms the reflector while the others run
+    // the right update, instead of every thread forming it after that update (the entries are the
+    // values the right update writes).
     t.sync();  // the shift and deflation reads above precede the first update
+    const bool early = SeEarlyReflector<R>::value;
+    R u1, u2, beta, alpha;
+    bool have = make_reflector(x, y, z, u1, u2, beta, alpha);
     for (int k = lo; k <= hi - 2; ++k) {
-      R u1, u2, beta, alpha;
-      if (make_reflector(x, y, z, u1, u2, beta, alpha)) {
+      const bool more = k + 1 <= hi - 2;  // a next step exists (then k + 3 <= hi)
+      R nu1 = R(0.0), nu2 = R(0.0), nbeta = R(0.0), nalpha = R(0.0);
+      bool nhave = false;
+      if (have) {
         const int c0 = k > lo ? k : lo;
         const int r1 = (k + 3 <= hi) ? k + 3 : hi;
         // phase 1: rows k..k+2 from the left (columns c0..m-1) and the first qa rows of Q; phase 2:
@@ -309,12 +327,34 @@ SE_HD inline int schur(R* H, int ld, R* Q, int ldq, int m, double hnorm_, const 
           a[0] -= d;
           a[st] -= d * u1;
           a[2 * st] -= d * u2;
+          if (early && more && idx < 3) {  // column c0 + idx = k + idx
+            snap[idx] = a[st];
+            snap[3 + idx] = a[2 * st];
+            snap[6 + idx] = H[(k + 3) * ld + k + idx];
+          }
         }
         t.sync();
         if (k > lo && t.lane == 0) {
           H[k * ld + k - 1] = alpha;
           H[(k + 1) * ld + k - 1] = 0.0;
           H[(k + 2) * ld + k - 1] = 0.0;
+        }
+        if (early && more && t.lane == t.size - 1) {  // the last thread, usually idle in the right update
+          R v[3];
+          for (int rr = 0; rr < 3; ++rr) {
+            const R a0 = snap[3 * rr], a1 = snap[3 * rr + 1], a2 = snap[3 * rr + 2];
+            R d = a0;
+            se_mac(d, u1, a1);
+            se_mac(d, u2, a2);
+            d = se_fin(d) * beta;
+            v[rr] = a0 - d;
+          }
+          const bool ok = make_reflector(v[0], v[1], v[2], nu1, nu2, nbeta, nalpha);
+          snap[9] = nu1;
+          snap[10] = nu2;
+          snap[11] = nbeta;
+          snap[12] = nalpha;
+          snap[13] = ok ? R(1.0) : R(0.0);
         }
         for (int idx = t.lane; idx < (r1 + 1) + (m - qa); idx += t.size) {
           R* a = (idx <= r1) ? H + idx * ld + k : Q + (qa + idx - (r1 + 1)) * ldq + k;
@@ -327,11 +367,28 @@ SE_HD inline int schur(R* H, int ld, R* Q, int ldq, int m, double hnorm_, const 
           a[2] -= d * u2;
         }
         t.sync();
+        if (more && early) {
+          nu1 = snap[9];
+          nu2 = snap[10];
+          nbeta = snap[11];
+          nalpha = snap[12];
+          nhave = snap[13] != R(0.0);
+        } else if (more) {
+          nhave = make_reflector(H[(k + 1) * ld + k], H[(k + 2) * ld + k], H[(k + 3) * ld + k], nu1, nu2, nbeta,
+                                 nalpha);
+        }
+      } else if (more) {
+        nhave = make_reflector(H[(k + 1) * ld + k], H[(k + 2) * ld + k], H[(k + 3) * ld + k], nu1, nu2, nbeta,
+                               nalpha);
       }
-      x = H[(k + 1) * ld + k];
-      y = H[(k + 2) * ld + k];
-      z = (k + 3 <= hi) ? H[(k + 3) * ld + k] : 0.0;
+      u1 = nu1;
+      u2 = nu2;
+      beta = nbeta;
+      alpha = nalpha;
+      have = nhave;
     }
+    x = H[(hi - 1) * ld + hi - 2];
+    y = H[hi * ld + hi - 2];
     // final 2-element reflector on rows hi-1, hi
     {
       R u1, u2, beta, alpha;
