@@ -1120,11 +1120,11 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, actv, d_kd, kvB, W);
     A2LS_LAUNCH();
   };
-  auto orthonormalize_W_into_V0 = [&]() {
-    k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, d_active, d_kd, kvB, W);
+  auto orthonormalize_W_into_V0 = [&](const int* actv) {
+    k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, actv, d_kd, kvB, W);
     A2LS_LAUNCH();
     // no previous basis: jb = 0; R written into H's last rows (discarded)
-    k_orth<TV, T><<<N, ORTH_THREADS, orth_smem_for(gcap_k), st>>>(h->d_ni, d_vo, P, d_pv, d_active, 0, b, V, W,
+    k_orth<TV, T><<<N, ORTH_THREADS, orth_smem_for(gcap_k), st>>>(h->d_ni, d_vo, P, d_pv, actv, 0, b, V, W,
                                                                   Rscr, 0, 0, 0, nullptr, d_rank, gcap_k,
                                                                   orc_for(gcap_k));
     A2LS_LAUNCH();
@@ -1141,20 +1141,82 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     k_random_block<T><<<N, 256, 0, st>>>(h->d_ni, d_vo, P, 0, d_pv, d_active, h->opt.seed, 0, W);
     A2LS_LAUNCH();
   }
-  orthonormalize_W_into_V0();
+  orthonormalize_W_into_V0(d_active);
   A2LS_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * N * P * P, st));
 
+  // --- restarted block Krylov cycles, in two interleaved groups of subdomains --------------------
+  // The subdomains alternate between two groups, each with its own stream.  After a group's
+  // Rayleigh-Ritz step the host reads that group's convergence flags and queues its next cycle while
+  // the other group still runs: the latency-bound Rayleigh-Ritz and the tails of the block solves of
+  // one group overlap the other group's work.  Each group touches only its own subdomains' slices of
+  // V, W, H and Y.  With per-kernel timing on, one group on the handle's stream keeps the kernels'
+  // times free of overlap.
+  const int ngroups = h->opt.timing ? 1 : 2;
   RRParams prm{s * b, b, s, tol, nevmax, h->opt.tau};
   const int max_cycles = h->opt.eig_max_cycles > 0 ? h->opt.eig_max_cycles : 60;
-  std::vector<int> conv(N, 0), cycles(N, 0);
-  int cycle = 0;
-  std::vector<int> actk(N);
-  for (; cycle < max_cycles; ++cycle) {
-    for (int i = 0; i < N; ++i) actk[i] = act[i] && !full[i];
-    A2LS_CUDA(cudaMemcpyAsync(d_actk, actk.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  std::vector<int> cycles(N, 0);
+  struct Group {
+    std::vector<int> act, actk;
+    int* d_act = nullptr;
+    int* d_actk = nullptr;
+    int* h_conv = nullptr;  // pinned: N flags, then the status words
+    cudaStream_t s = nullptr;
+    cudaEvent_t done = nullptr;
+    int cycle = 0;
+    bool finished = false;
+  };
+  Group grp[2];
+  struct GroupStreams {  // the second stream and the pinned buffers, released on every exit path
+    a2ls_handle* h;
+    cudaStream_t orig, s1 = nullptr;
+    Group* g;
+    ~GroupStreams() {
+      if (s1) {
+        cudaStreamSynchronize(s1);
+        cudaStreamDestroy(s1);
+      }
+      for (int q = 0; q < 2; ++q) {
+        if (g[q].done) cudaEventDestroy(g[q].done);
+        if (g[q].h_conv) cudaFreeHost(g[q].h_conv);
+      }
+      h->st = orig;
+    }
+  } guard{h, st, nullptr, grp};
+  grp[0].s = st;
+  if (ngroups == 2) {
+    A2LS_CUDA(cudaStreamCreateWithFlags(&guard.s1, cudaStreamNonBlocking));
+    grp[1].s = guard.s1;
+    cudaEvent_t ready;
+    A2LS_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    A2LS_CUDA(cudaEventRecord(ready, st));
+    A2LS_CUDA(cudaStreamWaitEvent(guard.s1, ready, 0));
+    A2LS_CUDA(cudaEventDestroy(ready));
+  }
+  for (int g = 0; g < ngroups; ++g) {
+    Group& G = grp[g];
+    G.act.assign(N, 0);
+    G.actk.assign(N, 0);
+    for (int i = g; i < N; i += ngroups) G.act[i] = act[i];
+    G.d_act = dalloc<int>(h, N);
+    G.d_actk = dalloc<int>(h, N);
+    A2LS_CUDA(cudaMallocHost(&G.h_conv, sizeof(int) * (N + ST_WORDS)));
+    A2LS_CUDA(cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming));
+    A2LS_CUDA(cudaMemcpyAsync(G.d_act, G.act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+  }
+  A2LS_CUDA(cudaStreamSynchronize(st));
+  auto use_stream = [&](cudaStream_t s2) {
+    st = s2;
+    h->st = s2;
+  };
+  // one cycle of group g: s block steps, Rayleigh-Ritz, then the flags and status copied to the host
+  auto queue_cycle = [&](int g) {
+    Group& G = grp[g];
+    use_stream(G.s);
+    for (int i = 0; i < N; ++i) G.actk[i] = G.act[i] && !full[i];
+    A2LS_CUDA(cudaMemcpyAsync(G.d_actk, G.actk.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
     for (int j = 0; j < s; ++j) {
-      const int* actv = (j == 0) ? d_active : d_actk;
-      const std::vector<int>& acth = (j == 0) ? act : actk;
+      const int* actv = (j == 0) ? G.d_act : G.d_actk;
+      const std::vector<int>& acth = (j == 0) ? G.act : G.actk;
       fwd_flops = bwd_flops = 0.0;
       double orth_flops = 0.0;
       for (int i = 0; i < N; ++i) {
@@ -1181,32 +1243,64 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
       // Hessenberg reduction plus Francis iteration) and the coefficients of b Ritz vectors (2 b m^2)
       double rr_flops = 0.0;
       for (int i = 0; i < N; ++i) {
-        if (!act[i]) continue;
+        if (!G.act[i]) continue;
         const double m = full[i] ? (double)mfull[i] : (double)s * b;
         rr_flops += 25.0 * m * m * m + 2.0 * b * m * m;
       }
       KTime kt(h, KT_EIG_RR, rr_flops);
-      k_rayleigh_ritz<RT><<<N, RR_THREADS, rr_smem, st>>>(prm, d_full, d_mfull, d_nf, d_active, H, Y, d_ycols, d_zcols,
+      k_rayleigh_ritz<RT><<<N, RR_THREADS, rr_smem, st>>>(prm, d_full, d_mfull, d_nf, G.d_act, H, Y, d_ycols, d_zcols,
                                               eigout, d_conv, h->d_status);
       A2LS_LAUNCH();
     }
-    A2LS_CUDA(cudaMemcpyAsync(conv.data(), d_conv, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
-    sync_and_check(h, "local eigensolve");
-    int remaining = 0;
-    for (int i = 0; i < N; ++i) {
-      if (act[i]) {
-        cycles[i] = cycle + 1;
-        if (conv[i] || full[i]) act[i] = 0;
-        else ++remaining;
+    A2LS_CUDA(cudaMemcpyAsync(G.h_conv, d_conv, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+    A2LS_CUDA(cudaMemcpyAsync(G.h_conv + N, h->d_status, sizeof(int) * ST_WORDS, cudaMemcpyDeviceToHost, st));
+    A2LS_CUDA(cudaEventRecord(G.done, st));
+  };
+  for (int g = 0; g < ngroups; ++g) queue_cycle(g);
+  if (ngroups == 1) grp[1].finished = true;
+  while (!grp[0].finished || !grp[1].finished) {
+    for (int g = 0; g < ngroups; ++g) {
+      Group& G = grp[g];
+      if (G.finished) continue;
+      A2LS_CUDA(cudaEventSynchronize(G.done));
+      if (G.h_conv[N + ST_CODE] != 0) sync_and_check(h, "local eigensolve");  // raises the recorded error
+      int remaining = 0;
+      for (int i = g; i < N; i += ngroups) {
+        if (G.act[i]) {
+          cycles[i] = G.cycle + 1;
+          if (G.h_conv[i] || full[i]) G.act[i] = 0;
+          else ++remaining;
+        }
       }
+      // after the last cycle V and Y stay as they are: the unconverged subdomains keep their Ritz vectors
+      if (remaining == 0 || G.cycle + 1 == max_cycles) {
+        G.finished = true;
+        continue;
+      }
+      ++G.cycle;
+      use_stream(G.s);
+      A2LS_CUDA(cudaMemcpyAsync(G.d_act, G.act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+      // restart block: W = V[:, 0:sb] Y[:, 0:b]
+      k_vy<TV, T><<<N, EIG_THREADS, vy_smem, st>>>(h->d_ni, d_vo, P, d_msb, d_pv, G.d_act, V, Y, W);
+      A2LS_LAUNCH();
+      orthonormalize_W_into_V0(G.d_act);
+      queue_cycle(g);
     }
-    // after the last cycle V and Y stay as they are: the unconverged subdomains keep their Ritz vectors
-    if (remaining == 0 || cycle + 1 == max_cycles) break;
-    A2LS_CUDA(cudaMemcpyAsync(d_active, act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
-    // restart block: W = V[:, 0:sb] Y[:, 0:b]
-    k_vy<TV, T><<<N, EIG_THREADS, vy_smem, st>>>(h->d_ni, d_vo, P, d_msb, d_pv, d_active, V, Y, W);
-    A2LS_LAUNCH();
-    orthonormalize_W_into_V0();
+  }
+  // both groups done: continue on the handle's stream after the second stream's work
+  if (ngroups == 2) {
+    cudaEvent_t joined;
+    A2LS_CUDA(cudaEventCreateWithFlags(&joined, cudaEventDisableTiming));
+    A2LS_CUDA(cudaEventRecord(joined, guard.s1));
+    A2LS_CUDA(cudaStreamWaitEvent(guard.orig, joined, 0));
+    A2LS_CUDA(cudaEventDestroy(joined));
+  }
+  use_stream(guard.orig);
+  sync_and_check(h, "local eigensolve");
+  for (int i = 0; i < N; ++i) act[i] = grp[i % ngroups].act[i];
+  for (int g = 0; g < ngroups; ++g) {
+    dfree(h, grp[g].d_act);
+    dfree(h, grp[g].d_actk);
   }
   int unconverged = 0;
   for (int i = 0; i < N; ++i) unconverged += act[i];
