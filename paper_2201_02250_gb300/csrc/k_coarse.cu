@@ -148,19 +148,20 @@ __global__ void k_pair_bitmap(int N, const int* ni, const int* off, const int* i
   }
 }
 
-constexpr int TRIP_CAP = 2048;
+constexpr int EB_ROWS = 64;  // rows of Omega_i per batch in k_e_blocks
 
 // E(i, j) = sum over rows l of supp(W_i), entries A(g(l), k), memberships (j, l') of k:
 //           W_i[l, :]^T A(g, k) W_j[l', :]
+// formed as W_i^T Y with Y = A(Omega_i, Omega_j) W_j, a batch of EB_ROWS rows of Omega_i at a time:
+// one warp per row builds Y's row (lane c owns columns c and c + 32, every lane walks the row's
+// couplings), then the CTA adds W_i(batch)^T Y to its m_i x m_j outputs.
 __global__ void __launch_bounds__(256) k_e_blocks(const int2* pairs, const int* ni, const int* off,
                                                   const int* idx, const double* D, const int* rowptr,
                                                   const int* colind, const double* val, const int* mrow,
                                                   const int* mpos, const int* msub, const int* m,
                                                   const int* coff, const int64_t* woff, const double* W,
-                                                  double* E, int n0, int rows_per_batch) {
-  __shared__ int tl[TRIP_CAP], tp[TRIP_CAP];
-  __shared__ double ta[TRIP_CAP];
-  __shared__ int cnt;
+                                                  double* E, int n0) {
+  __shared__ double Ys[EB_ROWS][MAXM + 1];
   const int i = pairs[blockIdx.x].x, j = pairs[blockIdx.x].y;
   const int mi = m[i], mj = m[j], oi = off[i], oj = off[j];
   const double* Wi = W + woff[i];
@@ -171,36 +172,37 @@ __global__ void __launch_bounds__(256) k_e_blocks(const int2* pairs, const int* 
   for (int u = 0; u < PER; ++u) acc[u] = 0.0;
   const int nout = mi * mj;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int l0 = 0; l0 < ni[i]; l0 += rows_per_batch) {
-    if (threadIdx.x == 0) cnt = 0;
-    __syncthreads();
-    const int l1 = min(ni[i], l0 + rows_per_batch);
-    for (int l = l0 + wid; l < l1; l += 8) {
-      if (D[oi + l] == 0.0) continue;
-      const int g = idx[oi + l];
-      for (int q = rowptr[g] + lane; q < rowptr[g + 1]; q += 32) {
-        const int k = colind[q];
-        for (int t = mrow[k]; t < mrow[k + 1]; ++t) {
-          if (msub[t] != j || D[mpos[t]] == 0.0) continue;
-          const int at = atomicAdd(&cnt, 1);
-          if (at < TRIP_CAP) {
-            tl[at] = l;
-            tp[at] = mpos[t] - oj;
-            ta[at] = val[q];
+  const int n = ni[i];
+  for (int l0 = 0; l0 < n; l0 += EB_ROWS) {
+    const int rows = min(EB_ROWS, n - l0);
+    for (int r = wid; r < rows; r += 8) {
+      const int l = l0 + r;
+      double y0 = 0.0, y1 = 0.0;
+      if (D[oi + l] != 0.0) {
+        const int g = idx[oi + l];
+        for (int q = rowptr[g]; q < rowptr[g + 1]; ++q) {
+          const int k = colind[q];
+          const double a = val[q];
+          for (int t = mrow[k]; t < mrow[k + 1]; ++t) {
+            if (msub[t] != j || D[mpos[t]] == 0.0) continue;
+            const double* wr = Wj + (int64_t)(mpos[t] - oj) * mj;
+            if (lane < mj) y0 += a * wr[lane];
+            if (lane + 32 < mj) y1 += a * wr[lane + 32];
           }
         }
       }
+      if (lane < mj) Ys[r][lane] = y0;
+      if (lane + 32 < mj) Ys[r][lane + 32] = y1;
     }
     __syncthreads();
-    const int ntrip = min(cnt, TRIP_CAP);
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const int e = threadIdx.x + u * 256;
       if (e < nout) {
-        const int a = e / mj, b = e % mj;
-        double s = 0.0;
-        for (int t = 0; t < ntrip; ++t) s += Wi[(int64_t)tl[t] * mi + a] * ta[t] * Wj[(int64_t)tp[t] * mj + b];
-        acc[u] += s;
+        const int a = e / mj, c = e % mj;
+        double sum = 0.0;
+        for (int r = 0; r < rows; ++r) sum += Wi[(int64_t)(l0 + r) * mi + a] * Ys[r][c];
+        acc[u] += sum;
       }
     }
     __syncthreads();
@@ -311,11 +313,9 @@ void build_coarse_operator(a2ls_handle* h) {
   if (!pairs.empty()) {
     int2* d_pairs = dalloc<int2>(h, pairs.size());
     A2LS_CUDA(cudaMemcpyAsync(d_pairs, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice, st));
-    const int per_row = std::max(1, h->max_rownnz * h->max_memb);
-    const int rpb = std::max(1, TRIP_CAP / per_row);
     k_e_blocks<<<(int)pairs.size(), 256, 0, st>>>(d_pairs, h->d_ni, h->d_off, h->d_idx, h->d_D, h->rowptr,
                                                    h->colind, h->val, h->d_mrow, h->d_mpos, h->d_msub, h->d_m,
-                                                   h->d_coff, h->d_woff, h->d_W, E, n0, rpb);
+                                                   h->d_coff, h->d_woff, h->d_W, E, n0);
     A2LS_LAUNCH();
     A2LS_CUDA(cudaStreamSynchronize(st));
     dfree(h, d_pairs);

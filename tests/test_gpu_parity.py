@@ -149,6 +149,20 @@ def c1():
     return prob, ref
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_two_stream_eigensolve_is_bitwise_the_serial_one(c1, precision):
+    """The eigen cycles run in two interleaved groups of subdomains on two streams, or in one group
+    when per-kernel timing is on; every subdomain's arithmetic is the same either way."""
+    prob, _ = c1
+    P2 = setup_gpu(prob, precision=precision)             # two groups
+    P1 = setup_gpu(prob, precision=precision, timing=1)   # one group
+    for w2, w1 in zip(P2.coarse_basis(), P1.coarse_basis()):
+        np.testing.assert_array_equal(w2, w1)
+    np.testing.assert_array_equal(P2.eig_stats(), P1.eig_stats())
+    P2.close()
+    P1.close()
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
 def test_apply_c1_matches_oracle(c1, precision, tol):
     prob, ref = c1
