@@ -769,7 +769,9 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
   }
   se::hessenberg(S, ld, Q, m, m, vtmp, team);
   __shared__ R snap[14];
-  const int rc = se::schur(S, ld, Q, m, m, snorm, team, snap);
+  // the Ritz pairs are wanted to a relative residual of prm.tol: a subdiagonal entry below 1e-3 tol of
+  // its diagonal neighbours is already far below what the residual test resolves
+  const int rc = se::schur(S, ld, Q, m, m, snorm, team, snap, 1e-3 * prm.tol);
   if (rc != 0 && threadIdx.x == 0) raise_status(st, A2LS_ERR_EIGEN, i, 2);
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -211,18 +211,23 @@ SE_HD inline void split_2x2(R* H, int ld, R* Q, int ldq, int m, int p, const Tea
 // clusters of eigenvalues near zero from stalling the iteration; the result is
 // backward stable relative to hnorm.  Returns 0 on success, -1 on no convergence.
 // snap: 14 values of scratch shared by the team (may be null for a one-thread team).
+// local_tol (>= the machine epsilon of R; 0 selects it): the neighbour-relative test may use a looser
+// threshold when the caller needs the Schur form only to that relative accuracy; the test against
+// hnorm always uses the machine epsilon.
 template <class R>
-SE_HD inline int schur(R* H, int ld, R* Q, int ldq, int m, double hnorm_, const Team& t, R* snap = nullptr) {
+SE_HD inline int schur(R* H, int ld, R* Q, int ldq, int m, double hnorm_, const Team& t, R* snap = nullptr,
+                       double local_tol = 0.0) {
   R snap_local[14];
   if (!snap) snap = snap_local;
   const R eps = R(SeEps<R>::v), hnorm = R(hnorm_);
+  const R leps = R(local_tol > SeEps<R>::v ? local_tol : SeEps<R>::v);
   int hi = m - 1, iter = 0, total = 0;
   while (hi >= 0) {
     int lo = hi;
     while (lo > 0) {
       R s = se_abs(H[(lo - 1) * ld + lo - 1]) + se_abs(H[lo * ld + lo]);
       const R sub = se_abs(H[lo * ld + lo - 1]);
-      if (sub <= eps * s || sub <= eps * hnorm) break;
+      if (sub <= leps * s || sub <= eps * hnorm) break;
       --lo;
     }
     if (lo > 0) {
