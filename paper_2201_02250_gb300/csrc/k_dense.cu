@@ -145,7 +145,10 @@ __device__ __forceinline__ void cta_gemm_n8(const T* __restrict__ A, int64_t lda
       sB[k * 9 + c] = (c < Nc && kk < K) ? (Acc)B[kk * ldb + c] : (Acc)0;
     }
     __syncthreads();
-    if (tx * 2 < Nc) {
+    // a triangular A has no entries of row ty in this chunk when the chunk lies wholly right of the
+    // diagonal (unit lower) or wholly left of it (upper); whole warps skip together
+    const bool zero_chunk = (amask == 1 && k0 > ty) || (amask == 2 && k0 + GK - 1 < ty);
+    if (tx * 2 < Nc && !zero_chunk) {
 #pragma unroll 8
       for (int k = 0; k < GK; ++k) {
         const Acc a = sA[k * 65 + ty];
