@@ -515,18 +515,23 @@ __device__ void gram_product(const TX* X, const TY* Y, int64_t ldx, int n, int n
 // rel_floor is the squared unit roundoff of the arithmetic that formed G (at least 1e-28), below which
 // a pivot is rounding noise.  It is floored so that inv(R) amplifies that noise to O(1) at most and a
 // zero column stays zero.  Returns 1 when no pivot was floored (valid on every lane).
-__device__ int warp_cholesky_inverse(double* G, int p, double* Ri, double abs_floor, double rel_floor) {
+// min_ratio (optional): the smallest squared pivot over the largest diagonal entry, a lower bound of
+// 1 / cond(W)^2 for G = W^T W.
+__device__ int warp_cholesky_inverse(double* G, int p, double* Ri, double abs_floor, double rel_floor,
+                                     double* min_ratio = nullptr) {
   const int lane = threadIdx.x & 31;
   double gm = 0.0;
   for (int a = lane; a < p; a += 32) gm = fmax(gm, G[a * p + a]);
   for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
   const double floor_d = fmax(rel_floor * gm, abs_floor);
   int ok = 1;
+  double dmin = INFINITY;
   for (int a = 0; a < p; ++a) {
     double part = 0.0;
     for (int q = lane; q < a; q += 32) part += G[q * p + a] * G[q * p + a];
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     double d = G[a * p + a] - part;
+    dmin = fmin(dmin, d);
     if (!(d > floor_d)) {
       ok = 0;
       d = floor_d;
@@ -551,6 +556,7 @@ __device__ int warp_cholesky_inverse(double* G, int p, double* Ri, double abs_fl
     }
   }
   __syncwarp();
+  if (min_ratio) *min_ratio = gm > 0.0 ? dmin / gm : 0.0;
   return ok;
 }
 
@@ -620,13 +626,20 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
       __syncthreads();
     }
   }
-  // Shifted Cholesky QR 3 (a shifted first pass keeps the Cholesky factorisation defined for
-  // nearly rank-deficient blocks, two plain passes restore orthogonality):
-  // R_total = R3 R2 R1 goes to H[hr:hr+p, hc:hc+p]
-  for (int pass = 0; pass < 3; ++pass) {
+  // Cholesky QR: a plain first pass, kept when its Gram matrix is well conditioned (smallest squared
+  // pivot above plain_ratio of the largest diagonal entry, i.e. cond(W) below about 1e4 in double-float
+  // and FP64), followed by one more plain pass (Cholesky QR2); otherwise that factor is discarded and
+  // shifted Cholesky QR3 runs (a shifted first pass keeps the factorisation defined for nearly
+  // rank-deficient blocks, two plain passes restore orthogonality).
+  // R_total = R_last ... R_1 goes to H[hr:hr+p, hc:hc+p]
+  const double plain_ratio = fmax(1e-8, 1e3 * Unit<Acc>::u);
+  __shared__ int retry_shifted;
+  bool shifted = false;
+  int passes = 2;
+  for (int pass = 0; pass < passes; ++pass) {
     gram_product<Acc>(Wi, Wi, (int64_t)ldx, n, p, p, true, sw, sw, G, sv, orc);
     if (tid < 32) {
-      if (pass == 0) {
+      if (pass == 0 && shifted) {
         double tr = 0.0;
         for (int a = tid; a < p; a += 32) tr += G[a * p + a];
         for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
@@ -635,13 +648,22 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
         for (int a = tid; a < p; a += 32) G[a * p + a] += shift;
         __syncwarp();
       }
-      const int ok = warp_cholesky_inverse(G, p, Ri, Tiny<Acc>::v, fmax(1e-28, Unit<Acc>::u * Unit<Acc>::u));
+      double ratio = 0.0;
+      const int ok = warp_cholesky_inverse(G, p, Ri, Tiny<Acc>::v, fmax(1e-28, Unit<Acc>::u * Unit<Acc>::u),
+                                           &ratio);
       if (tid == 0) {
+        retry_shifted = (pass == 0 && !shifted && !(ok && ratio > plain_ratio)) ? 1 : 0;
         rank_ok = ok;
-        if (!ok && rank_flag) atomicAdd(rank_flag + i, 1);
+        if (!ok && !retry_shifted && rank_flag) atomicAdd(rank_flag + i, 1);
       }
     }
     __syncthreads();
+    if (retry_shifted) {  // uniform across the CTA
+      shifted = true;
+      passes = 3;
+      pass = -1;
+      continue;
+    }
     if (pass == 0) {
       for (int e = tid; e < p * p; e += ORTH_THREADS) {
         const int a = e / p, c = e % p;
