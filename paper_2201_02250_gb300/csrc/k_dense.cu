@@ -310,35 +310,38 @@ __global__ void __launch_bounds__(256, 2) k_lu(int N, const int* ni, const int* 
     // 1. the diagonal block: LU in shared memory
     for (int e = tid; e < w * w; e += 256) Dm[(e / w) * 65 + e % w] = (Acc)A[(int64_t)(k0 + e / w) * L + k0 + e % w];
     __syncthreads();
-    for (int c = 0; c < w; ++c) {
+    // Thread (ty, tx) = (tid / 64, tid % 64) owns column tx and the rows ty, ty + 4, ...; step c subtracts
+    // a21 (a12 / pivot)^T from the trailing block, and the multipliers of L are formed after the loop.
+    // The owner of entry (c+1, c+1) checks the next pivot right after its own update and forms its
+    // reciprocal in the working arithmetic, so each step needs one barrier.
+    auto pivot = [&](int c) {
       if (allow_last_zero && k0 + c == n - 1) {
         // record the last pivot of A~_ii and replace it by the scale; the eigensolver decides from it
         // whether A~_ii is singular
-        if (tid == 0) {
-          last_pivot[i] = (double)Dm[c * 65 + c];
-          Dm[c * 65 + c] = (Acc)scale;
-          rdiag[c] = Acc(1.0) / Dm[c * 65 + c];
+        last_pivot[i] = (double)Dm[c * 65 + c];
+        Dm[c * 65 + c] = (Acc)scale;
+      } else if (fabs((double)Dm[c * 65 + c]) <= tiny) {
+        raise_status(st, A2LS_ERR_SINGULAR, i, k0 + c);
+        Dm[c * 65 + c] = (Acc)scale;
+      }
+      rdiag[c] = Acc(1.0) / Dm[c * 65 + c];
+    };
+    if (tid == 0) pivot(0);
+    __syncthreads();
+    {
+      const int cx = tid & (TB - 1), ry = tid >> 6;
+      for (int c = 0; c + 1 < w; ++c) {
+        if (cx > c && cx < w) {
+          const Acc u = Dm[c * 65 + cx] * rdiag[c];
+          for (int r = c + 1 + ((ry - c - 1) & 3); r < w; r += 4) Dm[r * 65 + cx] -= Dm[r * 65 + c] * u;
+          if (cx == c + 1 && ry == ((c + 1) & 3)) pivot(c + 1);
         }
-        break;
+        __syncthreads();
       }
-      // one thread checks the pivot and forms its reciprocal in the working arithmetic
-      if (tid == 0) {
-        if (fabs((double)Dm[c * 65 + c]) <= tiny) {
-          raise_status(st, A2LS_ERR_SINGULAR, i, k0 + c);
-          Dm[c * 65 + c] = (Acc)scale;
-        }
-        rdiag[c] = Acc(1.0) / Dm[c * 65 + c];
-      }
-      __syncthreads();
-      const Acc pinv = rdiag[c];
-      for (int r = c + 1 + tid; r < w; r += 256) Dm[r * 65 + c] = Dm[r * 65 + c] * pinv;
-      __syncthreads();
-      const int m = w - 1 - c;
-      for (int e = tid; e < m * m; e += 256) {
-        const int r = c + 1 + e / m, cc = c + 1 + e % m;
-        Dm[r * 65 + cc] -= Dm[r * 65 + c] * Dm[c * 65 + cc];
-      }
-      __syncthreads();
+    }
+    for (int e = tid; e < w * w; e += 256) {
+      const int r = e / w, c = e % w;
+      if (r > c) Dm[r * 65 + c] *= rdiag[c];
     }
     __syncthreads();
     for (int e = tid; e < w * w; e += 256) A[(int64_t)(k0 + e / w) * L + k0 + e % w] = (T)Dm[(e / w) * 65 + e % w];
