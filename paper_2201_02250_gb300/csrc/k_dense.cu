@@ -21,101 +21,8 @@ template <> struct AccOf<float> { using type = float; };
 template <> struct AccOf<double> { using type = double; };
 template <> struct AccOf<dfloat> { using type = dfloat; };
 
-// ---------------------------------------------------------------------------
-// CTA-wide 64x64 tile product: acc += A(0:M, 0:K) * B(0:K, 0:Nc), 256 threads,
-// each thread owns rows ty*4..ty*4+3 and columns tx*4..tx*4+3.
-// amask: 0 = A as stored, 1 = unit lower (strict lower + 1 on diagonal), 2 = upper.
-// ---------------------------------------------------------------------------
+// depth of the operand chunks staged by the tile products
 constexpr int GK = 32;
-
-template <class T, class Acc>
-__device__ __forceinline__ void cta_gemm(const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
-                                         int64_t ldb, int M, int Nc, int K, int amask, Acc (&acc)[4][4],
-                                         Acc* sA, Acc* sB, int bmask = 0) {
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  for (int k0 = 0; k0 < K; k0 += GK) {
-    // load A(0:64, k0:k0+32) transposed into sA[k][m] and B(k0:k0+32, 0:64) into sB[k][n]
-    for (int e = tid; e < 64 * GK; e += 256) {
-      int m = e / GK, k = e % GK;
-      Acc v = 0;
-      int kk = k0 + k;
-      if (m < M && kk < K) {
-        if (amask == 0) v = (Acc)A[m * lda + kk];
-        else if (amask == 1) v = (kk < m) ? (Acc)A[m * lda + kk] : (kk == m ? (Acc)1 : (Acc)0);
-        else v = (kk >= m) ? (Acc)A[m * lda + kk] : (Acc)0;
-      }
-      sA[k * 65 + m] = v;
-    }
-    for (int e = tid; e < GK * 64; e += 256) {
-      int k = e / 64, c = e % 64;
-      int kk = k0 + k;
-      Acc v = 0;
-      if (c < Nc && kk < K && (bmask != 2 || c >= kk)) v = (Acc)B[kk * ldb + c];
-      sB[k * 65 + c] = v;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < GK; ++k) {
-      Acc a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        a[u] = sA[k * 65 + ty * 4 + u];
-        b[u] = sB[k * 65 + tx * 4 + u];
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) mac(acc[u][v], a[u], b[v]);
-    }
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Narrow tile product for p <= 32 right-hand sides: acc += A(0:M, 0:K) * B(0:K, 0:Nc),
-// M <= 64, Nc <= 32; 256 threads, thread (ty, tx) owns rows 2ty, 2ty+1 and columns 4tx..4tx+3.
-// amask as in cta_gemm.
-// ---------------------------------------------------------------------------
-template <class T, class Acc>
-__device__ __forceinline__ void cta_gemm_n32(const T* __restrict__ A, int64_t lda, const T* __restrict__ B,
-                                             int64_t ldb, int M, int Nc, int K, int amask, Acc (&acc)[2][4],
-                                             Acc* sA, Acc* sB) {
-  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
-  for (int k0 = 0; k0 < K; k0 += GK) {
-    for (int e = tid; e < 64 * GK; e += 256) {
-      const int m = e / GK, k = e % GK;
-      Acc v = 0;
-      const int kk = k0 + k;
-      if (m < M && kk < K) {
-        if (amask == 0) v = (Acc)A[m * lda + kk];
-        else if (amask == 1) v = (kk < m) ? (Acc)A[m * lda + kk] : (kk == m ? (Acc)1 : (Acc)0);
-        else v = (kk >= m) ? (Acc)A[m * lda + kk] : (Acc)0;
-      }
-      sA[k * 65 + m] = v;
-    }
-    for (int e = tid; e < GK * 32; e += 256) {
-      const int k = e / 32, c = e % 32;
-      const int kk = k0 + k;
-      sB[k * 33 + c] = (c < Nc && kk < K) ? (Acc)B[kk * ldb + c] : (Acc)0;
-    }
-    __syncthreads();
-    if (tx * 4 < Nc) {
-#pragma unroll 8
-      for (int k = 0; k < GK; ++k) {
-        const Acc a0 = sA[k * 65 + ty * 2], a1 = sA[k * 65 + ty * 2 + 1];
-        Acc b[4];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) b[v] = sB[k * 33 + tx * 4 + v];
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          mac(acc[0][v], a0, b[v]);
-          mac(acc[1][v], a1, b[v]);
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Narrowest tile product for the column chunks of the eigen solves: M <= 64 rows, Nc <= 8
