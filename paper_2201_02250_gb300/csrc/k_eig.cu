@@ -758,8 +758,9 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
   const int ld = m + 1;
   // sized for the launch's largest m and block size b (two CTAs per SM fit for m = 72, b = 24)
   R* S = reinterpret_cast<R*>(sm);   // m x ld
-  R* Q = S + m * ld;                 // m x m
-  R* xs = Q + m * m;                 // b lanes x m
+  R* Q = S + m * ld;                 // m x ld (an odd row stride keeps the row-wise column updates
+                                     // of Q off a single shared-memory bank pair)
+  R* xs = Q + m * ld;                // b lanes x m
   R* ys = xs + prm.b * m;            // b lanes x m
   R* vtmp = ys + prm.b * m;          // m (Hessenberg scratch, then the moduli)
   double* mod = reinterpret_cast<double*>(vtmp);
@@ -770,7 +771,7 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
   const se::Team team{(int)threadIdx.x, (int)blockDim.x};
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     S[(e / m) * ld + e % m] = (R)Hi[(e / m) * EIG_MAXP + e % m];
-    Q[(e / m) * m + e % m] = (R)((e / m == e % m) ? 1.0 : 0.0);
+    Q[(e / m) * ld + e % m] = (R)((e / m == e % m) ? 1.0 : 0.0);
   }
   __syncthreads();
   double snorm = 0.0;
@@ -789,11 +790,11 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
     }
     return;
   }
-  se::hessenberg(S, ld, Q, m, m, vtmp, team);
+  se::hessenberg(S, ld, Q, ld, m, vtmp, team);
   __shared__ R snap[14];
   // the Ritz pairs are wanted to a relative residual of prm.tol: a subdiagonal entry below 1e-3 tol of
   // its diagonal neighbours is already far below what the residual test resolves
-  const int rc = se::schur(S, ld, Q, m, m, snorm, team, snap, 1e-3 * prm.tol);
+  const int rc = se::schur(S, ld, Q, ld, m, snorm, team, snap, 1e-3 * prm.tol);
   if (rc != 0 && threadIdx.x == 0) raise_status(st, A2LS_ERR_EIGEN, i, 2);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -844,7 +845,7 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
     const int j = e / m, a = e % m;
     const R* x = xs + j * m;
     const R* y = ys + j * m;
-    const R* Qa = Q + a * m;
+    const R* Qa = Q + a * ld;
     R qx = 0.0, qy = 0.0;
     for (int c = 0, cc = a; c < m; ++c, cc = (cc + 1 == m) ? 0 : cc + 1) {
       mac(qx, Qa[cc], x[cc]);
@@ -1090,7 +1091,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   int m_max = s * b;
   for (int i = 0; i < N; ++i)
     if (full[i]) m_max = std::max(m_max, mfull[i]);
-  const size_t rr_smem = sizeof(double) * ((size_t)m_max * (m_max + 1) + (size_t)m_max * m_max + 2 * (size_t)b * m_max +
+  const size_t rr_smem = sizeof(double) * ((size_t)m_max * (m_max + 1) + (size_t)m_max * (m_max + 1) + 2 * (size_t)b * m_max +
                                            3 * (size_t)m_max) +
                          sizeof(int) * EIG_MAXP + 64;
   const size_t vy_smem = sizeof(Acc) * (EIG_MAXP * EIG_MAXP + RC * EIG_MAXP);
