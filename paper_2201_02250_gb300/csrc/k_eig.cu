@@ -774,13 +774,30 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
     Q[(e / m) * ld + e % m] = (R)((e / m == e % m) ? 1.0 : 0.0);
   }
   __syncthreads();
+  // largest |H| entry and finiteness, reduced over the CTA
+  __shared__ double red_norm[RR_THREADS / 32];
+  __shared__ int red_fin[RR_THREADS / 32];
   double snorm = 0.0;
-  bool finite = true;
-  for (int e = 0; e < m * m; ++e) {
+  int fin = 1;
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const double v = Hi[(e / m) * EIG_MAXP + e % m];
-    finite = finite && isfinite(v);
+    fin &= isfinite(v) ? 1 : 0;
     snorm = fmax(snorm, fabs(v));
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    snorm = fmax(snorm, __shfl_xor_sync(0xffffffffu, snorm, o));
+    fin &= __shfl_xor_sync(0xffffffffu, fin, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red_norm[threadIdx.x >> 5] = snorm;
+    red_fin[threadIdx.x >> 5] = fin;
+  }
+  __syncthreads();
+  for (int w = 0; w < (int)blockDim.x / 32; ++w) {
+    snorm = fmax(snorm, red_norm[w]);
+    fin &= red_fin[w];
+  }
+  const bool finite = fin != 0;
   if (!finite) {
     if (threadIdx.x == 0) {
       raise_status(st, A2LS_ERR_EIGEN, i, 4);
