@@ -52,7 +52,7 @@ template <> struct Tiny<dfloat> { static constexpr double v = 1e-30; };
 
 constexpr int EIG_THREADS = 256;
 constexpr int EIG_MAXP = 96;   // column capacity of the Krylov basis
-constexpr int RC = 16;         // rows staged per chunk in the Gram kernels
+constexpr int VY_RC = 32;      // rows staged per chunk in k_vy (32 rows x 8 column triples: a thread each)
 
 __device__ __forceinline__ double hash_uniform(uint64_t seed, uint64_t a, uint64_t b, uint64_t c) {
   // splitmix64 of a counter built from (seed, a, b, c); uniform in (-1, 1)
@@ -942,23 +942,35 @@ __global__ void __launch_bounds__(EIG_THREADS) k_vy(const int* ni, const int64_t
   const int i = blockIdx.x;
   if (active && !active[i]) return;
   const int n = ni[i], m = mvec[i], q = qvec[i];
-  Acc* sy = reinterpret_cast<Acc*>(sm);             // m x q
-  Acc* sv = sy + EIG_MAXP * EIG_MAXP;               // RC x m
+  Acc* sy = reinterpret_cast<Acc*>(sm);             // m x q (padded to 3 ncg columns with zeros)
+  Acc* sv = sy + EIG_MAXP * EIG_MAXP;               // VY_RC x m
   const double* Yi = Y + (int64_t)i * EIG_MAXP * EIG_MAXP;
-  for (int e = threadIdx.x; e < m * q; e += EIG_THREADS) sy[(e / q) * EIG_MAXP + e % q] = (Acc)Yi[(e / q) * EIG_MAXP + e % q];
+  const int ncg = (q + 2) / 3, qp = 3 * ncg;        // groups of 3 output columns, one per thread
+  for (int e = threadIdx.x; e < m * qp; e += EIG_THREADS) {
+    const int a = e / qp, c = e % qp;
+    sy[a * EIG_MAXP + c] = c < q ? (Acc)Yi[a * EIG_MAXP + c] : (Acc)0;
+  }
   const T* Vi = V + xoff[i];
   TX* Xi = X + xoff[i];
-  for (int l0 = 0; l0 < n; l0 += RC) {
-    const int rows = min(RC, n - l0);
+  for (int l0 = 0; l0 < n; l0 += VY_RC) {
+    const int rows = min(VY_RC, n - l0);
     __syncthreads();
     for (int e = threadIdx.x; e < rows * m; e += EIG_THREADS)
       sv[(e / m) * EIG_MAXP + e % m] = (Acc)Vi[(int64_t)(l0 + e / m) * ldx + e % m];
     __syncthreads();
-    for (int e = threadIdx.x; e < rows * q; e += EIG_THREADS) {
-      const int r = e / q, c = e % q;
-      Acc s = 0;
-      for (int a = 0; a < m; ++a) mac(s, sv[r * EIG_MAXP + a], sy[a * EIG_MAXP + c]);
-      Xi[(int64_t)(l0 + r) * ldx + c] = (TX)finish(s);
+    for (int e = threadIdx.x; e < rows * ncg; e += EIG_THREADS) {
+      const int r = e / ncg, c = 3 * (e % ncg);
+      Acc s0 = 0, s1 = 0, s2 = 0;
+      for (int a = 0; a < m; ++a) {
+        const Acc v = sv[r * EIG_MAXP + a];
+        mac(s0, v, sy[a * EIG_MAXP + c]);
+        mac(s1, v, sy[a * EIG_MAXP + c + 1]);
+        mac(s2, v, sy[a * EIG_MAXP + c + 2]);
+      }
+      TX* x = Xi + (int64_t)(l0 + r) * ldx + c;
+      x[0] = (TX)finish(s0);
+      if (c + 1 < q) x[1] = (TX)finish(s1);
+      if (c + 2 < q) x[2] = (TX)finish(s2);
     }
   }
 }
@@ -1111,7 +1123,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   const size_t rr_smem = sizeof(double) * ((size_t)m_max * (m_max + 1) + (size_t)m_max * (m_max + 1) + 2 * (size_t)b * m_max +
                                            3 * (size_t)m_max) +
                          sizeof(int) * EIG_MAXP + 64;
-  const size_t vy_smem = sizeof(Acc) * (EIG_MAXP * EIG_MAXP + RC * EIG_MAXP);
+  const size_t vy_smem = sizeof(Acc) * (EIG_MAXP * EIG_MAXP + VY_RC * EIG_MAXP);
   A2LS_CUDA(cudaFuncSetAttribute(k_orth<TV, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orth_smem));
   A2LS_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_smem));
   A2LS_CUDA(cudaFuncSetAttribute(k_vy<TV, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vy_smem));
