@@ -24,6 +24,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -157,7 +158,9 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.idx = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # samples go to A2LS_CLOCKS_DIR when set (to keep them with other run output), else a temp dir
+        out_dir = os.environ.get("A2LS_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"a2ls_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
