@@ -187,7 +187,8 @@ int a2ls_trim_memory(void);
 enum {
   A2LS_Q_SIZES = 0,      /* int64[8]: n, N, n0, sum n_i, max n_i, sum m_i rows stored, precision, variant */
   A2LS_Q_SUBDOMAINS = 1, /* int32[(N+1) + N + sum n_i]: offsets, n_I per subdomain, local->global
-                            indices (each subdomain: Omega_Ii ascending, then Omega_Gamma_i ascending) */
+                            indices (each subdomain: Omega_Ii ascending, then Omega_Gamma_i layer by
+                            layer: the nodes of the first overlap step ascending, then the second's, ...) */
   A2LS_Q_LUMP = 2,       /* double[sum n_i]: s_i of Definition 3.1 on overlap rows, 0 on interior rows */
   A2LS_Q_FACTORS = 3,    /* (precision type)[sum over i of n_i*ld_i] then int64[N+1] offsets and
                             int32[N] ld: LU of A_ii without pivoting, row-major, unit-lower L below

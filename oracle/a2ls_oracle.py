@@ -67,7 +67,9 @@ def overlapping_subdomains(A: sp.spmatrix, part: np.ndarray, delta: int) -> list
     Omega_Gamma_i holds the nodes at distance one in G(A) from Omega_Ii.
     READING: an overlap of delta layers repeats that step delta times,
     Omega^(k) = Omega^(k-1) U adj(Omega^(k-1)), and Omega_Gamma_i is every node
-    added in the process.  Both parts are listed in ascending global order.
+    added in the process.  The interior is listed in ascending global order, the
+    overlap layer by layer (the nodes added by step 1 ascending, then those of
+    step 2, ...); the method is invariant under any ordering of Omega_Gamma_i.
     """
     nbrs = adjacency_lists(A)
     N = int(part.max()) + 1
@@ -76,6 +78,7 @@ def overlapping_subdomains(A: sp.spmatrix, part: np.ndarray, delta: int) -> list
         interior = np.flatnonzero(part == i)
         member = set(interior.tolist())
         frontier = set(member)
+        layers = []
         for _ in range(delta):
             new = set()
             for j in frontier:
@@ -84,7 +87,8 @@ def overlapping_subdomains(A: sp.spmatrix, part: np.ndarray, delta: int) -> list
                         new.add(int(k))
             member |= new
             frontier = new
-        gamma = np.array(sorted(member - set(interior.tolist())), dtype=np.int64)
+            layers.extend(sorted(new))
+        gamma = np.array(layers, dtype=np.int64)
         subs.append(Subdomain(interior.astype(np.int64), gamma))
     return subs
 

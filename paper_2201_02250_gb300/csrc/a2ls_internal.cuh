@@ -74,13 +74,15 @@ struct a2ls_handle {
   double* val = nullptr;
   int* part = nullptr;
 
-  // subdomains: local order = [Omega_I ascending, Omega_Gamma ascending]
+  // subdomains: local order = [Omega_I ascending, Omega_Gamma layer by layer, ascending in a layer]
   std::vector<int> h_off, h_nI, h_n, h_ld;   // h_off has N+1 entries
   std::vector<int64_t> h_foff;               // offsets of dense local matrices (elements), N+1
   int *d_off = nullptr, *d_nI = nullptr, *d_ni = nullptr, *d_ld = nullptr;
   int64_t* d_foff = nullptr;
   int* d_idx = nullptr;                      // sum n_i: local -> global
   int* d_ipos = nullptr;                     // n: local index of a node inside its own part
+  int* d_gstart = nullptr;                   // N x (delta + 2): local start of the interior, each
+                                             // overlap layer, and n_i
   int* d_sched = nullptr;                    // N: subdomains by decreasing size (work order)
   int* d_counter = nullptr;                  // work-queue counter of the persistent kernels
   int ls_width = 0;                          // CTA width of the local solves (autotuned)

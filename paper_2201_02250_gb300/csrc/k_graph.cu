@@ -191,77 +191,55 @@ __global__ void k_bitmap_count(int W, const unsigned* interior, const unsigned* 
   }
 }
 
-// Emit the ordered index list of every subdomain: interior ascending, then overlap ascending.
-// One CTA per subdomain, one word per thread per chunk, block-wide exclusive scans.
-__global__ void k_bitmap_emit(int W, const unsigned* interior, const unsigned* member, const int* off,
-                              const int* nI, int* idx, int* ipos) {
-  int i = blockIdx.x;
-  const unsigned* ib = interior + (size_t)i * W;
-  const unsigned* mb = member + (size_t)i * W;
-  __shared__ int warp_a[32], warp_g[32];
-  __shared__ int base_a, base_g;
-  if (threadIdx.x == 0) {
-    base_a = 0;
-    base_g = 0;
-  }
+// Emit the ordered index list of every subdomain: interior ascending, then the overlap layer by
+// layer (the nodes the first growth step adds, ascending, then those of the second step, ...).
+// Listing the layer next to the interior first keeps the overlap nodes without interior couplings
+// out of the interior columns' envelope of the local factors.  One CTA per subdomain, one word per
+// thread per chunk, block-wide exclusive scans.
+__global__ void k_bitmap_emit(int N, int W, const unsigned* interior, const unsigned* layers, int delta,
+                              const int* off, int* idx, int* ipos, int* gstart) {
+  const int i = blockIdx.x;
+  __shared__ int warp_c[32];
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int w0 = 0; w0 < W; w0 += blockDim.x) {
-    int w = w0 + threadIdx.x;
-    unsigned bi = 0, bg = 0;
-    if (w < W) {
-      bi = ib[w];
-      bg = mb[w] & ~bi;
-    }
-    int ca = __popc(bi), cg = __popc(bg);
-    int xa = ca, xg = cg;  // inclusive warp scans
-    for (int o = 1; o < 32; o <<= 1) {
-      int ya = __shfl_up_sync(0xffffffffu, xa, o);
-      int yg = __shfl_up_sync(0xffffffffu, xg, o);
-      if (lane >= o) {
-        xa += ya;
-        xg += yg;
+  const int o_i = off[i];
+  for (int g = 0; g <= delta; ++g) {
+    if (threadIdx.x == 0) gstart[(size_t)i * (delta + 2) + g] = base;
+    const unsigned* gb = (g == 0) ? interior + (size_t)i * W : layers + ((size_t)(g - 1) * N + i) * W;
+    for (int w0 = 0; w0 < W; w0 += blockDim.x) {
+      const int w = w0 + threadIdx.x;
+      unsigned bits = (w < W) ? gb[w] : 0u;
+      const int c = __popc(bits);
+      int x = c;  // inclusive warp scan
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
       }
-    }
-    if (lane == 31) {
-      warp_a[wid] = xa;
-      warp_g[wid] = xg;
-    }
-    __syncthreads();
-    int pa = base_a, pg = base_g;
-    for (int k = 0; k < wid; ++k) {
-      pa += warp_a[k];
-      pg += warp_g[k];
-    }
-    pa += xa - ca;
-    pg += xg - cg;
-    int o_i = off[i], n_I = nI[i];
-    while (bi) {
-      int b = __ffs(bi) - 1;
-      bi &= bi - 1;
-      int j = w * 32 + b;
-      idx[o_i + pa] = j;
-      ipos[j] = pa;
-      ++pa;
-    }
-    while (bg) {
-      int b = __ffs(bg) - 1;
-      bg &= bg - 1;
-      idx[o_i + n_I + pg] = w * 32 + b;
-      ++pg;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int ta = 0, tg = 0;
-      for (int k = 0; k < nw; ++k) {
-        ta += warp_a[k];
-        tg += warp_g[k];
+      if (lane == 31) warp_c[wid] = x;
+      __syncthreads();
+      int p = base;
+      for (int k = 0; k < wid; ++k) p += warp_c[k];
+      p += x - c;
+      while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const int j = w * 32 + b;
+        idx[o_i + p] = j;
+        if (g == 0) ipos[j] = p;
+        ++p;
       }
-      base_a += ta;
-      base_g += tg;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int t = 0;
+        for (int k = 0; k < nw; ++k) t += warp_c[k];
+        base += t;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
+  if (threadIdx.x == 0) gstart[(size_t)i * (delta + 2) + delta + 1] = base;
 }
 
 // ---------------------------------------------------------------------------
@@ -381,12 +359,15 @@ void build_subdomains(a2ls_handle* h) {
   A2LS_LAUNCH();
   A2LS_CUDA(cudaMemcpyAsync(member, interior, bw * 4, cudaMemcpyDeviceToDevice, st));
   A2LS_CUDA(cudaMemcpyAsync(frontier, interior, bw * 4, cudaMemcpyDeviceToDevice, st));
+  // the nodes each step adds (the overlap layers), kept to order Omega_Gamma by layer
+  unsigned* layers = dalloc<unsigned>(h, bw * std::max(h->delta, 1));
   for (int layer = 0; layer < h->delta; ++layer) {
     k_bitmap_expand<<<grid_for((int64_t)bw, 256), 256, 0, st>>>(N, W, frontier, member, next,
                                                                  h->rowptr, h->colind, trow, tcol);
     A2LS_LAUNCH();
     k_bitmap_merge<<<grid_for((int64_t)bw, 256), 256, 0, st>>>(bw, frontier, member, next);
     A2LS_LAUNCH();
+    A2LS_CUDA(cudaMemcpyAsync(layers + (size_t)layer * bw, frontier, bw * 4, cudaMemcpyDeviceToDevice, st));
   }
   int* cI = dalloc<int>(h, N);
   int* cG = dalloc<int>(h, N);
@@ -439,8 +420,10 @@ void build_subdomains(a2ls_handle* h) {
     A2LS_CUDA(cudaMemcpyAsync(h->d_sched, order.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
     A2LS_CUDA(cudaStreamSynchronize(st));
   }
-  k_bitmap_emit<<<N, 256, 0, st>>>(W, interior, member, h->d_off, h->d_nI, h->d_idx, h->d_ipos);
+  h->d_gstart = dalloc<int>(h, (size_t)N * (h->delta + 2));
+  k_bitmap_emit<<<N, 256, 0, st>>>(N, W, interior, layers, h->delta, h->d_off, h->d_idx, h->d_ipos, h->d_gstart);
   A2LS_LAUNCH();
+  dfree(h, layers);
   dfree(h, interior);
   dfree(h, member);
   dfree(h, frontier);
@@ -507,7 +490,8 @@ __device__ __forceinline__ void atomic_max_pos(double* addr, double v) {
 
 template <class T, class TT>
 __global__ void k_extract(int S, int N, const int* off, const int* nI, const int* ni, const int* ld,
-                          const int64_t* foff, const int* idx, const int* ipos, const int* part,
+                          const int64_t* foff, const int* idx, const int* ipos, const int* gstart, int delta,
+                          const int* part,
                           const int* rowptr, const int* colind, const double* val, const int64_t* lrow,
                           int* lcol, double* lval, double* lump, T* dA, TT* dAt, double* dscale) {
   const int lane = threadIdx.x & 31;
@@ -532,13 +516,18 @@ __global__ void k_extract(int S, int N, const int* off, const int* nI, const int
       if (part[k] == i) {
         lk = ipos[k];
       } else {
-        int a0 = o + n_I, b0 = o + n_i;  // overlap list, ascending
-        while (a0 < b0) {
-          int mid = (a0 + b0) >> 1;
-          int v = idx[mid];
-          if (v < k) a0 = mid + 1; else b0 = mid;
+        // the overlap list is ascending within each layer: search the layers in turn
+        const int* gs = gstart + (size_t)i * (delta + 2);
+        for (int g = 1; g <= delta && lk < 0; ++g) {
+          int a0 = o + gs[g], b0 = o + gs[g + 1];
+          const int e0 = b0;
+          while (a0 < b0) {
+            int mid = (a0 + b0) >> 1;
+            int v = idx[mid];
+            if (v < k) a0 = mid + 1; else b0 = mid;
+          }
+          if (a0 < e0 && idx[a0] == k) lk = a0 - o;
         }
-        if (a0 < o + n_i && idx[a0] == k) lk = a0 - o;
       }
       lcol[lb + (q - r0)] = lk;
       lval[lb + (q - r0)] = a;
@@ -565,7 +554,8 @@ __global__ void k_extract(int S, int N, const int* off, const int* nI, const int
 template <class TA, class TT>
 static void launch_extract(a2ls_handle* h, void* dense_A, void* dense_At, double* dense_scale, int blocks) {
   k_extract<TA, TT><<<blocks, 256, 0, h->st>>>(
-      h->sum_n, h->N, h->d_off, h->d_nI, h->d_ni, h->d_ld, h->d_foff, h->d_idx, h->d_ipos, h->part, h->rowptr,
+      h->sum_n, h->N, h->d_off, h->d_nI, h->d_ni, h->d_ld, h->d_foff, h->d_idx, h->d_ipos, h->d_gstart, h->delta,
+      h->part, h->rowptr,
       h->colind, h->val, h->d_lrow, h->d_lcol, h->d_lval, h->d_lump, static_cast<TA*>(dense_A),
       static_cast<TT*>(dense_At), dense_scale);
   A2LS_LAUNCH();

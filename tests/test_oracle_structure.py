@@ -54,7 +54,9 @@ def test_overlap_matches_networkx_bfs(case, delta):
         G2.add_node("src")
         G2.add_edges_from(("src", int(v)) for v in interior)
         dist = nx.single_source_shortest_path_length(G2, "src", cutoff=delta + 1)
-        expect = sorted(v for v, d in dist.items() if v != "src" and 2 <= d <= delta + 1)
+        # Omega_Gamma layer by layer (distance from the interior), ascending within a layer
+        expect = sorted((v for v, d in dist.items() if v != "src" and 2 <= d <= delta + 1),
+                        key=lambda v: (dist[v], v))
         assert s.interior.tolist() == interior.tolist()
         assert s.gamma.tolist() == expect
 
