@@ -69,7 +69,8 @@ def overlapping_subdomains(A: sp.spmatrix, part: np.ndarray, delta: int) -> list
     Omega^(k) = Omega^(k-1) U adj(Omega^(k-1)), and Omega_Gamma_i is every node
     added in the process.  The interior is listed in ascending global order, the
     overlap layer by layer (the nodes added by step 1 ascending, then those of
-    step 2, ...); the method is invariant under any ordering of Omega_Gamma_i.
+    step 2, ...).  Section 2 defines Omega_Gamma_i as a set and Eqs. 2.3-2.4 use
+    it only through R_i, so the method is invariant under any ordering of it.
     """
     nbrs = adjacency_lists(A)
     N = int(part.max()) + 1
