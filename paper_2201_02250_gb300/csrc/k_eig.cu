@@ -1092,7 +1092,6 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   double* H = dalloc<double>(h, (size_t)N * P * P);
   double* Y = dalloc<double>(h, (size_t)N * P * P);
   double* Rscr = dalloc<double>(h, (size_t)N * P * P);
-  int* d_actk = dalloc<int>(h, N);  // active and not solved in the full space (block steps j >= 1)
   const int nevmax = std::max(nev, 1) + 1;
   double* eigout = dalloc<double>(h, (size_t)N * nevmax * 2);
   A2LS_CUDA(cudaMemsetAsync(V, 0, sizeof(TV) * hvo[N], st));
