@@ -1,0 +1,43 @@
+"""CPU checks of bench.py: the reference arm (the oracle timed on the host cores) prints the JSON
+line of the bench contract, and the roofline entries scale the measured per-subdomain DRAM traffic
+by the launch's subdomains and divide the algorithmic work by the measured launch time."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def test_reference_arm_json_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "higher_is_better", "config", "e2e",
+                "cpu_baseline"):
+        assert key in line, key
+    assert line["higher_is_better"] is False and line["unit"] == "s" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_roofline_entry_arithmetic():
+    import bench
+    # 3 launches, 6 ms and 6e12 flops in all: 2e12 flops per launch / 2 ms = 1000 TFLOP/s
+    e = bench.roofline_entry("eig_orthogonalisation", 3, 6.0, 6e12, 6780.0, subdomains=256)
+    assert e["bound"] == "alu" and e["dtype"] == "f32x2"
+    assert e["achieved"] == pytest.approx(1000.0)
+    assert e["frac"] == pytest.approx(1000.0 / bench.FP32X2_PEAK_TFLOPS_DERIVED)
+    assert e["traffic"] == pytest.approx(bench.NCU_TRAFFIC_PER_SUBDOMAIN["eig_orthogonalisation"] * 256)
+    # a kernel without a capture reports no traffic; the plain form's kernels use the FP64 peak
+    e = bench.roofline_entry("coarse_lu", 1, 1.0, 1e9, 6780.0, fp32=False, subdomains=256)
+    assert e["traffic"] is None and e["peak"] == bench.FP64_PEAK_TFLOPS_NOMINAL
+    # the apply's local solves are HBM bound: 1e9 bytes per launch / 0.5 ms against the measured copy rate
+    e = bench.roofline_entry("apply_local_solves", 2, 1.0, 2e9, 6780.0)
+    assert e["bound"] == "hbm" and e["achieved"] == pytest.approx(2000.0)
+    assert e["frac"] == pytest.approx(2000.0 / 6780.0)
