@@ -343,43 +343,8 @@ __global__ void k_mu_fix(const int* ni, const int* off, const int64_t* xoff, int
 }
 
 // ---------------------------------------------------------------------------
-// Orthogonalisation: block CGS2 of W against V[:, 0:jb], then Cholesky QR twice.
-// Writes the Gram coefficients into H[0:jb, hc:hc+p] and R into H[hr:hr+p, hc:hc+p]
-// and the orthonormal block into V[:, vout:vout+p].  full != 0: only H[0:jb, hc:hc+p].
+// Orthogonalisation (k_orth and its helpers): block CGS2 of W against the basis, then Cholesky QR.
 // ---------------------------------------------------------------------------
-__device__ void small_cholesky_inverse(double* G, int p, double* Ri, int& rank_ok, double abs_floor) {
-  // G (p x p, stride p) = R^T R; R overwrites the upper triangle of G; Ri = inv(R) (stride p); one thread.
-  // A pivot at or below 1e-28 of the largest diagonal (or abs_floor) marks a rank-deficient block; it is
-  // floored so that inv(R) stays finite in the working precision and a zero column stays zero.
-  rank_ok = 1;
-  double gmax = 0.0;
-  for (int a = 0; a < p; ++a) gmax = fmax(gmax, G[a * p + a]);
-  const double floor_d = fmax(1e-28 * gmax, abs_floor);
-  for (int a = 0; a < p; ++a) {
-    double d = G[a * p + a];
-    for (int q = 0; q < a; ++q) d -= G[q * p + a] * G[q * p + a];
-    if (!(d > floor_d)) {
-      rank_ok = 0;
-      d = floor_d;
-    }
-    const double r = sqrt(d);
-    G[a * p + a] = r;
-    for (int c = a + 1; c < p; ++c) {
-      double v = G[a * p + c];
-      for (int q = 0; q < a; ++q) v -= G[q * p + a] * G[q * p + c];
-      G[a * p + c] = v / r;
-    }
-  }
-  for (int c = 0; c < p; ++c) {
-    for (int a = c + 1; a < p; ++a) Ri[a * p + c] = 0.0;
-    Ri[c * p + c] = 1.0 / G[c * p + c];
-    for (int a = c - 1; a >= 0; --a) {
-      double v = 0.0;
-      for (int q = a + 1; q <= c; ++q) v += G[a * p + q] * Ri[q * p + c];
-      Ri[a * p + c] = -v / G[a * p + a];
-    }
-  }
-}
 
 constexpr int ORTH_THREADS = 512;
 constexpr int ORC_MAX = 64;              // rows staged per chunk in k_orth (64, or 32 with full-space Gram)

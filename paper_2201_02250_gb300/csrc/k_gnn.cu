@@ -45,14 +45,6 @@ __host__ __device__ constexpr int off_ws(int t) { return OFF_L1 + (t - 1) * L_ST
 __host__ __device__ constexpr int off_wn(int t) { return off_ws(t) + WIDTH * WIDTH; }
 __host__ __device__ constexpr int off_b(int t) { return off_wn(t) + WIDTH * WIDTH; }
 
-// parameters stored in bfloat16 for the forward pass: every weight matrix, not the biases
-__host__ __device__ inline bool is_weight(int p) {
-  if (p < OFF_BIN) return true;
-  if (p < OFF_L1) return false;
-  if (p >= OFF_WOUT) return true;
-  return ((p - OFF_L1) % L_STRIDE) < 2 * WIDTH * WIDTH;
-}
-
 __device__ __forceinline__ float bf(const __nv_bfloat16* w, int p) { return __bfloat162float(w[p]); }
 
 }  // namespace gnn

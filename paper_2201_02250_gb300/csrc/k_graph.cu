@@ -89,11 +89,6 @@ __global__ void k_part_range(int n, const int* part, int* minmax) {
   }
 }
 
-__global__ void k_count_int(int n, const int* keys, int* counts) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-    atomicAdd(counts + keys[j], 1);
-}
-
 // ---------------------------------------------------------------------------
 // transposed pattern (for the graph of A + A^T)
 // ---------------------------------------------------------------------------
@@ -503,7 +498,7 @@ __global__ void k_extract(int S, int N, const int* off, const int* nI, const int
       int mid = (lo + hi) >> 1;
       if (off[mid] <= p) lo = mid; else hi = mid;
     }
-    const int i = lo, o = off[i], l = p - o, n_I = nI[i], n_i = ni[i];
+    const int i = lo, o = off[i], l = p - o, n_I = nI[i];
     const int j = idx[p];
     const int64_t base = foff[i] + (int64_t)l * ld[i];
     const int r0 = rowptr[j], r1 = rowptr[j + 1];
