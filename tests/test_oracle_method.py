@@ -181,6 +181,29 @@ def test_condition_bound_hpd_dd():
         assert kappa <= bound, (kappa, bound)
 
 
+def test_condition_bound_counts_by_hand():
+    """Section 3.2's bound (k_c + 1)(2 + (2 k_c + 1) k_m / tau) with k_c and k_m counted by hand.
+
+    4-node example (parts {0,1}, {2,3}, overlap 1): Omega_1 = {0,1,2} and Omega_2 = {1,2,3}
+    intersect, so two colours; nodes 1 and 2 lie in both, so k_m = 2 and the bound is
+    3 (2 + 10 / tau).  4 x 4 blocks of a 12 x 12 five-point grid, overlap 1: Omega_i reaches the
+    first row or column of each edge neighbour's block, so diagonal neighbours share the corner
+    node of the block between them (the overlap graph is the king's graph, four colours, and the
+    greedy colouring in block order uses four); a corner node lies in its own subdomain and in the
+    two whose blocks touch it, so k_m = 3 and the bound is 5 (2 + 27 / tau).
+    """
+    g, A, part = _golden_problem()
+    subs = O.overlapping_subdomains(A, part, 1)
+    assert O.coloring_number(subs) == 2 and O.multiplicity_number(subs, 4) == 2
+    for tau in (0.1, 0.3, 0.5):
+        assert O.condition_bound(subs, 4, tau) == pytest.approx(3.0 * (2.0 + 10.0 / tau), rel=1e-15)
+    P0 = pde.tiny_conv_diff(m=12, nb=4, overlap=1)
+    subs = O.overlapping_subdomains(P0.A, P0.part, 1)
+    assert O.coloring_number(subs) == 4 and O.multiplicity_number(subs, 144) == 3
+    for tau in (0.1, 0.3, 0.5):
+        assert O.condition_bound(subs, 144, tau) == pytest.approx(5.0 * (2.0 + 27.0 / tau), rel=1e-15)
+
+
 def test_coarse_space_improves_on_one_level():
     P0 = pde.tiny_hpd_dd(m=16, nb=4, overlap=1, contrast=1e4)
     P = O.setup(P0.A, P0.part, 1, nev=4)
@@ -209,6 +232,9 @@ def test_gmres_matches_brute_force_minimal_residual(flexible):
     res = O.gmres(P0.A, M, P0.b, rtol=1e-14, restart=30, max_it=8, flexible=flexible)
     for k in range(1, 7):
         assert abs(res.history[k - 1] - _krylov_min_residual(P0.A, M, P0.b, k)) <= 1e-9
+    # the iterate returned after 8 steps attains the minimal residual over the Krylov space
+    assert not res.converged and res.iters == 8
+    assert abs(res.relres - _krylov_min_residual(P0.A, M, P0.b, 8)) <= 1e-9
 
 
 def test_gmres_distinct_eigenvalues_and_restart():

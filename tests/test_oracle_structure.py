@@ -32,7 +32,7 @@ def test_golden_overlap_and_splitting():
 
 
 @pytest.mark.parametrize("delta", [0, 1, 2, 3])
-@pytest.mark.parametrize("case", ["tiny_conv", "bfs3d", "random"])
+@pytest.mark.parametrize("case", ["tiny_conv", "bfs3d", "random", "one_sided"])
 def test_overlap_matches_networkx_bfs(case, delta):
     if case == "tiny_conv":
         P = pde.tiny_conv_diff(m=10, nb=3)
@@ -40,10 +40,14 @@ def test_overlap_matches_networkx_bfs(case, delta):
     elif case == "bfs3d":
         A = pde.conv_diff_3d(7, 100.0)
         part = pde.bfs_region_partition(A, 6, 30, 90, seed=5)
-    else:
+    elif case == "random":
         A = pde.random_dd_matrix(80, 0.04, seed=3)
         part = (np.arange(80) * 5 // 80).astype(np.int32)
-    G = nx.Graph()
+    else:
+        # every coupling one-sided (upper triangle only): the graph is that of A + A^T, not of A
+        A = sp.triu(pde.random_dd_matrix(80, 0.04, seed=3)).tocsr()
+        part = (np.arange(80) * 5 // 80).astype(np.int32)
+    G = nx.Graph()  # undirected: an entry a_ij gives the edge {i, j}, the pattern of A + A^T
     G.add_nodes_from(range(A.shape[0]))
     Acoo = A.tocoo()
     G.add_edges_from((int(i), int(j)) for i, j in zip(Acoo.row, Acoo.col) if i != j)
