@@ -475,16 +475,40 @@ __device__ void gram_product(const TX* X, const TY* Y, int64_t ldx, int n, int n
   }
 }
 
-// One warp: G (p x p, stride p) = R^T R by Cholesky, R into G's upper triangle, Ri = inv(R) (stride p).
-// A pivot at or below rel_floor of the largest diagonal (or abs_floor) marks a rank-deficient block:
-// rel_floor is the squared unit roundoff of the arithmetic that formed G (at least 1e-28), below which
-// a pivot is rounding noise.  It is floored so that inv(R) amplifies that noise to O(1) at most and a
-// zero column stays zero.  Returns 1 when no pivot was floored (valid on every lane).
-// min_ratio (optional): the smallest squared pivot over the largest diagonal entry, a lower bound of
-// 1 / cond(W)^2 for G = W^T W.
-__device__ int warp_cholesky_inverse(double* G, int p, double* Ri, double abs_floor, double rel_floor,
-                                     double* min_ratio = nullptr) {
+// One warp: G (p x p, stride p, upper triangle read) = R^T R by Cholesky, R into G's upper triangle,
+// Ri = inv(R) (stride p).  The factorisation runs on the diagonally scaled Gram matrix
+// Gs = D^-1 G D^-1, D = sqrt(diag G) (1 for a column at or below abs_floor), so that the pivot tests
+// see the conditioning of W's normalised columns and not the spread of their norms (the residual
+// columns of nearly converged Ritz vectors are orders of magnitude shorter than the others);
+// R = Rs D and inv(R) = D^-1 inv(Rs).  shift_u > 0: Gs + shift_u tr(Gs) I (shifted Cholesky QR).
+// A pivot at or below rel_floor of the largest diagonal entry of Gs (or abs_floor) marks a
+// rank-deficient block: rel_floor is the squared unit roundoff of the arithmetic that formed G (at
+// least 1e-28), below which a pivot is rounding noise.  The pivot is floored and the rest of its row
+// of Rs set to zero, so that inv(R) amplifies that noise to O(1) at most, a zero column stays zero,
+// and no later pivot inherits the floored one's growth; W = W inv(R) R still holds, and the next
+// Cholesky QR pass restores the orthogonality.  Returns 1 when no pivot was floored (valid on every
+// lane).  dsc: p doubles of scratch.  min_ratio (optional): the smallest squared pivot over the
+// largest diagonal entry of Gs, a lower bound of 1 / cond(W D^-1)^2.
+__device__ int warp_cholesky_inverse(double* G, int p, double* Ri, double* dsc, double abs_floor,
+                                     double rel_floor, double shift_u = 0.0, double* min_ratio = nullptr) {
   const int lane = threadIdx.x & 31;
+  for (int a = lane; a < p; a += 32) {
+    const double g = G[a * p + a];
+    dsc[a] = g > abs_floor ? sqrt(g) : 1.0;
+  }
+  __syncwarp();
+  for (int e = lane; e < p * p; e += 32) {
+    const int a = e / p, c = e % p;
+    if (c >= a) G[e] = G[e] / dsc[a] / dsc[c];
+  }
+  __syncwarp();
+  double tr = 0.0;
+  for (int a = lane; a < p; a += 32) tr += G[a * p + a];
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+  if (shift_u > 0.0) {
+    for (int a = lane; a < p; a += 32) G[a * p + a] += shift_u * tr;
+    __syncwarp();
+  }
   double gm = 0.0;
   for (int a = lane; a < p; a += 32) gm = fmax(gm, G[a * p + a]);
   for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
@@ -497,15 +521,20 @@ __device__ int warp_cholesky_inverse(double* G, int p, double* Ri, double abs_fl
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
     double d = G[a * p + a] - part;
     dmin = fmin(dmin, d);
-    if (!(d > floor_d)) {
+    const bool floored = !(d > floor_d);
+    if (floored) {
       ok = 0;
       d = floor_d;
     }
     const double r = sqrt(d);
     for (int c = a + 1 + lane; c < p; c += 32) {
-      double v = G[a * p + c];
-      for (int q = 0; q < a; ++q) v -= G[q * p + a] * G[q * p + c];
-      G[a * p + c] = v / r;
+      double v = 0.0;
+      if (!floored) {
+        v = G[a * p + c];
+        for (int q = 0; q < a; ++q) v -= G[q * p + a] * G[q * p + c];
+        v /= r;
+      }
+      G[a * p + c] = v;
     }
     __syncwarp();
     if (lane == 0) G[a * p + a] = r;
@@ -518,6 +547,15 @@ __device__ int warp_cholesky_inverse(double* G, int p, double* Ri, double abs_fl
       double v = 0.0;
       for (int q = a + 1; q <= c; ++q) v += G[a * p + q] * Ri[q * p + c];
       Ri[a * p + c] = -v / G[a * p + a];
+    }
+  }
+  __syncwarp();
+  // back to the unscaled factors: R = Rs D, inv(R) = D^-1 inv(Rs)
+  for (int e = lane; e < p * p; e += 32) {
+    const int a = e / p, c = e % p;
+    if (c >= a) {
+      G[e] *= dsc[c];
+      Ri[e] /= dsc[a];
     }
   }
   __syncwarp();
@@ -548,7 +586,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
   double* Hi = H + (int64_t)i * EIG_MAXP * EIG_MAXP;
   double* G = sm;                               // gcap: Gram, then R in place
   double* Ri = G + gcap;                        // gcap
-  double* trow = Ri + gcap;                     // EIG_MAXP
+  double* trow = Ri + gcap;                     // EIG_MAXP: column scales of the Cholesky
   Acc* sv = reinterpret_cast<Acc*>(trow + EIG_MAXP);           // orc * SROW
   Acc* sw = sv + orc * SROW;                                   // orc * SROW
   __shared__ int rank_ok;
@@ -604,18 +642,12 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
   for (int pass = 0; pass < passes; ++pass) {
     gram_product<Acc>(Wi, Wi, (int64_t)ldx, n, p, p, true, sw, sw, G, sv, orc);
     if (tid < 32) {
-      if (pass == 0 && shifted) {
-        double tr = 0.0;
-        for (int a = tid; a < p; a += 32) tr += G[a * p + a];
-        for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
-        const double u = Unit<Acc>::u;
-        const double shift = 11.0 * ((double)n * p + (double)p * (p + 1)) * u * tr;
-        for (int a = tid; a < p; a += 32) G[a * p + a] += shift;
-        __syncwarp();
-      }
+      // shifted pass: Gs + 11 (n p + p (p + 1)) u tr(Gs) I
+      const double shift_u =
+          (pass == 0 && shifted) ? 11.0 * ((double)n * p + (double)p * (p + 1)) * Unit<Acc>::u : 0.0;
       double ratio = 0.0;
-      const int ok = warp_cholesky_inverse(G, p, Ri, Tiny<Acc>::v, fmax(1e-28, Unit<Acc>::u * Unit<Acc>::u),
-                                           &ratio);
+      const int ok = warp_cholesky_inverse(G, p, Ri, trow, Tiny<Acc>::v, fmax(1e-28, Unit<Acc>::u * Unit<Acc>::u),
+                                           shift_u, &ratio);
       if (tid == 0) {
         retry_shifted = (pass == 0 && !shifted && !(ok && ratio > plain_ratio)) ? 1 : 0;
         rank_ok = ok;

@@ -66,6 +66,23 @@ def test_setup_batch_and_solve_multi(precision):
         P.close()
 
 
+# Full-size mixed-batch systems whose local eigensolves used to break down: the Krylov blocks of
+# nearly converged Ritz vectors have columns over several orders of magnitude in norm, which the
+# orthogonalisation's Cholesky QR must factor through the diagonally scaled Gram matrix
+# (system 0: 201^2 grid, Peclet 409, 25 subdomains; system 32: 177^2 grid, 16 subdomains).
+@pytest.mark.parametrize("k,precision,seed", [(0, "fp64", 0), (32, "fp32", 1)])
+def test_full_size_batch_systems_set_up_and_solve(k, precision, seed):
+    prob = pde.config_c5()[k]
+    (P,) = a2ls().setup_batch([_tensors(prob)], precision=precision, seed=seed)
+    b = prob.meta["B"][0]
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    it, rr, ok = P.solve(torch.as_tensor(b, device="cuda"), x, 1e-8)
+    true = np.linalg.norm(b - prob.A @ x.cpu().numpy()) / np.linalg.norm(b)
+    assert ok and true <= 1e-8, (it, rr, true)
+    assert 0 <= P.eig_unconverged() <= P.sizes()["N"]
+    P.close()
+
+
 def test_strict_eigensolve_fails_and_lenient_keeps_ritz_vectors():
     prob = pde.tiny_conv_diff(m=40, nb=3, overlap=2, nev=6)
     mod = a2ls()
