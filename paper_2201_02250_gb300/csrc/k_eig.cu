@@ -629,11 +629,12 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
       __syncthreads();
     }
   }
-  // Cholesky QR: a plain first pass, kept when its Gram matrix is well conditioned (smallest squared
-  // pivot above plain_ratio of the largest diagonal entry, i.e. cond(W) below about 1e4 in double-float
-  // and FP64), followed by one more plain pass (Cholesky QR2); otherwise that factor is discarded and
-  // shifted Cholesky QR3 runs (a shifted first pass keeps the factorisation defined for nearly
-  // rank-deficient blocks, two plain passes restore orthogonality).
+  // Cholesky QR: a plain first pass, kept when its diagonally scaled Gram matrix is well conditioned
+  // (smallest squared pivot above plain_ratio of the largest diagonal entry, i.e. cond of W's
+  // normalised columns below about 1e4 in double-float and FP64), followed by one more plain pass
+  // (Cholesky QR2); otherwise that factor is discarded and shifted Cholesky QR3 runs (a shifted first
+  // pass keeps the factorisation defined for nearly rank-deficient blocks, two plain passes restore
+  // orthogonality).
   // R_total = R_last ... R_1 goes to H[hr:hr+p, hc:hc+p]
   const double plain_ratio = fmax(1e-8, 1e3 * Unit<Acc>::u);
   __shared__ int retry_shifted;
