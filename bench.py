@@ -47,7 +47,7 @@ FP32X2_PEAK_TFLOPS_DERIVED = 152 * 128 * 2.07e9 * 2 / 12 / 1e12
 # mixed-form kernels, from one ncu capture of each on the 256x256 case (64 subdomains of the C2 size;
 # the kernels work subdomain by subdomain, so the traffic of a launch grows with the subdomains it
 # covers).  A kernel changed after its capture has no entry (traffic null).
-NCU_TRAFFIC_PER_SUBDOMAIN = {"eig_orthogonalisation": 0.4316e6, "eig_triangular_solves": 1.0622e6}
+NCU_TRAFFIC_PER_SUBDOMAIN = {"eig_triangular_solves": 1.0622e6}
 MIXED_KERNEL_DTYPE = {"lu_local": "f32", "lu_splitting": "f32x2", "eig_triangular_solves": "f32x2",
                       "eig_orthogonalisation": "f32x2", "eig_rayleigh_ritz": "f32x2", "coarse_lu": "f32x2",
                       "coarse_inverse": "f32x2"}

@@ -33,8 +33,10 @@ def test_roofline_entry_arithmetic():
     assert e["bound"] == "alu" and e["dtype"] == "f32x2"
     assert e["achieved"] == pytest.approx(1000.0)
     assert e["frac"] == pytest.approx(1000.0 / bench.FP32X2_PEAK_TFLOPS_DERIVED)
-    assert e["traffic"] == pytest.approx(bench.NCU_TRAFFIC_PER_SUBDOMAIN["eig_orthogonalisation"] * 256)
-    # a kernel without a capture reports no traffic; the plain form's kernels use the FP64 peak
+    # traffic: per subdomain from the capture, times the subdomains of the launch; none without one
+    e = bench.roofline_entry("eig_triangular_solves", 3, 6.0, 6e12, 6780.0, subdomains=256)
+    assert e["traffic"] == pytest.approx(bench.NCU_TRAFFIC_PER_SUBDOMAIN["eig_triangular_solves"] * 256)
+    # the plain form's kernels use the FP64 peak
     e = bench.roofline_entry("coarse_lu", 1, 1.0, 1e9, 6780.0, fp32=False, subdomains=256)
     assert e["traffic"] is None and e["peak"] == bench.FP64_PEAK_TFLOPS_NOMINAL
     # the apply's local solves are HBM bound: 1e9 bytes per launch / 0.5 ms against the measured copy rate
