@@ -249,7 +249,9 @@ def bfs_region_partition(A: sp.csr_matrix, nparts: int, tmin: int, tmax: int, se
     region seeds are distinct random nodes.  Regions grow one node at a time
     in round-robin order until their target is met or their frontier is
     exhausted.  Connected groups of nodes left unclaimed join the smallest
-    adjacent region.
+    adjacent region when that keeps it within tmax; a larger group is shared
+    among the regions around it, which grow into it one node at a time, the
+    smallest region first.
     """
     n = A.shape[0]
     rng = np.random.Generator(np.random.PCG64(seed + 100000))
@@ -303,9 +305,40 @@ def bfs_region_partition(A: sp.csr_matrix, nparts: int, tmin: int, tmax: int, se
                 elif part[k] >= 0:
                     nbr_regions.add(int(part[k]))
         target = min(nbr_regions, key=lambda r: (size[r], r))
+        if size[target] + len(comp) <= tmax:
+            for u in comp:
+                part[u] = target
+            size[target] += len(comp)
+            continue
+        in_comp = set(comp)
         for u in comp:
-            part[u] = target
-        size[target] += len(comp)
+            part[u] = -1
+        fronts = {r: deque() for r in sorted(nbr_regions)}
+        for u in comp:
+            for k in indices[indptr[u]:indptr[u + 1]]:
+                if part[k] >= 0:
+                    fronts[int(part[k])].append(int(k))
+        left = len(comp)
+        while left:
+            claimed = False
+            for r in sorted(fronts, key=lambda r: (size[r], r)):
+                q = fronts[r]
+                while q and not claimed:
+                    v = q[0]
+                    for k in indices[indptr[v]:indptr[v + 1]]:
+                        if part[k] == -1 and int(k) in in_comp:
+                            part[k] = r
+                            size[r] += 1
+                            q.append(int(k))
+                            left -= 1
+                            claimed = True
+                            break
+                    if not claimed:
+                        q.popleft()
+                if claimed:
+                    break
+            if not claimed:
+                raise RuntimeError("unclaimed nodes left in a connected group")
     return part.astype(np.int32)
 
 
