@@ -148,8 +148,15 @@ def test_gradient_matches_central_differences(sub):
 
 
 def test_bf16_forward_uses_rounded_weights():
+    """bfloat16 holds the weight matrices only: the biases (given values bfloat16 cannot hold
+    here) stay in full precision."""
     Aii, lump, n_I = _subdomain_inputs()[1]
-    theta = gnn.init_params(9)
+    d = gnn.unpack(gnn.init_params(9))
+    rng = np.random.default_rng(12)
+    for k in d:
+        if k.startswith("b"):
+            d[k] = 0.1 * rng.standard_normal(d[k].shape)
+    theta = gnn.pack(d)
     W, S, X = gnn.graph_and_features(Aii, lump, n_I)
     c16 = gnn.forward(gnn.unpack(theta), W, S, X, bf16=True)
     rounded = gnn.unpack(theta)

@@ -1,10 +1,12 @@
-"""The oracle's pins catch plausible mistakes.
+"""The oracles' pins catch plausible mistakes.
 
-Each case plants one mistake in one oracle function, of the kind a restatement of the paper could
-contain (a dropped term, a wrong sign, a wrong index set, a transposed operand, a reversed order):
-the function's source is edited in memory at one place, compiled, and swapped in for the duration
-of the test.  Then the pins of test_oracle_structure and test_oracle_method run, and at least one
-of them must fail.  Nothing is written to disk and nothing here touches the CUDA path.
+Each case plants one mistake in one oracle function, of the kind a restatement of the paper (or of
+the warm-start network's calculus) could contain (a dropped term, a wrong sign, a wrong index set,
+a transposed operand, a reversed order): the function's source is edited in memory at one place,
+compiled, and swapped in for the duration of the test.  Then the pins of that oracle run
+(test_oracle_structure and test_oracle_method for the method, test_gnn_oracle for the network),
+and at least one of them must fail.  Nothing is written to disk and nothing here touches the CUDA
+path.
 """
 import inspect
 import itertools
@@ -14,14 +16,16 @@ import warnings
 import pytest
 
 from oracle import a2ls_oracle as O
+from oracle import gnn_oracle as G
+from tests import test_gnn_oracle as TG
 from tests import test_oracle_method as TM
 from tests import test_oracle_structure as TS
 
 
-def _pins():
-    """Every pin of the two oracle test modules with every parameter combination."""
+def _pins(modules):
+    """Every pin of the given test modules with every parameter combination."""
     out = []
-    for mod in (TS, TM):
+    for mod in modules:
         for name in sorted(dir(mod)):
             if not name.startswith("test_"):
                 continue
@@ -45,14 +49,11 @@ def _pins():
     return out
 
 
-PINS = _pins()
-
-
-def _mutant(func_name: str, old: str, new: str):
-    """The oracle function func_name with the one occurrence of `old` in its source replaced."""
-    src = textwrap.dedent(inspect.getsource(getattr(O, func_name)))
+def _mutant(module, func_name: str, old: str, new: str):
+    """The function func_name of `module` with the one occurrence of `old` in its source replaced."""
+    src = textwrap.dedent(inspect.getsource(getattr(module, func_name)))
     assert src.count(old) == 1, (func_name, old)
-    ns = dict(vars(O))
+    ns = dict(vars(module))
     exec(compile(src.replace(old, new), f"<{func_name} with a planted mistake>", "exec"), ns)
     return ns[func_name]
 
@@ -109,13 +110,43 @@ MUTANTS = {
     "multiplicity_counts_once": ("multiplicity_number", "count[s.idx] += 1", "count[s.interior] += 1"),
 }
 
+# the warm-start network (forward, propagation, loss, backward, Adam, bfloat16 rounding)
+GNN_MUTANTS = {
+    "edge_weight_scale": ("graph_and_features", "/ (2.0 * den[mutual])", "/ den[mutual]"),
+    "overlap_flag_on_interior": ("graph_and_features", "X[n_I:, 3] = 1.0", "X[:n_I, 3] = 1.0"),
+    "propagation_weights_swapped": ("propagate", "(1.0 - ALPHA) * (S @ p) + ALPHA * p0",
+                                    "ALPHA * (S @ p) + (1.0 - ALPHA) * p0"),
+    "adjoint_last_term_dropped": ("propagate_adjoint", "return g + acc", "return acc"),
+    "forward_aggregates_with_S": ("forward", "m = W @ h", "m = S @ h"),
+    "forward_rounds_biases": ("forward", "(round_bf16(v) if bf16 and k.startswith(\"W\") else v)",
+                              "(round_bf16(v) if bf16 else v)"),
+    "loss_gradient_sign": ("loss_and_dY", "dY = -2.0 * R @ C.T / m", "dY = 2.0 * R @ C.T / m"),
+    "backward_aggregation_dropped": ("backward", "dh = dpre @ P[f\"W_s{t}\"].T + W.T @ (dpre @ P[f\"W_n{t}\"].T)",
+                                     "dh = dpre @ P[f\"W_s{t}\"].T"),
+    "backward_neighbour_grad_transposed": ("backward", "grads[f\"W_n{t}\"] = c[f\"m{t}\"].T @ dpre",
+                                           "grads[f\"W_n{t}\"] = dpre.T @ c[f\"m{t}\"]"),
+    "backward_bias_doubled": ("backward", "grads[f\"b_{t}\"] = dpre.sum(axis=0)",
+                              "grads[f\"b_{t}\"] = 2.0 * dpre.sum(axis=0)"),
+    "backward_relu_mask_of_wrong_layer": ("backward", "dpre = dh * (c[f\"pre{t}\"] > 0)",
+                                          "dpre = dh * (c[f\"pre{t - 1}\"] > 0)"),
+    "adam_without_bias_correction": ("adam_step", "mhat = m / (1.0 - beta1 ** t)", "mhat = m"),
+    "bf16_truncates": ("round_bf16", "((f + 0x7FFF + lsb) >> 16) << 16", "(f >> 16) << 16"),
+    "sample_mean_over_all": ("sample_loss_grad", "return (tot / cnt, g / cnt) if cnt else (0.0, g)",
+                             "return (tot / len(subdomains), g / len(subdomains)) if cnt else (0.0, g)"),
+}
 
-@pytest.mark.parametrize("mutant", sorted(MUTANTS))
-def test_pins_catch_planted_mistake(mutant, monkeypatch):
-    func, old, new = MUTANTS[mutant]
-    monkeypatch.setattr(O, func, _mutant(func, old, new))
+SUITES = {"method": (O, (TS, TM), MUTANTS), "network": (G, (TG,), GNN_MUTANTS)}
+PINS = {name: _pins(mods) for name, (_, mods, _) in SUITES.items()}
+CASES = [(suite, m) for suite, (_, _, muts) in SUITES.items() for m in sorted(muts)]
+
+
+@pytest.mark.parametrize("suite,mutant", CASES)
+def test_pins_catch_planted_mistake(suite, mutant, monkeypatch):
+    module, _, muts = SUITES[suite]
+    func, old, new = muts[mutant]
+    monkeypatch.setattr(module, func, _mutant(module, func, old, new))
     failed = None
-    for label, f, kw in PINS:
+    for label, f, kw in PINS[suite]:
         try:
             with warnings.catch_warnings():
                 warnings.simplefilter("ignore")
@@ -126,18 +157,20 @@ def test_pins_catch_planted_mistake(mutant, monkeypatch):
     assert failed is not None, f"no pin fails with the planted mistake {mutant}"
 
 
-def test_unmutated_copies_pass():
+@pytest.mark.parametrize("suite", sorted(SUITES))
+def test_unmutated_copies_pass(suite):
     """The compile-and-swap mechanism itself changes nothing: every pin passes on copies of the
     oracle functions compiled from their unedited source."""
-    funcs = sorted({f for f, _, _ in MUTANTS.values()})
+    module, _, muts = SUITES[suite]
+    funcs = sorted({f for f, _, _ in muts.values()})
     mp = pytest.MonkeyPatch()
     try:
         for func in funcs:
-            src = textwrap.dedent(inspect.getsource(getattr(O, func)))
-            ns = dict(vars(O))
+            src = textwrap.dedent(inspect.getsource(getattr(module, func)))
+            ns = dict(vars(module))
             exec(compile(src, f"<{func} copy>", "exec"), ns)
-            mp.setattr(O, func, ns[func])
-        for label, f, kw in PINS:
+            mp.setattr(module, func, ns[func])
+        for label, f, kw in PINS[suite]:
             with warnings.catch_warnings():
                 warnings.simplefilter("ignore")
                 f(**kw)
