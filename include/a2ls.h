@@ -266,10 +266,11 @@ int a2ls_set_coarse_basis(a2ls_handle* h, const int32_t* m, const double* W);
  *   r, z : device, n doubles each, owned by the caller; they must not alias.
  * The call allocates nothing.  Its scratch vectors (2n + 2 n0 doubles, plus sum of the subdomain
  * sizes for the ASM variants or the multiplicity partition of unity) come from a fixed array of
- * 1,048,576 doubles (8 MiB) in the library's static device memory, which every GPU that loads the
- * library holds until the process exits; larger problems get A2LS_ERR_ARG.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with that device current, so
- * make that first call before any stream capture.  The handle must have been set up on the current
+ * 1,048,576 doubles (8 MiB) in the library's static device memory, which every GPU on which a
+ * handle is set up holds until the process exits; larger problems get A2LS_ERR_ARG.  a2ls_setup loads the
+ * array on its device (the one allocation it needs, made while setup allocates anyway); each call
+ * then looks up the array's device address (cudaGetSymbolAddress) with the handle's device current,
+ * which allocates nothing once the array is loaded.  The handle must have been set up on the current
  * device (A2LS_ERR_STATE otherwise).  All calls on a device share the one array and overwrite every
  * scratch value they read, so no clearing is needed, but calls whose work overlaps on the GPU
  * (other streams, handles or threads) race on it.  Asynchronous on the handle's stream.

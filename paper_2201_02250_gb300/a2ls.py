@@ -393,14 +393,6 @@ class WarmStartNet:
     def adam_step(self, lr: float):
         _check(lib().a2ls_gnn_adam_step(self._g, float(lr)))
 
-    def envelope(self) -> np.ndarray:
-        """(N, 4): envelope LU flops (all pivots, overlap pivots), L row-envelope and U column-envelope entries."""
-        return np.frombuffer(self._query(Q_ENVELOPE), dtype=np.float64).reshape(-1, 4).copy()
-
-    def eig_unconverged(self) -> int:
-        """Subdomains whose local eigensolve stopped at eig_max_cycles without reaching eig_tol."""
-        return int(np.frombuffer(self._query(Q_EIG_UNCONVERGED), dtype=np.int32)[0])
-
     def launches(self) -> int:
         return int(lib().a2ls_gnn_launches(self._g))
 

@@ -196,6 +196,9 @@ void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv,
 template <class T> void block_solve(a2ls_handle* h, const T* fac, T* X, const int64_t* xoff, int col0, int ldx,
                                     const int* pvec, int pmax, const int* active, int forward, int backward);
 
+// k_static.cu: loads the module of a2ls_apply_static's static scratch on the current device
+void prime_static_scratch();
+
 // k_gnn.cu: the warm-start network's proposal, Y = sum n_i x 16 FP32 on the handle's stream
 void gnn_infer(a2ls_handle* h, const a2ls_gnn* model, float* Y);
 

@@ -463,6 +463,8 @@ int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int
       else autotune_local_solves<float>(h, static_cast<float*>(h->d_fac), h->d_t, scratch, mode);
       h->opt.timing = timing;
     }
+    // load the module holding a2ls_apply_static's scratch array now, while allocation is allowed
+    prime_static_scratch();
     sync_and_check(h, "setup");
     h->times[Phase::SETUP_TOTAL] = total.stop();
     *out = h;

@@ -11,7 +11,6 @@
 #include "a2ls_internal.cuh"
 
 #include <algorithm>
-#include <mutex>
 
 namespace a2ls {
 
@@ -27,7 +26,7 @@ __global__ void k_prolong(int n, const int* mrow, const int* mpos, const int* ms
 __global__ void k_combine(int n, const int* mrow, const int* mpos, const double* __restrict__ yloc,
                           const double* __restrict__ q, double* z);
 
-// 1 Mi doubles = 8 MiB per device, held from library load until process exit
+// 1 Mi doubles = 8 MiB per device, held from the first a2ls_setup on that device until process exit
 constexpr size_t STATIC_SCRATCH_DOUBLES = size_t(1) << 20;
 static __device__ __align__(256) double g_static_scratch[STATIC_SCRATCH_DOUBLES];
 
@@ -51,23 +50,18 @@ static int guarded_call(F&& f) {
   }
 }
 
-constexpr int MAX_DEVICES = 64;
-static double* s_scratch_addr[MAX_DEVICES];
-static std::mutex s_scratch_mutex;
-
-// Device address of the static scratch on the current device (looked up once per device).
+// Device address of the static scratch on the current device.  Looked up on every call, so that a
+// context the caller recreated (cudaDeviceReset) is never written through a stale address.  The
+// lookup loads the module that holds the array the first time it runs in a context; with CUDA's lazy
+// module loading that load maps the array's 8 MiB, so a2ls_setup performs it (prime_static_scratch)
+// and the apply itself then only reads the address of an already loaded module.
 static double* static_scratch_address() {
-  int dev = 0;
-  A2LS_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= MAX_DEVICES) fail(A2LS_ERR_ARG, "device ordinal %d out of range", dev);
-  std::lock_guard<std::mutex> lock(s_scratch_mutex);
-  if (!s_scratch_addr[dev]) {
-    void* p = nullptr;
-    A2LS_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
-    s_scratch_addr[dev] = static_cast<double*>(p);
-  }
-  return s_scratch_addr[dev];
+  void* p = nullptr;
+  A2LS_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+  return static_cast<double*>(p);
 }
+
+void prime_static_scratch() { (void)static_scratch_address(); }
 
 static size_t pad32(size_t v) { return (v + 31) / 32 * 32; }
 

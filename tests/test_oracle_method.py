@@ -6,6 +6,7 @@ condition-number bound of Section 3.2, library eigen-solvers on the special
 cases where they apply, and a brute-force Krylov least-squares check of GMRES.
 """
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -44,6 +45,27 @@ def test_golden_gevp_and_coarse_operator():
     E = P.coarse.E
     np.testing.assert_allclose(np.sort(np.linalg.eigvalsh(E)),
                                np.sort(np.linalg.eigvalsh(frac_array(g["E_times5"]) / 5)), atol=1e-14)
+
+
+@pytest.mark.parametrize("case", range(5))
+def test_golden_tau_selection(case):
+    """Eq. 3.2 on the worked example: the pairs with |lambda| > 1/tau are kept (strictly), at most nev."""
+    g, A, part = _golden_problem()
+    c = g["tau_selection"][case]
+    tau = float(Fraction(c["tau"]))
+    kept = frac_vector(c["kept"]) if c["kept"] else np.zeros(0)
+    P = O.setup(A, part, 1, nev=3, tau=tau, keep_local=True)
+    for e, w, vec in zip(P.eig, P.coarse.W, g["gevp_top_vector"]):
+        assert e.kernel_dim == 0
+        np.testing.assert_allclose(np.sort(e.selected.real)[::-1], kept, atol=1e-13)
+        assert w.shape[1] == len(kept)
+        if len(kept) == 1:   # span(D_i u), u the eigenvector of 3
+            u = frac_vector(vec) * np.array([1.0, 1.0, 0.0])
+            u /= np.linalg.norm(u)
+            assert abs(abs(w[:, 0] @ u) - 1.0) < 1e-13
+        if len(kept) == 2:   # D_i [u v] spans the interior nodes
+            np.testing.assert_allclose(w @ w.T, np.diag([1.0, 1.0, 0.0]), atol=1e-13)
+    assert P.coarse.n0 == 2 * len(kept)
 
 
 def test_single_subdomain_no_overlap_is_exact_inverse():

@@ -80,6 +80,9 @@ MUTANTS = {
     "gevp_pair_real_part_twice": ("local_gevp", "np.stack([u.real, u.imag], axis=1)",
                                   "np.stack([u.real, u.real], axis=1)"),
     "gevp_kernel_part_dropped": ("local_gevp", "kernel_cols = VK @ Vt[:r].T", "kernel_cols = VK[:, :0]"),
+    # Eq. 3.2: the threshold |lambda| > 1/tau
+    "tau_threshold_not_inverted": ("local_gevp", "np.abs(lam) > 1.0 / tau", "np.abs(lam) > tau"),
+    "tau_threshold_doubled": ("local_gevp", "np.abs(lam) > 1.0 / tau", "np.abs(lam) > 2.0 / tau"),
     # coarse space and Eq. 2.2 / 2.4
     "coarse_operator_transposed": ("coarse_space_from_W", "Phi.T @ (A @ Phi)", "Phi.T @ (A.T @ Phi)"),
     "coarse_columns_not_orthonormalised": ("orthonormal_columns", "return Q[:, keep]", "return W"),

@@ -30,8 +30,10 @@ def _cuda():
 @pytest.mark.parametrize("variant,pou,precision", [
     ("deflated_ras", "boolean", "fp64"),
     ("deflated_ras", "boolean", "fp32"),
+    ("deflated_ras", "multiplicity", "fp64"),   # RAS that combines yloc with the coarse q
     ("additive_asm", "multiplicity", "fp64"),
     ("ras", "boolean", "fp64"),
+    ("asm", "boolean", "fp64"),                 # yloc right after q and t, no coarse pieces
 ])
 def test_apply_static_matches_apply(variant, pou, precision):
     from paper_2201_02250_gb300 import a2ls
@@ -39,14 +41,19 @@ def test_apply_static_matches_apply(variant, pou, precision):
     P, _keep = a2ls.from_scipy(prob.A, prob.part, prob.overlap, prob.nev, variant=variant, pou=pou,
                                precision=precision)
     rng = np.random.Generator(np.random.PCG64(5))
-    for call in range(2):
-        r = torch.as_tensor(rng.uniform(-1, 1, prob.n), device="cuda")
-        z_ref = torch.empty_like(r)
-        z = torch.full_like(r, float("nan"))
+    rs = [torch.as_tensor(rng.uniform(-1, 1, prob.n), device="cuda") for _ in range(2)]
+    z_refs = [torch.empty_like(r) for r in rs]
+    zs = [torch.full_like(r, float("nan")) for r in rs]
+    for r, z_ref in zip(rs, z_refs):
         P.apply(r, z_ref)
-        P.apply_static(r, z)
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    for call in range(2):   # the first static call after setup included: no device memory is taken
+        P.apply_static(rs[call], zs[call])
         torch.cuda.synchronize()
-        a, b = z.cpu().numpy(), z_ref.cpu().numpy()
+        assert torch.cuda.mem_get_info()[0] == free_before, call
+    for call in range(2):
+        a, b = zs[call].cpu().numpy(), z_refs[call].cpu().numpy()
         assert np.all(np.isfinite(a))
         assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b), (call, np.linalg.norm(a - b))
     P.close()
