@@ -208,20 +208,100 @@ def local_gevp(Aii: np.ndarray, Atil: np.ndarray, d: np.ndarray, nev: int,
     C = Atil
     VK, VR = _null_space(C)
     dimK = VK.shape[1]
-    kernel_cols = np.zeros((Aii.shape[0], 0))
-    if dimK > 0:
-        BV = B @ VK
-        _, sv, Vt = np.linalg.svd(BV)
-        tol = max(BV.shape) * EPS * max(np.linalg.norm(B, 2), 1e-300)
-        r = int(np.sum(sv > tol))
-        kernel_cols = VK @ Vt[:r].T
+    kernel_cols = _kernel_part(B, VK)
     kdim = kernel_cols.shape[1]
     Bc = VR.T @ B @ VR
     Cc = VR.T @ C @ VR
     lam, a = sla.eig(Bc, Cc)
+    return _select_eigenpairs(lam, lambda j: VR @ a[:, j], kernel_cols, nev, tau, dimK)
+
+
+def local_gevp_fast(Aii: sp.spmatrix, Atil: sp.spmatrix, d: np.ndarray, nev: int,
+                    tau: float | None = None, seed: int = 0) -> LocalEigen:
+    """Oracle-fast form of local_gevp for subdomains too large for dense QZ (Eqs. 3.1-3.2).
+
+    The same compressed pencil (V_R^T B V_R, V_R^T C V_R), with B = D_i A_ii D_i and C = A~_ii kept
+    sparse, and the same kernel part and selection.  Its largest-|lambda| eigenpairs are found by
+    Arnoldi (ARPACK through scipy.sparse.linalg.eigs) on the operator T_R = C_R^{-1} B_R, the inverted
+    form of the pencil, applied in the full local space: for u in range(V_R), T u = y solves
+        [[C, V_K], [V_K^T, 0]] [y; s] = [B u; 0],
+    i.e. V_R^T C y = V_R^T B u with y orthogonal to ker(C), which is V_R T_R V_R^T u (the bordered
+    matrix is factored once by sparse LU).  T maps every vector into range(V_R), so its non-zero
+    eigenvalues are those of T_R and their eigenvectors lie in range(V_R).  ker(C) comes from the
+    dense SVD, as in local_gevp.  The start vector is a seeded uniform vector projected onto
+    range(V_R).
+    """
+    import scipy.sparse.linalg as spla
+
+    n = Aii.shape[0]
+    Dm = sp.diags(d)
+    B = (Dm @ sp.csr_matrix(Aii) @ Dm).tocsr()
+    C = sp.csr_matrix(Atil)
+    VK, _ = _null_space(C.toarray())
+    dimK = VK.shape[1]
+    kernel_cols = _kernel_part(B, VK)
+    kdim = kernel_cols.shape[1]
+    want = min(max(nev - kdim, 0), n - dimK)
+    if want == 0:
+        return _select_eigenpairs(np.zeros(0, dtype=complex), None, kernel_cols, nev, tau, dimK)
+    K = sp.bmat([[C, sp.csr_matrix(VK)], [sp.csr_matrix(VK.T), None]], format="csc")
+    lu = spla.splu(K)
+    rhs = np.zeros(n + dimK)
+
+    def T(u):
+        rhs[:n] = B @ np.asarray(u).ravel()
+        return lu.solve(rhs)[:n]
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    v0 = rng.uniform(-1.0, 1.0, n)
+    v0 -= VK @ (VK.T @ v0)
+    k = min(want + 2, n - dimK - 2)   # two more than kept, so that a pair cut at the end is seen
+    if k < want + 1:
+        raise ValueError("local_gevp_fast: subdomain too small for Arnoldi, use local_gevp")
+    op = spla.LinearOperator((n, n), matvec=T, dtype=np.float64)
+    lam, U = spla.eigs(op, k=k, which="LM", v0=v0, tol=1e-13, ncv=min(n - dimK - 1, max(2 * k + 1, 40)),
+                       maxiter=100 * n)
+    return _select_eigenpairs(lam, lambda j: U[:, j], kernel_cols, nev, tau, dimK)
+
+
+def sparse_local_matrices(A: sp.spmatrix, sub: Subdomain) -> tuple:
+    """A_ii and A~_ii (Definition 3.1) as sparse matrices, for local_gevp_fast."""
+    A = A.tocsr()
+    idx = sub.idx
+    Aii = A[idx][:, idx].tocsr()
+    s = lumped_row_sums(A, sub)
+    nI = sub.n_I
+    At = Aii.tolil()
+    for j in range(len(s)):
+        At[nI + j, nI + j] -= s[j]
+    return Aii, At.tocsr()
+
+
+def _kernel_part(B, VK: np.ndarray) -> np.ndarray:
+    """(L_i cap K_i)^{perp K_i} (Eq. 3.2): V_K times the right singular vectors of B V_K whose
+    singular value is non-zero (above max(shape) * eps * ||B||_2)."""
+    if VK.shape[1] == 0:
+        return np.zeros((VK.shape[0], 0))
+    BV = B @ VK
+    _, sv, Vt = np.linalg.svd(BV)
+    Bn = np.linalg.norm(B.toarray() if sp.issparse(B) else B, 2)
+    tol = max(BV.shape) * EPS * max(Bn, 1e-300)
+    r = int(np.sum(sv > tol))
+    return VK @ Vt[:r].T
+
+
+def _select_eigenpairs(lam: np.ndarray, vector, kernel_cols: np.ndarray, nev: int, tau, dimK: int) -> LocalEigen:
+    """Selection of Eq. 3.2 from finite eigenvalues ``lam`` (any order) with eigenvectors ``vector(j)``.
+
+    READING: sorted by |lambda| descending (the kernel part, lambda = infinity, first); the first
+    nev - dim(kernel part) finite pairs are kept, or with tau > 0 only those with |lambda| > 1/tau
+    among them; a complex-conjugate pair cut by the count keeps its partner; a pair contributes the
+    real basis [Re u, Im u].
+    """
+    n = kernel_cols.shape[0]
+    kdim = kernel_cols.shape[1]
     order = np.lexsort((-lam.imag, -np.abs(lam)))  # |lambda| descending, +imag first in a pair
     lam = lam[order]
-    a = a[:, order]
     budget = min(max(nev - kdim, 0), len(lam))
     if tau is not None and tau > 0:
         budget = min(budget, int(np.sum(np.abs(lam) > 1.0 / tau)))
@@ -236,7 +316,7 @@ def local_gevp(Aii: np.ndarray, Atil: np.ndarray, d: np.ndarray, nev: int,
     for j in range(take):
         if j in done:
             continue
-        u = VR @ a[:, j]
+        u = vector(order[j])
         if abs(lam[j].imag) > 0:
             # find the partner within the taken set and mark it
             for k in range(j + 1, take):
@@ -246,7 +326,7 @@ def local_gevp(Aii: np.ndarray, Atil: np.ndarray, d: np.ndarray, nev: int,
             cols.append(np.stack([u.real, u.imag], axis=1))
         else:
             cols.append(u.real[:, None])
-    Z = np.concatenate(cols, axis=1) if cols else np.zeros((Aii.shape[0], 0))
+    Z = np.concatenate(cols, axis=1) if cols else np.zeros((n, 0))
     return LocalEigen(Z=Z, kernel_dim=kdim, eigvals=lam, selected=lam[:take], dimK=dimK)
 
 

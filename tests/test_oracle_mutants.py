@@ -18,6 +18,7 @@ import pytest
 from oracle import a2ls_oracle as O
 from oracle import gnn_oracle as G
 from tests import test_gnn_oracle as TG
+from tests import test_oracle_fast as TF
 from tests import test_oracle_method as TM
 from tests import test_oracle_structure as TS
 
@@ -75,14 +76,14 @@ MUTANTS = {
     # Eqs. 3.1-3.2: pencil, kernel part, order, real basis
     "gevp_without_D": ("local_gevp", "B = (d[:, None] * Aii) * d[None, :]", "B = Aii"),
     "gevp_swapped_pencil": ("local_gevp", "lam, a = sla.eig(Bc, Cc)", "lam, a = sla.eig(Cc, Bc)"),
-    "gevp_smallest_first": ("local_gevp", "np.lexsort((-lam.imag, -np.abs(lam)))",
+    "gevp_smallest_first": ("_select_eigenpairs", "np.lexsort((-lam.imag, -np.abs(lam)))",
                             "np.lexsort((-lam.imag, np.abs(lam)))"),
-    "gevp_pair_real_part_twice": ("local_gevp", "np.stack([u.real, u.imag], axis=1)",
+    "gevp_pair_real_part_twice": ("_select_eigenpairs", "np.stack([u.real, u.imag], axis=1)",
                                   "np.stack([u.real, u.real], axis=1)"),
-    "gevp_kernel_part_dropped": ("local_gevp", "kernel_cols = VK @ Vt[:r].T", "kernel_cols = VK[:, :0]"),
+    "gevp_kernel_part_dropped": ("_kernel_part", "return VK @ Vt[:r].T", "return VK[:, :0]"),
     # Eq. 3.2: the threshold |lambda| > 1/tau
-    "tau_threshold_not_inverted": ("local_gevp", "np.abs(lam) > 1.0 / tau", "np.abs(lam) > tau"),
-    "tau_threshold_doubled": ("local_gevp", "np.abs(lam) > 1.0 / tau", "np.abs(lam) > 2.0 / tau"),
+    "tau_threshold_not_inverted": ("_select_eigenpairs", "np.abs(lam) > 1.0 / tau", "np.abs(lam) > tau"),
+    "tau_threshold_doubled": ("_select_eigenpairs", "np.abs(lam) > 1.0 / tau", "np.abs(lam) > 2.0 / tau"),
     # coarse space and Eq. 2.2 / 2.4
     "coarse_operator_transposed": ("coarse_space_from_W", "Phi.T @ (A @ Phi)", "Phi.T @ (A.T @ Phi)"),
     "coarse_columns_not_orthonormalised": ("orthonormal_columns", "return Q[:, keep]", "return W"),
@@ -138,7 +139,16 @@ GNN_MUTANTS = {
                              "return (tot / len(subdomains), g / len(subdomains)) if cnt else (0.0, g)"),
 }
 
-SUITES = {"method": (O, (TS, TM), MUTANTS), "network": (G, (TG,), GNN_MUTANTS)}
+# the oracle-fast local eigensolve (Arnoldi on the inverted pencil), pinned by the dense-QZ oracle
+FAST_MUTANTS = {
+    "fast_operator_without_D": ("local_gevp_fast", "B = (Dm @ sp.csr_matrix(Aii) @ Dm).tocsr()",
+                                "B = sp.csr_matrix(Aii)"),
+    "fast_operator_transposed": ("local_gevp_fast", "return lu.solve(rhs)[:n]", "return lu.solve(rhs, trans=\"T\")[:n]"),
+    "fast_smallest_magnitude": ("local_gevp_fast", 'which="LM"', 'which="SM"'),
+    "fast_splitting_sign": ("sparse_local_matrices", "-= s[j]", "+= s[j]"),
+}
+
+SUITES = {"method": (O, (TS, TM), MUTANTS), "network": (G, (TG,), GNN_MUTANTS), "fast": (O, (TF,), FAST_MUTANTS)}
 PINS = {name: _pins(mods) for name, (_, mods, _) in SUITES.items()}
 CASES = [(suite, m) for suite, (_, _, muts) in SUITES.items() for m in sorted(muts)]
 
