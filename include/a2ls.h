@@ -125,6 +125,13 @@ typedef struct {
                                the Ritz vectors it reached (still a valid coarse space, possibly a weaker
                                one; counted by A2LS_Q_EIG_UNCONVERGED); 1: a2ls_setup fails with
                                A2LS_ERR_EIGEN instead */
+  int32_t eig_stall_cycles; /* stagnation stop of the local eigensolves, default 8: a subdomain whose
+                               largest relative residual of the wanted Ritz pairs has not halved over
+                               this many cycles stops with the Ritz vectors it has (counted as
+                               unconverged, and as stagnated by A2LS_Q_EIG_UNCONVERGED); 0 = off */
+  int32_t tensor_cores;     /* 1 (default): the trailing updates of the double-float LU run on the tensor
+                               cores (BF16 digit products accumulated exactly in FP32, to double-float
+                               accuracy); 0: on the FP32 pipe */
 } a2ls_options;
 
 /* Fills *opt with the defaults listed above.  Never fails. */
@@ -203,7 +210,10 @@ enum {
   A2LS_Q_EIGSTATS = 8,   /* int32[2*N]: eigen cycles run and kernel dimension per subdomain */
   A2LS_Q_LAUNCHES = 9,   /* int64[1]: kernels this handle has launched so far */
   A2LS_Q_TUNING = 11,    /* int32[2]: CTA width chosen for the local solves, CUDA graphs held */
-  A2LS_Q_EIG_UNCONVERGED = 12, /* int32[1]: subdomains whose eigensolve stopped at eig_max_cycles */
+  A2LS_Q_EIG_UNCONVERGED = 12, /* int32[2]: subdomains whose eigensolve stopped short of eig_tol, and how
+                                  many of them by the stagnation stop (the others ran eig_max_cycles) */
+  A2LS_Q_EIGRES = 14,    /* double[N]: per subdomain the largest residual ||T u - lambda u|| / |lambda| of
+                            the wanted Ritz pairs at its last eigen cycle (0 without a Krylov part) */
   A2LS_Q_ENVELOPE = 13,  /* double[4*N]: per subdomain the flops of an LU confined to the envelope of the
                             local pattern (all pivots; overlap pivots only), and the entries of L's row
                             envelope and U's column envelope (sum_r r - f_r + 1, sum_c c - g_c + 1), f_r / g_c

@@ -264,6 +264,40 @@ def local_gevp_fast(Aii: sp.spmatrix, Atil: sp.spmatrix, d: np.ndarray, nev: int
     return _select_eigenpairs(lam, lambda j: U[:, j], kernel_cols, nev, tau, dimK)
 
 
+def _fast_one(job: tuple) -> LocalEigen:
+    Aii, Atil, d, nev, tau = job
+    return local_gevp_fast(Aii, Atil, d, nev, tau)
+
+
+def local_eigen_fast_many(A: sp.spmatrix, subs: list, D: list, nev: int, indices, tau: float | None = None,
+                          workers: int = 1) -> list:
+    """local_gevp_fast for the subdomains ``indices`` (in that order), optionally in a pool of
+    ``workers`` processes started with spawn (one BLAS thread each)."""
+    jobs = []
+    for i in indices:
+        Aii, Atil = sparse_local_matrices(A, subs[i])
+        jobs.append((Aii, Atil, D[i], nev, tau))
+    if workers <= 1:
+        return [_fast_one(j) for j in jobs]
+    import multiprocessing
+    import os
+    from concurrent.futures import ProcessPoolExecutor
+
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"   # inherited by the spawned workers before they import numpy
+    try:
+        with ProcessPoolExecutor(max_workers=workers, mp_context=multiprocessing.get_context("spawn")) as ex:
+            return list(ex.map(_fast_one, jobs, chunksize=1))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
 def sparse_local_matrices(A: sp.spmatrix, sub: Subdomain) -> tuple:
     """A_ii and A~_ii (Definition 3.1) as sparse matrices, for local_gevp_fast."""
     A = A.tocsr()

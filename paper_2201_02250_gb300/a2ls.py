@@ -20,7 +20,7 @@ FP64, FP32, FP32X2 = 0, 1, 2
 VARIANTS = {"deflated_ras": 0, "deflated_asm": 1, "additive_ras": 2, "additive_asm": 3, "ras": 4, "asm": 5}
 POU = {"boolean": 0, "multiplicity": 1}
 (Q_SIZES, Q_SUBDOMAINS, Q_LUMP, Q_FACTORS, Q_COARSE, Q_EIGVALS, Q_TIMES, Q_EINV, Q_EIGSTATS, Q_LAUNCHES,
- Q_KERNEL_TIMES, Q_TUNING, Q_EIG_UNCONVERGED, Q_ENVELOPE) = range(14)
+ Q_KERNEL_TIMES, Q_TUNING, Q_EIG_UNCONVERGED, Q_ENVELOPE, Q_EIGRES) = range(15)
 TRACKED_KERNELS = ["lu_local", "lu_splitting", "eig_triangular_solves", "eig_orthogonalisation",
                    "eig_rayleigh_ritz", "coarse_lu", "coarse_inverse", "apply_local_solves"]
 PHASES = ["graph", "extract", "lu", "eig_coarse", "coarse", "setup_total", "solve_total", "apply"]
@@ -44,7 +44,8 @@ class Options(ctypes.Structure):
                 ("eig_max_cycles", ctypes.c_int32), ("eig_tol", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("stream", ctypes.c_void_p), ("timing", ctypes.c_int32),
                 ("eig_precision", ctypes.c_int32), ("graphs", ctypes.c_int32), ("warm_start", ctypes.c_void_p),
-                ("eig_strict", ctypes.c_int32)]
+                ("eig_strict", ctypes.c_int32), ("eig_stall_cycles", ctypes.c_int32),
+                ("tensor_cores", ctypes.c_int32)]
 
 
 _LIB = None
@@ -290,8 +291,16 @@ class Preconditioner:
         return np.frombuffer(self._query(Q_ENVELOPE), dtype=np.float64).reshape(-1, 4).copy()
 
     def eig_unconverged(self) -> int:
-        """Subdomains whose local eigensolve stopped at eig_max_cycles without reaching eig_tol."""
+        """Subdomains whose local eigensolve stopped without reaching eig_tol."""
         return int(np.frombuffer(self._query(Q_EIG_UNCONVERGED), dtype=np.int32)[0])
+
+    def eig_stalled(self) -> int:
+        """Subdomains of eig_unconverged() that the stagnation stop ended."""
+        return int(np.frombuffer(self._query(Q_EIG_UNCONVERGED), dtype=np.int32)[1])
+
+    def eig_residuals(self) -> np.ndarray:
+        """(N,): largest relative residual of the wanted Ritz pairs at each subdomain's last cycle."""
+        return np.frombuffer(self._query(Q_EIGRES), dtype=np.float64).copy()
 
     def launches(self) -> int:
         return int(np.frombuffer(self._query(Q_LAUNCHES), dtype=np.int64)[0])

@@ -125,7 +125,9 @@ struct a2ls_handle {
   int zld = 0;
   std::vector<int> h_zcols;                  // N: columns of Z_i in use
   std::vector<int> h_eigstats;               // 2*N
-  int eig_unconverged = 0;                   // subdomains whose eigensolve stopped at eig_max_cycles
+  int eig_unconverged = 0;                   // subdomains whose eigensolve stopped short of eig_tol
+  int eig_stalled = 0;                       // ... of them stopped by the stagnation stop
+  std::vector<double> h_eigres;              // N: worst relative Ritz residual at the last cycle
 
   // apply workspace
   double *d_g = nullptr, *d_c = nullptr, *d_q = nullptr, *d_t = nullptr, *d_yloc = nullptr;

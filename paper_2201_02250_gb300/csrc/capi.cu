@@ -359,6 +359,8 @@ void a2ls_default_options(a2ls_options* o) {
   o->graphs = 1;
   o->warm_start = nullptr;
   o->eig_strict = 0;
+  o->eig_stall_cycles = 8;
+  o->tensor_cores = 1;
 }
 
 const char* a2ls_last_error(void) { return g_last_error.c_str(); }
@@ -655,10 +657,13 @@ int a2ls_query(a2ls_handle* h, int32_t what, void* out, int64_t capacity, int64_
         put(h->h_env.data(), sizeof(double) * h->h_env.size());
         break;
       case A2LS_Q_EIG_UNCONVERGED: {
-        const int32_t v = h->eig_unconverged;
-        put(&v, sizeof(v));
+        const int32_t v[2] = {h->eig_unconverged, h->eig_stalled};
+        put(v, sizeof(v));
         break;
       }
+      case A2LS_Q_EIGRES:
+        put(h->h_eigres.data(), sizeof(double) * h->h_eigres.size());
+        break;
       case A2LS_Q_KERNEL_TIMES: {
         collect_kernel_times(h);
         for (int k = 0; k < KT_COUNT; ++k) {

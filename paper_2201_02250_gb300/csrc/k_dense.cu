@@ -11,8 +11,10 @@
 // diagonal and inv(U_bb) on and above it.  A triangular solve is then a
 // sequence of dense matrix-vector products (no sequential substitution).
 #include "a2ls_internal.cuh"
+#include "tc_dfloat.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace a2ls {
 
@@ -190,14 +192,35 @@ __device__ __forceinline__ void tile_gemm(FA fa, FB fb, int K, Acc (&acc)[4][4],
 // overlap rows is left in place); 1 the remaining columns [n_I, n).
 constexpr size_t lu_smem_elems() { return 2 * (size_t)TB * 65 + 2 * (size_t)TGK * TS; }
 
-template <class T>
-__global__ void __launch_bounds__(256, 2) k_lu(int N, const int* ni, const int* ld, const int64_t* foff,
+// TC (double-float only): the trailing update A22 -= L21 U12 runs on the tensor cores as digit-split
+// BF16 products (tc_dfloat.cuh) in 128 x 64 tiles; its operand digits reuse the shared memory of the
+// other steps, so one CTA runs per SM, holding all of that SM's TMEM.
+template <class T, bool TC>
+__global__ void __launch_bounds__(256, TC ? 1 : 2) k_lu(int N, const int* ni, const int* ld, const int64_t* foff,
                                             T* fac, int allow_last_zero, double* last_pivot,
                                             const double* dscale, int* st, const int* sched, const int* nI,
                                             int phase, const int* off, const int* pf, const int* pg) {
   using Acc = typename AccOf<T>::type;
+  static_assert(!TC || std::is_same<T, dfloat>::value, "tensor-core trailing update is for double-float");
   extern __shared__ __align__(16) unsigned char lu_smem_raw[];
   __shared__ unsigned char lnz[MAXN_LOCAL / TB + 1], unz[MAXN_LOCAL / TB + 1];
+  __shared__ __align__(8) uint64_t tc_bar;
+  __shared__ uint32_t tc_base;
+  __shared__ int tc_eA[TC ? tcdf::TM : 1], tc_eB[TC ? tcdf::TN : 1];
+  __shared__ float tc_red[TC ? 4 * tcdf::TN : 1];
+  tcdf::Ctx ctx{lu_smem_raw, &tc_bar, 0u, 0u, tc_eA, tc_eB};
+  bool tc_fail = false;
+  if constexpr (TC) {
+    if (threadIdx.x == 0) tc::mbar_init(&tc_bar, 1);
+    if (threadIdx.x < 32) {
+      tc::tmem_alloc(&tc_base, tcdf::TMEM_COLS);
+      tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    ctx.tmem = tc_base;
+  }
   __shared__ Acc rdiag[TB];                       // reciprocals of the diagonal block's pivots
   Acc* Dm = reinterpret_cast<Acc*>(lu_smem_raw);  // 64 x 65: the diagonal block, factored in place
   Acc* Iv = Dm + TB * 65;                         // 64 x 65: inv(L11) strictly below, inv(U11) on/above
@@ -321,6 +344,37 @@ __global__ void __launch_bounds__(256, 2) k_lu(int N, const int* ni, const int* 
     }
     __syncthreads();  // L21 and U12 complete before the trailing update reads them
     // 4. A22 -= L21 U12
+    if constexpr (TC) {
+      const int rtiles = (n - c0 + tcdf::TM - 1) / tcdf::TM;
+      for (int rt = 0; rt < rtiles && !tc_fail; ++rt) {
+        const int ta = 2 * rt, tb2 = 2 * rt + 1;   // the two 64-row tiles of this 128-row tile
+        if (!lnz[ta] && !(tb2 < tiles && lnz[tb2])) continue;
+        const int r0 = c0 + rt * tcdf::TM, rows = min(tcdf::TM, n - r0);
+        tcdf::split_a(ctx, [&](int m, int k) -> dfloat {
+          return (m < rows && k < w) ? (dfloat)A[(int64_t)(r0 + m) * L + k0 + k] : dfloat(0.f, 0.f);
+        });
+        for (int ct = 0; ct < tiles; ++ct) {
+          if (!unz[ct]) continue;
+          const int cs = c0 + ct * TB, cols = min(TB, n - cs);
+          tcdf::split_b(ctx, [&](int k, int c) -> dfloat {
+            return (k < w && c < cols) ? (dfloat)A[(int64_t)(k0 + k) * L + cs + c] : dfloat(0.f, 0.f);
+          }, tc_red);
+          if (!tcdf::multiply(ctx)) {
+            if (threadIdx.x == 0) raise_status(st, A2LS_ERR_TIMEOUT, i, k0);
+            tc_fail = true;
+            break;
+          }
+          tcdf::epilogue(ctx, [&](int m, int c, dfloat v) {
+            if (m < rows && c < cols) {
+              T* p = A + (int64_t)(r0 + m) * L + cs + c;
+              *p = (T)((dfloat)*p - v);
+            }
+          });
+        }
+      }
+      __syncthreads();
+      if (tc_fail) break;
+    } else {
     for (int t = 0; t < tiles * tiles; ++t) {
       if (!lnz[t / tiles] || !unz[t % tiles]) continue;
       const int r0 = c0 + (t / tiles) * TB, cs = c0 + (t % tiles) * TB;
@@ -345,17 +399,34 @@ __global__ void __launch_bounds__(256, 2) k_lu(int N, const int* ni, const int* 
         }
     }
     __syncthreads();
+    }
+  }
+  if constexpr (TC) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x < 32) tc::tmem_dealloc(ctx.tmem, tcdf::TMEM_COLS);
   }
 }
 
 template <class T>
 void lu_batched(a2ls_handle* h, T* fac, int allow_last_zero, double* last_pivot, double* diag_scale, int phase) {
   using Acc = typename AccOf<T>::type;
+  if constexpr (std::is_same<T, dfloat>::value) {
+    if (h->opt.tensor_cores) {
+      const size_t smem = std::max(lu_smem_elems() * sizeof(Acc), tcdf::SMEM_BYTES);
+      A2LS_CUDA(cudaFuncSetAttribute(k_lu<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_lu<T, true><<<h->N, 256, smem, h->st>>>(h->N, h->d_ni, h->d_ld, h->d_foff, fac, allow_last_zero, last_pivot,
+                                                diag_scale, h->d_status, h->d_sched, h->d_nI, phase, h->d_off,
+                                                h->d_pf, h->d_pg);
+      A2LS_LAUNCH();
+      return;
+    }
+  }
   const size_t smem = lu_smem_elems() * sizeof(Acc);
-  A2LS_CUDA(cudaFuncSetAttribute(k_lu<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_lu<T><<<h->N, 256, smem, h->st>>>(h->N, h->d_ni, h->d_ld, h->d_foff, fac, allow_last_zero, last_pivot,
-                                      diag_scale, h->d_status, h->d_sched, h->d_nI, phase, h->d_off, h->d_pf,
-                                      h->d_pg);
+  A2LS_CUDA(cudaFuncSetAttribute(k_lu<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_lu<T, false><<<h->N, 256, smem, h->st>>>(h->N, h->d_ni, h->d_ld, h->d_foff, fac, allow_last_zero, last_pivot,
+                                             diag_scale, h->d_status, h->d_sched, h->d_nI, phase, h->d_off, h->d_pf,
+                                             h->d_pg);
   A2LS_LAUNCH();
 }
 
@@ -600,6 +671,183 @@ __global__ void __launch_bounds__(THREADS) k_local_solve(
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined local solves: the same block triangular solves, organised so that a step's memory
+// latency overlaps other work.  Each CTA (THREADS threads, persistent over the same work queue) keeps
+// the gathered vector in shared memory; per 64-row block the panel product reads the factor rows
+// with RU independent vector loads per row in flight before they are used, and the block's 64x64
+// diagonal tile (the inverted triangles) is fetched into one of two shared buffers by asynchronous
+// copies (cp.async) one block ahead, so the tile product reads shared memory only.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_but_last() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// diagonal tile of block b (rows r0 .. r0 + tb, columns r0 .. min(r0 + 64, L)) into dst (64 x 64, T)
+template <class T, int THREADS>
+__device__ __forceinline__ void prefetch_tile(const T* __restrict__ M, int64_t L, int r0, int tb, T* dst) {
+  constexpr int PER16 = 16 / sizeof(T);                   // elements per 16-byte copy
+  const int cols = (int)min((int64_t)TB, L - r0);         // a multiple of 4 elements (L and r0 are)
+  const int chunks = (cols + PER16 - 1) / PER16;
+  for (int e = threadIdx.x; e < tb * chunks; e += THREADS) {
+    const int r = e / chunks, c = (e % chunks) * PER16;
+    cp_async16(dst + r * TB + c, M + (int64_t)(r0 + r) * L + r0 + c);
+  }
+  cp_async_commit();
+}
+
+template <class T, int THREADS, int RU>
+__global__ void __launch_bounds__(THREADS) k_local_solve2(
+    const int* off, const int* nI, const int* ni, const int* ld, const int64_t* foff, const int* idx,
+    const double* D, const T* __restrict__ fac, const double* __restrict__ t, const double* __restrict__ q,
+    double* __restrict__ out, int mode, const int* sched, int* counter, int nwork, const int* toff, const int* tf,
+    const int* tg) {
+  using Acc = typename AccOf<T>::type;
+  using V = typename Vec<T>::type;
+  constexpr int VW = Vec<T>::W;
+  constexpr int WARPS = THREADS / 32;
+  constexpr int RPW = TB / WARPS;   // rows of a block per warp
+  extern __shared__ __align__(16) unsigned char ls2_smem[];
+  T* tile = reinterpret_cast<T*>(ls2_smem);                        // 2 x 64 x 64
+  Acc* x = reinterpret_cast<Acc*>(ls2_smem + 2 * TB * TB * sizeof(T));
+  __shared__ Acc s[TB];
+  __shared__ int item;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int w = item;
+    __syncthreads();
+    if (w >= nwork) break;
+    const int i = sched[w];
+    const int n = ni[i], o = off[i];
+    const int64_t L = ld[i];
+    const T* M = fac + foff[i];
+    const int nb = (n + TB - 1) / TB;
+    const int* tfi = tf + toff[i];
+    const int* tgi = tg + toff[i];
+    prefetch_tile<T, THREADS>(M, L, 0, min(TB, n), tile);
+    for (int l = threadIdx.x; l < L; l += THREADS) x[l] = (l < n) ? (Acc)t[idx[o + l]] : (Acc)0;
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int bb = 0; bb < nb; ++bb) {
+        const int b = pass == 0 ? bb : nb - 1 - bb;
+        const int r0 = b * TB, tb = min(TB, n - r0);
+        const int step = pass * nb + bb;
+        T* cur = tile + (step & 1) * TB * TB;
+        // fetch the next step's diagonal tile (the backward sweep starts at the last block again)
+        if (step + 1 < 2 * nb) {
+          const int nbb = (bb + 1 < nb) ? bb + 1 : 0;
+          const int npass = (bb + 1 < nb) ? pass : 1;
+          const int b2 = npass == 0 ? nbb : nb - 1 - nbb;
+          prefetch_tile<T, THREADS>(M, L, b2 * TB, min(TB, n - b2 * TB), tile + ((step + 1) & 1) * TB * TB);
+        }
+        Acc part[RPW];
+#pragma unroll
+        for (int u = 0; u < RPW; ++u) part[u] = 0;
+        // panel columns: forward [first envelope column, r0); backward the 64-column tiles right of the
+        // block that reach up to it (U's column envelope)
+        auto panel = [&](int c0, int c1) {
+          const int nv = (c1 - c0) / VW;
+          const V* rowp[RPW];
+#pragma unroll
+          for (int u = 0; u < RPW; ++u)
+            rowp[u] = reinterpret_cast<const V*>(M + (int64_t)(r0 + min(wid + u * WARPS, tb - 1)) * L + c0);
+          int v = lane;
+          for (; v + 32 * (RU - 1) < nv; v += 32 * RU) {
+            V a[RU][RPW];
+#pragma unroll
+            for (int k = 0; k < RU; ++k)
+#pragma unroll
+              for (int u = 0; u < RPW; ++u) a[k][u] = __ldg(rowp[u] + v + 32 * k);
+#pragma unroll
+            for (int k = 0; k < RU; ++k) {
+              const Acc* xv = x + c0 + (v + 32 * k) * VW;
+#pragma unroll
+              for (int u = 0; u < RPW; ++u) part[u] += dot_vec<T, Acc>(a[k][u], xv);
+            }
+          }
+          for (; v < nv; v += 32) {
+            const Acc* xv = x + c0 + v * VW;
+#pragma unroll
+            for (int u = 0; u < RPW; ++u) part[u] += dot_vec<T, Acc>(__ldg(rowp[u] + v), xv);
+          }
+        };
+        if (pass == 0) {
+          const int fs = (tfi[b] / VW) * VW;
+          if (r0 > fs) panel(fs, r0);
+        } else {
+          for (int cb = b + 1; cb < nb; ++cb) {
+            if (tgi[cb] > r0 + tb - 1) continue;
+            const int e0 = cb * TB, e1 = (cb == nb - 1) ? (int)L : e0 + TB;
+            panel(e0, e1);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < RPW; ++u) {
+          Acc p = part[u];
+          for (int sh = 16; sh > 0; sh >>= 1) p += __shfl_xor_sync(0xffffffffu, p, sh);
+          const int r = wid + u * WARPS;
+          if (lane == 0 && r < tb) s[r] = x[r0 + r] - p;
+        }
+        // this step's tile has landed; the next step's (the most recent group) may still be in flight
+        if (step + 1 < 2 * nb) cp_async_wait_but_last();
+        else cp_async_wait_all();
+        __syncthreads();
+        // x[r0 + r] = sum_c Tinv[r][c] s[c] with the unit-lower (forward) or upper (backward) inverse
+#pragma unroll
+        for (int u = 0; u < RPW; ++u) {
+          const int r = wid + u * WARPS;
+          Acc p = 0;
+          if (r < tb) {
+            for (int c = lane; c < tb; c += 32) {
+              const Acc a = (Acc)cur[r * TB + c];
+              if (pass == 0) p += (c < r) ? a * s[c] : (c == r ? s[c] : (Acc)0);
+              else p += (c >= r) ? a * s[c] : (Acc)0;
+            }
+          }
+          for (int sh = 16; sh > 0; sh >>= 1) p += __shfl_xor_sync(0xffffffffu, p, sh);
+          if (lane == 0 && r < tb) x[r0 + r] = p;
+        }
+        __syncthreads();
+      }
+    }
+    if (mode == 0) {
+      const int n_I = nI[i];
+      for (int l = threadIdx.x; l < n_I; l += THREADS) {
+        const int g = idx[o + l];
+        out[g] = (q ? q[g] : 0.0) + (double)x[l];
+      }
+    } else {
+      for (int l = threadIdx.x; l < n; l += THREADS) out[o + l] = (mode == 1 ? D[o + l] : 1.0) * (double)x[l];
+    }
+    __syncthreads();
+  }
+}
+
+template <class T, int THREADS, int RU>
+static void launch_local_solve2(a2ls_handle* h, const T* fac, const double* t, const double* q, double* z, int mode) {
+  using Acc = typename AccOf<T>::type;
+  const size_t smem = 2 * TB * TB * sizeof(T) + sizeof(Acc) * round_up(h->max_n, 4);
+  A2LS_CUDA(cudaFuncSetAttribute(k_local_solve2<T, THREADS, RU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(2 * TB * TB * sizeof(T) + sizeof(Acc) * MAXN_LOCAL)));
+  int per_sm = 1, sms = 152, dev = 0;
+  A2LS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local_solve2<T, THREADS, RU>, THREADS, smem));
+  A2LS_CUDA(cudaGetDevice(&dev));
+  A2LS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = std::max(1, std::min(h->N, sms * std::max(per_sm, 1)));
+  A2LS_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->st));
+  k_local_solve2<T, THREADS, RU><<<grid, THREADS, smem, h->st>>>(
+      h->d_off, h->d_nI, h->d_ni, h->d_ld, h->d_foff, h->d_idx, h->d_D, fac, t, q, z, mode, h->d_sched,
+      h->d_counter, h->N, h->d_toff, h->d_tf, h->d_tg);
+  A2LS_LAUNCH();
+}
+
 template <class T, int THREADS>
 static void launch_local_solve(a2ls_handle* h, const T* fac, const double* t, const double* q, double* z, int mode) {
   using Acc = typename AccOf<T>::type;
@@ -623,12 +871,20 @@ static void launch_local_solve(a2ls_handle* h, const T* fac, const double* t, co
   A2LS_LAUNCH();
 }
 
+// configurations of the local solves the autotuner chooses from: 256 / 512 / 1024 = the one-pass kernel
+// with that CTA width; 1256 / 1512 / 2256 = the pipelined kernel with 256 or 512 threads and two
+// (1xxx) or four (2xxx) vector loads per row in flight
 template <class T>
 static void launch_local_solve_width(a2ls_handle* h, int width, const T* fac, const double* t, const double* q,
                                      double* z, int mode) {
-  if (width == 256) launch_local_solve<T, 256>(h, fac, t, q, z, mode);
-  else if (width == 1024) launch_local_solve<T, 1024>(h, fac, t, q, z, mode);
-  else launch_local_solve<T, 512>(h, fac, t, q, z, mode);
+  switch (width) {
+    case 256: launch_local_solve<T, 256>(h, fac, t, q, z, mode); break;
+    case 1024: launch_local_solve<T, 1024>(h, fac, t, q, z, mode); break;
+    case 1256: launch_local_solve2<T, 256, 2>(h, fac, t, q, z, mode); break;
+    case 1512: launch_local_solve2<T, 512, 2>(h, fac, t, q, z, mode); break;
+    case 2256: launch_local_solve2<T, 256, 4>(h, fac, t, q, z, mode); break;
+    default: launch_local_solve<T, 512>(h, fac, t, q, z, mode); break;
+  }
 }
 
 template <class T>
@@ -650,14 +906,14 @@ void local_solves(a2ls_handle* h, const T* fac, const double* t, const double* q
 template <class T>
 void autotune_local_solves(a2ls_handle* h, const T* fac, const double* t, double* scratch, int mode) {
   char key[128];
-  snprintf(key, sizeof(key), "local_solve_%s_N%d_max%d_mode%d", sizeof(T) == 8 ? "fp64" : "fp32", h->N, h->max_n,
+  snprintf(key, sizeof(key), "local_solve2_%s_N%d_max%d_mode%d", sizeof(T) == 8 ? "fp64" : "fp32", h->N, h->max_n,
            mode);
   int cached = autotune_lookup(key);
   if (cached > 0) {
     h->ls_width = cached;
     return;
   }
-  const int widths[3] = {256, 512, 1024};
+  const int widths[6] = {256, 512, 1024, 1256, 1512, 2256};
   float best_ms = 1e30f;
   int best = 512;
   cudaEvent_t e0, e1;

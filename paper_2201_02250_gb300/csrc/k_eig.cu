@@ -740,13 +740,14 @@ struct RRParams {
 template <class R>
 __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull, const int* nf,
                                 const int* active, const double* H, double* Y, int* ycols, int* zcols,
-                                double* eigout, int* conv, int* st) {
+                                double* eigout, int* conv, double* worst, int* st) {
   extern __shared__ double sm[];
   const int i = blockIdx.x;
   if (active && !active[i]) return;
   if (nf[i] <= 0) {
     if (threadIdx.x == 0) {
       conv[i] = 1;
+      worst[i] = 0.0;
       ycols[i] = 0;
       zcols[i] = 0;
     }
@@ -847,6 +848,8 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
   const int nsel = nsel_s;
   double* Yi = Y + (int64_t)i * EIG_MAXP * EIG_MAXP;
   int conv_all = 1;
+  __shared__ unsigned long long worst_bits;   // largest res / |lambda| of the wanted pairs (>= 0)
+  if (threadIdx.x == 0) worst_bits = 0ull;
   // Schur vectors: one selected eigenvalue per thread (a pair's +imag member is the first of its block)
   if ((int)threadIdx.x < nsel) {
     const int j = threadIdx.x;
@@ -909,6 +912,9 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
     const bool wanted = sel_col[j] < zc_s;
     if (wanted && !(res <= prm.tol * lam)) conv_all = 0;
     if (wanted) {
+      const double ratio = res / lam;
+      // non-negative doubles order like their bit patterns; a NaN or infinite ratio counts as huge
+      atomicMax(&worst_bits, (unsigned long long)__double_as_longlong(ratio < 1e300 ? ratio : 1e300));
       double* eo = eigout + (int64_t)i * prm.nevmax * 2;
       // slot order follows the columns; the kernel part is stored separately by the host
       eo[2 * j] = wr[pidx];
@@ -925,6 +931,7 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
   conv_all = __syncthreads_and(conv_all);
   if (threadIdx.x == 0) {
     conv[i] = conv_all;
+    worst[i] = __longlong_as_double((long long)worst_bits);
     ycols[i] = ncol_s;
     zcols[i] = zc_s;
   }
@@ -1067,6 +1074,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   int* d_nf = dalloc<int>(h, N);
   int* d_active = dalloc<int>(h, N);
   int* d_conv = dalloc<int>(h, N);
+  double* d_worst = dalloc<double>(h, N);
   int* d_ycols = dalloc<int>(h, N);
   int* d_zcols = dalloc<int>(h, N);
   int* d_msb = dalloc<int>(h, N);
@@ -1205,12 +1213,15 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   const int ngroups = h->opt.timing ? 1 : 2;
   RRParams prm{s * b, b, s, tol, nevmax, h->opt.tau};
   const int max_cycles = h->opt.eig_max_cycles > 0 ? h->opt.eig_max_cycles : 60;
-  std::vector<int> cycles(N, 0);
+  const int stall_cycles = h->opt.eig_stall_cycles;
+  std::vector<int> cycles(N, 0), best_cycle(N, 0), stalled(N, 0);
+  std::vector<double> best(N, INFINITY), worst(N, 0.0);
   struct Group {
     std::vector<int> act, actk;
     int* d_act = nullptr;
     int* d_actk = nullptr;
     int* h_conv = nullptr;  // pinned: N flags, then the status words
+    double* h_worst = nullptr;  // pinned: N worst relative residuals of the wanted Ritz pairs
     cudaStream_t s = nullptr;
     cudaEvent_t done = nullptr;
     int cycle = 0;
@@ -1229,6 +1240,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
       for (int q = 0; q < 2; ++q) {
         if (g[q].done) cudaEventDestroy(g[q].done);
         if (g[q].h_conv) cudaFreeHost(g[q].h_conv);
+        if (g[q].h_worst) cudaFreeHost(g[q].h_worst);
       }
       h->st = orig;
     }
@@ -1251,6 +1263,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     G.d_act = dalloc<int>(h, N);
     G.d_actk = dalloc<int>(h, N);
     A2LS_CUDA(cudaMallocHost(&G.h_conv, sizeof(int) * (N + ST_WORDS)));
+    A2LS_CUDA(cudaMallocHost(&G.h_worst, sizeof(double) * N));
     A2LS_CUDA(cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming));
     A2LS_CUDA(cudaMemcpyAsync(G.d_act, G.act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
   }
@@ -1300,11 +1313,12 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
       }
       KTime kt(h, KT_EIG_RR, rr_flops);
       k_rayleigh_ritz<RT><<<N, RR_THREADS, rr_smem, st>>>(prm, d_full, d_mfull, d_nf, G.d_act, H, Y, d_ycols, d_zcols,
-                                              eigout, d_conv, h->d_status);
+                                              eigout, d_conv, d_worst, h->d_status);
       A2LS_LAUNCH();
     }
     A2LS_CUDA(cudaMemcpyAsync(G.h_conv, d_conv, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
     A2LS_CUDA(cudaMemcpyAsync(G.h_conv + N, h->d_status, sizeof(int) * ST_WORDS, cudaMemcpyDeviceToHost, st));
+    A2LS_CUDA(cudaMemcpyAsync(G.h_worst, d_worst, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     A2LS_CUDA(cudaEventRecord(G.done, st));
   };
   for (int g = 0; g < ngroups; ++g) queue_cycle(g);
@@ -1319,8 +1333,23 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
       for (int i = g; i < N; i += ngroups) {
         if (G.act[i]) {
           cycles[i] = G.cycle + 1;
-          if (G.h_conv[i] || full[i]) G.act[i] = 0;
-          else ++remaining;
+          const double w = G.h_worst[i];
+          worst[i] = w;
+          if (G.h_conv[i] || full[i]) {
+            G.act[i] = 0;
+            continue;
+          }
+          // stagnation stop: a subdomain whose worst wanted residual has not halved over the last
+          // eig_stall_cycles cycles keeps the Ritz vectors it has (still a valid coarse space)
+          if (w < 0.5 * best[i]) {
+            best[i] = w;
+            best_cycle[i] = G.cycle;
+          } else if (stall_cycles > 0 && G.cycle - best_cycle[i] >= stall_cycles) {
+            G.act[i] = 0;
+            stalled[i] = 1;
+            continue;
+          }
+          ++remaining;
         }
       }
       // after the last cycle V and Y stay as they are: the unconverged subdomains keep their Ritz vectors
@@ -1353,12 +1382,18 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     dfree(h, grp[g].d_act);
     dfree(h, grp[g].d_actk);
   }
-  int unconverged = 0;
-  for (int i = 0; i < N; ++i) unconverged += act[i];
+  int unconverged = 0, nstalled = 0;
+  for (int i = 0; i < N; ++i) {
+    unconverged += act[i] || stalled[i];
+    nstalled += stalled[i];
+  }
   h->eig_unconverged = unconverged;
+  h->eig_stalled = nstalled;
+  h->h_eigres = worst;
   if (unconverged && h->opt.eig_strict)
-    fail(A2LS_ERR_EIGEN, "local eigensolve did not reach tolerance %.1e in %d cycles for %d subdomains", tol,
-         max_cycles, unconverged);
+    fail(A2LS_ERR_EIGEN,
+         "local eigensolve did not reach tolerance %.1e for %d subdomains (%d stagnated, the others ran %d cycles)",
+         tol, unconverged, nstalled, max_cycles);
 
   // --- final coarse vectors: Z = [k | V Y[:, 0:zc]] ------------------------------------------
   for (int i = 0; i < N; ++i) act[i] = nf[i] > 0 ? 1 : 0;

@@ -1,0 +1,207 @@
+// Double-float tile products on the tensor cores: C(128 x 64) -= A(128 x 64) B(64 x 64), where A, B
+// and C hold double-float values, computed with BF16 x BF16 -> FP32 tcgen05 MMAs.
+//
+// Method (an error-free splitting in the manner of Ozaki, Ogita, Oishi and Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 2012): every row of A is scaled by a power of two 2^eA_r >= its
+// largest magnitude, every column of B by 2^eB_c, and each scaled value y in [-1, 1] is written as six
+// base-256 digits, y = sum_s t_s 256^-(s+1) with integers |t_0| <= 256, |t_s| <= 128 (s > 0), obtained by
+// repeated rounding to the nearest integer (each step is exact in double-float arithmetic).  Digit s
+// is stored as the BF16 value t_s 2^(-8 s), which is exact (at most 8 significant bits).  The product
+// of digit i of A and digit j of B then has the natural weight 2^(-8 (i + j)), and the 21 digit pairs
+// with i + j <= 5 are accumulated by the tensor cores in five FP32 accumulators, one for each weight
+// 0..3 and one for the weights 4 and 5 together.  Over 64 terms the sums of weight 0..3 stay below
+// 2^24 units of their weight, so FP32 accumulates them exactly whatever the order; only the last
+// accumulator rounds, at a relative level of 2^-56.  The result, 2^(eA_r + eB_c - 16) times the sum
+// of the accumulators, is formed in double-float; its error is about 2^-45 of (|A| |B|)_rc, that of a
+// double-float tile product.
+//
+// Shared memory: A digits 6 x 16 KiB, B digits 6 x 8 KiB (144 KiB), K-major canonical layout
+// (tc_sm100.cuh).  TMEM: 5 accumulators x 64 columns (512 columns allocated: one CTA per SM).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "dfloat.cuh"
+#include "tc_sm100.cuh"
+
+namespace a2ls {
+namespace tcdf {
+
+constexpr int TM = 128, TN = 64, TK = 64;   // tile shape
+constexpr int NDIG = 6;                      // base-256 digits per value
+constexpr int NACC = 5;                      // accumulators: weights 0, 1, 2, 3 and {4, 5}
+constexpr uint32_t A_DIGIT_BYTES = TM * TK * 2;
+constexpr uint32_t B_DIGIT_BYTES = TN * TK * 2;
+constexpr size_t SMEM_BYTES = (size_t)NDIG * (A_DIGIT_BYTES + B_DIGIT_BYTES);   // 147456
+constexpr uint32_t TMEM_COLS = 512;
+constexpr long WAIT_LIMIT = 1L << 26;        // polls of the completion barrier before giving up
+
+// the six digits of y = x / 2^e (|y| <= 1), as BF16 values t_s 2^(-8 s)
+__device__ __forceinline__ void df_digits(dfloat x, int e, __nv_bfloat16 (&d)[NDIG]) {
+  float yh = ldexpf(x.hi, -e), yl = ldexpf(x.lo, -e);
+#pragma unroll
+  for (int s = 0; s < NDIG; ++s) {
+    const float t = rintf(__fmul_rn(yh, 256.f));
+    d[s] = __float2bfloat16_rn(ldexpf(t, -8 * s));
+    // y <- 256 y - t: exact (256 y is exact and t is within one half of it)
+    yh = __fsub_rn(__fmul_rn(yh, 256.f), t);
+    yl = __fmul_rn(yl, 256.f);
+    const dfloat r = df_two_sum(yh, yl);
+    yh = r.hi;
+    yl = r.lo;
+  }
+}
+
+// exponent e with |v| < 2^e (0 for v = 0)
+__device__ __forceinline__ int scale_exponent(float maxabs) {
+  int e = 0;
+  if (maxabs > 0.f) frexpf(maxabs, &e);
+  return e;
+}
+
+struct Ctx {
+  unsigned char* smem;   // SMEM_BYTES, 16-byte aligned
+  uint64_t* bar;         // completion mbarrier (initialised with count 1)
+  uint32_t tmem;         // TMEM base address (TMEM_COLS columns)
+  uint32_t phase;        // parity of the next completion
+  int* eA;               // shared, TM row exponents
+  int* eB;               // shared, TN column exponents
+};
+
+// A digits: rows [0, TM) x k [0, TK) of A(m, k) = fa(m, k) (zero outside), 256 threads: two per row.
+template <class FA>
+__device__ __forceinline__ void split_a(Ctx& c, FA fa) {
+  const int tid = threadIdx.x, r = tid >> 1, h = tid & 1;
+  dfloat v[32];
+  float mx = 0.f;
+#pragma unroll
+  for (int q = 0; q < 32; ++q) {
+    v[q] = fa(r, h * 32 + q);
+    mx = fmaxf(mx, fabsf(v[q].hi));
+  }
+  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+  const int e = scale_exponent(mx);
+  if (h == 0) c.eA[r] = e;
+#pragma unroll
+  for (int q8 = 0; q8 < 4; ++q8) {
+    __nv_bfloat16 dg[8][NDIG];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) df_digits(v[q8 * 8 + q], e, dg[q]);
+    const uint32_t off = tc::operand_offset(r, h * 32 + q8 * 8, TK);
+#pragma unroll
+    for (int s = 0; s < NDIG; ++s) {
+      __nv_bfloat162 p0 = __halves2bfloat162(dg[0][s], dg[1][s]), p1 = __halves2bfloat162(dg[2][s], dg[3][s]),
+                     p2 = __halves2bfloat162(dg[4][s], dg[5][s]), p3 = __halves2bfloat162(dg[6][s], dg[7][s]);
+      uint4 w;
+      w.x = *reinterpret_cast<uint32_t*>(&p0);
+      w.y = *reinterpret_cast<uint32_t*>(&p1);
+      w.z = *reinterpret_cast<uint32_t*>(&p2);
+      w.w = *reinterpret_cast<uint32_t*>(&p3);
+      *reinterpret_cast<uint4*>(c.smem + s * A_DIGIT_BYTES + off) = w;
+    }
+  }
+}
+
+// B digits: k [0, TK) x columns [0, TN) of B(k, n) = fb(k, n), stored as the K-major operand (n, k);
+// 256 threads: column n = tid % 64, k quarter tid / 64.  red: shared scratch of 4 x TN floats.
+template <class FB>
+__device__ __forceinline__ void split_b(Ctx& c, FB fb, float* red) {
+  const int tid = threadIdx.x, n = tid & (TN - 1), qk = tid >> 6;
+  dfloat v[16];
+  float mx = 0.f;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    v[q] = fb(qk * 16 + q, n);
+    mx = fmaxf(mx, fabsf(v[q].hi));
+  }
+  red[qk * TN + n] = mx;
+  __syncthreads();
+  mx = fmaxf(fmaxf(red[n], red[TN + n]), fmaxf(red[2 * TN + n], red[3 * TN + n]));
+  const int e = scale_exponent(mx);
+  if (qk == 0) c.eB[n] = e;
+#pragma unroll
+  for (int q8 = 0; q8 < 2; ++q8) {
+    __nv_bfloat16 dg[8][NDIG];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) df_digits(v[q8 * 8 + q], e, dg[q]);
+    const uint32_t off = tc::operand_offset(n, qk * 16 + q8 * 8, TK);
+#pragma unroll
+    for (int s = 0; s < NDIG; ++s) {
+      __nv_bfloat162 p0 = __halves2bfloat162(dg[0][s], dg[1][s]), p1 = __halves2bfloat162(dg[2][s], dg[3][s]),
+                     p2 = __halves2bfloat162(dg[4][s], dg[5][s]), p3 = __halves2bfloat162(dg[6][s], dg[7][s]);
+      uint4 w;
+      w.x = *reinterpret_cast<uint32_t*>(&p0);
+      w.y = *reinterpret_cast<uint32_t*>(&p1);
+      w.z = *reinterpret_cast<uint32_t*>(&p2);
+      w.w = *reinterpret_cast<uint32_t*>(&p3);
+      *reinterpret_cast<uint4*>(c.smem + NDIG * A_DIGIT_BYTES + s * B_DIGIT_BYTES + off) = w;
+    }
+  }
+}
+
+// After split_a / split_b by all threads: the 84 MMAs of the 21 digit pairs, issued by thread 0, then
+// a bounded wait by every thread.  Returns false (on every thread) if the products did not complete.
+__device__ __forceinline__ bool multiply(Ctx& c) {
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x == 0) {
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(TM, TN);
+    const uint32_t a0 = tc::smem_u32(c.smem), b0 = a0 + NDIG * A_DIGIT_BYTES;
+    uint32_t started = 0;   // bit g: accumulator g already written in this tile
+#pragma unroll 1
+    for (int i = 0; i < NDIG; ++i)
+#pragma unroll 1
+      for (int j = 0; i + j < NDIG; ++j) {
+        const int g = min(i + j, NACC - 1);
+#pragma unroll
+        for (int kk = 0; kk < TK / 16; ++kk) {
+          const uint64_t ad = tc::smem_desc(a0 + i * A_DIGIT_BYTES + kk * 256, 128, TK * 16);
+          const uint64_t bd = tc::smem_desc(b0 + j * B_DIGIT_BYTES + kk * 256, 128, TK * 16);
+          tc::mma_bf16(c.tmem + g * TN, ad, bd, idesc, (started >> g) & 1u);
+          started |= 1u << g;
+        }
+      }
+    tc::commit(c.bar);
+  }
+  __syncwarp();
+  const bool ok = tc::mbar_wait_bounded(c.bar, c.phase, WAIT_LIMIT);
+  c.phase ^= 1u;
+  tc::fence_after_sync();
+  return __syncthreads_and(ok) != 0;
+}
+
+// The tile result for this thread's 32 outputs, handed to out(m, n, value) per element: warp w reads
+// TMEM lanes (rows) 32 (w % 4) .. + 31 and columns 32 (w / 4) .. + 31.  Ends with the fences and
+// barrier that let the next tile reuse TMEM and shared memory.
+template <class OUT>
+__device__ __forceinline__ void epilogue(Ctx& c, OUT out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = (warp & 3) * 32 + lane, n0 = (warp >> 2) * 32;
+  const uint32_t lane_addr = c.tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  const int em = c.eA[m];
+#pragma unroll 1
+  for (int cb = 0; cb < 32; cb += 8) {
+    float acc[NACC][8];
+#pragma unroll
+    for (int g = 0; g < NACC; ++g) tc::tmem_ld8(lane_addr + g * TN + n0 + cb, acc[g]);
+    tc::tmem_wait_ld();
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      // exact sum of the first two accumulators, then the smaller ones in decreasing weight
+      dfloat s = df_two_sum(acc[0][q], acc[1][q]);
+      s = s + dfloat(acc[2][q], 0.f);
+      s = s + dfloat(acc[3][q], 0.f);
+      s = s + dfloat(acc[4][q], 0.f);
+      const int e = em + c.eB[n0 + cb + q] - 16;
+      out(m, n0 + cb + q, dfloat(ldexpf(s.hi, e), ldexpf(s.lo, e)));
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+}
+
+}  // namespace tcdf
+}  // namespace a2ls

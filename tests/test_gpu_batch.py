@@ -145,3 +145,25 @@ def test_memory_pool_keeps_and_trims_blocks():
     assert ok and true <= 1e-8
     P.close()
     mod.trim_memory()
+
+
+def test_stagnation_stop_ends_unreachable_eigensolves():
+    """An eigen-residual target below what the arithmetic reaches: with the stagnation stop the
+    subdomains stop once their worst wanted residual has not halved over eig_stall_cycles cycles,
+    long before eig_max_cycles, and keep their Ritz vectors; without it they run every cycle."""
+    prob = pde.tiny_conv_diff(m=40, nb=3, overlap=2, nev=6)
+    mod = a2ls()
+    P = mod.setup_batch([_tensors(prob)], eig_tol=1e-17, eig_stall_cycles=4, eig_max_cycles=60)[0]
+    cycles = P.eig_stats()[:, 0]
+    res = P.eig_residuals()
+    assert P.eig_stalled() == P.eig_unconverged() > 0
+    assert cycles.max() < 60
+    assert np.all(np.isfinite(res)) and np.all(res >= 0) and res.max() < 1e-8
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    it, rr, ok = P.solve(torch.as_tensor(prob.b, device="cuda"), x, 1e-8)
+    assert ok
+    P.close()
+    P0 = mod.setup_batch([_tensors(prob)], eig_tol=1e-17, eig_stall_cycles=0, eig_max_cycles=12)[0]
+    assert P0.eig_stalled() == 0 and P0.eig_unconverged() > 0
+    assert P0.eig_stats()[:, 0].max() == 12
+    P0.close()

@@ -1,0 +1,246 @@
+"""Full-size parity against the oracle at the two large workloads.
+
+* 2D high-contrast diffusion, 512 x 512 (n = 262144, 256 subdomains, overlap 2, nev 16): the
+  oracle's own coarse space from its oracle-fast local eigensolve (Arnoldi on the inverted pencil of
+  Eqs. 3.1-3.2, pinned against dense QZ in test_oracle_fast) for all 256 subdomains, and the oracle's
+  LU-factored local matrices, give the oracle's preconditioner of Eq. 2.4.  With that coarse basis
+  injected into the GPU preconditioner, the apply is compared element by element and GMRES counts
+  within +-1.  The GPU's own coarse space is compared with the oracle's by subspace angles on 16
+  sampled subdomains where the eigenvalue gap at the cut is at least 1 %.
+* 3D convection-diffusion, 96^3 (n = 884736, 512 uneven subdomains, overlap 1, nev 12): index lists,
+  lumped sums and coarse-space angles on 16 sampled subdomains; the apply on the interiors of the
+  sampled subdomains with an injected seeded coarse basis (any basis exercises the same code path),
+  computed one subdomain at a time by the oracle; GMRES to a true relative residual of 1e-8.
+
+Element-wise tolerance of the apply (derived, not fitted): on an interior node of subdomain i the
+apply is q + (A_ii^{-1} t)_l with t = r - A q.  A backward-stable local solve in unit roundoff u has a
+forward error below c n_i u kappa_inf(A_ii) ||y_i||_inf, so each node is held to
+    |z_gpu - z_or| <= 8 n_i u kappa_inf(A_ii) ||y_i||_inf + 8 n0 u kappa_inf(A_00) ||q||_inf,
+with kappa from LAPACK's condition estimate of the oracle's own factors (u = 2^-53 for FP64 factors,
+2^-24 for FP32 factors).
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import a2ls_oracle as O
+from workloads import pde
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+WORKERS = max(1, min(16, (os.cpu_count() or 2) - 1))
+U64, U32 = 2.0 ** -53, 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("CUDA device required")
+    from paper_2201_02250_gb300 import _build
+    _build.build()
+
+
+def a2ls():
+    from paper_2201_02250_gb300 import a2ls as mod
+    return mod
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda")
+
+
+def apply_gpu(P, r):
+    z = torch.empty(len(r), dtype=torch.float64, device="cuda")
+    P.apply(dev(r), z)
+    torch.cuda.synchronize()
+    return z.cpu().numpy()
+
+
+def sin_angle(U, V):
+    Qu = np.linalg.qr(U)[0]
+    Qv = np.linalg.qr(V)[0]
+    return np.linalg.norm(Qv - Qu @ (Qu.T @ Qv), 2)
+
+
+def kappa_inf(lu, A):
+    """LAPACK's estimate of the infinity-norm condition number from an LU factorisation."""
+    rc, info = sla.lapack.dgecon(lu[0], np.linalg.norm(A, np.inf), norm="I")
+    return 1.0 / max(rc, 1e-300)
+
+
+def gap_ok(eigvals, m):
+    """|lambda_m| / |lambda_{m+1}| >= 1.01 at the cut after m finite eigenvalues."""
+    a = np.abs(eigvals)
+    return len(a) > m and (m == 0 or a[m - 1] >= 1.01 * a[m])
+
+
+# ---------------------------------------------------------------------------
+# 2D high-contrast diffusion, 512 x 512
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def c2_oracle():
+    prob = pde.config_c2()
+    subs = O.overlapping_subdomains(prob.A, prob.part, prob.overlap)
+    D = O.partition_of_unity(subs, prob.n)
+    eig = O.local_eigen_fast_many(prob.A, subs, D, prob.nev, range(len(subs)), workers=WORKERS)
+    W = [O.orthonormal_columns(d[:, None] * e.Z) for d, e in zip(D, eig)]
+    lus, kap = [], []
+    for s in subs:
+        a = O.local_matrix(prob.A, s)
+        lus.append(sla.lu_factor(a))
+        kap.append(kappa_inf(lus[-1], a))
+    kap = np.array(kap)
+    P = O.Preconditioner(A=prob.A.tocsr(), subs=subs, D=D, local_lu=lus,
+                         coarse=O.coarse_space_from_W(prob.A, subs, W), eig=eig)
+    kE = kappa_inf(P.coarse.E_lu, P.coarse.E)
+    return prob, subs, D, eig, W, P, kap, kE
+
+
+def elementwise_bound(P, subs, kap, kE, r, u):
+    q = O.coarse_correction(P, r)
+    t = r - P.A @ q
+    bound = np.zeros(P.n)
+    n0 = P.coarse.n0
+    for s, lu, k in zip(subs, P.local_lu, kap):
+        y = sla.lu_solve(lu, t[s.idx])
+        bound[s.interior] = 8 * s.n_i * u * k * np.abs(y).max()
+    return bound + 8 * n0 * U64 * kE * np.abs(q).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_c2_apply_elementwise_and_gmres_with_oracle_coarse_space(c2_oracle, precision):
+    prob, subs, D, eig, W, Por, kap, kE = c2_oracle
+    P, _keep = a2ls().from_scipy(prob.A, prob.part, prob.overlap, prob.nev, precision=precision)
+    P.set_coarse_basis(W)
+    rng = np.random.Generator(np.random.PCG64(22))
+    u = U64 if precision == "fp64" else U32
+    for _ in range(2):
+        r = rng.uniform(-1.0, 1.0, prob.n)
+        z = apply_gpu(P, r)
+        zo = O.apply(Por, r)
+        bound = elementwise_bound(Por, subs, kap, kE, r, u)
+        err = np.abs(z - zo)
+        print(f"c2 {precision}: max err {err.max():.3e}, max err/bound {np.max(err / bound):.3e}, "
+              f"normwise {np.linalg.norm(z - zo) / np.linalg.norm(zo):.3e}")
+        assert np.all(err <= bound)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    it, rr, ok = P.solve(dev(prob.b), x, 1e-8)
+    res = O.gmres(prob.A, lambda v: O.apply(Por, v), prob.b, rtol=1e-8)
+    true = np.linalg.norm(prob.b - prob.A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
+    print(f"c2 {precision}: GMRES {it} (oracle {res.iters}), true relres {true:.2e}")
+    assert ok and true <= 1e-8 and res.converged
+    assert abs(it - res.iters) <= 1
+    P.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_c2_coarse_space_matches_oracle(c2_oracle, precision):
+    prob, subs, D, eig, W, Por, kap, kE = c2_oracle
+    P, _keep = a2ls().from_scipy(prob.A, prob.part, prob.overlap, prob.nev, precision=precision)
+    Wg = P.coarse_basis()
+    evg = P.eigenvalues()
+    # FP64 eigensolve to an eigen-residual of 1e-10; the mixed form's double-float one to 1e-4
+    tol = 1e-6 if precision == "fp64" else 1e-2
+    checked = 0
+    worst = 0.0
+    for i in range(0, len(subs), 16):
+        e = eig[i]
+        m = len(e.selected)
+        if not gap_ok(e.eigvals, m) or Wg[i].shape[1] != W[i].shape[1]:
+            continue
+        s = sin_angle(W[i], Wg[i])
+        worst = max(worst, s)
+        assert s < tol, (i, s)
+        lam_g = np.sort(np.abs(evg[i][np.isfinite(evg[i])]))[::-1]
+        lam_o = np.sort(np.abs(e.selected))[::-1]
+        assert len(lam_g) == len(lam_o)
+        np.testing.assert_allclose(lam_g, lam_o,
+                                   rtol=1e-8 if precision == "fp64" else 1e-3)
+        checked += 1
+    print(f"c2 {precision}: {checked} sampled subdomains, largest sine {worst:.2e}")
+    assert checked >= 12
+    P.close()
+
+
+# ---------------------------------------------------------------------------
+# 3D convection-diffusion, 96^3, 512 uneven subdomains
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def c3_oracle():
+    prob = pde.config_c3()
+    subs = O.overlapping_subdomains(prob.A, prob.part, prob.overlap)
+    D = O.partition_of_unity(subs, prob.n)
+    sizes = np.array([s.n_i for s in subs])
+    # 16 samples: the largest, the smallest and 14 spread over the size order
+    order = np.argsort(sizes)
+    sample = sorted(set(int(order[k]) for k in np.linspace(0, len(subs) - 1, 16).round().astype(int)))
+    eig = dict(zip(sample, O.local_eigen_fast_many(prob.A, subs, D, prob.nev, sample, workers=WORKERS)))
+    return prob, subs, D, sample, eig
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_c3_full_size(c3_oracle, precision):
+    prob, subs, D, sample, eig = c3_oracle
+    P, _keep = a2ls().from_scipy(prob.A, prob.part, prob.overlap, prob.nev, precision=precision)
+    sz = P.sizes()
+    assert sz["N"] == 512 and sz["max_ni"] == max(s.n_i for s in subs)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    it, rr, ok = P.solve(dev(prob.b), x, 1e-8)
+    true = np.linalg.norm(prob.b - prob.A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
+    print(f"c3 {precision}: GMRES {it}, true relres {true:.2e}, unconverged eigensolves {P.eig_unconverged()}")
+    assert ok and true <= 1e-8 and it <= 60
+    subs_gpu = P.subdomains()
+    lumps = P.lump()
+    Wg = P.coarse_basis()
+    tol = 1e-6 if precision == "fp64" else 1e-2
+    checked = 0
+    for i in sample:
+        s = subs[i]
+        np.testing.assert_array_equal(subs_gpu[i][0], s.interior)
+        np.testing.assert_array_equal(subs_gpu[i][1], s.gamma)
+        np.testing.assert_allclose(lumps[i][s.n_I:], O.lumped_row_sums(prob.A, s), rtol=1e-14)
+        e = eig[i]
+        m = e.Z.shape[1]
+        if gap_ok(e.eigvals, len(e.selected)) and Wg[i].shape[1] == m:
+            sn = sin_angle(O.orthonormal_columns(D[i][:, None] * e.Z), Wg[i])
+            assert sn < tol, (i, sn)
+            checked += 1
+    print(f"c3 {precision}: coarse spaces compared on {checked} of {len(sample)} sampled subdomains")
+    assert checked >= 8
+    P.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_c3_apply_on_sampled_subdomains(c3_oracle, precision):
+    """Eq. 2.4 with a seeded coarse basis (4 columns per subdomain, W_i = orth(D_i G_i)) injected into
+    both sides; the oracle evaluates z on the interiors of the sampled subdomains one at a time."""
+    prob, subs, D, sample, eig = c3_oracle
+    rng = np.random.Generator(np.random.PCG64(33))
+    W = [O.orthonormal_columns(d[:, None] * rng.uniform(-1.0, 1.0, (s.n_i, 4))) for s, d in zip(subs, D)]
+    P, _keep = a2ls().from_scipy(prob.A, prob.part, prob.overlap, prob.nev, precision=precision,
+                                 eig_max_cycles=1, eig_tol=1.0)
+    P.set_coarse_basis(W)
+    cs = O.coarse_space_from_W(prob.A, subs, W)
+    kE = kappa_inf(cs.E_lu, cs.E)
+    r = rng.uniform(-1.0, 1.0, prob.n)
+    z = apply_gpu(P, r)
+    g = cs.Phi.T @ r
+    q = cs.Phi @ sla.lu_solve(cs.E_lu, g)
+    t = r - prob.A @ q
+    u = U64 if precision == "fp64" else U32
+    worst = 0.0
+    for i in sample:
+        s = subs[i]
+        Aii = O.local_matrix(prob.A, s)
+        lu = sla.lu_factor(Aii)
+        y = sla.lu_solve(lu, t[s.idx])
+        zo = q[s.interior] + y[:s.n_I]
+        bound = 8 * s.n_i * u * kappa_inf(lu, Aii) * np.abs(y).max() + 8 * cs.n0 * U64 * kE * np.abs(q).max()
+        err = np.abs(z[s.interior] - zo)
+        worst = max(worst, float(np.max(err / bound)))
+        assert np.all(err <= bound), (i, err.max(), bound)
+    print(f"c3 {precision}: apply on {len(sample)} sampled interiors, max err/bound {worst:.2e}")
+    P.close()
