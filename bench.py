@@ -357,6 +357,7 @@ def run_ours(args, rank: int, world: int, device):
         return e0.elapsed_time(e1) / reps
 
     kt_before = P.kernel_times()
+    tuning = P.tuning()["local_solve_threads"]
     apply_ms_mixed = time_apply(P)
     kt_after = P.kernel_times()
     ab_mixed = apply_bytes(P, prob, 4)
@@ -410,7 +411,7 @@ def run_ours(args, rank: int, world: int, device):
         "apply_ms_mixed": apply_ms_mixed, "apply_ms_plain": apply_ms_plain, "ab_mixed": ab_mixed,
         "ab_plain": ab_plain, "plain_tol": plain_tol, "loc_ms": loc_ms, "e2e_ms": e2e_ms, "h2d": h2d, "d2h": prob.n * 8,
         "clocks": clocks.summary(), "true_relres": true_relres, "dominant": dom, "kern": kern,
-        "hbm_peak": hbm_peak, "info64": info64,
+        "hbm_peak": hbm_peak, "info64": info64, "tuning": tuning,
     }
 
 
@@ -498,7 +499,7 @@ def report(args, res, world) -> dict:
                   "gbs": round(res["ab_mixed"]["apply"] / (res["apply_ms_mixed"] * 1e-3) / 1e9, 1),
                   "local_solve_kernel_ms": round(res["loc_ms"], 4), "local_solve_kernel_gbs": round(apply_local_gbs, 1),
                   "frac_of_measured_hbm": apply_local_gbs / res["hbm_peak"] if res["hbm_peak"] else None,
-                  "bytes": res["ab_mixed"]["apply"]},
+                  "bytes": res["ab_mixed"]["apply"], "local_solve_config": res["tuning"]},
         "roofline": roof,
         "dtype": ("f32 local factors and solves; f32x2 (double-float) splitting LU (trailing update as BF16 digit "
                   "products on tcgen05), eigensolves and coarse factorisation; f64 GMRES, SpMV, coarse apply"),

@@ -59,8 +59,11 @@ typedef enum {
  * forms the explicit inverse of the coarse operator from its FP64 factors in
  * double-float.
  * A2LS_FP32X2 (eigensolve only) is double-float arithmetic: each value is an unevaluated sum
- * of two FP32 numbers (48-bit significand, FP32 exponent range), computed on the FP32 pipe. */
-enum { A2LS_FP64 = 0, A2LS_FP32 = 1, A2LS_FP32X2 = 2 };
+ * of two FP32 numbers (48-bit significand, FP32 exponent range), computed on the FP32 pipe.
+ * A2LS_BF16 (local factors only) factors A_ii in FP32 as A2LS_FP32 does and stores the factors in
+ * bfloat16 (8-bit significand, half the bytes of the apply's dominant stream); the local solves read
+ * them and accumulate in FP32, and flexible GMRES absorbs the rounding of the stored factors. */
+enum { A2LS_FP64 = 0, A2LS_FP32 = 1, A2LS_FP32X2 = 2, A2LS_BF16 = 3 };
 
 /* Preconditioner variants (Section 2).  DEFLATED_RAS is Eq. 2.4, the one the
  * paper uses in all experiments. */
@@ -98,7 +101,7 @@ typedef struct {
 } a2ls_csr;
 
 typedef struct {
-  int32_t precision;        /* A2LS_FP64 (default) or A2LS_FP32 */
+  int32_t precision;        /* A2LS_FP64 (default), A2LS_FP32 or A2LS_BF16 */
   int32_t variant;          /* A2LS_DEFLATED_RAS (default) ... */
   int32_t pou;              /* A2LS_POU_BOOLEAN (default) or A2LS_POU_MULTIPLICITY */
   int32_t restart;          /* GMRES restart length, default 30 (Section 4) */
@@ -197,7 +200,7 @@ enum {
                             indices (each subdomain: Omega_Ii ascending, then Omega_Gamma_i layer by
                             layer: the nodes of the first overlap step ascending, then the second's, ...) */
   A2LS_Q_LUMP = 2,       /* double[sum n_i]: s_i of Definition 3.1 on overlap rows, 0 on interior rows */
-  A2LS_Q_FACTORS = 3,    /* (precision type)[sum over i of n_i*ld_i] then int64[N+1] offsets and
+  A2LS_Q_FACTORS = 3,    /* (precision type: double, float or bfloat16)[sum over i of n_i*ld_i] then int64[N+1] offsets and
                             int32[N] ld: LU of A_ii without pivoting, row-major, unit-lower L below
                             the diagonal; each 64x64 diagonal tile holds inv(L_bb) strictly below
                             its diagonal and inv(U_bb) on and above it */

@@ -16,7 +16,7 @@ from . import _build
 
 A2LS_OK, A2LS_ERR_ARG, A2LS_ERR_SINGULAR, A2LS_ERR_NOT_CONVERGED = 0, 1, 2, 3
 A2LS_ERR_EIGEN, A2LS_ERR_TIMEOUT, A2LS_ERR_CUDA, A2LS_ERR_OOM, A2LS_ERR_STATE = 4, 5, 6, 7, 8
-FP64, FP32, FP32X2 = 0, 1, 2
+FP64, FP32, FP32X2, BF16 = 0, 1, 2, 3
 VARIANTS = {"deflated_ras": 0, "deflated_asm": 1, "additive_ras": 2, "additive_asm": 3, "ras": 4, "asm": 5}
 POU = {"boolean": 0, "multiplicity": 1}
 (Q_SIZES, Q_SUBDOMAINS, Q_LUMP, Q_FACTORS, Q_COARSE, Q_EIGVALS, Q_TIMES, Q_EINV, Q_EIGSTATS, Q_LAUNCHES,
@@ -132,7 +132,7 @@ def default_options(**kw) -> Options:
         if k == "pou" and isinstance(v, str):
             v = POU[v]
         if k in ("precision", "eig_precision") and isinstance(v, str):
-            v = {"fp64": FP64, "fp32": FP32, "fp32x2": FP32X2}[v]
+            v = {"fp64": FP64, "fp32": FP32, "fp32x2": FP32X2, "bf16": BF16}[v]
         if k == "warm_start":
             v = None if v is None else v._g.value
         setattr(o, k, v)
@@ -239,9 +239,12 @@ class Preconditioner:
         sz = self.sizes()
         N = sz["N"]
         raw = self._query(Q_FACTORS)
-        es = 8 if sz["precision"] == FP64 else 4
         tail = (N + 1) * 8 + N * 4
-        vals = np.frombuffer(raw[:len(raw) - tail], dtype=np.float64 if es == 8 else np.float32)
+        if sz["precision"] == BF16:   # bfloat16: the upper half of an FP32 value
+            bits = np.frombuffer(raw[:len(raw) - tail], dtype=np.uint16).astype(np.uint32) << 16
+            vals = bits.view(np.float32)
+        else:
+            vals = np.frombuffer(raw[:len(raw) - tail], dtype=np.float64 if sz["precision"] == FP64 else np.float32)
         foff = np.frombuffer(raw[len(raw) - tail:len(raw) - N * 4], dtype=np.int64)
         ld = np.frombuffer(raw[len(raw) - N * 4:], dtype=np.int32)
         subs = self.subdomains()

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "../../include/a2ls.h"
 #include "dfloat.cuh"
 
@@ -195,8 +197,29 @@ template <class T> void autotune_local_solves(a2ls_handle* h, const T* fac, cons
 int autotune_lookup(const char* key);            // 0 if unknown
 void autotune_store(const char* key, int value);
 void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv, int band);
+// skip_p_le > 0: subdomains with at most that many columns are left to another kernel
 template <class T> void block_solve(a2ls_handle* h, const T* fac, T* X, const int64_t* xoff, int col0, int ldx,
-                                    const int* pvec, int pmax, const int* active, int forward, int backward);
+                                    const int* pvec, int pmax, const int* active, int forward, int backward,
+                                    int skip_p_le = 0);
+
+// k_tcsolve.cu: double-float block triangular solves of the eigensolver on the tensor cores
+struct TcSolve {
+  bool ready = false;
+  int64_t ntiles = 0;
+  int64_t *d_ftoff = nullptr, *d_ftab = nullptr, *d_xdoff = nullptr;
+  unsigned char *d_fdig = nullptr, *d_xdig = nullptr;
+};
+void tc_solve_prepare(a2ls_handle* h, const dfloat* fac, TcSolve& ts);   // digits of the factor tiles
+void tc_solve_release(a2ls_handle* h, TcSolve& ts);
+// one sweep over the subdomains with 1 <= p <= 32 columns (forward: inv(L), else inv(U))
+void tc_block_solve(a2ls_handle* h, const TcSolve& ts, dfloat* X, const int64_t* xoff, int col0, int ldx,
+                    const int* pvec, const int* active, int forward, unsigned char* xdig = nullptr);
+constexpr int TC_SOLVE_MAX_P = 32;
+
+// k_dense.cu: FP32 local factors rounded to the bfloat16 storage of A2LS_BF16 (fac_elems values)
+void factors_to_bf16(a2ls_handle* h, const float* src, __nv_bfloat16* dst);
+// the apply's local solves with the handle's factor type
+void local_solves_any(a2ls_handle* h, const double* t, const double* q, double* z, int mode);
 
 // k_static.cu: loads the module of a2ls_apply_static's static scratch on the current device
 void prime_static_scratch();

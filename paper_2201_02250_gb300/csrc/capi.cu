@@ -396,7 +396,8 @@ int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int
     if (nev < 0) fail(A2LS_ERR_ARG, "nev must be >= 0");
     a2ls_options o;
     if (opt) o = *opt; else a2ls_default_options(&o);
-    if (o.precision != A2LS_FP64 && o.precision != A2LS_FP32) fail(A2LS_ERR_ARG, "unknown precision %d", o.precision);
+    if (o.precision != A2LS_FP64 && o.precision != A2LS_FP32 && o.precision != A2LS_BF16)
+      fail(A2LS_ERR_ARG, "unknown precision %d", o.precision);
     if (o.variant < 0 || o.variant > A2LS_ONE_LEVEL_ASM) fail(A2LS_ERR_ARG, "unknown variant %d", o.variant);
     if (o.pou != A2LS_POU_BOOLEAN && o.pou != A2LS_POU_MULTIPLICITY) fail(A2LS_ERR_ARG, "unknown partition of unity %d", o.pou);
     h = new a2ls_handle();
@@ -449,6 +450,13 @@ int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int
       else if (ep == A2LS_FP32) factor_and_coarse<float, float>(h, need_coarse, h->times);
       else factor_and_coarse<float, dfloat>(h, need_coarse, h->times);
     }
+    if (o.precision == A2LS_BF16) {
+      // the FP32 factors rounded to their bfloat16 storage
+      __nv_bfloat16* fb = dalloc<__nv_bfloat16>(h, h->fac_elems);
+      factors_to_bf16(h, static_cast<const float*>(h->d_fac), fb);
+      dfree(h, h->d_fac);
+      h->d_fac = fb;
+    }
     // apply workspace
     h->d_q = dalloc<double>(h, h->n);
     h->d_t = dalloc<double>(h, h->n);
@@ -462,6 +470,8 @@ int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int
       const int timing = h->opt.timing;
       h->opt.timing = 0;
       if (o.precision == A2LS_FP64) autotune_local_solves<double>(h, static_cast<double*>(h->d_fac), h->d_t, scratch, mode);
+      else if (o.precision == A2LS_BF16)
+        autotune_local_solves<__nv_bfloat16>(h, static_cast<__nv_bfloat16*>(h->d_fac), h->d_t, scratch, mode);
       else autotune_local_solves<float>(h, static_cast<float*>(h->d_fac), h->d_t, scratch, mode);
       h->opt.timing = timing;
     }
@@ -620,7 +630,7 @@ int a2ls_query(a2ls_handle* h, int32_t what, void* out, int64_t capacity, int64_
         put_dev(h->d_lump, sizeof(double) * h->sum_n);
         break;
       case A2LS_Q_FACTORS: {
-        const size_t es = h->opt.precision == A2LS_FP64 ? 8 : 4;
+        const size_t es = h->opt.precision == A2LS_FP64 ? 8 : (h->opt.precision == A2LS_BF16 ? 2 : 4);
         put_dev(h->d_fac, es * h->fac_elems);
         put(h->h_foff.data(), sizeof(int64_t) * (N + 1));
         put(h->h_ld.data(), sizeof(int) * N);

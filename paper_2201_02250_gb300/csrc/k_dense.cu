@@ -19,6 +19,7 @@
 namespace a2ls {
 
 template <class T> struct AccOf;
+template <> struct AccOf<__nv_bfloat16> { using type = float; };
 template <> struct AccOf<float> { using type = float; };
 template <> struct AccOf<double> { using type = double; };
 template <> struct AccOf<dfloat> { using type = dfloat; };
@@ -364,12 +365,14 @@ __global__ void __launch_bounds__(256, TC ? 1 : 2) k_lu(int N, const int* ni, co
             tc_fail = true;
             break;
           }
-          tcdf::epilogue(ctx, [&](int m, int c, dfloat v) {
-            if (m < rows && c < cols) {
-              T* p = A + (int64_t)(r0 + m) * L + cs + c;
-              *p = (T)((dfloat)*p - v);
-            }
-          });
+          tcdf::epilogue(
+              ctx,
+              [&](int m, int c) -> dfloat {
+                return (m < rows && c < cols) ? (dfloat)A[(int64_t)(r0 + m) * L + cs + c] : dfloat(0.f, 0.f);
+              },
+              [&](int m, int c, dfloat prev, dfloat v) {
+                if (m < rows && c < cols) A[(int64_t)(r0 + m) * L + cs + c] = (T)(prev - v);
+              });
         }
       }
       __syncthreads();
@@ -517,6 +520,7 @@ template <class T> void invert_diag_tiles(a2ls_handle* h, T* fac) {
 // The gathered vector lives in shared memory; 512 threads = 16 warps.
 // ---------------------------------------------------------------------------
 template <class T> struct Vec;
+template <> struct Vec<__nv_bfloat16> { using type = uint4; static constexpr int W = 8; };
 template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
 template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
 
@@ -529,6 +533,18 @@ __device__ __forceinline__ float dot_vec<float, float>(const float4& a, const fl
 template <>
 __device__ __forceinline__ double dot_vec<double, double>(const double2& a, const double* x) {
   return a.x * x[0] + a.y * x[1];
+}
+// eight bfloat16 values: the high half of each 32-bit word is the upper element, the low half the lower
+template <>
+__device__ __forceinline__ float dot_vec<__nv_bfloat16, float>(const uint4& a, const float* x) {
+  const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    s += __uint_as_float(w[k] << 16) * x[2 * k];
+    s += __uint_as_float(w[k] & 0xffff0000u) * x[2 * k + 1];
+  }
+  return s;
 }
 
 
@@ -706,7 +722,7 @@ __global__ void __launch_bounds__(THREADS) k_local_solve2(
     const int* off, const int* nI, const int* ni, const int* ld, const int64_t* foff, const int* idx,
     const double* D, const T* __restrict__ fac, const double* __restrict__ t, const double* __restrict__ q,
     double* __restrict__ out, int mode, const int* sched, int* counter, int nwork, const int* toff, const int* tf,
-    const int* tg) {
+    const int* tg, const int* __restrict__ pf, const int* __restrict__ pg) {
   using Acc = typename AccOf<T>::type;
   using V = typename Vec<T>::type;
   constexpr int VW = Vec<T>::W;
@@ -752,19 +768,42 @@ __global__ void __launch_bounds__(THREADS) k_local_solve2(
         for (int u = 0; u < RPW; ++u) part[u] = 0;
         // panel columns: forward [first envelope column, r0); backward the 64-column tiles right of the
         // block that reach up to it (U's column envelope)
+        // Only the factor entries inside the envelope are loaded: in the forward sweep row r of L starts at
+        // its first envelope column pf[r]; in the backward sweep U[r][c] can be non-zero only if column c
+        // starts at or above row r (pg[c] <= r), tested per vector of VW columns.  The other lanes skip
+        // their loads (the entries there are exact zeros).
         auto panel = [&](int c0, int c1) {
           const int nv = (c1 - c0) / VW;
           const V* rowp[RPW];
+          int lim[RPW];   // forward: first vector of the row; backward: the row index
 #pragma unroll
-          for (int u = 0; u < RPW; ++u)
-            rowp[u] = reinterpret_cast<const V*>(M + (int64_t)(r0 + min(wid + u * WARPS, tb - 1)) * L + c0);
+          for (int u = 0; u < RPW; ++u) {
+            const int r = r0 + min(wid + u * WARPS, tb - 1);
+            rowp[u] = reinterpret_cast<const V*>(M + (int64_t)r * L + c0);
+            lim[u] = pass == 0 ? (pf[o + r] - c0) / VW : r;
+          }
+          const V zero = {};
+          auto vec_start = [&](int vv) -> int {   // backward: smallest first row of the vector's columns
+            int g = 0x7fffffff;
+            const int c = c0 + vv * VW;
+#pragma unroll
+            for (int q = 0; q < VW; ++q)
+              if (c + q < n) g = min(g, __ldg(pg + o + c + q));
+            return g;
+          };
           int v = lane;
           for (; v + 32 * (RU - 1) < nv; v += 32 * RU) {
             V a[RU][RPW];
 #pragma unroll
-            for (int k = 0; k < RU; ++k)
+            for (int k = 0; k < RU; ++k) {
+              const int vv = v + 32 * k;
+              const int gs = pass == 0 ? 0 : vec_start(vv);
 #pragma unroll
-              for (int u = 0; u < RPW; ++u) a[k][u] = __ldg(rowp[u] + v + 32 * k);
+              for (int u = 0; u < RPW; ++u) {
+                const bool in = pass == 0 ? vv >= lim[u] : gs <= lim[u];
+                a[k][u] = in ? __ldg(rowp[u] + vv) : zero;
+              }
+            }
 #pragma unroll
             for (int k = 0; k < RU; ++k) {
               const Acc* xv = x + c0 + (v + 32 * k) * VW;
@@ -774,8 +813,12 @@ __global__ void __launch_bounds__(THREADS) k_local_solve2(
           }
           for (; v < nv; v += 32) {
             const Acc* xv = x + c0 + v * VW;
+            const int gs = pass == 0 ? 0 : vec_start(v);
 #pragma unroll
-            for (int u = 0; u < RPW; ++u) part[u] += dot_vec<T, Acc>(__ldg(rowp[u] + v), xv);
+            for (int u = 0; u < RPW; ++u) {
+              const bool in = pass == 0 ? v >= lim[u] : gs <= lim[u];
+              if (in) part[u] += dot_vec<T, Acc>(__ldg(rowp[u] + v), xv);
+            }
           }
         };
         if (pass == 0) {
@@ -833,35 +876,40 @@ __global__ void __launch_bounds__(THREADS) k_local_solve2(
 template <class T, int THREADS, int RU>
 static void launch_local_solve2(a2ls_handle* h, const T* fac, const double* t, const double* q, double* z, int mode) {
   using Acc = typename AccOf<T>::type;
-  const size_t smem = 2 * TB * TB * sizeof(T) + sizeof(Acc) * round_up(h->max_n, 4);
-  A2LS_CUDA(cudaFuncSetAttribute(k_local_solve2<T, THREADS, RU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(2 * TB * TB * sizeof(T) + sizeof(Acc) * MAXN_LOCAL)));
+  const size_t smem = 2 * TB * TB * sizeof(T) + sizeof(Acc) * round_up(h->max_n, 8);
   int per_sm = 1, sms = 152, dev = 0;
-  A2LS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local_solve2<T, THREADS, RU>, THREADS, smem));
   A2LS_CUDA(cudaGetDevice(&dev));
+  static bool configured[64] = {};   // per (instantiation, device), as for the one-pass kernel
+  if (dev >= 64 || !configured[dev]) {
+    A2LS_CUDA(cudaFuncSetAttribute(k_local_solve2<T, THREADS, RU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(2 * TB * TB * sizeof(T) + sizeof(Acc) * MAXN_LOCAL)));
+    if (dev < 64) configured[dev] = true;
+  }
+  A2LS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local_solve2<T, THREADS, RU>, THREADS, smem));
   A2LS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = std::max(1, std::min(h->N, sms * std::max(per_sm, 1)));
   A2LS_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->st));
   k_local_solve2<T, THREADS, RU><<<grid, THREADS, smem, h->st>>>(
       h->d_off, h->d_nI, h->d_ni, h->d_ld, h->d_foff, h->d_idx, h->d_D, fac, t, q, z, mode, h->d_sched,
-      h->d_counter, h->N, h->d_toff, h->d_tf, h->d_tg);
+      h->d_counter, h->N, h->d_toff, h->d_tf, h->d_tg, h->d_pf, h->d_pg);
   A2LS_LAUNCH();
 }
 
 template <class T, int THREADS>
 static void launch_local_solve(a2ls_handle* h, const T* fac, const double* t, const double* q, double* z, int mode) {
   using Acc = typename AccOf<T>::type;
-  const size_t smem = sizeof(Acc) * round_up(h->max_n, 4);
-  static bool configured[2] = {false, false};
-  if (!configured[sizeof(T) == 8]) {
+  const size_t smem = sizeof(Acc) * round_up(h->max_n, 8);
+  int dev = 0;
+  A2LS_CUDA(cudaGetDevice(&dev));
+  // the attribute belongs to this kernel instantiation on this device: set once per (instantiation, device)
+  static bool configured[64] = {};
+  if (dev >= 64 || !configured[dev]) {
     A2LS_CUDA(cudaFuncSetAttribute(k_local_solve<T, THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)(sizeof(Acc) * MAXN_LOCAL)));
-    configured[sizeof(T) == 8] = true;
+    if (dev < 64) configured[dev] = true;
   }
   int per_sm = 1, sms = 152;
   A2LS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_local_solve<T, THREADS>, THREADS, smem));
-  int dev = 0;
-  A2LS_CUDA(cudaGetDevice(&dev));
   A2LS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = std::max(1, std::min(h->N, sms * std::max(per_sm, 1)));
   A2LS_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->st));
@@ -906,8 +954,8 @@ void local_solves(a2ls_handle* h, const T* fac, const double* t, const double* q
 template <class T>
 void autotune_local_solves(a2ls_handle* h, const T* fac, const double* t, double* scratch, int mode) {
   char key[128];
-  snprintf(key, sizeof(key), "local_solve2_%s_N%d_max%d_mode%d", sizeof(T) == 8 ? "fp64" : "fp32", h->N, h->max_n,
-           mode);
+  snprintf(key, sizeof(key), "local_solve2_%s_N%d_max%d_mode%d",
+           sizeof(T) == 8 ? "fp64" : (sizeof(T) == 4 ? "fp32" : "bf16"), h->N, h->max_n, mode);
   int cached = autotune_lookup(key);
   if (cached > 0) {
     h->ls_width = cached;
@@ -950,12 +998,13 @@ __global__ void __launch_bounds__(256) k_block_solve(const int* ni, const int* l
                                                      const int64_t* xoff, int col0, int ldx,
                                                      const int* pvec, const int* active, int forward,
                                                      int backward, const int* sched, const int* toff,
-                                                     const int* tf, const int* tg) {
+                                                     const int* tf, const int* tg, int skip_p_le) {
   using Acc = typename AccOf<T>::type;
   __shared__ Acc sA[GK * 65], sB[GK * 9];
   const int i = sched ? sched[blockIdx.x] : blockIdx.x;  // largest subdomains first
   if (active && !active[i]) return;
   const int p = pvec[i];
+  if (p <= skip_p_le) return;
   const int c0 = blockIdx.y * 8;
   if (c0 >= p) return;
   const int pc = min(8, p - c0);
@@ -1012,10 +1061,11 @@ __global__ void __launch_bounds__(256) k_block_solve(const int* ni, const int* l
 
 template <class T>
 void block_solve(a2ls_handle* h, const T* fac, T* X, const int64_t* xoff, int col0, int ldx, const int* pvec,
-                 int pmax, const int* active, int forward, int backward) {
+                 int pmax, const int* active, int forward, int backward, int skip_p_le) {
+  if (pmax <= skip_p_le) return;
   dim3 grid(h->N, (std::max(pmax, 1) + 7) / 8);
   k_block_solve<T><<<grid, 256, 0, h->st>>>(h->d_ni, h->d_ld, h->d_foff, fac, X, xoff, col0, ldx, pvec, active,
-                                           forward, backward, h->d_sched, h->d_toff, h->d_tf, h->d_tg);
+                                           forward, backward, h->d_sched, h->d_toff, h->d_tf, h->d_tg, skip_p_le);
   A2LS_LAUNCH();
 }
 
@@ -1024,17 +1074,20 @@ template void lu_batched<double>(a2ls_handle*, double*, int, double*, double*, i
 template void invert_diag_tiles<float>(a2ls_handle*, float*);
 template void invert_diag_tiles<double>(a2ls_handle*, double*);
 template void local_solves<float>(a2ls_handle*, const float*, const double*, const double*, double*, int);
+template void local_solves<__nv_bfloat16>(a2ls_handle*, const __nv_bfloat16*, const double*, const double*, double*,
+                                          int);
+template void autotune_local_solves<__nv_bfloat16>(a2ls_handle*, const __nv_bfloat16*, const double*, double*, int);
 template void local_solves<double>(a2ls_handle*, const double*, const double*, const double*, double*, int);
 template void autotune_local_solves<float>(a2ls_handle*, const float*, const double*, double*, int);
 template void autotune_local_solves<double>(a2ls_handle*, const double*, const double*, double*, int);
 template void block_solve<float>(a2ls_handle*, const float*, float*, const int64_t*, int, int, const int*, int,
-                                  const int*, int, int);
+                                  const int*, int, int, int);
 template void block_solve<double>(a2ls_handle*, const double*, double*, const int64_t*, int, int, const int*, int,
-                                   const int*, int, int);
+                                   const int*, int, int, int);
 template void lu_batched<dfloat>(a2ls_handle*, dfloat*, int, double*, double*, int);
 template void invert_diag_tiles<dfloat>(a2ls_handle*, dfloat*);
 template void block_solve<dfloat>(a2ls_handle*, const dfloat*, dfloat*, const int64_t*, int, int, const int*, int,
-                                   const int*, int, int);
+                                   const int*, int, int, int);
 
 }  // namespace a2ls
 
@@ -1279,7 +1332,7 @@ void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv,
   if (band <= 0 || band >= n) band = n;
   const int64_t nn = (int64_t)n * n;
   const int grid = (int)std::min<int64_t>(152 * 8, (nn + 255) / 256 + 1);
-  if (h->opt.precision == A2LS_FP32) {
+  if (h->opt.precision != A2LS_FP64) {
     k_to_dfloat_inplace<<<grid, 256, 0, h->st>>>(nn, E);
     A2LS_LAUNCH();
     dense_inverse_t<dfloat>(h, reinterpret_cast<dfloat*>(E), n, scale, reinterpret_cast<dfloat*>(Einv), band);
@@ -1288,6 +1341,24 @@ void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv,
   } else {
     dense_inverse_t<double>(h, E, n, scale, Einv, band);
   }
+}
+
+__global__ void k_to_bf16(int64_t count, const float* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = __float2bfloat16_rn(src[e]);
+}
+
+void factors_to_bf16(a2ls_handle* h, const float* src, __nv_bfloat16* dst) {
+  const int64_t count = (int64_t)h->fac_elems;
+  k_to_bf16<<<(int)std::min<int64_t>(152 * 16, (count + 255) / 256 + 1), 256, 0, h->st>>>(count, src, dst);
+  A2LS_LAUNCH();
+}
+
+void local_solves_any(a2ls_handle* h, const double* t, const double* q, double* z, int mode) {
+  if (h->opt.precision == A2LS_FP64) local_solves<double>(h, static_cast<const double*>(h->d_fac), t, q, z, mode);
+  else if (h->opt.precision == A2LS_BF16)
+    local_solves<__nv_bfloat16>(h, static_cast<const __nv_bfloat16*>(h->d_fac), t, q, z, mode);
+  else local_solves<float>(h, static_cast<const float*>(h->d_fac), t, q, z, mode);
 }
 
 }  // namespace a2ls

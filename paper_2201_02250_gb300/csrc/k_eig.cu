@@ -1162,19 +1162,40 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     lvalB = lv;
     DB = dv;
   }
+  // double-float solves on the tensor cores for the subdomains with at most 32 columns (the others,
+  // small full-space subdomains, on the FP32 pipe)
+  TcSolve tcs;
+  struct TcsGuard {
+    a2ls_handle* h;
+    TcSolve& t;
+    ~TcsGuard() { tc_solve_release(h, t); }
+  } tcs_guard{h, tcs};
+  if constexpr (std::is_same<T, dfloat>::value) {
+    if (h->opt.tensor_cores) tc_solve_prepare(h, fac, tcs);
+  }
+  auto solve_sweep = [&](const int* actv, int forward) {
+    if constexpr (std::is_same<T, dfloat>::value) {
+      if (tcs.ready) {
+        tc_block_solve(h, tcs, W, d_vo, 0, P, d_pv, actv, forward);
+        block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, pmax, actv, forward, !forward, TC_SOLVE_MAX_P);
+        return;
+      }
+    }
+    block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, pmax, actv, forward, !forward);
+  };
   auto apply_T = [&](int vcol, const int* actv) {
     k_bmul<TV, T><<<dim3(N, 8), 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, vcol, d_pv, actv, h->d_lrow, h->d_lcol,
                                              lvalB, DB, V, W);
     A2LS_LAUNCH();
     {
       KTime kt(h, KT_EIG_SOLVE, fwd_flops);
-      block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, pmax, actv, 1, 0);
+      solve_sweep(actv, 1);
     }
     k_mu_fix<T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_vo, P, d_pv, actv, d_kd, hvec, W);
     A2LS_LAUNCH();
     {
       KTime kt(h, KT_EIG_SOLVE, bwd_flops);
-      block_solve<T>(h, fac, W, d_vo, 0, P, d_pv, pmax, actv, 0, 1);
+      solve_sweep(actv, 0);
     }
     k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, actv, d_kd, kvB, W);
     A2LS_LAUNCH();

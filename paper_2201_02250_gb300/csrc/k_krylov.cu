@@ -140,10 +140,7 @@ static void local_part(a2ls_handle* h, const double* t, const double* q, double*
   const bool boolean = h->opt.pou == A2LS_POU_BOOLEAN;
   const int mode = ras ? (boolean ? 0 : 1) : 2;
   double* out = (mode == 0) ? z : h->d_yloc;
-  if (h->opt.precision == A2LS_FP64)
-    local_solves<double>(h, static_cast<const double*>(h->d_fac), t, q, out, mode);
-  else
-    local_solves<float>(h, static_cast<const float*>(h->d_fac), t, q, out, mode);
+  local_solves_any(h, t, q, out, mode);
   if (mode != 0) {
     k_combine<<<grid1d(h->n), 256, 0, h->st>>>(h->n, h->d_mrow, h->d_mpos, h->d_yloc, q, z);
     A2LS_LAUNCH();

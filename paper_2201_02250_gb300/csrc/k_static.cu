@@ -96,10 +96,7 @@ static void apply_static(a2ls_handle* h, const double* r, double* z) {
 
   auto local = [&](const double* tin, const double* qin) {
     double* out = (mode == 0) ? z : yloc;
-    if (h->opt.precision == A2LS_FP64)
-      local_solves<double>(h, static_cast<const double*>(h->d_fac), tin, qin, out, mode);
-    else
-      local_solves<float>(h, static_cast<const float*>(h->d_fac), tin, qin, out, mode);
+    local_solves_any(h, tin, qin, out, mode);
     if (mode != 0) {
       k_combine<<<grid_n, 256, 0, st>>>(h->n, h->d_mrow, h->d_mpos, yloc, qin, z);
       A2LS_LAUNCH();

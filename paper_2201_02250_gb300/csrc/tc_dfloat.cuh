@@ -4,19 +4,21 @@
 // Method (an error-free splitting in the manner of Ozaki, Ogita, Oishi and Rump, "Error-free
 // transformations of matrix multiplication by using fast routines of matrix multiplication and its
 // applications", Numer. Algorithms 2012): every row of A is scaled by a power of two 2^eA_r >= its
-// largest magnitude, every column of B by 2^eB_c, and each scaled value y in [-1, 1] is written as six
+// largest magnitude, every column of B by 2^eB_c, and each scaled value y in [-1, 1] is written as seven
 // base-256 digits, y = sum_s t_s 256^-(s+1) with integers |t_0| <= 256, |t_s| <= 128 (s > 0), obtained by
 // repeated rounding to the nearest integer (each step is exact in double-float arithmetic).  Digit s
 // is stored as the BF16 value t_s 2^(-8 s), which is exact (at most 8 significant bits).  The product
-// of digit i of A and digit j of B then has the natural weight 2^(-8 (i + j)), and the 21 digit pairs
-// with i + j <= 5 are accumulated by the tensor cores in five FP32 accumulators, one for each weight
-// 0..3 and one for the weights 4 and 5 together.  Over 64 terms the sums of weight 0..3 stay below
+// of digit i of A and digit j of B then has the natural weight 2^(-8 (i + j)), and the 28 digit pairs
+// with i + j <= 6 are accumulated by the tensor cores in five FP32 accumulators, one for each weight
+// 0..3 and one for the weights 4 to 6 together.  Over 64 terms the sums of weight 0..3 stay below
 // 2^24 units of their weight, so FP32 accumulates them exactly whatever the order; only the last
 // accumulator rounds, at a relative level of 2^-56.  The result, 2^(eA_r + eB_c - 16) times the sum
-// of the accumulators, is formed in double-float; its error is about 2^-45 of (|A| |B|)_rc, that of a
-// double-float tile product.
+// of the accumulators, is formed in double-float.  Its error is about 2^-52 of max_k |A_rk| max_k |B_kc|
+// (seven digits: the dropped pairs weigh 2^-56 and less), which stays below the double-float product's
+// error bound of a few 2^-47 (|A| |B|)_rc unless the largest entries of the row and of the column sit
+// at different k and exceed their partners by more than about 2^5.
 //
-// Shared memory: A digits 6 x 16 KiB, B digits 6 x 8 KiB (144 KiB), K-major canonical layout
+// Shared memory: A digits 7 x 16 KiB, B digits 7 x 8 KiB (168 KiB), K-major canonical layout
 // (tc_sm100.cuh).  TMEM: 5 accumulators x 64 columns (512 columns allocated: one CTA per SM).
 #pragma once
 
@@ -29,15 +31,15 @@ namespace a2ls {
 namespace tcdf {
 
 constexpr int TM = 128, TN = 64, TK = 64;   // tile shape
-constexpr int NDIG = 6;                      // base-256 digits per value
-constexpr int NACC = 5;                      // accumulators: weights 0, 1, 2, 3 and {4, 5}
+constexpr int NDIG = 7;                      // base-256 digits per value
+constexpr int NACC = 5;                      // accumulators: weights 0, 1, 2, 3 and {4, 5, 6}
 constexpr uint32_t A_DIGIT_BYTES = TM * TK * 2;
 constexpr uint32_t B_DIGIT_BYTES = TN * TK * 2;
-constexpr size_t SMEM_BYTES = (size_t)NDIG * (A_DIGIT_BYTES + B_DIGIT_BYTES);   // 147456
+constexpr size_t SMEM_BYTES = (size_t)NDIG * (A_DIGIT_BYTES + B_DIGIT_BYTES);   // 172032
 constexpr uint32_t TMEM_COLS = 512;
 constexpr long WAIT_LIMIT = 1L << 26;        // polls of the completion barrier before giving up
 
-// the six digits of y = x / 2^e (|y| <= 1), as BF16 values t_s 2^(-8 s)
+// the NDIG digits of y = x / 2^e (|y| <= 1), as BF16 values t_s 2^(-8 s)
 __device__ __forceinline__ void df_digits(dfloat x, int e, __nv_bfloat16 (&d)[NDIG]) {
   float yh = ldexpf(x.hi, -e), yl = ldexpf(x.lo, -e);
 #pragma unroll
@@ -140,7 +142,7 @@ __device__ __forceinline__ void split_b(Ctx& c, FB fb, float* red) {
   }
 }
 
-// After split_a / split_b by all threads: the 84 MMAs of the 21 digit pairs, issued by thread 0, then
+// After split_a / split_b by all threads: the 112 MMAs of the 28 digit pairs, issued by thread 0, then
 // a bounded wait by every thread.  Returns false (on every thread) if the products did not complete.
 __device__ __forceinline__ bool multiply(Ctx& c) {
   tc::fence_proxy_async();
@@ -150,19 +152,21 @@ __device__ __forceinline__ bool multiply(Ctx& c) {
   if (threadIdx.x == 0) {
     constexpr uint32_t idesc = tc::idesc_bf16_f32(TM, TN);
     const uint32_t a0 = tc::smem_u32(c.smem), b0 = a0 + NDIG * A_DIGIT_BYTES;
-    uint32_t started = 0;   // bit g: accumulator g already written in this tile
-#pragma unroll 1
-    for (int i = 0; i < NDIG; ++i)
-#pragma unroll 1
-      for (int j = 0; i + j < NDIG; ++j) {
-        const int g = min(i + j, NACC - 1);
+    // descriptors of the first K-chunk of digit plane 0; the others differ only in the start address
+    // field (address / 16, low bits), which no offset here carries out of
+    const uint64_t ad0 = tc::smem_desc(a0, 128, TK * 16), bd0 = tc::smem_desc(b0, 128, TK * 16);
 #pragma unroll
-        for (int kk = 0; kk < TK / 16; ++kk) {
-          const uint64_t ad = tc::smem_desc(a0 + i * A_DIGIT_BYTES + kk * 256, 128, TK * 16);
-          const uint64_t bd = tc::smem_desc(b0 + j * B_DIGIT_BYTES + kk * 256, 128, TK * 16);
-          tc::mma_bf16(c.tmem + g * TN, ad, bd, idesc, (started >> g) & 1u);
-          started |= 1u << g;
-        }
+    for (int i = 0; i < NDIG; ++i)
+#pragma unroll
+      for (int j = 0; j < NDIG - i; ++j) {
+        const int g = (i + j < NACC - 1) ? i + j : NACC - 1;
+        // the first product into accumulator g overwrites it: (i, j) = (0, g) for g < NACC - 1, and
+        // (0, NACC - 1) for the last one
+        const bool first = (i == 0 && j == g);
+#pragma unroll
+        for (int kk = 0; kk < TK / 16; ++kk)
+          tc::mma_bf16(c.tmem + g * TN, ad0 + ((i * A_DIGIT_BYTES + kk * 256) >> 4),
+                       bd0 + ((j * B_DIGIT_BYTES + kk * 256) >> 4), idesc, (first && kk == 0) ? 0u : 1u);
       }
     tc::commit(c.bar);
   }
@@ -173,17 +177,21 @@ __device__ __forceinline__ bool multiply(Ctx& c) {
   return __syncthreads_and(ok) != 0;
 }
 
-// The tile result for this thread's 32 outputs, handed to out(m, n, value) per element: warp w reads
-// TMEM lanes (rows) 32 (w % 4) .. + 31 and columns 32 (w / 4) .. + 31.  Ends with the fences and
-// barrier that let the next tile reuse TMEM and shared memory.
-template <class OUT>
-__device__ __forceinline__ void epilogue(Ctx& c, OUT out) {
+// The tile result for this thread's 32 outputs: warp w reads TMEM lanes (rows) 32 (w % 4) .. + 31 and
+// columns 32 (w / 4) .. + 31.  Per group of 8 columns, old(m, n) is fetched first for all 8 (so that
+// the loads are in flight together), then out(m, n, old value, product) is called per element.  Ends
+// with the fences and barrier that let the next tile reuse TMEM and shared memory.
+template <class OLD, class OUT>
+__device__ __forceinline__ void epilogue(Ctx& c, OLD old, OUT out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m = (warp & 3) * 32 + lane, n0 = (warp >> 2) * 32;
   const uint32_t lane_addr = c.tmem + ((uint32_t)((warp & 3) * 32) << 16);
   const int em = c.eA[m];
 #pragma unroll 1
   for (int cb = 0; cb < 32; cb += 8) {
+    dfloat prev[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) prev[q] = old(m, n0 + cb + q);
     float acc[NACC][8];
 #pragma unroll
     for (int g = 0; g < NACC; ++g) tc::tmem_ld8(lane_addr + g * TN + n0 + cb, acc[g]);
@@ -196,7 +204,7 @@ __device__ __forceinline__ void epilogue(Ctx& c, OUT out) {
       s = s + dfloat(acc[3][q], 0.f);
       s = s + dfloat(acc[4][q], 0.f);
       const int e = em + c.eB[n0 + cb + q] - 16;
-      out(m, n0 + cb + q, dfloat(ldexpf(s.hi, e), ldexpf(s.lo, e)));
+      out(m, n0 + cb + q, prev[q], dfloat(ldexpf(s.hi, e), ldexpf(s.lo, e)));
     }
   }
   tc::fence_before_sync();

@@ -219,6 +219,75 @@ def test_coarse_space_matches_oracle(c1, name, eigp):
     P.close()
 
 
+@pytest.mark.parametrize("name,eig_tol", [("c1", 1e-10), ("conv40", 1e-10), ("uneven3d", 1e-6)])
+def test_tensor_core_double_float_matches_fp32_pipe(c1, name, eig_tol):
+    """The double-float splitting LU and eigen triangular solves on the tensor cores (BF16 digit
+    products accumulated exactly in FP32) against the same double-float kernels on the FP32 pipe: both
+    carry 48-bit significands.  Where both eigensolves reach the target (the far-from-normal 3D
+    convection-diffusion subdomains level off above 1e-10 in either arithmetic, so that case uses
+    1e-6), the eigenvalues agree to 100 x the target and the spans to 10 x the target over the 1 %
+    gap at the cut (the oracle's spectrum decides the gap)."""
+    if name == "c1":
+        prob = c1[0]
+    elif name == "conv40":
+        prob = pde.tiny_conv_diff(m=40, nb=3, overlap=2, nev=6)
+    else:
+        A = pde.conv_diff_3d(14, 100.0)
+        prob = pde.Problem("uneven3d", A, pde.bfs_region_partition(A, 6, 200, 700, seed=9), 1, 8,
+                           pde.rhs_uniform(A.shape[0], 9), {})
+    ref = c1[1] if name == "c1" else O.setup(prob.A, prob.part, prob.overlap, prob.nev)
+    Pt = setup_gpu(prob, eig_precision="fp32x2", tensor_cores=1, eig_tol=eig_tol)
+    Ps = setup_gpu(prob, eig_precision="fp32x2", tensor_cores=0, eig_tol=eig_tol)
+    rt, rs = Pt.eig_residuals(), Ps.eig_residuals()
+    evt, evs = Pt.eigenvalues(), Ps.eigenvalues()
+    compared = 0
+    for i, (wt, ws, et, es) in enumerate(zip(Pt.coarse_basis(), Ps.coarse_basis(), evt, evs)):
+        # a complex-conjugate pair at the cut may be kept whole by one side only
+        if rt[i] > eig_tol or rs[i] > eig_tol or wt.shape != ws.shape:
+            continue
+        ft = np.sort(np.abs(et[np.isfinite(et.real)]))
+        fs = np.sort(np.abs(es[np.isfinite(es.real)]))
+        np.testing.assert_allclose(ft, fs, rtol=max(1e-8, 100 * eig_tol))
+        if wt.shape[1] and _gap_ok(ref.eig[i], prob.nev):
+            assert angles(wt, ws).max() < max(1e-6, 10 * eig_tol / 0.01)
+        compared += 1
+    assert compared >= len(rt) // 2, (rt, rs)
+    for P in (Pt, Ps):
+        x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+        it, rr, ok = P.solve(dev(prob.b), x, 1e-8)
+        assert ok and rr <= 1e-8
+    Pt.close()
+    Ps.close()
+
+
+def test_bf16_local_factors(c1):
+    """BF16 storage of the local factors: every stored value is the FP32 factor rounded to the nearest
+    bfloat16 (checked against the FP32 form's factors, which the same FP32 factorisation produces), the
+    apply with the oracle's coarse basis is within the bound that the rounding of the stored factors
+    allows (relative perturbation 2^-9 of every factor entry, amplified by the local condition numbers
+    of these problems, below 30), and flexible GMRES still reaches 1e-8 within twice the FP64 count."""
+    prob, ref = c1
+    Pb = setup_gpu(prob, precision="bf16")
+    Pf = setup_gpu(prob, precision="fp32")
+    fb, ff = Pb.factors(), Pf.factors()
+    for b, f in zip(fb, ff):
+        r = torch.as_tensor(f.astype(np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
+        np.testing.assert_array_equal(b.astype(np.float32), r)
+    Pb.set_coarse_basis(ref.coarse.W)
+    z = apply_gpu(Pb, prob.b)
+    zr = O.apply(ref, prob.b)
+    err = np.linalg.norm(z - zr) / np.linalg.norm(zr)
+    assert err <= 30 * 2.0 ** -9, err
+    P2 = setup_gpu(prob, precision="bf16")
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    it, rr, ok = P2.solve(dev(prob.b), x, 1e-8)
+    true = np.linalg.norm(prob.b - prob.A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
+    res = O.gmres(prob.A, lambda v: O.apply(ref, v), prob.b, rtol=1e-8)
+    assert ok and true <= 1e-8 and it <= 2 * res.iters, (it, res.iters, true)
+    for P in (Pb, Pf, P2):
+        P.close()
+
+
 def test_full_coarse_space_gives_exact_inverse():
     """Boolean D and nev = |Omega_Ii|: R_0^H is square and M_deflated^{-1} = A^{-1} (Eq. 2.4)."""
     prob = pde.tiny_conv_diff(m=8, nb=2, overlap=1, nev=16)
