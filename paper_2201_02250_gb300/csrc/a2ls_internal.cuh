@@ -109,6 +109,12 @@ struct a2ls_handle {
   // local factors (block-inverted LU, precision = opt.precision)
   void* d_fac = nullptr;
   size_t fac_elems = 0;
+  // layout of d_fac: the factorisation's (ld_i = n_i rounded to 4, offsets h_foff), except for the
+  // bfloat16 storage, whose rows start on 16-byte boundaries (ld_i rounded to 8)
+  std::vector<int> h_fld;
+  std::vector<int64_t> h_ffoff;
+  int* d_fld = nullptr;
+  int64_t* d_ffoff = nullptr;
 
   // coarse space
   int n0 = 0;
@@ -216,8 +222,9 @@ void tc_block_solve(a2ls_handle* h, const TcSolve& ts, dfloat* X, const int64_t*
                     const int* pvec, const int* active, int forward, unsigned char* xdig = nullptr);
 constexpr int TC_SOLVE_MAX_P = 32;
 
-// k_dense.cu: FP32 local factors rounded to the bfloat16 storage of A2LS_BF16 (fac_elems values)
-void factors_to_bf16(a2ls_handle* h, const float* src, __nv_bfloat16* dst);
+// k_dense.cu: FP32 local factors rounded to the bfloat16 storage of A2LS_BF16, in the layout
+// h_fld / h_ffoff (which this call sets up); returns the new storage
+__nv_bfloat16* factors_to_bf16(a2ls_handle* h, const float* src);
 // the apply's local solves with the handle's factor type
 void local_solves_any(a2ls_handle* h, const double* t, const double* q, double* z, int mode);
 

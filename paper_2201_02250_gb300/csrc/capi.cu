@@ -450,10 +450,13 @@ int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int
       else if (ep == A2LS_FP32) factor_and_coarse<float, float>(h, need_coarse, h->times);
       else factor_and_coarse<float, dfloat>(h, need_coarse, h->times);
     }
+    h->h_fld = h->h_ld;
+    h->h_ffoff = h->h_foff;
+    h->d_fld = h->d_ld;
+    h->d_ffoff = h->d_foff;
     if (o.precision == A2LS_BF16) {
-      // the FP32 factors rounded to their bfloat16 storage
-      __nv_bfloat16* fb = dalloc<__nv_bfloat16>(h, h->fac_elems);
-      factors_to_bf16(h, static_cast<const float*>(h->d_fac), fb);
+      // the FP32 factors rounded to their bfloat16 storage (rows on 16-byte boundaries)
+      __nv_bfloat16* fb = factors_to_bf16(h, static_cast<const float*>(h->d_fac));
       dfree(h, h->d_fac);
       h->d_fac = fb;
     }
@@ -631,9 +634,9 @@ int a2ls_query(a2ls_handle* h, int32_t what, void* out, int64_t capacity, int64_
         break;
       case A2LS_Q_FACTORS: {
         const size_t es = h->opt.precision == A2LS_FP64 ? 8 : (h->opt.precision == A2LS_BF16 ? 2 : 4);
-        put_dev(h->d_fac, es * h->fac_elems);
-        put(h->h_foff.data(), sizeof(int64_t) * (N + 1));
-        put(h->h_ld.data(), sizeof(int) * N);
+        put_dev(h->d_fac, es * (size_t)h->h_ffoff[N]);
+        put(h->h_ffoff.data(), sizeof(int64_t) * (N + 1));
+        put(h->h_fld.data(), sizeof(int) * N);
         break;
       }
       case A2LS_Q_COARSE: {

@@ -360,19 +360,24 @@ __global__ void __launch_bounds__(256, TC ? 1 : 2) k_lu(int N, const int* ni, co
           tcdf::split_b(ctx, [&](int k, int c) -> dfloat {
             return (k < w && c < cols) ? (dfloat)A[(int64_t)(k0 + k) * L + cs + c] : dfloat(0.f, 0.f);
           }, tc_red);
+          // while the MMAs run: this tile's A22 rows (read by the epilogue) and the next column tile of
+          // U12 (read by the next split) into L2
+          tcdf::prefetch_rows_l2(A + (int64_t)r0 * L + cs, L * (int64_t)sizeof(T), rows, cols * (int)sizeof(T));
+          {
+            int nt = ct + 1;
+            while (nt < tiles && !unz[nt]) ++nt;
+            if (nt < tiles) {
+              const int cs2 = c0 + nt * TB;
+              tcdf::prefetch_rows_l2(A + (int64_t)k0 * L + cs2, L * (int64_t)sizeof(T), w,
+                                     min(TB, n - cs2) * (int)sizeof(T));
+            }
+          }
           if (!tcdf::multiply(ctx)) {
             if (threadIdx.x == 0) raise_status(st, A2LS_ERR_TIMEOUT, i, k0);
             tc_fail = true;
             break;
           }
-          tcdf::epilogue(
-              ctx,
-              [&](int m, int c) -> dfloat {
-                return (m < rows && c < cols) ? (dfloat)A[(int64_t)(r0 + m) * L + cs + c] : dfloat(0.f, 0.f);
-              },
-              [&](int m, int c, dfloat prev, dfloat v) {
-                if (m < rows && c < cols) A[(int64_t)(r0 + m) * L + cs + c] = (T)(prev - v);
-              });
+          tcdf::epilogue_subtract(ctx, reinterpret_cast<dfloat*>(A) + (int64_t)r0 * L + cs, L, rows, cols);
         }
       }
       __syncthreads();
@@ -890,7 +895,7 @@ static void launch_local_solve2(a2ls_handle* h, const T* fac, const double* t, c
   const int grid = std::max(1, std::min(h->N, sms * std::max(per_sm, 1)));
   A2LS_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->st));
   k_local_solve2<T, THREADS, RU><<<grid, THREADS, smem, h->st>>>(
-      h->d_off, h->d_nI, h->d_ni, h->d_ld, h->d_foff, h->d_idx, h->d_D, fac, t, q, z, mode, h->d_sched,
+      h->d_off, h->d_nI, h->d_ni, h->d_fld, h->d_ffoff, h->d_idx, h->d_D, fac, t, q, z, mode, h->d_sched,
       h->d_counter, h->N, h->d_toff, h->d_tf, h->d_tg, h->d_pf, h->d_pg);
   A2LS_LAUNCH();
 }
@@ -913,7 +918,7 @@ static void launch_local_solve(a2ls_handle* h, const T* fac, const double* t, co
   A2LS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int grid = std::max(1, std::min(h->N, sms * std::max(per_sm, 1)));
   A2LS_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->st));
-  k_local_solve<T, THREADS><<<grid, THREADS, smem, h->st>>>(h->d_off, h->d_nI, h->d_ni, h->d_ld, h->d_foff, h->d_idx,
+  k_local_solve<T, THREADS><<<grid, THREADS, smem, h->st>>>(h->d_off, h->d_nI, h->d_ni, h->d_fld, h->d_ffoff, h->d_idx,
                                                             h->d_D, fac, t, q, z, mode, h->d_sched, h->d_counter,
                                                             h->N, h->d_toff, h->d_tf, h->d_tg);
   A2LS_LAUNCH();
@@ -1343,15 +1348,36 @@ void dense_inverse(a2ls_handle* h, double* E, int n, double scale, double* Einv,
   }
 }
 
-__global__ void k_to_bf16(int64_t count, const float* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
-    dst[e] = __float2bfloat16_rn(src[e]);
+// row r of subdomain blockIdx.x: FP32 (leading dimension ld) to bfloat16 (leading dimension ld2 >= ld,
+// padding zero)
+__global__ void k_to_bf16(const int* ni, const int* ld, const int64_t* foff, const int* ld2, const int64_t* foff2,
+                          const float* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
+  const int i = blockIdx.x;
+  const int n = ni[i], L = ld[i], L2 = ld2[i];
+  const float* s = src + foff[i];
+  __nv_bfloat16* d = dst + foff2[i];
+  for (int r = blockIdx.y; r < n; r += gridDim.y)
+    for (int c = threadIdx.x; c < L2; c += blockDim.x)
+      d[(int64_t)r * L2 + c] = __float2bfloat16_rn(c < L ? s[(int64_t)r * L + c] : 0.f);
 }
 
-void factors_to_bf16(a2ls_handle* h, const float* src, __nv_bfloat16* dst) {
-  const int64_t count = (int64_t)h->fac_elems;
-  k_to_bf16<<<(int)std::min<int64_t>(152 * 16, (count + 255) / 256 + 1), 256, 0, h->st>>>(count, src, dst);
+__nv_bfloat16* factors_to_bf16(a2ls_handle* h, const float* src) {
+  const int N = h->N;
+  h->h_fld.assign(N, 0);
+  h->h_ffoff.assign(N + 1, 0);
+  for (int i = 0; i < N; ++i) {
+    h->h_fld[i] = (int)round_up(h->h_n[i], 8);
+    h->h_ffoff[i + 1] = h->h_ffoff[i] + (int64_t)h->h_fld[i] * h->h_n[i];
+  }
+  h->d_fld = dalloc<int>(h, N);
+  h->d_ffoff = dalloc<int64_t>(h, N + 1);
+  A2LS_CUDA(cudaMemcpyAsync(h->d_fld, h->h_fld.data(), sizeof(int) * N, cudaMemcpyHostToDevice, h->st));
+  A2LS_CUDA(cudaMemcpyAsync(h->d_ffoff, h->h_ffoff.data(), sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice,
+                            h->st));
+  __nv_bfloat16* dst = dalloc<__nv_bfloat16>(h, (size_t)h->h_ffoff[N]);
+  k_to_bf16<<<dim3(N, 64), 256, 0, h->st>>>(h->d_ni, h->d_ld, h->d_foff, h->d_fld, h->d_ffoff, src, dst);
   A2LS_LAUNCH();
+  return dst;
 }
 
 void local_solves_any(a2ls_handle* h, const double* t, const double* q, double* z, int mode) {

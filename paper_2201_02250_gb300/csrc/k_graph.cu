@@ -384,7 +384,7 @@ void build_subdomains(a2ls_handle* h) {
     h->h_n[i] = hI[i] + hG[i];
     if (h->h_n[i] > MAXN_LOCAL)
       fail(A2LS_ERR_ARG, "subdomain %d has %d rows; at most %d are supported", i, h->h_n[i], MAXN_LOCAL);
-    h->h_ld[i] = (int)round_up(h->h_n[i], 8);   // rows on 16-byte boundaries for every factor type
+    h->h_ld[i] = (int)round_up(h->h_n[i], 4);
     h->h_off[i + 1] = h->h_off[i] + h->h_n[i];
     h->h_foff[i + 1] = h->h_foff[i] + (int64_t)h->h_ld[i] * h->h_n[i];
     h->max_n = std::max(h->max_n, h->h_n[i]);

@@ -11,7 +11,7 @@
 //     column in a scratch array, so that each later block reads digits instead of splitting again;
 //   * per 64-row block, the tiles of its panel stream through two shared-memory stages by cp.async,
 //     their 112 M=64 x N=32 x K=16 MMAs (28 digit pairs) fill one of two TMEM buffers while the CTA
-//     folds the previous tile's five accumulators into double-float registers; then the diagonal
+//     folds the previous tile's five accumulator blocks into double-float registers; then the diagonal
 //     tile product X_b = inv(T_bb) (X_b - panel) runs the same way and X_b's digits are stored.
 // One CTA of 256 threads per subdomain (largest first); 173 KB of shared memory and 512 TMEM columns.
 #include "a2ls_internal.cuh"
@@ -22,14 +22,16 @@
 namespace a2ls {
 namespace tcs {
 
-constexpr int M = 64, NC = 32, K = 64, NDIG = tcdf::NDIG, NACC = tcdf::NACC;
+constexpr int M = 64, NC = 32, K = 64, NDIG = tcdf::NDIG;
+// FP32 accumulator blocks of NC columns: digit weights 0, 1, 2, 3 (exact) and 4-6 together
+constexpr int NBLK = 5;
 constexpr uint32_t A_PLANE = M * K * 2;            // 8 KiB
 constexpr uint32_t B_PLANE = NC * K * 2;           // 4 KiB
 constexpr uint32_t A_TILE = NDIG * A_PLANE + M * 4;   // digit planes, then int32 row exponents
 constexpr uint32_t B_TILE = NDIG * B_PLANE + NC * 4;  // digit planes, then int32 column exponents
 constexpr uint32_t STAGE = A_TILE + B_TILE;
 constexpr size_t SMEM = 2 * (size_t)STAGE;
-constexpr uint32_t BUF_COLS = NACC * NC;           // TMEM columns of one accumulator buffer
+constexpr uint32_t BUF_COLS = NBLK * NC;           // TMEM columns of one accumulator buffer
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int THREADS = 256;
 static_assert(A_TILE % 16 == 0 && B_TILE % 16 == 0, "16-byte copies");
@@ -154,7 +156,11 @@ __device__ __forceinline__ void split_columns(const dfloat* S, unsigned char* ds
   }
 }
 
-// the 112 MMAs of one tile product (A digits at a, B digits at b) into TMEM buffer `buf`, then a commit
+// The 112 MMAs of one tile product (A digits at a, B digits at b) into TMEM buffer `buf`, then a commit:
+// pair (i, j) of digits, M = 64, N = 32, into the block of its weight i + j (weights 4 to 6 share the
+// last block).  The blocks of weight 0 to 3 stay below 2^24 units of their weight over 64 terms and are
+// exact; the shared last block rounds at 2^-56 of the result.  The first product into a block is the
+// pair (0, j) with j its first weight; it overwrites the block.
 __device__ __forceinline__ void issue_mmas(uint32_t tmem, int buf, const unsigned char* a, const unsigned char* bsm,
                                            uint64_t* bar) {
   constexpr uint32_t idesc = tc::idesc_bf16_f32(M, NC);
@@ -165,19 +171,15 @@ __device__ __forceinline__ void issue_mmas(uint32_t tmem, int buf, const unsigne
   for (int i = 0; i < NDIG; ++i)
 #pragma unroll
     for (int j = 0; j < NDIG - i; ++j) {
-      const int g = (i + j < NACC - 1) ? i + j : NACC - 1;
-      const bool first = (i == 0 && j == g);
 #pragma unroll
       for (int kk = 0; kk < K / 16; ++kk)
-        tc::mma_bf16(tmem + buf * BUF_COLS + g * NC, ad0 + ((i * A_PLANE + kk * 256) >> 4),
-                     bd0 + ((j * B_PLANE + kk * 256) >> 4), idesc, (first && kk == 0) ? 0u : 1u);
+        tc::mma_bf16(tmem + buf * BUF_COLS + (i + j < NBLK ? i + j : NBLK - 1) * NC,
+                     ad0 + ((i * A_PLANE + kk * 256) >> 4), bd0 + ((j * B_PLANE + kk * 256) >> 4), idesc,
+                     (i == 0 && j < NBLK && kk == 0) ? 0u : 1u);
     }
   tc::commit(bar);
 }
 
-// The tile result of TMEM buffer `buf` for this thread's row and 16 columns (M = 64: row 16 (w % 4) +
-// lane sits in TMEM lane 32 (w % 4) + lane, lanes 16-31 of each quarter are unused); scales from the
-// stage's exponents.  f(col, value) per column for lanes < 16.
 template <class F>
 __device__ __forceinline__ void fold(uint32_t tmem, int buf, const int* eA, const int* eB, F f) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -187,17 +189,17 @@ __device__ __forceinline__ void fold(uint32_t tmem, int buf, const int* eA, cons
   const int er = eA[row];
 #pragma unroll
   for (int c8 = 0; c8 < 16; c8 += 8) {
-    float acc[NACC][8];
+    float acc[NBLK][8];
 #pragma unroll
-    for (int g = 0; g < NACC; ++g) tc::tmem_ld8(base + g * NC + c8, acc[g]);
+    for (int g = 0; g < NBLK; ++g) tc::tmem_ld8(base + g * NC + c8, acc[g]);
     tc::tmem_wait_ld();
     if (lane < 16) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
+        // exact sum of the two leading blocks, then the smaller ones in decreasing weight
         dfloat s = df_two_sum(acc[0][q], acc[1][q]);
-        s = s + dfloat(acc[2][q], 0.f);
-        s = s + dfloat(acc[3][q], 0.f);
-        s = s + dfloat(acc[4][q], 0.f);
+#pragma unroll
+        for (int g = 2; g < NBLK; ++g) s = s + dfloat(acc[g][q], 0.f);
         const int col = h * 16 + c8 + q;
         const int e = er + eB[col] - 16;
         f(col, dfloat(ldexpf(s.hi, e), ldexpf(s.lo, e)));
@@ -218,6 +220,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_solve_tc(
   __shared__ uint32_t tbase;
   __shared__ float red[8 * NC];
   __shared__ int tiles[MAXN_LOCAL / M + 1];
+  __shared__ int sexpA[2][M], sexpB[2][NC];   // scale exponents of the tiles in flight
   const int i = sched[blockIdx.x];
   if (active && !active[i]) return;
   const int p = pvec[i];
@@ -275,35 +278,41 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_solve_tc(
       copy_async(sgt, fdig + tab[(int64_t)b * (nb + 1) + c], A_TILE, pol_stream);
       copy_async(sgt + A_TILE, xd + (size_t)c * B_TILE, B_TILE, pol_keep);
     };
+    // Pipeline per tile tt: wait for its operands, save its scale exponents (the stage is refilled
+    // before the fold reads them), issue its MMAs into TMEM buffer tt & 1, wait for tile tt - 1's MMAs,
+    // start loading tile tt + 1 into the stage tile tt - 1 used, then fold tile tt - 1.  The copies of
+    // tile tt + 1 thus overlap tile tt's MMAs and tile tt - 1's fold.
     if (T > 0) load(0);
     for (int tt = 0; tt < T && ok; ++tt) {
       cp_wait_all();
       tc::fence_proxy_async();
       tc::fence_before_sync();
-      __syncthreads();
+      __syncthreads();   // every thread's copies of tile tt have landed
       tc::fence_after_sync();
+      {
+        const unsigned char* sp = stage[tt & 1];
+        if (tid < M) sexpA[tt & 1][tid] = reinterpret_cast<const int*>(sp + NDIG * A_PLANE)[tid];
+        else if (tid < M + NC) sexpB[tt & 1][tid - M] = reinterpret_cast<const int*>(sp + A_TILE + NDIG * B_PLANE)[tid - M];
+      }
       if (tid == 0) issue_mmas(tmem, tt & 1, stage[tt & 1], stage[tt & 1] + A_TILE, &bar[tt & 1]);
       __syncwarp();
       if (tt > 0) {
         const int u = (tt - 1) & 1;
         ok = __syncthreads_and(wait_mma(u)) != 0;
         if (!ok) break;
-        const unsigned char* sp = stage[u];
-        fold(tmem, u, reinterpret_cast<const int*>(sp + NDIG * A_PLANE),
-             reinterpret_cast<const int*>(sp + A_TILE + NDIG * B_PLANE), [&](int col, dfloat v) { acc[col - h * 16] += v; });
+        if (tt + 1 < T) load(tt + 1);   // stage u is free: tile tt - 1's MMAs have completed
+        fold(tmem, u, sexpA[u], sexpB[u], [&](int col, dfloat v) { acc[col - h * 16] += v; });
         tc::fence_before_sync();
+        __syncthreads();   // TMEM buffer u is read before tile tt + 1's MMAs overwrite it
+      } else {
+        if (tt + 1 < T) load(tt + 1);   // stage 1 has not been used yet
+        __syncthreads();   // the saved exponents of tile 0 are visible before its fold
       }
-      __syncthreads();
-      if (tt + 1 < T) load(tt + 1);
     }
     if (T > 0 && ok) {
       const int u = (T - 1) & 1;
       ok = __syncthreads_and(wait_mma(u)) != 0;
-      if (ok) {
-        const unsigned char* sp = stage[u];
-        fold(tmem, u, reinterpret_cast<const int*>(sp + NDIG * A_PLANE),
-             reinterpret_cast<const int*>(sp + A_TILE + NDIG * B_PLANE), [&](int col, dfloat v) { acc[col - h * 16] += v; });
-      }
+      if (ok) fold(tmem, u, sexpA[u], sexpB[u], [&](int col, dfloat v) { acc[col - h * 16] += v; });
       tc::fence_before_sync();
       __syncthreads();
     }

@@ -9,17 +9,16 @@
 // repeated rounding to the nearest integer (each step is exact in double-float arithmetic).  Digit s
 // is stored as the BF16 value t_s 2^(-8 s), which is exact (at most 8 significant bits).  The product
 // of digit i of A and digit j of B then has the natural weight 2^(-8 (i + j)), and the 28 digit pairs
-// with i + j <= 6 are accumulated by the tensor cores in five FP32 accumulators, one for each weight
-// 0..3 and one for the weights 4 to 6 together.  Over 64 terms the sums of weight 0..3 stay below
-// 2^24 units of their weight, so FP32 accumulates them exactly whatever the order; only the last
-// accumulator rounds, at a relative level of 2^-56.  The result, 2^(eA_r + eB_c - 16) times the sum
-// of the accumulators, is formed in double-float.  Its error is about 2^-52 of max_k |A_rk| max_k |B_kc|
+// with i + j <= 6 are accumulated by the tensor cores in seven FP32 accumulator blocks, one per weight.
+// Block d sums d + 1 pairs over 64 terms, at most 9 x 2^20 units of its weight, below 2^24, so FP32
+// accumulates every block exactly whatever the order.  The result, 2^(eA_r + eB_c - 16) times the sum
+// of the blocks, is formed in double-float.  Its error is about 2^-52 of max_k |A_rk| max_k |B_kc|
 // (seven digits: the dropped pairs weigh 2^-56 and less), which stays below the double-float product's
 // error bound of a few 2^-47 (|A| |B|)_rc unless the largest entries of the row and of the column sit
 // at different k and exceed their partners by more than about 2^5.
 //
 // Shared memory: A digits 7 x 16 KiB, B digits 7 x 8 KiB (168 KiB), K-major canonical layout
-// (tc_sm100.cuh).  TMEM: 5 accumulators x 64 columns (512 columns allocated: one CTA per SM).
+// (tc_sm100.cuh).  TMEM: 7 accumulator blocks x 64 columns (512 columns allocated: one CTA per SM).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -32,7 +31,7 @@ namespace tcdf {
 
 constexpr int TM = 128, TN = 64, TK = 64;   // tile shape
 constexpr int NDIG = 7;                      // base-256 digits per value
-constexpr int NACC = 5;                      // accumulators: weights 0, 1, 2, 3 and {4, 5, 6}
+constexpr int NBLK = NDIG;                   // exact accumulator blocks, one per digit weight 0 .. 6
 constexpr uint32_t A_DIGIT_BYTES = TM * TK * 2;
 constexpr uint32_t B_DIGIT_BYTES = TN * TK * 2;
 constexpr size_t SMEM_BYTES = (size_t)NDIG * (A_DIGIT_BYTES + B_DIGIT_BYTES);   // 172032
@@ -142,7 +141,7 @@ __device__ __forceinline__ void split_b(Ctx& c, FB fb, float* red) {
   }
 }
 
-// After split_a / split_b by all threads: the 112 MMAs of the 28 digit pairs, issued by thread 0, then
+// After split_a / split_b by all threads: the 40 MMAs of the 28 digit pairs, issued by thread 0, then
 // a bounded wait by every thread.  Returns false (on every thread) if the products did not complete.
 __device__ __forceinline__ bool multiply(Ctx& c) {
   tc::fence_proxy_async();
@@ -150,23 +149,23 @@ __device__ __forceinline__ bool multiply(Ctx& c) {
   __syncthreads();
   tc::fence_after_sync();
   if (threadIdx.x == 0) {
-    constexpr uint32_t idesc = tc::idesc_bf16_f32(TM, TN);
     const uint32_t a0 = tc::smem_u32(c.smem), b0 = a0 + NDIG * A_DIGIT_BYTES;
     // descriptors of the first K-chunk of digit plane 0; the others differ only in the start address
     // field (address / 16, low bits), which no offset here carries out of
     const uint64_t ad0 = tc::smem_desc(a0, 128, TK * 16), bd0 = tc::smem_desc(b0, 128, TK * 16);
+    // The B digit planes are consecutive 64-row groups of one K-major operand, so an MMA with A digit i
+    // and B digits j0 .. j0 + nj - 1 (N = 64 nj <= 256) writes pair (i, j) into block i + j, the
+    // block of its weight.  The two MMAs of digit 0 write all seven blocks first; the others add.
 #pragma unroll
     for (int i = 0; i < NDIG; ++i)
 #pragma unroll
-      for (int j = 0; j < NDIG - i; ++j) {
-        const int g = (i + j < NACC - 1) ? i + j : NACC - 1;
-        // the first product into accumulator g overwrites it: (i, j) = (0, g) for g < NACC - 1, and
-        // (0, NACC - 1) for the last one
-        const bool first = (i == 0 && j == g);
+      for (int j0 = 0; j0 < NDIG - i; j0 += 4) {
+        const int nj = (NDIG - i - j0) < 4 ? (NDIG - i - j0) : 4;
+        const uint32_t idesc = tc::idesc_bf16_f32(TM, TN * nj);
 #pragma unroll
         for (int kk = 0; kk < TK / 16; ++kk)
-          tc::mma_bf16(c.tmem + g * TN, ad0 + ((i * A_DIGIT_BYTES + kk * 256) >> 4),
-                       bd0 + ((j * B_DIGIT_BYTES + kk * 256) >> 4), idesc, (first && kk == 0) ? 0u : 1u);
+          tc::mma_bf16(c.tmem + (i + j0) * TN, ad0 + ((i * A_DIGIT_BYTES + kk * 256) >> 4),
+                       bd0 + ((j0 * B_DIGIT_BYTES + kk * 256) >> 4), idesc, (i == 0 && kk == 0) ? 0u : 1u);
       }
     tc::commit(c.bar);
   }
@@ -177,35 +176,65 @@ __device__ __forceinline__ bool multiply(Ctx& c) {
   return __syncthreads_and(ok) != 0;
 }
 
-// The tile result for this thread's 32 outputs: warp w reads TMEM lanes (rows) 32 (w % 4) .. + 31 and
-// columns 32 (w / 4) .. + 31.  Per group of 8 columns, old(m, n) is fetched first for all 8 (so that
-// the loads are in flight together), then out(m, n, old value, product) is called per element.  Ends
-// with the fences and barrier that let the next tile reuse TMEM and shared memory.
-template <class OLD, class OUT>
-__device__ __forceinline__ void epilogue(Ctx& c, OLD old, OUT out) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m = (warp & 3) * 32 + lane, n0 = (warp >> 2) * 32;
+// L2 prefetch of rows [0, rows) x bytes [0, row_bytes) starting at base with the given row pitch,
+// spread over the CTA (one 128-byte line per request)
+__device__ __forceinline__ void prefetch_rows_l2(const void* base, int64_t pitch_bytes, int rows, int row_bytes) {
+  // one request per 128-byte line the row's bytes touch, at the line's aligned start (a row may start
+  // anywhere in a line; no request reaches past the row's last byte's line)
+  if (row_bytes <= 0) return;
+  const int lines = (row_bytes + 127) / 128 + 1;
+  for (int e = threadIdx.x; e < rows * lines; e += blockDim.x) {
+    const uintptr_t first = reinterpret_cast<uintptr_t>(base) + (uintptr_t)((e / lines) * pitch_bytes);
+    const uintptr_t line = (first & ~(uintptr_t)127) + (uintptr_t)(e % lines) * 128;
+    if (line <= first + row_bytes - 1) asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
+  }
+}
+
+// C(rows x cols) -= the tile product, for C in global memory (double-float, row pitch ldc elements),
+// coalesced: in two halves of 32 columns, the old values are read row-contiguously into shared memory
+// (the B digits' region, free once the MMAs have completed), each thread subtracts the product for 16
+// outputs of its TMEM lane (warp w: rows 32 (w % 4) .., columns 16 (w / 4) .. of the half), and the
+// half is written back row-contiguously.  Ends with the fences and barrier that let the next tile reuse
+// TMEM and shared memory.
+constexpr int SUB_LD = 33;   // staging row stride in double-float values (odd: spreads the banks)
+__device__ __forceinline__ void epilogue_subtract(Ctx& c, dfloat* C, int64_t ldc, int rows, int cols) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m = (warp & 3) * 32 + lane, nq = (warp >> 2) * 16;
   const uint32_t lane_addr = c.tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  dfloat* S = reinterpret_cast<dfloat*>(c.smem + NDIG * A_DIGIT_BYTES);   // TM x SUB_LD
   const int em = c.eA[m];
 #pragma unroll 1
-  for (int cb = 0; cb < 32; cb += 8) {
-    dfloat prev[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) prev[q] = old(m, n0 + cb + q);
-    float acc[NACC][8];
-#pragma unroll
-    for (int g = 0; g < NACC; ++g) tc::tmem_ld8(lane_addr + g * TN + n0 + cb, acc[g]);
-    tc::tmem_wait_ld();
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      // exact sum of the first two accumulators, then the smaller ones in decreasing weight
-      dfloat s = df_two_sum(acc[0][q], acc[1][q]);
-      s = s + dfloat(acc[2][q], 0.f);
-      s = s + dfloat(acc[3][q], 0.f);
-      s = s + dfloat(acc[4][q], 0.f);
-      const int e = em + c.eB[n0 + cb + q] - 16;
-      out(m, n0 + cb + q, prev[q], dfloat(ldexpf(s.hi, e), ldexpf(s.lo, e)));
+  for (int half = 0; half < 2; ++half) {
+    const int cbase = half * 32;
+    // old values: one warp per row, one 8-byte value per thread (C's column offset can be odd: the
+    // overlap phase of the factorisation starts at column n_I, so wider accesses could be misaligned)
+    for (int e = tid; e < TM * 32; e += 256) {
+      const int r = e >> 5, cc = e & 31, col = cbase + cc;
+      S[r * SUB_LD + cc] = (r < rows && col < cols) ? C[(int64_t)r * ldc + col] : dfloat(0.f, 0.f);
     }
+    __syncthreads();
+#pragma unroll
+    for (int cb = 0; cb < 16; cb += 8) {
+      float acc[NBLK][8];
+#pragma unroll
+      for (int g = 0; g < NBLK; ++g) tc::tmem_ld8(lane_addr + g * TN + cbase + nq + cb, acc[g]);
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        dfloat sum = df_two_sum(acc[0][q], acc[1][q]);
+#pragma unroll
+        for (int g = 2; g < NBLK; ++g) sum = sum + dfloat(acc[g][q], 0.f);
+        const int e = em + c.eB[cbase + nq + cb + q] - 16;
+        dfloat& o = S[m * SUB_LD + nq + cb + q];
+        o = o - dfloat(ldexpf(sum.hi, e), ldexpf(sum.lo, e));
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < TM * 32; e += 256) {
+      const int r = e >> 5, cc = e & 31, col = cbase + cc;
+      if (r < rows && col < cols) C[(int64_t)r * ldc + col] = S[r * SUB_LD + cc];
+    }
+    __syncthreads();
   }
   tc::fence_before_sync();
   __syncthreads();
