@@ -46,16 +46,17 @@ FP32_PEAK_TFLOPS_DERIVED = 152 * 128 * 2 * 2.07e9 / 1e12
 # double-float multiply-add = 12 FP32 instructions (4 for the exact product, 6 for TwoSum, 2 adds):
 # 2 flops per 12 lane-instructions of the FP32 pipe
 FP32X2_PEAK_TFLOPS_DERIVED = 152 * 128 * 2.07e9 * 2 / 12 / 1e12
-# arithmetic of each tracked kernel in the mixed form (the plain form is FP64 throughout)
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per subdomain and launch of the
-# mixed-form kernels, from one ncu capture of each on the 256x256 case (64 subdomains of the C2 size;
-# the kernels work subdomain by subdomain, so the traffic of a launch grows with the subdomains it
-# covers).  A kernel changed after its capture has no entry (traffic null).
-NCU_TRAFFIC_PER_SUBDOMAIN = {"eig_triangular_solves": 1.0622e6}
-MIXED_KERNEL_DTYPE = {"lu_local": "f32", "lu_splitting": "f32x2", "eig_triangular_solves": "f32x2",
+# arithmetic of each tracked kernel in the mixed form (the plain form is FP64 throughout): "f32x2-tc"
+# = double-float products as BF16 digit products on the tensor cores (28 digit pairs per product)
+MIXED_KERNEL_DTYPE = {"lu_local": "f32", "lu_splitting": "f32x2-tc", "eig_triangular_solves": "f32x2-tc",
                       "eig_orthogonalisation": "f32x2", "eig_rayleigh_ritz": "f32x2", "coarse_lu": "f32x2",
                       "coarse_inverse": "f32x2"}
-
+DIGIT_PAIRS = 28
+BF16_PEAK_KEY = "bf16_tflops"
+# tensor-pipe activity (sm__pipe_tensor_cycles_active, % of the active SMs' cycles) of the tensor-core
+# kernels in one ncu capture on the 48^3 case (profiles/); DRAM traffic per launch is not scaled to
+# the 96^3 launches, whose active subdomains change from cycle to cycle (traffic null)
+NCU_TENSOR_ACTIVE = {"lu_splitting": 0.074, "eig_triangular_solves": 0.137}
 
 def parse_args():
     p = argparse.ArgumentParser()
@@ -460,18 +461,25 @@ def roofline_entry(name: str, launches: int, ms: float, work: float, hbm_peak, f
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     ach = work / launches / (per_launch_ms * 1e-3) / 1e12 if launches else None
     dt = MIXED_KERNEL_DTYPE.get(name, "f64") if fp32 else "f64"
+    if dt == "f32x2-tc":
+        bf16 = measured_peaks().get(BF16_PEAK_KEY)
+        peak = bf16 / DIGIT_PAIRS if bf16 else None
+        return {"kernel": name, "bound": "tensor", "dtype": "f32x2 as BF16 digit products", "achieved": ach,
+                "peak": peak, "unit": "TFLOP/s", "frac": (ach / peak) if (ach and peak) else None, "traffic": None,
+                "launches": launches, "avg_launch_ms": per_launch_ms,
+                "peak_source": f"measured bf16 (MEASURED_PEAKS.json {BF16_PEAK_KEY}) / {DIGIT_PAIRS} digit-pair products "
+                               "per double-float product (algorithmic double-float flops)",
+                "frac_of_fp32_pipe_double_float_peak": (ach / FP32X2_PEAK_TFLOPS_DERIVED) if ach else None,
+                "tensor_pipe_active_ncu": NCU_TENSOR_ACTIVE.get(name)}
     if dt == "f32":
         peak, src = FP32_PEAK_TFLOPS_DERIVED, "FP32 SIMT peak from unit counts x 2.07 GHz"
     elif dt == "f32x2":
         peak, src = FP32X2_PEAK_TFLOPS_DERIVED, "FP32 SIMT lane rate x 2.07 GHz / 12 instructions per double-float FMA"
     else:
         peak, src = FP64_PEAK_TFLOPS_NOMINAL, "nominal FP64 SIMT rate of the pool's recipe table"
-    per_sub = NCU_TRAFFIC_PER_SUBDOMAIN.get(name) if fp32 else None
-    traffic = per_sub * subdomains if (per_sub and subdomains) else None
     return {"kernel": name, "bound": "alu", "dtype": dt, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": (ach / peak) if ach else None, "traffic": traffic,
+            "frac": (ach / peak) if ach else None, "traffic": None,
             "launches": launches, "avg_launch_ms": per_launch_ms, "peak_source": src}
-
 
 def report(args, res, world) -> dict:
     prob = res["prob"]

@@ -33,9 +33,12 @@ def test_roofline_entry_arithmetic():
     assert e["bound"] == "alu" and e["dtype"] == "f32x2"
     assert e["achieved"] == pytest.approx(1000.0)
     assert e["frac"] == pytest.approx(1000.0 / bench.FP32X2_PEAK_TFLOPS_DERIVED)
-    # traffic: per subdomain from the capture, times the subdomains of the launch; none without one
+    # the tensor-core double-float kernels: the measured BF16 peak over the 28 digit-pair products
     e = bench.roofline_entry("eig_triangular_solves", 3, 6.0, 6e12, 6780.0, subdomains=256)
-    assert e["traffic"] == pytest.approx(bench.NCU_TRAFFIC_PER_SUBDOMAIN["eig_triangular_solves"] * 256)
+    assert e["bound"] == "tensor" and e["traffic"] is None
+    bf16 = bench.measured_peaks().get(bench.BF16_PEAK_KEY)
+    if bf16:
+        assert e["peak"] == pytest.approx(bf16 / 28) and e["frac"] == pytest.approx(1000.0 / (bf16 / 28))
     # the plain form's kernels use the FP64 peak
     e = bench.roofline_entry("coarse_lu", 1, 1.0, 1e9, 6780.0, fp32=False, subdomains=256)
     assert e["traffic"] is None and e["peak"] == bench.FP64_PEAK_TFLOPS_NOMINAL
