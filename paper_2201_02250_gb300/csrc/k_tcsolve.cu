@@ -156,13 +156,15 @@ __device__ __forceinline__ void split_columns(const dfloat* S, unsigned char* ds
   }
 }
 
-// The 112 MMAs of one tile product (A digits at a, B digits at b) into TMEM buffer `buf`, then a commit:
-// pair (i, j) of digits, M = 64, N = 32, into the block of its weight i + j (weights 4 to 6 share the
-// last block).  The blocks of weight 0 to 3 stay below 2^24 units of their weight over 64 terms and are
-// exact; the shared last block rounds at 2^-56 of the result.  The first product into a block is the
-// pair (0, j) with j its first weight; it overwrites the block.
+// The 112 MMAs of one tile product (A digits at a, B digits at b) into TMEM buffer `buf`: pair (i, j) of
+// digits, M = 64, N = 32, into the block of its weight i + j (weights 4 to 6 share the last block).  The
+// blocks of weight 0 to 3 stay below 2^24 units of their weight over 64 terms and are exact; the shared
+// last block rounds at 2^-56 of the result.  Two threads of different warps issue in parallel, each for
+// its own blocks (part 0: weights 0-3, 40 MMAs; part 1: weights 4-6, 72 MMAs), then each commits to the
+// barrier (initialised for two arrivals).  The first product into a block, pair (0, j) with j its
+// first weight, overwrites it; the MMAs of one issuing thread run in order.
 __device__ __forceinline__ void issue_mmas(uint32_t tmem, int buf, const unsigned char* a, const unsigned char* bsm,
-                                           uint64_t* bar) {
+                                           uint64_t* bar, int part) {
   constexpr uint32_t idesc = tc::idesc_bf16_f32(M, NC);
   const uint32_t a0 = tc::smem_u32(a), b0 = tc::smem_u32(bsm);
   // descriptors of the first K-chunk of plane 0; the others differ only in the start address field
@@ -171,6 +173,7 @@ __device__ __forceinline__ void issue_mmas(uint32_t tmem, int buf, const unsigne
   for (int i = 0; i < NDIG; ++i)
 #pragma unroll
     for (int j = 0; j < NDIG - i; ++j) {
+      if ((i + j >= NBLK - 1) != (part == 1)) continue;
 #pragma unroll
       for (int kk = 0; kk < K / 16; ++kk)
         tc::mma_bf16(tmem + buf * BUF_COLS + (i + j < NBLK ? i + j : NBLK - 1) * NC,
@@ -227,9 +230,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_solve_tc(
   if (p < 1 || p > NC) return;
   const int n = ni[i], nb = (n + M - 1) / M;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (tid == 0) {
-    tc::mbar_init(&bar[0], 1);
-    tc::mbar_init(&bar[1], 1);
+  if (tid == 0) {   // two arrivals per phase: the two MMA-issuing threads commit separately
+    tc::mbar_init(&bar[0], 2);
+    tc::mbar_init(&bar[1], 2);
   }
   if (warp == 0) {
     tc::tmem_alloc(&tbase, TMEM_COLS);
@@ -294,7 +297,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_solve_tc(
         if (tid < M) sexpA[tt & 1][tid] = reinterpret_cast<const int*>(sp + NDIG * A_PLANE)[tid];
         else if (tid < M + NC) sexpB[tt & 1][tid - M] = reinterpret_cast<const int*>(sp + A_TILE + NDIG * B_PLANE)[tid - M];
       }
-      if (tid == 0) issue_mmas(tmem, tt & 1, stage[tt & 1], stage[tt & 1] + A_TILE, &bar[tt & 1]);
+      if (tid == 0 || tid == 32) issue_mmas(tmem, tt & 1, stage[tt & 1], stage[tt & 1] + A_TILE, &bar[tt & 1], tid >> 5);
       __syncwarp();
       if (tt > 0) {
         const int u = (tt - 1) & 1;
@@ -337,7 +340,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_block_solve_tc(
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (tid == 0) issue_mmas(tmem, 0, stage[0], stage[0] + A_TILE, &bar[0]);
+    if (tid == 0 || tid == 32) issue_mmas(tmem, 0, stage[0], stage[0] + A_TILE, &bar[0], tid >> 5);
     __syncwarp();
     ok = __syncthreads_and(wait_mma(0)) != 0;
     if (!ok) break;
