@@ -135,6 +135,10 @@ typedef struct {
   int32_t tensor_cores;     /* 1 (default): the trailing updates of the double-float LU run on the tensor
                                cores (BF16 digit products accumulated exactly in FP32, to double-float
                                accuracy); 0: on the FP32 pipe */
+  int32_t eig_thick_restart; /* 1 (default): a restart of the local eigensolves keeps the block of Ritz
+                               vectors together with its image under the operator, so that a restarted
+                               cycle spans the same block Krylov space with one block application fewer;
+                               0: explicit restart from the Ritz vectors alone */
 } a2ls_options;
 
 /* Fills *opt with the defaults listed above.  Never fails. */

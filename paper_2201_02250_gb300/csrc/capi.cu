@@ -361,6 +361,7 @@ void a2ls_default_options(a2ls_options* o) {
   o->eig_strict = 0;
   o->eig_stall_cycles = 8;
   o->tensor_cores = 1;
+  o->eig_thick_restart = 1;
 }
 
 const char* a2ls_last_error(void) { return g_last_error.c_str(); }

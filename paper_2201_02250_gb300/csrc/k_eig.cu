@@ -565,14 +565,15 @@ __device__ int warp_cholesky_inverse(double* G, int p, double* Ri, double* dsc, 
 
 // Orthogonalisation: block CGS2 of W against V[:, 0:jb], then Cholesky QR three times (the first
 // shifted).  Writes the Gram coefficients into H[0:jb, hc:hc+p] and R into H[hr:hr+p, hc:hc+p] and
-// the orthonormal block into V[:, vout:vout+p].  full != 0: only H[0:jb, hc:hc+p].
+// the orthonormal block into V[:, vout:vout+p].  full != 0: only H[0:jb, hc:hc+p].  illcond (if given):
+// set to 1 for a subdomain whose block needed the shifted factorisation (an ill-conditioned block).
 // Shared memory: G and Ri (gcap doubles each), trow, two staging chunks of orc x EIG_MAXP.
 template <class T, class TW>
 __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int64_t* xoff, int ldx,
                                                         const int* pvec, const int* active, int jb_blocks,
                                                         int bcols, T* V, TW* W, double* H, int hr, int hc,
                                                         int vout, const int* fullv, int* rank_flag, int gcap,
-                                                        int orc) {
+                                                        int orc, int* illcond) {
   using Acc = typename EAcc<T>::type;
   extern __shared__ __align__(16) double sm[];
   const int i = blockIdx.x;
@@ -653,6 +654,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
         retry_shifted = (pass == 0 && !shifted && !(ok && ratio > plain_ratio)) ? 1 : 0;
         rank_ok = ok;
         if (!ok && !retry_shifted && rank_flag) atomicAdd(rank_flag + i, 1);
+        if (retry_shifted && illcond) illcond[i] = 1;
       }
     }
     __syncthreads();
@@ -735,15 +737,17 @@ struct RRParams {
   double tol;
   int nevmax;      // slots per subdomain in the eigenvalue export
   double tau;      // > 0: keep only |lambda| > 1 / tau (Eq. 3.2), at most nev
+  double thick_spread;  // > 0: a thick restart is allowed while |theta_1| <= thick_spread |theta_b|
 };
 
 template <class R>
 __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull, const int* nf,
                                 const int* active, const double* H, double* Y, int* ycols, int* zcols,
-                                double* eigout, int* conv, double* worst, int* st) {
+                                double* eigout, int* conv, double* worst, int* illcond, int* thick, int* st) {
   extern __shared__ double sm[];
   const int i = blockIdx.x;
   if (active && !active[i]) return;
+  if (threadIdx.x == 0) thick[i] = 0;
   if (nf[i] <= 0) {
     if (threadIdx.x == 0) {
       conv[i] = 1;
@@ -843,6 +847,12 @@ __global__ void k_rayleigh_ritz(RRParams prm, const int* full, const int* mfull,
     nsel_s = nsel;
     ncol_s = col;
     zc_s = zc;
+    // thick restart (Krylov mode): the Arnoldi relation it carries over holds to about u |theta_1|
+    // (absolute); it is used while that stays far below the kept Ritz values' tolerance and no block of
+    // this cycle was ill-conditioned, otherwise the next restart is explicit
+    const bool spread_ok = nsel > 0 && mod[perm[0]] <= prm.thick_spread * mod[sel_pos[nsel - 1]];
+    thick[i] = (!full[i] && col == bc && spread_ok && !illcond[i]) ? 1 : 0;
+    illcond[i] = 0;
   }
   __syncthreads();
   const int nsel = nsel_s;
@@ -998,6 +1008,155 @@ __global__ void k_final_z(const int* ni, const int* off, const int64_t* xoff, in
 }
 
 // ---------------------------------------------------------------------------
+// Thick restart of the block Krylov iteration.  A cycle ends with T V_m = V_{m+b} Hb, Hb = H[0:m+b, 0:m]
+// (m = s b).  With Q an orthonormal basis of the kept Ritz coefficients Y[0:m, 0:b],
+//     T (V_m Q) = V_{m+b} Hb Q = (V_m Q) G + V_{m+b} E,   G = Q^T Hb[0:m] Q,   E = Hb Q - [Q; 0] G,
+// and E = Q2 R2 with Q2 orthonormal and orthogonal to [Q; 0].  The restarted basis is
+// V' = V_{m+b} U, U = [[Q; 0], Q2] (2b columns), and the first block column of H becomes [G; R2], so the
+// block Arnoldi relation T V'_0 = V'_0 G + V'_1 R2 holds and the cycle goes on with block step 1: the
+// space it builds is the block Krylov space of V_m Q that an explicit restart from V_m Q builds, with
+// one application of T fewer per cycle.  No invariance of span Q is assumed (a complex pair cut at the
+// block edge keeps its real part only).
+// One CTA per subdomain, FP64.  Writes U ((m+b) x 2b, stride EIG_MAXP) into Uout and H[0:m+b, 0:m]
+// (zero but for [G; R2] in the first block column).
+constexpr int TR_THREADS = 128;  // >= m + b (at most EIG_MAXP)
+
+__device__ double tr_cta_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();  // red may still be read by the previous call
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+// Column c of U (mb rows, stride ld) orthogonalised against columns 0..c-1 by classical Gram-Schmidt:
+// at least two passes, more (up to four) while a pass removes more than half of the norm.  The
+// coefficients are added to coef[0..c-1] (if given).  *n0: the norm before; returns the norm after
+// (the column is not normalised), negative when the fourth pass still cancelled (numerically
+// dependent).  Whole CTA; mb <= blockDim.x.
+__device__ double tr_orth_column(double* U, int ld, int mb, int c, double* coef, double* dots, double* red,
+                                 double* n0) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  double x = tid < mb ? U[tid * ld + c] : 0.0;
+  double nrm = sqrt(tr_cta_sum(x * x, red));
+  *n0 = nrm;
+  if (c == 0) return nrm;
+  for (int pass = 0; pass < 4; ++pass) {
+    for (int k = wid; k < c; k += nw) {
+      double d = 0.0;
+      for (int a = lane; a < mb; a += 32) d += U[a * ld + k] * U[a * ld + c];
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (lane == 0) dots[k] = d;
+    }
+    __syncthreads();
+    if (tid < mb) {
+      double v = U[tid * ld + c];
+      for (int k = 0; k < c; ++k) v -= dots[k] * U[tid * ld + k];
+      U[tid * ld + c] = v;
+      x = v;
+    }
+    if (coef && tid < c) coef[tid] += dots[tid];
+    const double nn = sqrt(tr_cta_sum(x * x, red));
+    const bool again = pass == 0 || nn < 0.5 * nrm;
+    nrm = nn;
+    if (!again) return nrm;
+  }
+  return -nrm;
+}
+
+__global__ void __launch_bounds__(TR_THREADS) k_thick_restart(const int* active, int m, int b, const double* Y,
+                                                           double* H, double* Uout, int* st) {
+  extern __shared__ double sm[];
+  const int i = blockIdx.x;
+  if (active && !active[i]) return;
+  const int tid = threadIdx.x, mb = m + b, ld = 2 * b;
+  double* U = sm;              // mb x 2b
+  double* Gs = U + mb * ld;    // b x b
+  double* R2 = Gs + b * b;     // b x b
+  double* coef = R2 + b * b;   // 2b
+  double* dots = coef + ld;    // 2b
+  __shared__ double red[TR_THREADS / 32];
+  const double* Yi = Y + (int64_t)i * EIG_MAXP * EIG_MAXP;
+  double* Hi = H + (int64_t)i * EIG_MAXP * EIG_MAXP;
+  double* Ui = Uout + (int64_t)i * EIG_MAXP * EIG_MAXP;
+  for (int e = tid; e < mb * b; e += blockDim.x) {
+    const int a = e / b, c = e % b;
+    U[a * ld + c] = a < m ? Yi[a * EIG_MAXP + c] : 0.0;
+  }
+  for (int e = tid; e < 2 * b * b; e += blockDim.x) Gs[e] = 0.0;  // Gs and R2
+  __syncthreads();
+  // Q: a column (numerically) dependent on the ones before it is replaced by the first unit vector
+  // e_r (r < m) that is not
+  int cand = 0;
+  for (int c = 0; c < b; ++c) {
+    double n0 = 0.0;
+    double nrm = tr_orth_column(U, ld, mb, c, nullptr, dots, red, &n0);
+    while (!(nrm > 1e-12 * n0) && cand < m) {
+      if (tid < mb) U[tid * ld + c] = (tid == cand) ? 1.0 : 0.0;
+      ++cand;
+      nrm = tr_orth_column(U, ld, mb, c, nullptr, dots, red, &n0);
+    }
+    if (!(nrm > 0.0)) {
+      if (tid == 0) raise_status(st, A2LS_ERR_EIGEN, i, 5);
+      return;  // uniform: every thread holds the same norm
+    }
+    if (tid < mb) U[tid * ld + c] /= nrm;
+  }
+  __syncthreads();
+  // Hb Q into U[:, b:2b]
+  for (int e = tid; e < mb * b; e += blockDim.x) {
+    const int a = e / b, c = e % b;
+    const double* Ha = Hi + a * EIG_MAXP;
+    double sum = 0.0;
+    for (int k = 0; k < m; ++k) sum += Ha[k] * U[k * ld + c];
+    U[a * ld + b + c] = sum;
+  }
+  __syncthreads();
+  // G and R2 by Gram-Schmidt of Hb Q against [Q; 0] and the second block's earlier columns.  Any
+  // remainder the Gram-Schmidt passes leave orthogonal is kept, however small (a nearly exact Ritz
+  // vector has a tiny one: its direction is then arbitrary, and R2's diagonal entry keeps the relation
+  // exact).  Only a remainder that four passes keep cancelling (rounding noise) or an exact zero is
+  // dropped: R2's diagonal entry 0, the column replaced by a unit vector, the residual rows first.
+  // No threshold scales with |Hb|: one huge Ritz value (a nearly singular splitting) would then
+  // drop the residuals of all the others.
+  int cand2 = 0;
+  for (int c = 0; c < b; ++c) {
+    __syncthreads();  // coef of the previous column read
+    if (tid < ld) coef[tid] = 0.0;
+    __syncthreads();
+    double n0 = 0.0;
+    double nrm = tr_orth_column(U, ld, mb, b + c, coef, dots, red, &n0);
+    if (tid < b) Gs[tid * b + c] = coef[tid];
+    if (tid < c) R2[tid * b + c] = coef[b + tid];
+    if (nrm > 0.0) {
+      if (tid == 0) R2[c * b + c] = nrm;
+    } else {
+      while (!(nrm > 1e-12 * n0) && cand2 < mb) {
+        const int r = cand2 < b ? m + cand2 : cand2 - b;
+        if (tid < mb) U[tid * ld + b + c] = (tid == r) ? 1.0 : 0.0;
+        ++cand2;
+        nrm = tr_orth_column(U, ld, mb, b + c, nullptr, dots, red, &n0);
+      }
+      if (!(nrm > 0.0)) {
+        if (tid == 0) raise_status(st, A2LS_ERR_EIGEN, i, 5);
+        return;
+      }
+    }
+    if (tid < mb) U[tid * ld + b + c] /= nrm;
+  }
+  __syncthreads();
+  for (int e = tid; e < mb * ld; e += blockDim.x) Ui[(e / ld) * EIG_MAXP + e % ld] = U[e];
+  for (int e = tid; e < mb * m; e += blockDim.x) {
+    const int a = e / m, c = e % m;
+    double v = 0.0;
+    if (c < b) v = a < b ? Gs[a * b + c] : (a < 2 * b ? R2[(a - b) * b + c] : 0.0);
+    Hi[a * EIG_MAXP + c] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // driver
 // ---------------------------------------------------------------------------
 // T: the factors of A~_ii and the applications of T; TV: the Krylov basis and its orthogonalisation
@@ -1132,6 +1291,23 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   A2LS_CUDA(cudaFuncSetAttribute(k_orth<TV, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)orth_smem));
   A2LS_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rr_smem));
   A2LS_CUDA(cudaFuncSetAttribute(k_vy<TV, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vy_smem));
+  A2LS_CUDA(cudaFuncSetAttribute(k_vy<TV, TV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vy_smem));
+  // thick restart (needs a block step after the kept block: s >= 2)
+  const bool thick = h->opt.eig_thick_restart != 0 && s >= 2;
+  const size_t tr_smem = sizeof(double) * ((size_t)(s + 1) * b * 2 * b + 2 * (size_t)b * b + 4 * (size_t)b);
+  A2LS_CUDA(cudaFuncSetAttribute(k_thick_restart, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tr_smem));
+  int* d_illcond = dalloc<int>(h, N);  // per cycle: a block step needed the shifted factorisation
+  int* d_thick = dalloc<int>(h, N);    // per cycle: the next restart may be thick
+  A2LS_CUDA(cudaMemsetAsync(d_illcond, 0, sizeof(int) * N, st));
+  A2LS_CUDA(cudaMemsetAsync(d_thick, 0, sizeof(int) * N, st));
+  int* d_mb = dalloc<int>(h, N);  // rows of U: (s + 1) b
+  int* d_b2 = dalloc<int>(h, N);  // columns of U: 2 b
+  {
+    std::vector<int> mbv(N, (s + 1) * b), b2v(N, 2 * b);
+    A2LS_CUDA(cudaMemcpyAsync(d_mb, mbv.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    A2LS_CUDA(cudaMemcpyAsync(d_b2, b2v.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    A2LS_CUDA(cudaStreamSynchronize(st));
+  }
 
   // T applied to V[:, vcol : vcol + p] -> W[:, 0:p]; fwd/bwd_flops: the two triangular halves over the
   // active set, counted inside the envelope of the factors
@@ -1206,7 +1382,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     // no previous basis: jb = 0; R written into H's last rows (discarded)
     k_orth<TV, T><<<N, ORTH_THREADS, orth_smem_for(gcap_k), st>>>(h->d_ni, d_vo, P, d_pv, actv, 0, b, V, W,
                                                                   Rscr, 0, 0, 0, nullptr, d_rank, gcap_k,
-                                                                  orc_for(gcap_k));
+                                                                  orc_for(gcap_k), nullptr);
     A2LS_LAUNCH();
   };
 
@@ -1232,16 +1408,20 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   // V, W, H and Y.  With per-kernel timing on, one group on the handle's stream keeps the kernels'
   // times free of overlap.
   const int ngroups = h->opt.timing ? 1 : 2;
-  RRParams prm{s * b, b, s, tol, nevmax, h->opt.tau};
+  // thick restarts while u |theta_1| stays below 1e-2 tol |theta_b| with a margin of 64 for the rounding
+  // of the block steps
+  RRParams prm{s * b, b, s, tol, nevmax, h->opt.tau, thick ? 1e-2 * tol / (64.0 * Unit<T>::u) : 0.0};
   const int max_cycles = h->opt.eig_max_cycles > 0 ? h->opt.eig_max_cycles : 60;
   const int stall_cycles = h->opt.eig_stall_cycles;
   std::vector<int> cycles(N, 0), best_cycle(N, 0), stalled(N, 0);
   std::vector<double> best(N, INFINITY), worst(N, 0.0);
   struct Group {
-    std::vector<int> act, actk;
+    std::vector<int> act, actk, thk, exl;  // exl/thk: restarted explicitly / thick
     int* d_act = nullptr;
     int* d_actk = nullptr;
-    int* h_conv = nullptr;  // pinned: N flags, then the status words
+    int* d_thk = nullptr;
+    int* d_exl = nullptr;
+    int* h_conv = nullptr;  // pinned: N convergence flags, N thick-restart flags, then the status words
     double* h_worst = nullptr;  // pinned: N worst relative residuals of the wanted Ritz pairs
     cudaStream_t s = nullptr;
     cudaEvent_t done = nullptr;
@@ -1283,7 +1463,11 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     for (int i = g; i < N; i += ngroups) G.act[i] = act[i];
     G.d_act = dalloc<int>(h, N);
     G.d_actk = dalloc<int>(h, N);
-    A2LS_CUDA(cudaMallocHost(&G.h_conv, sizeof(int) * (N + ST_WORDS)));
+    G.thk.assign(N, 0);
+    G.exl.assign(N, 0);
+    G.d_thk = dalloc<int>(h, N);
+    G.d_exl = dalloc<int>(h, N);
+    A2LS_CUDA(cudaMallocHost(&G.h_conv, sizeof(int) * (2 * N + ST_WORDS)));
     A2LS_CUDA(cudaMallocHost(&G.h_worst, sizeof(double) * N));
     A2LS_CUDA(cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming));
     A2LS_CUDA(cudaMemcpyAsync(G.d_act, G.act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
@@ -1294,14 +1478,9 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     h->st = s2;
   };
   // one cycle of group g: s block steps, Rayleigh-Ritz, then the flags and status copied to the host
-  auto queue_cycle = [&](int g) {
-    Group& G = grp[g];
-    use_stream(G.s);
-    for (int i = 0; i < N; ++i) G.actk[i] = G.act[i] && !full[i];
-    A2LS_CUDA(cudaMemcpyAsync(G.d_actk, G.actk.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
-    for (int j = 0; j < s; ++j) {
-      const int* actv = (j == 0) ? G.d_act : G.d_actk;
-      const std::vector<int>& acth = (j == 0) ? G.act : G.actk;
+  // j0 = 1 after a thick restart: block 0 and block 1 of V and H's first block column are in place
+  // block step j over the subdomains actv (acth on the host): T V_j, orthogonalised -> V_{j+1}, H
+  auto block_step = [&](int j, const int* actv, const std::vector<int>& acth) {
       fwd_flops = bwd_flops = 0.0;
       double orth_flops = 0.0;
       for (int i = 0; i < N; ++i) {
@@ -1319,9 +1498,20 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
         const int gcap = (j == 0) ? gcap_f : gcap_k;
         k_orth<TV, T><<<N, ORTH_THREADS, orth_smem_for(gcap), st>>>(h->d_ni, d_vo, P, d_pv, actv, j + 1, b, V, W, H,
                                                       (j + 1) * b, j * b, (j + 1) * b, d_full, d_rank, gcap,
-                                                      orc_for(gcap));
+                                                      orc_for(gcap), d_illcond);
         A2LS_LAUNCH();
       }
+  };
+  auto queue_cycle = [&](int g, int j0) {
+    Group& G = grp[g];
+    use_stream(G.s);
+    for (int i = 0; i < N; ++i) G.actk[i] = G.act[i] && !full[i];
+    A2LS_CUDA(cudaMemcpyAsync(G.d_actk, G.actk.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    for (int j = j0; j < s; ++j) {
+      if (j == 0)
+        block_step(j, G.d_act, G.act);
+      else
+        block_step(j, G.d_actk, G.actk);
     }
     {
       // algorithmic work: a real Schur form with its orthogonal factor (25 m^3, the usual count for
@@ -1334,22 +1524,23 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
       }
       KTime kt(h, KT_EIG_RR, rr_flops);
       k_rayleigh_ritz<RT><<<N, RR_THREADS, rr_smem, st>>>(prm, d_full, d_mfull, d_nf, G.d_act, H, Y, d_ycols, d_zcols,
-                                              eigout, d_conv, d_worst, h->d_status);
+                                              eigout, d_conv, d_worst, d_illcond, d_thick, h->d_status);
       A2LS_LAUNCH();
     }
     A2LS_CUDA(cudaMemcpyAsync(G.h_conv, d_conv, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
-    A2LS_CUDA(cudaMemcpyAsync(G.h_conv + N, h->d_status, sizeof(int) * ST_WORDS, cudaMemcpyDeviceToHost, st));
+    A2LS_CUDA(cudaMemcpyAsync(G.h_conv + N, d_thick, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+    A2LS_CUDA(cudaMemcpyAsync(G.h_conv + 2 * N, h->d_status, sizeof(int) * ST_WORDS, cudaMemcpyDeviceToHost, st));
     A2LS_CUDA(cudaMemcpyAsync(G.h_worst, d_worst, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
     A2LS_CUDA(cudaEventRecord(G.done, st));
   };
-  for (int g = 0; g < ngroups; ++g) queue_cycle(g);
+  for (int g = 0; g < ngroups; ++g) queue_cycle(g, 0);
   if (ngroups == 1) grp[1].finished = true;
   while (!grp[0].finished || !grp[1].finished) {
     for (int g = 0; g < ngroups; ++g) {
       Group& G = grp[g];
       if (G.finished) continue;
       A2LS_CUDA(cudaEventSynchronize(G.done));
-      if (G.h_conv[N + ST_CODE] != 0) sync_and_check(h, "local eigensolve");  // raises the recorded error
+      if (G.h_conv[2 * N + ST_CODE] != 0) sync_and_check(h, "local eigensolve");  // raises the recorded error
       int remaining = 0;
       for (int i = g; i < N; i += ngroups) {
         if (G.act[i]) {
@@ -1381,11 +1572,32 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
       ++G.cycle;
       use_stream(G.s);
       A2LS_CUDA(cudaMemcpyAsync(G.d_act, G.act.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
-      // restart block: W = V[:, 0:sb] Y[:, 0:b]
-      k_vy<TV, T><<<N, EIG_THREADS, vy_smem, st>>>(h->d_ni, d_vo, P, d_msb, d_pv, G.d_act, V, Y, W);
-      A2LS_LAUNCH();
-      orthonormalize_W_into_V0(G.d_act);
-      queue_cycle(g);
+      // thick restart where the Rayleigh-Ritz step allowed it, explicit restart elsewhere
+      int nthk = 0, nexl = 0;
+      for (int i = 0; i < N; ++i) {
+        G.thk[i] = G.act[i] && thick && G.h_conv[N + i];
+        G.exl[i] = G.act[i] && !G.thk[i];
+        nthk += G.thk[i];
+        nexl += G.exl[i];
+      }
+      if (nthk) {
+        // V[:, 0:2b] = V[:, 0:(s+1)b] U in place, H's first block column [G; R2]
+        A2LS_CUDA(cudaMemcpyAsync(G.d_thk, G.thk.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+        k_thick_restart<<<N, TR_THREADS, tr_smem, st>>>(G.d_thk, s * b, b, Y, H, Rscr, h->d_status);
+        A2LS_LAUNCH();
+        k_vy<TV, TV><<<N, EIG_THREADS, vy_smem, st>>>(h->d_ni, d_vo, P, d_mb, d_b2, G.d_thk, V, Rscr, V);
+        A2LS_LAUNCH();
+      }
+      if (nexl) {
+        // explicit restart block: W = V[:, 0:sb] Y[:, 0:b], orthonormalised into V_0; with thick
+        // restarts elsewhere in the group, block step 0 of these subdomains runs here
+        A2LS_CUDA(cudaMemcpyAsync(G.d_exl, G.exl.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+        k_vy<TV, T><<<N, EIG_THREADS, vy_smem, st>>>(h->d_ni, d_vo, P, d_msb, d_pv, G.d_exl, V, Y, W);
+        A2LS_LAUNCH();
+        orthonormalize_W_into_V0(G.d_exl);
+        if (thick) block_step(0, G.d_exl, G.exl);
+      }
+      queue_cycle(g, thick ? 1 : 0);
     }
   }
   // both groups done: continue on the handle's stream after the second stream's work
