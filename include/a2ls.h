@@ -139,6 +139,12 @@ typedef struct {
                                vectors together with its image under the operator, so that a restarted
                                cycle spans the same block Krylov space with one block application fewer;
                                0: explicit restart from the Ritz vectors alone */
+  int32_t local_solve_kernel; /* 0 (default): the apply's local-solve kernel is picked by timing the
+                               candidates on the handle's own factors; otherwise that candidate:
+                               256, 512, 1024 (one-pass kernel, CTA width), 1256, 1512, 2256
+                               (pipelined kernel), 3000 / 3004 / 3008 (streaming kernel on the
+                               repacked factors: one CTA of 8 consumer warps, two of 4, two of 8 per
+                               SM; FP32 and BF16 factors only) */
 } a2ls_options;
 
 /* Fills *opt with the defaults listed above.  Never fails. */

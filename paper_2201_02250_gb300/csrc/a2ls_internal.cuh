@@ -60,6 +60,28 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 struct Phase { enum { SETUP_GRAPH, SETUP_EXTRACT, SETUP_LU, SETUP_EIG, SETUP_COARSE, SETUP_TOTAL,
                       SOLVE_TOTAL, SOLVE_APPLY, COUNT }; };
 
+// the apply's local factors repacked as one stream in solve order (k_stream.cu)
+struct StreamSolve {
+  bool ready = false;
+  int elem_bytes = 0, nchunks = 0, xcap = 0;
+  int64_t stream_elems = 0;
+  void* d_stream = nullptr;
+  int4* d_meta = nullptr;                    // chunk headers, each followed by its segment records
+  int *d_mpos = nullptr, *d_choff = nullptr;
+  int64_t* d_soff = nullptr;
+  // launch shapes: [0] 8 consumer warps, one CTA per SM; [1] 4 consumer warps, two CTAs per SM; [2] 8
+  // consumer warps, two CTAs per SM
+  struct Shape {
+    bool ready = false;
+    int ncta = 0, nstages = 0;
+    size_t smem = 0;
+    int *d_cta_off = nullptr, *d_cta_list = nullptr;   // static assignment of the subdomains to CTAs
+  } shape[3];
+};
+constexpr int LS_STREAM = 3000;   // local-solve configurations of the streaming kernel: shape 0
+constexpr int LS_STREAM2 = 3004;  // ... shape 1
+constexpr int LS_STREAM3 = 3008;  // ... shape 2
+
 }  // namespace a2ls
 
 struct a2ls_handle {
@@ -87,7 +109,8 @@ struct a2ls_handle {
                                              // overlap layer, and n_i
   int* d_sched = nullptr;                    // N: subdomains by decreasing size (work order)
   int* d_counter = nullptr;                  // work-queue counter of the persistent kernels
-  int ls_width = 0;                          // CTA width of the local solves (autotuned)
+  int ls_width = 0;                          // configuration of the local solves (autotuned)
+  a2ls::StreamSolve ss;                      // packed factors of the streaming local solves
   int sum_n = 0, max_n = 0;
   int max_rownnz = 0, max_memb = 0;          // largest row of A, largest membership count
   // node -> memberships (flat local positions off_i + l), sorted by subdomain
@@ -221,6 +244,12 @@ void tc_solve_release(a2ls_handle* h, TcSolve& ts);
 void tc_block_solve(a2ls_handle* h, const TcSolve& ts, dfloat* X, const int64_t* xoff, int col0, int ldx,
                     const int* pvec, const int* active, int forward, unsigned char* xdig = nullptr);
 constexpr int TC_SOLVE_MAX_P = 32;
+
+// k_stream.cu: pack the factors (after the diagonal tiles are inverted) into the stream of the
+// streaming local solves, and those solves (FP32 or BF16 factors)
+template <class T> void stream_prepare(a2ls_handle* h, const T* fac);
+template <class T> void launch_local_solve_stream(a2ls_handle* h, int config, const double* t, const double* q,
+                                                  double* z, int mode);
 
 // k_dense.cu: FP32 local factors rounded to the bfloat16 storage of A2LS_BF16, in the layout
 // h_fld / h_ffoff (which this call sets up); returns the new storage

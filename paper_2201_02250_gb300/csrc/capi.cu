@@ -362,6 +362,7 @@ void a2ls_default_options(a2ls_options* o) {
   o->eig_stall_cycles = 8;
   o->tensor_cores = 1;
   o->eig_thick_restart = 1;
+  o->local_solve_kernel = 0;
 }
 
 const char* a2ls_last_error(void) { return g_last_error.c_str(); }
@@ -401,6 +402,14 @@ int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int
       fail(A2LS_ERR_ARG, "unknown precision %d", o.precision);
     if (o.variant < 0 || o.variant > A2LS_ONE_LEVEL_ASM) fail(A2LS_ERR_ARG, "unknown variant %d", o.variant);
     if (o.pou != A2LS_POU_BOOLEAN && o.pou != A2LS_POU_MULTIPLICITY) fail(A2LS_ERR_ARG, "unknown partition of unity %d", o.pou);
+    {
+      const int k = o.local_solve_kernel;
+      if (k != 0 && k != 256 && k != 512 && k != 1024 && k != 1256 && k != 1512 && k != 2256 && k != LS_STREAM &&
+          k != LS_STREAM2 && k != LS_STREAM3)
+        fail(A2LS_ERR_ARG, "unknown local_solve_kernel %d", k);
+      if ((k == LS_STREAM || k == LS_STREAM2 || k == LS_STREAM3) && o.precision == A2LS_FP64)
+        fail(A2LS_ERR_ARG, "local_solve_kernel %d needs FP32 or BF16 local factors", k);
+    }
     h = new a2ls_handle();
     h->opt = o;
     h->st = static_cast<cudaStream_t>(o.stream);
@@ -461,6 +470,9 @@ int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int
       dfree(h, h->d_fac);
       h->d_fac = fb;
     }
+    // the factors repacked for the streaming local solves
+    if (o.precision == A2LS_BF16) stream_prepare<__nv_bfloat16>(h, static_cast<const __nv_bfloat16*>(h->d_fac));
+    else if (o.precision == A2LS_FP32) stream_prepare<float>(h, static_cast<const float*>(h->d_fac));
     // apply workspace
     h->d_q = dalloc<double>(h, h->n);
     h->d_t = dalloc<double>(h, h->n);
@@ -473,7 +485,13 @@ int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int
       double* scratch = mode == 0 ? h->d_q : h->d_yloc;
       const int timing = h->opt.timing;
       h->opt.timing = 0;
-      if (o.precision == A2LS_FP64) autotune_local_solves<double>(h, static_cast<double*>(h->d_fac), h->d_t, scratch, mode);
+      if ((o.local_solve_kernel == LS_STREAM && !h->ss.shape[0].ready) ||
+          (o.local_solve_kernel == LS_STREAM2 && !h->ss.shape[1].ready) ||
+          (o.local_solve_kernel == LS_STREAM3 && !h->ss.shape[2].ready))
+        fail(A2LS_ERR_ARG, "the streaming local solves of shape %d do not fit this device's shared memory",
+             o.local_solve_kernel);
+      if (o.local_solve_kernel > 0) h->ls_width = o.local_solve_kernel;
+      else if (o.precision == A2LS_FP64) autotune_local_solves<double>(h, static_cast<double*>(h->d_fac), h->d_t, scratch, mode);
       else if (o.precision == A2LS_BF16)
         autotune_local_solves<__nv_bfloat16>(h, static_cast<__nv_bfloat16*>(h->d_fac), h->d_t, scratch, mode);
       else autotune_local_solves<float>(h, static_cast<float*>(h->d_fac), h->d_t, scratch, mode);

@@ -926,7 +926,9 @@ static void launch_local_solve(a2ls_handle* h, const T* fac, const double* t, co
 
 // configurations of the local solves the autotuner chooses from: 256 / 512 / 1024 = the one-pass kernel
 // with that CTA width; 1256 / 1512 / 2256 = the pipelined kernel with 256 or 512 threads and two
-// (1xxx) or four (2xxx) vector loads per row in flight
+// (1xxx) or four (2xxx) vector loads per row in flight; 3000 / 3004 / 3008 = the streaming kernel on
+// the packed factors (FP32 and BF16 factors) with 8 consumer warps and one CTA per SM / 4 consumer
+// warps and two CTAs per SM / 8 consumer warps and two CTAs per SM
 template <class T>
 static void launch_local_solve_width(a2ls_handle* h, int width, const T* fac, const double* t, const double* q,
                                      double* z, int mode) {
@@ -936,6 +938,14 @@ static void launch_local_solve_width(a2ls_handle* h, int width, const T* fac, co
     case 1256: launch_local_solve2<T, 256, 2>(h, fac, t, q, z, mode); break;
     case 1512: launch_local_solve2<T, 512, 2>(h, fac, t, q, z, mode); break;
     case 2256: launch_local_solve2<T, 256, 4>(h, fac, t, q, z, mode); break;
+    case LS_STREAM:
+    case LS_STREAM2:
+    case LS_STREAM3:
+      if constexpr (!std::is_same<T, double>::value) {
+        launch_local_solve_stream<T>(h, width, t, q, z, mode);
+        break;
+      }
+      [[fallthrough]];
     default: launch_local_solve<T, 512>(h, fac, t, q, z, mode); break;
   }
 }
@@ -959,14 +969,20 @@ void local_solves(a2ls_handle* h, const T* fac, const double* t, const double* q
 template <class T>
 void autotune_local_solves(a2ls_handle* h, const T* fac, const double* t, double* scratch, int mode) {
   char key[128];
-  snprintf(key, sizeof(key), "local_solve2_%s_N%d_max%d_mode%d",
+  snprintf(key, sizeof(key), "local_solve3_%s_N%d_max%d_mode%d",
            sizeof(T) == 8 ? "fp64" : (sizeof(T) == 4 ? "fp32" : "bf16"), h->N, h->max_n, mode);
   int cached = autotune_lookup(key);
-  if (cached > 0) {
+  if (cached > 0 && (cached != LS_STREAM || h->ss.shape[0].ready) && (cached != LS_STREAM2 || h->ss.shape[1].ready) &&
+      (cached != LS_STREAM3 || h->ss.shape[2].ready)) {
     h->ls_width = cached;
     return;
   }
-  const int widths[6] = {256, 512, 1024, 1256, 1512, 2256};
+  std::vector<int> widths = {256, 512, 1024, 1256, 1512, 2256};
+  if (!std::is_same<T, double>::value) {
+    if (h->ss.shape[0].ready) widths.push_back(LS_STREAM);
+    if (h->ss.shape[1].ready) widths.push_back(LS_STREAM2);
+    if (h->ss.shape[2].ready) widths.push_back(LS_STREAM3);
+  }
   float best_ms = 1e30f;
   int best = 512;
   cudaEvent_t e0, e1;

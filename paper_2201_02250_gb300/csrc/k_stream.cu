@@ -1,0 +1,633 @@
+// Streaming local solves of the apply: z_i = inv(U_i) inv(L_i) R_i r for every subdomain (the local
+// solves of the deflated RAS apply, Eq. 2.4), organised so that the factor bytes flow from HBM at the
+// copy engine's rate while the dependent triangular-solve chain runs on the SMs.
+//
+// Apply format.  After the factorisation the block-inverted LU factors of each subdomain are packed
+// once into one contiguous stream in the order the solves consume them:
+//   forward, block b = 0 .. nb-1:   LP  rows r of the block: L[r][f_r .. r0)         (row envelope)
+//                                   LD  row rr of inv(L_bb): columns r0 .. r0 + rr   (strictly lower)
+//   backward, block b = nb-1 .. 0:  UD  row rr of inv(U_bb): columns r0 + rr .. r0 + 64
+//                                   UP  column c of the block: U[g_c .. r0)[c]       (column envelope,
+//                                       stored as a row of U^T)
+// Every segment starts and ends on a 16-byte boundary (its column range rounded outwards; the entries
+// added are exact zeros).  U is kept by columns because its column envelope is the compact one (for
+// the layer-ordered overlapping subdomains a row-wise envelope of U holds twice the entries); the
+// backward sweep is therefore right-looking: once x_b is known, every earlier row r receives
+// -U[r][c] x_c from the columns c of block b.
+// Consecutive segments of one kind and block are grouped into chunks of at most 32 KB and 64
+// segments; a chunk is one contiguous byte range of the stream.  The UP columns of a block are laid
+// out by increasing first row.
+//
+// Kernel.  One CTA per SM, persistent over a static largest-first (LPT) assignment of the subdomains.
+// One producer warp streams the chunks through a ring of shared-memory stages with bulk asynchronous
+// copies (cp.async.bulk, completion counted in bytes on an mbarrier per stage); each stage also
+// receives the chunk's header and segment records, so that the consumers read no global memory but
+// the right-hand side and their outputs.  Eight consumer warps run the solves from shared memory:
+// the panel products, the 64 x 64 triangle products of the diagonal blocks and the right-looking
+// updates, with the gathered right-hand side and the solution held in shared memory.  The producer
+// runs ahead across block and subdomain boundaries, so the loads never wait for the solve chain.
+// Every wait is bounded; a wait that gives up records A2LS_ERR_TIMEOUT and the CTA leaves after its
+// copies in flight have landed.
+#include "a2ls_internal.cuh"
+#include "tc_sm100.cuh"
+
+#include <algorithm>
+#include <queue>
+
+namespace a2ls {
+namespace lss {
+
+constexpr int STAGE_DATA = 32768;                // factor bytes per stage
+constexpr int STAGE_RECS = 64;                   // segment records per chunk at most (one 64-row block)
+constexpr int STAGE_META = 16 * (1 + STAGE_RECS);  // chunk header and its records (16 bytes each)
+constexpr int STAGE_BYTES = STAGE_META + STAGE_DATA;
+constexpr int MAX_STAGES = 8;
+constexpr long WAIT_LIMIT = 1L << 26;            // polls of an mbarrier before giving up
+enum { LP = 0, LD = 1, UD = 2, UP = 3 };
+
+template <class T> struct V16;                   // elements per 16 bytes
+template <> struct V16<float> { static constexpr int W = 4; };
+template <> struct V16<__nv_bfloat16> { static constexpr int W = 8; };
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// sum over the 16 bytes at d (shared memory) times x[0 .. W)
+__device__ __forceinline__ float dot16(const float* d, const float* x) {
+  const float4 a = *reinterpret_cast<const float4*>(d);
+  const float4 b = *reinterpret_cast<const float4*>(x);
+  return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w);  // two independent chains
+}
+__device__ __forceinline__ float dot16(const __nv_bfloat16* d, const float* x) {
+  const uint4 a = *reinterpret_cast<const uint4*>(d);
+  const float4 b0 = *reinterpret_cast<const float4*>(x);
+  const float4 b1 = *reinterpret_cast<const float4*>(x + 4);
+  // a 32-bit word holds two bfloat16 values, the lower-indexed one in the low half
+  const float s0 = __uint_as_float(a.x << 16) * b0.x + __uint_as_float(a.x & 0xffff0000u) * b0.y;
+  const float s1 = __uint_as_float(a.y << 16) * b0.z + __uint_as_float(a.y & 0xffff0000u) * b0.w;
+  const float s2 = __uint_as_float(a.z << 16) * b1.x + __uint_as_float(a.z & 0xffff0000u) * b1.y;
+  const float s3 = __uint_as_float(a.w << 16) * b1.z + __uint_as_float(a.w & 0xffff0000u) * b1.w;
+  return (s0 + s1) + (s2 + s3);
+}
+// acc[0 .. W) += d[0 .. W) * s
+__device__ __forceinline__ void axpy16(float (&acc)[4], const float* d, float s) {
+  const float4 a = *reinterpret_cast<const float4*>(d);
+  acc[0] += a.x * s;
+  acc[1] += a.y * s;
+  acc[2] += a.z * s;
+  acc[3] += a.w * s;
+}
+__device__ __forceinline__ void axpy16(float (&acc)[8], const __nv_bfloat16* d, float s) {
+  const uint4 a = *reinterpret_cast<const uint4*>(d);
+  const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    acc[2 * k] += __uint_as_float(w[k] << 16) * s;
+    acc[2 * k + 1] += __uint_as_float(w[k] & 0xffff0000u) * s;
+  }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// global -> shared bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned), completion
+// counted on bar
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   tc::smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
+               : "memory");
+}
+// named barrier 1 over the NT consumer threads; returns the OR of v over them (uniform)
+template <int NT>
+__device__ __forceinline__ int consumer_sync_or(int v) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.s32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, %2, p;\n\t"
+      "selp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(v), "n"(NT)
+      : "memory");
+  return r;
+}
+
+}  // namespace lss
+}  // namespace a2ls
+
+
+namespace a2ls {
+namespace lss {
+
+// meta: per chunk a header int4 {segments, kind | block << 2, elements, element offset of its data in
+// the subdomain's stream} followed by its segment records int4 {element offset, first column, end
+// column, row}; the row is the local row (LP), the local column (UP) or the row inside the block (LD,
+// UD).  mpos: per chunk the index of its header in meta.
+// xcap: floats of each shared vector (the largest subdomain rounded up to 64 rows).
+// CW consumer warps and one producer warp; CTAS_PER_SM CTAs share an SM, each on its own subdomains, so
+// that one CTA's dependent chain of diagonal steps overlaps the others' panel streaming.
+template <class T, int CW, int CTAS_PER_SM>
+__global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_stream(
+    int nstages, int xcap, const int* __restrict__ cta_off, const int* __restrict__ cta_list,
+    const int* __restrict__ choff, const int* __restrict__ mpos, const int4* __restrict__ meta,
+    const int64_t* __restrict__ soff, const T* __restrict__ stream, const int* __restrict__ off,
+    const int* __restrict__ nI, const int* __restrict__ ni, const int* __restrict__ idx, const double* __restrict__ D,
+    const double* __restrict__ t, const double* __restrict__ q, double* __restrict__ out, int mode, int* st) {
+  constexpr int W = V16<T>::W;
+  constexpr int CONSUMER_WARPS = CW, CONSUMERS = 32 * CW;
+  constexpr int TPR = CONSUMERS / 64, CPT = 64 / TPR;  // diagonal blocks: threads per row, columns per thread
+  extern __shared__ __align__(128) unsigned char sm[];
+  unsigned char* stages = sm;                                                  // nstages x STAGE_BYTES
+  float* rhs = reinterpret_cast<float*>(sm + (size_t)nstages * STAGE_BYTES);  // xcap: R_i r, then the solution
+  float* x = rhs + xcap;                                                       // xcap: y, then the backward work
+  float* lp = x + xcap;                                                        // 2 x 64: panel products of a
+                                                                               // block, by block parity
+  __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES];
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < nstages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], CONSUMER_WARPS);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int g0 = cta_off[blockIdx.x], g1 = cta_off[blockIdx.x + 1];
+
+  if (warp == CONSUMER_WARPS) {
+    // ---- producer warp: the chunk headers are read 32 at a time (one per lane); lane 0 issues the
+    // copies of every chunk of this CTA's subdomains, in order
+    int k = 0;
+    bool ok = true;
+    for (int g = g0; g < g1 && ok; ++g) {
+      const int i = cta_list[g];
+      const T* base = stream + soff[i];
+      const int c1 = choff[i + 1];
+      for (int cb = choff[i]; cb < c1 && ok; cb += 32) {
+        const int cnt = min(32, c1 - cb);
+        int mp = 0;
+        int4 hd = make_int4(0, 0, 0, 0);
+        if (lane < cnt) {
+          mp = mpos[cb + lane];
+          hd = meta[mp];
+        }
+        for (int u = 0; u < cnt; ++u, ++k) {
+          const int ump = __shfl_sync(0xffffffffu, mp, u);
+          const int nrec = __shfl_sync(0xffffffffu, hd.x, u);
+          const int elems = __shfl_sync(0xffffffffu, hd.z, u);
+          const int doff = __shfl_sync(0xffffffffu, hd.w, u);
+          const int s = k % nstages;
+          int good = 1;
+          if (lane == 0) {
+            good = tc::mbar_wait_bounded(&empty[s], ((k / nstages) & 1) ^ 1, WAIT_LIMIT) && !abort_flag;
+            if (good) {
+              const uint32_t mbytes = 16u * (uint32_t)(1 + nrec), dbytes = (uint32_t)elems * (uint32_t)sizeof(T);
+              unsigned char* dst = stages + (size_t)s * STAGE_BYTES;
+              mbar_arrive_expect_tx(&full[s], mbytes + dbytes);
+              bulk_g2s(dst, meta + ump, mbytes, &full[s]);
+              if (dbytes) bulk_g2s(dst + STAGE_META, base + doff, dbytes, &full[s]);
+            }
+          }
+          if (!__shfl_sync(0xffffffffu, good, 0)) {
+            ok = false;
+            break;
+          }
+        }
+      }
+    }
+    if (lane == 0) {
+      if (!ok) {
+        abort_flag = 1;
+        raise_status(st, A2LS_ERR_TIMEOUT, blockIdx.x, 10);
+      }
+      // the copies of the last chunk of every stage have landed before the CTA may leave
+      for (int j = max(0, k - nstages); j < k; ++j)
+        tc::mbar_wait_bounded(&full[j % nstages], (j / nstages) & 1, WAIT_LIMIT);
+    }
+    __syncwarp();
+    return;
+  }
+
+  // ---- consumers
+  int k = 0, aborted = 0;
+  for (int g = g0; g < g1; ++g) {
+    const int i = cta_list[g];
+    const int n = ni[i], o = off[i];
+    for (int l = tid; l < xcap; l += CONSUMERS) {
+      rhs[l] = l < n ? (float)t[idx[o + l]] : 0.f;
+      x[l] = 0.f;
+    }
+    if (tid < 128) lp[tid] = 0.f;
+    if (consumer_sync_or<CONSUMERS>(aborted)) {
+      aborted = 1;
+      break;
+    }
+    int jb = 0;  // panel rows of the current block dealt so far (round-robin base of the warps)
+    const int c1 = choff[i + 1];
+    for (int c = choff[i]; c < c1; ++c, ++k) {
+      const int s = k % nstages;
+      const unsigned char* sp = stages + (size_t)s * STAGE_BYTES;
+      const bool have = !aborted && tc::mbar_wait_bounded(&full[s], (k / nstages) & 1, WAIT_LIMIT);
+      int4 hd;
+      if (have) {
+        hd = *reinterpret_cast<const int4*>(sp);
+      } else {
+        aborted = 1;
+        hd = __ldg(&meta[__ldg(&mpos[c])]);  // the kind keeps the barriers of this warp in step
+      }
+      const int kind = hd.y & 3, b = hd.y >> 2, r0 = b * 64, tb = min(64, n - r0), nrec = hd.x;
+      const bool diag = kind == LD || kind == UD;
+      // a diagonal block needs every panel contribution before it
+      if (diag && consumer_sync_or<CONSUMERS>(aborted)) {
+        aborted = 1;
+        break;
+      }
+      if (have) {
+        const int4* rec = reinterpret_cast<const int4*>(sp) + 1;
+        const T* data = reinterpret_cast<const T*>(sp + STAGE_META);
+        const int dbase = hd.w;
+        float* lpb = lp + (b & 1) * 64;
+        if (kind == LP) {
+          // lp[r - r0] = L[r][f_r .. r0) y: one warp per row, dealt round-robin over the block's rows; a
+          // warp takes its rows two at a time, so that their loads and reductions interleave
+          for (int j = ((warp - jb) % CONSUMER_WARPS + CONSUMER_WARPS) % CONSUMER_WARPS; j < nrec;
+               j += 2 * CONSUMER_WARPS) {
+            const int j2 = j + CONSUMER_WARPS;
+            const bool two = j2 < nrec;
+            const int4 rc = rec[j];
+            const int4 rc2 = two ? rec[j2] : make_int4(0, 0, 0, 0);
+            const int nq = (rc.z - rc.y) / W, nq2 = (rc2.z - rc2.y) / W;
+            const T* d = data + (rc.x - dbase);
+            const T* d2 = data + (rc2.x - dbase);
+            const float* xv = x + rc.y;
+            const float* xv2 = x + rc2.y;
+            float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+            int qq = lane;
+            for (; qq + 32 < nq; qq += 64) {
+              a0 += dot16(d + qq * W, xv + qq * W);
+              a1 += dot16(d + (qq + 32) * W, xv + (qq + 32) * W);
+            }
+            if (qq < nq) a0 += dot16(d + qq * W, xv + qq * W);
+            qq = lane;
+            for (; qq + 32 < nq2; qq += 64) {
+              b0 += dot16(d2 + qq * W, xv2 + qq * W);
+              b1 += dot16(d2 + (qq + 32) * W, xv2 + (qq + 32) * W);
+            }
+            if (qq < nq2) b0 += dot16(d2 + qq * W, xv2 + qq * W);
+            float a = a0 + a1, bsum = b0 + b1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              a += __shfl_xor_sync(0xffffffffu, a, o);
+              bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+            }
+            if (lane == 0) {
+              lpb[rc.w - r0] = a;
+              if (two) lpb[rc2.w - r0] = bsum;
+            }
+          }
+          jb += nrec;
+        } else if (kind == LD) {
+          // y[r0 + rr] = s[rr] + sum_{c < rr} inv(L_bb)[rr][c] s[c], s = (R_i r)_b - lp; TPR threads a row
+          const int rr = tid / TPR, qd = tid % TPR;
+          float v = 0.f;
+          if (rr < tb) {
+            const T* d = data + (rec[rr].x - dbase);
+            const int cend = min(CPT * qd + CPT, rr);
+            float v1 = 0.f;
+            int cc = CPT * qd;
+            for (; cc + 1 < cend; cc += 2) {
+              v += to_f(d[cc]) * (rhs[r0 + cc] - lpb[cc]);
+              v1 += to_f(d[cc + 1]) * (rhs[r0 + cc + 1] - lpb[cc + 1]);
+            }
+            if (cc < cend) v += to_f(d[cc]) * (rhs[r0 + cc] - lpb[cc]);
+            v += v1;
+          }
+#pragma unroll
+          for (int sh = 1; sh < TPR; sh <<= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
+          if (rr < tb && qd == 0) x[r0 + rr] = rhs[r0 + rr] - lpb[rr] + v;
+          if (tid < 64) lp[((b + 1) & 1) * 64 + tid] = 0.f;  // the next block's panel products
+          jb = 0;
+        } else if (kind == UD) {
+          // solution rows: rhs[r0 + rr] = sum_{c >= rr} inv(U_bb)[rr][c] y[r0 + c]; TPR threads a row
+          const int rr = tid / TPR, qd = tid % TPR;
+          float v = 0.f;
+          if (rr < tb) {
+            const int4 rc = rec[rr];
+            const T* d = data + (rc.x - dbase) - (rc.y - r0);  // d[c] is column r0 + c
+            const int cend = min(CPT * qd + CPT, tb);
+            float v1 = 0.f;
+            int cc = max(CPT * qd, rr);
+            for (; cc + 1 < cend; cc += 2) {
+              v += to_f(d[cc]) * x[r0 + cc];
+              v1 += to_f(d[cc + 1]) * x[r0 + cc + 1];
+            }
+            if (cc < cend) v += to_f(d[cc]) * x[r0 + cc];
+            v += v1;
+          }
+#pragma unroll
+          for (int sh = 1; sh < TPR; sh <<= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
+          if (rr < tb && qd == 0) rhs[r0 + rr] = v;
+        } else {
+          // right-looking update of the rows above the block: y[r] -= sum_c U[r][c] x_c over the chunk's
+          // columns c; position p is always owned by the thread with p / W == tid (mod CONSUMERS), so that
+          // the chunks of one block update it in order without a barrier between them.  The chunk's
+          // columns come by increasing first row: the ones that reach p are a prefix.
+          const int cmin = rec[0].y;
+          constexpr int STRIDE = CONSUMERS * W;
+          int p = tid * W;
+          if (p < cmin) p += ((cmin - p + STRIDE - 1) / STRIDE) * STRIDE;
+          for (; p < r0; p += STRIDE) {
+            float acc[W];
+#pragma unroll
+            for (int v = 0; v < W; ++v) acc[v] = 0.f;
+            for (int j = 0; j < nrec; ++j) {
+              const int4 rc = rec[j];
+              if (rc.y > p) break;
+              axpy16(acc, data + (rc.x - dbase) + (p - rc.y), rhs[rc.w]);
+            }
+#pragma unroll
+            for (int v = 0; v < W; ++v) x[p + v] -= acc[v];
+          }
+        }
+      }
+      __syncwarp();
+      if (have && lane == 0) mbar_arrive(&empty[s]);
+      if (diag && consumer_sync_or<CONSUMERS>(aborted)) {
+        aborted = 1;
+        break;
+      }
+    }
+    if (aborted) break;
+    // rhs holds the local solution
+    if (mode == 0) {
+      const int n_I = nI[i];
+      for (int l = tid; l < n_I; l += CONSUMERS) {
+        const int gidx = idx[o + l];
+        out[gidx] = (q ? q[gidx] : 0.0) + (double)rhs[l];
+      }
+    } else {
+      for (int l = tid; l < n; l += CONSUMERS) out[o + l] = (mode == 1 ? D[o + l] : 1.0) * (double)rhs[l];
+    }
+    if (consumer_sync_or<CONSUMERS>(aborted)) {
+      aborted = 1;
+      break;
+    }
+  }
+  if (aborted) {
+    abort_flag = 1;
+    if (tid == 0) raise_status(st, A2LS_ERR_TIMEOUT, blockIdx.x, 11);
+  }
+}
+
+}  // namespace lss
+}  // namespace a2ls
+
+namespace a2ls {
+namespace lss {
+
+// Pack one chunk per warp: every segment of the chunk copied from the dense block-inverted factors F
+// (row-major, leading dimension ld) into the stream; entries outside a segment's own part (the
+// rounding of its column range, the other triangle of a diagonal tile, columns past n) are written
+// as zeros.
+template <class T>
+__global__ void k_pack_stream(int nchunks, int N, const int* __restrict__ choff, const int* __restrict__ mpos,
+                              const int4* __restrict__ meta, const int64_t* __restrict__ soff,
+                              const int* __restrict__ ni, const int* __restrict__ ld, const int64_t* __restrict__ foff,
+                              const T* __restrict__ fac, T* __restrict__ stream) {
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < nchunks; c += gridDim.x * wpb) {
+    int lo = 0, hi = N;  // choff[lo] <= c < choff[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (choff[mid] <= c) lo = mid; else hi = mid;
+    }
+    const int i = lo, n = ni[i];
+    const int64_t L = ld[i];
+    const T* F = fac + foff[i];
+    T* S = stream + soff[i];
+    const int4* hd = meta + mpos[c];
+    const int kind = hd->y & 3, r0 = (hd->y >> 2) * 64, tb = min(64, n - r0);
+    for (int j = 1; j <= hd->x; ++j) {
+      const int4 rc = hd[j];
+      const int len = rc.z - rc.y;
+      for (int e = lane; e < len; e += 32) {
+        const int col = rc.y + e;
+        T v = T(0.f);
+        if (kind == LP) {
+          v = F[(int64_t)rc.w * L + col];                                     // L[r][col], col < r0 <= r
+        } else if (kind == LD) {
+          if (col < r0 + rc.w) v = F[(int64_t)(r0 + rc.w) * L + col];         // inv(L_bb), strictly lower
+        } else if (kind == UD) {
+          if (col >= r0 + rc.w && col < r0 + tb) v = F[(int64_t)(r0 + rc.w) * L + col];  // inv(U_bb), upper
+        } else {
+          v = F[(int64_t)col * L + rc.w];                                     // U[col][c], col < r0 <= c
+        }
+        S[rc.x + e] = v;
+      }
+    }
+  }
+}
+
+}  // namespace lss
+
+// ---------------------------------------------------------------------------
+// Host side: the plan of the stream (segments, chunks, offsets), the packing, the schedule.
+// ---------------------------------------------------------------------------
+template <class T>
+void stream_prepare(a2ls_handle* h, const T* fac) {
+  using namespace lss;
+  constexpr int W = V16<T>::W;
+  cudaStream_t st = h->st;
+  const int N = h->N;
+  std::vector<int> pf(h->sum_n), pg(h->sum_n);
+  A2LS_CUDA(cudaMemcpyAsync(pf.data(), h->d_pf, sizeof(int) * h->sum_n, cudaMemcpyDeviceToHost, st));
+  A2LS_CUDA(cudaMemcpyAsync(pg.data(), h->d_pg, sizeof(int) * h->sum_n, cudaMemcpyDeviceToHost, st));
+  A2LS_CUDA(cudaStreamSynchronize(st));
+  auto lo = [](int v) { return v / W * W; };
+  auto up = [](int v) { return (v + W - 1) / W * W; };
+  const int stage_elems = STAGE_DATA / (int)sizeof(T);
+  std::vector<int4> meta;
+  std::vector<int> mpos, choff(N + 1, 0);
+  std::vector<int64_t> soff(N + 1, 0);
+  std::vector<double> cost(N, 0.0);
+  meta.reserve((size_t)h->sum_n * 4 + (size_t)N * 64);
+  for (int i = 0; i < N; ++i) {
+    const int n = h->h_n[i], o = h->h_off[i], nb = (n + TB - 1) / TB;
+    int off = 0;
+    choff[i] = (int)mpos.size();
+    int hdr = -1;  // header of the open chunk in meta
+    auto close = [&]() { hdr = -1; };
+    // segment [cs, ce) of `row`, appended to the open chunk while it fits
+    auto add = [&](int kind, int b, int cs, int ce, int row) {
+      const int len = ce - cs;
+      if (hdr >= 0 && (meta[hdr].y != (kind | (b << 2)) || meta[hdr].z + len > stage_elems ||
+                       meta[hdr].x >= STAGE_RECS))
+        close();
+      if (hdr < 0) {
+        hdr = (int)meta.size();
+        mpos.push_back(hdr);
+        meta.push_back(make_int4(0, kind | (b << 2), 0, off));
+      }
+      meta.push_back(make_int4(off, cs, ce, row));
+      meta[hdr].x += 1;
+      meta[hdr].z += len;
+      off += len;
+    };
+    for (int b = 0; b < nb; ++b) {
+      const int r0 = b * TB, tb = std::min(TB, n - r0);
+      for (int r = r0; r < r0 + tb; ++r) {
+        const int cs = lo(pf[o + r]);
+        if (cs < r0) add(LP, b, cs, r0, r);
+      }
+      close();
+      for (int rr = 0; rr < tb; ++rr) add(LD, b, r0, r0 + up(rr), rr);
+      close();
+    }
+    for (int b = nb - 1; b >= 0; --b) {
+      const int r0 = b * TB, tb = std::min(TB, n - r0);
+      for (int rr = 0; rr < tb; ++rr) add(UD, b, r0 + lo(rr), r0 + up(tb), rr);
+      close();
+      // the block's columns by increasing first row (the update of a row reads a prefix of a chunk)
+      std::vector<std::pair<int, int>> cols;
+      for (int c = r0; c < r0 + tb; ++c) {
+        const int cs = lo(pg[o + c]);
+        if (cs < r0) cols.push_back({cs, c});
+      }
+      std::stable_sort(cols.begin(), cols.end());
+      for (const auto& pc : cols) add(UP, b, pc.first, r0, pc.second);
+      close();
+    }
+    soff[i + 1] = soff[i] + off;
+    // copy time of the bytes plus the dependent chain of 2 nb diagonal steps (about 2 us each, the time
+    // the copy engine moves 64 KB for one SM)
+    cost[i] = (double)off * sizeof(T) + 2.0 * nb * 65536.0;
+  }
+  choff[N] = (int)mpos.size();
+  // device copies of the plan
+  StreamSolve& S = h->ss;
+  S.elem_bytes = (int)sizeof(T);
+  S.nchunks = (int)mpos.size();
+  S.stream_elems = soff[N];
+  S.d_stream = dalloc<T>(h, (size_t)soff[N] + W);
+  S.d_meta = dalloc<int4>(h, meta.size());
+  S.d_mpos = dalloc<int>(h, mpos.size());
+  S.d_choff = dalloc<int>(h, N + 1);
+  S.d_soff = dalloc<int64_t>(h, N + 1);
+  A2LS_CUDA(cudaMemcpyAsync(S.d_meta, meta.data(), sizeof(int4) * meta.size(), cudaMemcpyHostToDevice, st));
+  A2LS_CUDA(cudaMemcpyAsync(S.d_mpos, mpos.data(), sizeof(int) * mpos.size(), cudaMemcpyHostToDevice, st));
+  A2LS_CUDA(cudaMemcpyAsync(S.d_choff, choff.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, st));
+  A2LS_CUDA(cudaMemcpyAsync(S.d_soff, soff.data(), sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, st));
+  int dev = 0, sms = 152, optin = 0, per_sm = 0;
+  A2LS_CUDA(cudaGetDevice(&dev));
+  A2LS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  A2LS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  A2LS_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  const int wpb = 8;
+  const int blocks = std::max(1, std::min(sms * 16, (S.nchunks + wpb - 1) / wpb));
+  k_pack_stream<T><<<blocks, 32 * wpb, 0, st>>>(S.nchunks, N, S.d_choff, S.d_mpos, S.d_meta, S.d_soff, h->d_ni,
+                                                h->d_fld, h->d_ffoff, fac, static_cast<T*>(S.d_stream));
+  A2LS_LAUNCH();
+  S.xcap = (int)round_up(h->max_n, TB);
+  const size_t fixed = sizeof(float) * (2 * (size_t)S.xcap + 2 * 64);  // the two vectors, the panel products
+  // the kernel shapes: 8 consumer warps, one CTA per SM; 4 consumer warps, two CTAs per SM; 8 consumer
+  // warps, two CTAs per SM
+  for (int v = 0; v < 3; ++v) {
+    StreamSolve::Shape& sh = S.shape[v];
+    const int ctas = v == 0 ? 1 : 2;
+    // shared memory per CTA: the SM's share less the 1 KB the hardware reserves per CTA and the static part
+    const size_t budget = std::min<size_t>((size_t)optin, (size_t)per_sm / ctas - 1024) - 512;
+    sh.nstages = (int)std::min<size_t>(MAX_STAGES, budget > fixed ? (budget - fixed) / STAGE_BYTES : 0);
+    sh.smem = (size_t)sh.nstages * STAGE_BYTES + fixed;
+    if (sh.nstages < 2) continue;
+    int occ = 0;
+    if (v == 0) {
+      A2LS_CUDA(cudaFuncSetAttribute(k_local_solve_stream<T, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sh.smem));
+      A2LS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_local_solve_stream<T, 8, 1>, 288, sh.smem));
+    } else if (v == 1) {
+      A2LS_CUDA(cudaFuncSetAttribute(k_local_solve_stream<T, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sh.smem));
+      A2LS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_local_solve_stream<T, 4, 2>, 160, sh.smem));
+    } else {
+      A2LS_CUDA(cudaFuncSetAttribute(k_local_solve_stream<T, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)sh.smem));
+      A2LS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_local_solve_stream<T, 8, 2>, 288, sh.smem));
+    }
+    if (occ < ctas) continue;
+    // largest-first assignment of the subdomains to the least-loaded CTA
+    const int G = std::max(1, std::min(N, sms * ctas));
+    std::vector<int> order(N);
+    for (int i = 0; i < N; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    using Load = std::pair<double, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int g = 0; g < G; ++g) heap.push({0.0, g});
+    std::vector<std::vector<int>> lists(G);
+    for (int i : order) {
+      Load l = heap.top();
+      heap.pop();
+      lists[l.second].push_back(i);
+      heap.push({l.first + cost[i], l.second});
+    }
+    std::vector<int> cta_off(G + 1, 0), cta_list;
+    cta_list.reserve(N);
+    for (int g = 0; g < G; ++g) {
+      cta_list.insert(cta_list.end(), lists[g].begin(), lists[g].end());
+      cta_off[g + 1] = (int)cta_list.size();
+    }
+    sh.ncta = G;
+    sh.d_cta_off = dalloc<int>(h, G + 1);
+    sh.d_cta_list = dalloc<int>(h, N);
+    A2LS_CUDA(cudaMemcpyAsync(sh.d_cta_off, cta_off.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, st));
+    A2LS_CUDA(cudaMemcpyAsync(sh.d_cta_list, cta_list.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    sh.ready = true;
+  }
+  S.ready = S.shape[0].ready || S.shape[1].ready || S.shape[2].ready;
+  A2LS_CUDA(cudaStreamSynchronize(st));
+}
+
+// config: LS_STREAM (8 consumer warps, one CTA per SM), LS_STREAM2 (4 consumer warps, two CTAs per SM) or
+// LS_STREAM3 (8 consumer warps, two CTAs per SM)
+template <class T>
+void launch_local_solve_stream(a2ls_handle* h, int config, const double* t, const double* q, double* z, int mode) {
+  using namespace lss;
+  const StreamSolve& S = h->ss;
+  const int v = config == LS_STREAM2 ? 1 : (config == LS_STREAM3 ? 2 : 0);
+  const StreamSolve::Shape& sh = S.shape[v];
+  if (!sh.ready || S.elem_bytes != (int)sizeof(T)) fail(A2LS_ERR_ARG, "streaming local solves not prepared");
+  if (v == 0)
+    k_local_solve_stream<T, 8, 1><<<sh.ncta, 288, sh.smem, h->st>>>(
+        sh.nstages, S.xcap, sh.d_cta_off, sh.d_cta_list, S.d_choff, S.d_mpos, S.d_meta, S.d_soff,
+        static_cast<const T*>(S.d_stream), h->d_off, h->d_nI, h->d_ni, h->d_idx, h->d_D, t, q, z, mode, h->d_status);
+  else if (v == 2)
+    k_local_solve_stream<T, 8, 2><<<sh.ncta, 288, sh.smem, h->st>>>(
+        sh.nstages, S.xcap, sh.d_cta_off, sh.d_cta_list, S.d_choff, S.d_mpos, S.d_meta, S.d_soff,
+        static_cast<const T*>(S.d_stream), h->d_off, h->d_nI, h->d_ni, h->d_idx, h->d_D, t, q, z, mode, h->d_status);
+  else
+    k_local_solve_stream<T, 4, 2><<<sh.ncta, 160, sh.smem, h->st>>>(
+        sh.nstages, S.xcap, sh.d_cta_off, sh.d_cta_list, S.d_choff, S.d_mpos, S.d_meta, S.d_soff,
+        static_cast<const T*>(S.d_stream), h->d_off, h->d_nI, h->d_ni, h->d_idx, h->d_D, t, q, z, mode, h->d_status);
+  A2LS_LAUNCH();
+}
+
+template void stream_prepare<float>(a2ls_handle*, const float*);
+template void stream_prepare<__nv_bfloat16>(a2ls_handle*, const __nv_bfloat16*);
+template void launch_local_solve_stream<float>(a2ls_handle*, int, const double*, const double*, double*, int);
+template void launch_local_solve_stream<__nv_bfloat16>(a2ls_handle*, int, const double*, const double*, double*,
+                                                        int);
+
+}  // namespace a2ls

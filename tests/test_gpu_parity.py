@@ -430,6 +430,58 @@ def test_uneven_subdomains_and_ragged_tiles():
     P2.close()
 
 
+def _stream_case(name):
+    if name == "uneven3d":   # 10 BFS regions of 60-300 rows + overlap: several tiles, ragged tails
+        A = pde.conv_diff_3d(12, 100.0)
+        part = pde.bfs_region_partition(A, 10, 60, 300, seed=11)
+        return pde.Problem("bfs3d", A, part, 1, 5, pde.rhs_uniform(A.shape[0], 11))
+    return pde.tiny_conv_diff(m=12, nb=3, overlap=1, nev=3)   # subdomains of one partial tile
+
+
+@pytest.mark.parametrize("name", ["uneven3d", "tiny12"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("variant,pou", [("deflated_ras", "boolean"), ("deflated_ras", "multiplicity"),
+                                         ("deflated_asm", "boolean")])
+def test_streaming_local_solves(name, precision, variant, pou):
+    """The streaming local-solve kernel (factors repacked in solve order: L by rows, U by columns and the
+    inverted diagonal triangles, streamed through shared memory by bulk copies; right-looking backward
+    sweep), in its three launch shapes (one CTA of 8 consumer warps per SM, two CTAs of 4 or of 8 per SM), against
+    the oracle and against the one-pass kernel on the same stored factors, in all three
+    output modes (RAS with Boolean or multiplicity weights, ASM): both kernels are within the FP32
+    tolerance of the apply (1e-4; for BF16 factors the bound of their rounding, 30 x 2^-9) of the
+    oracle's FP64 apply with the same coarse basis, and flexible GMRES takes the same number of
+    iterations (+-1) with either kernel."""
+    prob = _stream_case(name)
+    ref = O.setup(prob.A, prob.part, prob.overlap, prob.nev, pou=pou)
+    tol = 1e-4 if precision == "fp32" else 30 * 2.0 ** -9
+    zs = {}
+    its = {}
+    for k in (3000, 3004, 3008, 256):
+        P = setup_gpu(prob, precision=precision, variant=variant, pou=pou, local_solve_kernel=k)
+        assert P.tuning()["local_solve_threads"] == k
+        P.set_coarse_basis(ref.coarse.W)
+        for j, r in enumerate((prob.b, np.sin(np.arange(prob.n)))):
+            z = apply_gpu(P, r)
+            zr = O.apply(ref, r, variant)
+            assert np.linalg.norm(z - zr) <= tol * np.linalg.norm(zr), (k, j)
+            zs[(k, j)] = z
+        x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+        it, rr, ok = P.solve(dev(prob.b), x, 1e-8)
+        assert ok, k
+        its[k] = it
+        P.close()
+    for k in (3000, 3004, 3008):
+        for j in range(2):
+            assert np.linalg.norm(zs[(k, j)] - zs[(256, j)]) <= tol * np.linalg.norm(zs[(256, j)])
+        assert abs(its[k] - its[256]) <= 1, its
+
+
+def test_streaming_kernel_refused_for_fp64_factors():
+    prob = pde.tiny_conv_diff(m=12, nb=3, overlap=1, nev=3)
+    with pytest.raises(a2ls().A2lsError, match="local_solve_kernel"):
+        setup_gpu(prob, precision="fp64", local_solve_kernel=3000)
+
+
 # ---------------------------------------------------------------------------
 # error reporting (host- and device-detected), no faults
 # ---------------------------------------------------------------------------
