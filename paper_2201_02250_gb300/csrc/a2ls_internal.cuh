@@ -68,6 +68,7 @@ struct StreamSolve {
   void* d_stream = nullptr;
   int4* d_meta = nullptr;                    // chunk headers, each followed by its segment records
   int *d_mpos = nullptr, *d_choff = nullptr;
+  int* d_order = nullptr;                    // work-queue order of the subdomains (by decreasing cost)
   int64_t* d_soff = nullptr;
   // launch shapes: [0] 8 consumer warps, one CTA per SM; [1] 4 consumer warps, two CTAs per SM; [2] 8
   // consumer warps, two CTAs per SM
@@ -75,7 +76,6 @@ struct StreamSolve {
     bool ready = false;
     int ncta = 0, nstages = 0;
     size_t smem = 0;
-    int *d_cta_off = nullptr, *d_cta_list = nullptr;   // static assignment of the subdomains to CTAs
   } shape[3];
 };
 constexpr int LS_STREAM = 3000;   // local-solve configurations of the streaming kernel: shape 0

@@ -4,25 +4,28 @@
 //
 // Apply format.  After the factorisation the block-inverted LU factors of each subdomain are packed
 // once into one contiguous stream in the order the solves consume them:
-//   forward, block b = 0 .. nb-1:   LP  rows r of the block: L[r][f_r .. r0)         (row envelope)
+//   forward, block b = 0 .. nb-1:   LP  panel L[r0 .. r0 + 64)[c_b .. r0), column-major (64 rows a
+//                                       column), c_b the first envelope column of the block's rows
 //                                   LD  row rr of inv(L_bb): columns r0 .. r0 + rr   (strictly lower)
 //   backward, block b = nb-1 .. 0:  UD  row rr of inv(U_bb): columns r0 + rr .. r0 + 64
-//                                   UP  column c of the block: U[g_c .. r0)[c]       (column envelope,
-//                                       stored as a row of U^T)
-// Every segment starts and ends on a 16-byte boundary (its column range rounded outwards; the entries
-// added are exact zeros).  U is kept by columns because its column envelope is the compact one (for
-// the layer-ordered overlapping subdomains a row-wise envelope of U holds twice the entries); the
-// backward sweep is therefore right-looking: once x_b is known, every earlier row r receives
-// -U[r][c] x_c from the columns c of block b.
-// Consecutive segments of one kind and block are grouped into chunks of at most 32 KB and 64
-// segments; a chunk is one contiguous byte range of the stream.  The UP columns of a block are laid
-// out by increasing first row.
-//
-// Kernel.  One CTA per SM, persistent over a static largest-first (LPT) assignment of the subdomains.
+//                                   UP  panel U[g_b .. r0)[r0 .. r0 + 64), in row blocks stored
+//                                       column-major, g_b the first envelope row of the block's columns
+// The panels are dense over the block (the entries outside a row's or column's own envelope are exact
+// zeros: 19 % more bytes than the envelope on the 96^3 convection-diffusion subdomains) because a dense
+// panel is a plain product in shared memory: a thread takes a few rows and a subset of the columns, with
+// no per-row reductions.  U's panel runs along the block's columns, the envelope that U keeps, so the
+// backward sweep is right-looking: once x_b is known, every earlier row r receives
+// -U[r][r0 .. r0 + 64) x_b.  The diagonal triangles are stored by rows, each row on 16-byte
+// boundaries (its column range rounded outwards; the entries added are zeros).
+// Chunks hold at most 32 KB: 128 (FP32) or 256 (BF16) columns of an L panel, 28 groups of 16 bytes of
+// rows of a U panel (a column stride of 64 bytes modulo 128 keeps the reads conflict-free), or one
+// diagonal triangle with its row records.
+
+// Kernel.  One or two CTAs per SM, persistent over a work queue of the subdomains (largest first).
 // One producer warp streams the chunks through a ring of shared-memory stages with bulk asynchronous
 // copies (cp.async.bulk, completion counted in bytes on an mbarrier per stage); each stage also
-// receives the chunk's header and segment records, so that the consumers read no global memory but
-// the right-hand side and their outputs.  Eight consumer warps run the solves from shared memory:
+// receives the chunk's header (and a triangle's row records), so that the consumers read no global
+// memory but the right-hand side and their outputs.  The consumer warps run the solves from shared memory:
 // the panel products, the 64 x 64 triangle products of the diagonal blocks and the right-looking
 // updates, with the gathered right-hand side and the solution held in shared memory.  The producer
 // runs ahead across block and subdomain boundaries, so the loads never wait for the solve chain.
@@ -87,6 +90,24 @@ __device__ __forceinline__ void axpy16(float (&acc)[8], const __nv_bfloat16* d, 
   }
 }
 
+// the W values of the 16 bytes at d (shared memory)
+__device__ __forceinline__ void unpack16(const float* d, float (&v)[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(d);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = a.z;
+  v[3] = a.w;
+}
+__device__ __forceinline__ void unpack16(const __nv_bfloat16* d, float (&v)[8]) {
+  const uint4 a = *reinterpret_cast<const uint4*>(d);
+  const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[2 * k] = __uint_as_float(w[k] << 16);
+    v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+  }
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -136,10 +157,13 @@ namespace lss {
 // UD).  mpos: per chunk the index of its header in meta.
 // xcap: floats of each shared vector (the largest subdomain rounded up to 64 rows).
 // CW consumer warps and one producer warp; CTAS_PER_SM CTAs share an SM, each on its own subdomains, so
-// that one CTA's dependent chain of diagonal steps overlaps the others' panel streaming.
+// that one CTA's dependent chain of diagonal steps overlaps the others' panel streaming.  Work queue:
+// the producer claims the next subdomain (in the order sched, largest first; *counter zero at launch)
+// when it reaches that subdomain's first chunk, and every stage carries the subdomain it belongs to; a
+// stage marked -1 ends the work.
 template <class T, int CW, int CTAS_PER_SM>
 __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_stream(
-    int nstages, int xcap, const int* __restrict__ cta_off, const int* __restrict__ cta_list,
+    int nstages, int xcap, int nwork, const int* __restrict__ sched, int* __restrict__ counter,
     const int* __restrict__ choff, const int* __restrict__ mpos, const int4* __restrict__ meta,
     const int64_t* __restrict__ soff, const T* __restrict__ stream, const int* __restrict__ off,
     const int* __restrict__ nI, const int* __restrict__ ni, const int* __restrict__ idx, const double* __restrict__ D,
@@ -151,9 +175,10 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
   unsigned char* stages = sm;                                                  // nstages x STAGE_BYTES
   float* rhs = reinterpret_cast<float*>(sm + (size_t)nstages * STAGE_BYTES);  // xcap: R_i r, then the solution
   float* x = rhs + xcap;                                                       // xcap: y, then the backward work
-  float* lp = x + xcap;                                                        // 2 x 64: panel products of a
-                                                                               // block, by block parity
+  float* part = x + xcap;                                                      // CW x 64: each warp's panel sums
+  float* s64 = part + CW * 64;                                                 // 64: the block's s = rhs - L y
   __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES];
+  __shared__ int stage_sub[MAX_STAGES];
   __shared__ volatile int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
@@ -165,15 +190,34 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const int g0 = cta_off[blockIdx.x], g1 = cta_off[blockIdx.x + 1];
 
   if (warp == CONSUMER_WARPS) {
-    // ---- producer warp: the chunk headers are read 32 at a time (one per lane); lane 0 issues the
-    // copies of every chunk of this CTA's subdomains, in order
+    // ---- producer warp: claims subdomains one after another; their chunk headers are read 32 at a time
+    // (one per lane); lane 0 issues the copies of every chunk, in order
     int k = 0;
     bool ok = true;
-    for (int g = g0; g < g1 && ok; ++g) {
-      const int i = cta_list[g];
+    for (;;) {
+      int i = -1;
+      if (lane == 0) {
+        const int w = atomicAdd(counter, 1);
+        i = w < nwork ? sched[w] : -1;
+      }
+      i = __shfl_sync(0xffffffffu, i, 0);
+      if (i < 0) {
+        // the end of the work: a stage without copies, marked -1
+        if (lane == 0) {
+          const int s = k % nstages;
+          if (tc::mbar_wait_bounded(&empty[s], ((k / nstages) & 1) ^ 1, WAIT_LIMIT) && !abort_flag) {
+            stage_sub[s] = -1;
+            mbar_arrive_expect_tx(&full[s], 0);
+            ++k;
+          } else {
+            ok = false;
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        break;
+      }
       const T* base = stream + soff[i];
       const int c1 = choff[i + 1];
       for (int cb = choff[i]; cb < c1 && ok; cb += 32) {
@@ -186,7 +230,8 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
         }
         for (int u = 0; u < cnt; ++u, ++k) {
           const int ump = __shfl_sync(0xffffffffu, mp, u);
-          const int nrec = __shfl_sync(0xffffffffu, hd.x, u);
+          const int hx = __shfl_sync(0xffffffffu, hd.x, u), hkind = __shfl_sync(0xffffffffu, hd.y, u) & 3;
+          const int nrec = (hkind == LD || hkind == UD) ? hx : 0;  // panels carry no records
           const int elems = __shfl_sync(0xffffffffu, hd.z, u);
           const int doff = __shfl_sync(0xffffffffu, hd.w, u);
           const int s = k % nstages;
@@ -196,6 +241,7 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
             if (good) {
               const uint32_t mbytes = 16u * (uint32_t)(1 + nrec), dbytes = (uint32_t)elems * (uint32_t)sizeof(T);
               unsigned char* dst = stages + (size_t)s * STAGE_BYTES;
+              stage_sub[s] = i;  // published to the consumers by the arrival below
               mbar_arrive_expect_tx(&full[s], mbytes + dbytes);
               bulk_g2s(dst, meta + ump, mbytes, &full[s]);
               if (dbytes) bulk_g2s(dst + STAGE_META, base + doff, dbytes, &full[s]);
@@ -207,6 +253,7 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
           }
         }
       }
+      if (!ok) break;
     }
     if (lane == 0) {
       if (!ok) {
@@ -223,24 +270,33 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
 
   // ---- consumers
   int k = 0, aborted = 0;
-  for (int g = g0; g < g1; ++g) {
-    const int i = cta_list[g];
+  for (;;) {
+    // the first stage of the next subdomain (or the end mark); the barrier also keeps the previous
+    // subdomain's output ahead of the gather below
+    bool have0 = !aborted && tc::mbar_wait_bounded(&full[k % nstages], (k / nstages) & 1, WAIT_LIMIT);
+    if (!have0) aborted = 1;
+    const int i = have0 ? stage_sub[k % nstages] : -1;
+    if (consumer_sync_or<CONSUMERS>(aborted)) {
+      aborted = 1;
+      break;
+    }
+    if (i < 0) break;  // the same stage for every warp: uniform
     const int n = ni[i], o = off[i];
     for (int l = tid; l < xcap; l += CONSUMERS) {
       rhs[l] = l < n ? (float)t[idx[o + l]] : 0.f;
       x[l] = 0.f;
     }
-    if (tid < 128) lp[tid] = 0.f;
+    for (int e = tid; e < CW * 64; e += CONSUMERS) part[e] = 0.f;
     if (consumer_sync_or<CONSUMERS>(aborted)) {
       aborted = 1;
       break;
     }
-    int jb = 0;  // panel rows of the current block dealt so far (round-robin base of the warps)
     const int c1 = choff[i + 1];
     for (int c = choff[i]; c < c1; ++c, ++k) {
       const int s = k % nstages;
       const unsigned char* sp = stages + (size_t)s * STAGE_BYTES;
-      const bool have = !aborted && tc::mbar_wait_bounded(&full[s], (k / nstages) & 1, WAIT_LIMIT);
+      // (the first chunk's stage was waited for above)
+      const bool have = !aborted && (c == choff[i] || tc::mbar_wait_bounded(&full[s], (k / nstages) & 1, WAIT_LIMIT));
       int4 hd;
       if (have) {
         hd = *reinterpret_cast<const int4*>(sp);
@@ -248,59 +304,61 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
         aborted = 1;
         hd = __ldg(&meta[__ldg(&mpos[c])]);  // the kind keeps the barriers of this warp in step
       }
-      const int kind = hd.y & 3, b = hd.y >> 2, r0 = b * 64, tb = min(64, n - r0), nrec = hd.x;
+      const int kind = hd.y & 3, b = hd.y >> 2, r0 = b * 64, tb = min(64, n - r0);
       const bool diag = kind == LD || kind == UD;
       // a diagonal block needs every panel contribution before it
       if (diag && consumer_sync_or<CONSUMERS>(aborted)) {
         aborted = 1;
         break;
       }
+      if (kind == LD) {
+        // s = (R_i r)_b - L_b y from the warps' panel sums, which are then cleared for the next block
+        if (tid < 64) {
+          float sum = 0.f;
+#pragma unroll
+          for (int w = 0; w < CW; ++w) {
+            sum += part[w * 64 + tid];
+            part[w * 64 + tid] = 0.f;
+          }
+          s64[tid] = rhs[r0 + tid] - sum;
+        }
+        if (consumer_sync_or<CONSUMERS>(aborted)) {
+          aborted = 1;
+          break;
+        }
+      }
       if (have) {
         const int4* rec = reinterpret_cast<const int4*>(sp) + 1;
         const T* data = reinterpret_cast<const T*>(sp + STAGE_META);
         const int dbase = hd.w;
-        float* lpb = lp + (b & 1) * 64;
         if (kind == LP) {
-          // lp[r - r0] = L[r][f_r .. r0) y: one warp per row, dealt round-robin over the block's rows; a
-          // warp takes its rows two at a time, so that their loads and reductions interleave
-          for (int j = ((warp - jb) % CONSUMER_WARPS + CONSUMER_WARPS) % CONSUMER_WARPS; j < nrec;
-               j += 2 * CONSUMER_WARPS) {
-            const int j2 = j + CONSUMER_WARPS;
-            const bool two = j2 < nrec;
-            const int4 rc = rec[j];
-            const int4 rc2 = two ? rec[j2] : make_int4(0, 0, 0, 0);
-            const int nq = (rc.z - rc.y) / W, nq2 = (rc2.z - rc2.y) / W;
-            const T* d = data + (rc.x - dbase);
-            const T* d2 = data + (rc2.x - dbase);
-            const float* xv = x + rc.y;
-            const float* xv2 = x + rc2.y;
-            float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
-            int qq = lane;
-            for (; qq + 32 < nq; qq += 64) {
-              a0 += dot16(d + qq * W, xv + qq * W);
-              a1 += dot16(d + (qq + 32) * W, xv + (qq + 32) * W);
-            }
-            if (qq < nq) a0 += dot16(d + qq * W, xv + qq * W);
-            qq = lane;
-            for (; qq + 32 < nq2; qq += 64) {
-              b0 += dot16(d2 + qq * W, xv2 + qq * W);
-              b1 += dot16(d2 + (qq + 32) * W, xv2 + (qq + 32) * W);
-            }
-            if (qq < nq2) b0 += dot16(d2 + qq * W, xv2 + qq * W);
-            float a = a0 + a1, bsum = b0 + b1;
+          // part[warp][r] += sum over the chunk's columns c of L[r0 + r][c] y[c]: the chunk is column-major
+          // (64 rows a column); a thread takes W rows (row group g) and the columns sub, sub + NSUB, ...
+          constexpr int G = 64 / W, NSUB = CONSUMERS / G;
+          const int g = tid % G, sub = tid / G;
+          const int c0 = hd.x, ncols = hd.z / 64;
+          const float* yc = x + c0;
+          float acc[W];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-              a += __shfl_xor_sync(0xffffffffu, a, o);
-              bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
-            }
-            if (lane == 0) {
-              lpb[rc.w - r0] = a;
-              if (two) lpb[rc2.w - r0] = bsum;
-            }
+          for (int v = 0; v < W; ++v) acc[v] = 0.f;
+#pragma unroll 4
+          for (int c = sub; c < ncols; c += NSUB) {
+            float e[W];
+            unpack16(data + c * 64 + g * W, e);
+            const float yv = yc[c];
+#pragma unroll
+            for (int v = 0; v < W; ++v) acc[v] += e[v] * yv;
           }
-          jb += nrec;
+          // the warp's 32 / G column subsets summed; lanes below G hold the sums of their W rows
+#pragma unroll
+          for (int o = G; o < 32; o <<= 1)
+#pragma unroll
+            for (int v = 0; v < W; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+          if (lane < G)
+#pragma unroll
+            for (int v = 0; v < W; ++v) part[warp * 64 + g * W + v] += acc[v];
         } else if (kind == LD) {
-          // y[r0 + rr] = s[rr] + sum_{c < rr} inv(L_bb)[rr][c] s[c], s = (R_i r)_b - lp; TPR threads a row
+          // y[r0 + rr] = s[rr] + sum_{c < rr} inv(L_bb)[rr][c] s[c]; TPR threads a row
           const int rr = tid / TPR, qd = tid % TPR;
           float v = 0.f;
           if (rr < tb) {
@@ -309,17 +367,15 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
             float v1 = 0.f;
             int cc = CPT * qd;
             for (; cc + 1 < cend; cc += 2) {
-              v += to_f(d[cc]) * (rhs[r0 + cc] - lpb[cc]);
-              v1 += to_f(d[cc + 1]) * (rhs[r0 + cc + 1] - lpb[cc + 1]);
+              v += to_f(d[cc]) * s64[cc];
+              v1 += to_f(d[cc + 1]) * s64[cc + 1];
             }
-            if (cc < cend) v += to_f(d[cc]) * (rhs[r0 + cc] - lpb[cc]);
+            if (cc < cend) v += to_f(d[cc]) * s64[cc];
             v += v1;
           }
 #pragma unroll
           for (int sh = 1; sh < TPR; sh <<= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
-          if (rr < tb && qd == 0) x[r0 + rr] = rhs[r0 + rr] - lpb[rr] + v;
-          if (tid < 64) lp[((b + 1) & 1) * 64 + tid] = 0.f;  // the next block's panel products
-          jb = 0;
+          if (rr < tb && qd == 0) x[r0 + rr] = s64[rr] + v;
         } else if (kind == UD) {
           // solution rows: rhs[r0 + rr] = sum_{c >= rr} inv(U_bb)[rr][c] y[r0 + c]; TPR threads a row
           const int rr = tid / TPR, qd = tid % TPR;
@@ -341,25 +397,34 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
           for (int sh = 1; sh < TPR; sh <<= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
           if (rr < tb && qd == 0) rhs[r0 + rr] = v;
         } else {
-          // right-looking update of the rows above the block: y[r] -= sum_c U[r][c] x_c over the chunk's
-          // columns c; position p is always owned by the thread with p / W == tid (mod CONSUMERS), so that
-          // the chunks of one block update it in order without a barrier between them.  The chunk's
-          // columns come by increasing first row: the ones that reach p are a prefix.
-          const int cmin = rec[0].y;
-          constexpr int STRIDE = CONSUMERS * W;
-          int p = tid * W;
-          if (p < cmin) p += ((cmin - p + STRIDE - 1) / STRIDE) * STRIDE;
-          for (; p < r0; p += STRIDE) {
+          // right-looking update of the rows above the block: y[r] -= sum_{cc < 64} U[r][r0 + cc] x[r0 + cc]
+          // for the chunk's rows r = ra .. ra + R.  The chunk is column-major, R rows a column (R x the
+          // element size = 64 bytes modulo 128, so that the two columns a quarter-warp reads fall on
+          // different banks); a warp takes 4 groups of W rows and its lanes 8 column subsets
+          const int ra = hd.x, R = hd.z / 64, ng = R / W;
+          const int sub = lane >> 2;
+          for (int gb = warp * 4; gb < ng; gb += 4 * CW) {
+            const int gq = gb + (lane & 3);
             float acc[W];
 #pragma unroll
             for (int v = 0; v < W; ++v) acc[v] = 0.f;
-            for (int j = 0; j < nrec; ++j) {
-              const int4 rc = rec[j];
-              if (rc.y > p) break;
-              axpy16(acc, data + (rc.x - dbase) + (p - rc.y), rhs[rc.w]);
+            if (gq < ng) {
+#pragma unroll 4
+              for (int cc = sub; cc < 64; cc += 8) {
+                float e[W];
+                unpack16(data + cc * R + gq * W, e);
+                const float xv = rhs[r0 + cc];
+#pragma unroll
+                for (int v = 0; v < W; ++v) acc[v] += e[v] * xv;
+              }
             }
 #pragma unroll
-            for (int v = 0; v < W; ++v) x[p + v] -= acc[v];
+            for (int o = 4; o < 32; o <<= 1)
+#pragma unroll
+              for (int v = 0; v < W; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+            if (gq < ng && lane < 4)
+#pragma unroll
+              for (int v = 0; v < W; ++v) x[ra + gq * W + v] -= acc[v];
           }
         }
       }
@@ -380,10 +445,6 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
       }
     } else {
       for (int l = tid; l < n; l += CONSUMERS) out[o + l] = (mode == 1 ? D[o + l] : 1.0) * (double)rhs[l];
-    }
-    if (consumer_sync_or<CONSUMERS>(aborted)) {
-      aborted = 1;
-      break;
     }
   }
   if (aborted) {
@@ -421,22 +482,36 @@ __global__ void k_pack_stream(int nchunks, int N, const int* __restrict__ choff,
     T* S = stream + soff[i];
     const int4* hd = meta + mpos[c];
     const int kind = hd->y & 3, r0 = (hd->y >> 2) * 64, tb = min(64, n - r0);
-    for (int j = 1; j <= hd->x; ++j) {
-      const int4 rc = hd[j];
-      const int len = rc.z - rc.y;
-      for (int e = lane; e < len; e += 32) {
-        const int col = rc.y + e;
-        T v = T(0.f);
-        if (kind == LP) {
-          v = F[(int64_t)rc.w * L + col];                                     // L[r][col], col < r0 <= r
-        } else if (kind == LD) {
-          if (col < r0 + rc.w) v = F[(int64_t)(r0 + rc.w) * L + col];         // inv(L_bb), strictly lower
-        } else if (kind == UD) {
-          if (col >= r0 + rc.w && col < r0 + tb) v = F[(int64_t)(r0 + rc.w) * L + col];  // inv(U_bb), upper
-        } else {
-          v = F[(int64_t)col * L + rc.w];                                     // U[col][c], col < r0 <= c
+    if (kind == LP) {
+      // column-major: (c0 + cl, rr) at cl * 64 + rr, L[r0 + rr][c0 + cl] (zero below the block's rows)
+      const int c0 = hd->x, ncols = hd->z / 64;
+      T* dst = S + hd->w;
+      for (int e = lane; e < ncols * 64; e += 32) {
+        const int cl = e >> 6, rr = e & 63;
+        dst[e] = rr < tb ? F[(int64_t)(r0 + rr) * L + c0 + cl] : T(0.f);
+      }
+    } else if (kind == UP) {
+      // column-major: (ra + rl, cc) at cc * R + rl, U[ra + rl][r0 + cc] (zero past the block's columns)
+      const int ra = hd->x, R = hd->z / 64;
+      T* dst = S + hd->w;
+      for (int e = lane; e < R * 64; e += 32) {
+        const int cc = e / R, rl = e % R;
+        dst[e] = cc < tb ? F[(int64_t)(ra + rl) * L + r0 + cc] : T(0.f);
+      }
+    } else {
+      for (int j = 1; j <= hd->x; ++j) {
+        const int4 rc = hd[j];
+        const int len = rc.z - rc.y;
+        for (int e = lane; e < len; e += 32) {
+          const int col = rc.y + e;
+          T v = T(0.f);
+          if (kind == LD) {
+            if (col < r0 + rc.w) v = F[(int64_t)(r0 + rc.w) * L + col];                    // inv(L_bb), lower
+          } else {
+            if (col >= r0 + rc.w && col < r0 + tb) v = F[(int64_t)(r0 + rc.w) * L + col];  // inv(U_bb), upper
+          }
+          S[rc.x + e] = v;
         }
-        S[rc.x + e] = v;
       }
     }
   }
@@ -460,6 +535,10 @@ void stream_prepare(a2ls_handle* h, const T* fac) {
   auto lo = [](int v) { return v / W * W; };
   auto up = [](int v) { return (v + W - 1) / W * W; };
   const int stage_elems = STAGE_DATA / (int)sizeof(T);
+  // panel chunks: L by 64-row columns (32 KB), U by 64-column row blocks of 28 groups of W rows (the
+  // column stride, 448 bytes, is 64 modulo 128)
+  const int lp_cols = STAGE_DATA / (64 * (int)sizeof(T));
+  const int up_rows = 28 * W;
   std::vector<int4> meta;
   std::vector<int> mpos, choff(N + 1, 0);
   std::vector<int64_t> soff(N + 1, 0);
@@ -487,13 +566,18 @@ void stream_prepare(a2ls_handle* h, const T* fac) {
       meta[hdr].z += len;
       off += len;
     };
+    // a panel chunk: header {first column or row, kind | block << 2, elements, data offset}, no records
+    auto panel = [&](int kind, int b, int first, int count) {
+      mpos.push_back((int)meta.size());
+      meta.push_back(make_int4(first, kind | (b << 2), 64 * count, off));
+      off += 64 * count;
+    };
     for (int b = 0; b < nb; ++b) {
       const int r0 = b * TB, tb = std::min(TB, n - r0);
-      for (int r = r0; r < r0 + tb; ++r) {
-        const int cs = lo(pf[o + r]);
-        if (cs < r0) add(LP, b, cs, r0, r);
-      }
-      close();
+      // L panel of the block: columns from the first envelope column of its rows up to r0, all 64 rows
+      int cmin = r0;
+      for (int r = r0; r < r0 + tb; ++r) cmin = std::min(cmin, lo(pf[o + r]));
+      for (int c = cmin; c < r0; c += lp_cols) panel(LP, b, c, std::min(lp_cols, r0 - c));
       for (int rr = 0; rr < tb; ++rr) add(LD, b, r0, r0 + up(rr), rr);
       close();
     }
@@ -501,19 +585,14 @@ void stream_prepare(a2ls_handle* h, const T* fac) {
       const int r0 = b * TB, tb = std::min(TB, n - r0);
       for (int rr = 0; rr < tb; ++rr) add(UD, b, r0 + lo(rr), r0 + up(tb), rr);
       close();
-      // the block's columns by increasing first row (the update of a row reads a prefix of a chunk)
-      std::vector<std::pair<int, int>> cols;
-      for (int c = r0; c < r0 + tb; ++c) {
-        const int cs = lo(pg[o + c]);
-        if (cs < r0) cols.push_back({cs, c});
-      }
-      std::stable_sort(cols.begin(), cols.end());
-      for (const auto& pc : cols) add(UP, b, pc.first, r0, pc.second);
-      close();
+      // U panel of the block: rows from the first envelope row of its columns up to r0, all 64 columns
+      int rmin = r0;
+      for (int c = r0; c < r0 + tb; ++c) rmin = std::min(rmin, lo(pg[o + c]));
+      for (int r = rmin; r < r0; r += up_rows) panel(UP, b, r, std::min(up_rows, r0 - r));
     }
     soff[i + 1] = soff[i] + off;
-    // copy time of the bytes plus the dependent chain of 2 nb diagonal steps (about 2 us each, the time
-    // the copy engine moves 64 KB for one SM)
+    // work-queue order: copy time of the bytes plus the dependent chain of 2 nb diagonal steps (about
+    // 2 us each, the time the copy engine moves 64 KB for one SM)
     cost[i] = (double)off * sizeof(T) + 2.0 * nb * 65536.0;
   }
   choff[N] = (int)mpos.size();
@@ -542,7 +621,8 @@ void stream_prepare(a2ls_handle* h, const T* fac) {
                                                 h->d_fld, h->d_ffoff, fac, static_cast<T*>(S.d_stream));
   A2LS_LAUNCH();
   S.xcap = (int)round_up(h->max_n, TB);
-  const size_t fixed = sizeof(float) * (2 * (size_t)S.xcap + 2 * 64);  // the two vectors, the panel products
+  // the two vectors, the warps' panel sums (8 warps at most) and the block's s
+  const size_t fixed = sizeof(float) * (2 * (size_t)S.xcap + 8 * 64 + 64);
   // the kernel shapes: 8 consumer warps, one CTA per SM; 4 consumer warps, two CTAs per SM; 8 consumer
   // warps, two CTAs per SM
   for (int v = 0; v < 3; ++v) {
@@ -568,35 +648,16 @@ void stream_prepare(a2ls_handle* h, const T* fac) {
       A2LS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_local_solve_stream<T, 8, 2>, 288, sh.smem));
     }
     if (occ < ctas) continue;
-    // largest-first assignment of the subdomains to the least-loaded CTA
-    const int G = std::max(1, std::min(N, sms * ctas));
-    std::vector<int> order(N);
-    for (int i = 0; i < N; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-    using Load = std::pair<double, int>;
-    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-    for (int g = 0; g < G; ++g) heap.push({0.0, g});
-    std::vector<std::vector<int>> lists(G);
-    for (int i : order) {
-      Load l = heap.top();
-      heap.pop();
-      lists[l.second].push_back(i);
-      heap.push({l.first + cost[i], l.second});
-    }
-    std::vector<int> cta_off(G + 1, 0), cta_list;
-    cta_list.reserve(N);
-    for (int g = 0; g < G; ++g) {
-      cta_list.insert(cta_list.end(), lists[g].begin(), lists[g].end());
-      cta_off[g + 1] = (int)cta_list.size();
-    }
-    sh.ncta = G;
-    sh.d_cta_off = dalloc<int>(h, G + 1);
-    sh.d_cta_list = dalloc<int>(h, N);
-    A2LS_CUDA(cudaMemcpyAsync(sh.d_cta_off, cta_off.data(), sizeof(int) * (G + 1), cudaMemcpyHostToDevice, st));
-    A2LS_CUDA(cudaMemcpyAsync(sh.d_cta_list, cta_list.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
+    sh.ncta = std::max(1, std::min(N, sms * ctas));
     sh.ready = true;
   }
   S.ready = S.shape[0].ready || S.shape[1].ready || S.shape[2].ready;
+  // the work order of the queue: the subdomains by decreasing cost
+  std::vector<int> order(N);
+  for (int i = 0; i < N; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  S.d_order = dalloc<int>(h, N);
+  A2LS_CUDA(cudaMemcpyAsync(S.d_order, order.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
   A2LS_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -609,17 +670,18 @@ void launch_local_solve_stream(a2ls_handle* h, int config, const double* t, cons
   const int v = config == LS_STREAM2 ? 1 : (config == LS_STREAM3 ? 2 : 0);
   const StreamSolve::Shape& sh = S.shape[v];
   if (!sh.ready || S.elem_bytes != (int)sizeof(T)) fail(A2LS_ERR_ARG, "streaming local solves not prepared");
+  A2LS_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->st));
   if (v == 0)
     k_local_solve_stream<T, 8, 1><<<sh.ncta, 288, sh.smem, h->st>>>(
-        sh.nstages, S.xcap, sh.d_cta_off, sh.d_cta_list, S.d_choff, S.d_mpos, S.d_meta, S.d_soff,
+        sh.nstages, S.xcap, h->N, S.d_order, h->d_counter, S.d_choff, S.d_mpos, S.d_meta, S.d_soff,
         static_cast<const T*>(S.d_stream), h->d_off, h->d_nI, h->d_ni, h->d_idx, h->d_D, t, q, z, mode, h->d_status);
   else if (v == 2)
     k_local_solve_stream<T, 8, 2><<<sh.ncta, 288, sh.smem, h->st>>>(
-        sh.nstages, S.xcap, sh.d_cta_off, sh.d_cta_list, S.d_choff, S.d_mpos, S.d_meta, S.d_soff,
+        sh.nstages, S.xcap, h->N, S.d_order, h->d_counter, S.d_choff, S.d_mpos, S.d_meta, S.d_soff,
         static_cast<const T*>(S.d_stream), h->d_off, h->d_nI, h->d_ni, h->d_idx, h->d_D, t, q, z, mode, h->d_status);
   else
     k_local_solve_stream<T, 4, 2><<<sh.ncta, 160, sh.smem, h->st>>>(
-        sh.nstages, S.xcap, sh.d_cta_off, sh.d_cta_list, S.d_choff, S.d_mpos, S.d_meta, S.d_soff,
+        sh.nstages, S.xcap, h->N, S.d_order, h->d_counter, S.d_choff, S.d_mpos, S.d_meta, S.d_soff,
         static_cast<const T*>(S.d_stream), h->d_off, h->d_nI, h->d_ni, h->d_idx, h->d_D, t, q, z, mode, h->d_status);
   A2LS_LAUNCH();
 }
