@@ -170,7 +170,9 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
     const double* __restrict__ t, const double* __restrict__ q, double* __restrict__ out, int mode, int* st) {
   constexpr int W = V16<T>::W;
   constexpr int CONSUMER_WARPS = CW, CONSUMERS = 32 * CW;
-  constexpr int TPR = CONSUMERS / 64, CPT = 64 / TPR;  // diagonal blocks: threads per row, columns per thread
+  // diagonal blocks: LPR lanes a row (one 16-byte vector each), RPI rows a warp step, RPW rows a warp,
+  // IT steps
+  constexpr int LPR = 64 / W, RPI = 32 / LPR, RPW = 64 / CW, IT = RPW / RPI;
   extern __shared__ __align__(128) unsigned char sm[];
   unsigned char* stages = sm;                                                  // nstages x STAGE_BYTES
   float* rhs = reinterpret_cast<float*>(sm + (size_t)nstages * STAGE_BYTES);  // xcap: R_i r, then the solution
@@ -358,44 +360,67 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
 #pragma unroll
             for (int v = 0; v < W; ++v) part[warp * 64 + g * W + v] += acc[v];
         } else if (kind == LD) {
-          // y[r0 + rr] = s[rr] + sum_{c < rr} inv(L_bb)[rr][c] s[c]; TPR threads a row
-          const int rr = tid / TPR, qd = tid % TPR;
-          float v = 0.f;
-          if (rr < tb) {
-            const T* d = data + (rec[rr].x - dbase);
-            const int cend = min(CPT * qd + CPT, rr);
-            float v1 = 0.f;
-            int cc = CPT * qd;
-            for (; cc + 1 < cend; cc += 2) {
-              v += to_f(d[cc]) * s64[cc];
-              v1 += to_f(d[cc + 1]) * s64[cc + 1];
+          // y[r0 + rr] = s[rr] + sum_{c < rr} inv(L_bb)[rr][c] s[c]: LPR lanes a row, one 16-byte vector
+          // each; a warp's rows RPI at a time, their reductions interleaved at the end
+          const int q = lane % LPR, sl = lane / LPR;
+          float sv[W], e[W], acc[IT];
+#pragma unroll
+          for (int v = 0; v < W; ++v) sv[v] = s64[q * W + v];
+#pragma unroll
+          for (int it = 0; it < IT; ++it) {
+            const int rr = warp * RPW + it * RPI + sl;
+            float a = 0.f;
+            if (rr < tb) {
+              const int4 rc = rec[rr];
+              if (q * W < rc.z - rc.y) {
+                unpack16(data + (rc.x - dbase) + q * W, e);
+#pragma unroll
+                for (int v = 0; v < W; ++v)
+                  if (q * W + v < rr) a += e[v] * sv[v];
+              }
             }
-            if (cc < cend) v += to_f(d[cc]) * s64[cc];
-            v += v1;
+            acc[it] = a;
           }
 #pragma unroll
-          for (int sh = 1; sh < TPR; sh <<= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
-          if (rr < tb && qd == 0) x[r0 + rr] = s64[rr] + v;
+          for (int o = 1; o < LPR; o <<= 1)
+#pragma unroll
+            for (int it = 0; it < IT; ++it) acc[it] += __shfl_xor_sync(0xffffffffu, acc[it], o);
+#pragma unroll
+          for (int it = 0; it < IT; ++it) {
+            const int rr = warp * RPW + it * RPI + sl;
+            if (rr < tb && q == 0) x[r0 + rr] = s64[rr] + acc[it];
+          }
         } else if (kind == UD) {
-          // solution rows: rhs[r0 + rr] = sum_{c >= rr} inv(U_bb)[rr][c] y[r0 + c]; TPR threads a row
-          const int rr = tid / TPR, qd = tid % TPR;
-          float v = 0.f;
-          if (rr < tb) {
-            const int4 rc = rec[rr];
-            const T* d = data + (rc.x - dbase) - (rc.y - r0);  // d[c] is column r0 + c
-            const int cend = min(CPT * qd + CPT, tb);
-            float v1 = 0.f;
-            int cc = max(CPT * qd, rr);
-            for (; cc + 1 < cend; cc += 2) {
-              v += to_f(d[cc]) * x[r0 + cc];
-              v1 += to_f(d[cc + 1]) * x[r0 + cc + 1];
+          // solution rows: rhs[r0 + rr] = sum_{c >= rr} inv(U_bb)[rr][c] y[r0 + c], mapped as above
+          const int q = lane % LPR, sl = lane / LPR;
+          float yv[W], e[W], acc[IT];
+#pragma unroll
+          for (int v = 0; v < W; ++v) yv[v] = x[r0 + q * W + v];
+#pragma unroll
+          for (int it = 0; it < IT; ++it) {
+            const int rr = warp * RPW + it * RPI + sl;
+            float a = 0.f;
+            if (rr < tb) {
+              const int4 rc = rec[rr];
+              const int first = rc.y - r0;  // the row's first stored column, rr rounded down
+              if (q * W >= first && q * W < rc.z - r0) {
+                unpack16(data + (rc.x - dbase) + (q * W - first), e);
+#pragma unroll
+                for (int v = 0; v < W; ++v)
+                  if (q * W + v >= rr && q * W + v < tb) a += e[v] * yv[v];
+              }
             }
-            if (cc < cend) v += to_f(d[cc]) * x[r0 + cc];
-            v += v1;
+            acc[it] = a;
           }
 #pragma unroll
-          for (int sh = 1; sh < TPR; sh <<= 1) v += __shfl_xor_sync(0xffffffffu, v, sh);
-          if (rr < tb && qd == 0) rhs[r0 + rr] = v;
+          for (int o = 1; o < LPR; o <<= 1)
+#pragma unroll
+            for (int it = 0; it < IT; ++it) acc[it] += __shfl_xor_sync(0xffffffffu, acc[it], o);
+#pragma unroll
+          for (int it = 0; it < IT; ++it) {
+            const int rr = warp * RPW + it * RPI + sl;
+            if (rr < tb && q == 0) rhs[r0 + rr] = acc[it];
+          }
         } else {
           // right-looking update of the rows above the block: y[r] -= sum_{cc < 64} U[r][r0 + cc] x[r0 + cc]
           // for the chunk's rows r = ra .. ra + R.  The chunk is column-major, R rows a column (R x the
