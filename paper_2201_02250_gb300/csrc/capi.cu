@@ -298,6 +298,19 @@ static void factor_and_coarse(a2ls_handle* h, bool need_coarse, double* times) {
   // when it runs in at least the precision of the A_ii factors; only the Schur complement on the
   // overlap rows is factored twice.
   const bool share = need_coarse && Unit<TT>::u <= Unit<T>::u;
+  // With a shared factorisation the overlap pivots of A_ii (T) need only the Schur complement copied
+  // from the splitting's interior factors: they run on a second stream, alongside the splitting's
+  // overlap pivots and the eigensolve, and join the handle's stream at the end (sequential when the
+  // per-kernel timing is on, so that each kernel's events see it alone).
+  struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t done = nullptr;
+    ~SideStream() {
+      if (done) cudaEventDestroy(done);
+      if (s) cudaStreamDestroy(s);
+    }
+  } side;
+  const bool overlap_local = share && !h->opt.timing;
   if (!share) {
     KTime kt(h, KT_LU_LOCAL, lu_flops);
     lu_batched<T>(h, fa, 0, nullptr, dscale);
@@ -309,13 +322,33 @@ static void factor_and_coarse(a2ls_handle* h, bool need_coarse, double* times) {
       if (share) {
         lu_batched<TT>(h, ft, 1, lastp, dscale, 0);
         schur_copy<TT, T>(h, ft, fa, lastp);
+        if (overlap_local) {
+          cudaEvent_t copied;
+          A2LS_CUDA(cudaEventCreateWithFlags(&copied, cudaEventDisableTiming));
+          A2LS_CUDA(cudaEventRecord(copied, st));
+          A2LS_CUDA(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking));
+          A2LS_CUDA(cudaEventCreateWithFlags(&side.done, cudaEventDisableTiming));
+          A2LS_CUDA(cudaStreamWaitEvent(side.s, copied, 0));
+          A2LS_CUDA(cudaEventDestroy(copied));
+          {
+            struct Restore {  // the handle's stream comes back on every exit path
+              a2ls_handle* h;
+              cudaStream_t st;
+              ~Restore() { h->st = st; }
+            } restore{h, st};
+            h->st = side.s;
+            lu_batched<T>(h, fa, 0, nullptr, dscale, 1);
+            invert_diag_tiles<T>(h, fa);
+          }
+          A2LS_CUDA(cudaEventRecord(side.done, side.s));
+        }
         lu_batched<TT>(h, ft, 1, lastp, dscale, 1);
       } else {
         lu_batched<TT>(h, ft, 1, lastp, dscale);
       }
       invert_diag_tiles<TT>(h, ft);
     }
-    if (share) {
+    if (share && !overlap_local) {
       KTime kt(h, KT_LU_LOCAL, gamma_flops);
       lu_batched<T>(h, fa, 0, nullptr, dscale, 1);
       invert_diag_tiles<T>(h, fa);
@@ -328,6 +361,7 @@ static void factor_and_coarse(a2ls_handle* h, bool need_coarse, double* times) {
     eigensolve(h, ft, lastp, dscale);  // ends with the coarse operator
     dfree(h, ft);
   }
+  if (side.done) A2LS_CUDA(cudaStreamWaitEvent(st, side.done, 0));  // the A_ii factors are complete
   times[Phase::SETUP_EIG] = tm.stop();
   dfree(h, dscale);
   dfree(h, lastp);
