@@ -23,7 +23,7 @@ POU = {"boolean": 0, "multiplicity": 1}
  Q_KERNEL_TIMES, Q_TUNING, Q_EIG_UNCONVERGED, Q_ENVELOPE, Q_EIGRES) = range(15)
 TRACKED_KERNELS = ["lu_local", "lu_splitting", "eig_triangular_solves", "eig_orthogonalisation",
                    "eig_rayleigh_ritz", "coarse_lu", "coarse_inverse", "apply_local_solves"]
-PHASES = ["graph", "extract", "lu", "eig_coarse", "coarse", "setup_total", "solve_total", "apply"]
+PHASES = ["graph", "extract", "lu", "eig_coarse", "coarse", "setup_total", "solve_total", "apply", "apply_prep"]
 
 
 class A2lsError(RuntimeError):

@@ -58,7 +58,7 @@ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 // The handle: every device array the preconditioner owns.
 // ---------------------------------------------------------------------------
 struct Phase { enum { SETUP_GRAPH, SETUP_EXTRACT, SETUP_LU, SETUP_EIG, SETUP_COARSE, SETUP_TOTAL,
-                      SOLVE_TOTAL, SOLVE_APPLY, COUNT }; };
+                      SOLVE_TOTAL, SOLVE_APPLY, SETUP_APPLY_PREP, COUNT }; };
 
 // the apply's local factors repacked as one stream in solve order (k_stream.cu)
 struct StreamSolve {
@@ -66,8 +66,8 @@ struct StreamSolve {
   int elem_bytes = 0, nchunks = 0, xcap = 0;
   int64_t stream_elems = 0;
   void* d_stream = nullptr;
-  int4* d_meta = nullptr;                    // chunk headers, each followed by its segment records
-  int *d_mpos = nullptr, *d_choff = nullptr;
+  int4* d_meta = nullptr;                    // chunk headers
+  int* d_choff = nullptr;                    // chunks of each subdomain
   int* d_order = nullptr;                    // work-queue order of the subdomains (by decreasing cost)
   int64_t* d_soff = nullptr;
   // launch shapes: [0] 8 consumer warps, one CTA per SM; [1] 4 consumer warps, two CTAs per SM; [2] 8

@@ -494,6 +494,7 @@ int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int
       else if (ep == A2LS_FP32) factor_and_coarse<float, float>(h, need_coarse, h->times);
       else factor_and_coarse<float, dfloat>(h, need_coarse, h->times);
     }
+    Timer tprep(st);
     h->h_fld = h->h_ld;
     h->h_ffoff = h->h_foff;
     h->d_fld = h->d_ld;
@@ -534,6 +535,7 @@ int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int
     // load the module holding a2ls_apply_static's scratch array now, while allocation is allowed
     prime_static_scratch();
     sync_and_check(h, "setup");
+    h->times[Phase::SETUP_APPLY_PREP] = tprep.stop();
     h->times[Phase::SETUP_TOTAL] = total.stop();
     *out = h;
     return A2LS_OK;

@@ -443,21 +443,25 @@ void lu_batched(a2ls_handle* h, T* fac, int allow_last_zero, double* last_pivot,
 // eliminated both share every factor entry and their Schur complements on the overlap differ by
 // diag(s_i): dst = src + diag(s_i) on the overlap block, converted to the precision of the A_ii
 // factors.  When the subdomain has no overlap rows the splitting's replaced last pivot is restored.
+// Only the entries inside the envelope are copied (dst is zero elsewhere): row r from its first
+// envelope column pf_r, skipping the 64-column tiles of U whose columns all start below row r.
 template <class TS, class TD>
 __global__ void k_schur_copy(const int* ni, const int* nI, const int* ld, const int64_t* foff, const int* off,
                              const TS* __restrict__ src, TD* __restrict__ dst, const double* lump,
-                             const double* last_pivot) {
+                             const double* last_pivot, const int* __restrict__ pf, const int* __restrict__ toff,
+                             const int* __restrict__ tg) {
   const int i = blockIdx.x;
   const int n = ni[i], n_I = nI[i];
   const int64_t L = ld[i];
   const TS* S = src + foff[i];
   TD* D = dst + foff[i];
+  const int* tgi = tg + toff[i];
   for (int r = blockIdx.y; r < n; r += gridDim.y) {
     const TS* Sr = S + (int64_t)r * L;
     TD* Dr = D + (int64_t)r * L;
     // off-diagonal entries convert directly (a double-float pair rounds to FP32 as hi + lo)
-    for (int c = threadIdx.x; c < n; c += blockDim.x)
-      if (c != r) Dr[c] = (TD)Sr[c];
+    for (int c = pf[off[i] + r] + threadIdx.x; c < n; c += blockDim.x)
+      if (c != r && (c < r || tgi[c / TB] <= r)) Dr[c] = (TD)Sr[c];
     if (threadIdx.x == 0) {
       double v = (double)Sr[r];
       if (r >= n_I) v += lump[off[i] + r];
@@ -471,7 +475,7 @@ template <class TS, class TD>
 void schur_copy(a2ls_handle* h, const TS* src, TD* dst, const double* last_pivot) {
   dim3 grid(h->N, 32);
   k_schur_copy<TS, TD><<<grid, 256, 0, h->st>>>(h->d_ni, h->d_nI, h->d_ld, h->d_foff, h->d_off, src, dst,
-                                                h->d_lump, last_pivot);
+                                                h->d_lump, last_pivot, h->d_pf, h->d_toff, h->d_tg);
   A2LS_LAUNCH();
 }
 template void schur_copy<double, double>(a2ls_handle*, const double*, double*, const double*);

@@ -19,12 +19,12 @@
 // boundaries (its column range rounded outwards; the entries added are zeros).
 // Chunks hold at most 32 KB: 128 (FP32) or 256 (BF16) columns of an L panel, 28 groups of 16 bytes of
 // rows of a U panel (a column stride of 64 bytes modulo 128 keeps the reads conflict-free), or one
-// diagonal triangle with its row records.
+// diagonal triangle (its row offsets are prefix sums of the rounded row lengths).
 
 // Kernel.  One or two CTAs per SM, persistent over a work queue of the subdomains (largest first).
 // One producer warp streams the chunks through a ring of shared-memory stages with bulk asynchronous
 // copies (cp.async.bulk, completion counted in bytes on an mbarrier per stage); each stage also
-// receives the chunk's header (and a triangle's row records), so that the consumers read no global
+// receives the chunk's header, so that the consumers read no global
 // memory but the right-hand side and their outputs.  The consumer warps run the solves from shared memory:
 // the panel products, the 64 x 64 triangle products of the diagonal blocks and the right-looking
 // updates, with the gathered right-hand side and the solution held in shared memory.  The producer
@@ -41,12 +41,31 @@ namespace a2ls {
 namespace lss {
 
 constexpr int STAGE_DATA = 32768;                // factor bytes per stage
-constexpr int STAGE_RECS = 64;                   // segment records per chunk at most (one 64-row block)
-constexpr int STAGE_META = 16 * (1 + STAGE_RECS);  // chunk header and its records (16 bytes each)
+constexpr int STAGE_META = 16;                   // the chunk's header
 constexpr int STAGE_BYTES = STAGE_META + STAGE_DATA;
 constexpr int MAX_STAGES = 8;
 constexpr long WAIT_LIMIT = 1L << 26;            // polls of an mbarrier before giving up
 enum { LP = 0, LD = 1, UD = 2, UP = 3 };
+
+// The diagonal triangles of a block (tb rows) are stored by rows rounded to W elements: row rr of
+// inv(L_bb) holds columns r0 .. r0 + up(rr), row rr of inv(U_bb) columns r0 + lo(rr) .. r0 + up(tb).
+// Their offsets are prefix sums with closed forms: sum_{j < m} lo(j) and sum_{j < m} up(j).
+template <int W> __host__ __device__ __forceinline__ int tri_sumlo(int m) {
+  const int q = m / W, r = m % W;
+  return W * (W * q * (q - 1) / 2 + r * q);
+}
+template <int W> __host__ __device__ __forceinline__ int tri_sumup(int m) {
+  return tri_sumlo<W>(m) + W * (m - (m + W - 1) / W);
+}
+template <int W> __host__ __device__ __forceinline__ int tri_lo(int v) { return v / W * W; }
+template <int W> __host__ __device__ __forceinline__ int tri_up(int v) { return (v + W - 1) / W * W; }
+// elements of a block's triangles and the offset of row rr in them
+template <int W> __host__ __device__ __forceinline__ int ld_elems(int tb) { return tri_sumup<W>(tb); }
+template <int W> __host__ __device__ __forceinline__ int ld_off(int rr) { return tri_sumup<W>(rr); }
+template <int W> __host__ __device__ __forceinline__ int ud_elems(int tb) { return tb * tri_up<W>(tb) - tri_sumlo<W>(tb); }
+template <int W> __host__ __device__ __forceinline__ int ud_off(int rr, int tb) {
+  return rr * tri_up<W>(tb) - tri_sumlo<W>(rr);
+}
 
 template <class T> struct V16;                   // elements per 16 bytes
 template <> struct V16<float> { static constexpr int W = 4; };
@@ -151,10 +170,8 @@ __device__ __forceinline__ int consumer_sync_or(int v) {
 namespace a2ls {
 namespace lss {
 
-// meta: per chunk a header int4 {segments, kind | block << 2, elements, element offset of its data in
-// the subdomain's stream} followed by its segment records int4 {element offset, first column, end
-// column, row}; the row is the local row (LP), the local column (UP) or the row inside the block (LD,
-// UD).  mpos: per chunk the index of its header in meta.
+// meta: per chunk a header int4 {first column (LP) or row (UP) of the panel, kind | block << 2,
+// elements, element offset of its data in the subdomain's stream}.
 // xcap: floats of each shared vector (the largest subdomain rounded up to 64 rows).
 // CW consumer warps and one producer warp; CTAS_PER_SM CTAs share an SM, each on its own subdomains, so
 // that one CTA's dependent chain of diagonal steps overlaps the others' panel streaming.  Work queue:
@@ -164,8 +181,8 @@ namespace lss {
 template <class T, int CW, int CTAS_PER_SM>
 __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_stream(
     int nstages, int xcap, int nwork, const int* __restrict__ sched, int* __restrict__ counter,
-    const int* __restrict__ choff, const int* __restrict__ mpos, const int4* __restrict__ meta,
-    const int64_t* __restrict__ soff, const T* __restrict__ stream, const int* __restrict__ off,
+    const int* __restrict__ choff, const int4* __restrict__ meta, const int64_t* __restrict__ soff,
+    const T* __restrict__ stream, const int* __restrict__ off,
     const int* __restrict__ nI, const int* __restrict__ ni, const int* __restrict__ idx, const double* __restrict__ D,
     const double* __restrict__ t, const double* __restrict__ q, double* __restrict__ out, int mode, int* st) {
   constexpr int W = V16<T>::W;
@@ -224,16 +241,9 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
       const int c1 = choff[i + 1];
       for (int cb = choff[i]; cb < c1 && ok; cb += 32) {
         const int cnt = min(32, c1 - cb);
-        int mp = 0;
         int4 hd = make_int4(0, 0, 0, 0);
-        if (lane < cnt) {
-          mp = mpos[cb + lane];
-          hd = meta[mp];
-        }
+        if (lane < cnt) hd = meta[cb + lane];
         for (int u = 0; u < cnt; ++u, ++k) {
-          const int ump = __shfl_sync(0xffffffffu, mp, u);
-          const int hx = __shfl_sync(0xffffffffu, hd.x, u), hkind = __shfl_sync(0xffffffffu, hd.y, u) & 3;
-          const int nrec = (hkind == LD || hkind == UD) ? hx : 0;  // panels carry no records
           const int elems = __shfl_sync(0xffffffffu, hd.z, u);
           const int doff = __shfl_sync(0xffffffffu, hd.w, u);
           const int s = k % nstages;
@@ -241,11 +251,11 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
           if (lane == 0) {
             good = tc::mbar_wait_bounded(&empty[s], ((k / nstages) & 1) ^ 1, WAIT_LIMIT) && !abort_flag;
             if (good) {
-              const uint32_t mbytes = 16u * (uint32_t)(1 + nrec), dbytes = (uint32_t)elems * (uint32_t)sizeof(T);
+              const uint32_t mbytes = STAGE_META, dbytes = (uint32_t)elems * (uint32_t)sizeof(T);
               unsigned char* dst = stages + (size_t)s * STAGE_BYTES;
               stage_sub[s] = i;  // published to the consumers by the arrival below
               mbar_arrive_expect_tx(&full[s], mbytes + dbytes);
-              bulk_g2s(dst, meta + ump, mbytes, &full[s]);
+              bulk_g2s(dst, meta + cb + u, mbytes, &full[s]);
               if (dbytes) bulk_g2s(dst + STAGE_META, base + doff, dbytes, &full[s]);
             }
           }
@@ -304,7 +314,7 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
         hd = *reinterpret_cast<const int4*>(sp);
       } else {
         aborted = 1;
-        hd = __ldg(&meta[__ldg(&mpos[c])]);  // the kind keeps the barriers of this warp in step
+        hd = __ldg(&meta[c]);  // the kind keeps the barriers of this warp in step
       }
       const int kind = hd.y & 3, b = hd.y >> 2, r0 = b * 64, tb = min(64, n - r0);
       const bool diag = kind == LD || kind == UD;
@@ -330,9 +340,7 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
         }
       }
       if (have) {
-        const int4* rec = reinterpret_cast<const int4*>(sp) + 1;
         const T* data = reinterpret_cast<const T*>(sp + STAGE_META);
-        const int dbase = hd.w;
         if (kind == LP) {
           // part[warp][r] += sum over the chunk's columns c of L[r0 + r][c] y[c]: the chunk is column-major
           // (64 rows a column); a thread takes W rows (row group g) and the columns sub, sub + NSUB, ...
@@ -371,9 +379,8 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
             const int rr = warp * RPW + it * RPI + sl;
             float a = 0.f;
             if (rr < tb) {
-              const int4 rc = rec[rr];
-              if (q * W < rc.z - rc.y) {
-                unpack16(data + (rc.x - dbase) + q * W, e);
+              if (q * W < tri_up<W>(rr)) {
+                unpack16(data + ld_off<W>(rr) + q * W, e);
 #pragma unroll
                 for (int v = 0; v < W; ++v)
                   if (q * W + v < rr) a += e[v] * sv[v];
@@ -401,10 +408,9 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
             const int rr = warp * RPW + it * RPI + sl;
             float a = 0.f;
             if (rr < tb) {
-              const int4 rc = rec[rr];
-              const int first = rc.y - r0;  // the row's first stored column, rr rounded down
-              if (q * W >= first && q * W < rc.z - r0) {
-                unpack16(data + (rc.x - dbase) + (q * W - first), e);
+              const int first = tri_lo<W>(rr);  // the row's first stored column
+              if (q * W >= first && q * W < tri_up<W>(tb)) {
+                unpack16(data + ud_off<W>(rr, tb) + (q * W - first), e);
 #pragma unroll
                 for (int v = 0; v < W; ++v)
                   if (q * W + v >= rr && q * W + v < tb) a += e[v] * yv[v];
@@ -489,8 +495,8 @@ namespace lss {
 // rounding of its column range, the other triangle of a diagonal tile, columns past n) are written
 // as zeros.
 template <class T>
-__global__ void k_pack_stream(int nchunks, int N, const int* __restrict__ choff, const int* __restrict__ mpos,
-                              const int4* __restrict__ meta, const int64_t* __restrict__ soff,
+__global__ void k_pack_stream(int nchunks, int N, const int* __restrict__ choff, const int4* __restrict__ meta,
+                              const int64_t* __restrict__ soff,
                               const int* __restrict__ ni, const int* __restrict__ ld, const int64_t* __restrict__ foff,
                               const T* __restrict__ fac, T* __restrict__ stream) {
   const int lane = threadIdx.x & 31;
@@ -505,7 +511,7 @@ __global__ void k_pack_stream(int nchunks, int N, const int* __restrict__ choff,
     const int64_t L = ld[i];
     const T* F = fac + foff[i];
     T* S = stream + soff[i];
-    const int4* hd = meta + mpos[c];
+    const int4* hd = meta + c;
     const int kind = hd->y & 3, r0 = (hd->y >> 2) * 64, tb = min(64, n - r0);
     if (kind == LP) {
       // column-major: (c0 + cl, rr) at cl * 64 + rr, L[r0 + rr][c0 + cl] (zero below the block's rows)
@@ -524,18 +530,19 @@ __global__ void k_pack_stream(int nchunks, int N, const int* __restrict__ choff,
         dst[e] = cc < tb ? F[(int64_t)(ra + rl) * L + r0 + cc] : T(0.f);
       }
     } else {
-      for (int j = 1; j <= hd->x; ++j) {
-        const int4 rc = hd[j];
-        const int len = rc.z - rc.y;
-        for (int e = lane; e < len; e += 32) {
-          const int col = rc.y + e;
+      constexpr int W = V16<T>::W;
+      T* dst = S + hd->w;
+      for (int rr = 0; rr < tb; ++rr) {
+        const int c0 = kind == LD ? 0 : tri_lo<W>(rr), c1 = kind == LD ? tri_up<W>(rr) : tri_up<W>(tb);
+        T* row = dst + (kind == LD ? ld_off<W>(rr) : ud_off<W>(rr, tb)) - c0;
+        for (int c = c0 + lane; c < c1; c += 32) {
           T v = T(0.f);
           if (kind == LD) {
-            if (col < r0 + rc.w) v = F[(int64_t)(r0 + rc.w) * L + col];                    // inv(L_bb), lower
+            if (c < rr) v = F[(int64_t)(r0 + rr) * L + r0 + c];                // inv(L_bb), strictly lower
           } else {
-            if (col >= r0 + rc.w && col < r0 + tb) v = F[(int64_t)(r0 + rc.w) * L + col];  // inv(U_bb), upper
+            if (c >= rr && c < tb) v = F[(int64_t)(r0 + rr) * L + r0 + c];     // inv(U_bb), upper
           }
-          S[rc.x + e] = v;
+          row[c] = v;
         }
       }
     }
@@ -558,81 +565,56 @@ void stream_prepare(a2ls_handle* h, const T* fac) {
   A2LS_CUDA(cudaMemcpyAsync(pg.data(), h->d_pg, sizeof(int) * h->sum_n, cudaMemcpyDeviceToHost, st));
   A2LS_CUDA(cudaStreamSynchronize(st));
   auto lo = [](int v) { return v / W * W; };
-  auto up = [](int v) { return (v + W - 1) / W * W; };
-  const int stage_elems = STAGE_DATA / (int)sizeof(T);
   // panel chunks: L by 64-row columns (32 KB), U by 64-column row blocks of 28 groups of W rows (the
   // column stride, 448 bytes, is 64 modulo 128)
   const int lp_cols = STAGE_DATA / (64 * (int)sizeof(T));
   const int up_rows = 28 * W;
-  std::vector<int4> meta;
-  std::vector<int> mpos, choff(N + 1, 0);
+  std::vector<int4> meta;  // one header per chunk
+  std::vector<int> choff(N + 1, 0);
   std::vector<int64_t> soff(N + 1, 0);
   std::vector<double> cost(N, 0.0);
-  meta.reserve((size_t)h->sum_n * 4 + (size_t)N * 64);
+  meta.reserve((size_t)h->sum_n / 8 + (size_t)N * 64);
   for (int i = 0; i < N; ++i) {
     const int n = h->h_n[i], o = h->h_off[i], nb = (n + TB - 1) / TB;
     int off = 0;
-    choff[i] = (int)mpos.size();
-    int hdr = -1;  // header of the open chunk in meta
-    auto close = [&]() { hdr = -1; };
-    // segment [cs, ce) of `row`, appended to the open chunk while it fits
-    auto add = [&](int kind, int b, int cs, int ce, int row) {
-      const int len = ce - cs;
-      if (hdr >= 0 && (meta[hdr].y != (kind | (b << 2)) || meta[hdr].z + len > stage_elems ||
-                       meta[hdr].x >= STAGE_RECS))
-        close();
-      if (hdr < 0) {
-        hdr = (int)meta.size();
-        mpos.push_back(hdr);
-        meta.push_back(make_int4(0, kind | (b << 2), 0, off));
-      }
-      meta.push_back(make_int4(off, cs, ce, row));
-      meta[hdr].x += 1;
-      meta[hdr].z += len;
-      off += len;
-    };
-    // a panel chunk: header {first column or row, kind | block << 2, elements, data offset}, no records
-    auto panel = [&](int kind, int b, int first, int count) {
-      mpos.push_back((int)meta.size());
-      meta.push_back(make_int4(first, kind | (b << 2), 64 * count, off));
-      off += 64 * count;
+    choff[i] = (int)meta.size();
+    // header {first column or row (panels), kind | block << 2, elements, data offset}
+    auto chunk = [&](int kind, int b, int first, int elems) {
+      meta.push_back(make_int4(first, kind | (b << 2), elems, off));
+      off += elems;
     };
     for (int b = 0; b < nb; ++b) {
       const int r0 = b * TB, tb = std::min(TB, n - r0);
       // L panel of the block: columns from the first envelope column of its rows up to r0, all 64 rows
       int cmin = r0;
       for (int r = r0; r < r0 + tb; ++r) cmin = std::min(cmin, lo(pf[o + r]));
-      for (int c = cmin; c < r0; c += lp_cols) panel(LP, b, c, std::min(lp_cols, r0 - c));
-      for (int rr = 0; rr < tb; ++rr) add(LD, b, r0, r0 + up(rr), rr);
-      close();
+      for (int c = cmin; c < r0; c += lp_cols) chunk(LP, b, c, 64 * std::min(lp_cols, r0 - c));
+      chunk(LD, b, 0, ld_elems<W>(tb));
     }
     for (int b = nb - 1; b >= 0; --b) {
       const int r0 = b * TB, tb = std::min(TB, n - r0);
-      for (int rr = 0; rr < tb; ++rr) add(UD, b, r0 + lo(rr), r0 + up(tb), rr);
-      close();
+      chunk(UD, b, 0, ud_elems<W>(tb));
       // U panel of the block: rows from the first envelope row of its columns up to r0, all 64 columns
       int rmin = r0;
       for (int c = r0; c < r0 + tb; ++c) rmin = std::min(rmin, lo(pg[o + c]));
-      for (int r = rmin; r < r0; r += up_rows) panel(UP, b, r, std::min(up_rows, r0 - r));
+      for (int r = rmin; r < r0; r += up_rows) chunk(UP, b, r, 64 * std::min(up_rows, r0 - r));
     }
     soff[i + 1] = soff[i] + off;
     // work-queue order: copy time of the bytes plus the dependent chain of 2 nb diagonal steps (about
     // 2 us each, the time the copy engine moves 64 KB for one SM)
     cost[i] = (double)off * sizeof(T) + 2.0 * nb * 65536.0;
   }
-  choff[N] = (int)mpos.size();
+  choff[N] = (int)meta.size();
   // device copies of the plan
   StreamSolve& S = h->ss;
   S.elem_bytes = (int)sizeof(T);
-  S.nchunks = (int)mpos.size();
+  S.nchunks = (int)meta.size();
   S.stream_elems = soff[N];
   S.d_stream = dalloc<T>(h, (size_t)soff[N] + W);
   S.d_meta = dalloc<int4>(h, meta.size());
-  S.d_mpos = dalloc<int>(h, mpos.size());
   S.d_choff = dalloc<int>(h, N + 1);
   S.d_soff = dalloc<int64_t>(h, N + 1);
   A2LS_CUDA(cudaMemcpyAsync(S.d_meta, meta.data(), sizeof(int4) * meta.size(), cudaMemcpyHostToDevice, st));
-  A2LS_CUDA(cudaMemcpyAsync(S.d_mpos, mpos.data(), sizeof(int) * mpos.size(), cudaMemcpyHostToDevice, st));
   A2LS_CUDA(cudaMemcpyAsync(S.d_choff, choff.data(), sizeof(int) * (N + 1), cudaMemcpyHostToDevice, st));
   A2LS_CUDA(cudaMemcpyAsync(S.d_soff, soff.data(), sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, st));
   int dev = 0, sms = 152, optin = 0, per_sm = 0;
@@ -642,7 +624,7 @@ void stream_prepare(a2ls_handle* h, const T* fac) {
   A2LS_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
   const int wpb = 8;
   const int blocks = std::max(1, std::min(sms * 16, (S.nchunks + wpb - 1) / wpb));
-  k_pack_stream<T><<<blocks, 32 * wpb, 0, st>>>(S.nchunks, N, S.d_choff, S.d_mpos, S.d_meta, S.d_soff, h->d_ni,
+  k_pack_stream<T><<<blocks, 32 * wpb, 0, st>>>(S.nchunks, N, S.d_choff, S.d_meta, S.d_soff, h->d_ni,
                                                 h->d_fld, h->d_ffoff, fac, static_cast<T*>(S.d_stream));
   A2LS_LAUNCH();
   S.xcap = (int)round_up(h->max_n, TB);
@@ -698,15 +680,15 @@ void launch_local_solve_stream(a2ls_handle* h, int config, const double* t, cons
   A2LS_CUDA(cudaMemsetAsync(h->d_counter, 0, sizeof(int), h->st));
   if (v == 0)
     k_local_solve_stream<T, 8, 1><<<sh.ncta, 288, sh.smem, h->st>>>(
-        sh.nstages, S.xcap, h->N, S.d_order, h->d_counter, S.d_choff, S.d_mpos, S.d_meta, S.d_soff,
+        sh.nstages, S.xcap, h->N, S.d_order, h->d_counter, S.d_choff, S.d_meta, S.d_soff,
         static_cast<const T*>(S.d_stream), h->d_off, h->d_nI, h->d_ni, h->d_idx, h->d_D, t, q, z, mode, h->d_status);
   else if (v == 2)
     k_local_solve_stream<T, 8, 2><<<sh.ncta, 288, sh.smem, h->st>>>(
-        sh.nstages, S.xcap, h->N, S.d_order, h->d_counter, S.d_choff, S.d_mpos, S.d_meta, S.d_soff,
+        sh.nstages, S.xcap, h->N, S.d_order, h->d_counter, S.d_choff, S.d_meta, S.d_soff,
         static_cast<const T*>(S.d_stream), h->d_off, h->d_nI, h->d_ni, h->d_idx, h->d_D, t, q, z, mode, h->d_status);
   else
     k_local_solve_stream<T, 4, 2><<<sh.ncta, 160, sh.smem, h->st>>>(
-        sh.nstages, S.xcap, h->N, S.d_order, h->d_counter, S.d_choff, S.d_mpos, S.d_meta, S.d_soff,
+        sh.nstages, S.xcap, h->N, S.d_order, h->d_counter, S.d_choff, S.d_meta, S.d_soff,
         static_cast<const T*>(S.d_stream), h->d_off, h->d_nI, h->d_ni, h->d_idx, h->d_D, t, q, z, mode, h->d_status);
   A2LS_LAUNCH();
 }
