@@ -72,6 +72,9 @@ def parse_args():
                         "the 2D one on 256x256 with 64 subdomains (small cases for ncu captures)")
     p.add_argument("--no-plain", action="store_true", help="skip the plain FP64 form")
     p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg with host buffers")
+    p.add_argument("--local-solve-kernel", type=int, default=0,
+                   help="force the apply's local-solve kernel of the mixed form (a2ls_options::local_solve_kernel; "
+                        "0 = the autotuner's choice)")
     return p.parse_args()
 
 
@@ -289,8 +292,9 @@ def run_ours(args, rank: int, world: int, device):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        extra = {"local_solve_kernel": args.local_solve_kernel} if precision != "fp64" and args.local_solve_kernel else {}
         P = a2ls.Preconditioner(rowptr, colind, val, part, prob.overlap, prob.nev, stream=stream,
-                                precision=precision, timing=timing, eig_tol=eig_tol)
+                                precision=precision, timing=timing, eig_tol=eig_tol, **extra)
         it, rr, ok = P.solve(b, x, 1e-8)
         e1.record(stream)
         e1.synchronize()
