@@ -1189,6 +1189,13 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
                                                h->d_lrow, h->d_lcol, h->d_lval, h->d_lump, h->d_D, d_off1, X1,
                                                eps_work, kvec, d_kd, d_kpart, h->d_status);
   A2LS_LAUNCH();
+  cudaEvent_t tested;  // the factors are final from here on
+  A2LS_CUDA(cudaEventCreateWithFlags(&tested, cudaEventDisableTiming));
+  A2LS_CUDA(cudaEventRecord(tested, st));
+  struct EventGuard {
+    cudaEvent_t e;
+    ~EventGuard() { cudaEventDestroy(e); }
+  } tested_guard{tested};
   A2LS_CUDA(cudaMemsetAsync(X1, 0, sizeof(T) * hoff1[N], st));
   k_load_vec<T><<<N, 256, 0, st>>>(h->d_ni, h->d_off, d_off1, 1, kvec, d_kd, X1);
   A2LS_LAUNCH();
@@ -1198,6 +1205,44 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   std::vector<int> kd(N), kpart(N);
   A2LS_CUDA(cudaMemcpyAsync(kd.data(), d_kd, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
   A2LS_CUDA(cudaMemcpyAsync(kpart.data(), d_kpart, sizeof(int) * N, cudaMemcpyDeviceToHost, st));
+  // double-float solves on the tensor cores for the subdomains with at most 32 columns (the others,
+  // small full-space subdomains, on the FP32 pipe).  Their factor digits depend only on the factors as
+  // the kernel test left them: they are prepared on a second stream while the rest of the kernel
+  // detection above runs, and the cycles below wait for them.
+  TcSolve tcs;
+  struct TcsGuard {
+    a2ls_handle* h;
+    TcSolve& t;
+    ~TcsGuard() { tc_solve_release(h, t); }
+  } tcs_guard{h, tcs};
+  struct PrepStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t done = nullptr;
+    ~PrepStream() {
+      if (done) cudaEventDestroy(done);
+      if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+    }
+  } prep;
+  if constexpr (std::is_same<T, dfloat>::value) {
+    if (h->opt.tensor_cores) {
+      A2LS_CUDA(cudaStreamCreateWithFlags(&prep.s, cudaStreamNonBlocking));
+      A2LS_CUDA(cudaEventCreateWithFlags(&prep.done, cudaEventDisableTiming));
+      A2LS_CUDA(cudaStreamWaitEvent(prep.s, tested, 0));
+      {
+        struct Restore {  // the handle's stream comes back on every exit path
+          a2ls_handle* h;
+          cudaStream_t st;
+          ~Restore() { h->st = st; }
+        } restore{h, st};
+        h->st = prep.s;
+        tc_solve_prepare(h, fac, tcs);
+      }
+      A2LS_CUDA(cudaEventRecord(prep.done, prep.s));
+    }
+  }
   sync_and_check(h, "kernel detection of the local splittings");
   dfree(h, X1);
 
@@ -1338,17 +1383,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     lvalB = lv;
     DB = dv;
   }
-  // double-float solves on the tensor cores for the subdomains with at most 32 columns (the others,
-  // small full-space subdomains, on the FP32 pipe)
-  TcSolve tcs;
-  struct TcsGuard {
-    a2ls_handle* h;
-    TcSolve& t;
-    ~TcsGuard() { tc_solve_release(h, t); }
-  } tcs_guard{h, tcs};
-  if constexpr (std::is_same<T, dfloat>::value) {
-    if (h->opt.tensor_cores) tc_solve_prepare(h, fac, tcs);
-  }
+  if (prep.done) A2LS_CUDA(cudaStreamWaitEvent(st, prep.done, 0));  // the factor digits are ready
   auto solve_sweep = [&](const int* actv, int forward) {
     if constexpr (std::is_same<T, dfloat>::value) {
       if (tcs.ready) {

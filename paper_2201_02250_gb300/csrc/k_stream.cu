@@ -490,18 +490,20 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
 namespace a2ls {
 namespace lss {
 
-// Pack one chunk per warp: every segment of the chunk copied from the dense block-inverted factors F
-// (row-major, leading dimension ld) into the stream; entries outside a segment's own part (the
-// rounding of its column range, the other triangle of a diagonal tile, columns past n) are written
-// as zeros.
+// Pack one chunk per CTA (256 threads) from the dense block-inverted factors F (row-major, leading
+// dimension ld) into the stream.  The panels are transposes of F's layout: they pass through a shared
+// tile (row stride padded by one element) so that both the reads of F and the writes of the stream
+// are coalesced.  Entries outside a segment's own part (the other triangle of a diagonal tile, rows or
+// columns past the block, the rounding of a triangle's rows) are written as zeros.
 template <class T>
-__global__ void k_pack_stream(int nchunks, int N, const int* __restrict__ choff, const int4* __restrict__ meta,
-                              const int64_t* __restrict__ soff,
-                              const int* __restrict__ ni, const int* __restrict__ ld, const int64_t* __restrict__ foff,
-                              const T* __restrict__ fac, T* __restrict__ stream) {
-  const int lane = threadIdx.x & 31;
-  const int wpb = blockDim.x >> 5;
-  for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < nchunks; c += gridDim.x * wpb) {
+__global__ void __launch_bounds__(256) k_pack_stream(int nchunks, int N, const int* __restrict__ choff,
+                                                     const int4* __restrict__ meta, const int64_t* __restrict__ soff,
+                                                     const int* __restrict__ ni, const int* __restrict__ ld,
+                                                     const int64_t* __restrict__ foff, const T* __restrict__ fac,
+                                                     T* __restrict__ stream) {
+  __shared__ T tile[64 * 65];
+  const int tid = threadIdx.x;
+  for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
     int lo = 0, hi = N;  // choff[lo] <= c < choff[hi]
     while (hi - lo > 1) {
       const int mid = (lo + hi) >> 1;
@@ -510,39 +512,55 @@ __global__ void k_pack_stream(int nchunks, int N, const int* __restrict__ choff,
     const int i = lo, n = ni[i];
     const int64_t L = ld[i];
     const T* F = fac + foff[i];
-    T* S = stream + soff[i];
-    const int4* hd = meta + c;
-    const int kind = hd->y & 3, r0 = (hd->y >> 2) * 64, tb = min(64, n - r0);
+    const int4 hd = meta[c];
+    T* dst = stream + soff[i] + hd.w;
+    const int kind = hd.y & 3, r0 = (hd.y >> 2) * 64, tb = min(64, n - r0);
     if (kind == LP) {
-      // column-major: (c0 + cl, rr) at cl * 64 + rr, L[r0 + rr][c0 + cl] (zero below the block's rows)
-      const int c0 = hd->x, ncols = hd->z / 64;
-      T* dst = S + hd->w;
-      for (int e = lane; e < ncols * 64; e += 32) {
-        const int cl = e >> 6, rr = e & 63;
-        dst[e] = rr < tb ? F[(int64_t)(r0 + rr) * L + c0 + cl] : T(0.f);
+      // column-major: (c0 + cl, rr) at cl * 64 + rr = L[r0 + rr][c0 + cl], in groups of 64 columns
+      const int c0 = hd.x, ncols = hd.z / 64;
+      for (int g = 0; g < ncols; g += 64) {
+        const int gc = min(64, ncols - g);
+        __syncthreads();
+        for (int e = tid; e < 64 * 64; e += 256) {
+          const int rr = e >> 6, cl = e & 63;
+          if (cl < gc) tile[rr * 65 + cl] = rr < tb ? F[(int64_t)(r0 + rr) * L + c0 + g + cl] : T(0.f);
+        }
+        __syncthreads();
+        for (int e = tid; e < gc * 64; e += 256) {
+          const int cl = e >> 6, rr = e & 63;
+          dst[(int64_t)(g + cl) * 64 + rr] = tile[rr * 65 + cl];
+        }
       }
     } else if (kind == UP) {
-      // column-major: (ra + rl, cc) at cc * R + rl, U[ra + rl][r0 + cc] (zero past the block's columns)
-      const int ra = hd->x, R = hd->z / 64;
-      T* dst = S + hd->w;
-      for (int e = lane; e < R * 64; e += 32) {
-        const int cc = e / R, rl = e % R;
-        dst[e] = cc < tb ? F[(int64_t)(ra + rl) * L + r0 + cc] : T(0.f);
+      // column-major: (ra + rl, cc) at cc * R + rl = U[ra + rl][r0 + cc], in groups of 64 rows
+      const int ra = hd.x, R = hd.z / 64;
+      for (int g = 0; g < R; g += 64) {
+        const int gr = min(64, R - g);
+        __syncthreads();
+        for (int e = tid; e < 64 * 64; e += 256) {
+          const int rl = e >> 6, cc = e & 63;
+          if (rl < gr) tile[rl * 65 + cc] = cc < tb ? F[(int64_t)(ra + g + rl) * L + r0 + cc] : T(0.f);
+        }
+        __syncthreads();
+        for (int e = tid; e < 64 * gr; e += 256) {
+          const int cc = e / gr, rl = e % gr;
+          dst[(int64_t)cc * R + g + rl] = tile[rl * 65 + cc];
+        }
       }
     } else {
       constexpr int W = V16<T>::W;
-      T* dst = S + hd->w;
-      for (int rr = 0; rr < tb; ++rr) {
+      const int warp = tid >> 5, lane = tid & 31;
+      for (int rr = warp; rr < tb; rr += 8) {
         const int c0 = kind == LD ? 0 : tri_lo<W>(rr), c1 = kind == LD ? tri_up<W>(rr) : tri_up<W>(tb);
         T* row = dst + (kind == LD ? ld_off<W>(rr) : ud_off<W>(rr, tb)) - c0;
-        for (int c = c0 + lane; c < c1; c += 32) {
+        for (int cc = c0 + lane; cc < c1; cc += 32) {
           T v = T(0.f);
           if (kind == LD) {
-            if (c < rr) v = F[(int64_t)(r0 + rr) * L + r0 + c];                // inv(L_bb), strictly lower
+            if (cc < rr) v = F[(int64_t)(r0 + rr) * L + r0 + cc];               // inv(L_bb), strictly lower
           } else {
-            if (c >= rr && c < tb) v = F[(int64_t)(r0 + rr) * L + r0 + c];     // inv(U_bb), upper
+            if (cc >= rr && cc < tb) v = F[(int64_t)(r0 + rr) * L + r0 + cc];   // inv(U_bb), upper
           }
-          row[c] = v;
+          row[cc] = v;
         }
       }
     }
@@ -622,9 +640,8 @@ void stream_prepare(a2ls_handle* h, const T* fac) {
   A2LS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   A2LS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   A2LS_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-  const int wpb = 8;
-  const int blocks = std::max(1, std::min(sms * 16, (S.nchunks + wpb - 1) / wpb));
-  k_pack_stream<T><<<blocks, 32 * wpb, 0, st>>>(S.nchunks, N, S.d_choff, S.d_meta, S.d_soff, h->d_ni,
+  const int blocks = std::max(1, std::min(sms * 16, S.nchunks));
+  k_pack_stream<T><<<blocks, 256, 0, st>>>(S.nchunks, N, S.d_choff, S.d_meta, S.d_soff, h->d_ni,
                                                 h->d_fld, h->d_ffoff, fac, static_cast<T*>(S.d_stream));
   A2LS_LAUNCH();
   S.xcap = (int)round_up(h->max_n, TB);
