@@ -1017,88 +1017,103 @@ __global__ void k_final_z(const int* ni, const int* off, const int64_t* xoff, in
 // space it builds is the block Krylov space of V_m Q that an explicit restart from V_m Q builds, with
 // one application of T fewer per cycle.  No invariance of span Q is assumed (a complex pair cut at the
 // block edge keeps its real part only).
-// One CTA per subdomain, FP64.  Writes U ((m+b) x 2b, stride EIG_MAXP) into Uout and H[0:m+b, 0:m]
-// (zero but for [G; R2] in the first block column).
+// One CTA per subdomain, in the arithmetic R of the Rayleigh-Ritz step (FP64, or double-float in the
+// mixed form, where it runs on the FP32 pipe instead of GB300's slow FP64 units).  Writes U ((m+b) x 2b,
+// stride EIG_MAXP) into Uout and H[0:m+b, 0:m] (zero but for [G; R2] in the first block column).
 constexpr int TR_THREADS = 128;  // >= m + b (at most EIG_MAXP)
 
-__device__ double tr_cta_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+__device__ __forceinline__ double tr_sqrt(double v) { return sqrt(v); }
+__device__ __forceinline__ dfloat tr_sqrt(dfloat v) { return se_sqrt(v); }
+
+template <class R>
+__device__ R tr_cta_sum(R v, R* red) {
+  for (int o = 16; o > 0; o >>= 1) v += warp_xor<R>(v, o);
   __syncthreads();  // red may still be read by the previous call
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  double s = 0.0;
+  R s = R(0.0);
   for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
   return s;
 }
 
 // Column c of U (mb rows, stride ld) orthogonalised against columns 0..c-1 by classical Gram-Schmidt:
 // at least two passes, more (up to four) while a pass removes more than half of the norm.  The
-// coefficients are added to coef[0..c-1] (if given).  *n0: the norm before; returns the norm after
-// (the column is not normalised), negative when the fourth pass still cancelled (numerically
-// dependent).  Whole CTA; mb <= blockDim.x.
-__device__ double tr_orth_column(double* U, int ld, int mb, int c, double* coef, double* dots, double* red,
-                                 double* n0) {
+// coefficients are added to coef[0..c-1] (if given).  *n0: the norm before; *ok: false when the fourth
+// pass still cancelled (numerically dependent); returns the norm after (the column is not
+// normalised).  Whole CTA; mb <= blockDim.x.
+template <class R>
+__device__ R tr_orth_column(R* U, int ld, int mb, int c, R* coef, R* dots, R* red, double* n0, bool* ok) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  double x = tid < mb ? U[tid * ld + c] : 0.0;
-  double nrm = sqrt(tr_cta_sum(x * x, red));
-  *n0 = nrm;
+  R x = tid < mb ? U[tid * ld + c] : R(0.0);
+  R sq = R(0.0);
+  mac(sq, x, x);
+  R nrm = tr_sqrt(finish(tr_cta_sum(finish(sq), red)));
+  *n0 = (double)nrm;
+  *ok = true;
   if (c == 0) return nrm;
   for (int pass = 0; pass < 4; ++pass) {
     for (int k = wid; k < c; k += nw) {
-      double d = 0.0;
-      for (int a = lane; a < mb; a += 32) d += U[a * ld + k] * U[a * ld + c];
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      R d = R(0.0);
+      for (int a = lane; a < mb; a += 32) mac(d, U[a * ld + k], U[a * ld + c]);
+      d = finish(d);
+      for (int o = 16; o > 0; o >>= 1) d += warp_xor<R>(d, o);
       if (lane == 0) dots[k] = d;
     }
     __syncthreads();
     if (tid < mb) {
-      double v = U[tid * ld + c];
-      for (int k = 0; k < c; ++k) v -= dots[k] * U[tid * ld + k];
+      R v = U[tid * ld + c];
+      for (int k = 0; k < c; ++k) mac(v, -dots[k], U[tid * ld + k]);
+      v = finish(v);
       U[tid * ld + c] = v;
       x = v;
     }
     if (coef && tid < c) coef[tid] += dots[tid];
-    const double nn = sqrt(tr_cta_sum(x * x, red));
-    const bool again = pass == 0 || nn < 0.5 * nrm;
+    sq = R(0.0);
+    mac(sq, x, x);
+    const R nn = tr_sqrt(finish(tr_cta_sum(finish(sq), red)));
+    const bool again = pass == 0 || (double)nn < 0.5 * (double)nrm;
     nrm = nn;
     if (!again) return nrm;
   }
-  return -nrm;
+  *ok = false;
+  return nrm;
 }
 
+template <class R>
 __global__ void __launch_bounds__(TR_THREADS) k_thick_restart(const int* active, int m, int b, const double* Y,
                                                            double* H, double* Uout, int* st) {
   extern __shared__ double sm[];
   const int i = blockIdx.x;
   if (active && !active[i]) return;
   const int tid = threadIdx.x, mb = m + b, ld = 2 * b;
-  double* U = sm;              // mb x 2b
-  double* Gs = U + mb * ld;    // b x b
-  double* R2 = Gs + b * b;     // b x b
-  double* coef = R2 + b * b;   // 2b
-  double* dots = coef + ld;    // 2b
-  __shared__ double red[TR_THREADS / 32];
+  R* U = reinterpret_cast<R*>(sm);  // mb x 2b
+  R* Gs = U + mb * ld;              // b x b
+  R* R2 = Gs + b * b;               // b x b
+  R* coef = R2 + b * b;             // 2b
+  R* dots = coef + ld;              // 2b
+  __shared__ R red[TR_THREADS / 32];
   const double* Yi = Y + (int64_t)i * EIG_MAXP * EIG_MAXP;
   double* Hi = H + (int64_t)i * EIG_MAXP * EIG_MAXP;
   double* Ui = Uout + (int64_t)i * EIG_MAXP * EIG_MAXP;
   for (int e = tid; e < mb * b; e += blockDim.x) {
     const int a = e / b, c = e % b;
-    U[a * ld + c] = a < m ? Yi[a * EIG_MAXP + c] : 0.0;
+    U[a * ld + c] = a < m ? R(Yi[a * EIG_MAXP + c]) : R(0.0);
   }
-  for (int e = tid; e < 2 * b * b; e += blockDim.x) Gs[e] = 0.0;  // Gs and R2
+  for (int e = tid; e < 2 * b * b; e += blockDim.x) Gs[e] = R(0.0);  // Gs and R2
   __syncthreads();
   // Q: a column (numerically) dependent on the ones before it is replaced by the first unit vector
   // e_r (r < m) that is not
   int cand = 0;
   for (int c = 0; c < b; ++c) {
     double n0 = 0.0;
-    double nrm = tr_orth_column(U, ld, mb, c, nullptr, dots, red, &n0);
-    while (!(nrm > 1e-12 * n0) && cand < m) {
-      if (tid < mb) U[tid * ld + c] = (tid == cand) ? 1.0 : 0.0;
+    bool ok = true;
+    R nrm = tr_orth_column(U, ld, mb, c, (R*)nullptr, dots, red, &n0, &ok);
+    while (!(ok && (double)nrm > 1e-12 * n0) && cand < m) {
+      if (tid < mb) U[tid * ld + c] = R((tid == cand) ? 1.0 : 0.0);
       ++cand;
-      nrm = tr_orth_column(U, ld, mb, c, nullptr, dots, red, &n0);
+      nrm = tr_orth_column(U, ld, mb, c, (R*)nullptr, dots, red, &n0, &ok);
     }
-    if (!(nrm > 0.0)) {
+    if (!((double)nrm > 0.0)) {
       if (tid == 0) raise_status(st, A2LS_ERR_EIGEN, i, 5);
       return;  // uniform: every thread holds the same norm
     }
@@ -1109,9 +1124,9 @@ __global__ void __launch_bounds__(TR_THREADS) k_thick_restart(const int* active,
   for (int e = tid; e < mb * b; e += blockDim.x) {
     const int a = e / b, c = e % b;
     const double* Ha = Hi + a * EIG_MAXP;
-    double sum = 0.0;
-    for (int k = 0; k < m; ++k) sum += Ha[k] * U[k * ld + c];
-    U[a * ld + b + c] = sum;
+    R sum = R(0.0);
+    for (int k = 0; k < m; ++k) mac(sum, R(Ha[k]), U[k * ld + c]);
+    U[a * ld + b + c] = finish(sum);
   }
   __syncthreads();
   // G and R2 by Gram-Schmidt of Hb Q against [Q; 0] and the second block's earlier columns.  Any
@@ -1124,22 +1139,23 @@ __global__ void __launch_bounds__(TR_THREADS) k_thick_restart(const int* active,
   int cand2 = 0;
   for (int c = 0; c < b; ++c) {
     __syncthreads();  // coef of the previous column read
-    if (tid < ld) coef[tid] = 0.0;
+    if (tid < ld) coef[tid] = R(0.0);
     __syncthreads();
     double n0 = 0.0;
-    double nrm = tr_orth_column(U, ld, mb, b + c, coef, dots, red, &n0);
+    bool ok = true;
+    R nrm = tr_orth_column(U, ld, mb, b + c, coef, dots, red, &n0, &ok);
     if (tid < b) Gs[tid * b + c] = coef[tid];
     if (tid < c) R2[tid * b + c] = coef[b + tid];
-    if (nrm > 0.0) {
+    if (ok && (double)nrm > 0.0) {
       if (tid == 0) R2[c * b + c] = nrm;
     } else {
-      while (!(nrm > 1e-12 * n0) && cand2 < mb) {
+      while (!(ok && (double)nrm > 1e-12 * n0) && cand2 < mb) {
         const int r = cand2 < b ? m + cand2 : cand2 - b;
-        if (tid < mb) U[tid * ld + b + c] = (tid == r) ? 1.0 : 0.0;
+        if (tid < mb) U[tid * ld + b + c] = R((tid == r) ? 1.0 : 0.0);
         ++cand2;
-        nrm = tr_orth_column(U, ld, mb, b + c, nullptr, dots, red, &n0);
+        nrm = tr_orth_column(U, ld, mb, b + c, (R*)nullptr, dots, red, &n0, &ok);
       }
-      if (!(nrm > 0.0)) {
+      if (!((double)nrm > 0.0)) {
         if (tid == 0) raise_status(st, A2LS_ERR_EIGEN, i, 5);
         return;
       }
@@ -1147,11 +1163,11 @@ __global__ void __launch_bounds__(TR_THREADS) k_thick_restart(const int* active,
     if (tid < mb) U[tid * ld + b + c] /= nrm;
   }
   __syncthreads();
-  for (int e = tid; e < mb * ld; e += blockDim.x) Ui[(e / ld) * EIG_MAXP + e % ld] = U[e];
+  for (int e = tid; e < mb * ld; e += blockDim.x) Ui[(e / ld) * EIG_MAXP + e % ld] = (double)U[e];
   for (int e = tid; e < mb * m; e += blockDim.x) {
     const int a = e / m, c = e % m;
     double v = 0.0;
-    if (c < b) v = a < b ? Gs[a * b + c] : (a < 2 * b ? R2[(a - b) * b + c] : 0.0);
+    if (c < b) v = a < b ? (double)Gs[a * b + c] : (a < 2 * b ? (double)R2[(a - b) * b + c] : 0.0);
     Hi[a * EIG_MAXP + c] = v;
   }
 }
@@ -1340,7 +1356,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   // thick restart (needs a block step after the kept block: s >= 2)
   const bool thick = h->opt.eig_thick_restart != 0 && s >= 2;
   const size_t tr_smem = sizeof(double) * ((size_t)(s + 1) * b * 2 * b + 2 * (size_t)b * b + 4 * (size_t)b);
-  A2LS_CUDA(cudaFuncSetAttribute(k_thick_restart, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tr_smem));
+  A2LS_CUDA(cudaFuncSetAttribute(k_thick_restart<RT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tr_smem));
   int* d_illcond = dalloc<int>(h, N);  // per cycle: a block step needed the shifted factorisation
   int* d_thick = dalloc<int>(h, N);    // per cycle: the next restart may be thick
   A2LS_CUDA(cudaMemsetAsync(d_illcond, 0, sizeof(int) * N, st));
@@ -1618,7 +1634,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
       if (nthk) {
         // V[:, 0:2b] = V[:, 0:(s+1)b] U in place, H's first block column [G; R2]
         A2LS_CUDA(cudaMemcpyAsync(G.d_thk, G.thk.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
-        k_thick_restart<<<N, TR_THREADS, tr_smem, st>>>(G.d_thk, s * b, b, Y, H, Rscr, h->d_status);
+        k_thick_restart<RT><<<N, TR_THREADS, tr_smem, st>>>(G.d_thk, s * b, b, Y, H, Rscr, h->d_status);
         A2LS_LAUNCH();
         k_vy<TV, TV><<<N, EIG_THREADS, vy_smem, st>>>(h->d_ni, d_vo, P, d_mb, d_b2, G.d_thk, V, Rscr, V);
         A2LS_LAUNCH();
