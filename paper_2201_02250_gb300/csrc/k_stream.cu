@@ -20,15 +20,15 @@
 // Chunks hold at most 32 KB: 128 (FP32) or 256 (BF16) columns of an L panel, 28 groups of 16 bytes of
 // rows of a U panel (a column stride of 64 bytes modulo 128 keeps the reads conflict-free), or one
 // diagonal triangle (its row offsets are prefix sums of the rounded row lengths).
-
+//
 // Kernel.  One or two CTAs per SM, persistent over a work queue of the subdomains (largest first).
 // One producer warp streams the chunks through a ring of shared-memory stages with bulk asynchronous
 // copies (cp.async.bulk, completion counted in bytes on an mbarrier per stage); each stage also
-// receives the chunk's header, so that the consumers read no global
-// memory but the right-hand side and their outputs.  The consumer warps run the solves from shared memory:
-// the panel products, the 64 x 64 triangle products of the diagonal blocks and the right-looking
-// updates, with the gathered right-hand side and the solution held in shared memory.  The producer
-// runs ahead across block and subdomain boundaries, so the loads never wait for the solve chain.
+// receives the chunk's header, so that the consumers read no global memory but the right-hand side
+// and their outputs.  The consumer warps run the solves from shared memory: the panel products, the
+// 64 x 64 triangle products of the diagonal blocks and the right-looking updates, with the gathered
+// right-hand side and the solution held in shared memory.  The producer runs ahead across block and
+// subdomain boundaries, so the loads never wait for the solve chain.
 // Every wait is bounded; a wait that gives up records A2LS_ERR_TIMEOUT and the CTA leaves after its
 // copies in flight have landed.
 #include "a2ls_internal.cuh"
@@ -71,44 +71,6 @@ template <class T> struct V16;                   // elements per 16 bytes
 template <> struct V16<float> { static constexpr int W = 4; };
 template <> struct V16<__nv_bfloat16> { static constexpr int W = 8; };
 
-__device__ __forceinline__ float to_f(float v) { return v; }
-__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-// sum over the 16 bytes at d (shared memory) times x[0 .. W)
-__device__ __forceinline__ float dot16(const float* d, const float* x) {
-  const float4 a = *reinterpret_cast<const float4*>(d);
-  const float4 b = *reinterpret_cast<const float4*>(x);
-  return (a.x * b.x + a.y * b.y) + (a.z * b.z + a.w * b.w);  // two independent chains
-}
-__device__ __forceinline__ float dot16(const __nv_bfloat16* d, const float* x) {
-  const uint4 a = *reinterpret_cast<const uint4*>(d);
-  const float4 b0 = *reinterpret_cast<const float4*>(x);
-  const float4 b1 = *reinterpret_cast<const float4*>(x + 4);
-  // a 32-bit word holds two bfloat16 values, the lower-indexed one in the low half
-  const float s0 = __uint_as_float(a.x << 16) * b0.x + __uint_as_float(a.x & 0xffff0000u) * b0.y;
-  const float s1 = __uint_as_float(a.y << 16) * b0.z + __uint_as_float(a.y & 0xffff0000u) * b0.w;
-  const float s2 = __uint_as_float(a.z << 16) * b1.x + __uint_as_float(a.z & 0xffff0000u) * b1.y;
-  const float s3 = __uint_as_float(a.w << 16) * b1.z + __uint_as_float(a.w & 0xffff0000u) * b1.w;
-  return (s0 + s1) + (s2 + s3);
-}
-// acc[0 .. W) += d[0 .. W) * s
-__device__ __forceinline__ void axpy16(float (&acc)[4], const float* d, float s) {
-  const float4 a = *reinterpret_cast<const float4*>(d);
-  acc[0] += a.x * s;
-  acc[1] += a.y * s;
-  acc[2] += a.z * s;
-  acc[3] += a.w * s;
-}
-__device__ __forceinline__ void axpy16(float (&acc)[8], const __nv_bfloat16* d, float s) {
-  const uint4 a = *reinterpret_cast<const uint4*>(d);
-  const uint32_t w[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    acc[2 * k] += __uint_as_float(w[k] << 16) * s;
-    acc[2 * k + 1] += __uint_as_float(w[k] & 0xffff0000u) * s;
-  }
-}
-
 // the W values of the 16 bytes at d (shared memory)
 __device__ __forceinline__ void unpack16(const float* d, float (&v)[4]) {
   const float4 a = *reinterpret_cast<const float4*>(d);
@@ -125,12 +87,6 @@ __device__ __forceinline__ void unpack16(const __nv_bfloat16* d, float (&v)[8]) 
     v[2 * k] = __uint_as_float(w[k] << 16);
     v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
   }
-}
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -162,13 +118,6 @@ __device__ __forceinline__ int consumer_sync_or(int v) {
       : "memory");
   return r;
 }
-
-}  // namespace lss
-}  // namespace a2ls
-
-
-namespace a2ls {
-namespace lss {
 
 // meta: per chunk a header int4 {first column (LP) or row (UP) of the panel, kind | block << 2,
 // elements, element offset of its data in the subdomain's stream}.
@@ -483,12 +432,6 @@ __global__ void __launch_bounds__(32 * CW + 32, CTAS_PER_SM) k_local_solve_strea
     if (tid == 0) raise_status(st, A2LS_ERR_TIMEOUT, blockIdx.x, 11);
   }
 }
-
-}  // namespace lss
-}  // namespace a2ls
-
-namespace a2ls {
-namespace lss {
 
 // Pack one chunk per CTA (256 threads) from the dense block-inverted factors F (row-major, leading
 // dimension ld) into the stream.  The panels are transposes of F's layout: they pass through a shared
