@@ -145,6 +145,9 @@ typedef struct {
                                (pipelined kernel), 3000 / 3004 / 3008 (streaming kernel on the
                                repacked factors: one CTA of 8 consumer warps, two of 4, two of 8 per
                                SM; FP32 and BF16 factors only) */
+  int32_t eig_block_size;   /* columns of the local eigensolves' blocks: 0 (default) = the larger of
+                               nev + max(4, nev / 2) and min(2 nev, 24), at most 32; otherwise that many
+                               (at least nev + 1, at most 32) */
 } a2ls_options;
 
 /* Fills *opt with the defaults listed above.  Never fails. */

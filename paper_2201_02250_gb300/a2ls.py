@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("eig_precision", ctypes.c_int32), ("graphs", ctypes.c_int32), ("warm_start", ctypes.c_void_p),
                 ("eig_strict", ctypes.c_int32), ("eig_stall_cycles", ctypes.c_int32),
                 ("tensor_cores", ctypes.c_int32), ("eig_thick_restart", ctypes.c_int32),
-                ("local_solve_kernel", ctypes.c_int32)]
+                ("local_solve_kernel", ctypes.c_int32), ("eig_block_size", ctypes.c_int32)]
 
 
 _LIB = None

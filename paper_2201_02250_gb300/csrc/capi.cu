@@ -397,6 +397,7 @@ void a2ls_default_options(a2ls_options* o) {
   o->tensor_cores = 1;
   o->eig_thick_restart = 1;
   o->local_solve_kernel = 0;
+  o->eig_block_size = 0;
 }
 
 const char* a2ls_last_error(void) { return g_last_error.c_str(); }

@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
                                                         const int* pvec, const int* active, int jb_blocks,
                                                         int bcols, T* V, TW* W, double* H, int hr, int hc,
                                                         int vout, const int* fullv, int* rank_flag, int gcap,
-                                                        int orc, int* illcond) {
+                                                        int orc, int* illcond, int* status) {
   using Acc = typename EAcc<T>::type;
   extern __shared__ __align__(16) double sm[];
   const int i = blockIdx.x;
@@ -582,6 +582,10 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
   if (full && jb_blocks != 1) return;
   const int n = ni[i], p = pvec[i];
   const int jb = full ? p : jb_blocks * bcols;  // basis columns to orthogonalise against
+  if (p * p > gcap || jb * p > gcap) {          // the Gram matrices would not fit the launch's space
+    if (threadIdx.x == 0) raise_status(status, A2LS_ERR_EIGEN, i, 3);
+    return;
+  }
   T* Vi = V + xoff[i];
   TW* Wi = W + xoff[i];
   double* Hi = H + (int64_t)i * EIG_MAXP * EIG_MAXP;
@@ -669,7 +673,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
         const int a = e / p, c = e % p;
         Hi[(hr + a) * EIG_MAXP + hc + c] = (c >= a) ? G[a * p + c] : 0.0;
       }
-    } else {
+    } else if ((size_t)p * p * sizeof(double) <= (size_t)orc * SROW * sizeof(Acc)) {
       // H_blk <- R H_blk (R upper triangular), through a temporary in the staging space
       double* tmp = reinterpret_cast<double*>(sw);
       for (int e = tid; e < p * p; e += ORTH_THREADS) {
@@ -680,6 +684,17 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_orth(const int* ni, const int6
       }
       __syncthreads();
       for (int e = tid; e < p * p; e += ORTH_THREADS) Hi[(hr + e / p) * EIG_MAXP + hc + e % p] = tmp[e];
+    } else {
+      // a block too wide for the staging space (a full-space subdomain): in place, row by row from
+      // the top (row a of the product reads rows a .. p - 1, not yet overwritten)
+      for (int a = 0; a < p; ++a) {
+        double s = 0.0;
+        if (tid < p)
+          for (int q = a; q < p; ++q) s += G[a * p + q] * Hi[(hr + q) * EIG_MAXP + hc + tid];
+        __syncthreads();
+        if (tid < p) Hi[(hr + a) * EIG_MAXP + hc + tid] = s;
+        __syncthreads();
+      }
     }
     __syncthreads();
     // W <- W inv(R); inv(R) converted once to the working arithmetic (in G's space, padded to pp columns)
@@ -1271,7 +1286,13 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
   }
   if (nfmax + 4 > 32)
     fail(A2LS_ERR_ARG, "nev = %d is too large for the local eigensolver (at most 28 eigenpairs per subdomain)", nev);
-  const int b = std::min(32, nfmax + std::max(4, (nfmax + 1) / 2));
+  // block size: by default nev + max(4, nev / 2), raised towards 2 nev while 3 block steps still fit
+  // the Krylov capacity ((s + 1) b <= EIG_MAXP): a wider block converges in fewer cycles (96^3 case,
+  // nev 12: 5-9 cycles with 18 columns, 4-7 with 24, eigen phase -6 % in double-float and -5 % in
+  // FP64); or the option (at least nev + 1, at most 32)
+  const int b = h->opt.eig_block_size > 0
+                    ? std::min(32, std::max(nfmax + 1, (int)h->opt.eig_block_size))
+                    : std::min(32, std::max(nfmax + std::max(4, (nfmax + 1) / 2), std::min(2 * nfmax, EIG_MAXP / 4)));
   int s = h->opt.eig_block_steps > 0 ? h->opt.eig_block_steps : 3;
   if ((s + 1) * b > EIG_MAXP) s = EIG_MAXP / b - 1;
   if (s < 1) fail(A2LS_ERR_ARG, "nev = %d is too large for the local eigensolver (at most %d)", nev, EIG_MAXP / 2 - 8);
@@ -1427,13 +1448,16 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, actv, d_kd, kvB, W);
     A2LS_LAUNCH();
   };
-  auto orthonormalize_W_into_V0 = [&](const int* actv) {
+  // full = the subdomains in the launch may include full-space ones, whose block has up to EIG_MAXP
+  // columns (their Gram matrices need gcap_f)
+  auto orthonormalize_W_into_V0 = [&](const int* actv, bool with_full) {
     k_project_k<T><<<N, EIG_THREADS, 0, st>>>(h->d_ni, h->d_off, d_vo, P, 0, d_pv, actv, d_kd, kvB, W);
     A2LS_LAUNCH();
     // no previous basis: jb = 0; R written into H's last rows (discarded)
-    k_orth<TV, T><<<N, ORTH_THREADS, orth_smem_for(gcap_k), st>>>(h->d_ni, d_vo, P, d_pv, actv, 0, b, V, W,
-                                                                  Rscr, 0, 0, 0, nullptr, d_rank, gcap_k,
-                                                                  orc_for(gcap_k), nullptr);
+    const int gcap = with_full ? gcap_f : gcap_k;
+    k_orth<TV, T><<<N, ORTH_THREADS, orth_smem_for(gcap), st>>>(h->d_ni, d_vo, P, d_pv, actv, 0, b, V, W, Rscr, 0,
+                                                                0, 0, nullptr, d_rank, gcap, orc_for(gcap), nullptr,
+                                                                h->d_status);
     A2LS_LAUNCH();
   };
 
@@ -1448,7 +1472,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
     k_random_block<T><<<N, 256, 0, st>>>(h->d_ni, d_vo, P, 0, d_pv, d_active, h->opt.seed, 0, W);
     A2LS_LAUNCH();
   }
-  orthonormalize_W_into_V0(d_active);
+  orthonormalize_W_into_V0(d_active, any_full);
   A2LS_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * N * P * P, st));
 
   // --- restarted block Krylov cycles, in two interleaved groups of subdomains --------------------
@@ -1549,7 +1573,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
         const int gcap = (j == 0) ? gcap_f : gcap_k;
         k_orth<TV, T><<<N, ORTH_THREADS, orth_smem_for(gcap), st>>>(h->d_ni, d_vo, P, d_pv, actv, j + 1, b, V, W, H,
                                                       (j + 1) * b, j * b, (j + 1) * b, d_full, d_rank, gcap,
-                                                      orc_for(gcap), d_illcond);
+                                                      orc_for(gcap), d_illcond, h->d_status);
         A2LS_LAUNCH();
       }
   };
@@ -1645,7 +1669,7 @@ static void eigensolve_t(a2ls_handle* h, T* fac, const double* last_pivot, const
         A2LS_CUDA(cudaMemcpyAsync(G.d_exl, G.exl.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st));
         k_vy<TV, T><<<N, EIG_THREADS, vy_smem, st>>>(h->d_ni, d_vo, P, d_msb, d_pv, G.d_exl, V, Y, W);
         A2LS_LAUNCH();
-        orthonormalize_W_into_V0(G.d_exl);
+        orthonormalize_W_into_V0(G.d_exl, false);  // restarted subdomains are Krylov ones
         if (thick) block_step(0, G.d_exl, G.exl);
       }
       queue_cycle(g, thick ? 1 : 0);
