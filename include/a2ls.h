@@ -206,6 +206,33 @@ const char* a2ls_last_error(void);
  */
 int a2ls_trim_memory(void);
 
+/*
+ * a2ls_partition -- the non-overlapping partition Omega_Ii that a2ls_setup takes (Section 2).  The
+ * paper partitions the graph of A^T + A with ParMETIS (Section 4); this is the library's own
+ * partitioner of the same graph: multilevel recursive bisection (heavy-edge matching, growing from
+ * several starts on the coarsest graph, Fiduccia-Mattheyses refinement on every level).  It runs on
+ * the host and needs no GPU.
+ *   n, rowptr, colind : HOST CSR pattern of A (n + 1 and rowptr[n] int32 entries; the values are not
+ *                       needed).  The graph is the off-diagonal pattern of A + A^T, unit weights.
+ *   nparts            : number of parts N, 1 <= N <= n.
+ *   seed              : seeds the coarsening's visiting order (the result is a pure function of the
+ *                       pattern, nparts and seed).
+ *   part              : HOST, n int32 values written in [0, N); every part is non-empty.  Each
+ *                       bisection keeps its sides within 2 % of an average final part of their target
+ *                       weights, so parts hold n / N vertices to within a few per cent.  Parts of a
+ *                       connected graph are connected: a part left in several pieces keeps the
+ *                       largest, the others join the neighbouring part they share most edges with
+ *                       (connectivity before balance; a subdomain in several floating pieces would
+ *                       give its splitting a kernel of dimension above one).  The halves of the top
+ *                       recursion levels run on up to 16 host threads; the result does not depend on
+ *                       their scheduling.
+ * Copy part to the device for a2ls_setup.  Errors: ARG (n < 1, nparts outside [1, n], NULL pointers,
+ * rowptr not starting at 0 or decreasing, column index outside [0, n)); the caller's buffers are
+ * only read, except part.
+ */
+int a2ls_partition(int32_t n, const int32_t* rowptr, const int32_t* colind, int32_t nparts, uint64_t seed,
+                   int32_t* part);
+
 /* Items for a2ls_query.  All results are copied to host memory. */
 enum {
   A2LS_Q_SIZES = 0,      /* int64[8]: n, N, n0, sum n_i, max n_i, sum m_i rows stored, precision, variant */

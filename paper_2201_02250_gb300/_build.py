@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libA2LS.so")
 SOURCES = ["capi.cu", "k_graph.cu", "k_dense.cu", "k_eig.cu", "k_coarse.cu", "k_krylov.cu", "k_static.cu", "k_gnn.cu",
-           "k_tcsolve.cu", "k_stream.cu"]
+           "k_tcsolve.cu", "k_stream.cu", "partition.cu"]
 HEADERS = [os.path.join(CSRC, "a2ls_internal.cuh"), os.path.join(CSRC, "small_eig.cuh"),
            os.path.join(CSRC, "tc_sm100.cuh"), os.path.join(CSRC, "tc_dfloat.cuh"), os.path.join(CSRC, "dfloat.cuh"),
            os.path.join(ROOT, "include", "a2ls.h")]

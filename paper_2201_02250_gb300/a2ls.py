@@ -88,8 +88,9 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     L.a2ls_solve_multi.argtypes = [vp, i32, vp, vp, f64, vp, vp]
     L.a2ls_setup_batch.argtypes = [i32, vp, vp, vp, vp, ctypes.POINTER(Options), vp]
     L.a2ls_trim_memory.argtypes = []
+    L.a2ls_partition.argtypes = [i32, vp, vp, i32, ctypes.c_uint64, vp]
     for f in ("a2ls_setup", "a2ls_apply", "a2ls_solve", "a2ls_query", "a2ls_set_coarse_basis", "a2ls_spmv",
-              "a2ls_apply_static", "a2ls_solve_multi", "a2ls_setup_batch", "a2ls_trim_memory"):
+              "a2ls_apply_static", "a2ls_solve_multi", "a2ls_setup_batch", "a2ls_trim_memory", "a2ls_partition"):
         getattr(L, f).restype = ctypes.c_int
     # learned warm start
     i64 = ctypes.c_int64
@@ -331,6 +332,20 @@ class Preconditioner:
 def trim_memory() -> None:
     """Return the unused blocks of the library's device memory pools to the system (a2ls_trim_memory)."""
     _check(lib().a2ls_trim_memory())
+
+
+def partition(rowptr, colind, nparts: int, seed: int = 0) -> np.ndarray:
+    """k-way partition of the graph of A + A^T (a2ls_partition, host side, no GPU needed).
+
+    rowptr, colind: the CSR pattern of A as host arrays; returns part (int32, n values in [0, nparts)).
+    """
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    n = int(rp.size - 1)
+    part = np.empty(max(n, 0), dtype=np.int32)
+    _check(lib().a2ls_partition(n, ctypes.c_void_p(rp.ctypes.data), ctypes.c_void_p(ci.ctypes.data if ci.size else 0),
+                                int(nparts), ctypes.c_uint64(seed), ctypes.c_void_p(part.ctypes.data)))
+    return part
 
 
 def from_scipy(A, part, overlap: int, nev: int, device: str = "cuda", **opts):

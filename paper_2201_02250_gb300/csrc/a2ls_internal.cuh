@@ -24,6 +24,9 @@ struct Error : std::runtime_error {
 };
 
 [[noreturn]] void fail(int code, const char* fmt, ...);
+// host-side k-way partition of the graph of A + A^T (partition.cu); errors through fail()
+void partition_graph(int32_t n, const int32_t* rowptr, const int32_t* colind, int32_t nparts, uint64_t seed,
+                     int32_t* part);
 void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 #define A2LS_CUDA(x) ::a2ls::check_cuda((x), #x, __FILE__, __LINE__)
 // every kernel launch of the library goes through this macro: error check and per-handle count

@@ -402,6 +402,15 @@ void a2ls_default_options(a2ls_options* o) {
 
 const char* a2ls_last_error(void) { return g_last_error.c_str(); }
 
+int a2ls_partition(int32_t n, const int32_t* rowptr, const int32_t* colind, int32_t nparts, uint64_t seed,
+                   int32_t* part) {
+  set_error("");
+  return guarded([&] {
+    partition_graph(n, rowptr, colind, nparts, seed, part);
+    return (int)A2LS_OK;
+  });
+}
+
 int a2ls_trim_memory(void) {
   set_error("");
   std::lock_guard<std::mutex> lk(g_pool_mutex);

@@ -1,0 +1,248 @@
+"""a2ls_partition: the library's partitioner of the graph of A + A^T (the paper partitions A^T + A
+with ParMETIS, Section 4; the method itself takes the non-overlapping partition of Section 2 as
+given).  Host code: every test runs on the CPU through the C ABI.
+
+A partitioner is a heuristic, so it is pinned by what the mathematics fixes: graphs whose optimal
+cut is known (paths, two cliques joined by one edge, equal components, straight cuts of grids),
+brute force over every balanced bisection of small random graphs, the symmetrisation A + A^T, and the
+invariants the method needs (every vertex in one part, every part non-empty, balanced sizes)."""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.sparse.csgraph import connected_components
+
+from paper_2201_02250_gb300 import a2ls, _build
+from oracle import a2ls_oracle as orc
+from workloads import pde
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    _build.build()
+    return a2ls.lib(build_if_missing=False)
+
+
+def _csr(M) -> sp.csr_matrix:
+    A = sp.csr_matrix(M, dtype=np.float64)
+    A.sort_indices()
+    return A
+
+
+def _cut(A, part) -> int:
+    """Edges of the graph of A + A^T whose ends lie in different parts."""
+    C = sp.triu(abs(A) + abs(A).T, 1).tocoo()
+    return int(np.count_nonzero(part[C.row] != part[C.col]))
+
+
+def _grid(dims) -> sp.csr_matrix:
+    """Pattern of the 5-point (2D) or 7-point (3D) stencil on a grid of the given dimensions."""
+    A = None
+    for k in range(len(dims)):
+        t = None
+        for j, d in enumerate(dims):
+            m = sp.diags([np.ones(d - 1), np.ones(d - 1)], [-1, 1]) if j == k else sp.identity(d)
+            t = m if t is None else sp.kron(t, m)
+        A = t if A is None else A + t
+    return _csr(A + sp.identity(A.shape[0]))
+
+
+def _check_valid(part, n, k):
+    assert part.shape == (n,) and part.dtype == np.int32
+    assert part.min() >= 0 and part.max() < k
+    assert np.all(np.bincount(part, minlength=k) > 0)
+
+
+@pytest.mark.parametrize("n,k", [(100, 2), (100, 3), (100, 5), (100, 8), (37, 7)])
+def test_path_graph_is_cut_k_minus_1_times(n, k):
+    # a path splits into k non-empty parts with no fewer than k - 1 cut edges, reached by contiguous runs
+    A = _csr(sp.diags([np.ones(n - 1), 2 * np.ones(n), np.ones(n - 1)], [-1, 0, 1]))
+    p = a2ls.partition(A.indptr, A.indices, k)
+    _check_valid(p, n, k)
+    assert _cut(A, p) == k - 1
+    assert np.all(np.abs(np.bincount(p) - n / k) <= 1.5)
+
+
+def test_two_cliques_joined_by_one_edge():
+    m = 20
+    M = np.zeros((2 * m, 2 * m))
+    M[:m, :m] = 1
+    M[m:, m:] = 1
+    M[m - 1, m] = M[m, m - 1] = 1
+    A = _csr(M)
+    p = a2ls.partition(A.indptr, A.indices, 2)
+    assert _cut(A, p) == 1
+    assert len(set(p[:m])) == 1 and len(set(p[m:])) == 1 and p[0] != p[-1]
+
+
+@pytest.mark.parametrize("ncomp", [4, 8])
+def test_equal_components_become_the_parts(ncomp):
+    A = _csr(sp.block_diag([_grid((10, 10))] * ncomp))
+    p = a2ls.partition(A.indptr, A.indices, ncomp)
+    assert _cut(A, p) == 0
+    for c in range(ncomp):
+        assert len(set(p[100 * c:100 * (c + 1)])) == 1
+
+
+def test_bisection_matches_brute_force_on_small_random_graphs():
+    # every bisection with side weights in the partitioner's window (n = 12: 6 +- 1) enumerated.  A
+    # balanced result has the optimal cut.  Where the refined bisection left a side in several pieces,
+    # the connectivity step moved the smaller pieces to the side they are joined to: the cut then
+    # drops below the balanced optimum and the sides leave the window (connected parts come first)
+    rng = np.random.default_rng(0)
+    n = 12
+    masks = np.arange(1 << n)
+    bits = (masks[:, None] >> np.arange(n)) & 1            # bits[m, v]: side of v in bisection m
+    balanced = np.isin(bits.sum(axis=1), (5, 6, 7))
+    repaired = 0
+    for t in range(40):
+        M = np.triu((rng.random((n, n)) < 0.3).astype(float), 1)
+        A = _csr(M + M.T + np.eye(n))
+        p = a2ls.partition(A.indptr, A.indices, 2, seed=t)
+        u, v = np.nonzero(np.triu(M + M.T, 1))
+        cuts = (bits[:, u] != bits[:, v]).sum(axis=1)
+        if 5 <= np.count_nonzero(p == 0) <= 7:
+            assert _cut(A, p) == cuts[balanced].min(), t
+        else:
+            repaired += 1
+            assert _cut(A, p) < cuts[balanced].min(), t
+    assert repaired <= 5
+
+
+@pytest.mark.parametrize("dims,k,optimum,slack", [
+    ((64, 64), 2, 64, 1.15),           # one straight cut
+    ((64, 64), 4, 128, 1.20),          # two straight cuts
+    ((16, 16, 16), 2, 256, 1.15),      # one plane
+    ((32, 32, 32), 8, 3 * 1024, 1.15), # three planes
+])
+def test_grid_cuts_close_to_the_straight_cuts(dims, k, optimum, slack):
+    A = _grid(dims)
+    p = a2ls.partition(A.indptr, A.indices, k, seed=1)
+    _check_valid(p, A.shape[0], k)
+    assert optimum <= _cut(A, p) <= slack * optimum
+
+
+@pytest.mark.parametrize("k", [2, 3, 7, 16, 64])
+def test_parts_are_balanced(k):
+    A = _grid((48, 48))
+    n = A.shape[0]
+    p = a2ls.partition(A.indptr, A.indices, k, seed=3)
+    _check_valid(p, n, k)
+    sizes = np.bincount(p, minlength=k)
+    assert sizes.max() <= 1.06 * n / k + 1 and sizes.min() >= 0.94 * n / k - 1
+
+
+def test_graph_is_that_of_a_plus_a_transpose():
+    # a pattern holding only the upper triangle gives the same graph as its symmetrisation
+    A = _grid((20, 20))
+    U = _csr(sp.triu(A))
+    p_u = a2ls.partition(U.indptr, U.indices, 6, seed=2)
+    p_s = a2ls.partition(A.indptr, A.indices, 6, seed=2)
+    np.testing.assert_array_equal(p_u, p_s)
+    # the diagonal is ignored
+    N = _csr(A - sp.diags(A.diagonal()))
+    N.eliminate_zeros()
+    np.testing.assert_array_equal(a2ls.partition(N.indptr, N.indices, 6, seed=2), p_s)
+
+
+def test_deterministic_for_a_seed_and_valid_for_others():
+    A = _grid((30, 30))
+    p1 = a2ls.partition(A.indptr, A.indices, 9, seed=7)
+    np.testing.assert_array_equal(p1, a2ls.partition(A.indptr, A.indices, 9, seed=7))
+    for seed in range(4):
+        _check_valid(a2ls.partition(A.indptr, A.indices, 9, seed=seed), A.shape[0], 9)
+
+
+@pytest.mark.parametrize("k", [1, 29, 30])
+def test_extreme_part_counts(k):
+    A = _grid((5, 6))
+    p = a2ls.partition(A.indptr, A.indices, k)
+    _check_valid(p, 30, k)
+    if k == 30:
+        assert sorted(p) == list(range(30))
+
+
+def test_graph_without_edges():
+    A = _csr(sp.identity(10))
+    p = a2ls.partition(A.indptr, A.indices, 4)
+    _check_valid(p, 10, 4)
+    assert np.bincount(p).max() <= 3
+
+
+def test_argument_errors():
+    A = _grid((4, 4))
+    rp, ci = A.indptr, A.indices
+    for k in (0, 17):
+        with pytest.raises(a2ls.A2lsError, match="nparts"):
+            a2ls.partition(rp, ci, k)
+    bad = ci.copy()
+    bad[3] = 16
+    with pytest.raises(a2ls.A2lsError, match="colind"):
+        a2ls.partition(rp, bad, 2)
+    dec = rp.copy()
+    dec[5] = dec[4] - 1
+    with pytest.raises(a2ls.A2lsError, match="decreases"):
+        a2ls.partition(dec, ci, 2)
+    with pytest.raises(a2ls.A2lsError, match="rowptr"):
+        a2ls.partition(rp + 1, ci, 2)
+    with pytest.raises(a2ls.A2lsError) as e:
+        a2ls.partition(np.zeros(1, np.int32), np.zeros(0, np.int32), 1)
+    assert e.value.code == a2ls.A2LS_ERR_ARG
+
+
+def _holey_grid(m, frac, seed):
+    """Largest connected piece of an m x m grid with a random fraction of its nodes removed."""
+    keep = np.random.default_rng(seed).random(m * m) > frac
+    G = _grid((m, m))[keep][:, keep]
+    _, lab = connected_components(G, directed=False)
+    big = lab == np.bincount(lab).argmax()
+    return _csr(G[big][:, big])
+
+
+@pytest.mark.parametrize("kind,seed,k", [("holes", s, k) for s in range(4) for k in (8, 32)] +
+                         [("random", s, k) for s in range(4) for k in (16, 50)])
+def test_parts_are_connected_where_the_graph_is(kind, seed, k):
+    # every part of a connected graph induces a connected subgraph (a part made of several pieces
+    # would give its subdomain several floating components, i.e. a larger kernel of the splitting)
+    A = _holey_grid(40, 0.15, seed) if kind == "holes" else _csr(pde.random_dd_matrix(2000, 0.002, seed))
+    ncomp, lab = connected_components(A, directed=False)
+    p = a2ls.partition(A.indptr, A.indices, k, seed=seed)
+    _check_valid(p, A.shape[0], k)
+    for c in range(k):
+        idx = np.nonzero(p == c)[0]
+        npieces, plab = connected_components(A[idx][:, idx], directed=False)
+        if ncomp == 1:
+            assert npieces == 1, c
+        else:  # pieces beyond the largest are whole components of the graph
+            sizes = np.bincount(plab)
+            for piece in np.nonzero(sizes < sizes.max())[0]:
+                members = idx[plab == piece]
+                assert np.count_nonzero(lab == lab[members[0]]) == members.size
+
+
+def test_star_graph_keeps_parts_connected_before_balanced():
+    # any balanced bisection of a star leaves the leaves' side in single-vertex pieces; all but one
+    # join the centre's part
+    n = 12
+    M = np.zeros((n, n))
+    M[0, 1:] = M[1:, 0] = 1
+    A = _csr(M + np.eye(n))
+    p = a2ls.partition(A.indptr, A.indices, 2)
+    _check_valid(p, n, 2)
+    assert sorted(np.bincount(p)) == [1, n - 1] and _cut(A, p) == 1
+
+
+def test_partition_drives_the_method():
+    # the oracle's two-level method (Eq. 2.4) on a convection-diffusion problem, with the partition
+    # from a2ls_partition: GMRES(30) reaches 1e-8 in a count close to that of the square blocks
+    A = pde.conv_diff_2d(24, 10.0, 0.3)
+    n = A.shape[0]
+    b = pde.rhs_uniform(n, 1)
+    p = a2ls.partition(A.indptr, A.indices, 9, seed=1)
+    its = {}
+    for name, part in (("partitioner", p), ("blocks", pde.block_partition_2d(24, 3))):
+        P = orc.setup(A, part, 1, 4)
+        r = orc.gmres(A, lambda v: orc.apply(P, v), b, rtol=1e-8)
+        assert r.converged and np.linalg.norm(b - A @ r.x) <= 1e-8 * np.linalg.norm(b)
+        its[name] = r.iters
+    assert its["partitioner"] <= its["blocks"] + 3, its
