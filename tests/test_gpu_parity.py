@@ -430,6 +430,26 @@ def test_uneven_subdomains_and_ragged_tiles():
     P2.close()
 
 
+def test_partitioner_output_matches_oracle():
+    # a2ls_partition (host) -> a2ls_setup: the apply with the oracle's coarse basis and the GMRES count
+    A = pde.conv_diff_3d(14, 100.0)
+    part = a2ls().partition(A.indptr, A.indices, 12, seed=4)
+    prob = pde.Problem("part3d", A, part, 1, 5, pde.rhs_uniform(A.shape[0], 4))
+    ref = O.setup(prob.A, prob.part, prob.overlap, prob.nev)
+    P = setup_gpu(prob)
+    P.set_coarse_basis(ref.coarse.W)
+    z = apply_gpu(P, prob.b)
+    zr = O.apply(ref, prob.b)
+    assert np.linalg.norm(z - zr) <= 1e-10 * np.linalg.norm(zr)
+    P2 = setup_gpu(prob)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    it, rr, ok = P2.solve(dev(prob.b), x, 1e-8)
+    res = O.gmres(prob.A, lambda v: O.apply(ref, v), prob.b, rtol=1e-8)
+    assert ok and abs(it - res.iters) <= 1
+    P.close()
+    P2.close()
+
+
 def _stream_case(name):
     if name == "uneven3d":   # 10 BFS regions of 60-300 rows + overlap: several tiles, ragged tails
         A = pde.conv_diff_3d(12, 100.0)
