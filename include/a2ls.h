@@ -148,6 +148,14 @@ typedef struct {
   int32_t eig_block_size;   /* columns of the local eigensolves' blocks: 0 (default) = the larger of
                                nev + max(4, nev / 2) and min(2 nev, 24), at most 32; otherwise that many
                                (at least nev + 1, at most 32) */
+  int32_t static_pivoting;  /* 0 (default): a pivot of a local LU (A_ii or the splitting A~_ii) at most
+                               1e-14 (FP64, double-float) or 1e-12 (FP32) times the subdomain's largest
+                               diagonal entry makes a2ls_setup fail with SINGULAR; 1: it is replaced by
+                               that largest entry and the factorisation goes on (static pivoting: the
+                               factors are those of A_ii plus a diagonal perturbation, which the outer
+                               (F)GMRES corrects; for matrices that are not diagonally dominant, whose
+                               unpivoted LU can meet a zero pivot).  Replacements are counted by
+                               A2LS_Q_PIVOT_BOOSTS.  The coarse LU keeps its SINGULAR check. */
 } a2ls_options;
 
 /* Fills *opt with the defaults listed above.  Never fails. */
@@ -255,6 +263,7 @@ enum {
   A2LS_Q_TUNING = 11,    /* int32[2]: CTA width chosen for the local solves, CUDA graphs held */
   A2LS_Q_EIG_UNCONVERGED = 12, /* int32[2]: subdomains whose eigensolve stopped short of eig_tol, and how
                                   many of them by the stagnation stop (the others ran eig_max_cycles) */
+  A2LS_Q_PIVOT_BOOSTS = 15, /* int32[1]: local LU pivots replaced under a2ls_options::static_pivoting */
   A2LS_Q_EIGRES = 14,    /* double[N]: per subdomain the largest residual ||T u - lambda u|| / |lambda| of
                             the wanted Ritz pairs at its last eigen cycle (0 without a Krylov part) */
   A2LS_Q_ENVELOPE = 13,  /* double[4*N]: per subdomain the flops of an LU confined to the envelope of the

@@ -20,7 +20,7 @@ FP64, FP32, FP32X2, BF16 = 0, 1, 2, 3
 VARIANTS = {"deflated_ras": 0, "deflated_asm": 1, "additive_ras": 2, "additive_asm": 3, "ras": 4, "asm": 5}
 POU = {"boolean": 0, "multiplicity": 1}
 (Q_SIZES, Q_SUBDOMAINS, Q_LUMP, Q_FACTORS, Q_COARSE, Q_EIGVALS, Q_TIMES, Q_EINV, Q_EIGSTATS, Q_LAUNCHES,
- Q_KERNEL_TIMES, Q_TUNING, Q_EIG_UNCONVERGED, Q_ENVELOPE, Q_EIGRES) = range(15)
+ Q_KERNEL_TIMES, Q_TUNING, Q_EIG_UNCONVERGED, Q_ENVELOPE, Q_EIGRES, Q_PIVOT_BOOSTS) = range(16)
 TRACKED_KERNELS = ["lu_local", "lu_splitting", "eig_triangular_solves", "eig_orthogonalisation",
                    "eig_rayleigh_ritz", "coarse_lu", "coarse_inverse", "apply_local_solves"]
 PHASES = ["graph", "extract", "lu", "eig_coarse", "coarse", "setup_total", "solve_total", "apply", "apply_prep"]
@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
                 ("eig_precision", ctypes.c_int32), ("graphs", ctypes.c_int32), ("warm_start", ctypes.c_void_p),
                 ("eig_strict", ctypes.c_int32), ("eig_stall_cycles", ctypes.c_int32),
                 ("tensor_cores", ctypes.c_int32), ("eig_thick_restart", ctypes.c_int32),
-                ("local_solve_kernel", ctypes.c_int32), ("eig_block_size", ctypes.c_int32)]
+                ("local_solve_kernel", ctypes.c_int32), ("eig_block_size", ctypes.c_int32),
+                ("static_pivoting", ctypes.c_int32)]
 
 
 _LIB = None
@@ -302,6 +303,10 @@ class Preconditioner:
     def eig_stalled(self) -> int:
         """Subdomains of eig_unconverged() that the stagnation stop ended."""
         return int(np.frombuffer(self._query(Q_EIG_UNCONVERGED), dtype=np.int32)[1])
+
+    def pivot_boosts(self) -> int:
+        """Local LU pivots replaced under static pivoting (0 without the option)."""
+        return int(np.frombuffer(self._query(Q_PIVOT_BOOSTS), dtype=np.int32)[0])
 
     def eig_residuals(self) -> np.ndarray:
         """(N,): largest relative residual of the wanted Ritz pairs at each subdomain's last cycle."""

@@ -34,7 +34,8 @@ void check_cuda(cudaError_t e, const char* what, const char* file, int line);
 
 // Device-side status words written by kernels (never trap): [0] first error
 // code, [1] the subdomain or row that raised it, [2] auxiliary information.
-enum { ST_CODE = 0, ST_WHERE = 1, ST_AUX = 2, ST_WORDS = 8 };
+// [3] counts the local LU pivots replaced under static pivoting.
+enum { ST_CODE = 0, ST_WHERE = 1, ST_AUX = 2, ST_BOOSTS = 3, ST_WORDS = 8 };
 
 __device__ __forceinline__ void raise_status(int* st, int code, int where, int aux) {
   if (atomicCAS(st + ST_CODE, 0, code) == 0) {
@@ -161,6 +162,7 @@ struct a2ls_handle {
   std::vector<int> h_eigstats;               // 2*N
   int eig_unconverged = 0;                   // subdomains whose eigensolve stopped short of eig_tol
   int eig_stalled = 0;                       // ... of them stopped by the stagnation stop
+  int pivot_boosts = 0;                      // local LU pivots replaced (static pivoting)
   std::vector<double> h_eigres;              // N: worst relative Ritz residual at the last cycle
 
   // apply workspace

@@ -202,6 +202,7 @@ void sync_and_check(a2ls_handle* h, const char* phase) {
   A2LS_CUDA(cudaStreamSynchronize(h->st));
   int s[ST_WORDS];
   A2LS_CUDA(cudaMemcpy(s, h->d_status, sizeof(s), cudaMemcpyDeviceToHost));
+  h->pivot_boosts = s[ST_BOOSTS];
   if (s[ST_CODE] != 0) {
     const int code = s[ST_CODE];
     int zero[ST_WORDS] = {0};
@@ -307,7 +308,11 @@ static void factor_and_coarse(a2ls_handle* h, bool need_coarse, double* times) {
     cudaEvent_t done = nullptr;
     ~SideStream() {
       if (done) cudaEventDestroy(done);
-      if (s) cudaStreamDestroy(s);
+      if (s) {
+        // on an error path the handle frees the factors next: nothing may still write them
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
     }
   } side;
   const bool overlap_local = share && !h->opt.timing;
@@ -398,6 +403,7 @@ void a2ls_default_options(a2ls_options* o) {
   o->eig_thick_restart = 1;
   o->local_solve_kernel = 0;
   o->eig_block_size = 0;
+  o->static_pivoting = 0;
 }
 
 const char* a2ls_last_error(void) { return g_last_error.c_str(); }
@@ -446,6 +452,7 @@ int a2ls_setup(const a2ls_csr* A, const int32_t* partition, int32_t overlap, int
       fail(A2LS_ERR_ARG, "unknown precision %d", o.precision);
     if (o.variant < 0 || o.variant > A2LS_ONE_LEVEL_ASM) fail(A2LS_ERR_ARG, "unknown variant %d", o.variant);
     if (o.pou != A2LS_POU_BOOLEAN && o.pou != A2LS_POU_MULTIPLICITY) fail(A2LS_ERR_ARG, "unknown partition of unity %d", o.pou);
+    if (o.static_pivoting != 0 && o.static_pivoting != 1) fail(A2LS_ERR_ARG, "static_pivoting must be 0 or 1");
     {
       const int k = o.local_solve_kernel;
       if (k != 0 && k != 256 && k != 512 && k != 1024 && k != 1256 && k != 1512 && k != 2256 && k != LS_STREAM &&
@@ -742,6 +749,11 @@ int a2ls_query(a2ls_handle* h, int32_t what, void* out, int64_t capacity, int64_
       case A2LS_Q_EIGRES:
         put(h->h_eigres.data(), sizeof(double) * h->h_eigres.size());
         break;
+      case A2LS_Q_PIVOT_BOOSTS: {
+        const int32_t v = h->pivot_boosts;
+        put(&v, sizeof(v));
+        break;
+      }
       case A2LS_Q_KERNEL_TIMES: {
         collect_kernel_times(h);
         for (int k = 0; k < KT_COUNT; ++k) {

@@ -200,7 +200,7 @@ template <class T, bool TC>
 __global__ void __launch_bounds__(256, TC ? 1 : 2) k_lu(int N, const int* ni, const int* ld, const int64_t* foff,
                                             T* fac, int allow_last_zero, double* last_pivot,
                                             const double* dscale, int* st, const int* sched, const int* nI,
-                                            int phase, const int* off, const int* pf, const int* pg) {
+                                            int phase, const int* off, const int* pf, const int* pg, int boost) {
   using Acc = typename AccOf<T>::type;
   static_assert(!TC || std::is_same<T, dfloat>::value, "tensor-core trailing update is for double-float");
   extern __shared__ __align__(16) unsigned char lu_smem_raw[];
@@ -252,7 +252,12 @@ __global__ void __launch_bounds__(256, TC ? 1 : 2) k_lu(int N, const int* ni, co
         last_pivot[i] = (double)Dm[c * 65 + c];
         Dm[c * 65 + c] = (Acc)scale;
       } else if (fabs((double)Dm[c * 65 + c]) <= tiny) {
-        raise_status(st, A2LS_ERR_SINGULAR, i, k0 + c);
+        // static pivoting: counted and replaced; otherwise an error (the replacement keeps the
+        // remaining steps finite until the host reads the status)
+        if (boost)
+          atomicAdd(st + ST_BOOSTS, 1);
+        else
+          raise_status(st, A2LS_ERR_SINGULAR, i, k0 + c);
         Dm[c * 65 + c] = (Acc)scale;
       }
       rdiag[c] = Acc(1.0) / Dm[c * 65 + c];
@@ -425,7 +430,7 @@ void lu_batched(a2ls_handle* h, T* fac, int allow_last_zero, double* last_pivot,
       A2LS_CUDA(cudaFuncSetAttribute(k_lu<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_lu<T, true><<<h->N, 256, smem, h->st>>>(h->N, h->d_ni, h->d_ld, h->d_foff, fac, allow_last_zero, last_pivot,
                                                 diag_scale, h->d_status, h->d_sched, h->d_nI, phase, h->d_off,
-                                                h->d_pf, h->d_pg);
+                                                h->d_pf, h->d_pg, h->opt.static_pivoting);
       A2LS_LAUNCH();
       return;
     }
@@ -434,7 +439,7 @@ void lu_batched(a2ls_handle* h, T* fac, int allow_last_zero, double* last_pivot,
   A2LS_CUDA(cudaFuncSetAttribute(k_lu<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   k_lu<T, false><<<h->N, 256, smem, h->st>>>(h->N, h->d_ni, h->d_ld, h->d_foff, fac, allow_last_zero, last_pivot,
                                              diag_scale, h->d_status, h->d_sched, h->d_nI, phase, h->d_off, h->d_pf,
-                                             h->d_pg);
+                                             h->d_pg, h->opt.static_pivoting);
   A2LS_LAUNCH();
 }
 

@@ -450,6 +450,40 @@ def test_partitioner_output_matches_oracle():
     P2.close()
 
 
+def _zero_pivot_problem():
+    """Convection-diffusion with a zero diagonal at each part's first interior node: not diagonally
+    dominant, and the unpivoted LU of every A_ii and A~_ii meets an exact zero as its first pivot."""
+    m = 24
+    A = pde.conv_diff_2d(m, 10.0, 0.3).tolil()
+    part = pde.block_partition_2d(m, 3)
+    for p in range(9):
+        A[int(np.nonzero(part == p)[0].min()), int(np.nonzero(part == p)[0].min())] = 0.0
+    A = sp.csr_matrix(A)
+    A.sort_indices()
+    return pde.Problem("zero_pivots", A, part, 1, 4, pde.rhs_uniform(A.shape[0], 2))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_static_pivoting_solves_what_unpivoted_lu_rejects(precision):
+    mod = a2ls()
+    prob = _zero_pivot_problem()
+    with pytest.raises(mod.A2lsError) as e:
+        setup_gpu(prob, precision=precision)
+    assert e.value.code == mod.A2LS_ERR_SINGULAR
+    P = setup_gpu(prob, precision=precision, static_pivoting=1)
+    assert P.pivot_boosts() >= 9  # at least the first pivot of each subdomain's shared interior block
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    it, rr, ok = P.solve(dev(prob.b), x, 1e-8)
+    xr = x.cpu().numpy()
+    assert ok and np.linalg.norm(prob.b - prob.A @ xr) <= 1.01e-8 * np.linalg.norm(prob.b)
+    # the oracle's partially pivoted factors need 13 iterations; the perturbed factors (an FP64 replay
+    # of the replacement on the CPU: 26) need more but stay within a small multiple
+    ref = O.setup(prob.A, prob.part, prob.overlap, prob.nev)
+    res = O.gmres(prob.A, lambda v: O.apply(ref, v), prob.b, rtol=1e-8)
+    assert it <= 3 * res.iters + 5
+    P.close()
+
+
 def _stream_case(name):
     if name == "uneven3d":   # 10 BFS regions of 60-300 rows + overlap: several tiles, ragged tails
         A = pde.conv_diff_3d(12, 100.0)

@@ -31,6 +31,7 @@ def test_exports_every_declared_symbol(lib):
 def test_default_options(lib):
     o = a2ls.default_options()
     assert (o.precision, o.variant, o.pou, o.restart, o.max_it, o.flexible) == (0, 0, 0, 30, 1000, -1)
+    assert (o.eig_block_size, o.static_pivoting) == (0, 0)
 
 
 def test_argument_errors_without_device(lib):
