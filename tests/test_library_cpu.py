@@ -48,6 +48,28 @@ def test_argument_errors_without_device(lib):
     assert lib.a2ls_trim_memory() == 0  # no pool exists before the first setup on a device
 
 
+@pytest.mark.parametrize("field,value,words", [
+    ("precision", 9, b"precision"), ("variant", 17, b"variant"), ("pou", 5, b"partition of unity"),
+    ("static_pivoting", 2, b"static_pivoting"), ("local_solve_kernel", 7, b"local_solve_kernel"),
+])
+def test_option_errors_without_device(lib, field, value, words):
+    # options are checked before the CSR arrays are touched: placeholder pointers are never read
+    csr = a2ls.CSR(4, 4, 8, 8, 8)
+    o = a2ls.default_options(**{field: value})
+    h = ctypes.c_void_p()
+    rc = lib.a2ls_setup(ctypes.byref(csr), ctypes.c_void_p(8), 1, 2, ctypes.byref(o), ctypes.byref(h))
+    assert rc == a2ls.A2LS_ERR_ARG and not h.value
+    assert words in lib.a2ls_last_error()
+
+
+def test_streaming_local_solves_refused_for_fp64_without_device(lib):
+    csr = a2ls.CSR(4, 4, 8, 8, 8)
+    o = a2ls.default_options(precision="fp64", local_solve_kernel=3000)
+    h = ctypes.c_void_p()
+    rc = lib.a2ls_setup(ctypes.byref(csr), ctypes.c_void_p(8), 1, 2, ctypes.byref(o), ctypes.byref(h))
+    assert rc == a2ls.A2LS_ERR_ARG and b"FP32 or BF16" in lib.a2ls_last_error()
+
+
 @pytest.fixture(scope="module")
 def small_eig_exe(tmp_path_factory):
     gxx = shutil.which("g++")
