@@ -70,6 +70,22 @@ def test_streaming_local_solves_refused_for_fp64_without_device(lib):
     assert rc == a2ls.A2LS_ERR_ARG and b"FP32 or BF16" in lib.a2ls_last_error()
 
 
+def test_c_program_compiles_links_and_calls_the_abi(lib, tmp_path):
+    # include/a2ls.h as strict C99 (no C++ in the header), C linkage of the exported symbols, and the
+    # entry points that need no GPU: default options, a2ls_partition, argument errors
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    exe = str(tmp_path / "c_consumer")
+    libdir = os.path.dirname(_build.LIB)
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(os.path.dirname(HERE), "include"), os.path.join(HERE, "cpp", "c_consumer.c"),
+                    "-L", libdir, "-lA2LS", "-Wl,-rpath," + libdir, "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "FAILED" not in r.stdout and r.stdout.count("ok:") >= 10
+
+
 @pytest.fixture(scope="module")
 def small_eig_exe(tmp_path_factory):
     gxx = shutil.which("g++")
