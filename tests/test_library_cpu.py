@@ -1,6 +1,7 @@
 """CPU-side checks of the CUDA library: it builds for sm_103a, loads, exports
 every function include/a2ls.h declares, rejects bad arguments before touching
-a device, and its small dense eigensolver (host-compiled) agrees with LAPACK."""
+a device, links into a strict C99 program, and its small dense eigensolver
+(host-compiled) agrees with LAPACK."""
 import ctypes
 import os
 import shutil
