@@ -266,6 +266,18 @@ def apply_bytes(P, prob, fac_bytes: int) -> dict:
     return {"apply": total, "local_kernel": local_kernel}
 
 
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest value over the ranks (the slowest replica sets the step time of the job); the
+    tensor lives on `device` (the rank's GPU under NCCL, the host under gloo)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args, rank: int, world: int, device):
     import numpy as np
     import torch
@@ -334,11 +346,7 @@ def run_ours(args, rank: int, world: int, device):
         mixed = timed("fp32", args.steps, args.warmup, timing=1)
     ms_mixed = [i["ms"] for i in mixed]
     step_ms = statistics.mean(ms_mixed)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([step_ms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(step_ms, world, device)
     x_last = None
     # accuracy of the last mixed solve, checked on the host in FP64
     info, P, x_last = one_step("fp32", 1, keep=True)

@@ -1,8 +1,11 @@
 """CPU checks of bench.py: the reference arm (the oracle timed on the host cores) prints the JSON
-line of the bench contract, and the roofline entries scale the measured per-subdomain DRAM traffic
-by the launch's subdomains and divide the algorithmic work by the measured launch time."""
+line of the bench contract, alone and as rank 0 of two torchrun ranks; the step time of a
+multi-rank job is the largest over the ranks (two gloo ranks); and the roofline entries scale the
+measured per-subdomain DRAM traffic by the launch's subdomains and divide the algorithmic work by the
+measured launch time."""
 import json
 import os
+import socket
 import subprocess
 import sys
 
@@ -46,3 +49,52 @@ def test_roofline_entry_arithmetic():
     e = bench.roofline_entry("apply_local_solves", 2, 1.0, 2e9, 6780.0)
     assert e["bound"] == "hbm" and e["achieved"] == pytest.approx(2000.0)
     assert e["frac"] == pytest.approx(2000.0 / 6780.0)
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _max_over_ranks_worker(rank: int, world: int, port: int, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        out.put((rank, bench.max_over_ranks([3.5, 7.25][rank], world)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_step_time_is_the_largest_over_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_max_over_ranks_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(out.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert got == {0: 7.25, 1: 7.25}
+
+
+def test_single_rank_needs_no_process_group():
+    import bench
+    assert bench.max_over_ranks(2.5, 1) == 2.5
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    # two ranks on one node: rank 0 times the oracle and prints the line, rank 1 exits 0 without work
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(_free_port()),
+                        os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1",
+                        "--warmup", "0", "--workload", "c3_small"],
+                       capture_output=True, text=True, timeout=900, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1 and lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2
