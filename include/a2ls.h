@@ -235,8 +235,8 @@ int a2ls_trim_memory(void);
  *                       recursion levels run on up to 16 host threads; the result does not depend on
  *                       their scheduling.
  * Copy part to the device for a2ls_setup.  Errors: ARG (n < 1, nparts outside [1, n], NULL pointers,
- * rowptr not starting at 0 or decreasing, column index outside [0, n)); the caller's buffers are
- * only read, except part.
+ * rowptr not starting at 0 or decreasing, column index outside [0, n)), OOM (host memory); the
+ * caller's buffers are only read, except part.
  */
 int a2ls_partition(int32_t n, const int32_t* rowptr, const int32_t* colind, int32_t nparts, uint64_t seed,
                    int32_t* part);

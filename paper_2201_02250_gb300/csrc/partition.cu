@@ -18,8 +18,10 @@
 #include <cstdint>
 #include <future>
 #include <limits>
+#include <new>
 #include <numeric>
 #include <queue>
+#include <system_error>
 #include <utility>
 #include <vector>
 
@@ -447,14 +449,16 @@ void recursive_bisection(const WGraph& g, const std::vector<int>& orig, int k, i
     recursive_bisection(h, horig, s == 0 ? k0 : k - k0, s == 0 ? first : first + k0, mix64(seed + 2 + s), part,
                         depth + 1);
   };
+  std::future<void> f0;
   if (depth < PARALLEL_DEPTH && g.n >= PARALLEL_MIN_N) {
-    std::future<void> f0 = std::async(std::launch::async, half, 0);
-    half(1);
-    f0.get();  // rethrows a failure of the other half
-  } else {
-    half(0);
-    half(1);
+    try {
+      f0 = std::async(std::launch::async, half, 0);
+    } catch (const std::system_error&) {  // no thread to be had: the calling thread does both halves
+    }
   }
+  if (!f0.valid()) half(0);
+  half(1);
+  if (f0.valid()) f0.get();  // rethrows a failure of the other half
 }
 
 // Connected parts where the graph allows it: a part whose vertices fall into several pieces
@@ -534,12 +538,16 @@ void partition_graph(int32_t n, const int32_t* rowptr, const int32_t* colind, in
   for (int64_t q = 0; q < rowptr[n]; ++q)
     if (colind[q] < 0 || colind[q] >= n)
       fail(A2LS_ERR_ARG, "a2ls_partition: colind[%lld] = %d outside [0, %d)", (long long)q, colind[q], n);
-  const WGraph g = symmetrised_graph(n, rowptr, colind);
-  std::vector<int> orig(n);
-  std::iota(orig.begin(), orig.end(), 0);
   std::fill(part, part + n, -1);
-  recursive_bisection(g, orig, nparts, 0, mix64(seed), part, 0);
-  connect_parts(g, nparts, part);
+  try {
+    const WGraph g = symmetrised_graph(n, rowptr, colind);
+    std::vector<int> orig(n);
+    std::iota(orig.begin(), orig.end(), 0);
+    recursive_bisection(g, orig, nparts, 0, mix64(seed), part, 0);
+    connect_parts(g, nparts, part);
+  } catch (const std::bad_alloc&) {
+    fail(A2LS_ERR_OOM, "a2ls_partition: out of host memory (n = %d, %d pattern entries)", n, rowptr[n]);
+  }
   std::vector<int64_t> count(nparts, 0);
   for (int i = 0; i < n; ++i) {
     if (part[i] < 0 || part[i] >= nparts) fail(A2LS_ERR_STATE, "a2ls_partition: vertex %d left unassigned", i);
