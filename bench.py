@@ -75,6 +75,9 @@ def parse_args():
     p.add_argument("--local-solve-kernel", type=int, default=0,
                    help="force the apply's local-solve kernel of the mixed form (a2ls_options::local_solve_kernel; "
                         "0 = the autotuner's choice)")
+    p.add_argument("--eig-block-size", type=int, default=0,
+                   help="columns of the local eigensolves' blocks, both forms (a2ls_options::eig_block_size; "
+                        "0 = the library's rule)")
     return p.parse_args()
 
 
@@ -266,6 +269,17 @@ def apply_bytes(P, prob, fac_bytes: int) -> dict:
     return {"apply": total, "local_kernel": local_kernel}
 
 
+def forced_options(args, precision: str) -> dict:
+    """Library options the command line fixes instead of the library's own choice: the local-solve kernel
+    (mixed form only) and the eigen block size (both forms)."""
+    opts = {}
+    if precision != "fp64" and args.local_solve_kernel:
+        opts["local_solve_kernel"] = args.local_solve_kernel
+    if args.eig_block_size:
+        opts["eig_block_size"] = args.eig_block_size
+    return opts
+
+
 def max_over_ranks(value: float, world: int, device=None) -> float:
     """The largest value over the ranks (the slowest replica sets the step time of the job); the
     tensor lives on `device` (the rank's GPU under NCCL, the host under gloo)."""
@@ -304,7 +318,7 @@ def run_ours(args, rank: int, world: int, device):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        extra = {"local_solve_kernel": args.local_solve_kernel} if precision != "fp64" and args.local_solve_kernel else {}
+        extra = forced_options(args, precision)
         P = a2ls.Preconditioner(rowptr, colind, val, part, prob.overlap, prob.nev, stream=stream,
                                 precision=precision, timing=timing, eig_tol=eig_tol, **extra)
         it, rr, ok = P.solve(b, x, 1e-8)
@@ -406,7 +420,7 @@ def run_ours(args, rank: int, world: int, device):
         dev_in = {k2: v.to(device, non_blocking=True) for k2, v in host.items()}
         x = torch.zeros(prob.n, dtype=torch.float64, device=device)
         Pe = a2ls.Preconditioner(dev_in["rowptr"], dev_in["colind"], dev_in["val"], dev_in["part"], prob.overlap,
-                                 prob.nev, stream=stream, precision="fp32")
+                                 prob.nev, stream=stream, precision="fp32", **forced_options(args, "fp32"))
         Pe.solve(dev_in["b"], x, 1e-8)
         xh_pinned.copy_(x, non_blocking=True)
         torch.cuda.synchronize(device)
@@ -527,7 +541,8 @@ def report(args, res, world) -> dict:
         "config": {"workload": workload, "n": prob.n, "nnz": int(prob.A.nnz), "subdomains": int(prob.nparts),
                    "overlap": prob.overlap, "nev": prob.nev, "rtol": 1e-8, "restart": 30,
                    "form": "mixed: FP32 A_ii factors, double-float splittings and eigensolves to 1e-4, FGMRES(30) FP64",
-                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}",
+                   **({"forced_options": forced_options(args, "fp32")} if forced_options(args, "fp32") else {})},
         "iters": mixed[-1]["iters"],
         "true_relres": res["true_relres"],
         "eig_unconverged_subdomains": mixed[-1]["eig_unconverged"],

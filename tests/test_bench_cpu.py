@@ -98,3 +98,13 @@ def test_reference_arm_under_torchrun_prints_once():
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1 and lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2
+
+
+def test_forced_options_only_when_given():
+    import argparse
+    import bench
+    a = argparse.Namespace(local_solve_kernel=0, eig_block_size=0)
+    assert bench.forced_options(a, "fp32") == {} and bench.forced_options(a, "fp64") == {}
+    a = argparse.Namespace(local_solve_kernel=3000, eig_block_size=18)
+    assert bench.forced_options(a, "fp32") == {"local_solve_kernel": 3000, "eig_block_size": 18}
+    assert bench.forced_options(a, "fp64") == {"eig_block_size": 18}  # the streaming kernel is FP32/BF16 only
