@@ -353,13 +353,26 @@ def partition(rowptr, colind, nparts: int, seed: int = 0) -> np.ndarray:
     return part
 
 
+def resolve_partition(A, part, seed: int = 0) -> np.ndarray:
+    """The partition array for A: `part` itself (n part ids), or, when `part` is an int N, the
+    partition of the graph of A + A^T into N parts by a2ls_partition."""
+    if isinstance(part, (int, np.integer)):
+        return partition(A.indptr, A.indices, int(part), seed=seed)
+    p = np.asarray(part, dtype=np.int32)
+    if p.shape != (A.shape[0],):
+        raise ValueError(f"partition has shape {p.shape}, expected ({A.shape[0]},)")
+    return p
+
+
 def from_scipy(A, part, overlap: int, nev: int, device: str = "cuda", **opts):
-    """Upload a scipy CSR matrix and partition, then set up; returns (Preconditioner, device tensors)."""
+    """Upload a scipy CSR matrix and partition, then set up; returns (Preconditioner, device tensors).
+
+    part: n part ids, or an int N to partition the graph of A + A^T into N parts (a2ls_partition)."""
     import torch
     rowptr = torch.as_tensor(np.asarray(A.indptr, dtype=np.int32), device=device)
     colind = torch.as_tensor(np.asarray(A.indices, dtype=np.int32), device=device)
     val = torch.as_tensor(np.asarray(A.data, dtype=np.float64), device=device)
-    p = torch.as_tensor(np.asarray(part, dtype=np.int32), device=device)
+    p = torch.as_tensor(resolve_partition(A, part), device=device)
     P = Preconditioner(rowptr, colind, val, p, overlap, nev, **opts)
     return P, (rowptr, colind, val, p)
 

@@ -246,3 +246,12 @@ def test_partition_drives_the_method():
         assert r.converged and np.linalg.norm(b - A @ r.x) <= 1e-8 * np.linalg.norm(b)
         its[name] = r.iters
     assert its["partitioner"] <= its["blocks"] + 3, its
+
+
+def test_resolve_partition_takes_an_array_or_a_part_count():
+    A = _grid((10, 10))
+    np.testing.assert_array_equal(a2ls.resolve_partition(A, 4), a2ls.partition(A.indptr, A.indices, 4))
+    given = np.arange(100) // 25
+    np.testing.assert_array_equal(a2ls.resolve_partition(A, given), given)
+    with pytest.raises(ValueError):
+        a2ls.resolve_partition(A, np.zeros(99, np.int32))
