@@ -255,3 +255,31 @@ def test_resolve_partition_takes_an_array_or_a_part_count():
     np.testing.assert_array_equal(a2ls.resolve_partition(A, given), given)
     with pytest.raises(ValueError):
         a2ls.resolve_partition(A, np.zeros(99, np.int32))
+
+
+def test_invariants_on_random_patterns():
+    # any pattern, any part count: every vertex in one part, every part non-empty, parts of a
+    # connected graph connected, the same result for the same seed
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=60, deadline=None, derandomize=True)
+    @hyp.given(n=st.integers(2, 300), density=st.floats(0.0, 0.08), k_frac=st.floats(0.0, 1.0),
+               seed=st.integers(0, 2**31 - 1), sym=st.booleans())
+    def check(n, density, k_frac, seed, sym):
+        rng = np.random.default_rng(seed)
+        M = sp.random(n, n, density=density, random_state=rng, format="csr")
+        if sym:
+            M = M + M.T
+        A = _csr(M + sp.identity(n))
+        k = 1 + int(k_frac * (n - 1))
+        p = a2ls.partition(A.indptr, A.indices, k, seed=seed % 1000)
+        _check_valid(p, n, k)
+        np.testing.assert_array_equal(p, a2ls.partition(A.indptr, A.indices, k, seed=seed % 1000))
+        ncomp, _ = connected_components(A, directed=False)
+        if ncomp == 1:
+            for c in range(k):
+                idx = np.nonzero(p == c)[0]
+                assert connected_components(A[idx][:, idx], directed=False)[0] == 1
+
+    check()
