@@ -166,7 +166,8 @@ void a2ls_default_options(a2ls_options* opt);
  *   A         : CSR matrix (device arrays, see a2ls_csr).
  *   partition : device, n int32 values in [0, N); every part non-empty.  This is
  *               the non-overlapping partition Omega_Ii of Section 2 (the paper
- *               obtains it from ParMETIS; here it is an input).
+ *               obtains it from ParMETIS; here it is an input, which
+ *               a2ls_partition can compute on the host).
  *   overlap   : number of adjacency layers delta >= 0 added around each part
  *               (Section 2 defines one layer; delta layers repeat it).
  *   nev       : eigenpairs kept per subdomain (Eq. 3.2; with tau > 0 an upper bound).
